@@ -1,0 +1,309 @@
+#!/usr/bin/env python3
+"""Throughput of the SIMPLE-TS time step (arXiv:1802.04243) on GB300.
+
+One benchmark step = one time step of the whole hot path: loop-2 iterations
+of face densities, energy, pseudo velocities, pressure, velocity correction,
+equation of state and residual reduction (plus the explicit convective terms
+for the explicit scheme), on the 1024 x 256 supersonic channel with one
+square obstacle (implicit upwind, FP64, Mach 2.5, Re 200, 2 loop-2
+iterations per step).  Metric: Mcell-steps/s = nx * ny * steps / second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the channel
+(the method needs no exchange between independent problems): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-steps/s FP64 vs FP32/FP64 mixed at stated error; % of HBM roofline"
+UNIT = "Mcell-steps/s"
+
+# Algorithmic traffic of the assembly kernel per cell and loop-2 iteration:
+# reads u, v, p, T, rho, Gamma of the previous iterate, rho^u, rho^v, and
+# u, v, T, rho of level n-1 (12 doubles); writes T, u^, d^u, v^, d^v (5 doubles).
+ASSEMBLE_BYTES_PER_CELL = 17 * 8
+# FP64 flops the assembly kernel executes per cell and iteration (implicit
+# upwind), from the ncu instruction counts of k_assemble: 2 * DFMA + DMUL +
+# DADD per thread, divided by the cells of the launch.
+ASSEMBLE_FP64_FLOPS_PER_CELL = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    import workloads as W
+    return W.c2_medium()
+
+
+def config_of(case, flush: str):
+    return {"workload": f"{case.name}: {case.nx}x{case.ny} channel, 1 square (side H/4) at L/4, "
+                        f"implicit upwind, Mach {case.mach_in}, Re {case.reynolds:g}, "
+                        f"{case.iters} loop-2 iterations per step",
+            "nx": case.nx, "ny": case.ny, "cells": case.cells, "scheme": "implicit-upwind",
+            "loop2_iters": case.iters, "l2": flush}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- cpu baseline
+
+def oracle_throughput(case, target_s: float = 12.0, max_steps: int = 400):
+    """Time the reference oracle (serial FP64 C) on the host on a bounded
+    number of time steps of the same workload; returns (Mcell-steps/s, steps, seconds)."""
+    import oracle
+    state = oracle.init(case)
+    t0 = time.perf_counter()
+    state = oracle.run(case, state, nsteps=1)[0]
+    t1 = time.perf_counter() - t0
+    n = max(1, min(max_steps, int(target_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(case, state, nsteps=n)
+    dt = time.perf_counter() - t0
+    return case.cells * n / dt / 1e6, n, dt
+
+
+# ------------------------------------------------------------------- ours
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_1802_04243_gb300 as sim
+    from paper_1802_04243_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    case = workload()
+    stream = torch.cuda.current_stream()
+    s = sim.Simulation(case, stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        s.step(1)
+    peak_fp64 = sim.alu_peak_gflops("fp64", 30.0, stream.cuda_stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2 (126 MB)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+
+    s.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clocks:
+        for k in range(args.steps):
+            flush.fill_(float(k))                  # evict the state from L2 between timed steps
+            starts[k].record(stream)
+            s.step(1)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    prof = s.profile_read()
+    s.profile(False)
+    res, iters, st = s.residuals()
+
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = case.cells * args.steps * world / (total_ms * 1e-3) / 1e6
+
+    # end to end through the C ABI with host buffers: every step uploads its
+    # input state from pinned host memory and reads the new state and the
+    # residuals back
+    host = {k: torch.from_numpy(v).pin_memory() for k, v in s.fields().items()}
+    h2d = sum(v.numel() * 8 for v in host.values())
+    d2h = h2d + 4 * 8
+    views = {k: v.numpy() for k, v in host.items()}
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    for _ in range(2):
+        s.set_fields(views); s.step(1)
+        for k in views: s.field(k, out=views[k])
+        s.residuals()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_fields(views)
+        s.step(1)
+        for k in views:
+            s.field(k, out=views[k])
+        s.residuals()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = case.cells * e2e_steps * world / float(te.item()) / 1e6
+    s.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    asm_ms, asm_n = prof["assemble"]
+    asm_avg_s = asm_ms / max(asm_n, 1) * 1e-3
+    launches = sum(n for _, n in prof.values())
+    if ASSEMBLE_FP64_FLOPS_PER_CELL:
+        ach = ASSEMBLE_FP64_FLOPS_PER_CELL * case.cells / asm_avg_s / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak_fp64 / 1e3, 4), "unit": "TFLOP/s",
+                "frac": round(ach / (peak_fp64 / 1e3), 4), "traffic": None,
+                "kernel": "k_assemble", "peak_source": "FP64 FMA probe measured in this run (simplets_alu_peak)"}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+        ach = ASSEMBLE_BYTES_PER_CELL * case.cells / asm_avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": None, "kernel": "k_assemble"}
+    roof["kernel_ms_avg"] = round(asm_avg_s * 1e3, 5)
+    roof["fp64_peak_gflops_measured"] = round(peak_fp64, 1)
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, n, secs = oracle_throughput(case)
+        cpu = {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} time steps of the same {case.nx}x{case.ny} channel from its seeded start "
+                         f"({secs:.1f} s, serial FP64 C oracle)"}
+
+    line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**config_of(case, "flushed between timed steps (256 MB write)"),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "gpu_launches": int(launches),
+            "kernels": {k: {"ms": round(ms, 4), "launches": n} for k, (ms, n) in prof.items() if n},
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks.summary(),
+            "residuals_last_step": [float(x) for x in res], "impl": "ours"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# -------------------------------------------------------------- reference
+
+def run_reference(args, rank, world):
+    """The reference arm: the serial FP64 oracle on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    case = workload()
+    state = oracle.init(case)
+    for _ in range(args.warmup):
+        t0 = time.perf_counter()
+        state = oracle.run(case, state, nsteps=1)[0]
+        t_step = time.perf_counter() - t0
+    budget = 150.0
+    n = args.steps if args.warmup == 0 or args.steps * t_step <= budget else max(1, int(budget / t_step))
+    t0 = time.perf_counter()
+    oracle.run(case, state, nsteps=n)
+    secs = time.perf_counter() - t0
+    value = case.cells * n / secs / 1e6
+    sample = (f"{n} of the {args.steps} requested time steps of the {case.nx}x{case.ny} channel "
+              f"({secs:.1f} s, serial FP64 C oracle on one host core)")
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(secs / n * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(case, "not applicable (host)"), "impl": "reference",
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "kind": "oracle", "cores": 1, "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * simplets.h -- C ABI of the GB300 implementation of the SIMPLE-TS time step
+ * (K. S. Shterev, "GPU implementation of algorithm SIMPLE-TS for calculation
+ * of unsteady, viscous, compressible and heat-conductive gas flows",
+ * arXiv:1802.04243).
+ *
+ * The library advances the 2D Navier-Stokes-Fourier system of Section 2
+ * (Eqs. pl4, pl2, pl3, pl6, pl5) on a staggered Cartesian finite-volume grid
+ * (Section 3.2, "Cell volume") with the SIMPLE-TS Jacobi iteration of
+ * Section 3.1 (Figs. 1 and 2, GPU column).  Every step of the sweep runs in
+ * the library's CUDA kernels on the device; the host only enqueues work.
+ *
+ * Conventions
+ *  - Every call returns a sim_status; nothing throws across the ABI.
+ *  - A sim_t owns all the device memory it uses; the caller owns every host
+ *    pointer it passes.  Input arrays are read during the call only.
+ *  - Host field arrays are row-major with x fastest, in the logical shape
+ *    (no ghost cells):  u: ny x (nx+1)   (u[j*(nx+1)+i], face i of row j)
+ *                       v: (ny+1) x nx   (v[j*nx+i], face j of column i)
+ *                       p, T, rho, Gamma: ny x nx.
+ *  - Lengths are in units of the obstacle side, velocities in units of
+ *    sqrt(2 R T0), p and T in units of the inflow pressure and the wall
+ *    temperature (Section 4).
+ *  - sim_step is asynchronous on the stream given to sim_create (NULL: the
+ *    legacy default stream); sim_fields, sim_residuals, sim_set_fields and
+ *    sim_destroy synchronise with it.
+ *  - After SIM_EDIVERGED the handle is in an error state; every call except
+ *    sim_set_fields, sim_fields, sim_last_error and sim_destroy then returns
+ *    SIM_ESTATE.  sim_set_fields of all four fields clears the state.
+ */
+#ifndef SIMPLETS_H
+#define SIMPLETS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sim_s *sim_t;
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_EINVAL = 1,      /* invalid argument or problem description */
+    SIM_ENOMEM = 2,      /* device or pinned host allocation failed */
+    SIM_ECUDA = 3,       /* a CUDA call failed (see sim_last_error) */
+    SIM_EDIVERGED = 4,   /* a residual became NaN or infinite */
+    SIM_ETIMEOUT = 5,    /* reserved */
+    SIM_ESTATE = 6       /* handle is in the error state after a divergence */
+} sim_status;
+
+/* side indices and side kinds */
+enum { SIM_W = 0, SIM_E = 1, SIM_S = 2, SIM_N = 3 };
+enum { SIM_BC_WALL = 0, SIM_BC_SYMMETRY = 1, SIM_BC_INFLOW = 2, SIM_BC_OUTFLOW = 3 };
+/* gas models */
+enum { SIM_GAS_IDEAL_RE = 0, SIM_GAS_HARD_SPHERE_KN = 1 };
+/* scheme flags for sim_step: time treatment of convection | spatial scheme */
+enum { SIM_EXPLICIT = 0, SIM_IMPLICIT = 1, SIM_UPWIND = 0, SIM_TVD = 2 };
+/* arithmetic of the sweep */
+enum { SIM_FP64 = 0, SIM_MIXED = 1 };
+/* field ids */
+enum { SIM_FIELD_U = 0, SIM_FIELD_V = 1, SIM_FIELD_P = 2, SIM_FIELD_T = 3,
+       SIM_FIELD_RHO = 4, SIM_FIELD_GAMMA = 5 };
+
+/* Grid (Section 3.2): nx x ny cells.  dx/dy give the nx (ny) cell sizes; when
+ * NULL the grid is uniform with sizes lx/nx and ly/ny.  nx, ny >= 4. */
+typedef struct {
+    int nx, ny;
+    double lx, ly;
+    const double *dx, *dy;
+} sim_grid;
+
+/* Gas and flow (Sections 2 and 4).
+ * SIM_GAS_IDEAL_RE: gamma, prandtl, visc_exp (Gamma = Gamma^lambda = T^visc_exp),
+ *   inflow Mach number and Reynolds number on the obstacle side give
+ *   A = 1/2, U_in = M sqrt(gamma/2), B = U_in/Re, C^T1 = B/Pr,
+ *   C^T2 = 2B(gamma-1)/gamma, C^T3 = (gamma-1)/gamma.
+ * SIM_GAS_HARD_SPHERE_KN: Eq. pl37 with Knudsen number kn (gamma = 5/3,
+ *   Pr = 2/3, Gamma = sqrt(T)); mach_in sets U_in.
+ * gx, gy: body force per unit mass (the rho g terms of Eqs. pl2, pl3). */
+typedef struct {
+    int model;
+    double gamma, prandtl, visc_exp;
+    double mach_in, reynolds, kn;
+    double gx, gy;
+} sim_gas;
+
+/* Boundaries, obstacles, start state and loop-2 control.
+ * side_kind: per side (W, E, S, N).  INFLOW only on W, OUTFLOW only on E;
+ *   S and N are WALL or SYMMETRY.  A wall is no-slip and isothermal (the
+ *   zeta = tau = 0 limit of Eqs. pl38, pl39) with tangential velocity
+ *   side_vel and temperature side_T.
+ * Obstacles: n_rect cell rectangles [i0, j0, i1, j1) (4 ints each), at
+ *   least 2 cells wide and at least 2 cells from every side; body_T is their
+ *   wall temperature.
+ * inflow_u/T/p: optional per-row inflow profile (ny entries); default
+ *   U_in, 1, 1.
+ * dt: time step; <= 0 selects cfl * min(dx, dy) / (U_ref + sqrt(gamma/2))
+ *   with cfl (default 0.2 when <= 0).
+ * iters: loop-2 iterations per step (>= 1); tol > 0 ends loop 2 early once
+ *   every residual <= tol (this reads the residuals back every iteration).
+ * seed, perturb: start state = inflow state of the row (rest when W is not an
+ *   inflow) times (1 + perturb xi), xi in [-1, 1) from splitmix64 of
+ *   (seed ^ (field<<40 + j<<20 + i)); v = perturb U_in xi.
+ * precision: SIM_FP64 or SIM_MIXED. */
+typedef struct {
+    int side_kind[4];
+    double side_vel[4];
+    double side_T[4];
+    double body_T;
+    int n_rect;
+    const int *rect;
+    const double *inflow_u, *inflow_T, *inflow_p;
+    double dt, cfl;
+    int iters;
+    double tol;
+    uint64_t seed;
+    double perturb;
+    int precision;
+} sim_bc;
+
+/* Validate the problem, allocate every device buffer and set the start state.
+ * stream: a cudaStream_t (may be NULL).  On success *out owns the handle.
+ * Errors: SIM_EINVAL (bad description), SIM_ENOMEM, SIM_ECUDA. */
+sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const sim_bc *bc,
+                      void *stream, sim_t *out);
+
+/* Advance n_steps time steps (Section 3.1, loop 1) with `scheme`
+ * (SIM_EXPLICIT or SIM_IMPLICIT, or-ed with SIM_UPWIND or SIM_TVD).  Each step
+ * runs the explicit convective terms (explicit scheme only; Eqs. pl15_11,
+ * pl31_1) and then `iters` loop-2 iterations: face densities (Eqs. pl8-pl11),
+ * temperature (Eqs. pl28-pl33), pseudo velocities (Eqs. pl14-pl16, pl20,
+ * pl21), pressure (Eqs. pl23, pl24), velocity correction (Eqs. pl18, pl19),
+ * rho = p/T (Eq. pl5) and the residual reduction.  Asynchronous unless
+ * tol > 0.  Errors: SIM_EINVAL (n_steps < 0, bad scheme), SIM_ECUDA,
+ * SIM_EDIVERGED (tol > 0 only), SIM_ESTATE. */
+sim_status sim_step(sim_t sim, int n_steps, int scheme);
+
+/* Copy one field of the current state into host_dst (n doubles, the logical
+ * shape of that field, boundary values included).  Synchronous.
+ * Errors: SIM_EINVAL (bad field or n), SIM_ECUDA. */
+sim_status sim_fields(sim_t sim, int field, double *host_dst, size_t n);
+
+/* Borrow the device array of one field of the current state.  *dev receives
+ * the address of element (i, j) = (0, 0); element (i, j) is at
+ * dev[j * (*pitch) + i] for -2 <= i, j (two ghost layers).  Valid until the
+ * next sim_step, sim_set_fields or sim_destroy.  Errors: SIM_EINVAL. */
+sim_status sim_field_ptr(sim_t sim, int field, void **dev, size_t *pitch);
+
+/* Overwrite the unknowns of one field (u, v, p or T; logical shape) of the
+ * current state from host_src; boundary values follow the boundary rules and
+ * rho, Gamma are recomputed.  Used for restart.  Synchronous.
+ * Errors: SIM_EINVAL, SIM_ECUDA. */
+sim_status sim_set_fields(sim_t sim, int field, const double *host_src, size_t n);
+
+/* Maximum |new - old| of u, v, p, T over the unknowns in the last loop-2
+ * iteration (Section 5: the only data read back per iteration), and the
+ * number of loop-2 iterations of the last step.  Synchronous.
+ * Returns SIM_EDIVERGED if a residual is NaN or infinite. */
+sim_status sim_residuals(sim_t sim, double out[4], int *iters_last_step);
+
+/* Non-dimensional coefficients in use: out[0..8] = A, B, C^T1_f, C^T2_f,
+ * C^T3_f, omega, U_in, dt, cells.  Errors: SIM_EINVAL. */
+sim_status sim_coefficients(sim_t sim, double out[9]);
+
+/* Kernel classes of the sweep, for sim_profile_read. */
+enum { SIM_K_FACES = 0, SIM_K_ASSEMBLE = 1, SIM_K_PRESSURE = 2, SIM_K_VELOCITY = 3, SIM_K_GHOSTS = 4,
+       SIM_K_EXPLICIT = 5, SIM_K_COUNT = 6 };
+
+/* Measurement hooks (not part of the method).  sim_profile(sim, 1) clears the
+ * counters and from then on brackets every kernel launch of sim_step with a
+ * pair of CUDA events on the handle's stream; sim_profile(sim, 0) stops the
+ * event timing.  Launches are counted whether or not timing is on.
+ * Errors: SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA. */
+sim_status sim_profile(sim_t sim, int enable);
+
+/* Launches of kernel class `kernel_class` since the last sim_profile(sim, 1)
+ * (or since sim_create), and their summed event-timed duration in ms (0 when
+ * timing was off).  Synchronous.  Errors: SIM_EINVAL, SIM_ECUDA. */
+sim_status sim_profile_read(sim_t sim, int kernel_class, double *ms, long long *launches);
+
+/* Text of the last error on this handle (never NULL). */
+const char *sim_last_error(sim_t sim);
+
+/* Release every resource of the handle (NULL is a no-op). */
+void sim_destroy(sim_t sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIMPLETS_H */

@@ -1,0 +1,28 @@
+/*
+ * simplets_probe.h -- arithmetic-throughput probe of the device, used as the
+ * ALU roofline of the SIMPLE-TS sweep.
+ *
+ * The paper measures operator cost with a "simplified test code": the energy
+ * equation evaluated on private variables in a loop with no memory traffic
+ * (Section 3.4).  This probe is the same idea reduced to the instruction the
+ * sweep is bound by: independent fused multiply-add chains on registers,
+ * in FP64 (the FP64 path) or FP32 (the mixed path), with no memory traffic.
+ */
+#ifndef SIMPLETS_PROBE_H
+#define SIMPLETS_PROBE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Measure the device's sustained fused-multiply-add rate on `stream`.
+ * kind: 0 = FP64 (DFMA), 1 = FP32 (FFMA).  The kernel fills every SM with
+ * independent FMA chains for about `millis` milliseconds (>= 1) and times
+ * itself with CUDA events.  *gflops receives 2 x FMAs / second / 1e9.
+ * Returns 0 on success, 1 on a bad argument, 3 on a CUDA error.  Synchronous. */
+int simplets_alu_peak(int kind, double millis, void *stream, double *gflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

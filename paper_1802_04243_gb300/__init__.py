@@ -1,0 +1,260 @@
+"""Python binding of libsimplets.so, the GB300 implementation of the SIMPLE-TS
+time step (K. S. Shterev, arXiv:1802.04243).
+
+The binding only marshals arguments: every step of the sweep runs in the
+library's CUDA kernels.  Names follow the C ABI of include/simplets.h.  The
+library is built in-tree (``paper_1802_04243_gb300.build.build()``); loading
+fails loudly when it is missing -- there is no CPU fallback.
+
+PyTorch supplies the CUDA stream (``torch.cuda.current_stream()``) and views
+of borrowed device fields (``Simulation.field_view``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsimplets.so")
+
+# status codes, sides, kinds, schemes, fields (include/simplets.h)
+SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_EDIVERGED, SIM_ETIMEOUT, SIM_ESTATE = range(7)
+SIM_W, SIM_E, SIM_S, SIM_N = range(4)
+SIM_BC_WALL, SIM_BC_SYMMETRY, SIM_BC_INFLOW, SIM_BC_OUTFLOW = range(4)
+SIM_GAS_IDEAL_RE, SIM_GAS_HARD_SPHERE_KN = range(2)
+SIM_EXPLICIT, SIM_IMPLICIT, SIM_UPWIND, SIM_TVD = 0, 1, 0, 2
+SIM_FP64, SIM_MIXED = 0, 1
+FIELDS = {"u": 0, "v": 1, "p": 2, "T": 3, "rho": 4, "gamma": 5}
+KERNELS = {"faces": 0, "assemble": 1, "pressure": 2, "velocity": 3, "ghosts": 4, "explicit": 5}
+STATUS = {0: "SIM_OK", 1: "SIM_EINVAL", 2: "SIM_ENOMEM", 3: "SIM_ECUDA", 4: "SIM_EDIVERGED",
+          5: "SIM_ETIMEOUT", 6: "SIM_ESTATE"}
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+class sim_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+                ("dx", _DP), ("dy", _DP)]
+
+
+class sim_gas(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("gamma", ctypes.c_double), ("prandtl", ctypes.c_double),
+                ("visc_exp", ctypes.c_double), ("mach_in", ctypes.c_double), ("reynolds", ctypes.c_double),
+                ("kn", ctypes.c_double), ("gx", ctypes.c_double), ("gy", ctypes.c_double)]
+
+
+class sim_bc(ctypes.Structure):
+    _fields_ = [("side_kind", ctypes.c_int * 4), ("side_vel", ctypes.c_double * 4),
+                ("side_T", ctypes.c_double * 4), ("body_T", ctypes.c_double),
+                ("n_rect", ctypes.c_int), ("rect", ctypes.POINTER(ctypes.c_int)),
+                ("inflow_u", _DP), ("inflow_T", _DP), ("inflow_p", _DP),
+                ("dt", ctypes.c_double), ("cfl", ctypes.c_double), ("iters", ctypes.c_int),
+                ("tol", ctypes.c_double), ("seed", ctypes.c_uint64), ("perturb", ctypes.c_double),
+                ("precision", ctypes.c_int)]
+
+
+class SimError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+# exported symbols and their signatures (the test of the ABI checks this list
+# against include/simplets.h)
+_SIGNATURES = {
+    "sim_create": ([ctypes.POINTER(sim_grid), ctypes.POINTER(sim_gas), ctypes.POINTER(sim_bc), ctypes.c_void_p,
+                    ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "sim_step": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "sim_fields": ([ctypes.c_void_p, ctypes.c_int, _DP, ctypes.c_size_t], ctypes.c_int),
+    "sim_field_ptr": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                       ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "sim_set_fields": ([ctypes.c_void_p, ctypes.c_int, _DP, ctypes.c_size_t], ctypes.c_int),
+    "sim_residuals": ([ctypes.c_void_p, _DP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "sim_coefficients": ([ctypes.c_void_p, _DP], ctypes.c_int),
+    "sim_profile": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "sim_profile_read": ([ctypes.c_void_p, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+    "sim_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
+    "simplets_alu_peak": ([ctypes.c_int, ctypes.c_double, ctypes.c_void_p, _DP], ctypes.c_int),
+    "sim_destroy": ([ctypes.c_void_p], None),
+}
+
+
+def load(path: Optional[str] = None):
+    """Load libsimplets.so (built by build.build()).  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with paper_1802_04243_gb300.build.build() "
+                               "(the CUDA library is required; there is no CPU fallback)")
+        lib = ctypes.CDLL(p)
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_DP)
+
+
+class _Desc:
+    """ctypes descriptions of a workload case, with the arrays they point to."""
+
+    def __init__(self, case):
+        c = case
+        self.keep = []
+
+        def arr(x, dtype=np.float64):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(x, dtype=dtype))
+            self.keep.append(a)
+            return a
+
+        dx, dy = arr(c.dx), arr(c.dy)
+        self.grid = sim_grid(c.nx, c.ny, c.lx, c.ly, _ptr(dx), _ptr(dy))
+        self.gas = sim_gas(c.gas_model, c.gamma, c.prandtl, c.visc_exp, c.mach_in, c.reynolds, c.kn, c.gx, c.gy)
+        rect = arr(np.asarray(c.rects, dtype=np.int32).reshape(-1), np.int32) if len(c.rects) else None
+        iu, iT, ip = arr(c.inflow_u), arr(c.inflow_T), arr(c.inflow_p)
+        bc = sim_bc()
+        for k in range(4):
+            bc.side_kind[k] = int(c.side_kind[k])
+            bc.side_vel[k] = float(c.side_vel[k])
+            bc.side_T[k] = float(c.side_T[k])
+        bc.body_T = c.body_T
+        bc.n_rect = len(c.rects)
+        bc.rect = rect.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if rect is not None else None
+        bc.inflow_u, bc.inflow_T, bc.inflow_p = _ptr(iu), _ptr(iT), _ptr(ip)
+        bc.dt, bc.cfl, bc.iters, bc.tol = c.dt, c.cfl, c.iters, c.tol
+        bc.seed, bc.perturb, bc.precision = c.seed, c.perturb, c.precision
+        self.bc = bc
+
+
+def scheme_of(implicit: bool, tvd: bool) -> int:
+    return (SIM_IMPLICIT if implicit else SIM_EXPLICIT) | (SIM_TVD if tvd else SIM_UPWIND)
+
+
+def alu_peak_gflops(kind: str = "fp64", millis: float = 50.0, stream: Optional[int] = None) -> float:
+    """Sustained FMA rate of the device (include/simplets_probe.h), in GFLOP/s."""
+    out = ctypes.c_double()
+    rc = load().simplets_alu_peak(0 if kind == "fp64" else 1, float(millis), ctypes.c_void_p(stream or 0),
+                                  ctypes.byref(out))
+    if rc:
+        raise SimError(SIM_ECUDA, f"simplets_alu_peak failed ({rc})")
+    return out.value
+
+
+class _CudaArray:
+    """__cuda_array_interface__ view of a borrowed device array."""
+
+    def __init__(self, ptr: int, shape, strides_bytes):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (ptr, False),
+                                         "strides": tuple(strides_bytes), "version": 2}
+
+
+class Simulation:
+    """One SIMPLE-TS problem on the GPU (owns a sim_t)."""
+
+    def __init__(self, case, stream: Optional[int] = None):
+        self.lib = load()
+        self.case = case
+        self._desc = _Desc(case)
+        h = ctypes.c_void_p()
+        st = self.lib.sim_create(ctypes.byref(self._desc.grid), ctypes.byref(self._desc.gas),
+                                 ctypes.byref(self._desc.bc), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if st != SIM_OK:
+            raise SimError(st, "sim_create failed (invalid description or no device)")
+        self.handle = h
+        self.scheme = scheme_of(case.implicit, case.tvd)
+
+    def _check(self, st: int):
+        if st != SIM_OK:
+            raise SimError(st, self.lib.sim_last_error(self.handle).decode())
+
+    def step(self, n: int = 1, scheme: Optional[int] = None):
+        self._check(self.lib.sim_step(self.handle, int(n), self.scheme if scheme is None else int(scheme)))
+
+    def shape(self, name: str):
+        nx, ny = self.case.nx, self.case.ny
+        return {"u": (ny, nx + 1), "v": (ny + 1, nx)}.get(name, (ny, nx))
+
+    def field(self, name: str, out: Optional[np.ndarray] = None) -> np.ndarray:
+        a = np.empty(self.shape(name)) if out is None else out
+        self._check(self.lib.sim_fields(self.handle, FIELDS[name], a.ctypes.data_as(_DP), a.size))
+        return a
+
+    def fields(self, names: Sequence[str] = ("u", "v", "p", "T")) -> Dict[str, np.ndarray]:
+        return {k: self.field(k) for k in names}
+
+    def set_field(self, name: str, values: np.ndarray):
+        a = np.ascontiguousarray(values, dtype=np.float64)
+        if a.shape != self.shape(name):
+            raise ValueError(f"{name}: shape {a.shape} != {self.shape(name)}")
+        self._check(self.lib.sim_set_fields(self.handle, FIELDS[name], a.ctypes.data_as(_DP), a.size))
+
+    def set_fields(self, state: Dict[str, np.ndarray]):
+        for k in ("u", "v", "p", "T"):
+            if k in state:
+                self.set_field(k, state[k])
+
+    def residuals(self):
+        out = np.zeros(4)
+        it = ctypes.c_int(0)
+        st = self.lib.sim_residuals(self.handle, out.ctypes.data_as(_DP), ctypes.byref(it))
+        if st not in (SIM_OK, SIM_EDIVERGED):
+            self._check(st)
+        return out, it.value, st
+
+    def coefficients(self) -> Dict[str, float]:
+        out = np.zeros(9)
+        self._check(self.lib.sim_coefficients(self.handle, out.ctypes.data_as(_DP)))
+        return dict(zip(("A", "B", "CT1f", "CT2f", "CT3f", "omega", "u_in", "dt", "cells"), out.tolist()))
+
+    def field_view(self, name: str):
+        """Zero-copy torch view (including the two ghost layers) of a device field
+        of the current state; valid until the next step."""
+        import torch
+        dev = ctypes.c_void_p()
+        pitch = ctypes.c_size_t()
+        self._check(self.lib.sim_field_ptr(self.handle, FIELDS[name], ctypes.byref(dev), ctypes.byref(pitch)))
+        ny, nx = self.shape(name)
+        base = dev.value - (2 * pitch.value + 2) * 8
+        arr = _CudaArray(base, (ny + 4, nx + 4), (pitch.value * 8, 8))
+        return torch.as_tensor(arr, device="cuda")
+
+    def profile(self, enable: bool = True):
+        self._check(self.lib.sim_profile(self.handle, int(bool(enable))))
+
+    def profile_read(self) -> Dict[str, tuple]:
+        out = {}
+        for name, k in KERNELS.items():
+            ms = ctypes.c_double()
+            n = ctypes.c_longlong()
+            self._check(self.lib.sim_profile_read(self.handle, k, ctypes.byref(ms), ctypes.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.sim_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

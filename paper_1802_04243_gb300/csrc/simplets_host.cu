@@ -1,0 +1,719 @@
+// simplets_host.cu -- host side of the C ABI declared in include/simplets.h:
+// problem validation, the non-dimensional coefficients, geometry flags, the
+// start state, device memory and the loop-1 / loop-2 driver of SIMPLE-TS
+// (arXiv:1802.04243, Section 3.1).  Every arithmetic step of the sweep runs in
+// the kernels of sweep_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "simplets.h"
+#include "stg_common.cuh"
+
+using namespace stg;
+
+namespace {
+
+enum CellKind { K_FLUID, K_SOLID, K_WALL, K_SYMM, K_INFLOW, K_OUTFLOW };
+
+struct Problem {
+    int nx, ny;
+    std::vector<double> dx, dy;                // logical cell sizes
+    int side_kind[4];
+    double side_vel[4], side_T[4], body_T;
+    std::vector<int> rect;                     // 4 per obstacle
+    std::vector<double> in_u, in_T, in_p;      // per row
+    double u_in, gamma;
+    Coef k;
+    int iters;
+    double tol;
+    uint64_t seed;
+    double perturb;
+    int precision;
+};
+
+}  // namespace
+
+struct sim_s {
+    Problem pb;
+    int pitch = 0;
+    size_t nelem = 0;                          // elements of one extended field
+    cudaStream_t stream = nullptr;
+    Geo geo{};
+    Sides sides{};
+    Level lv[3]{};
+    Work work{};
+    double *d_pool = nullptr;                  // every double array of the handle
+    uint16_t *d_flag = nullptr;
+    double *d_axis = nullptr;
+    double *d_stage = nullptr;                 // logical-shape staging array
+    unsigned long long *h_res = nullptr;       // pinned copy of the residuals
+    int cur = 0;                               // level holding the current state
+    int last_iters = 0;
+    bool diverged = false;
+    unsigned set_mask = 0;
+    // measurement hooks
+    long long launches[SIM_K_COUNT] = {0};
+    bool timing = false;
+    struct Mark { int cls; cudaEvent_t e0, e1; };
+    std::vector<Mark> marks;                   // recorded launches (timing on)
+    std::vector<cudaEvent_t> spare;            // reusable events
+    char err[256] = {0};
+};
+
+namespace {
+
+sim_status fail(sim_t s, sim_status st, const char *fmt, ...)
+{
+    if (s) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(s->err, sizeof s->err, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define CUDA_TRY(sim, call)                                                          \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return fail(sim, SIM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+// splitmix64 (Steele, Lea and Flood, 2014) used as a counter hash of
+// (seed, field, i, j); returns a double in [-1, 1).
+double hash_uniform(uint64_t seed, int field, int i, int j)
+{
+    uint64_t z = seed ^ (((uint64_t)field << 40) + ((uint64_t)j << 20) + (uint64_t)i);
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return (double)(z >> 11) * 0x1.0p-53 * 2.0 - 1.0;
+}
+
+// Non-dimensional parameters (Section 4 scaling; Eq. pl37 for the hard-sphere
+// gas).  The energy constants are the c_v-form C^Tk_f = gamma C^Tk (C^T3_f
+// with a minus sign), the form Eq. pl29 uses.
+sim_status derive_coefficients(const sim_gas *gas, Problem &pb, sim_t err)
+{
+    double ct1, ct2, ct3, gm;
+    Coef &k = pb.k;
+    k.A = 0.5;
+    if (gas->model == SIM_GAS_HARD_SPHERE_KN) {
+        const double pi = 3.14159265358979323846;
+        gm = 5.0 / 3.0;
+        k.omega = 0.5;
+        pb.u_in = gas->mach_in * std::sqrt(gm / 2.0);
+        k.B = 5.0 * std::sqrt(pi) * gas->kn / 16.0;
+        ct1 = gas->kn * std::sqrt(pi * 225.0 / 1024.0);
+        ct2 = std::sqrt(pi) * gas->kn / 4.0;
+        ct3 = 2.0 / 5.0;
+    } else if (gas->model == SIM_GAS_IDEAL_RE) {
+        if (!(gas->reynolds > 0.0) || !(gas->gamma > 1.0) || !(gas->prandtl > 0.0))
+            return fail(err, SIM_EINVAL, "ideal gas needs reynolds > 0, gamma > 1, prandtl > 0");
+        gm = gas->gamma;
+        k.omega = gas->visc_exp;
+        pb.u_in = gas->mach_in * std::sqrt(gm / 2.0);
+        k.B = pb.u_in / gas->reynolds;
+        ct1 = k.B / gas->prandtl;
+        ct2 = 2.0 * k.B * (gm - 1.0) / gm;
+        ct3 = (gm - 1.0) / gm;
+    } else {
+        return fail(err, SIM_EINVAL, "unknown gas model %d", gas->model);
+    }
+    pb.gamma = gm;
+    k.CT1f = gm * ct1;
+    k.CT2f = gm * ct2;
+    k.CT3f = -gm * ct3;
+    k.gx = gas->gx;
+    k.gy = gas->gy;
+    return SIM_OK;
+}
+
+sim_status read_problem(const sim_grid *gr, const sim_gas *gas, const sim_bc *bc, Problem &pb, sim_t err)
+{
+    if (!gr || !gas || !bc)
+        return fail(err, SIM_EINVAL, "null description");
+    if (gr->nx < 4 || gr->ny < 4 || gr->nx >= (1 << 20) || gr->ny >= (1 << 20))
+        return fail(err, SIM_EINVAL, "grid %d x %d outside [4, 2^20)", gr->nx, gr->ny);
+    pb.nx = gr->nx;
+    pb.ny = gr->ny;
+    pb.dx.resize(pb.nx);
+    pb.dy.resize(pb.ny);
+    for (int i = 0; i < pb.nx; i++) pb.dx[i] = gr->dx ? gr->dx[i] : gr->lx / pb.nx;
+    for (int j = 0; j < pb.ny; j++) pb.dy[j] = gr->dy ? gr->dy[j] : gr->ly / pb.ny;
+    for (double d : pb.dx) if (!(d > 0.0) || !std::isfinite(d)) return fail(err, SIM_EINVAL, "cell widths must be positive");
+    for (double d : pb.dy) if (!(d > 0.0) || !std::isfinite(d)) return fail(err, SIM_EINVAL, "cell heights must be positive");
+    for (int s = 0; s < 4; s++) {
+        int kd = bc->side_kind[s];
+        if (kd < 0 || kd > 3) return fail(err, SIM_EINVAL, "side %d: unknown kind %d", s, kd);
+        if (kd == SIM_BC_INFLOW && s != SIM_W) return fail(err, SIM_EINVAL, "inflow only on the west side");
+        if (kd == SIM_BC_OUTFLOW && s != SIM_E) return fail(err, SIM_EINVAL, "outflow only on the east side");
+        pb.side_kind[s] = kd;
+        pb.side_vel[s] = bc->side_vel[s];
+        pb.side_T[s] = bc->side_T[s];
+        if (kd == SIM_BC_WALL && !(bc->side_T[s] > 0.0)) return fail(err, SIM_EINVAL, "wall temperature must be positive");
+    }
+    pb.body_T = bc->body_T;
+    if (bc->n_rect < 0 || (bc->n_rect > 0 && !bc->rect)) return fail(err, SIM_EINVAL, "bad obstacle list");
+    if (bc->n_rect > 0 && !(bc->body_T > 0.0)) return fail(err, SIM_EINVAL, "obstacle temperature must be positive");
+    for (int r = 0; r < bc->n_rect; r++) {
+        const int *q = bc->rect + 4 * r;
+        if (q[0] < 2 || q[1] < 2 || q[2] > pb.nx - 2 || q[3] > pb.ny - 2 || q[2] - q[0] < 2 || q[3] - q[1] < 2)
+            return fail(err, SIM_EINVAL, "obstacle %d [%d,%d,%d,%d) must be >= 2 cells wide and >= 2 cells from the sides",
+                        r, q[0], q[1], q[2], q[3]);
+        pb.rect.insert(pb.rect.end(), q, q + 4);
+    }
+    if (bc->iters < 1) return fail(err, SIM_EINVAL, "iters must be >= 1");
+    if (!(bc->tol >= 0.0)) return fail(err, SIM_EINVAL, "tol must be >= 0");
+    if (bc->precision != SIM_FP64 && bc->precision != SIM_MIXED) return fail(err, SIM_EINVAL, "unknown precision");
+    pb.iters = bc->iters;
+    pb.tol = bc->tol;
+    pb.seed = bc->seed;
+    pb.perturb = bc->perturb;
+    pb.precision = bc->precision;
+    sim_status st = derive_coefficients(gas, pb, err);
+    if (st != SIM_OK) return st;
+    pb.in_u.resize(pb.ny);
+    pb.in_T.resize(pb.ny);
+    pb.in_p.resize(pb.ny);
+    for (int j = 0; j < pb.ny; j++) {
+        pb.in_u[j] = bc->inflow_u ? bc->inflow_u[j] : pb.u_in;
+        pb.in_T[j] = bc->inflow_T ? bc->inflow_T[j] : 1.0;
+        pb.in_p[j] = bc->inflow_p ? bc->inflow_p[j] : 1.0;
+        if (!(pb.in_T[j] > 0.0)) return fail(err, SIM_EINVAL, "inflow temperature must be positive");
+    }
+    // time step: given, or cfl * min cell size / (U_ref + sound speed)
+    if (bc->dt > 0.0) {
+        pb.k.dt = bc->dt;
+    } else {
+        double cfl = bc->cfl > 0.0 ? bc->cfl : 0.2, dmin = 1e300, uref = std::fabs(pb.u_in);
+        for (double d : pb.dx) dmin = std::fmin(dmin, d);
+        for (double d : pb.dy) dmin = std::fmin(dmin, d);
+        for (int s = 0; s < 4; s++) uref = std::fmax(uref, std::fabs(pb.side_vel[s]));
+        if (bc->inflow_u)
+            for (int j = 0; j < pb.ny; j++) uref = std::fmax(uref, std::fabs(bc->inflow_u[j]));
+        pb.k.dt = cfl * dmin / (uref + std::sqrt(pb.gamma / 2.0));
+    }
+    return SIM_OK;
+}
+
+// ----------------------------------------------------------- host geometry
+
+struct HostGrid {
+    int nx, ny, P;
+    std::vector<uint8_t> kind, side;           // over [-2, nx+2] x [-2, ny+2]
+    int at(int i, int j) const { return (j + G) * P + (i + G); }
+    bool in(int i, int j) const { return i >= -G && i <= nx + G && j >= -G && j <= ny + G; }
+    int k(int i, int j) const { return in(i, j) ? kind[at(i, j)] : K_WALL; }
+    bool fluid(int i, int j) const { return k(i, j) == K_FLUID; }
+    bool wall(int i, int j) const { int t = k(i, j); return t == K_SOLID || t == K_WALL; }
+};
+
+void classify(const Problem &pb, HostGrid &h)
+{
+    h.kind.assign((size_t)h.P * (pb.ny + 2 * G + 1), K_WALL);
+    h.side.assign(h.kind.size(), 0);
+    for (int j = -G; j <= pb.ny + G; j++)
+        for (int i = -G; i <= pb.nx + G; i++) {
+            int side = j < 0 ? SIM_S : j >= pb.ny ? SIM_N : i < 0 ? SIM_W : i >= pb.nx ? SIM_E : -1;
+            uint8_t t = K_FLUID;
+            if (side >= 0) {
+                switch (pb.side_kind[side]) {
+                case SIM_BC_WALL: t = K_WALL; break;
+                case SIM_BC_SYMMETRY: t = K_SYMM; break;
+                case SIM_BC_INFLOW: t = K_INFLOW; break;
+                default: t = K_OUTFLOW; break;
+                }
+            }
+            h.kind[h.at(i, j)] = t;
+            h.side[h.at(i, j)] = (uint8_t)(side < 0 ? 0 : side);
+        }
+    for (size_t r = 0; r < pb.rect.size(); r += 4)
+        for (int j = pb.rect[r + 1]; j < pb.rect[r + 3]; j++)
+            for (int i = pb.rect[r]; i < pb.rect[r + 2]; i++)
+                h.kind[h.at(i, j)] = K_SOLID;
+}
+
+std::vector<uint16_t> make_flags(const HostGrid &h)
+{
+    std::vector<uint16_t> f(h.kind.size(), 0);
+    auto uact = [&](int i, int j) { return h.fluid(i - 1, j) && h.fluid(i, j); };
+    auto vact = [&](int i, int j) { return h.fluid(i, j - 1) && h.fluid(i, j); };
+    for (int j = -G; j <= h.ny + G; j++)
+        for (int i = -G; i <= h.nx + G; i++) {
+            uint32_t b = 0;
+            if (h.fluid(i, j)) b |= F_FLUID;
+            if (h.wall(i, j)) b |= F_WALL;
+            if (uact(i, j)) b |= F_UACT;
+            if (h.wall(i - 1, j) && h.wall(i, j)) b |= F_UWALL;
+            if (vact(i, j)) b |= F_VACT;
+            if (h.wall(i, j - 1) && h.wall(i, j)) b |= F_VWALL;
+            bool cx = true, cy = true, ux = true, uy = true, vx = true, vy = true;
+            for (int q = -2; q <= 1; q++) {
+                cx = cx && h.fluid(i + q, j);
+                cy = cy && h.fluid(i, j + q);
+                ux = ux && uact(i + q, j);
+                uy = uy && uact(i, j + q);
+                vx = vx && vact(i + q, j);
+                vy = vy && vact(i, j + q);
+            }
+            if (cx) b |= F_TCX;
+            if (cy) b |= F_TCY;
+            if (ux) b |= F_TUX;
+            if (uy) b |= F_TUY;
+            if (vx) b |= F_TVX;
+            if (vy) b |= F_TVY;
+            f[h.at(i, j)] = (uint16_t)b;
+        }
+    return f;
+}
+
+// Axis factor table: 5 arrays of n + 2G + 1 entries over [-2, n+2].
+std::vector<double> make_axis(const std::vector<double> &dl)
+{
+    const int n = (int)dl.size(), m = n + 2 * G + 1;
+    std::vector<double> d(m), out(5 * (size_t)m, 0.0);
+    for (int i = -G; i <= n + G; i++) {
+        int s = i;
+        if (s < 0) s = -s - 1;                  // mirror about the west / south side
+        if (s >= n) s = 2 * n - 1 - s;          // mirror about the east / north side
+        d[i + G] = dl[s];
+    }
+    for (int q = 0; q < m; q++) {
+        const double di = d[q], dm = q > 0 ? d[q - 1] : d[q];
+        out[q] = di;
+        out[m + q] = 1.0 / di;
+        out[2 * m + q] = di / (dm + di);
+        out[3 * m + q] = dm / (dm + di);
+        out[4 * m + q] = 1.0 / (0.5 * (dm + di));
+    }
+    return out;
+}
+
+double gamma_of(const Problem &pb, double T) { return pb.k.omega == 0.5 ? std::sqrt(T) : std::pow(T, pb.k.omega); }
+
+// Stored values of every node that is not an unknown, and the start state of
+// the unknowns (inflow state of the row plus the seeded perturbation).
+void build_start_level(const Problem &pb, const HostGrid &h, std::vector<double> *f /* u v p T rho gam */)
+{
+    const int nx = pb.nx, ny = pb.ny;
+    const bool inflow = pb.side_kind[SIM_W] == SIM_BC_INFLOW;
+    auto row = [&](int j) { return j < 0 ? 0 : (j >= ny ? ny - 1 : j); };
+    for (int j = -G; j <= ny + G; j++)
+        for (int i = -G; i <= nx + G; i++) {
+            const int c = h.at(i, j);
+            const int t = h.k(i, j);
+            double p = 1.0, T = 1.0;
+            if (t == K_FLUID) {
+                if (inflow) { p = pb.in_p[j]; T = pb.in_T[j]; }
+                p *= 1.0 + pb.perturb * hash_uniform(pb.seed, 2, i, j);
+                T *= 1.0 + pb.perturb * hash_uniform(pb.seed, 3, i, j);
+            } else if (t == K_SOLID) {
+                T = pb.body_T;
+            } else if (t == K_WALL) {
+                T = pb.side_T[h.side[c]];
+            } else if (t == K_INFLOW) {
+                p = pb.in_p[row(j)];
+                T = pb.in_T[row(j)];
+            }
+            f[2][c] = p;
+            f[3][c] = T;
+            f[4][c] = p / T;
+            f[5][c] = gamma_of(pb, T);
+
+            // u face between cells (i-1, j) and (i, j)
+            const int tl = h.k(i - 1, j), tr = t;
+            double u = 0.0;
+            if (tl == K_FLUID && tr == K_FLUID) {
+                u = (inflow ? pb.in_u[j] : 0.0) * (1.0 + pb.perturb * hash_uniform(pb.seed, 0, i, j));
+            } else if (tl == K_FLUID || tr == K_FLUID) {
+                u = (tl == K_INFLOW || tr == K_INFLOW) ? pb.in_u[row(j)] : 0.0;
+            } else if (h.wall(i - 1, j) && h.wall(i, j)) {
+                // inside a wall: tangential wall speed behind a S/N wall, else 0
+                int sl = h.side[h.at(i - 1, j)], sr = h.side[c];
+                if (tl == K_WALL && (sl == SIM_S || sl == SIM_N)) u = pb.side_vel[sl];
+                else if (tr == K_WALL && (sr == SIM_S || sr == SIM_N)) u = pb.side_vel[sr];
+            } else if (tl == K_INFLOW || tr == K_INFLOW) {
+                u = pb.in_u[row(j)];
+            }
+            f[0][c] = u;
+
+            // v face between cells (i, j-1) and (i, j)
+            const int tb = h.k(i, j - 1), tt = t;
+            double v = 0.0;
+            if (tb == K_FLUID && tt == K_FLUID) {
+                v = pb.perturb * pb.u_in * hash_uniform(pb.seed, 1, i, j);
+            } else if (tb != K_FLUID && tt != K_FLUID && h.wall(i, j - 1) && h.wall(i, j)) {
+                int sb = h.side[h.at(i, j - 1)], st = h.side[c];
+                if (tb == K_WALL && (sb == SIM_W || sb == SIM_E)) v = pb.side_vel[sb];
+                else if (tt == K_WALL && (st == SIM_W || st == SIM_E)) v = pb.side_vel[st];
+            }
+            f[1][c] = v;
+        }
+}
+
+double *level_field(const Level &L, int f)
+{
+    switch (f) {
+    case SIM_FIELD_U: return L.u;
+    case SIM_FIELD_V: return L.v;
+    case SIM_FIELD_P: return L.p;
+    case SIM_FIELD_T: return L.T;
+    case SIM_FIELD_RHO: return L.rho;
+    default: return L.gam;
+    }
+}
+
+size_t field_count(const Problem &pb, int f)
+{
+    const size_t nx = pb.nx, ny = pb.ny;
+    return f == SIM_FIELD_U ? (nx + 1) * ny : f == SIM_FIELD_V ? nx * (ny + 1) : nx * ny;
+}
+
+cudaEvent_t take_event(sim_t s)
+{
+    if (!s->spare.empty()) {
+        cudaEvent_t e = s->spare.back();
+        s->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket one kernel launch: counts it, and times it when timing is on.
+struct Launch {
+    sim_t s;
+    int cls;
+    cudaEvent_t e0 = nullptr;
+    Launch(sim_t s_, int c) : s(s_), cls(c)
+    {
+        s->launches[cls]++;
+        if (s->timing) {
+            e0 = take_event(s);
+            cudaEventRecord(e0, s->stream);
+        }
+    }
+    ~Launch()
+    {
+        if (e0) {
+            cudaEvent_t e1 = take_event(s);
+            cudaEventRecord(e1, s->stream);
+            s->marks.push_back({cls, e0, e1});
+        }
+    }
+};
+
+int ghost_launches(const Sides &sd)
+{
+    const bool we = sd.kind[SIDE_E] == BC_OUTFLOW || sd.kind[SIDE_E] == BC_SYMMETRY || sd.kind[SIDE_W] == BC_SYMMETRY;
+    const bool sn = sd.kind[SIDE_S] == BC_SYMMETRY || sd.kind[SIDE_N] == BC_SYMMETRY;
+    return (int)we + (int)sn;
+}
+
+sim_status check_live(sim_t s)
+{
+    if (!s) return SIM_EINVAL;
+    if (s->diverged) return fail(s, SIM_ESTATE, "handle is in the error state after a divergence");
+    return SIM_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const sim_bc *bc, void *stream,
+                                 sim_t *out)
+{
+    if (!out) return SIM_EINVAL;
+    *out = nullptr;
+    sim_t s = new (std::nothrow) sim_s;
+    if (!s) return SIM_ENOMEM;
+    sim_status st = read_problem(grid, gas, bc, s->pb, s);
+    if (st != SIM_OK) {
+        sim_destroy(s);
+        return st;
+    }
+    const Problem &pb = s->pb;
+    s->stream = (cudaStream_t)stream;
+    s->pitch = ((pb.nx + 2 * G + 1) + 7) / 8 * 8;
+    const int rows = pb.ny + 2 * G + 1;
+    s->nelem = (size_t)s->pitch * rows;
+
+    HostGrid h;
+    h.nx = pb.nx;
+    h.ny = pb.ny;
+    h.P = s->pitch;
+    classify(pb, h);
+    std::vector<uint16_t> flags = make_flags(h);
+    std::vector<double> ax = make_axis(pb.dx), ay = make_axis(pb.dy);
+
+    // one pool for 3 levels x 6 fields + 9 work arrays
+    const size_t nfields = 3 * 6 + 9;
+    cudaError_t e = cudaMalloc(&s->d_pool, nfields * s->nelem * sizeof(double));
+    if (e != cudaSuccess) {
+        sim_destroy(s);
+        return e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA;
+    }
+    double *q = s->d_pool;
+    for (int l = 0; l < 3; l++) {
+        Level &L = s->lv[l];
+        L.u = q; q += s->nelem;
+        L.v = q; q += s->nelem;
+        L.p = q; q += s->nelem;
+        L.T = q; q += s->nelem;
+        L.rho = q; q += s->nelem;
+        L.gam = q; q += s->nelem;
+    }
+    Work &w = s->work;
+    w.rho_u = q; q += s->nelem;
+    w.rho_v = q; q += s->nelem;
+    w.uhat = q; q += s->nelem;
+    w.du = q; q += s->nelem;
+    w.vhat = q; q += s->nelem;
+    w.dv = q; q += s->nelem;
+    w.uexp = q; q += s->nelem;
+    w.vexp = q; q += s->nelem;
+    w.Texp = q; q += s->nelem;
+    const size_t nax = ax.size(), nay = ay.size();
+    const size_t stage = (size_t)(pb.nx + 1) * (pb.ny + 1);
+    if (cudaMalloc(&s->d_flag, flags.size() * sizeof(uint16_t)) != cudaSuccess ||
+        cudaMalloc(&s->d_axis, (nax + nay) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&s->d_stage, stage * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&w.res, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&s->h_res, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+        sim_destroy(s);
+        return SIM_ENOMEM;
+    }
+
+    s->geo.nx = pb.nx;
+    s->geo.ny = pb.ny;
+    s->geo.pitch = s->pitch;
+    s->geo.flag = s->d_flag;
+    const int mx = pb.nx + 2 * G + 1, my = pb.ny + 2 * G + 1;
+    const double *dax = s->d_axis, *day = s->d_axis + nax;
+    s->geo.x = Axis{dax, dax + mx, dax + 2 * mx, dax + 3 * mx, dax + 4 * mx};
+    s->geo.y = Axis{day, day + my, day + 2 * my, day + 3 * my, day + 4 * my};
+    for (int k = 0; k < 4; k++) s->sides.kind[k] = pb.side_kind[k];
+
+    std::vector<double> f[6];
+    for (auto &a : f) a.assign(s->nelem, 0.0);
+    build_start_level(pb, h, f);
+
+    CUDA_TRY(s, cudaMemcpyAsync(s->d_flag, flags.data(), flags.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(s, cudaMemcpyAsync(s->d_axis, ax.data(), nax * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(s, cudaMemcpyAsync(s->d_axis + nax, ay.data(), nay * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(s->d_pool + 18 * s->nelem, 0, 9 * s->nelem * sizeof(double), s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(w.res, 0, 4 * sizeof(unsigned long long), s->stream));
+    for (int l = 0; l < 3; l++)
+        for (int k = 0; k < 6; k++)
+            CUDA_TRY(s, cudaMemcpyAsync(level_field(s->lv[l], k), f[k].data(), s->nelem * sizeof(double),
+                                        cudaMemcpyHostToDevice, s->stream));
+    for (int l = 0; l < 3; l++) {
+        launch_derive(s->geo, pb.k, s->lv[l], s->stream);
+        launch_ghosts(s->geo, s->sides, s->lv[l], s->stream);
+    }
+    CUDA_TRY(s, cudaGetLastError());
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    *out = s;
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_step(sim_t s, int n_steps, int scheme)
+{
+    sim_status st = check_live(s);
+    if (st != SIM_OK) return st;
+    if (n_steps < 0 || (scheme & ~3)) return fail(s, SIM_EINVAL, "bad n_steps %d or scheme %d", n_steps, scheme);
+    const bool implicit = scheme & SIM_IMPLICIT, tvd = scheme & SIM_TVD;
+    const Problem &pb = s->pb;
+    for (int step = 0; step < n_steps; step++) {
+        const int prev = s->cur;
+        int old = prev, it = 0;
+        if (!implicit) {
+            { Launch l(s, SIM_K_FACES); launch_face_densities(s->geo, s->lv[prev], s->work, tvd, s->stream); }
+            { Launch l(s, SIM_K_EXPLICIT); launch_explicit_terms(s->geo, s->lv[prev], s->work, tvd, s->stream); }
+        }
+        for (it = 1; it <= pb.iters; it++) {
+            int nw = (old + 1) % 3;
+            if (nw == prev) nw = (nw + 1) % 3;
+            CUDA_TRY(s, cudaMemsetAsync(s->work.res, 0, 4 * sizeof(unsigned long long), s->stream));
+            { Launch l(s, SIM_K_FACES); launch_face_densities(s->geo, s->lv[old], s->work, tvd, s->stream); }
+            { Launch l(s, SIM_K_ASSEMBLE);
+              launch_assemble(s->geo, pb.k, s->lv[prev], s->lv[old], s->lv[nw], s->work, implicit, tvd, s->stream); }
+            { Launch l(s, SIM_K_PRESSURE);
+              launch_pressure(s->geo, pb.k, s->lv[prev], s->lv[old], s->lv[nw], s->work, s->stream); }
+            { Launch l(s, SIM_K_VELOCITY); launch_velocity(s->geo, s->lv[old], s->lv[nw], s->work, s->stream); }
+            if (ghost_launches(s->sides)) {
+                Launch l(s, SIM_K_GHOSTS);
+                s->launches[SIM_K_GHOSTS] += ghost_launches(s->sides) - 1;
+                launch_ghosts(s->geo, s->sides, s->lv[nw], s->stream);
+            }
+            old = nw;
+            if (pb.tol > 0.0) {
+                CUDA_TRY(s, cudaMemcpyAsync(s->h_res, s->work.res, 4 * sizeof(unsigned long long),
+                                            cudaMemcpyDeviceToHost, s->stream));
+                CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+                double mx = 0.0;
+                bool bad = false;
+                for (int q = 0; q < 4; q++) {
+                    double r;
+                    std::memcpy(&r, &s->h_res[q], sizeof r);
+                    if (!std::isfinite(r)) bad = true;
+                    mx = std::fmax(mx, r);
+                }
+                if (bad) {
+                    s->cur = old;
+                    s->last_iters = it;
+                    s->diverged = true;
+                    s->set_mask = 0;
+                    return fail(s, SIM_EDIVERGED, "non-finite residual in step %d, iteration %d", step, it);
+                }
+                if (mx <= pb.tol) break;
+            }
+        }
+        s->last_iters = it > pb.iters ? pb.iters : it;
+        s->cur = old;
+    }
+    CUDA_TRY(s, cudaGetLastError());
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_fields(sim_t s, int field, double *host_dst, size_t n)
+{
+    if (!s) return SIM_EINVAL;
+    if (field < 0 || field > 5 || !host_dst) return fail(s, SIM_EINVAL, "bad field %d or null destination", field);
+    const size_t need = field_count(s->pb, field);
+    if (n != need) return fail(s, SIM_EINVAL, "field %d has %zu elements, got %zu", field, need, n);
+    launch_gather(s->geo, field, s->lv[s->cur], s->d_stage, s->stream);
+    CUDA_TRY(s, cudaGetLastError());
+    CUDA_TRY(s, cudaMemcpyAsync(host_dst, s->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_field_ptr(sim_t s, int field, void **dev, size_t *pitch)
+{
+    if (!s) return SIM_EINVAL;
+    if (field < 0 || field > 5 || !dev || !pitch) return fail(s, SIM_EINVAL, "bad field %d or null output", field);
+    *dev = level_field(s->lv[s->cur], field) + (size_t)G * s->pitch + G;
+    *pitch = (size_t)s->pitch;
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_set_fields(sim_t s, int field, const double *host_src, size_t n)
+{
+    if (!s) return SIM_EINVAL;
+    if (field < 0 || field > 3 || !host_src) return fail(s, SIM_EINVAL, "only u, v, p, T can be set (field %d)", field);
+    const size_t need = field_count(s->pb, field);
+    if (n != need) return fail(s, SIM_EINVAL, "field %d has %zu elements, got %zu", field, need, n);
+    for (size_t q = 0; q < n; q++)
+        if (!std::isfinite(host_src[q]) || ((field == SIM_FIELD_T || field == SIM_FIELD_P) && !(host_src[q] > 0.0)))
+            return fail(s, SIM_EINVAL, "field %d: value %zu is not admissible", field, q);
+    const Level &L = s->lv[s->cur];
+    CUDA_TRY(s, cudaMemcpyAsync(s->d_stage, host_src, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    launch_scatter(s->geo, field, s->d_stage, L, s->stream);
+    launch_derive(s->geo, s->pb.k, L, s->stream);
+    launch_ghosts(s->geo, s->sides, L, s->stream);
+    CUDA_TRY(s, cudaGetLastError());
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    if (s->diverged) {
+        s->set_mask |= 1u << field;
+        if (s->set_mask == 0xFu) {
+            s->diverged = false;
+            s->set_mask = 0;
+        }
+    }
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_residuals(sim_t s, double out[4], int *iters_last_step)
+{
+    if (!s || !out) return SIM_EINVAL;
+    CUDA_TRY(s, cudaMemcpyAsync(s->h_res, s->work.res, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    bool bad = false;
+    for (int q = 0; q < 4; q++) {
+        std::memcpy(&out[q], &s->h_res[q], sizeof(double));
+        if (!std::isfinite(out[q])) bad = true;
+    }
+    if (iters_last_step) *iters_last_step = s->last_iters;
+    if (bad) {
+        s->diverged = true;
+        s->set_mask = 0;
+        return fail(s, SIM_EDIVERGED, "non-finite residual");
+    }
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_coefficients(sim_t s, double out[9])
+{
+    if (!s || !out) return SIM_EINVAL;
+    const Coef &k = s->pb.k;
+    out[0] = k.A; out[1] = k.B; out[2] = k.CT1f; out[3] = k.CT2f; out[4] = k.CT3f;
+    out[5] = k.omega; out[6] = s->pb.u_in; out[7] = k.dt; out[8] = (double)s->pb.nx * s->pb.ny;
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_profile(sim_t s, int enable)
+{
+    if (!s) return SIM_EINVAL;
+    if (enable) {
+        CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+        for (auto &m : s->marks) {
+            s->spare.push_back(m.e0);
+            s->spare.push_back(m.e1);
+        }
+        s->marks.clear();
+        for (auto &c : s->launches) c = 0;
+    }
+    s->timing = enable != 0;
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_profile_read(sim_t s, int cls, double *ms, long long *launches)
+{
+    if (!s || cls < 0 || cls >= SIM_K_COUNT || !ms || !launches) return SIM_EINVAL;
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    double total = 0.0;
+    for (auto &m : s->marks)
+        if (m.cls == cls) {
+            float t = 0.f;
+            CUDA_TRY(s, cudaEventElapsedTime(&t, m.e0, m.e1));
+            total += t;
+        }
+    *ms = total;
+    *launches = s->launches[cls];
+    return SIM_OK;
+}
+
+extern "C" const char *sim_last_error(sim_t s)
+{
+    return s ? s->err : "null handle";
+}
+
+extern "C" void sim_destroy(sim_t s)
+{
+    if (!s) return;
+    if (s->d_pool) cudaStreamSynchronize(s->stream);
+    cudaFree(s->d_pool);
+    cudaFree(s->d_flag);
+    cudaFree(s->d_axis);
+    cudaFree(s->d_stage);
+    cudaFree(s->work.res);
+    if (s->h_res) cudaFreeHost(s->h_res);
+    for (auto &m : s->marks) {
+        cudaEventDestroy(m.e0);
+        cudaEventDestroy(m.e1);
+    }
+    for (auto e : s->spare) cudaEventDestroy(e);
+    delete s;
+}

@@ -1,0 +1,198 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 reference oracle.
+
+Error metric (per field): max |gpu - oracle| / max |oracle| over the logical
+array, boundary values included.  The FP64 bar is 1e-9.  Implicit TVD
+amplifies rounding differences (see test_oracle_pins.test_rounding_sensitivity_per_scheme),
+so its runs are kept to 20 steps; the other schemes run 50-100 steps.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1802_04243_gb300 as sim
+import workloads as W
+from paper_1802_04243_gb300 import build
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+SCHEMES = [(False, False), (False, True), (True, False), (True, True)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    sim.load()
+
+
+def rel_err(a, b):
+    return {k: float(np.abs(a[k] - b[k]).max() / max(np.abs(b[k]).max(), 1e-300)) for k in b}
+
+
+def steps_for(implicit, tvd, n):
+    return min(n, 20) if (implicit and tvd) else n
+
+
+def run_both(case, nsteps, start=None):
+    with sim.Simulation(case) as s:
+        if start is not None:
+            s.set_fields(start)
+        s.step(nsteps)
+        g = s.fields()
+        gres, git, st = s.residuals()
+        assert st == sim.SIM_OK
+    o, ores, oit = oracle.run(case, start, nsteps=nsteps)
+    return g, o, gres, ores, git, oit
+
+
+def assert_parity(g, o, tol=TOL, what=""):
+    e = rel_err(g, o)
+    assert max(e.values()) <= tol, f"{what}: {e}"
+    return e
+
+
+# ------------------------------------------------------------ start state
+
+@pytest.mark.parametrize("case", [W.c1_small(), W.closed_box(), W.uniform_flow(),
+                                  W.c3_large().replace(nx=512, ny=128, rects=[[100, 40, 126, 66]])],
+                         ids=["c1", "box", "uniform", "c3-like"])
+def test_start_state_is_bitwise_identical(case):
+    with sim.Simulation(case) as s:
+        g = s.fields(("u", "v", "p", "T", "rho"))
+        coef = s.coefficients()
+    o = oracle.init(case)
+    for k in "uvpT":
+        assert np.array_equal(g[k], o[k]), k
+    assert np.array_equal(g["rho"], o["p"] / o["T"])
+    oc = oracle.coefficients(case)
+    for k in ("A", "B", "CT1f", "CT2f", "CT3f", "u_in", "dt"):
+        assert coef[k] == pytest.approx(oc[k], rel=1e-15), k
+
+
+# ------------------------------------------------------------ small cases
+
+@pytest.mark.parametrize("implicit,tvd", SCHEMES)
+def test_parity_channel_128x32(implicit, tvd):
+    case = W.c1_small().replace(implicit=implicit, tvd=tvd)
+    n = steps_for(implicit, tvd, case.steps)
+    g, o, gres, ores, git, oit = run_both(case, n)
+    assert_parity(g, o, what=f"{n} steps")
+    assert git == oit == case.iters
+    np.testing.assert_allclose(gres, ores, rtol=1e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("implicit,tvd", SCHEMES)
+def test_parity_box_nonuniform_moving_walls(implicit, tvd):
+    rng = np.random.default_rng(4)
+    nx, ny = 37, 29                                  # ragged: not a multiple of the 32 x 8 tile
+    dx, dy = rng.uniform(0.2, 0.35, nx), rng.uniform(0.2, 0.35, ny)
+    case = W.closed_box(implicit=implicit, tvd=tvd).replace(
+        nx=nx, ny=ny, dx=dx, dy=dy, lx=float(dx.sum()), ly=float(dy.sum()),
+        rects=[[5, 4, 12, 9], [20, 15, 24, 25]], gx=0.01, gy=-0.02, iters=3, perturb=1e-3, seed=21)
+    start = oracle.init(case)
+    start["u"] += 0.03 * rng.standard_normal(start["u"].shape)
+    start["v"] += 0.03 * rng.standard_normal(start["v"].shape)
+    g, o, *_ = run_both(case, steps_for(implicit, tvd, 40), start=start)
+    assert_parity(g, o)
+
+
+@pytest.mark.parametrize("implicit,tvd", SCHEMES)
+def test_parity_symmetry_sides_and_obstacle(implicit, tvd):
+    case = W.uniform_flow(nx=48, ny=20, implicit=implicit, tvd=tvd).replace(
+        rects=[[10, 6, 14, 12]], perturb=1e-3, seed=8)
+    g, o, *_ = run_both(case, steps_for(implicit, tvd, 60))
+    assert_parity(g, o)
+
+
+def test_parity_west_east_symmetry_box():
+    case = W.closed_box(n=20, implicit=True, tvd=False).replace(
+        side_kind=(W.SYMMETRY, W.SYMMETRY, W.WALL, W.WALL), perturb=1e-3, seed=3)
+    rng = np.random.default_rng(5)
+    start = oracle.init(case)
+    start["v"] += 0.02 * rng.standard_normal(start["v"].shape)
+    g, o, *_ = run_both(case, 50, start=start)
+    assert_parity(g, o)
+
+
+def test_parity_smallest_grid():
+    case = W.Case(name="tiny", nx=4, ny=4, lx=1.0, ly=1.0, side_kind=(W.INFLOW, W.OUTFLOW, W.WALL, W.WALL),
+                  mach_in=0.5, reynolds=20.0, perturb=1e-3)
+    for implicit, tvd in SCHEMES:
+        c = case.replace(implicit=implicit, tvd=tvd)
+        g, o, *_ = run_both(c, 20)
+        assert_parity(g, o, what=str((implicit, tvd)))
+
+
+def test_parity_inflow_profile_body_force_and_hard_sphere_gas():
+    ny = 24
+    y = (np.arange(ny) + 0.5) / ny
+    case = W.Case(name="hs", nx=40, ny=ny, lx=40 / 24, ly=1.0, gas_model=W.GAS_HARD_SPHERE_KN, kn=0.01,
+                  mach_in=1.2, side_vel=(0, 0, 0.1, -0.2), side_T=(1, 1, 1.1, 0.9), gx=0.05,
+                  inflow_u=0.8 * 4 * y * (1 - y), inflow_T=1 + 0.1 * y, inflow_p=np.ones(ny) * 1.05,
+                  rects=[[10, 8, 14, 14]], implicit=True, tvd=False, perturb=1e-3, seed=17)
+    g, o, *_ = run_both(case, 60)
+    assert_parity(g, o)
+
+
+def test_parity_loop2_tolerance_stop():
+    case = W.c1_small().replace(implicit=True, tvd=False, iters=50, tol=1e-4)
+    g, o, gres, ores, git, oit = run_both(case, 10)
+    assert git == oit and 1 < git < 50
+    assert_parity(g, o)
+
+
+def test_restart_through_host_fields_is_bitwise():
+    case = W.c1_small().replace(implicit=True, tvd=False)
+    with sim.Simulation(case) as a:
+        a.step(20)
+        full = a.fields()
+    with sim.Simulation(case) as b:
+        b.step(10)
+        mid = b.fields()
+    with sim.Simulation(case) as c:
+        c.set_fields(mid)
+        c.step(10)
+        again = c.fields()
+    for k in "uvpT":
+        assert np.array_equal(full[k], again[k]), k
+
+
+def test_divergence_is_reported_and_blocks_the_handle():
+    case = W.c1_small().replace(implicit=True, tvd=False, cfl=3.0)
+    with sim.Simulation(case) as s:
+        s.step(200)
+        res, _, st = s.residuals()
+        assert st == sim.SIM_EDIVERGED and not np.isfinite(res).all()
+        with pytest.raises(sim.SimError) as e:
+            s.step(1)
+        assert e.value.status == sim.SIM_ESTATE
+        start = oracle.init(case)
+        s.set_fields(start)
+        s.step(1)                                  # usable again after all four fields are set
+
+
+def test_field_view_is_zero_copy_and_matches_host_copy():
+    import torch
+    case = W.c1_small()
+    with sim.Simulation(case) as s:
+        s.step(3)
+        t = s.field_view("T")
+        host = s.field("T")
+        assert t.is_cuda and t.dtype == torch.float64
+        assert np.array_equal(t[2:-2, 2:-2].cpu().numpy(), host)
+
+
+# ------------------------------------------------------------ full sizes
+
+def test_parity_1024x256_implicit_100_steps():
+    case = W.c2_medium()
+    g, o, *_ = run_both(case, 100)
+    assert_parity(g, o)
+
+
+@pytest.mark.parametrize("make", [lambda: W.c3_large(implicit=True), lambda: W.c3_large(implicit=False),
+                                  W.c4_paper_scale], ids=["c3-implicit", "c3-explicit", "c4-implicit"])
+def test_parity_full_size_one_step(make):
+    case = make()
+    g, o, *_ = run_both(case, 1)
+    assert_parity(g, o)
