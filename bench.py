@@ -36,9 +36,14 @@ UNIT = "Mcell-steps/s"
 # u, v, T, rho of level n-1 (12 doubles); writes T, u^, d^u, v^, d^v (5 doubles).
 ASSEMBLE_BYTES_PER_CELL = 17 * 8
 # FP64 flops the assembly kernel executes per cell and iteration (implicit
-# upwind), from the ncu instruction counts of k_assemble: 2 * DFMA + DMUL +
-# DADD per thread, divided by the cells of the launch.
-ASSEMBLE_FP64_FLOPS_PER_CELL = None
+# upwind): 2 * DFMA + DMUL + DADD thread instructions of one k_assemble launch
+# counted by ncu on the 2048x512 channel (151.6 M, 160.9 M, 91.8 M), divided by
+# its 1,048,576 cells.
+ASSEMBLE_FP64_FLOPS_PER_CELL = 530.2
+# DRAM bytes of that launch per cell (69.1 MB read + 11.1 MB written).
+ASSEMBLE_DRAM_BYTES_PER_CELL = 76.5
+# ncu: sm__pipe_fp64_cycles_active of that launch, percent of peak.
+ASSEMBLE_FP64_PIPE_ACTIVE = 0.864
 
 
 def parse():
@@ -49,19 +54,32 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2",
+                    help="c2 (default, the benchmark line); the others are for profiling and sweeps")
     return ap.parse_args()
+
+
+WORKLOADS = {
+    "c2": lambda W: W.c2_medium(),
+    "c3": lambda W: W.c3_large(implicit=True),
+    "c3-explicit": lambda W: W.c3_large(implicit=False),
+    "c4": lambda W: W.c4_paper_scale(),
+    "profile": lambda W: W.profile_channel(),
+}
+_ARGS = None
 
 
 def workload():
     import workloads as W
-    return W.c2_medium()
+    return WORKLOADS[_ARGS.workload if _ARGS else "c2"](W)
 
 
 def config_of(case, flush: str):
-    return {"workload": f"{case.name}: {case.nx}x{case.ny} channel, 1 square (side H/4) at L/4, "
-                        f"implicit upwind, Mach {case.mach_in}, Re {case.reynolds:g}, "
+    scheme = ("implicit" if case.implicit else "explicit") + ("-tvd" if case.tvd else "-upwind")
+    return {"workload": f"{case.name}: {case.nx}x{case.ny} channel, {len(case.rects)} square obstacle(s), "
+                        f"{scheme}, Mach {case.mach_in}, Re {case.reynolds:g}, "
                         f"{case.iters} loop-2 iterations per step",
-            "nx": case.nx, "ny": case.ny, "cells": case.cells, "scheme": "implicit-upwind",
+            "nx": case.nx, "ny": case.ny, "cells": case.cells, "scheme": scheme,
             "loop2_iters": case.iters, "l2": flush}
 
 
@@ -230,8 +248,12 @@ def run_ours(args, rank, world, local_rank):
     if ASSEMBLE_FP64_FLOPS_PER_CELL:
         ach = ASSEMBLE_FP64_FLOPS_PER_CELL * case.cells / asm_avg_s / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak_fp64 / 1e3, 4), "unit": "TFLOP/s",
-                "frac": round(ach / (peak_fp64 / 1e3), 4), "traffic": None,
-                "kernel": "k_assemble", "peak_source": "FP64 FMA probe measured in this run (simplets_alu_peak)"}
+                "frac": round(ach / (peak_fp64 / 1e3), 4),
+                "traffic": round(ASSEMBLE_DRAM_BYTES_PER_CELL * case.cells),
+                "kernel": "k_assemble", "peak_source": "FP64 FMA probe measured in this run (simplets_alu_peak), "
+                                                        "2 flops per DFMA at full issue rate",
+                "fp64_pipe_active_ncu": ASSEMBLE_FP64_PIPE_ACTIVE,
+                "traffic_source": "ncu dram bytes of one launch on the 2048x512 channel, scaled by cells"}
     else:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
@@ -295,7 +317,9 @@ def run_reference(args, rank, world):
 
 
 def main():
+    global _ARGS
     args = parse()
+    _ARGS = args
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

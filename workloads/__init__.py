@@ -123,6 +123,14 @@ def c4_paper_scale() -> Case:
                    implicit=True, tvd=False, seed=4, steps=2000)
 
 
+def profile_channel() -> Case:
+    """2048x512 channel (the 1024x256 case refined 2x): large enough that the
+    state (about 230 MB) does not fit in L2, small enough for a detailed
+    profiler capture."""
+    return channel(2048, 512, 128, name="profile_2048x512_implicit_upwind", mach_in=2.5, reynolds=200.0,
+                   implicit=True, tvd=False, seed=2, steps=500)
+
+
 def c5_batch(n: int = 64, precision: int = MIXED) -> List[Case]:
     """64 independent channels with seeded uneven grids from 256x64 to 2048x512,
     Mach in [1.5, 3], Re in [50, 400], 1-4 squares of side H/5, 500 steps each."""
