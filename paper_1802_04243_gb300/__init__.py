@@ -81,6 +81,9 @@ _SIGNATURES = {
     "sim_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "simplets_alu_peak": ([ctypes.c_int, ctypes.c_double, ctypes.c_void_p, _DP], ctypes.c_int),
     "sim_destroy": ([ctypes.c_void_p], None),
+    "sim_step_noalloc": ([ctypes.POINTER(sim_grid), ctypes.POINTER(sim_gas), ctypes.POINTER(sim_bc), ctypes.c_int,
+                          ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.c_void_p, _DP], ctypes.c_int),
 }
 
 
