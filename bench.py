@@ -207,6 +207,42 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
     value = case.cells * args.steps * world / (total_ms * 1e-3) / 1e6
+    fp64_state = s.fields()
+
+    # the same workload and timing protocol with the mixed-precision sweep
+    # (FP32 assembly and relaxation; FP64 pressure accumulation, EOS and
+    # residuals), and its per-field error against the FP64 path after the
+    # same number of steps from the same start
+    import workloads as W
+    sm = sim.Simulation(case.replace(precision=W.MIXED), stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        sm.step(1)
+    sm.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        sm.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    mixed_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    mprof = sm.profile_read()
+    sm.profile(False)
+    mixed_state = sm.fields()
+    sm.close()
+    tm = torch.tensor([mixed_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    mixed_ms = float(tm.item())
+    mixed_err = {k: float(np.abs(mixed_state[k] - fp64_state[k]).max() / np.abs(fp64_state[k]).max())
+                 for k in ("u", "v", "p", "T")}
+    mixed = {"value": round(case.cells * args.steps * world / (mixed_ms * 1e-3) / 1e6, 3),
+             "ms_per_step": round(mixed_ms / args.steps, 5), "dtype": "f32 assembly / f64 pressure, EOS, residuals",
+             "max_rel_err_vs_fp64": {k: float(f"{v:.3e}") for k, v in mixed_err.items()},
+             "error_after_steps": args.warmup + args.steps,
+             "kernels": {k: {"ms": round(ms, 4), "launches": n} for k, (ms, n) in mprof.items() if n}}
 
     # end to end through the C ABI with host buffers: every step uploads its
     # input state from pinned host memory and reads the new state and the
@@ -279,7 +315,7 @@ def run_ours(args, rank, world, local_rank):
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps},
             "gpu_launches": int(launches),
             "kernels": {k: {"ms": round(ms, 4), "launches": n} for k, (ms, n) in prof.items() if n},
-            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks.summary(),
+            "roofline": roof, "mixed": mixed, "cpu_baseline": cpu, "clocks": clocks.summary(),
             "residuals_last_step": [float(x) for x in res], "impl": "ours"}
     print(json.dumps(line), flush=True)
     if dist:

@@ -52,6 +52,11 @@ struct sim_s {
     uint16_t *d_flag = nullptr;
     double *d_axis = nullptr;
     double *d_stage = nullptr;                 // logical-shape staging array
+    // mixed precision: FP32 shadow levels, FP32 scratch and grid factors
+    bool mixed = false;
+    Mixed mx{};
+    float *d_pool32 = nullptr;
+    float *d_axis32 = nullptr;
     unsigned long long *h_res = nullptr;       // pinned copy of the residuals
     int cur = 0;                               // level holding the current state
     int last_iters = 0;
@@ -505,6 +510,50 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
     s->geo.y = Axis{day, day + my, day + 2 * my, day + 3 * my, day + 4 * my};
     for (int k = 0; k < 4; k++) s->sides.kind[k] = pb.side_kind[k];
 
+    s->mixed = pb.precision == SIM_MIXED;
+    if (s->mixed) {
+        if (cudaMalloc(&s->d_pool32, 27 * s->nelem * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&s->d_axis32, (nax + nay) * sizeof(float)) != cudaSuccess) {
+            sim_destroy(s);
+            return SIM_ENOMEM;
+        }
+        float *p32 = s->d_pool32;
+        for (int l = 0; l < 3; l++) {
+            LevelT<float> &L = s->mx.lv[l];
+            L.u = p32; p32 += s->nelem;
+            L.v = p32; p32 += s->nelem;
+            L.p = p32; p32 += s->nelem;
+            L.T = p32; p32 += s->nelem;
+            L.rho = p32; p32 += s->nelem;
+            L.gam = p32; p32 += s->nelem;
+        }
+        WorkT<float> &w32 = s->mx.w;
+        w32.rho_u = p32; p32 += s->nelem;
+        w32.rho_v = p32; p32 += s->nelem;
+        w32.uhat = p32; p32 += s->nelem;
+        w32.du = p32; p32 += s->nelem;
+        w32.vhat = p32; p32 += s->nelem;
+        w32.dv = p32; p32 += s->nelem;
+        w32.uexp = p32; p32 += s->nelem;
+        w32.vexp = p32; p32 += s->nelem;
+        w32.Texp = p32;
+        const float *fx = s->d_axis32, *fy = s->d_axis32 + nax;
+        s->mx.g.nx = pb.nx;
+        s->mx.g.ny = pb.ny;
+        s->mx.g.pitch = s->pitch;
+        s->mx.g.flag = s->d_flag;
+        s->mx.g.x = AxisT<float>{fx, fx + mx, fx + 2 * mx, fx + 3 * mx, fx + 4 * mx};
+        s->mx.g.y = AxisT<float>{fy, fy + my, fy + 2 * my, fy + 3 * my, fy + 4 * my};
+        const Coef &k = pb.k;
+        s->mx.k = CoefT<float>{(float)k.A, (float)k.B, (float)k.CT1f, (float)k.CT2f, (float)k.CT3f,
+                               (float)k.omega, (float)k.dt, (float)k.gx, (float)k.gy};
+        std::vector<float> a32(nax + nay);
+        for (size_t q = 0; q < nax; q++) a32[q] = (float)ax[q];
+        for (size_t q = 0; q < nay; q++) a32[nax + q] = (float)ay[q];
+        CUDA_TRY(s, cudaMemcpy(s->d_axis32, a32.data(), a32.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CUDA_TRY(s, cudaMemsetAsync(s->mx.w.rho_u, 0, 9 * s->nelem * sizeof(float), s->stream));
+    }
+
     std::vector<double> f[6];
     for (auto &a : f) a.assign(s->nelem, 0.0);
     build_start_level(pb, h, f);
@@ -521,6 +570,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
     for (int l = 0; l < 3; l++) {
         launch_derive(s->geo, pb.k, s->lv[l], s->stream);
         launch_ghosts(s->geo, s->sides, s->lv[l], s->stream);
+        if (s->mixed) launch_shadow(s->geo, s->lv[l], s->mx.lv[l], s->nelem, s->stream);
     }
     CUDA_TRY(s, cudaGetLastError());
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
@@ -538,7 +588,10 @@ extern "C" sim_status sim_step(sim_t s, int n_steps, int scheme)
     for (int step = 0; step < n_steps; step++) {
         const int prev = s->cur;
         int old = prev, it = 0;
-        if (!implicit) {
+        if (!implicit && s->mixed) {
+            { Launch l(s, SIM_K_FACES); launch_face_densities_f32(s->mx, prev, tvd, s->stream); }
+            { Launch l(s, SIM_K_EXPLICIT); launch_explicit_terms_f32(s->mx, prev, tvd, s->stream); }
+        } else if (!implicit) {
             { Launch l(s, SIM_K_FACES); launch_face_densities(s->geo, s->lv[prev], s->work, tvd, s->stream); }
             { Launch l(s, SIM_K_EXPLICIT); launch_explicit_terms(s->geo, s->lv[prev], s->work, tvd, s->stream); }
         }
@@ -546,16 +599,33 @@ extern "C" sim_status sim_step(sim_t s, int n_steps, int scheme)
             int nw = (old + 1) % 3;
             if (nw == prev) nw = (nw + 1) % 3;
             CUDA_TRY(s, cudaMemsetAsync(s->work.res, 0, 4 * sizeof(unsigned long long), s->stream));
-            { Launch l(s, SIM_K_FACES); launch_face_densities(s->geo, s->lv[old], s->work, tvd, s->stream); }
-            { Launch l(s, SIM_K_ASSEMBLE);
-              launch_assemble(s->geo, pb.k, s->lv[prev], s->lv[old], s->lv[nw], s->work, implicit, tvd, s->stream); }
-            { Launch l(s, SIM_K_PRESSURE);
-              launch_pressure(s->geo, pb.k, s->lv[prev], s->lv[old], s->lv[nw], s->work, s->stream); }
-            { Launch l(s, SIM_K_VELOCITY); launch_velocity(s->geo, s->lv[old], s->lv[nw], s->work, s->stream); }
-            if (ghost_launches(s->sides)) {
-                Launch l(s, SIM_K_GHOSTS);
-                s->launches[SIM_K_GHOSTS] += ghost_launches(s->sides) - 1;
-                launch_ghosts(s->geo, s->sides, s->lv[nw], s->stream);
+            if (s->mixed) {
+                { Launch l(s, SIM_K_FACES); launch_face_densities_f32(s->mx, old, tvd, s->stream); }
+                { Launch l(s, SIM_K_ASSEMBLE);
+                  launch_assemble_f32(s->mx, prev, old, nw, s->lv[nw], implicit, tvd, s->stream); }
+                { Launch l(s, SIM_K_PRESSURE);
+                  launch_pressure_mixed(s->geo, pb.k, s->mx, s->lv[prev], s->lv[old], s->lv[nw], nw, s->work,
+                                        s->stream); }
+                { Launch l(s, SIM_K_VELOCITY);
+                  launch_velocity_mixed(s->geo, s->mx, s->lv[old], s->lv[nw], nw, s->work, s->stream); }
+                if (ghost_launches(s->sides)) {
+                    Launch l(s, SIM_K_GHOSTS);
+                    s->launches[SIM_K_GHOSTS] += 2 * ghost_launches(s->sides) - 1;
+                    launch_ghosts(s->geo, s->sides, s->lv[nw], s->stream);
+                    launch_ghosts_f32(s->mx, s->sides, nw, s->stream);
+                }
+            } else {
+                { Launch l(s, SIM_K_FACES); launch_face_densities(s->geo, s->lv[old], s->work, tvd, s->stream); }
+                { Launch l(s, SIM_K_ASSEMBLE);
+                  launch_assemble(s->geo, pb.k, s->lv[prev], s->lv[old], s->lv[nw], s->work, implicit, tvd, s->stream); }
+                { Launch l(s, SIM_K_PRESSURE);
+                  launch_pressure(s->geo, pb.k, s->lv[prev], s->lv[old], s->lv[nw], s->work, s->stream); }
+                { Launch l(s, SIM_K_VELOCITY); launch_velocity(s->geo, s->lv[old], s->lv[nw], s->work, s->stream); }
+                if (ghost_launches(s->sides)) {
+                    Launch l(s, SIM_K_GHOSTS);
+                    s->launches[SIM_K_GHOSTS] += ghost_launches(s->sides) - 1;
+                    launch_ghosts(s->geo, s->sides, s->lv[nw], s->stream);
+                }
             }
             old = nw;
             if (pb.tol > 0.0) {
@@ -623,6 +693,7 @@ extern "C" sim_status sim_set_fields(sim_t s, int field, const double *host_src,
     launch_scatter(s->geo, field, s->d_stage, L, s->stream);
     launch_derive(s->geo, s->pb.k, L, s->stream);
     launch_ghosts(s->geo, s->sides, L, s->stream);
+    if (s->mixed) launch_shadow(s->geo, L, s->mx.lv[s->cur], s->nelem, s->stream);
     CUDA_TRY(s, cudaGetLastError());
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
     if (s->diverged) {
@@ -709,6 +780,8 @@ extern "C" void sim_destroy(sim_t s)
     cudaFree(s->d_axis);
     cudaFree(s->d_stage);
     cudaFree(s->work.res);
+    cudaFree(s->d_pool32);
+    cudaFree(s->d_axis32);
     if (s->h_res) cudaFreeHost(s->h_res);
     for (auto &m : s->marks) {
         cudaEventDestroy(m.e0);

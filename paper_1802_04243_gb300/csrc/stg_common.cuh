@@ -33,27 +33,59 @@ enum : uint32_t {
 
 // Per-index grid factors, each array indexed by i + G (x) or j + G (y) over
 // the extended range [-2, n + 2].
-struct Axis {
-    const double *d;      // cell size
-    const double *rd;     // 1 / d
-    const double *wlo;    // d_i / (d_{i-1} + d_i): weight of index i-1 at face i
-    const double *whi;    // d_{i-1} / (d_{i-1} + d_i): weight of index i at face i
-    const double *rc;     // 1 / (0.5 (d_{i-1} + d_i)): inverse centre distance across face i
+template <typename R>
+struct AxisT {
+    const R *d;      // cell size
+    const R *rd;     // 1 / d
+    const R *wlo;    // d_i / (d_{i-1} + d_i): weight of index i-1 at face i
+    const R *whi;    // d_{i-1} / (d_{i-1} + d_i): weight of index i at face i
+    const R *rc;     // 1 / (0.5 (d_{i-1} + d_i)): inverse centre distance across face i
 };
 
-struct Geo {
+template <typename R>
+struct GeoT {
     int nx, ny;
     int pitch;
     const uint16_t *flag;
-    Axis x, y;
+    AxisT<R> x, y;
 };
 
-struct Coef {
-    double A, B, CT1f, CT2f, CT3f, omega, dt, gx, gy;
+template <typename R>
+struct CoefT {
+    R A, B, CT1f, CT2f, CT3f, omega, dt, gx, gy;
 };
 
-struct Level {
-    double *u, *v, *p, *T, *rho, *gam;
+// One state level: u, v at faces; p, T, rho, Gamma at cell centres.
+template <typename R>
+struct LevelT {
+    R *u, *v, *p, *T, *rho, *gam;
+};
+
+// Scratch of one loop-2 iteration (all extended-indexed).
+template <typename R>
+struct WorkT {
+    R *rho_u, *rho_v;              // face densities (Eqs. pl10, pl11)
+    R *uhat, *du, *vhat, *dv;      // pseudo velocities and d (Eqs. pl14, pl20, pl21)
+    R *uexp, *vexp, *Texp;         // explicit convective terms (Eqs. pl15_11, pl31_1)
+};
+
+using Axis = AxisT<double>;
+using Geo = GeoT<double>;
+using Coef = CoefT<double>;
+using Level = LevelT<double>;
+
+struct Work : WorkT<double> {
+    unsigned long long *res;       // 4 residual maxima as ordered bit patterns
+};
+
+// FP32 side of the mixed-precision sweep: FP32 grid factors and
+// coefficients, FP32 shadow copies of the three state levels (refreshed
+// whenever a level changes) and FP32 iteration scratch.
+struct Mixed {
+    GeoT<float> g;
+    CoefT<float> k;
+    LevelT<float> lv[3];
+    WorkT<float> w;
 };
 
 // Boundary description used by the ghost refresh.
@@ -63,14 +95,6 @@ struct Sides {
 
 enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
 enum { BC_WALL = 0, BC_SYMMETRY = 1, BC_INFLOW = 2, BC_OUTFLOW = 3 };
-
-// Scratch of one loop-2 iteration (all extended-indexed).
-struct Work {
-    double *rho_u, *rho_v;        // face densities (Eqs. pl10, pl11)
-    double *uhat, *du, *vhat, *dv; // pseudo velocities and d (Eqs. pl14, pl20, pl21)
-    double *uexp, *vexp, *Texp;   // explicit convective terms (Eqs. pl15_11, pl31_1)
-    unsigned long long *res;      // 4 residual maxima as ordered bit patterns
-};
 
 // Launch wrappers (sweep_kernels.cu).  All are asynchronous on `stream`.
 void launch_face_densities(const Geo &g, const Level &lv, const Work &w, bool tvd, void *stream);
@@ -84,5 +108,17 @@ void launch_ghosts(const Geo &g, const Sides &s, const Level &lv, void *stream);
 void launch_derive(const Geo &g, const Coef &c, const Level &lv, void *stream);
 void launch_scatter(const Geo &g, int field, const double *src, const Level &lv, void *stream);
 void launch_gather(const Geo &g, int field, const Level &lv, double *dst, void *stream);
+
+// Mixed precision (FP32 assembly, FP64 pressure accumulation / EOS / residuals).
+void launch_face_densities_f32(const Mixed &m, int level, bool tvd, void *stream);
+void launch_explicit_terms_f32(const Mixed &m, int prev, bool tvd, void *stream);
+void launch_assemble_f32(const Mixed &m, int prev, int old, int nw, const Level &nw64, bool implicit, bool tvd,
+                         void *stream);
+void launch_pressure_mixed(const Geo &g, const Coef &c, const Mixed &m, const Level &prev, const Level &old,
+                           const Level &nw, int nw32, const Work &w, void *stream);
+void launch_velocity_mixed(const Geo &g, const Mixed &m, const Level &old, const Level &nw, int nw32,
+                           const Work &w, void *stream);
+void launch_ghosts_f32(const Mixed &m, const Sides &s, int level, void *stream);
+void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, size_t nelem, void *stream);
 
 }  // namespace stg

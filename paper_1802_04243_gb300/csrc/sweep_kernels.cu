@@ -1,5 +1,8 @@
-// sweep_kernels.cu -- FP64 CUDA kernels of one SIMPLE-TS time step
+// sweep_kernels.cu -- CUDA kernels of one SIMPLE-TS time step
 // (K. S. Shterev, arXiv:1802.04243, Sections 3.1 and 3.2) for sm_103a.
+// The equation kernels are templated on the arithmetic type: double for the
+// FP64 path, float for the FP32 assembly of the mixed-precision path (whose
+// pressure accumulation, equation of state and residuals stay FP64).
 //
 // One loop-2 iteration (Section 3.1, Figs. 1 and 2, GPU column) runs as
 //   k_face_densities   rho^u, rho^v of every face            (Eqs. pl8-pl11)
@@ -30,59 +33,66 @@ struct Ix {
     __device__ __forceinline__ int operator()(int i, int j) const { return (j + G) * P + (i + G); }
 };
 
-__device__ __forceinline__ double at(const double *a, int i) { return a[i + G]; }
+template <typename R>
+__device__ __forceinline__ R at(const R *a, int i) { return a[i + G]; }
 
 // ---------------------------------------------------------------- limiter
 
 // Van Leer psi(r) = (r + |r|)/(1 + r) for r = num/den; 0 unless num and den
 // share a sign (a zero denominator falls back to first order).
-__device__ __forceinline__ double van_leer(double num, double den)
+template <typename R>
+__device__ __forceinline__ R van_leer(R num, R den)
 {
-    return (num * den > 0.0) ? 2.0 * num / (num + den) : 0.0;
+    return (num * den > R(0)) ? R(2) * num / (num + den) : R(0);
 }
 
 // Eq. pl15_2: correction at the face between nodes 2 and 3; d1..d4 are the
 // cell sizes of the four nodes.
-__device__ __forceinline__ double psi_surface(double f1, double f2, double f3, double f4,
-                                              double d1, double d2, double d3, double d4, double vel)
+template <typename R>
+__device__ __forceinline__ R psi_surface(R f1, R f2, R f3, R f4, R d1, R d2, R d3, R d4, R vel)
 {
-    if (vel > 0.0)
+    if (vel > R(0))
         return d2 / (d2 + d3) * van_leer((d2 + d3) * (f2 - f1), (d1 + d2) * (f3 - f2));
     return -d3 / (d2 + d3) * van_leer((d2 + d3) * (f4 - f3), (d3 + d4) * (f3 - f2));
 }
 
 // Eq. pl15_1: face midway between nodes 2 and 3; d1..d3 the node distances.
-__device__ __forceinline__ double psi_centre(double f1, double f2, double f3, double f4,
-                                             double d1, double d2, double d3, double vel)
+template <typename R>
+__device__ __forceinline__ R psi_centre(R f1, R f2, R f3, R f4, R d1, R d2, R d3, R vel)
 {
-    if (vel > 0.0)
-        return 0.5 * van_leer(d2 * (f2 - f1), d1 * (f3 - f2));
-    return -0.5 * van_leer(d2 * (f4 - f3), d3 * (f3 - f2));
+    if (vel > R(0))
+        return R(0.5) * van_leer(d2 * (f2 - f1), d1 * (f3 - f2));
+    return R(-0.5) * van_leer(d2 * (f4 - f3), d3 * (f3 - f2));
 }
 
-__device__ __forceinline__ double upwind(double a, double b, double vel) { return vel > 0.0 ? a : b; }
-__device__ __forceinline__ double pos(double x) { return fmax(0.0, x); }
+template <typename R>
+__device__ __forceinline__ R upwind(R a, R b, R vel) { return vel > R(0) ? a : b; }
+template <typename R>
+__device__ __forceinline__ R pos(R x) { return fmax(R(0), x); }
 
 // Value of node m seen from node a: reflected about the stored wall value when
 // the flag of m carries `wall_bit`.
-__device__ __forceinline__ double seen(const double *f, const uint16_t *flag, int a, int m, uint32_t wall_bit)
+template <typename R>
+__device__ __forceinline__ R seen(const R *f, const uint16_t *flag, int a, int m, uint32_t wall_bit)
 {
-    double fm = f[m];
-    return (flag[m] & wall_bit) ? 2.0 * fm - f[a] : fm;
+    R fm = f[m];
+    return (flag[m] & wall_bit) ? R(2) * fm - f[a] : fm;
 }
 
 // Gamma at the corner (x^f_i, y^f_j): bilinear in the four cell centres.
-__device__ __forceinline__ double gamma_corner(const Geo &g, const double *gam, int c, int i, int j)
+template <typename R>
+__device__ __forceinline__ R gamma_corner(const GeoT<R> &g, const R *gam, int c, int i, int j)
 {
     const int P = g.pitch;
-    double lo = at(g.x.wlo, i) * gam[c - P - 1] + at(g.x.whi, i) * gam[c - P];
-    double hi = at(g.x.wlo, i) * gam[c - 1] + at(g.x.whi, i) * gam[c];
+    R lo = at(g.x.wlo, i) * gam[c - P - 1] + at(g.x.whi, i) * gam[c - P];
+    R hi = at(g.x.wlo, i) * gam[c - 1] + at(g.x.whi, i) * gam[c];
     return at(g.y.wlo, j) * lo + at(g.y.whi, j) * hi;
 }
 
 // Eq. pl33: distance-weighted harmonic mean of Gamma^lambda across a face
 // between a node of size da and one of size db.
-__device__ __forceinline__ double harmonic(double ga, double gb, double da, double db)
+template <typename R>
+__device__ __forceinline__ R harmonic(R ga, R gb, R da, R db)
 {
     return (da + db) * ga * gb / (da * gb + db * ga);
 }
@@ -125,27 +135,27 @@ __device__ __forceinline__ void block_max2(unsigned long long a, unsigned long l
 
 // rho^u at u face (i,j) and rho^v at v face (i,j), Eqs. pl10, pl11, written as
 // the upwind value plus psi_s times the difference across the face.
-template <bool TVD>
-__global__ void __launch_bounds__(BX *BY) k_face_densities(Geo g, const double *__restrict__ u,
-                                                            const double *__restrict__ v,
-                                                            const double *__restrict__ rho,
-                                                            double *__restrict__ rho_u,
-                                                            double *__restrict__ rho_v)
+template <typename R, bool TVD>
+__global__ void __launch_bounds__(BX *BY) k_face_densities(GeoT<R> g, const R *__restrict__ u,
+                                                            const R *__restrict__ v,
+                                                            const R *__restrict__ rho,
+                                                            R *__restrict__ rho_u,
+                                                            R *__restrict__ rho_v)
 {
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     const int P = g.pitch;
     const int c = Ix{P}(i, j);
     if (i <= g.nx && j < g.ny) {
-        const double vel = u[c], rl = rho[c - 1], rr = rho[c];
-        double val = upwind(rl, rr, vel);
+        const R vel = u[c], rl = rho[c - 1], rr = rho[c];
+        R val = upwind(rl, rr, vel);
         if (TVD && (g.flag[c] & F_TCX))
             val += psi_surface(rho[c - 2], rl, rr, rho[c + 1], at(g.x.d, i - 2), at(g.x.d, i - 1),
                                at(g.x.d, i), at(g.x.d, i + 1), vel) * (rr - rl);
         rho_u[c] = val;
     }
     if (i < g.nx && j <= g.ny) {
-        const double vel = v[c], rb = rho[c - P], rt = rho[c];
-        double val = upwind(rb, rt, vel);
+        const R vel = v[c], rb = rho[c - P], rt = rho[c];
+        R val = upwind(rb, rt, vel);
         if (TVD && (g.flag[c] & F_TCY))
             val += psi_surface(rho[c - 2 * P], rb, rt, rho[c + P], at(g.y.d, j - 2), at(g.y.d, j - 1),
                                at(g.y.d, j), at(g.y.d, j + 1), vel) * (rt - rb);
@@ -156,21 +166,21 @@ __global__ void __launch_bounds__(BX *BY) k_face_densities(Geo g, const double *
 // ------------------------------------------------------- explicit terms
 
 // T^explicit of cell (i,j), Eq. pl31_1, all inputs at level n-1.
-template <bool TVD>
-__device__ double explicit_T(const Geo &g, const Level &L, const double *rho_u, const double *rho_v,
+template <typename R, bool TVD>
+__device__ R explicit_T(const GeoT<R> &g, const LevelT<R> &L, const R *rho_u, const R *rho_v,
                              int c, int i, int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
-    const double dxi = at(g.x.d, i), dyj = at(g.y.d, j);
-    const double *T = L.T;
-    const double Tp = T[c];
-    const double Tw = seen(T, fl, c, c - 1, F_WALL), Te = seen(T, fl, c, c + 1, F_WALL);
-    const double Ts = seen(T, fl, c, c - P, F_WALL), Tn = seen(T, fl, c, c + P, F_WALL);
-    const double uw = L.u[c], ue = L.u[c + 1], vs = L.v[c], vn = L.v[c + P];
-    const double Fw = rho_u[c] * uw * dyj, Fe = rho_u[c + 1] * ue * dyj;
-    const double Fs = rho_v[c] * vs * dxi, Fn = rho_v[c + P] * vn * dxi;
-    double pw = 0.0, pe = 0.0, ps = 0.0, pn = 0.0;
+    const R dxi = at(g.x.d, i), dyj = at(g.y.d, j);
+    const R *T = L.T;
+    const R Tp = T[c];
+    const R Tw = seen(T, fl, c, c - 1, F_WALL), Te = seen(T, fl, c, c + 1, F_WALL);
+    const R Ts = seen(T, fl, c, c - P, F_WALL), Tn = seen(T, fl, c, c + P, F_WALL);
+    const R uw = L.u[c], ue = L.u[c + 1], vs = L.v[c], vn = L.v[c + P];
+    const R Fw = rho_u[c] * uw * dyj, Fe = rho_u[c + 1] * ue * dyj;
+    const R Fs = rho_v[c] * vs * dxi, Fn = rho_v[c + P] * vn * dxi;
+    R pw = 0.0, pe = 0.0, ps = 0.0, pn = 0.0;
     if (TVD) {
         if (fl[c + 1] & F_TCX)
             pe = psi_surface(T[c - 1], Tp, Te, T[c + 2], at(g.x.d, i - 1), dxi, at(g.x.d, i + 1), at(g.x.d, i + 2), ue);
@@ -186,30 +196,30 @@ __device__ double explicit_T(const Geo &g, const Level &L, const double *rho_u, 
 }
 
 // v^explicit of v face (i,j), Eq. pl15_11, level n-1.
-template <bool TVD>
-__device__ double explicit_v(const Geo &g, const Level &L, const double *rho_u, int b, int i, int j)
+template <typename R, bool TVD>
+__device__ R explicit_v(const GeoT<R> &g, const LevelT<R> &L, const R *rho_u, int b, int i, int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
-    const double *v = L.v, *u = L.u;
-    const double dxi = at(g.x.d, i), dys = at(g.y.d, j - 1), dyp = at(g.y.d, j);
-    const double vP = v[b], vW = seen(v, fl, b, b - 1, F_VWALL), vE = seen(v, fl, b, b + 1, F_VWALL);
-    const double vS = v[b - P], vN = v[b + P];
-    const double uw1 = u[b - P], uw2 = u[b], ue1 = u[b + 1 - P], ue2 = u[b + 1];
-    const double Fw1 = rho_u[b - P] * uw1 * dys, Fw2 = rho_u[b] * uw2 * dyp;
-    const double Fe1 = rho_u[b + 1 - P] * ue1 * dys, Fe2 = rho_u[b + 1] * ue2 * dyp;
-    const double vbs = 0.5 * (vS + vP), vbn = 0.5 * (vP + vN);
-    double pw1 = 0, pw2 = 0, pe1 = 0, pe2 = 0, ps = 0, pn = 0;
+    const R *v = L.v, *u = L.u;
+    const R dxi = at(g.x.d, i), dys = at(g.y.d, j - 1), dyp = at(g.y.d, j);
+    const R vP = v[b], vW = seen(v, fl, b, b - 1, F_VWALL), vE = seen(v, fl, b, b + 1, F_VWALL);
+    const R vS = v[b - P], vN = v[b + P];
+    const R uw1 = u[b - P], uw2 = u[b], ue1 = u[b + 1 - P], ue2 = u[b + 1];
+    const R Fw1 = rho_u[b - P] * uw1 * dys, Fw2 = rho_u[b] * uw2 * dyp;
+    const R Fe1 = rho_u[b + 1 - P] * ue1 * dys, Fe2 = rho_u[b + 1] * ue2 * dyp;
+    const R vbs = R(0.5) * (vS + vP), vbn = R(0.5) * (vP + vN);
+    R pw1 = 0, pw2 = 0, pe1 = 0, pe2 = 0, ps = 0, pn = 0;
     if (TVD) {
         if (fl[b + 1] & F_TVX) {
-            const double f1 = v[b - 1], f4 = v[b + 2];
-            const double d1 = at(g.x.d, i - 1), d3 = at(g.x.d, i + 1), d4 = at(g.x.d, i + 2);
+            const R f1 = v[b - 1], f4 = v[b + 2];
+            const R d1 = at(g.x.d, i - 1), d3 = at(g.x.d, i + 1), d4 = at(g.x.d, i + 2);
             pe1 = psi_surface(f1, vP, vE, f4, d1, dxi, d3, d4, ue1);
             pe2 = psi_surface(f1, vP, vE, f4, d1, dxi, d3, d4, ue2);
         }
         if (fl[b] & F_TVX) {
-            const double f1 = v[b - 2];
-            const double d1 = at(g.x.d, i - 2), d2 = at(g.x.d, i - 1), d4 = at(g.x.d, i + 1);
+            const R f1 = v[b - 2];
+            const R d1 = at(g.x.d, i - 2), d2 = at(g.x.d, i - 1), d4 = at(g.x.d, i + 1);
             pw1 = psi_surface(f1, vW, vP, vE, d1, d2, dxi, d4, uw1);
             pw2 = psi_surface(f1, vW, vP, vE, d1, d2, dxi, d4, uw2);
         }
@@ -218,37 +228,37 @@ __device__ double explicit_v(const Geo &g, const Level &L, const double *rho_u, 
         if (fl[b] & F_TVY)
             ps = psi_centre(v[b - 2 * P], vS, vP, vN, at(g.y.d, j - 2), dys, dyp, vbs);
     }
-    return -0.5 * (Fe1 * (upwind(vP, vE, ue1) + (vE - vP) * pe1) + Fe2 * (upwind(vP, vE, ue2) + (vE - vP) * pe2))
-           + 0.5 * (Fw1 * (upwind(vW, vP, uw1) + (vP - vW) * pw1) + Fw2 * (upwind(vW, vP, uw2) + (vP - vW) * pw2))
+    return R(-0.5) * (Fe1 * (upwind(vP, vE, ue1) + (vE - vP) * pe1) + Fe2 * (upwind(vP, vE, ue2) + (vE - vP) * pe2))
+           + R(0.5) * (Fw1 * (upwind(vW, vP, uw1) + (vP - vW) * pw1) + Fw2 * (upwind(vW, vP, uw2) + (vP - vW) * pw2))
            - dxi * L.rho[b] * vbn * (upwind(vP, vN, vbn) + (vN - vP) * pn)
            + dxi * L.rho[b - P] * vbs * (upwind(vS, vP, vbs) + (vP - vS) * ps);
 }
 
 // u^explicit of u face (i,j): the mirror image of Eq. pl15_11, level n-1.
-template <bool TVD>
-__device__ double explicit_u(const Geo &g, const Level &L, const double *rho_v, int a, int i, int j)
+template <typename R, bool TVD>
+__device__ R explicit_u(const GeoT<R> &g, const LevelT<R> &L, const R *rho_v, int a, int i, int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
-    const double *u = L.u, *v = L.v;
-    const double dyj = at(g.y.d, j), dxw = at(g.x.d, i - 1), dxp = at(g.x.d, i);
-    const double uP = u[a], uS = seen(u, fl, a, a - P, F_UWALL), uN = seen(u, fl, a, a + P, F_UWALL);
-    const double uW = u[a - 1], uE = u[a + 1];
-    const double vs1 = v[a - 1], vs2 = v[a], vn1 = v[a - 1 + P], vn2 = v[a + P];
-    const double Fs1 = rho_v[a - 1] * vs1 * dxw, Fs2 = rho_v[a] * vs2 * dxp;
-    const double Fn1 = rho_v[a - 1 + P] * vn1 * dxw, Fn2 = rho_v[a + P] * vn2 * dxp;
-    const double ubw = 0.5 * (uW + uP), ube = 0.5 * (uP + uE);
-    double pn1 = 0, pn2 = 0, ps1 = 0, ps2 = 0, pe = 0, pw = 0;
+    const R *u = L.u, *v = L.v;
+    const R dyj = at(g.y.d, j), dxw = at(g.x.d, i - 1), dxp = at(g.x.d, i);
+    const R uP = u[a], uS = seen(u, fl, a, a - P, F_UWALL), uN = seen(u, fl, a, a + P, F_UWALL);
+    const R uW = u[a - 1], uE = u[a + 1];
+    const R vs1 = v[a - 1], vs2 = v[a], vn1 = v[a - 1 + P], vn2 = v[a + P];
+    const R Fs1 = rho_v[a - 1] * vs1 * dxw, Fs2 = rho_v[a] * vs2 * dxp;
+    const R Fn1 = rho_v[a - 1 + P] * vn1 * dxw, Fn2 = rho_v[a + P] * vn2 * dxp;
+    const R ubw = R(0.5) * (uW + uP), ube = R(0.5) * (uP + uE);
+    R pn1 = 0, pn2 = 0, ps1 = 0, ps2 = 0, pe = 0, pw = 0;
     if (TVD) {
         if (fl[a + P] & F_TUY) {
-            const double f1 = u[a - P], f4 = u[a + 2 * P];
-            const double d1 = at(g.y.d, j - 1), d3 = at(g.y.d, j + 1), d4 = at(g.y.d, j + 2);
+            const R f1 = u[a - P], f4 = u[a + 2 * P];
+            const R d1 = at(g.y.d, j - 1), d3 = at(g.y.d, j + 1), d4 = at(g.y.d, j + 2);
             pn1 = psi_surface(f1, uP, uN, f4, d1, dyj, d3, d4, vn1);
             pn2 = psi_surface(f1, uP, uN, f4, d1, dyj, d3, d4, vn2);
         }
         if (fl[a] & F_TUY) {
-            const double f1 = u[a - 2 * P];
-            const double d1 = at(g.y.d, j - 2), d2 = at(g.y.d, j - 1), d4 = at(g.y.d, j + 1);
+            const R f1 = u[a - 2 * P];
+            const R d1 = at(g.y.d, j - 2), d2 = at(g.y.d, j - 1), d4 = at(g.y.d, j + 1);
             ps1 = psi_surface(f1, uS, uP, uN, d1, d2, dyj, d4, vs1);
             ps2 = psi_surface(f1, uS, uP, uN, d1, d2, dyj, d4, vs2);
         }
@@ -257,25 +267,25 @@ __device__ double explicit_u(const Geo &g, const Level &L, const double *rho_v, 
         if (fl[a] & F_TUX)
             pw = psi_centre(u[a - 2], uW, uP, uE, at(g.x.d, i - 2), dxw, dxp, ubw);
     }
-    return -0.5 * (Fn1 * (upwind(uP, uN, vn1) + (uN - uP) * pn1) + Fn2 * (upwind(uP, uN, vn2) + (uN - uP) * pn2))
-           + 0.5 * (Fs1 * (upwind(uS, uP, vs1) + (uP - uS) * ps1) + Fs2 * (upwind(uS, uP, vs2) + (uP - uS) * ps2))
+    return R(-0.5) * (Fn1 * (upwind(uP, uN, vn1) + (uN - uP) * pn1) + Fn2 * (upwind(uP, uN, vn2) + (uN - uP) * pn2))
+           + R(0.5) * (Fs1 * (upwind(uS, uP, vs1) + (uP - uS) * ps1) + Fs2 * (upwind(uS, uP, vs2) + (uP - uS) * ps2))
            - dyj * L.rho[a] * ube * (upwind(uP, uE, ube) + (uE - uP) * pe)
            + dyj * L.rho[a - 1] * ubw * (upwind(uW, uP, ubw) + (uP - uW) * pw);
 }
 
-template <bool TVD>
-__global__ void __launch_bounds__(BX *BY) k_explicit_terms(Geo g, Level prev, Work w)
+template <typename R, bool TVD>
+__global__ void __launch_bounds__(BX *BY) k_explicit_terms(GeoT<R> g, LevelT<R> prev, WorkT<R> w)
 {
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     const int c = Ix{g.pitch}(i, j);
     if (i > g.nx || j > g.ny) return;
     const uint16_t f = g.flag[c];
     if (i < g.nx && j < g.ny)
-        w.Texp[c] = (f & F_FLUID) ? explicit_T<TVD>(g, prev, w.rho_u, w.rho_v, c, i, j) : 0.0;
+        w.Texp[c] = (f & F_FLUID) ? explicit_T<R, TVD>(g, prev, w.rho_u, w.rho_v, c, i, j) : R(0);
     if (j < g.ny)
-        w.uexp[c] = (f & F_UACT) ? explicit_u<TVD>(g, prev, w.rho_v, c, i, j) : 0.0;
+        w.uexp[c] = (f & F_UACT) ? explicit_u<R, TVD>(g, prev, w.rho_v, c, i, j) : R(0);
     if (i < g.nx)
-        w.vexp[c] = (f & F_VACT) ? explicit_v<TVD>(g, prev, w.rho_u, c, i, j) : 0.0;
+        w.vexp[c] = (f & F_VACT) ? explicit_v<R, TVD>(g, prev, w.rho_u, c, i, j) : R(0);
 }
 
 // ------------------------------------------------------------ temperature
@@ -283,61 +293,62 @@ __global__ void __launch_bounds__(BX *BY) k_explicit_terms(Geo g, Level prev, Wo
 // Energy source S^T_c of cell (i,j), Eq. pl29 with S^T_p = 0 (Eq. pl28):
 // viscous dissipation (Eq. pl7) and pressure work; velocities off their
 // nodes are bilinear interpolations, reflected across walls.
-__device__ double energy_source(const Geo &g, const Coef &k, const Level &L, int c, int i, int j)
+template <typename R>
+__device__ R energy_source(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, int c, int i, int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
-    const double *u = L.u, *v = L.v;
-    const double dxi = at(g.x.d, i), dyj = at(g.y.d, j);
-    const double rdx = at(g.x.rd, i), rdy = at(g.y.rd, j);
-    const double dudx = (u[c + 1] - u[c]) * rdx;
-    const double dvdy = (v[c + P] - v[c]) * rdy;
-    const double xl0 = at(g.x.wlo, i), xh0 = at(g.x.whi, i), xl1 = at(g.x.wlo, i + 1), xh1 = at(g.x.whi, i + 1);
-    const double yl0 = at(g.y.wlo, j), yh0 = at(g.y.whi, j), yl1 = at(g.y.wlo, j + 1), yh1 = at(g.y.whi, j + 1);
+    const R *u = L.u, *v = L.v;
+    const R dxi = at(g.x.d, i), dyj = at(g.y.d, j);
+    const R rdx = at(g.x.rd, i), rdy = at(g.y.rd, j);
+    const R dudx = (u[c + 1] - u[c]) * rdx;
+    const R dvdy = (v[c + P] - v[c]) * rdy;
+    const R xl0 = at(g.x.wlo, i), xh0 = at(g.x.whi, i), xl1 = at(g.x.wlo, i + 1), xh1 = at(g.x.whi, i + 1);
+    const R yl0 = at(g.y.wlo, j), yh0 = at(g.y.whi, j), yl1 = at(g.y.wlo, j + 1), yh1 = at(g.y.whi, j + 1);
     // v at (x^f_i, y^v_j) and (x^f_{i+1}, y^v_j)
-    const double v_w = 0.5 * ((xl0 * seen(v, fl, c, c - 1, F_VWALL) + xh0 * v[c])
+    const R v_w = R(0.5) * ((xl0 * seen(v, fl, c, c - 1, F_VWALL) + xh0 * v[c])
                               + (xl0 * seen(v, fl, c + P, c + P - 1, F_VWALL) + xh0 * v[c + P]));
-    const double v_e = 0.5 * ((xl1 * v[c] + xh1 * seen(v, fl, c, c + 1, F_VWALL))
+    const R v_e = R(0.5) * ((xl1 * v[c] + xh1 * seen(v, fl, c, c + 1, F_VWALL))
                               + (xl1 * v[c + P] + xh1 * seen(v, fl, c + P, c + P + 1, F_VWALL)));
     // u at (x^v_i, y^f_j) and (x^v_i, y^f_{j+1})
-    const double u_s = 0.5 * ((yl0 * seen(u, fl, c, c - P, F_UWALL) + yh0 * u[c])
+    const R u_s = R(0.5) * ((yl0 * seen(u, fl, c, c - P, F_UWALL) + yh0 * u[c])
                               + (yl0 * seen(u, fl, c + 1, c + 1 - P, F_UWALL) + yh0 * u[c + 1]));
-    const double u_n = 0.5 * ((yl1 * u[c] + yh1 * seen(u, fl, c, c + P, F_UWALL))
+    const R u_n = R(0.5) * ((yl1 * u[c] + yh1 * seen(u, fl, c, c + P, F_UWALL))
                               + (yl1 * u[c + 1] + yh1 * seen(u, fl, c + 1, c + 1 + P, F_UWALL)));
-    const double dvdx = (v_e - v_w) * rdx, dudy = (u_n - u_s) * rdy;
-    const double div = dudx + dvdy, shear = dvdx + dudy;
-    const double phi = 2.0 * (dudx * dudx + dvdy * dvdy) + shear * shear - (2.0 / 3.0) * div * div;
-    const double vol = dxi * dyj;
+    const R dvdx = (v_e - v_w) * rdx, dudy = (u_n - u_s) * rdy;
+    const R div = dudx + dvdy, shear = dvdx + dudy;
+    const R phi = R(2) * (dudx * dudx + dvdy * dvdy) + shear * shear - R(2.0 / 3.0) * div * div;
+    const R vol = dxi * dyj;
     return (k.CT2f * L.gam[c] * phi + k.CT3f * L.p[c] * div) * vol;
 }
 
 // New temperature of fluid cell (i,j): Eq. pl30 with the implicit
 // coefficients of Eq. pl31 or the explicit ones of Eq. pl31_1, conductances
 // Eq. pl32 with the harmonic mean Eq. pl33.
-template <bool IMPL, bool TVD>
-__device__ double temperature(const Geo &g, const Coef &k, const Level &prev, const Level &old,
-                              const Work &w, int c, int i, int j)
+template <typename R, bool IMPL, bool TVD>
+__device__ R temperature(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev, const LevelT<R> &old,
+                         const WorkT<R> &w, int c, int i, int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
-    const double *T = old.T, *gam = old.gam;
-    const double dxi = at(g.x.d, i), dyj = at(g.y.d, j);
-    const double dxw = at(g.x.d, i - 1), dxe = at(g.x.d, i + 1), dys = at(g.y.d, j - 1), dyn = at(g.y.d, j + 1);
-    const double Tp = T[c];
-    const double Tw = seen(T, fl, c, c - 1, F_WALL), Te = seen(T, fl, c, c + 1, F_WALL);
-    const double Ts = seen(T, fl, c, c - P, F_WALL), Tn = seen(T, fl, c, c + P, F_WALL);
-    const double uw = old.u[c], ue = old.u[c + 1], vs = old.v[c], vn = old.v[c + P];
-    const double Fw = w.rho_u[c] * uw * dyj, Fe = w.rho_u[c + 1] * ue * dyj;
-    const double Fs = w.rho_v[c] * vs * dxi, Fn = w.rho_v[c + P] * vn * dxi;
-    const double gp = gam[c];
-    const double Dw = k.CT1f * harmonic(gam[c - 1], gp, dxw, dxi) * dyj * at(g.x.rc, i);
-    const double De = k.CT1f * harmonic(gp, gam[c + 1], dxi, dxe) * dyj * at(g.x.rc, i + 1);
-    const double Ds = k.CT1f * harmonic(gam[c - P], gp, dys, dyj) * dxi * at(g.y.rc, j);
-    const double Dn = k.CT1f * harmonic(gp, gam[c + P], dyj, dyn) * dxi * at(g.y.rc, j + 1);
-    const double vol = dxi * dyj;
-    double a1, a2, a3, a4, a0, texp;
+    const R *T = old.T, *gam = old.gam;
+    const R dxi = at(g.x.d, i), dyj = at(g.y.d, j);
+    const R dxw = at(g.x.d, i - 1), dxe = at(g.x.d, i + 1), dys = at(g.y.d, j - 1), dyn = at(g.y.d, j + 1);
+    const R Tp = T[c];
+    const R Tw = seen(T, fl, c, c - 1, F_WALL), Te = seen(T, fl, c, c + 1, F_WALL);
+    const R Ts = seen(T, fl, c, c - P, F_WALL), Tn = seen(T, fl, c, c + P, F_WALL);
+    const R uw = old.u[c], ue = old.u[c + 1], vs = old.v[c], vn = old.v[c + P];
+    const R Fw = w.rho_u[c] * uw * dyj, Fe = w.rho_u[c + 1] * ue * dyj;
+    const R Fs = w.rho_v[c] * vs * dxi, Fn = w.rho_v[c + P] * vn * dxi;
+    const R gp = gam[c];
+    const R Dw = k.CT1f * harmonic(gam[c - 1], gp, dxw, dxi) * dyj * at(g.x.rc, i);
+    const R De = k.CT1f * harmonic(gp, gam[c + 1], dxi, dxe) * dyj * at(g.x.rc, i + 1);
+    const R Ds = k.CT1f * harmonic(gam[c - P], gp, dys, dyj) * dxi * at(g.y.rc, j);
+    const R Dn = k.CT1f * harmonic(gp, gam[c + P], dyj, dyn) * dxi * at(g.y.rc, j + 1);
+    const R vol = dxi * dyj;
+    R a1, a2, a3, a4, a0, texp;
     if (IMPL) {
-        double pw = 0.0, pe = 0.0, ps = 0.0, pn = 0.0;
+        R pw = 0.0, pe = 0.0, ps = 0.0, pn = 0.0;
         if (TVD) {
             if (fl[c] & F_TCX)
                 pw = psi_surface(T[c - 2], Tw, Tp, Te, at(g.x.d, i - 2), dxw, dxi, dxe, uw);
@@ -353,14 +364,14 @@ __device__ double temperature(const Geo &g, const Coef &k, const Level &prev, co
         a3 = pos(Fs) - Fs * ps + Ds;
         a4 = pos(-Fn) - Fn * pn + Dn;
         a0 = k.dt * (a1 + a2 + a3 + a4 + Fe - Fw + Fn - Fs) + old.rho[c] * vol;
-        texp = 0.0;
+        texp = R(0);
     } else {
         a1 = Dw; a2 = De; a3 = Ds; a4 = Dn;
         a0 = k.dt * (a1 + a2 + a3 + a4) + old.rho[c] * vol;
         texp = w.Texp[c];
     }
-    const double sc = energy_source(g, k, old, c, i, j);
-    const double rhs = k.dt * (a1 * Tw + a2 * Te + a3 * Ts + a4 * Tn + sc + texp) + prev.rho[c] * prev.T[c] * vol;
+    const R sc = energy_source(g, k, old, c, i, j);
+    const R rhs = k.dt * (a1 * Tw + a2 * Te + a3 * Ts + a4 * Tn + sc + texp) + prev.rho[c] * prev.T[c] * vol;
     return rhs / a0;
 }
 
@@ -368,114 +379,114 @@ __device__ double temperature(const Geo &g, const Coef &k, const Level &prev, co
 
 // u^ and d^u of u face (i,j) between fluid cells: the mirror image of
 // Eqs. pl14-pl16 and pl20 (the 4/3 normal-stress factor on the x direction).
-template <bool IMPL, bool TVD>
-__device__ void pseudo_u(const Geo &g, const Coef &k, const Level &prev, const Level &old, const Work &w,
-                         int a, int i, int j, double &uhat, double &du)
+template <typename R, bool IMPL, bool TVD>
+__device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev, const LevelT<R> &old,
+                         const WorkT<R> &w, int a, int i, int j, R &uhat, R &du)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
-    const double *u = old.u, *v = old.v, *gam = old.gam, *rho = old.rho;
-    const double dxw = at(g.x.d, i - 1), dxp = at(g.x.d, i), dyj = at(g.y.d, j);
-    const double uP = u[a];
-    const double uW = seen(u, fl, a, a - 1, F_UWALL), uE = seen(u, fl, a, a + 1, F_UWALL);
-    const double uS = seen(u, fl, a, a - P, F_UWALL), uN = seen(u, fl, a, a + P, F_UWALL);
-    const double ubw = 0.5 * (uW + uP), ube = 0.5 * (uP + uE);
-    const double Fbw = ubw * rho[a - 1] * dyj, Fbe = ube * rho[a] * dyj;
-    const double vs1 = v[a - 1], vs2 = v[a], vn1 = v[a - 1 + P], vn2 = v[a + P];
-    const double Fs1 = w.rho_v[a - 1] * vs1 * dxw, Fs2 = w.rho_v[a] * vs2 * dxp;
-    const double Fn1 = w.rho_v[a - 1 + P] * vn1 * dxw, Fn2 = w.rho_v[a + P] * vn2 * dxp;
-    const double gcs = gamma_corner(g, gam, a, i, j), gcn = gamma_corner(g, gam, a + P, i, j + 1);
-    const double Dxw = k.B * gam[a - 1] * dyj * at(g.x.rd, i - 1);
-    const double Dxe = k.B * gam[a] * dyj * at(g.x.rd, i);
-    const double wsum = dxp + dxw;
-    const double Dys = k.B * gcs * wsum * (0.5 * at(g.y.rc, j));
-    const double Dyn = k.B * gcn * wsum * (0.5 * at(g.y.rc, j + 1));
-    const double r2dt = 0.5 / k.dt;
-    const double trans = (rho[a] * dxp + rho[a - 1] * dxw) * dyj * r2dt;
-    const double b = (prev.rho[a] * dxp + prev.rho[a - 1] * dxw) * dyj * r2dt * prev.u[a]
+    const R *u = old.u, *v = old.v, *gam = old.gam, *rho = old.rho;
+    const R dxw = at(g.x.d, i - 1), dxp = at(g.x.d, i), dyj = at(g.y.d, j);
+    const R uP = u[a];
+    const R uW = seen(u, fl, a, a - 1, F_UWALL), uE = seen(u, fl, a, a + 1, F_UWALL);
+    const R uS = seen(u, fl, a, a - P, F_UWALL), uN = seen(u, fl, a, a + P, F_UWALL);
+    const R ubw = R(0.5) * (uW + uP), ube = R(0.5) * (uP + uE);
+    const R Fbw = ubw * rho[a - 1] * dyj, Fbe = ube * rho[a] * dyj;
+    const R vs1 = v[a - 1], vs2 = v[a], vn1 = v[a - 1 + P], vn2 = v[a + P];
+    const R Fs1 = w.rho_v[a - 1] * vs1 * dxw, Fs2 = w.rho_v[a] * vs2 * dxp;
+    const R Fn1 = w.rho_v[a - 1 + P] * vn1 * dxw, Fn2 = w.rho_v[a + P] * vn2 * dxp;
+    const R gcs = gamma_corner(g, gam, a, i, j), gcn = gamma_corner(g, gam, a + P, i, j + 1);
+    const R Dxw = k.B * gam[a - 1] * dyj * at(g.x.rd, i - 1);
+    const R Dxe = k.B * gam[a] * dyj * at(g.x.rd, i);
+    const R wsum = dxp + dxw;
+    const R Dys = k.B * gcs * wsum * (R(0.5) * at(g.y.rc, j));
+    const R Dyn = k.B * gcn * wsum * (R(0.5) * at(g.y.rc, j + 1));
+    const R r2dt = R(0.5) / k.dt;
+    const R trans = (rho[a] * dxp + rho[a - 1] * dxw) * dyj * r2dt;
+    const R b = (prev.rho[a] * dxp + prev.rho[a - 1] * dxw) * dyj * r2dt * prev.u[a]
                      + k.B * (gcn * (vn2 - vn1) - gcs * (vs2 - vs1)
-                              - (2.0 / 3.0) * gam[a] * (vn2 - vs2) + (2.0 / 3.0) * gam[a - 1] * (vn1 - vs1))
-                     + k.gx * (rho[a] * dxp + rho[a - 1] * dxw) * dyj * 0.5;
-    double a1, a2, a3, a4, a0, uexp;
+                              - R(2.0 / 3.0) * gam[a] * (vn2 - vs2) + R(2.0 / 3.0) * gam[a - 1] * (vn1 - vs1))
+                     + k.gx * (rho[a] * dxp + rho[a - 1] * dxw) * dyj * R(0.5);
+    R a1, a2, a3, a4, a0, uexp;
     if (IMPL) {
-        double pw = 0, pe = 0, ps1 = 0, ps2 = 0, pn1 = 0, pn2 = 0;
+        R pw = 0, pe = 0, ps1 = 0, ps2 = 0, pn1 = 0, pn2 = 0;
         if (TVD) {
             if (fl[a] & F_TUX)
                 pw = psi_centre(u[a - 2], uW, uP, uE, at(g.x.d, i - 2), dxw, dxp, ubw);
             if (fl[a + 1] & F_TUX)
                 pe = psi_centre(uW, uP, uE, u[a + 2], dxw, dxp, at(g.x.d, i + 1), ube);
             if (fl[a] & F_TUY) {
-                const double f1 = u[a - 2 * P];
-                const double d1 = at(g.y.d, j - 2), d2 = at(g.y.d, j - 1), d4 = at(g.y.d, j + 1);
+                const R f1 = u[a - 2 * P];
+                const R d1 = at(g.y.d, j - 2), d2 = at(g.y.d, j - 1), d4 = at(g.y.d, j + 1);
                 ps1 = psi_surface(f1, uS, uP, uN, d1, d2, dyj, d4, vs1);
                 ps2 = psi_surface(f1, uS, uP, uN, d1, d2, dyj, d4, vs2);
             }
             if (fl[a + P] & F_TUY) {
-                const double f4 = u[a + 2 * P];
-                const double d1 = at(g.y.d, j - 1), d3 = at(g.y.d, j + 1), d4 = at(g.y.d, j + 2);
+                const R f4 = u[a + 2 * P];
+                const R d1 = at(g.y.d, j - 1), d3 = at(g.y.d, j + 1), d4 = at(g.y.d, j + 2);
                 pn1 = psi_surface(uS, uP, uN, f4, d1, dyj, d3, d4, vn1);
                 pn2 = psi_surface(uS, uP, uN, f4, d1, dyj, d3, d4, vn2);
             }
         }
-        a1 = pos(Fbw) - Fbw * pw + (4.0 / 3.0) * Dxw;
-        a2 = pos(-Fbe) - Fbe * pe + (4.0 / 3.0) * Dxe;
-        a3 = 0.5 * (pos(Fs1) - Fs1 * ps1 + pos(Fs2) - Fs2 * ps2) + Dys;
-        a4 = 0.5 * (pos(-Fn1) - Fn1 * pn1 + pos(-Fn2) - Fn2 * pn2) + Dyn;
-        a0 = a1 + a2 + a3 + a4 + 0.5 * (Fn2 - Fs2 + Fn1 - Fs1) + Fbe - Fbw + trans;
-        uexp = 0.0;
+        a1 = pos(Fbw) - Fbw * pw + R(4.0 / 3.0) * Dxw;
+        a2 = pos(-Fbe) - Fbe * pe + R(4.0 / 3.0) * Dxe;
+        a3 = R(0.5) * (pos(Fs1) - Fs1 * ps1 + pos(Fs2) - Fs2 * ps2) + Dys;
+        a4 = R(0.5) * (pos(-Fn1) - Fn1 * pn1 + pos(-Fn2) - Fn2 * pn2) + Dyn;
+        a0 = a1 + a2 + a3 + a4 + R(0.5) * (Fn2 - Fs2 + Fn1 - Fs1) + Fbe - Fbw + trans;
+        uexp = R(0);
     } else {
-        a1 = (4.0 / 3.0) * Dxw; a2 = (4.0 / 3.0) * Dxe; a3 = Dys; a4 = Dyn;
+        a1 = R(4.0 / 3.0) * Dxw; a2 = R(4.0 / 3.0) * Dxe; a3 = Dys; a4 = Dyn;
         a0 = a1 + a2 + a3 + a4 + trans;
         uexp = w.uexp[a];
     }
-    const double r = 1.0 / a0;
+    const R r = R(1) / a0;
     uhat = (a1 * uW + a2 * uE + a3 * uS + a4 * uN + b + uexp) * r;
     du = k.A * dyj * r;
 }
 
 // v^ and d^v of v face (i,j) between fluid cells, Eqs. pl14-pl16, pl21
 // (implicit, Eq. pl15; explicit, Eq. pl15_11).
-template <bool IMPL, bool TVD>
-__device__ void pseudo_v(const Geo &g, const Coef &k, const Level &prev, const Level &old, const Work &w,
-                         int b, int i, int j, double &vhat, double &dv)
+template <typename R, bool IMPL, bool TVD>
+__device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev, const LevelT<R> &old,
+                         const WorkT<R> &w, int b, int i, int j, R &vhat, R &dv)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
-    const double *u = old.u, *v = old.v, *gam = old.gam, *rho = old.rho;
-    const double dys = at(g.y.d, j - 1), dyp = at(g.y.d, j), dxi = at(g.x.d, i);
-    const double vP = v[b];
-    const double vW = seen(v, fl, b, b - 1, F_VWALL), vE = seen(v, fl, b, b + 1, F_VWALL);
-    const double vS = seen(v, fl, b, b - P, F_VWALL), vN = seen(v, fl, b, b + P, F_VWALL);
-    const double vbs = 0.5 * (vS + vP), vbn = 0.5 * (vP + vN);
-    const double Fbs = vbs * rho[b - P] * dxi, Fbn = vbn * rho[b] * dxi;
-    const double uw1 = u[b - P], uw2 = u[b], ue1 = u[b + 1 - P], ue2 = u[b + 1];
-    const double Fw1 = w.rho_u[b - P] * uw1 * dys, Fw2 = w.rho_u[b] * uw2 * dyp;
-    const double Fe1 = w.rho_u[b + 1 - P] * ue1 * dys, Fe2 = w.rho_u[b + 1] * ue2 * dyp;
-    const double gcw = gamma_corner(g, gam, b, i, j), gce = gamma_corner(g, gam, b + 1, i + 1, j);
-    const double hsum = dyp + dys;
-    const double Dxw = k.B * gcw * hsum * (0.5 * at(g.x.rc, i));
-    const double Dxe = k.B * gce * hsum * (0.5 * at(g.x.rc, i + 1));
-    const double Dys = k.B * gam[b - P] * dxi * at(g.y.rd, j - 1);
-    const double Dyn = k.B * gam[b] * dxi * at(g.y.rd, j);
-    const double r2dt = 0.5 / k.dt;
-    const double trans = (rho[b] * dyp + rho[b - P] * dys) * dxi * r2dt;
-    const double bsrc = (prev.rho[b] * dyp + prev.rho[b - P] * dys) * dxi * r2dt * prev.v[b]
+    const R *u = old.u, *v = old.v, *gam = old.gam, *rho = old.rho;
+    const R dys = at(g.y.d, j - 1), dyp = at(g.y.d, j), dxi = at(g.x.d, i);
+    const R vP = v[b];
+    const R vW = seen(v, fl, b, b - 1, F_VWALL), vE = seen(v, fl, b, b + 1, F_VWALL);
+    const R vS = seen(v, fl, b, b - P, F_VWALL), vN = seen(v, fl, b, b + P, F_VWALL);
+    const R vbs = R(0.5) * (vS + vP), vbn = R(0.5) * (vP + vN);
+    const R Fbs = vbs * rho[b - P] * dxi, Fbn = vbn * rho[b] * dxi;
+    const R uw1 = u[b - P], uw2 = u[b], ue1 = u[b + 1 - P], ue2 = u[b + 1];
+    const R Fw1 = w.rho_u[b - P] * uw1 * dys, Fw2 = w.rho_u[b] * uw2 * dyp;
+    const R Fe1 = w.rho_u[b + 1 - P] * ue1 * dys, Fe2 = w.rho_u[b + 1] * ue2 * dyp;
+    const R gcw = gamma_corner(g, gam, b, i, j), gce = gamma_corner(g, gam, b + 1, i + 1, j);
+    const R hsum = dyp + dys;
+    const R Dxw = k.B * gcw * hsum * (R(0.5) * at(g.x.rc, i));
+    const R Dxe = k.B * gce * hsum * (R(0.5) * at(g.x.rc, i + 1));
+    const R Dys = k.B * gam[b - P] * dxi * at(g.y.rd, j - 1);
+    const R Dyn = k.B * gam[b] * dxi * at(g.y.rd, j);
+    const R r2dt = R(0.5) / k.dt;
+    const R trans = (rho[b] * dyp + rho[b - P] * dys) * dxi * r2dt;
+    const R bsrc = (prev.rho[b] * dyp + prev.rho[b - P] * dys) * dxi * r2dt * prev.v[b]
                         + k.B * (gce * (ue2 - ue1) - gcw * (uw2 - uw1)
-                                 - (2.0 / 3.0) * gam[b] * (ue2 - uw2) + (2.0 / 3.0) * gam[b - P] * (ue1 - uw1))
-                        + k.gy * (rho[b] * dyp + rho[b - P] * dys) * dxi * 0.5;
-    double a1, a2, a3, a4, a0, vexp;
+                                 - R(2.0 / 3.0) * gam[b] * (ue2 - uw2) + R(2.0 / 3.0) * gam[b - P] * (ue1 - uw1))
+                        + k.gy * (rho[b] * dyp + rho[b - P] * dys) * dxi * R(0.5);
+    R a1, a2, a3, a4, a0, vexp;
     if (IMPL) {
-        double pw1 = 0, pw2 = 0, pe1 = 0, pe2 = 0, ps = 0, pn = 0;
+        R pw1 = 0, pw2 = 0, pe1 = 0, pe2 = 0, ps = 0, pn = 0;
         if (TVD) {
             if (fl[b] & F_TVX) {
-                const double f1 = v[b - 2];
-                const double d1 = at(g.x.d, i - 2), d2 = at(g.x.d, i - 1), d4 = at(g.x.d, i + 1);
+                const R f1 = v[b - 2];
+                const R d1 = at(g.x.d, i - 2), d2 = at(g.x.d, i - 1), d4 = at(g.x.d, i + 1);
                 pw1 = psi_surface(f1, vW, vP, vE, d1, d2, dxi, d4, uw1);
                 pw2 = psi_surface(f1, vW, vP, vE, d1, d2, dxi, d4, uw2);
             }
             if (fl[b + 1] & F_TVX) {
-                const double f4 = v[b + 2];
-                const double d1 = at(g.x.d, i - 1), d3 = at(g.x.d, i + 1), d4 = at(g.x.d, i + 2);
+                const R f4 = v[b + 2];
+                const R d1 = at(g.x.d, i - 1), d3 = at(g.x.d, i + 1), d4 = at(g.x.d, i + 2);
                 pe1 = psi_surface(vW, vP, vE, f4, d1, dxi, d3, d4, ue1);
                 pe2 = psi_surface(vW, vP, vE, f4, d1, dxi, d3, d4, ue2);
             }
@@ -484,42 +495,50 @@ __device__ void pseudo_v(const Geo &g, const Coef &k, const Level &prev, const L
             if (fl[b + P] & F_TVY)
                 pn = psi_centre(vS, vP, vN, v[b + 2 * P], dys, dyp, at(g.y.d, j + 1), vbn);
         }
-        a1 = 0.5 * (pos(Fw2) - Fw2 * pw2 + pos(Fw1) - Fw1 * pw1) + Dxw;
-        a2 = 0.5 * (pos(-Fe2) - Fe2 * pe2 + pos(-Fe1) - Fe1 * pe1) + Dxe;
-        a3 = pos(Fbs) - Fbs * ps + (4.0 / 3.0) * Dys;
-        a4 = pos(-Fbn) - Fbn * pn + (4.0 / 3.0) * Dyn;
-        a0 = a1 + a2 + a3 + a4 + 0.5 * (Fe2 - Fw2 + Fe1 - Fw1) + Fbn - Fbs + trans;
-        vexp = 0.0;
+        a1 = R(0.5) * (pos(Fw2) - Fw2 * pw2 + pos(Fw1) - Fw1 * pw1) + Dxw;
+        a2 = R(0.5) * (pos(-Fe2) - Fe2 * pe2 + pos(-Fe1) - Fe1 * pe1) + Dxe;
+        a3 = pos(Fbs) - Fbs * ps + R(4.0 / 3.0) * Dys;
+        a4 = pos(-Fbn) - Fbn * pn + R(4.0 / 3.0) * Dyn;
+        a0 = a1 + a2 + a3 + a4 + R(0.5) * (Fe2 - Fw2 + Fe1 - Fw1) + Fbn - Fbs + trans;
+        vexp = R(0);
     } else {
-        a1 = Dxw; a2 = Dxe; a3 = (4.0 / 3.0) * Dys; a4 = (4.0 / 3.0) * Dyn;
+        a1 = Dxw; a2 = Dxe; a3 = R(4.0 / 3.0) * Dys; a4 = R(4.0 / 3.0) * Dyn;
         a0 = a1 + a2 + a3 + a4 + trans;
         vexp = w.vexp[b];
     }
-    const double r = 1.0 / a0;
+    const R r = R(1) / a0;
     vhat = (a1 * vW + a2 * vE + a3 * vS + a4 * vN + bsrc + vexp) * r;
     dv = k.A * dxi * r;
 }
 
-template <bool IMPL, bool TVD>
-__global__ void __launch_bounds__(BX *BY) k_assemble(Geo g, Coef k, Level prev, Level old, Level nw, Work w)
+// One thread per position: T of the cell, u^/d^u of the u face, v^/d^v of
+// the v face.  The new T goes to T_out (state precision) and, for the FP32
+// assembly of the mixed path, also to T32_out (the FP32 shadow copy).
+template <typename R, bool IMPL, bool TVD>
+__global__ void __launch_bounds__(BX *BY) k_assemble(GeoT<R> g, CoefT<R> k, LevelT<R> prev, LevelT<R> old,
+                                                      double *__restrict__ T_out, float *__restrict__ T32_out,
+                                                      WorkT<R> w)
 {
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     if (i > g.nx || j > g.ny) return;
     const int c = Ix{g.pitch}(i, j);
     const uint16_t f = g.flag[c];
-    if (i < g.nx && j < g.ny && (f & F_FLUID))
-        nw.T[c] = temperature<IMPL, TVD>(g, k, prev, old, w, c, i, j);
+    if (i < g.nx && j < g.ny && (f & F_FLUID)) {
+        const R Tn = temperature<R, IMPL, TVD>(g, k, prev, old, w, c, i, j);
+        T_out[c] = (double)Tn;
+        if (T32_out) T32_out[c] = (float)Tn;
+    }
     if (j < g.ny) {
-        double uh = old.u[c], d = 0.0;        // faces that are not unknowns: stored u, d = 0
+        R uh = old.u[c], d = R(0);            // faces that are not unknowns: stored u, d = 0
         if (f & F_UACT)
-            pseudo_u<IMPL, TVD>(g, k, prev, old, w, c, i, j, uh, d);
+            pseudo_u<R, IMPL, TVD>(g, k, prev, old, w, c, i, j, uh, d);
         w.uhat[c] = uh;
         w.du[c] = d;
     }
     if (i < g.nx) {
-        double vh = old.v[c], d = 0.0;
+        R vh = old.v[c], d = R(0);
         if (f & F_VACT)
-            pseudo_v<IMPL, TVD>(g, k, prev, old, w, c, i, j, vh, d);
+            pseudo_v<R, IMPL, TVD>(g, k, prev, old, w, c, i, j, vh, d);
         w.vhat[c] = vh;
         w.dv[c] = d;
     }
@@ -587,13 +606,14 @@ __global__ void __launch_bounds__(BX *BY) k_velocity(Geo g, Level old, Level nw,
 // ------------------------------------------------------------ ghost copies
 
 // West/east sides, one thread per row j in [0, ny].
-__global__ void k_ghost_we(Geo g, Sides s, Level L)
+template <typename R>
+__global__ void k_ghost_we(GeoT<R> g, Sides s, LevelT<R> L)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j > g.ny) return;
     const Ix ix{g.pitch};
     const int nx = g.nx;
-    double *sc[4] = {L.p, L.T, L.rho, L.gam};
+    R *sc[4] = {L.p, L.T, L.rho, L.gam};
     if (s.kind[SIDE_E] == BC_OUTFLOW) {
         if (j < g.ny) {
             const int src = ix(nx - 1, j);
@@ -601,12 +621,12 @@ __global__ void k_ghost_we(Geo g, Sides s, Level L)
                 sc[q][ix(nx, j)] = sc[q][src];
                 sc[q][ix(nx + 1, j)] = sc[q][src];
             }
-            const double us = L.u[src];
+            const R us = L.u[src];
             L.u[ix(nx, j)] = us;
             L.u[ix(nx + 1, j)] = us;
             L.u[ix(nx + 2, j)] = us;
         }
-        const double vs = L.v[ix(nx - 1, j)];
+        const R vs = L.v[ix(nx - 1, j)];
         L.v[ix(nx, j)] = vs;
         L.v[ix(nx + 1, j)] = vs;
     }
@@ -637,13 +657,14 @@ __global__ void k_ghost_we(Geo g, Sides s, Level L)
 }
 
 // South/north symmetry sides, one thread per column i in [-2, nx+2].
-__global__ void k_ghost_sn(Geo g, Sides s, Level L)
+template <typename R>
+__global__ void k_ghost_sn(GeoT<R> g, Sides s, LevelT<R> L)
 {
     const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - G;
     if (i > g.nx + G) return;
     const Ix ix{g.pitch};
     const int ny = g.ny;
-    double *sc[4] = {L.p, L.T, L.rho, L.gam};
+    R *sc[4] = {L.p, L.T, L.rho, L.gam};
     const bool cell = i <= g.nx + 1;
     if (s.kind[SIDE_S] == BC_SYMMETRY) {
         if (cell)
@@ -670,6 +691,104 @@ __global__ void k_ghost_sn(Geo g, Sides s, Level L)
             L.v[ix(i, ny + 1)] = -L.v[ix(i, ny - 1)];
             L.v[ix(i, ny + 2)] = -L.v[ix(i, ny - 2)];
         }
+    }
+}
+
+// --------------------------------------------------------- mixed precision
+
+// Mixed precision, pressure: the coefficients of Eqs. pl23, pl24 come from
+// the FP32 assembly (FP32 rho^u, d, u^ and the new T); the accumulation of
+// the neighbour pressures and the source, the division by a^p_0, the
+// equation of state rho = p/T and the residuals are FP64.  The FP64
+// reciprocals start from the FP32 reciprocal and take one Newton step
+// (relative error below 1e-14).  Gamma = T^omega is a coefficient: FP32.
+__global__ void __launch_bounds__(BX *BY) k_pressure_mixed(Geo g, Coef k, GeoT<float> g32, CoefT<float> k32,
+                                                            Level prev, Level old, Level nw, LevelT<float> nw32,
+                                                            WorkT<float> w, unsigned long long *res)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    const int P = g.pitch;
+    unsigned long long rp = 0, rT = 0;
+    if (i < g.nx && j < g.ny) {
+        const int c = Ix{P}(i, j);
+        if (g.flag[c] & F_FLUID) {
+            const float dxi = at(g32.x.d, i), dyj = at(g32.y.d, j);
+            const float ru_w = w.rho_u[c], ru_e = w.rho_u[c + 1], rv_s = w.rho_v[c], rv_n = w.rho_v[c + P];
+            const float apw = ru_w * w.du[c] * dyj, ape = ru_e * w.du[c + 1] * dyj;
+            const float aps = rv_s * w.dv[c] * dxi, apn = rv_n * w.dv[c + P] * dxi;
+            const float bpw = ru_w * w.uhat[c] * dyj, bpe = ru_e * w.uhat[c + 1] * dyj;
+            const float bps = rv_s * w.vhat[c] * dxi, bpn = rv_n * w.vhat[c + P] * dxi;
+            const float T32 = nw32.T[c];
+            const double Tn = nw.T[c];
+            const float ap0 = dxi * dyj / T32 + (apw + ape + aps + apn) * k32.dt;
+            const float div = (bpe - bpw) + (bpn - bps);
+            const double vol = at(g.x.d, i) * at(g.y.d, j);
+            const double bp = prev.rho[c] * vol - (double)(k32.dt * div);
+            double num = (double)apw * old.p[c - 1];
+            num = fma((double)ape, old.p[c + 1], num);
+            num = fma((double)aps, old.p[c - P], num);
+            num = fma((double)apn, old.p[c + P], num);
+            num = fma(num, k.dt, bp);
+            const double a0 = (double)ap0;
+            double r = (double)(1.0f / ap0);
+            r = fma(r, fma(-a0, r, 1.0), r);
+            const double pn = num * r;
+            double rt = (double)(1.0f / T32);
+            rt = fma(rt, fma(-Tn, rt, 1.0), rt);
+            const double rho = pn * rt;
+            const float gm = (k32.omega == 0.5f) ? sqrtf(T32) : powf(T32, k32.omega);
+            nw.p[c] = pn;
+            nw.rho[c] = rho;
+            nw.gam[c] = (double)gm;
+            nw32.p[c] = (float)pn;
+            nw32.rho[c] = (float)rho;
+            nw32.gam[c] = gm;
+            rp = ordered(pn - old.p[c]);
+            rT = ordered(Tn - old.T[c]);
+        }
+    }
+    block_max2(rp, rT, &res[2], &res[3]);
+}
+
+// Mixed precision, Eqs. pl18, pl19: FP32 correction of the FP32 pseudo
+// velocities by the FP64 pressure difference; FP64 residuals.
+__global__ void __launch_bounds__(BX *BY) k_velocity_mixed(Geo g, Level old, Level nw, LevelT<float> nw32,
+                                                            WorkT<float> w, unsigned long long *res)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    const int P = g.pitch;
+    unsigned long long ru = 0, rv = 0;
+    if (i <= g.nx && j <= g.ny) {
+        const int c = Ix{P}(i, j);
+        const uint16_t f = g.flag[c];
+        if (j < g.ny && (f & F_UACT)) {
+            const float un32 = w.uhat[c] - w.du[c] * (float)(nw.p[c] - nw.p[c - 1]);
+            const double un = (double)un32;
+            nw.u[c] = un;
+            nw32.u[c] = un32;
+            ru = ordered(un - old.u[c]);
+        }
+        if (i < g.nx && (f & F_VACT)) {
+            const float vn32 = w.vhat[c] - w.dv[c] * (float)(nw.p[c] - nw.p[c - P]);
+            const double vn = (double)vn32;
+            nw.v[c] = vn;
+            nw32.v[c] = vn32;
+            rv = ordered(vn - old.v[c]);
+        }
+    }
+    block_max2(ru, rv, &res[0], &res[1]);
+}
+
+// FP32 shadow copy of a whole FP64 level (every element, ghosts included).
+__global__ void k_shadow(Level L, LevelT<float> S, size_t n)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        S.u[q] = (float)L.u[q];
+        S.v[q] = (float)L.v[q];
+        S.p[q] = (float)L.p[q];
+        S.T[q] = (float)L.T[q];
+        S.rho[q] = (float)L.rho[q];
+        S.gam[q] = (float)L.gam[q];
     }
 }
 
@@ -723,7 +842,8 @@ __global__ void k_gather(Geo g, int field, Level L, double *dst)
     dst[(size_t)j * w + i] = field_of(L, field)[Ix{g.pitch}(i, j)];
 }
 
-dim3 grid_of(const Geo &g)
+template <typename R>
+dim3 grid_of(const GeoT<R> &g)
 {
     return dim3((unsigned)((g.nx + 1 + BX - 1) / BX), (unsigned)((g.ny + 1 + BY - 1) / BY));
 }
@@ -736,18 +856,19 @@ void launch_face_densities(const Geo &g, const Level &lv, const Work &w, bool tv
 {
     cudaStream_t s = (cudaStream_t)stream;
     if (tvd)
-        k_face_densities<true><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, lv.u, lv.v, lv.rho, w.rho_u, w.rho_v);
+        k_face_densities<double, true><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, lv.u, lv.v, lv.rho, w.rho_u, w.rho_v);
     else
-        k_face_densities<false><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, lv.u, lv.v, lv.rho, w.rho_u, w.rho_v);
+        k_face_densities<double, false><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, lv.u, lv.v, lv.rho, w.rho_u, w.rho_v);
 }
 
 void launch_explicit_terms(const Geo &g, const Level &prev, const Work &w, bool tvd, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
+    const WorkT<double> &wt = w;
     if (tvd)
-        k_explicit_terms<true><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, prev, w);
+        k_explicit_terms<double, true><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, prev, wt);
     else
-        k_explicit_terms<false><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, prev, w);
+        k_explicit_terms<double, false><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, prev, wt);
 }
 
 void launch_assemble(const Geo &g, const Coef &c, const Level &prev, const Level &old, const Level &nw,
@@ -755,10 +876,11 @@ void launch_assemble(const Geo &g, const Coef &c, const Level &prev, const Level
 {
     cudaStream_t s = (cudaStream_t)stream;
     const dim3 gr = grid_of(g), bl(BX, BY);
-    if (implicit && tvd) k_assemble<true, true><<<gr, bl, 0, s>>>(g, c, prev, old, nw, w);
-    else if (implicit) k_assemble<true, false><<<gr, bl, 0, s>>>(g, c, prev, old, nw, w);
-    else if (tvd) k_assemble<false, true><<<gr, bl, 0, s>>>(g, c, prev, old, nw, w);
-    else k_assemble<false, false><<<gr, bl, 0, s>>>(g, c, prev, old, nw, w);
+    const WorkT<double> &wt = w;
+    if (implicit && tvd) k_assemble<double, true, true><<<gr, bl, 0, s>>>(g, c, prev, old, nw.T, nullptr, wt);
+    else if (implicit) k_assemble<double, true, false><<<gr, bl, 0, s>>>(g, c, prev, old, nw.T, nullptr, wt);
+    else if (tvd) k_assemble<double, false, true><<<gr, bl, 0, s>>>(g, c, prev, old, nw.T, nullptr, wt);
+    else k_assemble<double, false, false><<<gr, bl, 0, s>>>(g, c, prev, old, nw.T, nullptr, wt);
 }
 
 void launch_pressure(const Geo &g, const Coef &c, const Level &prev, const Level &old, const Level &nw,
@@ -778,9 +900,72 @@ void launch_ghosts(const Geo &g, const Sides &sd, const Level &lv, void *stream)
     const bool we = sd.kind[SIDE_E] == BC_OUTFLOW || sd.kind[SIDE_E] == BC_SYMMETRY || sd.kind[SIDE_W] == BC_SYMMETRY;
     const bool sn = sd.kind[SIDE_S] == BC_SYMMETRY || sd.kind[SIDE_N] == BC_SYMMETRY;
     if (we)
-        k_ghost_we<<<(g.ny + 1 + 127) / 128, 128, 0, s>>>(g, sd, lv);
+        k_ghost_we<double><<<(g.ny + 1 + 127) / 128, 128, 0, s>>>(g, sd, lv);
     if (sn)
-        k_ghost_sn<<<(g.nx + 2 * G + 1 + 127) / 128, 128, 0, s>>>(g, sd, lv);
+        k_ghost_sn<double><<<(g.nx + 2 * G + 1 + 127) / 128, 128, 0, s>>>(g, sd, lv);
+}
+
+void launch_face_densities_f32(const Mixed &m, int level, bool tvd, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const LevelT<float> &L = m.lv[level];
+    if (tvd)
+        k_face_densities<float, true><<<grid_of(m.g), dim3(BX, BY), 0, s>>>(m.g, L.u, L.v, L.rho, m.w.rho_u, m.w.rho_v);
+    else
+        k_face_densities<float, false><<<grid_of(m.g), dim3(BX, BY), 0, s>>>(m.g, L.u, L.v, L.rho, m.w.rho_u, m.w.rho_v);
+}
+
+void launch_explicit_terms_f32(const Mixed &m, int prev, bool tvd, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (tvd)
+        k_explicit_terms<float, true><<<grid_of(m.g), dim3(BX, BY), 0, s>>>(m.g, m.lv[prev], m.w);
+    else
+        k_explicit_terms<float, false><<<grid_of(m.g), dim3(BX, BY), 0, s>>>(m.g, m.lv[prev], m.w);
+}
+
+void launch_assemble_f32(const Mixed &m, int prev, int old, int nw, const Level &nw64, bool implicit, bool tvd,
+                         void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const dim3 gr = grid_of(m.g), bl(BX, BY);
+    const LevelT<float> &P = m.lv[prev], &O = m.lv[old];
+    float *T32 = m.lv[nw].T;
+    if (implicit && tvd) k_assemble<float, true, true><<<gr, bl, 0, s>>>(m.g, m.k, P, O, nw64.T, T32, m.w);
+    else if (implicit) k_assemble<float, true, false><<<gr, bl, 0, s>>>(m.g, m.k, P, O, nw64.T, T32, m.w);
+    else if (tvd) k_assemble<float, false, true><<<gr, bl, 0, s>>>(m.g, m.k, P, O, nw64.T, T32, m.w);
+    else k_assemble<float, false, false><<<gr, bl, 0, s>>>(m.g, m.k, P, O, nw64.T, T32, m.w);
+}
+
+void launch_pressure_mixed(const Geo &g, const Coef &c, const Mixed &m, const Level &prev, const Level &old,
+                           const Level &nw, int nw32, const Work &w, void *stream)
+{
+    k_pressure_mixed<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, c, m.g, m.k, prev, old, nw,
+                                                                             m.lv[nw32], m.w, w.res);
+}
+
+void launch_velocity_mixed(const Geo &g, const Mixed &m, const Level &old, const Level &nw, int nw32,
+                           const Work &w, void *stream)
+{
+    k_velocity_mixed<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, old, nw, m.lv[nw32], m.w, w.res);
+}
+
+void launch_ghosts_f32(const Mixed &m, const Sides &sd, int level, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool we = sd.kind[SIDE_E] == BC_OUTFLOW || sd.kind[SIDE_E] == BC_SYMMETRY || sd.kind[SIDE_W] == BC_SYMMETRY;
+    const bool sn = sd.kind[SIDE_S] == BC_SYMMETRY || sd.kind[SIDE_N] == BC_SYMMETRY;
+    if (we)
+        k_ghost_we<float><<<(m.g.ny + 1 + 127) / 128, 128, 0, s>>>(m.g, sd, m.lv[level]);
+    if (sn)
+        k_ghost_sn<float><<<(m.g.nx + 2 * G + 1 + 127) / 128, 128, 0, s>>>(m.g, sd, m.lv[level]);
+}
+
+void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, size_t nelem, void *stream)
+{
+    (void)g;
+    const int blocks = (int)((nelem + 255) / 256 < 4096 ? (nelem + 255) / 256 : 4096);
+    k_shadow<<<blocks, 256, 0, (cudaStream_t)stream>>>(lv, lv32, nelem);
 }
 
 void launch_derive(const Geo &g, const Coef &c, const Level &lv, void *stream)

@@ -196,3 +196,45 @@ def test_parity_full_size_one_step(make):
     case = make()
     g, o, *_ = run_both(case, 1)
     assert_parity(g, o)
+
+
+# ------------------------------------------------------------ mixed precision
+
+MIXED_BOUND = 1e-4    # stated per-field bound of the FP32-assembly path against the FP64 oracle
+
+
+@pytest.mark.parametrize("implicit,tvd,steps", [(False, True, 50), (False, False, 100), (True, False, 100),
+                                                (True, True, 10)])
+def test_mixed_precision_error_against_fp64_oracle(implicit, tvd, steps):
+    case = W.c1_small().replace(implicit=implicit, tvd=tvd, precision=W.MIXED)
+    with sim.Simulation(case) as s:
+        start = s.fields()
+        s.step(steps)
+        g = s.fields()
+        _, _, st = s.residuals()
+    assert st == sim.SIM_OK
+    o, _, _ = oracle.run(case.replace(precision=W.FP64), start, nsteps=steps)
+    e = rel_err(g, o)
+    print("mixed", implicit, tvd, steps, e)
+    assert max(e.values()) <= MIXED_BOUND, e
+    assert max(e.values()) > 1e-12            # the FP32 assembly is really in use
+
+
+def test_mixed_precision_1024x256_100_steps():
+    case = W.c2_medium().replace(precision=W.MIXED)
+    with sim.Simulation(case) as s:
+        start = s.fields()
+        s.step(100)
+        g = s.fields()
+    o, _, _ = oracle.run(case.replace(precision=W.FP64), start, nsteps=100)
+    e = rel_err(g, o)
+    print("mixed c2", e)
+    assert max(e.values()) <= MIXED_BOUND, e
+
+
+def test_mixed_start_state_matches_fp64_start_state():
+    case = W.c1_small()
+    with sim.Simulation(case) as a, sim.Simulation(case.replace(precision=W.MIXED)) as b:
+        fa, fb = a.fields(), b.fields()
+    for k in "uvpT":
+        assert np.array_equal(fa[k], fb[k])
