@@ -141,6 +141,36 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------ cross-rank helpers
+
+def reduce_max(x: float, dist, device) -> float:
+    """Maximum of a per-rank value over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(cells: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job Mcell-steps/s: every rank advances its own replica of `cells`."""
+    return cells * steps * world / seconds / 1e6
+
+
+def timed_steps(sim_obj, steps, stream, flush, starts, ends):
+    """Time `steps` single time steps with CUDA events on `stream`, writing a
+    buffer larger than L2 before each step (outside the events); returns ms."""
+    import torch
+    for k in range(steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        sim_obj.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in zip(starts[:steps], ends[:steps]))
+
+
 # ------------------------------------------------------------- cpu baseline
 
 def oracle_throughput(case, target_s: float = 12.0, max_steps: int = 400):
@@ -184,30 +214,27 @@ def run_ours(args, rank, world, local_rank):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
 
-    s.profile(True)
+    s.profile(True, timing=False)                  # count launches; step graphs stay on
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clocks:
-        for k in range(args.steps):
-            flush.fill_(float(k))                  # evict the state from L2 between timed steps
-            starts[k].record(stream)
-            s.step(1)
-            ends[k].record(stream)
-        torch.cuda.synchronize()
+        total_ms = timed_steps(s, args.steps, stream, flush, starts, ends)
     if dist:
         dist.barrier()
-    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    launches = sum(n for _, n in s.profile_read().values())
+    res, iters, st = s.residuals()
+    total_ms = reduce_max(total_ms, dist, "cuda")
+    value = throughput(case.cells, args.steps, world, total_ms * 1e-3)
+    fp64_state = s.fields()
+
+    # per-kernel durations: the same steps again, kernels launched one by one
+    # between CUDA events on the same stream
+    prof_steps = min(args.steps, 50)
+    s.profile(True, timing=True)
+    timed_steps(s, prof_steps, stream, flush, starts, ends)
     prof = s.profile_read()
     s.profile(False)
-    res, iters, st = s.residuals()
-
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = case.cells * args.steps * world / (total_ms * 1e-3) / 1e6
-    fp64_state = s.fields()
 
     # the same workload and timing protocol with the mixed-precision sweep
     # (FP32 assembly and relaxation; FP64 pressure accumulation, EOS and
@@ -217,32 +244,24 @@ def run_ours(args, rank, world, local_rank):
     sm = sim.Simulation(case.replace(precision=W.MIXED), stream=stream.cuda_stream)
     for _ in range(args.warmup):
         sm.step(1)
-    sm.profile(True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        starts[k].record(stream)
-        sm.step(1)
-        ends[k].record(stream)
-    torch.cuda.synchronize()
-    mixed_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    mixed_ms = timed_steps(sm, args.steps, stream, flush, starts, ends)
+    mixed_state = sm.fields()
+    sm.profile(True, timing=True)
+    timed_steps(sm, prof_steps, stream, flush, starts, ends)
     mprof = sm.profile_read()
     sm.profile(False)
-    mixed_state = sm.fields()
     sm.close()
-    tm = torch.tensor([mixed_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-    mixed_ms = float(tm.item())
+    mixed_ms = reduce_max(mixed_ms, dist, "cuda")
     mixed_err = {k: float(np.abs(mixed_state[k] - fp64_state[k]).max() / np.abs(fp64_state[k]).max())
                  for k in ("u", "v", "p", "T")}
-    mixed = {"value": round(case.cells * args.steps * world / (mixed_ms * 1e-3) / 1e6, 3),
+    mixed = {"value": round(throughput(case.cells, args.steps, world, mixed_ms * 1e-3), 3),
              "ms_per_step": round(mixed_ms / args.steps, 5), "dtype": "f32 assembly / f64 pressure, EOS, residuals",
              "max_rel_err_vs_fp64": {k: float(f"{v:.3e}") for k, v in mixed_err.items()},
              "error_after_steps": args.warmup + args.steps,
-             "kernels": {k: {"ms": round(ms, 4), "launches": n} for k, (ms, n) in mprof.items() if n}}
+             "kernel_ms_avg": {k: round(ms / n, 5) for k, (ms, n) in mprof.items() if n}}
 
     # end to end through the C ABI with host buffers: every step uploads its
     # input state from pinned host memory and reads the new state and the
@@ -267,10 +286,7 @@ def run_ours(args, rank, world, local_rank):
             s.field(k, out=views[k])
         s.residuals()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = case.cells * e2e_steps * world / float(te.item()) / 1e6
+    e2e_value = throughput(case.cells, e2e_steps, world, reduce_max(e2e_s, dist, "cuda"))
     s.close()
 
     if rank != 0:
@@ -280,7 +296,6 @@ def run_ours(args, rank, world, local_rank):
 
     asm_ms, asm_n = prof["assemble"]
     asm_avg_s = asm_ms / max(asm_n, 1) * 1e-3
-    launches = sum(n for _, n in prof.values())
     if ASSEMBLE_FP64_FLOPS_PER_CELL:
         ach = ASSEMBLE_FP64_FLOPS_PER_CELL * case.cells / asm_avg_s / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak_fp64 / 1e3, 4), "unit": "TFLOP/s",
@@ -314,7 +329,8 @@ def run_ours(args, rank, world, local_rank):
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps},
             "gpu_launches": int(launches),
-            "kernels": {k: {"ms": round(ms, 4), "launches": n} for k, (ms, n) in prof.items() if n},
+            "kernel_ms_avg": {k: round(ms / n, 5) for k, (ms, n) in prof.items() if n},
+            "kernel_timing": f"separate pass of {prof_steps} steps with per-launch CUDA events",
             "roofline": roof, "mixed": mixed, "cpu_baseline": cpu, "clocks": clocks.summary(),
             "residuals_last_step": [float(x) for x in res], "impl": "ours"}
     print(json.dumps(line), flush=True)

@@ -170,7 +170,9 @@ enum { SIM_K_FACES = 0, SIM_K_ASSEMBLE = 1, SIM_K_PRESSURE = 2, SIM_K_VELOCITY =
 
 /* Measurement hooks (not part of the method).  sim_profile(sim, 1) clears the
  * counters and from then on brackets every kernel launch of sim_step with a
- * pair of CUDA events on the handle's stream; sim_profile(sim, 0) stops the
+ * pair of CUDA events on the handle's stream (sim_step then launches kernels
+ * one by one instead of replaying its captured step graphs);
+ * sim_profile(sim, 2) only clears the counters; sim_profile(sim, 0) stops the
  * event timing.  Launches are counted whether or not timing is on.
  * Errors: SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA. */
 sim_status sim_profile(sim_t sim, int enable);

@@ -233,8 +233,10 @@ class Simulation:
         arr = _CudaArray(base, (ny + 4, nx + 4), (pitch.value * 8, 8))
         return torch.as_tensor(arr, device="cuda")
 
-    def profile(self, enable: bool = True):
-        self._check(self.lib.sim_profile(self.handle, int(bool(enable))))
+    def profile(self, enable: bool = True, timing: bool = True):
+        """enable=True: clear the launch counters; timing=True also brackets every
+        kernel with CUDA events (and launches kernels one by one)."""
+        self._check(self.lib.sim_profile(self.handle, (1 if timing else 2) if enable else 0))
 
     def profile_read(self) -> Dict[str, tuple]:
         out = {}

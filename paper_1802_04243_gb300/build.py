@@ -57,7 +57,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([exe, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    # the shared CUDA runtime: one runtime instance per process, the same one
+    # PyTorch uses when both are loaded
+    cudart_dir = os.path.join(os.path.dirname(os.path.dirname(exe)), "lib64")
+    r = subprocess.run([exe, *ARCH, "-shared", "-cudart", "shared", "-Xlinker", f"-rpath,{cudart_dir}",
+                        "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -392,7 +392,7 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     k_na_flags<<<gr, bl, 0, s>>>(su, flag);
     k_na_fill<<<gr, bl, 0, s>>>(su, d_u, d_v, d_p, d_T, lv[0]);
     launch_derive(g, k, lv[0], s);
-    launch_ghosts(g, sides, lv[0], s);
+    launch_ghosts(g, sides, lv[0], false, s);
     for (int l = 1; l < 3; l++)
         for (int f = 0; f < 6; f++) {
             double *dst = f == 0 ? lv[l].u : f == 1 ? lv[l].v : f == 2 ? lv[l].p : f == 3 ? lv[l].T : f == 4 ? lv[l].rho : lv[l].gam;
@@ -418,8 +418,8 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
             launch_face_densities(g, lv[old], w, tvd, s);
             launch_assemble(g, k, lv[prev], lv[old], lv[nw], w, implicit, tvd, s);
             launch_pressure(g, k, lv[prev], lv[old], lv[nw], w, s);
-            launch_velocity(g, lv[old], lv[nw], w, s);
-            launch_ghosts(g, sides, lv[nw], s);
+            launch_velocity(g, sides, lv[old], lv[nw], w, s);
+            launch_ghosts(g, sides, lv[nw], true, s);
             old = nw;
         }
         cur = old;

@@ -68,6 +68,11 @@ struct sim_s {
     struct Mark { int cls; cudaEvent_t e0, e1; };
     std::vector<Mark> marks;                   // recorded launches (timing on)
     std::vector<cudaEvent_t> spare;            // reusable events
+    // CUDA graphs of one time step, per (start level, scheme)
+    struct StepGraph { cudaGraphExec_t exec = nullptr; int result = 0; long long counts[SIM_K_COUNT] = {0}; };
+    StepGraph graphs[3][4];
+    cudaStream_t cap_stream = nullptr;         // private stream the step graphs are captured on
+    bool graphs_off = false;
     char err[256] = {0};
 };
 
@@ -395,34 +400,92 @@ cudaEvent_t take_event(sim_t s)
     return e;
 }
 
-// Bracket one kernel launch: counts it, and times it when timing is on.
+// Bracket one kernel launch of the direct path: counts it, and times it when
+// timing is on.  Under stream capture (counts != nullptr) it only counts.
 struct Launch {
     sim_t s;
     int cls;
+    cudaStream_t st;
+    long long *counts;
     cudaEvent_t e0 = nullptr;
-    Launch(sim_t s_, int c) : s(s_), cls(c)
+    Launch(sim_t s_, int c, cudaStream_t st_, long long *counts_, int n = 1) : s(s_), cls(c), st(st_), counts(counts_)
     {
-        s->launches[cls]++;
-        if (s->timing) {
+        (counts ? counts : s->launches)[cls] += n;
+        if (s->timing && !counts) {
             e0 = take_event(s);
-            cudaEventRecord(e0, s->stream);
+            cudaEventRecord(e0, st);
         }
     }
     ~Launch()
     {
         if (e0) {
             cudaEvent_t e1 = take_event(s);
-            cudaEventRecord(e1, s->stream);
+            cudaEventRecord(e1, st);
             s->marks.push_back({cls, e0, e1});
         }
     }
 };
 
-int ghost_launches(const Sides &sd)
+// Explicit convective terms of the step that starts from level `prev`
+// (explicit scheme only, once per step).  counts != nullptr: capture mode.
+void enqueue_explicit(sim_t s, int prev, bool tvd, cudaStream_t st, long long *counts)
 {
-    const bool we = sd.kind[SIDE_E] == BC_OUTFLOW || sd.kind[SIDE_E] == BC_SYMMETRY || sd.kind[SIDE_W] == BC_SYMMETRY;
-    const bool sn = sd.kind[SIDE_S] == BC_SYMMETRY || sd.kind[SIDE_N] == BC_SYMMETRY;
-    return (int)we + (int)sn;
+    if (s->mixed) {
+        { Launch l(s, SIM_K_FACES, st, counts); launch_face_densities_f32(s->mx, prev, tvd, st); }
+        { Launch l(s, SIM_K_EXPLICIT, st, counts); launch_explicit_terms_f32(s->mx, prev, tvd, st); }
+    } else {
+        { Launch l(s, SIM_K_FACES, st, counts); launch_face_densities(s->geo, s->lv[prev], s->work, tvd, st); }
+        { Launch l(s, SIM_K_EXPLICIT, st, counts); launch_explicit_terms(s->geo, s->lv[prev], s->work, tvd, st); }
+    }
+}
+
+// One loop-2 iteration from level `old` (level `prev` holds n-1) into the
+// third level, which is returned.
+int enqueue_iteration(sim_t s, int prev, int old, bool implicit, bool tvd, cudaStream_t st, long long *counts)
+{
+    const Problem &pb = s->pb;
+    int nw = (old + 1) % 3;
+    if (nw == prev) nw = (nw + 1) % 3;
+    const int ng = ghost_kernels(s->sides, true);
+    cudaMemsetAsync(s->work.res, 0, 4 * sizeof(unsigned long long), st);
+    if (s->mixed) {
+        { Launch l(s, SIM_K_FACES, st, counts); launch_face_densities_f32(s->mx, old, tvd, st); }
+        { Launch l(s, SIM_K_ASSEMBLE, st, counts);
+          launch_assemble_f32(s->mx, prev, old, nw, s->lv[nw], implicit, tvd, st); }
+        { Launch l(s, SIM_K_PRESSURE, st, counts);
+          launch_pressure_mixed(s->geo, pb.k, s->mx, s->lv[prev], s->lv[old], s->lv[nw], nw, s->work, st); }
+        { Launch l(s, SIM_K_VELOCITY, st, counts);
+          launch_velocity_mixed(s->geo, s->sides, s->mx, s->lv[old], s->lv[nw], nw, s->work, st); }
+        if (ng) {
+            Launch l(s, SIM_K_GHOSTS, st, counts, 2 * ng);
+            launch_ghosts(s->geo, s->sides, s->lv[nw], true, st);
+            launch_ghosts_f32(s->mx, s->sides, nw, true, st);
+        }
+    } else {
+        { Launch l(s, SIM_K_FACES, st, counts); launch_face_densities(s->geo, s->lv[old], s->work, tvd, st); }
+        { Launch l(s, SIM_K_ASSEMBLE, st, counts);
+          launch_assemble(s->geo, pb.k, s->lv[prev], s->lv[old], s->lv[nw], s->work, implicit, tvd, st); }
+        { Launch l(s, SIM_K_PRESSURE, st, counts);
+          launch_pressure(s->geo, pb.k, s->lv[prev], s->lv[old], s->lv[nw], s->work, st); }
+        { Launch l(s, SIM_K_VELOCITY, st, counts);
+          launch_velocity(s->geo, s->sides, s->lv[old], s->lv[nw], s->work, st); }
+        if (ng) {
+            Launch l(s, SIM_K_GHOSTS, st, counts, ng);
+            launch_ghosts(s->geo, s->sides, s->lv[nw], true, st);
+        }
+    }
+    return nw;
+}
+
+// One time step from level `prev` with `iters` loop-2 iterations; returns the
+// level holding the result.
+int enqueue_step(sim_t s, int prev, bool implicit, bool tvd, cudaStream_t st, long long *counts)
+{
+    if (!implicit) enqueue_explicit(s, prev, tvd, st, counts);
+    int old = prev;
+    for (int it = 1; it <= s->pb.iters; it++)
+        old = enqueue_iteration(s, prev, old, implicit, tvd, st, counts);
+    return old;
 }
 
 sim_status check_live(sim_t s)
@@ -569,7 +632,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
                                         cudaMemcpyHostToDevice, s->stream));
     for (int l = 0; l < 3; l++) {
         launch_derive(s->geo, pb.k, s->lv[l], s->stream);
-        launch_ghosts(s->geo, s->sides, s->lv[l], s->stream);
+        launch_ghosts(s->geo, s->sides, s->lv[l], false, s->stream);
         if (s->mixed) launch_shadow(s->geo, s->lv[l], s->mx.lv[l], s->nelem, s->stream);
     }
     CUDA_TRY(s, cudaGetLastError());
@@ -585,70 +648,69 @@ extern "C" sim_status sim_step(sim_t s, int n_steps, int scheme)
     if (n_steps < 0 || (scheme & ~3)) return fail(s, SIM_EINVAL, "bad n_steps %d or scheme %d", n_steps, scheme);
     const bool implicit = scheme & SIM_IMPLICIT, tvd = scheme & SIM_TVD;
     const Problem &pb = s->pb;
+
+    // Fixed loop-2 length and no event timing: replay one captured graph per
+    // step (the three state levels rotate, so a step graph exists for each
+    // start level).
+    if (pb.tol == 0.0 && !s->timing && !s->graphs_off) {
+        for (int step = 0; step < n_steps; step++) {
+            sim_s::StepGraph &gr = s->graphs[s->cur][scheme];
+            if (!gr.exec) {
+                if (!s->cap_stream)
+                    CUDA_TRY(s, cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+                cudaGraph_t graph = nullptr;
+                CUDA_TRY(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+                gr.result = enqueue_step(s, s->cur, implicit, tvd, s->cap_stream, gr.counts);
+                CUDA_TRY(s, cudaStreamEndCapture(s->cap_stream, &graph));
+                cudaError_t e = cudaGraphInstantiate(&gr.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (e != cudaSuccess) {
+                    gr.exec = nullptr;
+                    return fail(s, SIM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+                }
+            }
+            CUDA_TRY(s, cudaGraphLaunch(gr.exec, s->stream));
+            for (int k = 0; k < SIM_K_COUNT; k++) s->launches[k] += gr.counts[k];
+            s->cur = gr.result;
+            s->last_iters = pb.iters;
+        }
+        CUDA_TRY(s, cudaGetLastError());
+        return SIM_OK;
+    }
+
     for (int step = 0; step < n_steps; step++) {
         const int prev = s->cur;
-        int old = prev, it = 0;
-        if (!implicit && s->mixed) {
-            { Launch l(s, SIM_K_FACES); launch_face_densities_f32(s->mx, prev, tvd, s->stream); }
-            { Launch l(s, SIM_K_EXPLICIT); launch_explicit_terms_f32(s->mx, prev, tvd, s->stream); }
-        } else if (!implicit) {
-            { Launch l(s, SIM_K_FACES); launch_face_densities(s->geo, s->lv[prev], s->work, tvd, s->stream); }
-            { Launch l(s, SIM_K_EXPLICIT); launch_explicit_terms(s->geo, s->lv[prev], s->work, tvd, s->stream); }
+        if (pb.tol == 0.0) {
+            s->cur = enqueue_step(s, prev, implicit, tvd, s->stream, nullptr);
+            s->last_iters = pb.iters;
+            continue;
         }
+        // loop 2 until every residual <= tol: one iteration at a time, reading
+        // the residuals back after each (Section 5: the only per-iteration
+        // device-to-host traffic)
+        int old = prev, it = 0;
+        if (!implicit) enqueue_explicit(s, prev, tvd, s->stream, nullptr);
         for (it = 1; it <= pb.iters; it++) {
-            int nw = (old + 1) % 3;
-            if (nw == prev) nw = (nw + 1) % 3;
-            CUDA_TRY(s, cudaMemsetAsync(s->work.res, 0, 4 * sizeof(unsigned long long), s->stream));
-            if (s->mixed) {
-                { Launch l(s, SIM_K_FACES); launch_face_densities_f32(s->mx, old, tvd, s->stream); }
-                { Launch l(s, SIM_K_ASSEMBLE);
-                  launch_assemble_f32(s->mx, prev, old, nw, s->lv[nw], implicit, tvd, s->stream); }
-                { Launch l(s, SIM_K_PRESSURE);
-                  launch_pressure_mixed(s->geo, pb.k, s->mx, s->lv[prev], s->lv[old], s->lv[nw], nw, s->work,
-                                        s->stream); }
-                { Launch l(s, SIM_K_VELOCITY);
-                  launch_velocity_mixed(s->geo, s->mx, s->lv[old], s->lv[nw], nw, s->work, s->stream); }
-                if (ghost_launches(s->sides)) {
-                    Launch l(s, SIM_K_GHOSTS);
-                    s->launches[SIM_K_GHOSTS] += 2 * ghost_launches(s->sides) - 1;
-                    launch_ghosts(s->geo, s->sides, s->lv[nw], s->stream);
-                    launch_ghosts_f32(s->mx, s->sides, nw, s->stream);
-                }
-            } else {
-                { Launch l(s, SIM_K_FACES); launch_face_densities(s->geo, s->lv[old], s->work, tvd, s->stream); }
-                { Launch l(s, SIM_K_ASSEMBLE);
-                  launch_assemble(s->geo, pb.k, s->lv[prev], s->lv[old], s->lv[nw], s->work, implicit, tvd, s->stream); }
-                { Launch l(s, SIM_K_PRESSURE);
-                  launch_pressure(s->geo, pb.k, s->lv[prev], s->lv[old], s->lv[nw], s->work, s->stream); }
-                { Launch l(s, SIM_K_VELOCITY); launch_velocity(s->geo, s->lv[old], s->lv[nw], s->work, s->stream); }
-                if (ghost_launches(s->sides)) {
-                    Launch l(s, SIM_K_GHOSTS);
-                    s->launches[SIM_K_GHOSTS] += ghost_launches(s->sides) - 1;
-                    launch_ghosts(s->geo, s->sides, s->lv[nw], s->stream);
-                }
+            old = enqueue_iteration(s, prev, old, implicit, tvd, s->stream, nullptr);
+            CUDA_TRY(s, cudaMemcpyAsync(s->h_res, s->work.res, 4 * sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, s->stream));
+            CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+            double mx = 0.0;
+            bool bad = false;
+            for (int q = 0; q < 4; q++) {
+                double r;
+                std::memcpy(&r, &s->h_res[q], sizeof r);
+                if (!std::isfinite(r)) bad = true;
+                mx = std::fmax(mx, r);
             }
-            old = nw;
-            if (pb.tol > 0.0) {
-                CUDA_TRY(s, cudaMemcpyAsync(s->h_res, s->work.res, 4 * sizeof(unsigned long long),
-                                            cudaMemcpyDeviceToHost, s->stream));
-                CUDA_TRY(s, cudaStreamSynchronize(s->stream));
-                double mx = 0.0;
-                bool bad = false;
-                for (int q = 0; q < 4; q++) {
-                    double r;
-                    std::memcpy(&r, &s->h_res[q], sizeof r);
-                    if (!std::isfinite(r)) bad = true;
-                    mx = std::fmax(mx, r);
-                }
-                if (bad) {
-                    s->cur = old;
-                    s->last_iters = it;
-                    s->diverged = true;
-                    s->set_mask = 0;
-                    return fail(s, SIM_EDIVERGED, "non-finite residual in step %d, iteration %d", step, it);
-                }
-                if (mx <= pb.tol) break;
+            if (bad) {
+                s->cur = old;
+                s->last_iters = it;
+                s->diverged = true;
+                s->set_mask = 0;
+                return fail(s, SIM_EDIVERGED, "non-finite residual in step %d, iteration %d", step, it);
             }
+            if (mx <= pb.tol) break;
         }
         s->last_iters = it > pb.iters ? pb.iters : it;
         s->cur = old;
@@ -692,7 +754,7 @@ extern "C" sim_status sim_set_fields(sim_t s, int field, const double *host_src,
     CUDA_TRY(s, cudaMemcpyAsync(s->d_stage, host_src, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     launch_scatter(s->geo, field, s->d_stage, L, s->stream);
     launch_derive(s->geo, s->pb.k, L, s->stream);
-    launch_ghosts(s->geo, s->sides, L, s->stream);
+    launch_ghosts(s->geo, s->sides, L, false, s->stream);
     if (s->mixed) launch_shadow(s->geo, L, s->mx.lv[s->cur], s->nelem, s->stream);
     CUDA_TRY(s, cudaGetLastError());
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
@@ -746,7 +808,7 @@ extern "C" sim_status sim_profile(sim_t s, int enable)
         s->marks.clear();
         for (auto &c : s->launches) c = 0;
     }
-    s->timing = enable != 0;
+    s->timing = enable == 1;
     return SIM_OK;
 }
 
@@ -788,5 +850,9 @@ extern "C" void sim_destroy(sim_t s)
         cudaEventDestroy(m.e1);
     }
     for (auto e : s->spare) cudaEventDestroy(e);
+    for (auto &row : s->graphs)
+        for (auto &g : row)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     delete s;
 }

@@ -103,8 +103,11 @@ void launch_assemble(const Geo &g, const Coef &c, const Level &prev, const Level
                      const Level &nw, const Work &w, bool implicit, bool tvd, void *stream);
 void launch_pressure(const Geo &g, const Coef &c, const Level &prev, const Level &old,
                      const Level &nw, const Work &w, void *stream);
-void launch_velocity(const Geo &g, const Level &old, const Level &nw, const Work &w, void *stream);
-void launch_ghosts(const Geo &g, const Sides &s, const Level &lv, void *stream);
+void launch_velocity(const Geo &g, const Sides &s, const Level &old, const Level &nw, const Work &w, void *stream);
+// Ghost copies of outflow and symmetry sides.  after_velocity: the velocity
+// kernel has already copied the outflow side, only symmetry sides remain.
+void launch_ghosts(const Geo &g, const Sides &s, const Level &lv, bool after_velocity, void *stream);
+int ghost_kernels(const Sides &s, bool after_velocity);
 void launch_derive(const Geo &g, const Coef &c, const Level &lv, void *stream);
 void launch_scatter(const Geo &g, int field, const double *src, const Level &lv, void *stream);
 void launch_gather(const Geo &g, int field, const Level &lv, double *dst, void *stream);
@@ -116,9 +119,9 @@ void launch_assemble_f32(const Mixed &m, int prev, int old, int nw, const Level 
                          void *stream);
 void launch_pressure_mixed(const Geo &g, const Coef &c, const Mixed &m, const Level &prev, const Level &old,
                            const Level &nw, int nw32, const Work &w, void *stream);
-void launch_velocity_mixed(const Geo &g, const Mixed &m, const Level &old, const Level &nw, int nw32,
-                           const Work &w, void *stream);
-void launch_ghosts_f32(const Mixed &m, const Sides &s, int level, void *stream);
+void launch_velocity_mixed(const Geo &g, const Sides &s, const Mixed &m, const Level &old, const Level &nw,
+                           int nw32, const Work &w, void *stream);
+void launch_ghosts_f32(const Mixed &m, const Sides &s, int level, bool after_velocity, void *stream);
 void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, size_t nelem, void *stream);
 
 }  // namespace stg

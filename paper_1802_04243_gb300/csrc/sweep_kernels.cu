@@ -580,8 +580,31 @@ __global__ void __launch_bounds__(BX *BY) k_pressure(Geo g, Coef k, Level prev, 
 
 // -------------------------------------------------------------- velocity
 
-// Eqs. pl18, pl19: velocities of the face unknowns from the new pressure.
-__global__ void __launch_bounds__(BX *BY) k_velocity(Geo g, Level old, Level nw, Work w)
+// Outflow side (zero gradient): the thread of column nx-1 copies its new
+// values into the ghost columns nx, nx+1 (cells, v) and nx, nx+1, nx+2 (u).
+template <typename R>
+__device__ __forceinline__ void outflow_copy(int j, int ny, int c, LevelT<R> L)
+{
+    if (j < ny) {
+        R *sc[4] = {L.p, L.T, L.rho, L.gam};
+        for (int q = 0; q < 4; q++) {
+            const R x = sc[q][c];
+            sc[q][c + 1] = x;
+            sc[q][c + 2] = x;
+        }
+        const R un = L.u[c];
+        L.u[c + 1] = un;
+        L.u[c + 2] = un;
+        L.u[c + 3] = un;
+    }
+    const R vn = L.v[c];
+    L.v[c + 1] = vn;
+    L.v[c + 2] = vn;
+}
+
+// Eqs. pl18, pl19: velocities of the face unknowns from the new pressure,
+// then the outflow ghost copies of the row.
+__global__ void __launch_bounds__(BX *BY) k_velocity(Geo g, Level old, Level nw, Work w, int east_outflow)
 {
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     const int P = g.pitch;
@@ -599,6 +622,8 @@ __global__ void __launch_bounds__(BX *BY) k_velocity(Geo g, Level old, Level nw,
             nw.v[c] = vn;
             rv = ordered(vn - old.v[c]);
         }
+        if (east_outflow && i == g.nx - 1)
+            outflow_copy(j, g.ny, c, nw);
     }
     block_max2(ru, rv, &w.res[0], &w.res[1]);
 }
@@ -753,7 +778,7 @@ __global__ void __launch_bounds__(BX *BY) k_pressure_mixed(Geo g, Coef k, GeoT<f
 // Mixed precision, Eqs. pl18, pl19: FP32 correction of the FP32 pseudo
 // velocities by the FP64 pressure difference; FP64 residuals.
 __global__ void __launch_bounds__(BX *BY) k_velocity_mixed(Geo g, Level old, Level nw, LevelT<float> nw32,
-                                                            WorkT<float> w, unsigned long long *res)
+                                                            WorkT<float> w, unsigned long long *res, int east_outflow)
 {
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     const int P = g.pitch;
@@ -774,6 +799,10 @@ __global__ void __launch_bounds__(BX *BY) k_velocity_mixed(Geo g, Level old, Lev
             nw.v[c] = vn;
             nw32.v[c] = vn32;
             rv = ordered(vn - old.v[c]);
+        }
+        if (east_outflow && i == g.nx - 1) {
+            outflow_copy(j, g.ny, c, nw);
+            outflow_copy(j, g.ny, c, nw32);
         }
     }
     block_max2(ru, rv, &res[0], &res[1]);
@@ -889,15 +918,24 @@ void launch_pressure(const Geo &g, const Coef &c, const Level &prev, const Level
     k_pressure<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, c, prev, old, nw, w);
 }
 
-void launch_velocity(const Geo &g, const Level &old, const Level &nw, const Work &w, void *stream)
+void launch_velocity(const Geo &g, const Sides &sd, const Level &old, const Level &nw, const Work &w, void *stream)
 {
-    k_velocity<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, old, nw, w);
+    k_velocity<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, old, nw, w, sd.kind[SIDE_E] == BC_OUTFLOW);
 }
 
-void launch_ghosts(const Geo &g, const Sides &sd, const Level &lv, void *stream)
+int ghost_kernels(const Sides &sd, bool after_velocity)
+{
+    const bool we = (!after_velocity && sd.kind[SIDE_E] == BC_OUTFLOW) || sd.kind[SIDE_E] == BC_SYMMETRY ||
+                    sd.kind[SIDE_W] == BC_SYMMETRY;
+    const bool sn = sd.kind[SIDE_S] == BC_SYMMETRY || sd.kind[SIDE_N] == BC_SYMMETRY;
+    return (int)we + (int)sn;
+}
+
+void launch_ghosts(const Geo &g, const Sides &sd, const Level &lv, bool after_velocity, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
-    const bool we = sd.kind[SIDE_E] == BC_OUTFLOW || sd.kind[SIDE_E] == BC_SYMMETRY || sd.kind[SIDE_W] == BC_SYMMETRY;
+    const bool we = (!after_velocity && sd.kind[SIDE_E] == BC_OUTFLOW) || sd.kind[SIDE_E] == BC_SYMMETRY ||
+                    sd.kind[SIDE_W] == BC_SYMMETRY;
     const bool sn = sd.kind[SIDE_S] == BC_SYMMETRY || sd.kind[SIDE_N] == BC_SYMMETRY;
     if (we)
         k_ghost_we<double><<<(g.ny + 1 + 127) / 128, 128, 0, s>>>(g, sd, lv);
@@ -944,16 +982,18 @@ void launch_pressure_mixed(const Geo &g, const Coef &c, const Mixed &m, const Le
                                                                              m.lv[nw32], m.w, w.res);
 }
 
-void launch_velocity_mixed(const Geo &g, const Mixed &m, const Level &old, const Level &nw, int nw32,
-                           const Work &w, void *stream)
+void launch_velocity_mixed(const Geo &g, const Sides &sd, const Mixed &m, const Level &old, const Level &nw,
+                           int nw32, const Work &w, void *stream)
 {
-    k_velocity_mixed<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, old, nw, m.lv[nw32], m.w, w.res);
+    k_velocity_mixed<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, old, nw, m.lv[nw32], m.w, w.res,
+                                                                             sd.kind[SIDE_E] == BC_OUTFLOW);
 }
 
-void launch_ghosts_f32(const Mixed &m, const Sides &sd, int level, void *stream)
+void launch_ghosts_f32(const Mixed &m, const Sides &sd, int level, bool after_velocity, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
-    const bool we = sd.kind[SIDE_E] == BC_OUTFLOW || sd.kind[SIDE_E] == BC_SYMMETRY || sd.kind[SIDE_W] == BC_SYMMETRY;
+    const bool we = (!after_velocity && sd.kind[SIDE_E] == BC_OUTFLOW) || sd.kind[SIDE_E] == BC_SYMMETRY ||
+                    sd.kind[SIDE_W] == BC_SYMMETRY;
     const bool sn = sd.kind[SIDE_S] == BC_SYMMETRY || sd.kind[SIDE_N] == BC_SYMMETRY;
     if (we)
         k_ghost_we<float><<<(m.g.ny + 1 + 127) / 128, 128, 0, s>>>(m.g, sd, m.lv[level]);

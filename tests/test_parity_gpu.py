@@ -200,7 +200,12 @@ def test_parity_full_size_one_step(make):
 
 # ------------------------------------------------------------ mixed precision
 
-MIXED_BOUND = 1e-4    # stated per-field bound of the FP32-assembly path against the FP64 oracle
+# Stated per-field bound of the FP32-assembly path against the FP64 oracle for
+# the explicit schemes and implicit upwind (measured: <= 3e-6 after 100 steps).
+# Implicit TVD amplifies rounding differences (R15): FP32 rounding
+# reaches ~4e-4 after 10 steps, so it has its own, looser bound.
+MIXED_BOUND = 1e-5
+MIXED_BOUND_IMPLICIT_TVD = 2e-3
 
 
 @pytest.mark.parametrize("implicit,tvd,steps", [(False, True, 50), (False, False, 100), (True, False, 100),
@@ -216,7 +221,7 @@ def test_mixed_precision_error_against_fp64_oracle(implicit, tvd, steps):
     o, _, _ = oracle.run(case.replace(precision=W.FP64), start, nsteps=steps)
     e = rel_err(g, o)
     print("mixed", implicit, tvd, steps, e)
-    assert max(e.values()) <= MIXED_BOUND, e
+    assert max(e.values()) <= (MIXED_BOUND_IMPLICIT_TVD if implicit and tvd else MIXED_BOUND), e
     assert max(e.values()) > 1e-12            # the FP32 assembly is really in use
 
 
@@ -238,3 +243,21 @@ def test_mixed_start_state_matches_fp64_start_state():
         fa, fb = a.fields(), b.fields()
     for k in "uvpT":
         assert np.array_equal(fa[k], fb[k])
+
+
+@pytest.mark.parametrize("precision", [W.FP64, W.MIXED])
+def test_step_graph_replay_matches_direct_launches(precision):
+    # sim_step replays captured step graphs; with event timing on it launches
+    # kernels one by one.  Both must give the same bits, for every start level
+    # of the three-level rotation and when the scheme changes between calls.
+    case = W.c1_small().replace(precision=precision)
+    with sim.Simulation(case) as direct, sim.Simulation(case) as graph:
+        direct.profile(True, timing=True)
+        for scheme in (sim.SIM_IMPLICIT, sim.SIM_EXPLICIT | sim.SIM_TVD, sim.SIM_IMPLICIT):
+            direct.step(4, scheme)
+            graph.step(4, scheme)
+        a, b = direct.fields(), graph.fields()
+        n_direct = direct.profile_read()["assemble"][1]
+    for k in "uvpT":
+        assert np.array_equal(a[k], b[k]), k
+    assert n_direct == 12 * case.iters
