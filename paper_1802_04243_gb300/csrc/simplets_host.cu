@@ -453,9 +453,9 @@ int enqueue_iteration(sim_t s, int prev, int old, bool implicit, bool tvd, cudaS
         { Launch l(s, SIM_K_ASSEMBLE, st, counts);
           launch_assemble_f32(s->mx, prev, old, nw, s->lv[nw], implicit, tvd, st); }
         { Launch l(s, SIM_K_PRESSURE, st, counts);
-          launch_pressure_mixed(s->geo, pb.k, s->mx, s->lv[prev], s->lv[old], s->lv[nw], nw, s->work, st); }
+          launch_pressure_mixed(s->geo, pb.k, s->mx, s->lv[prev], s->lv[old], old, s->lv[nw], nw, s->work, st); }
         { Launch l(s, SIM_K_VELOCITY, st, counts);
-          launch_velocity_mixed(s->geo, s->sides, s->mx, s->lv[old], s->lv[nw], nw, s->work, st); }
+          launch_velocity_mixed(s->geo, s->sides, s->mx, old, s->lv[nw], nw, s->work, st); }
         if (ng) {
             Launch l(s, SIM_K_GHOSTS, st, counts, 2 * ng);
             launch_ghosts(s->geo, s->sides, s->lv[nw], true, st);

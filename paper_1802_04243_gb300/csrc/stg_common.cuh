@@ -118,9 +118,9 @@ void launch_explicit_terms_f32(const Mixed &m, int prev, bool tvd, void *stream)
 void launch_assemble_f32(const Mixed &m, int prev, int old, int nw, const Level &nw64, bool implicit, bool tvd,
                          void *stream);
 void launch_pressure_mixed(const Geo &g, const Coef &c, const Mixed &m, const Level &prev, const Level &old,
-                           const Level &nw, int nw32, const Work &w, void *stream);
-void launch_velocity_mixed(const Geo &g, const Sides &s, const Mixed &m, const Level &old, const Level &nw,
-                           int nw32, const Work &w, void *stream);
+                           int old32, const Level &nw, int nw32, const Work &w, void *stream);
+void launch_velocity_mixed(const Geo &g, const Sides &s, const Mixed &m, int old32, const Level &nw, int nw32,
+                           const Work &w, void *stream);
 void launch_ghosts_f32(const Mixed &m, const Sides &s, int level, bool after_velocity, void *stream);
 void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, size_t nelem, void *stream);
 

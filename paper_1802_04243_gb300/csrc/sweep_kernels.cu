@@ -105,6 +105,52 @@ __device__ __forceinline__ unsigned long long ordered(double x)
     return (unsigned long long)__double_as_longlong(fabs(x));
 }
 
+// Ordered key of |x| for an FP64 value held as bits (integer pipe only).
+__device__ __forceinline__ unsigned long long ordered_bits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// FP32 <-> FP64 conversions on the integer pipe.  On GB300 the F2F
+// instructions issue on the FP64 pipe (1/64 of the FP32 rate); the mixed path
+// converts every value it moves between the two precisions, so it assembles
+// the IEEE bit patterns itself.
+// widen: exact FP32 -> FP64 (FP32 subnormals become zero).
+__device__ __forceinline__ double widen(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned sgn = b & 0x80000000u, e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+    unsigned hi = sgn | ((e + 896u) << 20) | (m >> 3);
+    unsigned lo = m << 29;
+    if (e == 0u) {
+        hi = sgn;
+        lo = 0u;
+    } else if (e == 0xFFu) {
+        hi = sgn | 0x7FF00000u | (m >> 3);
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// narrow: FP64 -> FP32 rounded to nearest (ties away from zero); magnitudes
+// below the FP32 normal range become zero, above it infinity; NaN stays NaN.
+__device__ __forceinline__ float narrow(double d)
+{
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned sgn = hi & 0x80000000u, e64 = (hi >> 20) & 0x7FFu;
+    const int e = (int)e64 - 896;
+    const unsigned mag = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    unsigned bits;
+    if (e64 == 0x7FFu)
+        bits = 0x7F800000u | (((hi & 0xFFFFFu) | lo) ? 0x400000u : 0u);
+    else if (e <= 0)
+        bits = 0u;
+    else if (e >= 255)
+        bits = 0x7F800000u;
+    else
+        bits = (((unsigned)e << 23) | mag) + ((lo >> 28) & 1u);
+    return __uint_as_float(sgn | bits);
+}
+
 __device__ __forceinline__ void block_max2(unsigned long long a, unsigned long long b,
                                            unsigned long long *da, unsigned long long *db)
 {
@@ -525,8 +571,12 @@ __global__ void __launch_bounds__(BX *BY) k_assemble(GeoT<R> g, CoefT<R> k, Leve
     const uint16_t f = g.flag[c];
     if (i < g.nx && j < g.ny && (f & F_FLUID)) {
         const R Tn = temperature<R, IMPL, TVD>(g, k, prev, old, w, c, i, j);
-        T_out[c] = (double)Tn;
-        if (T32_out) T32_out[c] = (float)Tn;
+        if constexpr (sizeof(R) == 4) {
+            T_out[c] = widen(Tn);
+            T32_out[c] = Tn;
+        } else {
+            T_out[c] = Tn;
+        }
     }
     if (j < g.ny) {
         R uh = old.u[c], d = R(0);            // faces that are not unknowns: stored u, d = 0
@@ -724,12 +774,15 @@ __global__ void k_ghost_sn(GeoT<R> g, Sides s, LevelT<R> L)
 // Mixed precision, pressure: the coefficients of Eqs. pl23, pl24 come from
 // the FP32 assembly (FP32 rho^u, d, u^ and the new T); the accumulation of
 // the neighbour pressures and the source, the division by a^p_0, the
-// equation of state rho = p/T and the residuals are FP64.  The FP64
+// equation of state rho = p/T and the residual of p are FP64.  The FP64
 // reciprocals start from the FP32 reciprocal and take one Newton step
 // (relative error below 1e-14).  Gamma = T^omega is a coefficient: FP32.
+// T carries FP32 values in this path, so its residual difference is formed
+// exactly in FP32.
 __global__ void __launch_bounds__(BX *BY) k_pressure_mixed(Geo g, Coef k, GeoT<float> g32, CoefT<float> k32,
-                                                            Level prev, Level old, Level nw, LevelT<float> nw32,
-                                                            WorkT<float> w, unsigned long long *res)
+                                                            Level prev, Level old, Level nw, LevelT<float> old32,
+                                                            LevelT<float> nw32, WorkT<float> w,
+                                                            unsigned long long *res)
 {
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     const int P = g.pitch;
@@ -744,40 +797,42 @@ __global__ void __launch_bounds__(BX *BY) k_pressure_mixed(Geo g, Coef k, GeoT<f
             const float bpw = ru_w * w.uhat[c] * dyj, bpe = ru_e * w.uhat[c + 1] * dyj;
             const float bps = rv_s * w.vhat[c] * dxi, bpn = rv_n * w.vhat[c + P] * dxi;
             const float T32 = nw32.T[c];
-            const double Tn = nw.T[c];
+            const double Tn = widen(T32);
             const float ap0 = dxi * dyj / T32 + (apw + ape + aps + apn) * k32.dt;
             const float div = (bpe - bpw) + (bpn - bps);
             const double vol = at(g.x.d, i) * at(g.y.d, j);
-            const double bp = prev.rho[c] * vol - (double)(k32.dt * div);
-            double num = (double)apw * old.p[c - 1];
-            num = fma((double)ape, old.p[c + 1], num);
-            num = fma((double)aps, old.p[c - P], num);
-            num = fma((double)apn, old.p[c + P], num);
+            const double bp = fma(prev.rho[c], vol, -widen(k32.dt * div));
+            double num = widen(apw) * old.p[c - 1];
+            num = fma(widen(ape), old.p[c + 1], num);
+            num = fma(widen(aps), old.p[c - P], num);
+            num = fma(widen(apn), old.p[c + P], num);
             num = fma(num, k.dt, bp);
-            const double a0 = (double)ap0;
-            double r = (double)(1.0f / ap0);
+            const double a0 = widen(ap0);
+            double r = widen(1.0f / ap0);
             r = fma(r, fma(-a0, r, 1.0), r);
             const double pn = num * r;
-            double rt = (double)(1.0f / T32);
+            double rt = widen(1.0f / T32);
             rt = fma(rt, fma(-Tn, rt, 1.0), rt);
             const double rho = pn * rt;
             const float gm = (k32.omega == 0.5f) ? sqrtf(T32) : powf(T32, k32.omega);
             nw.p[c] = pn;
             nw.rho[c] = rho;
-            nw.gam[c] = (double)gm;
-            nw32.p[c] = (float)pn;
-            nw32.rho[c] = (float)rho;
+            nw.gam[c] = widen(gm);
+            nw32.p[c] = narrow(pn);
+            nw32.rho[c] = narrow(rho);
             nw32.gam[c] = gm;
-            rp = ordered(pn - old.p[c]);
-            rT = ordered(Tn - old.T[c]);
+            rp = ordered_bits(pn - old.p[c]);
+            rT = ordered_bits(widen(T32 - old32.T[c]));
         }
     }
     block_max2(rp, rT, &res[2], &res[3]);
 }
 
 // Mixed precision, Eqs. pl18, pl19: FP32 correction of the FP32 pseudo
-// velocities by the FP64 pressure difference; FP64 residuals.
-__global__ void __launch_bounds__(BX *BY) k_velocity_mixed(Geo g, Level old, Level nw, LevelT<float> nw32,
+// velocities by the FP64 pressure difference.  u and v carry FP32 values in
+// this path: their residual differences are formed in FP32 and reduced as
+// FP64 bit patterns.
+__global__ void __launch_bounds__(BX *BY) k_velocity_mixed(Geo g, Level nw, LevelT<float> old32, LevelT<float> nw32,
                                                             WorkT<float> w, unsigned long long *res, int east_outflow)
 {
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
@@ -787,18 +842,16 @@ __global__ void __launch_bounds__(BX *BY) k_velocity_mixed(Geo g, Level old, Lev
         const int c = Ix{P}(i, j);
         const uint16_t f = g.flag[c];
         if (j < g.ny && (f & F_UACT)) {
-            const float un32 = w.uhat[c] - w.du[c] * (float)(nw.p[c] - nw.p[c - 1]);
-            const double un = (double)un32;
-            nw.u[c] = un;
+            const float un32 = w.uhat[c] - w.du[c] * narrow(nw.p[c] - nw.p[c - 1]);
+            nw.u[c] = widen(un32);
             nw32.u[c] = un32;
-            ru = ordered(un - old.u[c]);
+            ru = ordered_bits(widen(un32 - old32.u[c]));
         }
         if (i < g.nx && (f & F_VACT)) {
-            const float vn32 = w.vhat[c] - w.dv[c] * (float)(nw.p[c] - nw.p[c - P]);
-            const double vn = (double)vn32;
-            nw.v[c] = vn;
+            const float vn32 = w.vhat[c] - w.dv[c] * narrow(nw.p[c] - nw.p[c - P]);
+            nw.v[c] = widen(vn32);
             nw32.v[c] = vn32;
-            rv = ordered(vn - old.v[c]);
+            rv = ordered_bits(widen(vn32 - old32.v[c]));
         }
         if (east_outflow && i == g.nx - 1) {
             outflow_copy(j, g.ny, c, nw);
@@ -976,17 +1029,17 @@ void launch_assemble_f32(const Mixed &m, int prev, int old, int nw, const Level 
 }
 
 void launch_pressure_mixed(const Geo &g, const Coef &c, const Mixed &m, const Level &prev, const Level &old,
-                           const Level &nw, int nw32, const Work &w, void *stream)
+                           int old32, const Level &nw, int nw32, const Work &w, void *stream)
 {
     k_pressure_mixed<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, c, m.g, m.k, prev, old, nw,
-                                                                             m.lv[nw32], m.w, w.res);
+                                                                             m.lv[old32], m.lv[nw32], m.w, w.res);
 }
 
-void launch_velocity_mixed(const Geo &g, const Sides &sd, const Mixed &m, const Level &old, const Level &nw,
-                           int nw32, const Work &w, void *stream)
+void launch_velocity_mixed(const Geo &g, const Sides &sd, const Mixed &m, int old32, const Level &nw, int nw32,
+                           const Work &w, void *stream)
 {
-    k_velocity_mixed<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, old, nw, m.lv[nw32], m.w, w.res,
-                                                                             sd.kind[SIDE_E] == BC_OUTFLOW);
+    k_velocity_mixed<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, nw, m.lv[old32], m.lv[nw32], m.w,
+                                                                             w.res, sd.kind[SIDE_E] == BC_OUTFLOW);
 }
 
 void launch_ghosts_f32(const Mixed &m, const Sides &sd, int level, bool after_velocity, void *stream)
