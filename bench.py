@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched measurement")
+    ap.add_argument("--batch-steps", type=int, default=40)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2",
                     help="c2 (default, the benchmark line); the others are for profiling and sweeps")
     return ap.parse_args()
@@ -169,6 +171,73 @@ def timed_steps(sim_obj, steps, stream, flush, starts, ends):
         ends[k].record(stream)
     torch.cuda.synchronize()
     return sum(a.elapsed_time(b) for a, b in zip(starts[:steps], ends[:steps]))
+
+
+# ------------------------------------------------------------------ batches
+
+def run_batch(args, stream):
+    """64 independent channels of uneven size (256x64 .. 2048x512), mixed
+    precision, advanced together: tuned tiles, one launch per kernel phase over
+    all problems, each step a CUDA graph.  Compared with the same problems
+    stepped one after another, and with an FP64 batch for the error."""
+    import numpy as np
+    import torch
+
+    import paper_1802_04243_gb300 as sim
+    import workloads as W
+    cases = W.c5_batch(64, precision=W.MIXED)
+    cells = sum(c.cells for c in cases)
+    steps = max(1, min(args.batch_steps, args.steps))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(step_all):
+        ms = 0.0
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0.record(stream)
+            step_all()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        return ms
+
+    b = sim.Batch(cases, stream=stream.cuda_stream)
+    tile = b.tune()
+    for _ in range(args.warmup):
+        b.step(1)
+    batch_ms = timed(lambda: b.step(1))
+    mixed_fields = [b.fields(q) for q in range(len(cases))]
+    b.close()
+
+    singles = [sim.Simulation(c, stream=stream.cuda_stream) for c in cases]
+    for _ in range(args.warmup):
+        for h in singles:
+            h.step(1)
+
+    def step_each():
+        for h in singles:
+            h.step(1)
+    seq_ms = timed(step_each)
+    for h in singles:
+        h.close()
+
+    fb = sim.Batch([c.replace(precision=W.FP64) for c in cases], stream=stream.cuda_stream)
+    fb.step(args.warmup + steps)
+    err = {k: 0.0 for k in "uvpT"}
+    for q in range(len(cases)):
+        f64 = fb.fields(q)
+        for k in "uvpT":
+            err[k] = max(err[k], float(np.abs(mixed_fields[q][k] - f64[k]).max() / np.abs(f64[k]).max()))
+    fb.close()
+    return {"workload": "64 channels, nx ~ U{256..2048} (multiples of 32), ny = nx/4, Mach U[1.5,3], Re U[50,400], "
+                        "1-4 squares, implicit upwind, mixed precision, seeds 1000..1063",
+            "cells": cells, "steps": steps, "value": round(throughput(cells, steps, 1, batch_ms * 1e-3), 3),
+            "unit": UNIT, "ms_per_step": round(batch_ms / steps, 4), "tile": list(tile),
+            "one_by_one": {"value": round(throughput(cells, steps, 1, seq_ms * 1e-3), 3),
+                           "ms_per_step": round(seq_ms / steps, 4)},
+            "max_rel_err_vs_fp64_batch": {k: float(f"{v:.3e}") for k, v in err.items()},
+            "error_after_steps": args.warmup + steps}
 
 
 # ------------------------------------------------------------- cpu baseline
@@ -314,6 +383,8 @@ def run_ours(args, rank, world, local_rank):
     roof["kernel_ms_avg"] = round(asm_avg_s * 1e3, 5)
     roof["fp64_peak_gflops_measured"] = round(peak_fp64, 1)
 
+    batched = None if args.no_batch else run_batch(args, stream)
+
     cpu = None
     if not args.no_cpu_baseline:
         v, n, secs = oracle_throughput(case)
@@ -331,7 +402,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": int(launches),
             "kernel_ms_avg": {k: round(ms / n, 5) for k, (ms, n) in prof.items() if n},
             "kernel_timing": f"separate pass of {prof_steps} steps with per-launch CUDA events",
-            "roofline": roof, "mixed": mixed, "cpu_baseline": cpu, "clocks": clocks.summary(),
+            "roofline": roof, "mixed": mixed, "batched": batched, "cpu_baseline": cpu, "clocks": clocks.summary(),
             "residuals_last_step": [float(x) for x in res], "impl": "ours"}
     print(json.dumps(line), flush=True)
     if dist:

@@ -185,6 +185,45 @@ sim_status sim_profile_read(sim_t sim, int kernel_class, double *ms, long long *
 /* Text of the last error on this handle (never NULL). */
 const char *sim_last_error(sim_t sim);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent problems advanced together.  The paper solves one
+ * channel at a time; a batch runs the same time step (Section 3.1) for n
+ * problems of different sizes and parameters with one launch per kernel phase
+ * over all of them (a tile list that spans every problem), and replays whole
+ * steps as CUDA graphs.  The problems must share the precision and the number
+ * of loop-2 iterations, and use tol = 0.
+ * ------------------------------------------------------------------------ */
+typedef struct sim_batch_s *sim_batch_t;
+
+/* Create n problems (arrays of n descriptions, each as for sim_create) on one
+ * stream.  Errors: SIM_EINVAL (n < 1, a bad description, mixed precisions or
+ * loop-2 lengths, tol != 0), SIM_ENOMEM, SIM_ECUDA. */
+sim_status sim_batch_create(int n, const sim_grid *grids, const sim_gas *gases, const sim_bc *bcs,
+                            void *stream, sim_batch_t *out);
+
+/* Advance every problem n_steps time steps with `scheme` (as sim_step).
+ * Asynchronous.  Errors: SIM_EINVAL, SIM_ECUDA. */
+sim_status sim_batch_step(sim_batch_t batch, int n_steps, int scheme);
+
+/* One field of problem `instance` (as sim_fields).  Synchronous. */
+sim_status sim_batch_fields(sim_batch_t batch, int instance, int field, double *host_dst, size_t n);
+
+/* Residuals of problem `instance` in its last loop-2 iteration (as sim_residuals). */
+sim_status sim_batch_residuals(sim_batch_t batch, int instance, double out[4]);
+
+/* Autotune the work distribution of the batched kernels for `scheme`: times a
+ * few steps for each candidate tile shape (32x8, 64x4, 128x2, 16x16 threads)
+ * and CTA count, keeps the fastest, and restores the state of every problem
+ * afterwards.  out[0..2] = tile x, tile y, CTAs.  Synchronous; allocates a
+ * temporary copy of the state.  Errors: SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA. */
+sim_status sim_batch_tune(sim_batch_t batch, int scheme, int out[3]);
+
+/* Text of the last error on this batch (never NULL). */
+const char *sim_batch_last_error(sim_batch_t batch);
+
+/* Release the batch and all its problems (NULL is a no-op). */
+void sim_batch_destroy(sim_batch_t batch);
+
 /* Release every resource of the handle (NULL is a no-op). */
 void sim_destroy(sim_t sim);
 

@@ -81,6 +81,14 @@ _SIGNATURES = {
     "sim_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "simplets_alu_peak": ([ctypes.c_int, ctypes.c_double, ctypes.c_void_p, _DP], ctypes.c_int),
     "sim_destroy": ([ctypes.c_void_p], None),
+    "sim_batch_create": ([ctypes.c_int, ctypes.POINTER(sim_grid), ctypes.POINTER(sim_gas), ctypes.POINTER(sim_bc),
+                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "sim_batch_step": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "sim_batch_fields": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _DP, ctypes.c_size_t], ctypes.c_int),
+    "sim_batch_residuals": ([ctypes.c_void_p, ctypes.c_int, _DP], ctypes.c_int),
+    "sim_batch_tune": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "sim_batch_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
+    "sim_batch_destroy": ([ctypes.c_void_p], None),
     "sim_step_noalloc": ([ctypes.POINTER(sim_grid), ctypes.POINTER(sim_gas), ctypes.POINTER(sim_bc), ctypes.c_int,
                           ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                           ctypes.c_void_p, _DP], ctypes.c_int),
@@ -250,6 +258,78 @@ class Simulation:
     def close(self):
         if getattr(self, "handle", None):
             self.lib.sim_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many independent problems advanced together (sim_batch_*): one launch per
+    kernel phase over all of them, whole steps replayed as CUDA graphs."""
+
+    def __init__(self, cases, stream: Optional[int] = None):
+        self.lib = load()
+        self.cases = list(cases)
+        n = len(self.cases)
+        self._descs = [_Desc(c) for c in self.cases]
+        grids, gases, bcs = (sim_grid * n)(), (sim_gas * n)(), (sim_bc * n)()
+        for q, d in enumerate(self._descs):
+            grids[q], gases[q], bcs[q] = d.grid, d.gas, d.bc
+        self._arrays = (grids, gases, bcs)
+        h = ctypes.c_void_p()
+        st = self.lib.sim_batch_create(n, grids, gases, bcs, ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if st != SIM_OK:
+            raise SimError(st, "sim_batch_create failed")
+        self.handle = h
+        c0 = self.cases[0]
+        self.scheme = scheme_of(c0.implicit, c0.tvd)
+
+    def _check(self, st: int):
+        if st != SIM_OK:
+            raise SimError(st, self.lib.sim_batch_last_error(self.handle).decode())
+
+    def step(self, n: int = 1, scheme: Optional[int] = None):
+        self._check(self.lib.sim_batch_step(self.handle, int(n), self.scheme if scheme is None else int(scheme)))
+
+    def tune(self, scheme: Optional[int] = None):
+        out = (ctypes.c_int * 3)()
+        self._check(self.lib.sim_batch_tune(self.handle, self.scheme if scheme is None else int(scheme), out))
+        return tuple(out)
+
+    def field(self, instance: int, name: str) -> np.ndarray:
+        c = self.cases[instance]
+        shape = {"u": (c.ny, c.nx + 1), "v": (c.ny + 1, c.nx)}.get(name, (c.ny, c.nx))
+        a = np.empty(shape)
+        self._check(self.lib.sim_batch_fields(self.handle, instance, FIELDS[name], a.ctypes.data_as(_DP), a.size))
+        return a
+
+    def fields(self, instance: int, names: Sequence[str] = ("u", "v", "p", "T")) -> Dict[str, np.ndarray]:
+        return {k: self.field(instance, k) for k in names}
+
+    def residuals(self, instance: int):
+        out = np.zeros(4)
+        st = self.lib.sim_batch_residuals(self.handle, instance, out.ctypes.data_as(_DP))
+        if st not in (SIM_OK, SIM_EDIVERGED):
+            self._check(st)
+        return out, st
+
+    @property
+    def cells(self) -> int:
+        return sum(c.cells for c in self.cases)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.sim_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -856,3 +856,317 @@ extern "C" void sim_destroy(sim_t s)
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     delete s;
 }
+
+// ==================================================================== batches
+
+struct sim_batch_s {
+    std::vector<sim_t> inst;
+    cudaStream_t stream = nullptr;
+    bool mixed = false;
+    int iters = 1;
+    Inst *d_inst = nullptr;
+    int *d_tiles = nullptr;
+    size_t tiles_cap = 0;
+    BatchPlan plan{};
+    bool ghosts = false;                      // some problem has a symmetry side
+    struct Graph { cudaGraphExec_t exec = nullptr; int result = 0; };
+    Graph graphs[3][4];
+    cudaStream_t cap_stream = nullptr;
+    int cur = 0;
+    char err[256] = {0};
+};
+
+namespace {
+
+sim_status bfail(sim_batch_t b, sim_status st, const char *fmt, ...)
+{
+    if (b) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(b->err, sizeof b->err, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define BCUDA_TRY(b, call)                                                          \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            return bfail(b, SIM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+void drop_graphs(sim_batch_t b)
+{
+    for (auto &row : b->graphs)
+        for (auto &g : row)
+            if (g.exec) {
+                cudaGraphExecDestroy(g.exec);
+                g.exec = nullptr;
+            }
+}
+
+// Tile list for a tile shape: every problem's (nx+1) x (ny+1) positions cut
+// into tx x ty tiles; `grid` resident CTAs walk the list.
+sim_status plan_tiles(sim_batch_t b, int tx, int ty, int grid)
+{
+    std::vector<Inst> host(b->inst.size());
+    std::vector<int> tiles;
+    for (size_t q = 0; q < b->inst.size(); q++) {
+        const sim_t s = b->inst[q];
+        Inst &I = host[q];
+        I.g = s->geo;
+        I.k = s->pb.k;
+        I.g32 = s->mx.g;
+        I.k32 = s->mx.k;
+        for (int l = 0; l < 3; l++) {
+            I.lv[l] = s->lv[l];
+            I.lv32[l] = s->mx.lv[l];
+        }
+        I.w = s->work;
+        I.w32 = s->mx.w;
+        I.east_outflow = s->pb.side_kind[SIM_E] == SIM_BC_OUTFLOW;
+        I.tiles_x = (s->pb.nx + 1 + tx - 1) / tx;
+        const int tiles_y = (s->pb.ny + 1 + ty - 1) / ty;
+        I.tile0 = (int)tiles.size();
+        tiles.insert(tiles.end(), (size_t)I.tiles_x * tiles_y, (int)q);
+    }
+    if (!b->d_inst)
+        BCUDA_TRY(b, cudaMalloc(&b->d_inst, host.size() * sizeof(Inst)));
+    if (tiles.size() > b->tiles_cap) {
+        cudaFree(b->d_tiles);
+        b->d_tiles = nullptr;
+        BCUDA_TRY(b, cudaMalloc(&b->d_tiles, tiles.size() * sizeof(int)));
+        b->tiles_cap = tiles.size();
+    }
+    BCUDA_TRY(b, cudaMemcpyAsync(b->d_inst, host.data(), host.size() * sizeof(Inst), cudaMemcpyHostToDevice, b->stream));
+    BCUDA_TRY(b, cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
+    b->plan = BatchPlan{b->d_inst, b->d_tiles, (int)host.size(), (int)tiles.size(), tx, ty,
+                        grid > 0 ? std::min(grid, (int)tiles.size()) : (int)tiles.size()};
+    drop_graphs(b);
+    return SIM_OK;
+}
+
+// One time step of every problem from level `prev`; returns the result level.
+int enqueue_batch_step(sim_batch_t b, int prev, bool implicit, bool tvd, cudaStream_t st)
+{
+    const BatchPlan &bp = b->plan;
+    if (!implicit) {
+        launch_batch_faces(bp, b->mixed, prev, tvd, st);
+        launch_batch_explicit(bp, b->mixed, prev, tvd, st);
+    }
+    int old = prev;
+    for (int it = 1; it <= b->iters; it++) {
+        int nw = (old + 1) % 3;
+        if (nw == prev) nw = (nw + 1) % 3;
+        launch_batch_zero_res(bp, st);
+        launch_batch_faces(bp, b->mixed, old, tvd, st);
+        launch_batch_assemble(bp, b->mixed, prev, old, nw, implicit, tvd, st);
+        launch_batch_pressure(bp, b->mixed, prev, old, nw, st);
+        launch_batch_velocity(bp, b->mixed, old, nw, st);
+        if (b->ghosts)
+            for (sim_t s : b->inst)
+                if (ghost_kernels(s->sides, true)) {
+                    launch_ghosts(s->geo, s->sides, s->lv[nw], true, st);
+                    if (b->mixed) launch_ghosts_f32(s->mx, s->sides, nw, true, st);
+                }
+        old = nw;
+    }
+    return old;
+}
+
+void set_levels(sim_batch_t b, int cur)
+{
+    b->cur = cur;
+    for (sim_t s : b->inst) {
+        s->cur = cur;
+        s->last_iters = b->iters;
+    }
+}
+
+}  // namespace
+
+extern "C" sim_status sim_batch_create(int n, const sim_grid *grids, const sim_gas *gases, const sim_bc *bcs,
+                                       void *stream, sim_batch_t *out)
+{
+    if (!out) return SIM_EINVAL;
+    *out = nullptr;
+    if (n < 1 || !grids || !gases || !bcs) return SIM_EINVAL;
+    for (int q = 0; q < n; q++) {
+        if (bcs[q].precision != bcs[0].precision || bcs[q].iters != bcs[0].iters || bcs[q].tol != 0.0)
+            return SIM_EINVAL;
+    }
+    sim_batch_t b = new (std::nothrow) sim_batch_s;
+    if (!b) return SIM_ENOMEM;
+    b->stream = (cudaStream_t)stream;
+    b->mixed = bcs[0].precision == SIM_MIXED;
+    b->iters = bcs[0].iters;
+    for (int q = 0; q < n; q++) {
+        sim_t s = nullptr;
+        sim_status st = sim_create(&grids[q], &gases[q], &bcs[q], stream, &s);
+        if (st != SIM_OK) {
+            sim_batch_destroy(b);
+            return st;
+        }
+        b->inst.push_back(s);
+        if (ghost_kernels(s->sides, true)) b->ghosts = true;
+    }
+    sim_status st = plan_tiles(b, 32, 8, 0);
+    if (st != SIM_OK) {
+        sim_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_batch_step(sim_batch_t b, int n_steps, int scheme)
+{
+    if (!b) return SIM_EINVAL;
+    if (n_steps < 0 || (scheme & ~3)) return bfail(b, SIM_EINVAL, "bad n_steps %d or scheme %d", n_steps, scheme);
+    const bool implicit = scheme & SIM_IMPLICIT, tvd = scheme & SIM_TVD;
+    for (int step = 0; step < n_steps; step++) {
+        sim_batch_s::Graph &g = b->graphs[b->cur][scheme];
+        if (!g.exec) {
+            if (!b->cap_stream)
+                BCUDA_TRY(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            BCUDA_TRY(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+            g.result = enqueue_batch_step(b, b->cur, implicit, tvd, b->cap_stream);
+            BCUDA_TRY(b, cudaStreamEndCapture(b->cap_stream, &graph));
+            cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                g.exec = nullptr;
+                return bfail(b, SIM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+            }
+        }
+        BCUDA_TRY(b, cudaGraphLaunch(g.exec, b->stream));
+        set_levels(b, g.result);
+    }
+    BCUDA_TRY(b, cudaGetLastError());
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_batch_fields(sim_batch_t b, int instance, int field, double *host_dst, size_t n)
+{
+    if (!b || instance < 0 || instance >= (int)b->inst.size()) return SIM_EINVAL;
+    return sim_fields(b->inst[instance], field, host_dst, n);
+}
+
+extern "C" sim_status sim_batch_residuals(sim_batch_t b, int instance, double out[4])
+{
+    if (!b || instance < 0 || instance >= (int)b->inst.size()) return SIM_EINVAL;
+    return sim_residuals(b->inst[instance], out, nullptr);
+}
+
+extern "C" sim_status sim_batch_tune(sim_batch_t b, int scheme, int out[3])
+{
+    if (!b || !out || (scheme & ~3)) return SIM_EINVAL;
+    const bool implicit = scheme & SIM_IMPLICIT, tvd = scheme & SIM_TVD;
+    // keep a copy of every problem's current level (FP64 and FP32 shadow) and
+    // residual words, so that tuning leaves the simulation where it was
+    size_t total = 0;
+    for (sim_t s : b->inst) total += 6 * s->nelem * (sizeof(double) + (b->mixed ? sizeof(float) : 0)) + 32;
+    unsigned char *save = nullptr;
+    if (cudaMalloc(&save, total) != cudaSuccess) return bfail(b, SIM_ENOMEM, "no memory for the tuning copy");
+    const int start = b->cur;
+    auto copy_state = [&](bool to_save) -> cudaError_t {
+        unsigned char *p = save;
+        for (sim_t s : b->inst) {
+            const size_t n64 = s->nelem * sizeof(double), n32 = s->nelem * sizeof(float);
+            for (int f = 0; f < 6; f++) {
+                double *lvf = level_field(s->lv[start], f);
+                cudaError_t e = to_save ? cudaMemcpyAsync(p, lvf, n64, cudaMemcpyDeviceToDevice, b->stream)
+                                        : cudaMemcpyAsync(lvf, p, n64, cudaMemcpyDeviceToDevice, b->stream);
+                if (e != cudaSuccess) return e;
+                p += n64;
+                if (b->mixed) {
+                    const LevelT<float> &L = s->mx.lv[start];
+                    float *f32 = f == 0 ? L.u : f == 1 ? L.v : f == 2 ? L.p : f == 3 ? L.T : f == 4 ? L.rho : L.gam;
+                    e = to_save ? cudaMemcpyAsync(p, f32, n32, cudaMemcpyDeviceToDevice, b->stream)
+                                : cudaMemcpyAsync(f32, p, n32, cudaMemcpyDeviceToDevice, b->stream);
+                    if (e != cudaSuccess) return e;
+                    p += n32;
+                }
+            }
+            cudaError_t e = to_save ? cudaMemcpyAsync(p, s->work.res, 32, cudaMemcpyDeviceToDevice, b->stream)
+                                    : cudaMemcpyAsync(s->work.res, p, 32, cudaMemcpyDeviceToDevice, b->stream);
+            if (e != cudaSuccess) return e;
+            p += 32;
+        }
+        return cudaSuccess;
+    };
+    if (copy_state(true) != cudaSuccess) {
+        cudaFree(save);
+        return bfail(b, SIM_ECUDA, "saving the state before tuning failed");
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int shapes[4][2] = {{32, 8}, {64, 4}, {128, 2}, {16, 16}};
+    const int grids[3] = {2 * sms, 4 * sms, 0};       // 0: one CTA per tile
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bx = 32, by = 8, bg = 0;
+    sim_status st = SIM_OK;
+    for (auto &sh : shapes) {
+        for (int gsz : grids) {
+            if ((st = plan_tiles(b, sh[0], sh[1], gsz)) != SIM_OK) break;
+            int lv = start;
+            lv = enqueue_batch_step(b, lv, implicit, tvd, b->stream);     // warm-up
+            cudaEventRecord(e0, b->stream);
+            for (int r = 0; r < 3; r++) lv = enqueue_batch_step(b, lv, implicit, tvd, b->stream);
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = bfail(b, SIM_ECUDA, "tuning run failed");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bx = sh[0];
+                by = sh[1];
+                bg = gsz;
+            }
+            // next candidate starts from the saved state again
+            if (copy_state(false) != cudaSuccess) {
+                st = bfail(b, SIM_ECUDA, "restoring the state failed");
+                break;
+            }
+        }
+        if (st != SIM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(b->stream);
+    cudaFree(save);
+    if (st != SIM_OK) return st;
+    set_levels(b, start);
+    if ((st = plan_tiles(b, bx, by, bg)) != SIM_OK) return st;
+    out[0] = bx;
+    out[1] = by;
+    out[2] = b->plan.grid;
+    return SIM_OK;
+}
+
+extern "C" const char *sim_batch_last_error(sim_batch_t b)
+{
+    return b ? b->err : "null batch";
+}
+
+extern "C" void sim_batch_destroy(sim_batch_t b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_tiles);
+    for (sim_t s : b->inst) sim_destroy(s);
+    delete b;
+}

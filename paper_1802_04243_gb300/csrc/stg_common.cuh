@@ -88,6 +88,30 @@ struct Mixed {
     WorkT<float> w;
 };
 
+// One problem of a batch, as the batched kernels see it (device resident).
+struct Inst {
+    Geo g;
+    Coef k;
+    GeoT<float> g32;
+    CoefT<float> k32;
+    Level lv[3];
+    LevelT<float> lv32[3];
+    Work w;
+    WorkT<float> w32;
+    int east_outflow;
+    int tiles_x;          // tiles along x for the batch's tile shape
+    int tile0;            // index of this problem's first tile in the batch
+};
+
+// Work distribution of the batched kernels: tiles of tx x ty threads
+// (tx * ty = 256) over every problem, walked by `grid` resident CTAs.
+struct BatchPlan {
+    const Inst *inst;
+    const int *tile_inst; // problem of each tile
+    int n_inst, n_tiles;
+    int tx, ty, grid;
+};
+
 // Boundary description used by the ghost refresh.
 struct Sides {
     int kind[4];          // W, E, S, N
@@ -123,5 +147,14 @@ void launch_velocity_mixed(const Geo &g, const Sides &s, const Mixed &m, int old
                            const Work &w, void *stream);
 void launch_ghosts_f32(const Mixed &m, const Sides &s, int level, bool after_velocity, void *stream);
 void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, size_t nelem, void *stream);
+
+// Batched kernels: one launch per phase over every problem of a batch.
+void launch_batch_zero_res(const BatchPlan &bp, void *stream);
+void launch_batch_explicit(const BatchPlan &bp, bool mixed, int prev, bool tvd, void *stream);
+void launch_batch_faces(const BatchPlan &bp, bool mixed, int level, bool tvd, void *stream);
+void launch_batch_assemble(const BatchPlan &bp, bool mixed, int prev, int old, int nw, bool implicit, bool tvd,
+                           void *stream);
+void launch_batch_pressure(const BatchPlan &bp, bool mixed, int prev, int old, int nw, void *stream);
+void launch_batch_velocity(const BatchPlan &bp, bool mixed, int old, int nw, void *stream);
 
 }  // namespace stg

@@ -175,6 +175,7 @@ __device__ __forceinline__ void block_max2(unsigned long long a, unsigned long l
             if (b) atomicMax(db, b);
         }
     }
+    __syncthreads();       // the shared slots are reused by the block's next call
 }
 
 // ------------------------------------------------------- face densities
@@ -182,13 +183,10 @@ __device__ __forceinline__ void block_max2(unsigned long long a, unsigned long l
 // rho^u at u face (i,j) and rho^v at v face (i,j), Eqs. pl10, pl11, written as
 // the upwind value plus psi_s times the difference across the face.
 template <typename R, bool TVD>
-__global__ void __launch_bounds__(BX *BY) k_face_densities(GeoT<R> g, const R *__restrict__ u,
-                                                            const R *__restrict__ v,
-                                                            const R *__restrict__ rho,
-                                                            R *__restrict__ rho_u,
-                                                            R *__restrict__ rho_v)
+__device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const R *__restrict__ u, const R *__restrict__ v,
+                                                    const R *__restrict__ rho, R *__restrict__ rho_u,
+                                                    R *__restrict__ rho_v, int i, int j)
 {
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     const int P = g.pitch;
     const int c = Ix{P}(i, j);
     if (i <= g.nx && j < g.ny) {
@@ -207,6 +205,15 @@ __global__ void __launch_bounds__(BX *BY) k_face_densities(GeoT<R> g, const R *_
                                at(g.y.d, j), at(g.y.d, j + 1), vel) * (rt - rb);
         rho_v[c] = val;
     }
+}
+
+template <typename R, bool TVD>
+__global__ void __launch_bounds__(BX *BY) k_face_densities(GeoT<R> g, const R *__restrict__ u, const R *__restrict__ v,
+                                                            const R *__restrict__ rho, R *__restrict__ rho_u,
+                                                            R *__restrict__ rho_v)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    face_densities_body<R, TVD>(g, u, v, rho, rho_u, rho_v, i, j);
 }
 
 // ------------------------------------------------------- explicit terms
@@ -320,9 +327,9 @@ __device__ R explicit_u(const GeoT<R> &g, const LevelT<R> &L, const R *rho_v, in
 }
 
 template <typename R, bool TVD>
-__global__ void __launch_bounds__(BX *BY) k_explicit_terms(GeoT<R> g, LevelT<R> prev, WorkT<R> w)
+__device__ __forceinline__ void explicit_terms_body(const GeoT<R> &g, const LevelT<R> &prev, const WorkT<R> &w, int i,
+                                                    int j)
 {
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     const int c = Ix{g.pitch}(i, j);
     if (i > g.nx || j > g.ny) return;
     const uint16_t f = g.flag[c];
@@ -332,6 +339,13 @@ __global__ void __launch_bounds__(BX *BY) k_explicit_terms(GeoT<R> g, LevelT<R> 
         w.uexp[c] = (f & F_UACT) ? explicit_u<R, TVD>(g, prev, w.rho_v, c, i, j) : R(0);
     if (i < g.nx)
         w.vexp[c] = (f & F_VACT) ? explicit_v<R, TVD>(g, prev, w.rho_u, c, i, j) : R(0);
+}
+
+template <typename R, bool TVD>
+__global__ void __launch_bounds__(BX *BY) k_explicit_terms(GeoT<R> g, LevelT<R> prev, WorkT<R> w)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    explicit_terms_body<R, TVD>(g, prev, w, i, j);
 }
 
 // ------------------------------------------------------------ temperature
@@ -561,11 +575,10 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
 // the v face.  The new T goes to T_out (state precision) and, for the FP32
 // assembly of the mixed path, also to T32_out (the FP32 shadow copy).
 template <typename R, bool IMPL, bool TVD>
-__global__ void __launch_bounds__(BX *BY) k_assemble(GeoT<R> g, CoefT<R> k, LevelT<R> prev, LevelT<R> old,
-                                                      double *__restrict__ T_out, float *__restrict__ T32_out,
-                                                      WorkT<R> w)
+__device__ __forceinline__ void assemble_body(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev,
+                                              const LevelT<R> &old, double *__restrict__ T_out,
+                                              float *__restrict__ T32_out, const WorkT<R> &w, int i, int j)
 {
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     if (i > g.nx || j > g.ny) return;
     const int c = Ix{g.pitch}(i, j);
     const uint16_t f = g.flag[c];
@@ -594,13 +607,22 @@ __global__ void __launch_bounds__(BX *BY) k_assemble(GeoT<R> g, CoefT<R> k, Leve
     }
 }
 
+template <typename R, bool IMPL, bool TVD>
+__global__ void __launch_bounds__(BX *BY) k_assemble(GeoT<R> g, CoefT<R> k, LevelT<R> prev, LevelT<R> old,
+                                                      double *__restrict__ T_out, float *__restrict__ T32_out,
+                                                      WorkT<R> w)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    assemble_body<R, IMPL, TVD>(g, k, prev, old, T_out, T32_out, w, i, j);
+}
+
 // ---------------------------------------------------------------- pressure
 
 // Eqs. pl23, pl24 with the new T (point Jacobi in p^old), then rho = p/T
 // (Eq. pl5) and Gamma = T^omega, with the p and T residual maxima.
-__global__ void __launch_bounds__(BX *BY) k_pressure(Geo g, Coef k, Level prev, Level old, Level nw, Work w)
+__device__ __forceinline__ void pressure_body(const Geo &g, const Coef &k, const Level &prev, const Level &old,
+                                              const Level &nw, const Work &w, int i, int j)
 {
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     const int P = g.pitch;
     unsigned long long rp = 0, rT = 0;
     if (i < g.nx && j < g.ny) {
@@ -626,6 +648,12 @@ __global__ void __launch_bounds__(BX *BY) k_pressure(Geo g, Coef k, Level prev, 
         }
     }
     block_max2(rp, rT, &w.res[2], &w.res[3]);
+}
+
+__global__ void __launch_bounds__(BX *BY) k_pressure(Geo g, Coef k, Level prev, Level old, Level nw, Work w)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    pressure_body(g, k, prev, old, nw, w, i, j);
 }
 
 // -------------------------------------------------------------- velocity
@@ -654,9 +682,9 @@ __device__ __forceinline__ void outflow_copy(int j, int ny, int c, LevelT<R> L)
 
 // Eqs. pl18, pl19: velocities of the face unknowns from the new pressure,
 // then the outflow ghost copies of the row.
-__global__ void __launch_bounds__(BX *BY) k_velocity(Geo g, Level old, Level nw, Work w, int east_outflow)
+__device__ __forceinline__ void velocity_body(const Geo &g, const Level &old, const Level &nw, const Work &w,
+                                              int east_outflow, int i, int j)
 {
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     const int P = g.pitch;
     unsigned long long ru = 0, rv = 0;
     if (i <= g.nx && j <= g.ny) {
@@ -676,6 +704,12 @@ __global__ void __launch_bounds__(BX *BY) k_velocity(Geo g, Level old, Level nw,
             outflow_copy(j, g.ny, c, nw);
     }
     block_max2(ru, rv, &w.res[0], &w.res[1]);
+}
+
+__global__ void __launch_bounds__(BX *BY) k_velocity(Geo g, Level old, Level nw, Work w, int east_outflow)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    velocity_body(g, old, nw, w, east_outflow, i, j);
 }
 
 // ------------------------------------------------------------ ghost copies
@@ -779,12 +813,12 @@ __global__ void k_ghost_sn(GeoT<R> g, Sides s, LevelT<R> L)
 // (relative error below 1e-14).  Gamma = T^omega is a coefficient: FP32.
 // T carries FP32 values in this path, so its residual difference is formed
 // exactly in FP32.
-__global__ void __launch_bounds__(BX *BY) k_pressure_mixed(Geo g, Coef k, GeoT<float> g32, CoefT<float> k32,
-                                                            Level prev, Level old, Level nw, LevelT<float> old32,
-                                                            LevelT<float> nw32, WorkT<float> w,
-                                                            unsigned long long *res)
+__device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k, const GeoT<float> &g32,
+                                                    const CoefT<float> &k32, const Level &prev, const Level &old,
+                                                    const Level &nw, const LevelT<float> &old32,
+                                                    const LevelT<float> &nw32, const WorkT<float> &w,
+                                                    unsigned long long *res, int i, int j)
 {
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     const int P = g.pitch;
     unsigned long long rp = 0, rT = 0;
     if (i < g.nx && j < g.ny) {
@@ -828,14 +862,23 @@ __global__ void __launch_bounds__(BX *BY) k_pressure_mixed(Geo g, Coef k, GeoT<f
     block_max2(rp, rT, &res[2], &res[3]);
 }
 
+__global__ void __launch_bounds__(BX *BY) k_pressure_mixed(Geo g, Coef k, GeoT<float> g32, CoefT<float> k32,
+                                                            Level prev, Level old, Level nw, LevelT<float> old32,
+                                                            LevelT<float> nw32, WorkT<float> w,
+                                                            unsigned long long *res)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    pressure_mixed_body(g, k, g32, k32, prev, old, nw, old32, nw32, w, res, i, j);
+}
+
 // Mixed precision, Eqs. pl18, pl19: FP32 correction of the FP32 pseudo
 // velocities by the FP64 pressure difference.  u and v carry FP32 values in
 // this path: their residual differences are formed in FP32 and reduced as
 // FP64 bit patterns.
-__global__ void __launch_bounds__(BX *BY) k_velocity_mixed(Geo g, Level nw, LevelT<float> old32, LevelT<float> nw32,
-                                                            WorkT<float> w, unsigned long long *res, int east_outflow)
+__device__ __forceinline__ void velocity_mixed_body(const Geo &g, const Level &nw, const LevelT<float> &old32,
+                                                    const LevelT<float> &nw32, const WorkT<float> &w,
+                                                    unsigned long long *res, int east_outflow, int i, int j)
 {
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     const int P = g.pitch;
     unsigned long long ru = 0, rv = 0;
     if (i <= g.nx && j <= g.ny) {
@@ -861,6 +904,13 @@ __global__ void __launch_bounds__(BX *BY) k_velocity_mixed(Geo g, Level nw, Leve
     block_max2(ru, rv, &res[0], &res[1]);
 }
 
+__global__ void __launch_bounds__(BX *BY) k_velocity_mixed(Geo g, Level nw, LevelT<float> old32, LevelT<float> nw32,
+                                                            WorkT<float> w, unsigned long long *res, int east_outflow)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    velocity_mixed_body(g, nw, old32, nw32, w, res, east_outflow, i, j);
+}
+
 // FP32 shadow copy of a whole FP64 level (every element, ghosts included).
 __global__ void k_shadow(Level L, LevelT<float> S, size_t n)
 {
@@ -872,6 +922,89 @@ __global__ void k_shadow(Level L, LevelT<float> S, size_t n)
         S.rho[q] = (float)L.rho[q];
         S.gam[q] = (float)L.gam[q];
     }
+}
+
+
+// ------------------------------------------------------------ batched kernels
+
+// Walk the tiles of every problem of a batch with the resident CTAs; each
+// tile is tx x ty threads of one problem.
+template <typename F>
+__device__ __forceinline__ void for_tiles(const BatchPlan &bp, F &&f)
+{
+    for (int t = blockIdx.x; t < bp.n_tiles; t += gridDim.x) {
+        const Inst &I = bp.inst[bp.tile_inst[t]];
+        const int lt = t - I.tile0;
+        const int i = (lt % I.tiles_x) * bp.tx + threadIdx.x;
+        const int j = (lt / I.tiles_x) * bp.ty + threadIdx.y;
+        f(I, i, j);
+    }
+}
+
+__global__ void k_batch_zero_res(BatchPlan bp)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < bp.n_inst * 4) bp.inst[q >> 2].w.res[q & 3] = 0ull;
+}
+
+template <bool MIXED, bool TVD>
+__global__ void __launch_bounds__(256) k_batch_faces(BatchPlan bp, int level)
+{
+    for_tiles(bp, [&](const Inst &I, int i, int j) {
+        if constexpr (MIXED) {
+            const LevelT<float> &L = I.lv32[level];
+            face_densities_body<float, TVD>(I.g32, L.u, L.v, L.rho, I.w32.rho_u, I.w32.rho_v, i, j);
+        } else {
+            const Level &L = I.lv[level];
+            face_densities_body<double, TVD>(I.g, L.u, L.v, L.rho, I.w.rho_u, I.w.rho_v, i, j);
+        }
+    });
+}
+
+template <bool MIXED, bool TVD>
+__global__ void __launch_bounds__(256) k_batch_explicit(BatchPlan bp, int prev)
+{
+    for_tiles(bp, [&](const Inst &I, int i, int j) {
+        if constexpr (MIXED)
+            explicit_terms_body<float, TVD>(I.g32, I.lv32[prev], I.w32, i, j);
+        else
+            explicit_terms_body<double, TVD>(I.g, I.lv[prev], I.w, i, j);
+    });
+}
+
+template <bool MIXED, bool IMPL, bool TVD>
+__global__ void __launch_bounds__(256) k_batch_assemble(BatchPlan bp, int prev, int old, int nw)
+{
+    for_tiles(bp, [&](const Inst &I, int i, int j) {
+        if constexpr (MIXED)
+            assemble_body<float, IMPL, TVD>(I.g32, I.k32, I.lv32[prev], I.lv32[old], I.lv[nw].T, I.lv32[nw].T, I.w32,
+                                           i, j);
+        else
+            assemble_body<double, IMPL, TVD>(I.g, I.k, I.lv[prev], I.lv[old], I.lv[nw].T, nullptr, I.w, i, j);
+    });
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256) k_batch_pressure(BatchPlan bp, int prev, int old, int nw)
+{
+    for_tiles(bp, [&](const Inst &I, int i, int j) {
+        if constexpr (MIXED)
+            pressure_mixed_body(I.g, I.k, I.g32, I.k32, I.lv[prev], I.lv[old], I.lv[nw], I.lv32[old], I.lv32[nw],
+                                I.w32, I.w.res, i, j);
+        else
+            pressure_body(I.g, I.k, I.lv[prev], I.lv[old], I.lv[nw], I.w, i, j);
+    });
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256) k_batch_velocity(BatchPlan bp, int old, int nw)
+{
+    for_tiles(bp, [&](const Inst &I, int i, int j) {
+        if constexpr (MIXED)
+            velocity_mixed_body(I.g, I.lv[nw], I.lv32[old], I.lv32[nw], I.w32, I.w.res, I.east_outflow, i, j);
+        else
+            velocity_body(I.g, I.lv[old], I.lv[nw], I.w, I.east_outflow, i, j);
+    });
 }
 
 // ----------------------------------------------------- state maintenance
@@ -1074,6 +1207,69 @@ void launch_scatter(const Geo &g, int field, const double *src, const Level &lv,
 void launch_gather(const Geo &g, int field, const Level &lv, double *dst, void *stream)
 {
     k_gather<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, field, lv, dst);
+}
+
+}  // namespace stg
+
+namespace stg {
+
+void launch_batch_zero_res(const BatchPlan &bp, void *stream)
+{
+    k_batch_zero_res<<<(bp.n_inst * 4 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(bp);
+}
+
+void launch_batch_faces(const BatchPlan &bp, bool mixed, int level, bool tvd, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const dim3 bl(bp.tx, bp.ty);
+    if (mixed && tvd) k_batch_faces<true, true><<<bp.grid, bl, 0, s>>>(bp, level);
+    else if (mixed) k_batch_faces<true, false><<<bp.grid, bl, 0, s>>>(bp, level);
+    else if (tvd) k_batch_faces<false, true><<<bp.grid, bl, 0, s>>>(bp, level);
+    else k_batch_faces<false, false><<<bp.grid, bl, 0, s>>>(bp, level);
+}
+
+void launch_batch_explicit(const BatchPlan &bp, bool mixed, int prev, bool tvd, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const dim3 bl(bp.tx, bp.ty);
+    if (mixed && tvd) k_batch_explicit<true, true><<<bp.grid, bl, 0, s>>>(bp, prev);
+    else if (mixed) k_batch_explicit<true, false><<<bp.grid, bl, 0, s>>>(bp, prev);
+    else if (tvd) k_batch_explicit<false, true><<<bp.grid, bl, 0, s>>>(bp, prev);
+    else k_batch_explicit<false, false><<<bp.grid, bl, 0, s>>>(bp, prev);
+}
+
+void launch_batch_assemble(const BatchPlan &bp, bool mixed, int prev, int old, int nw, bool implicit, bool tvd,
+                           void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const dim3 bl(bp.tx, bp.ty);
+    const int code = (mixed ? 4 : 0) | (implicit ? 2 : 0) | (tvd ? 1 : 0);
+    switch (code) {
+    case 7: k_batch_assemble<true, true, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    case 6: k_batch_assemble<true, true, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    case 5: k_batch_assemble<true, false, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    case 4: k_batch_assemble<true, false, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    case 3: k_batch_assemble<false, true, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    case 2: k_batch_assemble<false, true, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    case 1: k_batch_assemble<false, false, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    default: k_batch_assemble<false, false, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    }
+}
+
+void launch_batch_pressure(const BatchPlan &bp, bool mixed, int prev, int old, int nw, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const dim3 bl(bp.tx, bp.ty);
+    if (mixed) k_batch_pressure<true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+    else k_batch_pressure<false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+}
+
+void launch_batch_velocity(const BatchPlan &bp, bool mixed, int old, int nw, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const dim3 bl(bp.tx, bp.ty);
+    if (mixed) k_batch_velocity<true><<<bp.grid, bl, 0, s>>>(bp, old, nw);
+    else k_batch_velocity<false><<<bp.grid, bl, 0, s>>>(bp, old, nw);
 }
 
 }  // namespace stg

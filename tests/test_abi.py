@@ -73,6 +73,19 @@ def test_invalid_descriptions_are_rejected_on_the_host(lib, bad):
     assert _create(case) == sim.SIM_EINVAL
 
 
+def test_batch_rejects_inconsistent_descriptions_on_the_host(lib):
+    import ctypes
+    cases = [W.c1_small(), W.c1_small().replace(precision=W.MIXED)]
+    descs = [sim._Desc(c) for c in cases]
+    grids, gases, bcs = (sim.sim_grid * 2)(), (sim.sim_gas * 2)(), (sim.sim_bc * 2)()
+    for q, d in enumerate(descs):
+        grids[q], gases[q], bcs[q] = d.grid, d.gas, d.bc
+    h = ctypes.c_void_p()
+    assert lib.sim_batch_create(2, grids, gases, bcs, None, ctypes.byref(h)) == sim.SIM_EINVAL
+    assert lib.sim_batch_create(0, grids, gases, bcs, None, ctypes.byref(h)) == sim.SIM_EINVAL
+    lib.sim_batch_destroy(None)
+
+
 def test_null_arguments(lib):
     assert lib.sim_create(None, None, None, None, None) == sim.SIM_EINVAL
     lib.sim_destroy(None)

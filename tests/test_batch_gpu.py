@@ -1,0 +1,84 @@
+"""Batches (sim_batch_*): one launch per kernel phase over many problems of
+different sizes and parameters.  Every problem of a batch must come out
+exactly as if it had been advanced alone with sim_step."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1802_04243_gb300 as sim
+import workloads as W
+from paper_1802_04243_gb300 import build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    sim.load()
+
+
+def small_batch(n=5, precision=W.MIXED, implicit=True, tvd=False):
+    cases = W.c5_batch(n=n, precision=precision)
+    # keep the test quick: shrink every problem by 4 in each direction
+    out = []
+    for c in cases:
+        nx, ny = c.nx // 4, c.ny // 4
+        side = max(2, int(round(ny / 5.0)))
+        out.append(W.channel(nx, ny, side, n_squares=len(c.rects), first_at_quarter=False, name=c.name,
+                             mach_in=c.mach_in, reynolds=c.reynolds, seed=c.seed, implicit=implicit, tvd=tvd,
+                             precision=precision))
+    return out
+
+
+@pytest.mark.parametrize("precision", [W.FP64, W.MIXED])
+@pytest.mark.parametrize("implicit,tvd", [(True, False), (False, True)])
+def test_batch_equals_problems_advanced_alone(precision, implicit, tvd):
+    cases = small_batch(precision=precision, implicit=implicit, tvd=tvd)
+    assert len({c.nx for c in cases}) > 1                      # uneven sizes
+    with sim.Batch(cases) as b:
+        b.step(7)
+        got = [b.fields(q) for q in range(len(cases))]
+        res = [b.residuals(q)[0] for q in range(len(cases))]
+    for q, c in enumerate(cases):
+        with sim.Simulation(c) as s:
+            s.step(7)
+            ref = s.fields()
+            rres, _, _ = s.residuals()
+        for k in "uvpT":
+            assert np.array_equal(got[q][k], ref[k]), (q, k)
+        np.testing.assert_array_equal(res[q], rres)
+
+
+def test_batch_fp64_matches_oracle():
+    cases = small_batch(n=3, precision=W.FP64)
+    with sim.Batch(cases) as b:
+        b.step(10)
+        got = [b.fields(q) for q in range(len(cases))]
+    for q, c in enumerate(cases):
+        o, _, _ = oracle.run(c, nsteps=10)
+        err = max(float(np.abs(got[q][k] - o[k]).max() / np.abs(o[k]).max()) for k in "uvpT")
+        assert err <= 1e-9, (q, err)
+
+
+def test_tuning_keeps_the_state_and_the_results():
+    cases = small_batch(n=4)
+    with sim.Batch(cases) as a, sim.Batch(cases) as b:
+        a.step(3)
+        b.step(3)
+        tx, ty, grid = b.tune()
+        assert tx * ty == 256 and grid >= 1
+        a.step(4)
+        b.step(4)                                  # replays graphs built for the tuned tiles
+        for q in range(len(cases)):
+            fa, fb = a.fields(q), b.fields(q)
+            for k in "uvpT":
+                assert np.array_equal(fa[k], fb[k]), (q, k)
+
+
+def test_batch_rejects_mixed_loop2_lengths():
+    cases = small_batch(n=2)
+    cases[1] = cases[1].replace(iters=3)
+    with pytest.raises(sim.SimError) as e:
+        sim.Batch(cases)
+    assert e.value.status == sim.SIM_EINVAL
