@@ -5,7 +5,8 @@
 // three state levels in the padded layout, the per-iteration scratch of the
 // sweep (face densities, pseudo velocities, d coefficients, explicit terms)
 // and the residual words -- is carved out of one file-scope device array.
-// The sweep itself runs through the same kernel launchers as sim_step.
+// The sweep itself runs through the same kernels as sim_step, over a
+// one-problem tile list that also lives in the array.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -150,6 +151,12 @@ __global__ void k_na_flags(Setup s, uint16_t *flag)
     if (uy) b |= F_TUY;
     if (vx) b |= F_TVX;
     if (vy) b |= F_TVY;
+    const int i0 = (i >= 0 ? i : i - 31) / 32 * 32;    // 32-wide row segment holding i
+    bool inner = true;
+    for (int q = -2; q <= 2 && inner; q++)
+        for (int r = i0 - 2; r <= i0 + 33 && inner; r++)
+            inner = nfluid(s, r, j + q);
+    if (inner) b |= F_INTERIOR;
     flag[nidx(s, i, j)] = (uint16_t)b;
 }
 
@@ -210,6 +217,16 @@ __global__ void k_na_fill(Setup s, const double *u_in, const double *v_in, const
 }
 
 // Bump allocator over the scratch (offsets only; nothing is allocated).
+// The problem descriptor of the equation kernels and its tile list (every
+// tile belongs to problem 0), written from the launch parameters so that no
+// host memory is read when the work runs.
+__global__ void k_na_plan(Inst I, Inst *dst, int *tiles, int n_tiles)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q == 0) *dst = I;
+    if (q < n_tiles) tiles[q] = 0;
+}
+
 struct Carver {
     unsigned char *base;
     size_t used = 0;
@@ -323,7 +340,7 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     const size_t nelem = (size_t)pitch * (ny + 2 * G + 1);
     const int mx = nx + 2 * G + 1, my = ny + 2 * G + 1;
     Carver cv{(unsigned char *)base};
-    double *pool = cv.take<double>(27 * nelem);
+    double *pool = cv.take<double>(31 * nelem);
     uint16_t *flag = cv.take<uint16_t>(nelem);
     uint8_t *kind = cv.take<uint8_t>(nelem);
     uint8_t *side = cv.take<uint8_t>(nelem);
@@ -334,6 +351,9 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     double *cin = cv.take<double>(3 * (size_t)ny);
     int *crect = cv.take<int>(4 * kMaxRects);
     unsigned long long *res = cv.take<unsigned long long>(4);
+    const int tiles_x = (nx + 1 + 31) / 32, n_tiles = tiles_x * ((ny + 1 + 7) / 8);
+    Inst *inst = cv.take<Inst>(1);
+    int *tiles = cv.take<int>(n_tiles);
     if (!cv.ok) return SIM_ENOMEM;           // the problem does not fit the static scratch
 
     cudaStream_t s = (cudaStream_t)stream;
@@ -345,7 +365,7 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     if (bc->inflow_p) NA_TRY(cudaMemcpyAsync(cin + 2 * ny, bc->inflow_p, ny * sizeof(double), cudaMemcpyHostToDevice, s));
     if (bc->n_rect) NA_TRY(cudaMemcpyAsync(crect, bc->rect, 4 * bc->n_rect * sizeof(int), cudaMemcpyHostToDevice, s));
     // the scratch keeps the previous call's contents: clear the work arrays
-    NA_TRY(cudaMemsetAsync(pool + 18 * nelem, 0, 9 * nelem * sizeof(double), s));
+    NA_TRY(cudaMemsetAsync(pool + 18 * nelem, 0, 13 * nelem * sizeof(double), s));
 
     Setup su{};
     su.nx = nx; su.ny = ny; su.pitch = pitch;
@@ -372,7 +392,9 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
         lv[l].T = q; q += nelem; lv[l].rho = q; q += nelem; lv[l].gam = q; q += nelem;
     }
     Work w{};
-    w.rho_u = q; q += nelem; w.rho_v = q; q += nelem; w.uhat = q; q += nelem; w.du = q; q += nelem;
+    w.rho_u = q; q += nelem; w.rho_v = q; q += nelem;
+    w.Fx = q; q += nelem; w.Fy = q; q += nelem; w.hx = q; q += nelem; w.hy = q; q += nelem;
+    w.uhat = q; q += nelem; w.du = q; q += nelem;
     w.vhat = q; q += nelem; w.dv = q; q += nelem; w.uexp = q; q += nelem; w.vexp = q; q += nelem;
     w.Texp = q;
     w.res = res;
@@ -401,6 +423,17 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
         }
     NA_TRY(cudaMemsetAsync(res, 0, 4 * sizeof(unsigned long long), s));
 
+    Inst one{};
+    one.g = g;
+    one.k = k;
+    for (int l = 0; l < 3; l++) one.lv[l] = lv[l];
+    one.w = w;
+    one.east_outflow = bc->side_kind[SIM_E] == SIM_BC_OUTFLOW;
+    one.tiles_x = tiles_x;
+    one.tile0 = 0;
+    k_na_plan<<<(n_tiles + 255) / 256, 256, 0, s>>>(one, inst, tiles, n_tiles);
+    const BatchPlan plan{inst, tiles, 1, n_tiles, 32, 8, n_tiles, one};
+
     // ------------------------------------------------- the time steps (S0-S9)
     const bool implicit = scheme & SIM_IMPLICIT, tvd = scheme & SIM_TVD;
     int cur = 0;
@@ -408,17 +441,17 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
         const int prev = cur;
         int old = prev;
         if (!implicit) {
-            launch_face_densities(g, lv[prev], w, tvd, s);
-            launch_explicit_terms(g, lv[prev], w, tvd, s);
+            launch_faces(plan, false, prev, tvd, s);
+            launch_explicit(plan, false, prev, tvd, s);
         }
         for (int it = 0; it < bc->iters; it++) {
             int nw = (old + 1) % 3;
             if (nw == prev) nw = (nw + 1) % 3;
             NA_TRY(cudaMemsetAsync(res, 0, 4 * sizeof(unsigned long long), s));
-            launch_face_densities(g, lv[old], w, tvd, s);
-            launch_assemble(g, k, lv[prev], lv[old], lv[nw], w, implicit, tvd, s);
-            launch_pressure(g, k, lv[prev], lv[old], lv[nw], w, s);
-            launch_velocity(g, sides, lv[old], lv[nw], w, s);
+            launch_faces(plan, false, old, tvd, s);
+            launch_assemble(plan, false, prev, old, nw, implicit, tvd, s);
+            launch_pressure(plan, false, prev, old, nw, s);
+            launch_velocity(plan, false, old, nw, s);
             launch_ghosts(g, sides, lv[nw], true, s);
             old = nw;
         }

@@ -57,6 +57,10 @@ struct sim_s {
     Mixed mx{};
     float *d_pool32 = nullptr;
     float *d_axis32 = nullptr;
+    // the one-problem tile list the equation kernels walk (32 x 8 tiles)
+    Inst *d_inst = nullptr;
+    int *d_tiles = nullptr;
+    BatchPlan plan{};
     unsigned long long *h_res = nullptr;       // pinned copy of the residuals
     int cur = 0;                               // level holding the current state
     int last_iters = 0;
@@ -281,6 +285,13 @@ std::vector<uint16_t> make_flags(const HostGrid &h)
             if (uy) b |= F_TUY;
             if (vx) b |= F_TVX;
             if (vy) b |= F_TVY;
+            // the 32-wide row segment holding i has no wall within two cells
+            const int i0 = (i >= 0 ? i : i - 31) / 32 * 32;
+            bool inner = true;
+            for (int q = -2; q <= 2 && inner; q++)
+                for (int r = i0 - 2; r <= i0 + 33 && inner; r++)
+                    inner = h.fluid(r, j + q);
+            if (inner) b |= F_INTERIOR;
             f[h.at(i, j)] = (uint16_t)b;
         }
     return f;
@@ -382,6 +393,32 @@ double *level_field(const Level &L, int f)
     }
 }
 
+// The problem as the equation kernels see it, cut into tiles of tx x ty
+// threads that start at entry `tile0` of the tile list.
+Inst inst_of(const sim_s *s, int tx, int tile0)
+{
+    Inst I{};
+    I.g = s->geo;
+    I.k = s->pb.k;
+    I.g32 = s->mx.g;
+    I.k32 = s->mx.k;
+    for (int l = 0; l < 3; l++) {
+        I.lv[l] = s->lv[l];
+        I.lv32[l] = s->mx.lv[l];
+    }
+    I.w = s->work;
+    I.w32 = s->mx.w;
+    I.east_outflow = s->pb.side_kind[SIM_E] == SIM_BC_OUTFLOW;
+    I.tiles_x = (s->pb.nx + 1 + tx - 1) / tx;
+    I.tile0 = tile0;
+    return I;
+}
+
+int tiles_of(const sim_s *s, int tx, int ty)
+{
+    return ((s->pb.nx + 1 + tx - 1) / tx) * ((s->pb.ny + 1 + ty - 1) / ty);
+}
+
 size_t field_count(const Problem &pb, int f)
 {
     const size_t nx = pb.nx, ny = pb.ny;
@@ -430,49 +467,26 @@ struct Launch {
 // (explicit scheme only, once per step).  counts != nullptr: capture mode.
 void enqueue_explicit(sim_t s, int prev, bool tvd, cudaStream_t st, long long *counts)
 {
-    if (s->mixed) {
-        { Launch l(s, SIM_K_FACES, st, counts); launch_face_densities_f32(s->mx, prev, tvd, st); }
-        { Launch l(s, SIM_K_EXPLICIT, st, counts); launch_explicit_terms_f32(s->mx, prev, tvd, st); }
-    } else {
-        { Launch l(s, SIM_K_FACES, st, counts); launch_face_densities(s->geo, s->lv[prev], s->work, tvd, st); }
-        { Launch l(s, SIM_K_EXPLICIT, st, counts); launch_explicit_terms(s->geo, s->lv[prev], s->work, tvd, st); }
-    }
+    { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, s->mixed, prev, tvd, st); }
+    { Launch l(s, SIM_K_EXPLICIT, st, counts); launch_explicit(s->plan, s->mixed, prev, tvd, st); }
 }
 
 // One loop-2 iteration from level `old` (level `prev` holds n-1) into the
 // third level, which is returned.
 int enqueue_iteration(sim_t s, int prev, int old, bool implicit, bool tvd, cudaStream_t st, long long *counts)
 {
-    const Problem &pb = s->pb;
     int nw = (old + 1) % 3;
     if (nw == prev) nw = (nw + 1) % 3;
     const int ng = ghost_kernels(s->sides, true);
     cudaMemsetAsync(s->work.res, 0, 4 * sizeof(unsigned long long), st);
-    if (s->mixed) {
-        { Launch l(s, SIM_K_FACES, st, counts); launch_face_densities_f32(s->mx, old, tvd, st); }
-        { Launch l(s, SIM_K_ASSEMBLE, st, counts);
-          launch_assemble_f32(s->mx, prev, old, nw, s->lv[nw], implicit, tvd, st); }
-        { Launch l(s, SIM_K_PRESSURE, st, counts);
-          launch_pressure_mixed(s->geo, pb.k, s->mx, s->lv[prev], s->lv[old], old, s->lv[nw], nw, s->work, st); }
-        { Launch l(s, SIM_K_VELOCITY, st, counts);
-          launch_velocity_mixed(s->geo, s->sides, s->mx, old, s->lv[nw], nw, s->work, st); }
-        if (ng) {
-            Launch l(s, SIM_K_GHOSTS, st, counts, 2 * ng);
-            launch_ghosts(s->geo, s->sides, s->lv[nw], true, st);
-            launch_ghosts_f32(s->mx, s->sides, nw, true, st);
-        }
-    } else {
-        { Launch l(s, SIM_K_FACES, st, counts); launch_face_densities(s->geo, s->lv[old], s->work, tvd, st); }
-        { Launch l(s, SIM_K_ASSEMBLE, st, counts);
-          launch_assemble(s->geo, pb.k, s->lv[prev], s->lv[old], s->lv[nw], s->work, implicit, tvd, st); }
-        { Launch l(s, SIM_K_PRESSURE, st, counts);
-          launch_pressure(s->geo, pb.k, s->lv[prev], s->lv[old], s->lv[nw], s->work, st); }
-        { Launch l(s, SIM_K_VELOCITY, st, counts);
-          launch_velocity(s->geo, s->sides, s->lv[old], s->lv[nw], s->work, st); }
-        if (ng) {
-            Launch l(s, SIM_K_GHOSTS, st, counts, ng);
-            launch_ghosts(s->geo, s->sides, s->lv[nw], true, st);
-        }
+    { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, s->mixed, old, tvd, st); }
+    { Launch l(s, SIM_K_ASSEMBLE, st, counts); launch_assemble(s->plan, s->mixed, prev, old, nw, implicit, tvd, st); }
+    { Launch l(s, SIM_K_PRESSURE, st, counts); launch_pressure(s->plan, s->mixed, prev, old, nw, st); }
+    { Launch l(s, SIM_K_VELOCITY, st, counts); launch_velocity(s->plan, s->mixed, old, nw, st); }
+    if (ng) {
+        Launch l(s, SIM_K_GHOSTS, st, counts, s->mixed ? 2 * ng : ng);
+        launch_ghosts(s->geo, s->sides, s->lv[nw], true, st);
+        if (s->mixed) launch_ghosts_f32(s->mx, s->sides, nw, true, st);
     }
     return nw;
 }
@@ -525,8 +539,8 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
     std::vector<uint16_t> flags = make_flags(h);
     std::vector<double> ax = make_axis(pb.dx), ay = make_axis(pb.dy);
 
-    // one pool for 3 levels x 6 fields + 9 work arrays
-    const size_t nfields = 3 * 6 + 9;
+    // one pool for 3 levels x 6 fields + 13 work arrays
+    const size_t nfields = 3 * 6 + 13;
     cudaError_t e = cudaMalloc(&s->d_pool, nfields * s->nelem * sizeof(double));
     if (e != cudaSuccess) {
         sim_destroy(s);
@@ -545,6 +559,10 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
     Work &w = s->work;
     w.rho_u = q; q += s->nelem;
     w.rho_v = q; q += s->nelem;
+    w.Fx = q; q += s->nelem;
+    w.Fy = q; q += s->nelem;
+    w.hx = q; q += s->nelem;
+    w.hy = q; q += s->nelem;
     w.uhat = q; q += s->nelem;
     w.du = q; q += s->nelem;
     w.vhat = q; q += s->nelem;
@@ -575,7 +593,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
 
     s->mixed = pb.precision == SIM_MIXED;
     if (s->mixed) {
-        if (cudaMalloc(&s->d_pool32, 27 * s->nelem * sizeof(float)) != cudaSuccess ||
+        if (cudaMalloc(&s->d_pool32, 31 * s->nelem * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&s->d_axis32, (nax + nay) * sizeof(float)) != cudaSuccess) {
             sim_destroy(s);
             return SIM_ENOMEM;
@@ -593,6 +611,10 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         WorkT<float> &w32 = s->mx.w;
         w32.rho_u = p32; p32 += s->nelem;
         w32.rho_v = p32; p32 += s->nelem;
+        w32.Fx = p32; p32 += s->nelem;
+        w32.Fy = p32; p32 += s->nelem;
+        w32.hx = p32; p32 += s->nelem;
+        w32.hy = p32; p32 += s->nelem;
         w32.uhat = p32; p32 += s->nelem;
         w32.du = p32; p32 += s->nelem;
         w32.vhat = p32; p32 += s->nelem;
@@ -614,7 +636,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         for (size_t q = 0; q < nax; q++) a32[q] = (float)ax[q];
         for (size_t q = 0; q < nay; q++) a32[nax + q] = (float)ay[q];
         CUDA_TRY(s, cudaMemcpy(s->d_axis32, a32.data(), a32.size() * sizeof(float), cudaMemcpyHostToDevice));
-        CUDA_TRY(s, cudaMemsetAsync(s->mx.w.rho_u, 0, 9 * s->nelem * sizeof(float), s->stream));
+        CUDA_TRY(s, cudaMemsetAsync(s->mx.w.rho_u, 0, 13 * s->nelem * sizeof(float), s->stream));
     }
 
     std::vector<double> f[6];
@@ -624,7 +646,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
     CUDA_TRY(s, cudaMemcpyAsync(s->d_flag, flags.data(), flags.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(s, cudaMemcpyAsync(s->d_axis, ax.data(), nax * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(s, cudaMemcpyAsync(s->d_axis + nax, ay.data(), nay * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    CUDA_TRY(s, cudaMemsetAsync(s->d_pool + 18 * s->nelem, 0, 9 * s->nelem * sizeof(double), s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(s->d_pool + 18 * s->nelem, 0, 13 * s->nelem * sizeof(double), s->stream));
     CUDA_TRY(s, cudaMemsetAsync(w.res, 0, 4 * sizeof(unsigned long long), s->stream));
     for (int l = 0; l < 3; l++)
         for (int k = 0; k < 6; k++)
@@ -635,6 +657,16 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         launch_ghosts(s->geo, s->sides, s->lv[l], false, s->stream);
         if (s->mixed) launch_shadow(s->geo, s->lv[l], s->mx.lv[l], s->nelem, s->stream);
     }
+    const Inst one = inst_of(s, 32, 0);
+    const int ntiles = tiles_of(s, 32, 8);
+    if (cudaMalloc(&s->d_inst, sizeof(Inst)) != cudaSuccess ||
+        cudaMalloc(&s->d_tiles, ntiles * sizeof(int)) != cudaSuccess) {
+        sim_destroy(s);
+        return SIM_ENOMEM;
+    }
+    CUDA_TRY(s, cudaMemcpyAsync(s->d_inst, &one, sizeof(Inst), cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(s->d_tiles, 0, ntiles * sizeof(int), s->stream));
+    s->plan = BatchPlan{s->d_inst, s->d_tiles, 1, ntiles, 32, 8, ntiles, one};
     CUDA_TRY(s, cudaGetLastError());
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
     *out = s;
@@ -844,6 +876,8 @@ extern "C" void sim_destroy(sim_t s)
     cudaFree(s->work.res);
     cudaFree(s->d_pool32);
     cudaFree(s->d_axis32);
+    cudaFree(s->d_inst);
+    cudaFree(s->d_tiles);
     if (s->h_res) cudaFreeHost(s->h_res);
     for (auto &m : s->marks) {
         cudaEventDestroy(m.e0);
@@ -914,22 +948,8 @@ sim_status plan_tiles(sim_batch_t b, int tx, int ty, int grid)
     std::vector<int> tiles;
     for (size_t q = 0; q < b->inst.size(); q++) {
         const sim_t s = b->inst[q];
-        Inst &I = host[q];
-        I.g = s->geo;
-        I.k = s->pb.k;
-        I.g32 = s->mx.g;
-        I.k32 = s->mx.k;
-        for (int l = 0; l < 3; l++) {
-            I.lv[l] = s->lv[l];
-            I.lv32[l] = s->mx.lv[l];
-        }
-        I.w = s->work;
-        I.w32 = s->mx.w;
-        I.east_outflow = s->pb.side_kind[SIM_E] == SIM_BC_OUTFLOW;
-        I.tiles_x = (s->pb.nx + 1 + tx - 1) / tx;
-        const int tiles_y = (s->pb.ny + 1 + ty - 1) / ty;
-        I.tile0 = (int)tiles.size();
-        tiles.insert(tiles.end(), (size_t)I.tiles_x * tiles_y, (int)q);
+        host[q] = inst_of(s, tx, (int)tiles.size());
+        tiles.insert(tiles.end(), (size_t)tiles_of(s, tx, ty), (int)q);
     }
     if (!b->d_inst)
         BCUDA_TRY(b, cudaMalloc(&b->d_inst, host.size() * sizeof(Inst)));
@@ -943,7 +963,7 @@ sim_status plan_tiles(sim_batch_t b, int tx, int ty, int grid)
     BCUDA_TRY(b, cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
     b->plan = BatchPlan{b->d_inst, b->d_tiles, (int)host.size(), (int)tiles.size(), tx, ty,
-                        grid > 0 ? std::min(grid, (int)tiles.size()) : (int)tiles.size()};
+                        grid > 0 ? std::min(grid, (int)tiles.size()) : (int)tiles.size(), host[0]};
     drop_graphs(b);
     return SIM_OK;
 }
@@ -953,18 +973,18 @@ int enqueue_batch_step(sim_batch_t b, int prev, bool implicit, bool tvd, cudaStr
 {
     const BatchPlan &bp = b->plan;
     if (!implicit) {
-        launch_batch_faces(bp, b->mixed, prev, tvd, st);
-        launch_batch_explicit(bp, b->mixed, prev, tvd, st);
+        launch_faces(bp, b->mixed, prev, tvd, st);
+        launch_explicit(bp, b->mixed, prev, tvd, st);
     }
     int old = prev;
     for (int it = 1; it <= b->iters; it++) {
         int nw = (old + 1) % 3;
         if (nw == prev) nw = (nw + 1) % 3;
-        launch_batch_zero_res(bp, st);
-        launch_batch_faces(bp, b->mixed, old, tvd, st);
-        launch_batch_assemble(bp, b->mixed, prev, old, nw, implicit, tvd, st);
-        launch_batch_pressure(bp, b->mixed, prev, old, nw, st);
-        launch_batch_velocity(bp, b->mixed, old, nw, st);
+        launch_zero_res(bp, st);
+        launch_faces(bp, b->mixed, old, tvd, st);
+        launch_assemble(bp, b->mixed, prev, old, nw, implicit, tvd, st);
+        launch_pressure(bp, b->mixed, prev, old, nw, st);
+        launch_velocity(bp, b->mixed, old, nw, st);
         if (b->ghosts)
             for (sim_t s : b->inst)
                 if (ghost_kernels(s->sides, true)) {

@@ -29,6 +29,8 @@ enum : uint32_t {
     F_TUY = 1u << 9,      // u faces j-2..j+1 of column i are unknowns
     F_TVX = 1u << 10,     // v faces i-2..i+1 of row j are unknowns
     F_TVY = 1u << 11,     // v faces j-2..j+1 of column i are unknowns
+    F_INTERIOR = 1u << 12, // no wall within two cells of any position of the aligned 32-wide
+                           // row segment holding (i,j): cells [32k-2, 32k+33] x [j-2, j+2] are fluid
 };
 
 // Per-index grid factors, each array indexed by i + G (x) or j + G (y) over
@@ -65,6 +67,8 @@ struct LevelT {
 template <typename R>
 struct WorkT {
     R *rho_u, *rho_v;              // face densities (Eqs. pl10, pl11)
+    R *Fx, *Fy;                    // mass fluxes F^x = rho^u u dy, F^y = rho^v v dx (Eqs. pl8, pl9)
+    R *hx, *hy;                    // harmonic-mean Gamma^lambda at x and y faces (Eq. pl33)
     R *uhat, *du, *vhat, *dv;      // pseudo velocities and d (Eqs. pl14, pl20, pl21)
     R *uexp, *vexp, *Texp;         // explicit convective terms (Eqs. pl15_11, pl31_1)
 };
@@ -88,7 +92,7 @@ struct Mixed {
     WorkT<float> w;
 };
 
-// One problem of a batch, as the batched kernels see it (device resident).
+// One problem of a tile list, as the equation kernels see it (device resident).
 struct Inst {
     Geo g;
     Coef k;
@@ -103,13 +107,14 @@ struct Inst {
     int tile0;            // index of this problem's first tile in the batch
 };
 
-// Work distribution of the batched kernels: tiles of tx x ty threads
-// (tx * ty = 256) over every problem, walked by `grid` resident CTAs.
+// Work distribution of the equation kernels: tiles of tx x ty threads
+// (tx * ty = 256) over every problem of the list, walked by `grid` CTAs.
 struct BatchPlan {
     const Inst *inst;
     const int *tile_inst; // problem of each tile
     int n_inst, n_tiles;
     int tx, ty, grid;
+    Inst one;             // copy of inst[0], read from the launch parameters when n_inst == 1
 };
 
 // Boundary description used by the ghost refresh.
@@ -121,40 +126,28 @@ enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
 enum { BC_WALL = 0, BC_SYMMETRY = 1, BC_INFLOW = 2, BC_OUTFLOW = 3 };
 
 // Launch wrappers (sweep_kernels.cu).  All are asynchronous on `stream`.
-void launch_face_densities(const Geo &g, const Level &lv, const Work &w, bool tvd, void *stream);
-void launch_explicit_terms(const Geo &g, const Level &prev, const Work &w, bool tvd, void *stream);
-void launch_assemble(const Geo &g, const Coef &c, const Level &prev, const Level &old,
-                     const Level &nw, const Work &w, bool implicit, bool tvd, void *stream);
-void launch_pressure(const Geo &g, const Coef &c, const Level &prev, const Level &old,
-                     const Level &nw, const Work &w, void *stream);
-void launch_velocity(const Geo &g, const Sides &s, const Level &old, const Level &nw, const Work &w, void *stream);
+//
+// Equation kernels: one launch per phase over a tile list (one problem or a
+// batch).  `mixed` selects the FP32 assembly of the mixed-precision path;
+// levels are indices into Inst::lv / Inst::lv32.
+void launch_zero_res(const BatchPlan &bp, void *stream);
+void launch_faces(const BatchPlan &bp, bool mixed, int level, bool tvd, void *stream);
+void launch_explicit(const BatchPlan &bp, bool mixed, int prev, bool tvd, void *stream);
+void launch_assemble(const BatchPlan &bp, bool mixed, int prev, int old, int nw, bool implicit, bool tvd,
+                     void *stream);
+void launch_pressure(const BatchPlan &bp, bool mixed, int prev, int old, int nw, void *stream);
+void launch_velocity(const BatchPlan &bp, bool mixed, int old, int nw, void *stream);
+
 // Ghost copies of outflow and symmetry sides.  after_velocity: the velocity
 // kernel has already copied the outflow side, only symmetry sides remain.
 void launch_ghosts(const Geo &g, const Sides &s, const Level &lv, bool after_velocity, void *stream);
+void launch_ghosts_f32(const Mixed &m, const Sides &s, int level, bool after_velocity, void *stream);
 int ghost_kernels(const Sides &s, bool after_velocity);
+
+// State maintenance.
 void launch_derive(const Geo &g, const Coef &c, const Level &lv, void *stream);
 void launch_scatter(const Geo &g, int field, const double *src, const Level &lv, void *stream);
 void launch_gather(const Geo &g, int field, const Level &lv, double *dst, void *stream);
-
-// Mixed precision (FP32 assembly, FP64 pressure accumulation / EOS / residuals).
-void launch_face_densities_f32(const Mixed &m, int level, bool tvd, void *stream);
-void launch_explicit_terms_f32(const Mixed &m, int prev, bool tvd, void *stream);
-void launch_assemble_f32(const Mixed &m, int prev, int old, int nw, const Level &nw64, bool implicit, bool tvd,
-                         void *stream);
-void launch_pressure_mixed(const Geo &g, const Coef &c, const Mixed &m, const Level &prev, const Level &old,
-                           int old32, const Level &nw, int nw32, const Work &w, void *stream);
-void launch_velocity_mixed(const Geo &g, const Sides &s, const Mixed &m, int old32, const Level &nw, int nw32,
-                           const Work &w, void *stream);
-void launch_ghosts_f32(const Mixed &m, const Sides &s, int level, bool after_velocity, void *stream);
 void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, size_t nelem, void *stream);
-
-// Batched kernels: one launch per phase over every problem of a batch.
-void launch_batch_zero_res(const BatchPlan &bp, void *stream);
-void launch_batch_explicit(const BatchPlan &bp, bool mixed, int prev, bool tvd, void *stream);
-void launch_batch_faces(const BatchPlan &bp, bool mixed, int level, bool tvd, void *stream);
-void launch_batch_assemble(const BatchPlan &bp, bool mixed, int prev, int old, int nw, bool implicit, bool tvd,
-                           void *stream);
-void launch_batch_pressure(const BatchPlan &bp, bool mixed, int prev, int old, int nw, void *stream);
-void launch_batch_velocity(const BatchPlan &bp, bool mixed, int old, int nw, void *stream);
 
 }  // namespace stg

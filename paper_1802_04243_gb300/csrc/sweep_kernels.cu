@@ -5,14 +5,15 @@
 // pressure accumulation, equation of state and residuals stay FP64).
 //
 // One loop-2 iteration (Section 3.1, Figs. 1 and 2, GPU column) runs as
-//   k_face_densities   rho^u, rho^v of every face            (Eqs. pl8-pl11)
-//   k_assemble         T, u^/d^u, v^/d^v of every node         (Eqs. pl14-pl16, pl20, pl21, pl28-pl33)
-//   k_pressure         p, rho = p/T, Gamma = T^omega, |dp|, |dT| (Eqs. pl23, pl24, pl5)
-//   k_velocity         u, v from the new p, |du|, |dv|          (Eqs. pl18, pl19)
-//   k_ghost_*          outflow / symmetry ghost copies
-// and, once per step for the explicit scheme, k_explicit_terms (Eqs. pl15_11,
+//   k_faces      rho^u, rho^v, mass fluxes and conductivities of every face (Eqs. pl8-pl11, pl33)
+//   k_assemble   T, u^/d^u, v^/d^v of every node         (Eqs. pl14-pl16, pl20, pl21, pl28-pl33)
+//   k_pressure   p, rho = p/T, Gamma = T^omega, |dp|, |dT| (Eqs. pl23, pl24, pl5)
+//   k_velocity   u, v from the new p, |du|, |dv|          (Eqs. pl18, pl19)
+//   k_ghost_*    outflow / symmetry ghost copies
+// and, once per step for the explicit scheme, k_explicit (Eqs. pl15_11,
 // pl31_1 and the u mirror).  Each thread owns one grid position (i, j) and
-// the cell, the u face and the v face with that index.
+// the cell, the u face and the v face with that index; the equation kernels
+// walk a list of tiles of one or more problems.
 //
 // Boundary rules: wall ghost and obstacle cells hold the wall state; a
 // temperature or tangential velocity read across a wall is reflected about
@@ -72,12 +73,16 @@ __device__ __forceinline__ R pos(R x) { return fmax(R(0), x); }
 
 // Value of node m seen from node a: reflected about the stored wall value when
 // the flag of m carries `wall_bit`.
-template <typename R>
+template <typename R, bool WALLS = true>
 __device__ __forceinline__ R seen(const R *f, const uint16_t *flag, int a, int m, uint32_t wall_bit)
 {
     R fm = f[m];
-    return (flag[m] & wall_bit) ? R(2) * fm - f[a] : fm;
+    if constexpr (!WALLS)
+        return fm;                 // caller knows no wall is in reach
+    else
+        return (flag[m] & wall_bit) ? R(2) * fm - f[a] : fm;
 }
+
 
 // Gamma at the corner (x^f_i, y^f_j): bilinear in the four cell centres.
 template <typename R>
@@ -178,15 +183,34 @@ __device__ __forceinline__ void block_max2(unsigned long long a, unsigned long l
     __syncthreads();       // the shared slots are reused by the block's next call
 }
 
+// 1/a.  FP64: Newton-Raphson reciprocal iteration r <- r (2 - a r) (two
+// steps, written as fused multiply-adds) from the FP32 reciprocal of a; it
+// replaces the longer IEEE division sequence on GB300's slow FP64 pipe and
+// is within a few ulp of 1/a.  Magnitudes outside [2^-100, 2^100] fall back
+// to the IEEE division.  FP32: the IEEE division.
+__device__ __forceinline__ float recip(float a) { return 1.0f / a; }
+__device__ __forceinline__ double recip(double a)
+{
+    const unsigned e = ((unsigned)__double2hiint(a) >> 20) & 0x7FFu;
+    if (e < 1023u - 100u || e > 1023u + 100u)
+        return 1.0 / a;
+    double r = widen(1.0f / narrow(a));
+    r = fma(r, fma(-a, r, 1.0), r);
+    r = fma(r, fma(-a, r, 1.0), r);
+    return r;
+}
+
 // ------------------------------------------------------- face densities
 
 // rho^u at u face (i,j) and rho^v at v face (i,j), Eqs. pl10, pl11, written as
 // the upwind value plus psi_s times the difference across the face.
 template <typename R, bool TVD>
 __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const R *__restrict__ u, const R *__restrict__ v,
-                                                    const R *__restrict__ rho, R *__restrict__ rho_u,
-                                                    R *__restrict__ rho_v, int i, int j)
+                                                    const R *__restrict__ rho, const R *__restrict__ gam,
+                                                    const WorkT<R> &w, int i, int j)
 {
+    R *__restrict__ rho_u = w.rho_u;
+    R *__restrict__ rho_v = w.rho_v;
     const int P = g.pitch;
     const int c = Ix{P}(i, j);
     if (i <= g.nx && j < g.ny) {
@@ -196,6 +220,8 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const R *_
             val += psi_surface(rho[c - 2], rl, rr, rho[c + 1], at(g.x.d, i - 2), at(g.x.d, i - 1),
                                at(g.x.d, i), at(g.x.d, i + 1), vel) * (rr - rl);
         rho_u[c] = val;
+        w.Fx[c] = val * vel * at(g.y.d, j);
+        w.hx[c] = harmonic(gam[c - 1], gam[c], at(g.x.d, i - 1), at(g.x.d, i));
     }
     if (i < g.nx && j <= g.ny) {
         const R vel = v[c], rb = rho[c - P], rt = rho[c];
@@ -204,24 +230,16 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const R *_
             val += psi_surface(rho[c - 2 * P], rb, rt, rho[c + P], at(g.y.d, j - 2), at(g.y.d, j - 1),
                                at(g.y.d, j), at(g.y.d, j + 1), vel) * (rt - rb);
         rho_v[c] = val;
+        w.Fy[c] = val * vel * at(g.x.d, i);
+        w.hy[c] = harmonic(gam[c - P], gam[c], at(g.y.d, j - 1), at(g.y.d, j));
     }
-}
-
-template <typename R, bool TVD>
-__global__ void __launch_bounds__(BX *BY) k_face_densities(GeoT<R> g, const R *__restrict__ u, const R *__restrict__ v,
-                                                            const R *__restrict__ rho, R *__restrict__ rho_u,
-                                                            R *__restrict__ rho_v)
-{
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    face_densities_body<R, TVD>(g, u, v, rho, rho_u, rho_v, i, j);
 }
 
 // ------------------------------------------------------- explicit terms
 
 // T^explicit of cell (i,j), Eq. pl31_1, all inputs at level n-1.
 template <typename R, bool TVD>
-__device__ R explicit_T(const GeoT<R> &g, const LevelT<R> &L, const R *rho_u, const R *rho_v,
-                             int c, int i, int j)
+__device__ R explicit_T(const GeoT<R> &g, const LevelT<R> &L, const R *Fx, const R *Fy, int c, int i, int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
@@ -231,8 +249,7 @@ __device__ R explicit_T(const GeoT<R> &g, const LevelT<R> &L, const R *rho_u, co
     const R Tw = seen(T, fl, c, c - 1, F_WALL), Te = seen(T, fl, c, c + 1, F_WALL);
     const R Ts = seen(T, fl, c, c - P, F_WALL), Tn = seen(T, fl, c, c + P, F_WALL);
     const R uw = L.u[c], ue = L.u[c + 1], vs = L.v[c], vn = L.v[c + P];
-    const R Fw = rho_u[c] * uw * dyj, Fe = rho_u[c + 1] * ue * dyj;
-    const R Fs = rho_v[c] * vs * dxi, Fn = rho_v[c + P] * vn * dxi;
+    const R Fw = Fx[c], Fe = Fx[c + 1], Fs = Fy[c], Fn = Fy[c + P];
     R pw = 0.0, pe = 0.0, ps = 0.0, pn = 0.0;
     if (TVD) {
         if (fl[c + 1] & F_TCX)
@@ -250,7 +267,7 @@ __device__ R explicit_T(const GeoT<R> &g, const LevelT<R> &L, const R *rho_u, co
 
 // v^explicit of v face (i,j), Eq. pl15_11, level n-1.
 template <typename R, bool TVD>
-__device__ R explicit_v(const GeoT<R> &g, const LevelT<R> &L, const R *rho_u, int b, int i, int j)
+__device__ R explicit_v(const GeoT<R> &g, const LevelT<R> &L, const R *Fx, int b, int i, int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
@@ -259,8 +276,7 @@ __device__ R explicit_v(const GeoT<R> &g, const LevelT<R> &L, const R *rho_u, in
     const R vP = v[b], vW = seen(v, fl, b, b - 1, F_VWALL), vE = seen(v, fl, b, b + 1, F_VWALL);
     const R vS = v[b - P], vN = v[b + P];
     const R uw1 = u[b - P], uw2 = u[b], ue1 = u[b + 1 - P], ue2 = u[b + 1];
-    const R Fw1 = rho_u[b - P] * uw1 * dys, Fw2 = rho_u[b] * uw2 * dyp;
-    const R Fe1 = rho_u[b + 1 - P] * ue1 * dys, Fe2 = rho_u[b + 1] * ue2 * dyp;
+    const R Fw1 = Fx[b - P], Fw2 = Fx[b], Fe1 = Fx[b + 1 - P], Fe2 = Fx[b + 1];
     const R vbs = R(0.5) * (vS + vP), vbn = R(0.5) * (vP + vN);
     R pw1 = 0, pw2 = 0, pe1 = 0, pe2 = 0, ps = 0, pn = 0;
     if (TVD) {
@@ -289,7 +305,7 @@ __device__ R explicit_v(const GeoT<R> &g, const LevelT<R> &L, const R *rho_u, in
 
 // u^explicit of u face (i,j): the mirror image of Eq. pl15_11, level n-1.
 template <typename R, bool TVD>
-__device__ R explicit_u(const GeoT<R> &g, const LevelT<R> &L, const R *rho_v, int a, int i, int j)
+__device__ R explicit_u(const GeoT<R> &g, const LevelT<R> &L, const R *Fy, int a, int i, int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
@@ -298,8 +314,7 @@ __device__ R explicit_u(const GeoT<R> &g, const LevelT<R> &L, const R *rho_v, in
     const R uP = u[a], uS = seen(u, fl, a, a - P, F_UWALL), uN = seen(u, fl, a, a + P, F_UWALL);
     const R uW = u[a - 1], uE = u[a + 1];
     const R vs1 = v[a - 1], vs2 = v[a], vn1 = v[a - 1 + P], vn2 = v[a + P];
-    const R Fs1 = rho_v[a - 1] * vs1 * dxw, Fs2 = rho_v[a] * vs2 * dxp;
-    const R Fn1 = rho_v[a - 1 + P] * vn1 * dxw, Fn2 = rho_v[a + P] * vn2 * dxp;
+    const R Fs1 = Fy[a - 1], Fs2 = Fy[a], Fn1 = Fy[a - 1 + P], Fn2 = Fy[a + P];
     const R ubw = R(0.5) * (uW + uP), ube = R(0.5) * (uP + uE);
     R pn1 = 0, pn2 = 0, ps1 = 0, ps2 = 0, pe = 0, pw = 0;
     if (TVD) {
@@ -334,18 +349,11 @@ __device__ __forceinline__ void explicit_terms_body(const GeoT<R> &g, const Leve
     if (i > g.nx || j > g.ny) return;
     const uint16_t f = g.flag[c];
     if (i < g.nx && j < g.ny)
-        w.Texp[c] = (f & F_FLUID) ? explicit_T<R, TVD>(g, prev, w.rho_u, w.rho_v, c, i, j) : R(0);
+        w.Texp[c] = (f & F_FLUID) ? explicit_T<R, TVD>(g, prev, w.Fx, w.Fy, c, i, j) : R(0);
     if (j < g.ny)
-        w.uexp[c] = (f & F_UACT) ? explicit_u<R, TVD>(g, prev, w.rho_v, c, i, j) : R(0);
+        w.uexp[c] = (f & F_UACT) ? explicit_u<R, TVD>(g, prev, w.Fy, c, i, j) : R(0);
     if (i < g.nx)
-        w.vexp[c] = (f & F_VACT) ? explicit_v<R, TVD>(g, prev, w.rho_u, c, i, j) : R(0);
-}
-
-template <typename R, bool TVD>
-__global__ void __launch_bounds__(BX *BY) k_explicit_terms(GeoT<R> g, LevelT<R> prev, WorkT<R> w)
-{
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    explicit_terms_body<R, TVD>(g, prev, w, i, j);
+        w.vexp[c] = (f & F_VACT) ? explicit_v<R, TVD>(g, prev, w.Fx, c, i, j) : R(0);
 }
 
 // ------------------------------------------------------------ temperature
@@ -353,7 +361,7 @@ __global__ void __launch_bounds__(BX *BY) k_explicit_terms(GeoT<R> g, LevelT<R> 
 // Energy source S^T_c of cell (i,j), Eq. pl29 with S^T_p = 0 (Eq. pl28):
 // viscous dissipation (Eq. pl7) and pressure work; velocities off their
 // nodes are bilinear interpolations, reflected across walls.
-template <typename R>
+template <typename R, bool WALLS>
 __device__ R energy_source(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, int c, int i, int j)
 {
     const int P = g.pitch;
@@ -366,15 +374,15 @@ __device__ R energy_source(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> 
     const R xl0 = at(g.x.wlo, i), xh0 = at(g.x.whi, i), xl1 = at(g.x.wlo, i + 1), xh1 = at(g.x.whi, i + 1);
     const R yl0 = at(g.y.wlo, j), yh0 = at(g.y.whi, j), yl1 = at(g.y.wlo, j + 1), yh1 = at(g.y.whi, j + 1);
     // v at (x^f_i, y^v_j) and (x^f_{i+1}, y^v_j)
-    const R v_w = R(0.5) * ((xl0 * seen(v, fl, c, c - 1, F_VWALL) + xh0 * v[c])
-                              + (xl0 * seen(v, fl, c + P, c + P - 1, F_VWALL) + xh0 * v[c + P]));
-    const R v_e = R(0.5) * ((xl1 * v[c] + xh1 * seen(v, fl, c, c + 1, F_VWALL))
-                              + (xl1 * v[c + P] + xh1 * seen(v, fl, c + P, c + P + 1, F_VWALL)));
+    const R v_w = R(0.5) * ((xl0 * seen<R, WALLS>(v, fl, c, c - 1, F_VWALL) + xh0 * v[c])
+                              + (xl0 * seen<R, WALLS>(v, fl, c + P, c + P - 1, F_VWALL) + xh0 * v[c + P]));
+    const R v_e = R(0.5) * ((xl1 * v[c] + xh1 * seen<R, WALLS>(v, fl, c, c + 1, F_VWALL))
+                              + (xl1 * v[c + P] + xh1 * seen<R, WALLS>(v, fl, c + P, c + P + 1, F_VWALL)));
     // u at (x^v_i, y^f_j) and (x^v_i, y^f_{j+1})
-    const R u_s = R(0.5) * ((yl0 * seen(u, fl, c, c - P, F_UWALL) + yh0 * u[c])
-                              + (yl0 * seen(u, fl, c + 1, c + 1 - P, F_UWALL) + yh0 * u[c + 1]));
-    const R u_n = R(0.5) * ((yl1 * u[c] + yh1 * seen(u, fl, c, c + P, F_UWALL))
-                              + (yl1 * u[c + 1] + yh1 * seen(u, fl, c + 1, c + 1 + P, F_UWALL)));
+    const R u_s = R(0.5) * ((yl0 * seen<R, WALLS>(u, fl, c, c - P, F_UWALL) + yh0 * u[c])
+                              + (yl0 * seen<R, WALLS>(u, fl, c + 1, c + 1 - P, F_UWALL) + yh0 * u[c + 1]));
+    const R u_n = R(0.5) * ((yl1 * u[c] + yh1 * seen<R, WALLS>(u, fl, c, c + P, F_UWALL))
+                              + (yl1 * u[c + 1] + yh1 * seen<R, WALLS>(u, fl, c + 1, c + 1 + P, F_UWALL)));
     const R dvdx = (v_e - v_w) * rdx, dudy = (u_n - u_s) * rdy;
     const R div = dudx + dvdy, shear = dvdx + dudy;
     const R phi = R(2) * (dudx * dudx + dvdy * dvdy) + shear * shear - R(2.0 / 3.0) * div * div;
@@ -385,26 +393,24 @@ __device__ R energy_source(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> 
 // New temperature of fluid cell (i,j): Eq. pl30 with the implicit
 // coefficients of Eq. pl31 or the explicit ones of Eq. pl31_1, conductances
 // Eq. pl32 with the harmonic mean Eq. pl33.
-template <typename R, bool IMPL, bool TVD>
+template <typename R, bool IMPL, bool TVD, bool WALLS>
 __device__ R temperature(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev, const LevelT<R> &old,
                          const WorkT<R> &w, int c, int i, int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
-    const R *T = old.T, *gam = old.gam;
+    const R *T = old.T;
     const R dxi = at(g.x.d, i), dyj = at(g.y.d, j);
     const R dxw = at(g.x.d, i - 1), dxe = at(g.x.d, i + 1), dys = at(g.y.d, j - 1), dyn = at(g.y.d, j + 1);
     const R Tp = T[c];
-    const R Tw = seen(T, fl, c, c - 1, F_WALL), Te = seen(T, fl, c, c + 1, F_WALL);
-    const R Ts = seen(T, fl, c, c - P, F_WALL), Tn = seen(T, fl, c, c + P, F_WALL);
+    const R Tw = seen<R, WALLS>(T, fl, c, c - 1, F_WALL), Te = seen<R, WALLS>(T, fl, c, c + 1, F_WALL);
+    const R Ts = seen<R, WALLS>(T, fl, c, c - P, F_WALL), Tn = seen<R, WALLS>(T, fl, c, c + P, F_WALL);
     const R uw = old.u[c], ue = old.u[c + 1], vs = old.v[c], vn = old.v[c + P];
-    const R Fw = w.rho_u[c] * uw * dyj, Fe = w.rho_u[c + 1] * ue * dyj;
-    const R Fs = w.rho_v[c] * vs * dxi, Fn = w.rho_v[c + P] * vn * dxi;
-    const R gp = gam[c];
-    const R Dw = k.CT1f * harmonic(gam[c - 1], gp, dxw, dxi) * dyj * at(g.x.rc, i);
-    const R De = k.CT1f * harmonic(gp, gam[c + 1], dxi, dxe) * dyj * at(g.x.rc, i + 1);
-    const R Ds = k.CT1f * harmonic(gam[c - P], gp, dys, dyj) * dxi * at(g.y.rc, j);
-    const R Dn = k.CT1f * harmonic(gp, gam[c + P], dyj, dyn) * dxi * at(g.y.rc, j + 1);
+    const R Fw = w.Fx[c], Fe = w.Fx[c + 1], Fs = w.Fy[c], Fn = w.Fy[c + P];
+    const R Dw = k.CT1f * w.hx[c] * dyj * at(g.x.rc, i);
+    const R De = k.CT1f * w.hx[c + 1] * dyj * at(g.x.rc, i + 1);
+    const R Ds = k.CT1f * w.hy[c] * dxi * at(g.y.rc, j);
+    const R Dn = k.CT1f * w.hy[c + P] * dxi * at(g.y.rc, j + 1);
     const R vol = dxi * dyj;
     R a1, a2, a3, a4, a0, texp;
     if (IMPL) {
@@ -430,16 +436,16 @@ __device__ R temperature(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
         a0 = k.dt * (a1 + a2 + a3 + a4) + old.rho[c] * vol;
         texp = w.Texp[c];
     }
-    const R sc = energy_source(g, k, old, c, i, j);
+    const R sc = energy_source<R, WALLS>(g, k, old, c, i, j);
     const R rhs = k.dt * (a1 * Tw + a2 * Te + a3 * Ts + a4 * Tn + sc + texp) + prev.rho[c] * prev.T[c] * vol;
-    return rhs / a0;
+    return rhs * recip(a0);
 }
 
 // ------------------------------------------------------ pseudo velocities
 
 // u^ and d^u of u face (i,j) between fluid cells: the mirror image of
 // Eqs. pl14-pl16 and pl20 (the 4/3 normal-stress factor on the x direction).
-template <typename R, bool IMPL, bool TVD>
+template <typename R, bool IMPL, bool TVD, bool WALLS>
 __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev, const LevelT<R> &old,
                          const WorkT<R> &w, int a, int i, int j, R &uhat, R &du)
 {
@@ -448,13 +454,12 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     const R *u = old.u, *v = old.v, *gam = old.gam, *rho = old.rho;
     const R dxw = at(g.x.d, i - 1), dxp = at(g.x.d, i), dyj = at(g.y.d, j);
     const R uP = u[a];
-    const R uW = seen(u, fl, a, a - 1, F_UWALL), uE = seen(u, fl, a, a + 1, F_UWALL);
-    const R uS = seen(u, fl, a, a - P, F_UWALL), uN = seen(u, fl, a, a + P, F_UWALL);
+    const R uW = seen<R, WALLS>(u, fl, a, a - 1, F_UWALL), uE = seen<R, WALLS>(u, fl, a, a + 1, F_UWALL);
+    const R uS = seen<R, WALLS>(u, fl, a, a - P, F_UWALL), uN = seen<R, WALLS>(u, fl, a, a + P, F_UWALL);
     const R ubw = R(0.5) * (uW + uP), ube = R(0.5) * (uP + uE);
     const R Fbw = ubw * rho[a - 1] * dyj, Fbe = ube * rho[a] * dyj;
     const R vs1 = v[a - 1], vs2 = v[a], vn1 = v[a - 1 + P], vn2 = v[a + P];
-    const R Fs1 = w.rho_v[a - 1] * vs1 * dxw, Fs2 = w.rho_v[a] * vs2 * dxp;
-    const R Fn1 = w.rho_v[a - 1 + P] * vn1 * dxw, Fn2 = w.rho_v[a + P] * vn2 * dxp;
+    const R Fs1 = w.Fy[a - 1], Fs2 = w.Fy[a], Fn1 = w.Fy[a - 1 + P], Fn2 = w.Fy[a + P];
     const R gcs = gamma_corner(g, gam, a, i, j), gcn = gamma_corner(g, gam, a + P, i, j + 1);
     const R Dxw = k.B * gam[a - 1] * dyj * at(g.x.rd, i - 1);
     const R Dxe = k.B * gam[a] * dyj * at(g.x.rd, i);
@@ -499,14 +504,14 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
         a0 = a1 + a2 + a3 + a4 + trans;
         uexp = w.uexp[a];
     }
-    const R r = R(1) / a0;
+    const R r = recip(a0);
     uhat = (a1 * uW + a2 * uE + a3 * uS + a4 * uN + b + uexp) * r;
     du = k.A * dyj * r;
 }
 
 // v^ and d^v of v face (i,j) between fluid cells, Eqs. pl14-pl16, pl21
 // (implicit, Eq. pl15; explicit, Eq. pl15_11).
-template <typename R, bool IMPL, bool TVD>
+template <typename R, bool IMPL, bool TVD, bool WALLS>
 __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev, const LevelT<R> &old,
                          const WorkT<R> &w, int b, int i, int j, R &vhat, R &dv)
 {
@@ -515,13 +520,12 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     const R *u = old.u, *v = old.v, *gam = old.gam, *rho = old.rho;
     const R dys = at(g.y.d, j - 1), dyp = at(g.y.d, j), dxi = at(g.x.d, i);
     const R vP = v[b];
-    const R vW = seen(v, fl, b, b - 1, F_VWALL), vE = seen(v, fl, b, b + 1, F_VWALL);
-    const R vS = seen(v, fl, b, b - P, F_VWALL), vN = seen(v, fl, b, b + P, F_VWALL);
+    const R vW = seen<R, WALLS>(v, fl, b, b - 1, F_VWALL), vE = seen<R, WALLS>(v, fl, b, b + 1, F_VWALL);
+    const R vS = seen<R, WALLS>(v, fl, b, b - P, F_VWALL), vN = seen<R, WALLS>(v, fl, b, b + P, F_VWALL);
     const R vbs = R(0.5) * (vS + vP), vbn = R(0.5) * (vP + vN);
     const R Fbs = vbs * rho[b - P] * dxi, Fbn = vbn * rho[b] * dxi;
     const R uw1 = u[b - P], uw2 = u[b], ue1 = u[b + 1 - P], ue2 = u[b + 1];
-    const R Fw1 = w.rho_u[b - P] * uw1 * dys, Fw2 = w.rho_u[b] * uw2 * dyp;
-    const R Fe1 = w.rho_u[b + 1 - P] * ue1 * dys, Fe2 = w.rho_u[b + 1] * ue2 * dyp;
+    const R Fw1 = w.Fx[b - P], Fw2 = w.Fx[b], Fe1 = w.Fx[b + 1 - P], Fe2 = w.Fx[b + 1];
     const R gcw = gamma_corner(g, gam, b, i, j), gce = gamma_corner(g, gam, b + 1, i + 1, j);
     const R hsum = dyp + dys;
     const R Dxw = k.B * gcw * hsum * (R(0.5) * at(g.x.rc, i));
@@ -566,9 +570,40 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
         a0 = a1 + a2 + a3 + a4 + trans;
         vexp = w.vexp[b];
     }
-    const R r = R(1) / a0;
+    const R r = recip(a0);
     vhat = (a1 * vW + a2 * vE + a3 * vS + a4 * vN + bsrc + vexp) * r;
     dv = k.A * dxi * r;
+}
+
+template <typename R, bool IMPL, bool TVD, bool WALLS>
+__device__ __forceinline__ void assemble_at(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev,
+                                            const LevelT<R> &old, double *__restrict__ T_out,
+                                            float *__restrict__ T32_out, const WorkT<R> &w, int c, uint16_t f,
+                                            int i, int j)
+{
+    if (i < g.nx && j < g.ny && (f & F_FLUID)) {
+        const R Tn = temperature<R, IMPL, TVD, WALLS>(g, k, prev, old, w, c, i, j);
+        if constexpr (sizeof(R) == 4) {
+            T_out[c] = widen(Tn);
+            T32_out[c] = Tn;
+        } else {
+            T_out[c] = Tn;
+        }
+    }
+    if (j < g.ny) {
+        R uh = old.u[c], d = R(0);            // faces that are not unknowns: stored u, d = 0
+        if (f & F_UACT)
+            pseudo_u<R, IMPL, TVD, WALLS>(g, k, prev, old, w, c, i, j, uh, d);
+        w.uhat[c] = uh;
+        w.du[c] = d;
+    }
+    if (i < g.nx) {
+        R vh = old.v[c], d = R(0);
+        if (f & F_VACT)
+            pseudo_v<R, IMPL, TVD, WALLS>(g, k, prev, old, w, c, i, j, vh, d);
+        w.vhat[c] = vh;
+        w.dv[c] = d;
+    }
 }
 
 // One thread per position: T of the cell, u^/d^u of the u face, v^/d^v of
@@ -582,38 +617,14 @@ __device__ __forceinline__ void assemble_body(const GeoT<R> &g, const CoefT<R> &
     if (i > g.nx || j > g.ny) return;
     const int c = Ix{g.pitch}(i, j);
     const uint16_t f = g.flag[c];
-    if (i < g.nx && j < g.ny && (f & F_FLUID)) {
-        const R Tn = temperature<R, IMPL, TVD>(g, k, prev, old, w, c, i, j);
-        if constexpr (sizeof(R) == 4) {
-            T_out[c] = widen(Tn);
-            T32_out[c] = Tn;
-        } else {
-            T_out[c] = Tn;
-        }
-    }
-    if (j < g.ny) {
-        R uh = old.u[c], d = R(0);            // faces that are not unknowns: stored u, d = 0
-        if (f & F_UACT)
-            pseudo_u<R, IMPL, TVD>(g, k, prev, old, w, c, i, j, uh, d);
-        w.uhat[c] = uh;
-        w.du[c] = d;
-    }
-    if (i < g.nx) {
-        R vh = old.v[c], d = R(0);
-        if (f & F_VACT)
-            pseudo_v<R, IMPL, TVD>(g, k, prev, old, w, c, i, j, vh, d);
-        w.vhat[c] = vh;
-        w.dv[c] = d;
-    }
-}
-
-template <typename R, bool IMPL, bool TVD>
-__global__ void __launch_bounds__(BX *BY) k_assemble(GeoT<R> g, CoefT<R> k, LevelT<R> prev, LevelT<R> old,
-                                                      double *__restrict__ T_out, float *__restrict__ T32_out,
-                                                      WorkT<R> w)
-{
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    assemble_body<R, IMPL, TVD>(g, k, prev, old, T_out, T32_out, w, i, j);
+    // Positions of wall-free 32-wide row segments take the variant without
+    // wall reflections (fewer instructions).  The choice depends on the
+    // position only, never on how threads form warps, so every tiling gives
+    // the same bits; with 32-wide tiles it is uniform across each warp.
+    if (f & F_INTERIOR)
+        assemble_at<R, IMPL, TVD, false>(g, k, prev, old, T_out, T32_out, w, c, f, i, j);
+    else
+        assemble_at<R, IMPL, TVD, true>(g, k, prev, old, T_out, T32_out, w, c, f, i, j);
 }
 
 // ---------------------------------------------------------------- pressure
@@ -648,12 +659,6 @@ __device__ __forceinline__ void pressure_body(const Geo &g, const Coef &k, const
         }
     }
     block_max2(rp, rT, &w.res[2], &w.res[3]);
-}
-
-__global__ void __launch_bounds__(BX *BY) k_pressure(Geo g, Coef k, Level prev, Level old, Level nw, Work w)
-{
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    pressure_body(g, k, prev, old, nw, w, i, j);
 }
 
 // -------------------------------------------------------------- velocity
@@ -704,12 +709,6 @@ __device__ __forceinline__ void velocity_body(const Geo &g, const Level &old, co
             outflow_copy(j, g.ny, c, nw);
     }
     block_max2(ru, rv, &w.res[0], &w.res[1]);
-}
-
-__global__ void __launch_bounds__(BX *BY) k_velocity(Geo g, Level old, Level nw, Work w, int east_outflow)
-{
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    velocity_body(g, old, nw, w, east_outflow, i, j);
 }
 
 // ------------------------------------------------------------ ghost copies
@@ -862,15 +861,6 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
     block_max2(rp, rT, &res[2], &res[3]);
 }
 
-__global__ void __launch_bounds__(BX *BY) k_pressure_mixed(Geo g, Coef k, GeoT<float> g32, CoefT<float> k32,
-                                                            Level prev, Level old, Level nw, LevelT<float> old32,
-                                                            LevelT<float> nw32, WorkT<float> w,
-                                                            unsigned long long *res)
-{
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    pressure_mixed_body(g, k, g32, k32, prev, old, nw, old32, nw32, w, res, i, j);
-}
-
 // Mixed precision, Eqs. pl18, pl19: FP32 correction of the FP32 pseudo
 // velocities by the FP64 pressure difference.  u and v carry FP32 values in
 // this path: their residual differences are formed in FP32 and reduced as
@@ -904,13 +894,6 @@ __device__ __forceinline__ void velocity_mixed_body(const Geo &g, const Level &n
     block_max2(ru, rv, &res[0], &res[1]);
 }
 
-__global__ void __launch_bounds__(BX *BY) k_velocity_mixed(Geo g, Level nw, LevelT<float> old32, LevelT<float> nw32,
-                                                            WorkT<float> w, unsigned long long *res, int east_outflow)
-{
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    velocity_mixed_body(g, nw, old32, nw32, w, res, east_outflow, i, j);
-}
-
 // FP32 shadow copy of a whole FP64 level (every element, ghosts included).
 __global__ void k_shadow(Level L, LevelT<float> S, size_t n)
 {
@@ -925,15 +908,38 @@ __global__ void k_shadow(Level L, LevelT<float> S, size_t n)
 }
 
 
-// ------------------------------------------------------------ batched kernels
+// ------------------------------------------------------- tile-list kernels
 
-// Walk the tiles of every problem of a batch with the resident CTAs; each
-// tile is tx x ty threads of one problem.
+// The equation kernels walk a tile list (BatchPlan): the tiles of one or
+// more problems, each tile tx x ty threads of one problem, taken by the
+// resident CTAs in turn.  A single problem is a list of one; every caller
+// runs these same kernels, so a problem's arithmetic does not depend on what
+// else shares the launch or on the tile shape.
+// The descriptor of the tile's problem is staged in shared memory: from the
+// launch parameters when the list holds one problem, else from the device
+// array.  Every kernel body reads it from there, so one compiled body serves
+// both sources.
 template <typename F>
 __device__ __forceinline__ void for_tiles(const BatchPlan &bp, F &&f)
 {
+    static_assert(sizeof(Inst) % 8 == 0, "Inst is copied as 8-byte words");
+    constexpr int kWords = sizeof(Inst) / 8;
+    __shared__ __align__(16) Inst sI;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+    int have = -1;
     for (int t = blockIdx.x; t < bp.n_tiles; t += gridDim.x) {
-        const Inst &I = bp.inst[bp.tile_inst[t]];
+        const int q = bp.n_inst == 1 ? 0 : bp.tile_inst[t];
+        if (q != have) {
+            if (have >= 0) __syncthreads();           // the previous problem's tile is done
+            const unsigned long long *src = bp.n_inst == 1
+                                                ? reinterpret_cast<const unsigned long long *>(&bp.one)
+                                                : reinterpret_cast<const unsigned long long *>(bp.inst + q);
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(&sI);
+            for (int w = tid; w < kWords; w += nthr) dst[w] = src[w];
+            __syncthreads();
+            have = q;
+        }
+        const Inst &I = sI;
         const int lt = t - I.tile0;
         const int i = (lt % I.tiles_x) * bp.tx + threadIdx.x;
         const int j = (lt / I.tiles_x) * bp.ty + threadIdx.y;
@@ -941,28 +947,28 @@ __device__ __forceinline__ void for_tiles(const BatchPlan &bp, F &&f)
     }
 }
 
-__global__ void k_batch_zero_res(BatchPlan bp)
+__global__ void k_zero_res(BatchPlan bp)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q < bp.n_inst * 4) bp.inst[q >> 2].w.res[q & 3] = 0ull;
 }
 
 template <bool MIXED, bool TVD>
-__global__ void __launch_bounds__(256) k_batch_faces(BatchPlan bp, int level)
+__global__ void __launch_bounds__(256) k_faces(const __grid_constant__ BatchPlan bp, int level)
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
         if constexpr (MIXED) {
             const LevelT<float> &L = I.lv32[level];
-            face_densities_body<float, TVD>(I.g32, L.u, L.v, L.rho, I.w32.rho_u, I.w32.rho_v, i, j);
+            face_densities_body<float, TVD>(I.g32, L.u, L.v, L.rho, L.gam, I.w32, i, j);
         } else {
             const Level &L = I.lv[level];
-            face_densities_body<double, TVD>(I.g, L.u, L.v, L.rho, I.w.rho_u, I.w.rho_v, i, j);
+            face_densities_body<double, TVD>(I.g, L.u, L.v, L.rho, L.gam, I.w, i, j);
         }
     });
 }
 
 template <bool MIXED, bool TVD>
-__global__ void __launch_bounds__(256) k_batch_explicit(BatchPlan bp, int prev)
+__global__ void __launch_bounds__(256) k_explicit(const __grid_constant__ BatchPlan bp, int prev)
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
         if constexpr (MIXED)
@@ -973,7 +979,7 @@ __global__ void __launch_bounds__(256) k_batch_explicit(BatchPlan bp, int prev)
 }
 
 template <bool MIXED, bool IMPL, bool TVD>
-__global__ void __launch_bounds__(256) k_batch_assemble(BatchPlan bp, int prev, int old, int nw)
+__global__ void __launch_bounds__(256) k_assemble(const __grid_constant__ BatchPlan bp, int prev, int old, int nw)
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
         if constexpr (MIXED)
@@ -985,7 +991,7 @@ __global__ void __launch_bounds__(256) k_batch_assemble(BatchPlan bp, int prev, 
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(256) k_batch_pressure(BatchPlan bp, int prev, int old, int nw)
+__global__ void __launch_bounds__(256) k_pressure(const __grid_constant__ BatchPlan bp, int prev, int old, int nw)
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
         if constexpr (MIXED)
@@ -997,7 +1003,7 @@ __global__ void __launch_bounds__(256) k_batch_pressure(BatchPlan bp, int prev, 
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(256) k_batch_velocity(BatchPlan bp, int old, int nw)
+__global__ void __launch_bounds__(256) k_velocity(const __grid_constant__ BatchPlan bp, int old, int nw)
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
         if constexpr (MIXED)
@@ -1067,48 +1073,6 @@ dim3 grid_of(const GeoT<R> &g)
 
 // ------------------------------------------------------------- launchers
 
-void launch_face_densities(const Geo &g, const Level &lv, const Work &w, bool tvd, void *stream)
-{
-    cudaStream_t s = (cudaStream_t)stream;
-    if (tvd)
-        k_face_densities<double, true><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, lv.u, lv.v, lv.rho, w.rho_u, w.rho_v);
-    else
-        k_face_densities<double, false><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, lv.u, lv.v, lv.rho, w.rho_u, w.rho_v);
-}
-
-void launch_explicit_terms(const Geo &g, const Level &prev, const Work &w, bool tvd, void *stream)
-{
-    cudaStream_t s = (cudaStream_t)stream;
-    const WorkT<double> &wt = w;
-    if (tvd)
-        k_explicit_terms<double, true><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, prev, wt);
-    else
-        k_explicit_terms<double, false><<<grid_of(g), dim3(BX, BY), 0, s>>>(g, prev, wt);
-}
-
-void launch_assemble(const Geo &g, const Coef &c, const Level &prev, const Level &old, const Level &nw,
-                     const Work &w, bool implicit, bool tvd, void *stream)
-{
-    cudaStream_t s = (cudaStream_t)stream;
-    const dim3 gr = grid_of(g), bl(BX, BY);
-    const WorkT<double> &wt = w;
-    if (implicit && tvd) k_assemble<double, true, true><<<gr, bl, 0, s>>>(g, c, prev, old, nw.T, nullptr, wt);
-    else if (implicit) k_assemble<double, true, false><<<gr, bl, 0, s>>>(g, c, prev, old, nw.T, nullptr, wt);
-    else if (tvd) k_assemble<double, false, true><<<gr, bl, 0, s>>>(g, c, prev, old, nw.T, nullptr, wt);
-    else k_assemble<double, false, false><<<gr, bl, 0, s>>>(g, c, prev, old, nw.T, nullptr, wt);
-}
-
-void launch_pressure(const Geo &g, const Coef &c, const Level &prev, const Level &old, const Level &nw,
-                     const Work &w, void *stream)
-{
-    k_pressure<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, c, prev, old, nw, w);
-}
-
-void launch_velocity(const Geo &g, const Sides &sd, const Level &old, const Level &nw, const Work &w, void *stream)
-{
-    k_velocity<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, old, nw, w, sd.kind[SIDE_E] == BC_OUTFLOW);
-}
-
 int ghost_kernels(const Sides &sd, bool after_velocity)
 {
     const bool we = (!after_velocity && sd.kind[SIDE_E] == BC_OUTFLOW) || sd.kind[SIDE_E] == BC_SYMMETRY ||
@@ -1127,52 +1091,6 @@ void launch_ghosts(const Geo &g, const Sides &sd, const Level &lv, bool after_ve
         k_ghost_we<double><<<(g.ny + 1 + 127) / 128, 128, 0, s>>>(g, sd, lv);
     if (sn)
         k_ghost_sn<double><<<(g.nx + 2 * G + 1 + 127) / 128, 128, 0, s>>>(g, sd, lv);
-}
-
-void launch_face_densities_f32(const Mixed &m, int level, bool tvd, void *stream)
-{
-    cudaStream_t s = (cudaStream_t)stream;
-    const LevelT<float> &L = m.lv[level];
-    if (tvd)
-        k_face_densities<float, true><<<grid_of(m.g), dim3(BX, BY), 0, s>>>(m.g, L.u, L.v, L.rho, m.w.rho_u, m.w.rho_v);
-    else
-        k_face_densities<float, false><<<grid_of(m.g), dim3(BX, BY), 0, s>>>(m.g, L.u, L.v, L.rho, m.w.rho_u, m.w.rho_v);
-}
-
-void launch_explicit_terms_f32(const Mixed &m, int prev, bool tvd, void *stream)
-{
-    cudaStream_t s = (cudaStream_t)stream;
-    if (tvd)
-        k_explicit_terms<float, true><<<grid_of(m.g), dim3(BX, BY), 0, s>>>(m.g, m.lv[prev], m.w);
-    else
-        k_explicit_terms<float, false><<<grid_of(m.g), dim3(BX, BY), 0, s>>>(m.g, m.lv[prev], m.w);
-}
-
-void launch_assemble_f32(const Mixed &m, int prev, int old, int nw, const Level &nw64, bool implicit, bool tvd,
-                         void *stream)
-{
-    cudaStream_t s = (cudaStream_t)stream;
-    const dim3 gr = grid_of(m.g), bl(BX, BY);
-    const LevelT<float> &P = m.lv[prev], &O = m.lv[old];
-    float *T32 = m.lv[nw].T;
-    if (implicit && tvd) k_assemble<float, true, true><<<gr, bl, 0, s>>>(m.g, m.k, P, O, nw64.T, T32, m.w);
-    else if (implicit) k_assemble<float, true, false><<<gr, bl, 0, s>>>(m.g, m.k, P, O, nw64.T, T32, m.w);
-    else if (tvd) k_assemble<float, false, true><<<gr, bl, 0, s>>>(m.g, m.k, P, O, nw64.T, T32, m.w);
-    else k_assemble<float, false, false><<<gr, bl, 0, s>>>(m.g, m.k, P, O, nw64.T, T32, m.w);
-}
-
-void launch_pressure_mixed(const Geo &g, const Coef &c, const Mixed &m, const Level &prev, const Level &old,
-                           int old32, const Level &nw, int nw32, const Work &w, void *stream)
-{
-    k_pressure_mixed<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, c, m.g, m.k, prev, old, nw,
-                                                                             m.lv[old32], m.lv[nw32], m.w, w.res);
-}
-
-void launch_velocity_mixed(const Geo &g, const Sides &sd, const Mixed &m, int old32, const Level &nw, int nw32,
-                           const Work &w, void *stream)
-{
-    k_velocity_mixed<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, nw, m.lv[old32], m.lv[nw32], m.w,
-                                                                             w.res, sd.kind[SIDE_E] == BC_OUTFLOW);
 }
 
 void launch_ghosts_f32(const Mixed &m, const Sides &sd, int level, bool after_velocity, void *stream)
@@ -1209,67 +1127,63 @@ void launch_gather(const Geo &g, int field, const Level &lv, double *dst, void *
     k_gather<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, field, lv, dst);
 }
 
-}  // namespace stg
-
-namespace stg {
-
-void launch_batch_zero_res(const BatchPlan &bp, void *stream)
+void launch_zero_res(const BatchPlan &bp, void *stream)
 {
-    k_batch_zero_res<<<(bp.n_inst * 4 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(bp);
+    k_zero_res<<<(bp.n_inst * 4 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(bp);
 }
 
-void launch_batch_faces(const BatchPlan &bp, bool mixed, int level, bool tvd, void *stream)
+void launch_faces(const BatchPlan &bp, bool mixed, int level, bool tvd, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
     const dim3 bl(bp.tx, bp.ty);
-    if (mixed && tvd) k_batch_faces<true, true><<<bp.grid, bl, 0, s>>>(bp, level);
-    else if (mixed) k_batch_faces<true, false><<<bp.grid, bl, 0, s>>>(bp, level);
-    else if (tvd) k_batch_faces<false, true><<<bp.grid, bl, 0, s>>>(bp, level);
-    else k_batch_faces<false, false><<<bp.grid, bl, 0, s>>>(bp, level);
+    if (mixed && tvd) k_faces<true, true><<<bp.grid, bl, 0, s>>>(bp, level);
+    else if (mixed) k_faces<true, false><<<bp.grid, bl, 0, s>>>(bp, level);
+    else if (tvd) k_faces<false, true><<<bp.grid, bl, 0, s>>>(bp, level);
+    else k_faces<false, false><<<bp.grid, bl, 0, s>>>(bp, level);
 }
 
-void launch_batch_explicit(const BatchPlan &bp, bool mixed, int prev, bool tvd, void *stream)
+void launch_explicit(const BatchPlan &bp, bool mixed, int prev, bool tvd, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
     const dim3 bl(bp.tx, bp.ty);
-    if (mixed && tvd) k_batch_explicit<true, true><<<bp.grid, bl, 0, s>>>(bp, prev);
-    else if (mixed) k_batch_explicit<true, false><<<bp.grid, bl, 0, s>>>(bp, prev);
-    else if (tvd) k_batch_explicit<false, true><<<bp.grid, bl, 0, s>>>(bp, prev);
-    else k_batch_explicit<false, false><<<bp.grid, bl, 0, s>>>(bp, prev);
+    if (mixed && tvd) k_explicit<true, true><<<bp.grid, bl, 0, s>>>(bp, prev);
+    else if (mixed) k_explicit<true, false><<<bp.grid, bl, 0, s>>>(bp, prev);
+    else if (tvd) k_explicit<false, true><<<bp.grid, bl, 0, s>>>(bp, prev);
+    else k_explicit<false, false><<<bp.grid, bl, 0, s>>>(bp, prev);
 }
 
-void launch_batch_assemble(const BatchPlan &bp, bool mixed, int prev, int old, int nw, bool implicit, bool tvd,
+void launch_assemble(const BatchPlan &bp, bool mixed, int prev, int old, int nw, bool implicit, bool tvd,
                            void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
     const dim3 bl(bp.tx, bp.ty);
     const int code = (mixed ? 4 : 0) | (implicit ? 2 : 0) | (tvd ? 1 : 0);
     switch (code) {
-    case 7: k_batch_assemble<true, true, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    case 6: k_batch_assemble<true, true, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    case 5: k_batch_assemble<true, false, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    case 4: k_batch_assemble<true, false, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    case 3: k_batch_assemble<false, true, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    case 2: k_batch_assemble<false, true, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    case 1: k_batch_assemble<false, false, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    default: k_batch_assemble<false, false, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    case 7: k_assemble<true, true, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    case 6: k_assemble<true, true, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    case 5: k_assemble<true, false, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    case 4: k_assemble<true, false, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    case 3: k_assemble<false, true, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    case 2: k_assemble<false, true, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    case 1: k_assemble<false, false, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    default: k_assemble<false, false, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
     }
 }
 
-void launch_batch_pressure(const BatchPlan &bp, bool mixed, int prev, int old, int nw, void *stream)
+void launch_pressure(const BatchPlan &bp, bool mixed, int prev, int old, int nw, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
     const dim3 bl(bp.tx, bp.ty);
-    if (mixed) k_batch_pressure<true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
-    else k_batch_pressure<false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+    if (mixed) k_pressure<true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+    else k_pressure<false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
 }
 
-void launch_batch_velocity(const BatchPlan &bp, bool mixed, int old, int nw, void *stream)
+void launch_velocity(const BatchPlan &bp, bool mixed, int old, int nw, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
     const dim3 bl(bp.tx, bp.ty);
-    if (mixed) k_batch_velocity<true><<<bp.grid, bl, 0, s>>>(bp, old, nw);
-    else k_batch_velocity<false><<<bp.grid, bl, 0, s>>>(bp, old, nw);
+    if (mixed) k_velocity<true><<<bp.grid, bl, 0, s>>>(bp, old, nw);
+    else k_velocity<false><<<bp.grid, bl, 0, s>>>(bp, old, nw);
 }
 
 }  // namespace stg
