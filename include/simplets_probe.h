@@ -1,6 +1,7 @@
 /*
  * simplets_probe.h -- arithmetic-throughput probe of the device, used as the
- * ALU roofline of the SIMPLE-TS sweep.
+ * ALU roofline of the SIMPLE-TS sweep, and a check of the sweep's FP64
+ * reciprocal against IEEE division.
  *
  * The paper measures operator cost with a "simplified test code": the energy
  * equation evaluated on private variables in a loop with no memory traffic
@@ -21,6 +22,16 @@ extern "C" {
  * itself with CUDA events.  *gflops receives 2 x FMAs / second / 1e9.
  * Returns 0 on success, 1 on a bad argument, 3 on a CUDA error.  Synchronous. */
 int simplets_alu_peak(int kind, double millis, void *stream, double *gflops);
+
+/* Check of the FP64 reciprocal the sweep uses in place of IEEE division
+ * (Newton-Raphson iteration r <- r (2 - x r), two steps from the FP32
+ * reciprocal of x; IEEE division for |x| outside [2^-100, 2^100]).
+ * host_x: n doubles (host memory).  host_out: 2n doubles (host memory)
+ * receiving, for each x[q], the sweep's reciprocal in host_out[2q] and the
+ * IEEE quotient 1/x[q] in host_out[2q+1], both computed on the device.
+ * Returns 0 on success, 1 on a bad argument, 3 on a CUDA error.  Synchronous;
+ * allocates and frees its own device buffers. */
+int simplets_recip_check(const double *host_x, int n, double *host_out);
 
 #ifdef __cplusplus
 }

@@ -80,6 +80,7 @@ _SIGNATURES = {
     "sim_profile_read": ([ctypes.c_void_p, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "sim_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "simplets_alu_peak": ([ctypes.c_int, ctypes.c_double, ctypes.c_void_p, _DP], ctypes.c_int),
+    "simplets_recip_check": ([_DP, ctypes.c_int, _DP], ctypes.c_int),
     "sim_destroy": ([ctypes.c_void_p], None),
     "sim_batch_create": ([ctypes.c_int, ctypes.POINTER(sim_grid), ctypes.POINTER(sim_gas), ctypes.POINTER(sim_bc),
                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
@@ -161,6 +162,17 @@ def alu_peak_gflops(kind: str = "fp64", millis: float = 50.0, stream: Optional[i
     if rc:
         raise SimError(SIM_ECUDA, f"simplets_alu_peak failed ({rc})")
     return out.value
+
+
+def recip_check(x) -> "tuple[np.ndarray, np.ndarray]":
+    """The sweep's FP64 reciprocal of each x and the IEEE quotient 1/x, both
+    computed on the device (include/simplets_probe.h)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    out = np.empty(2 * x.size)
+    rc = load().simplets_recip_check(x.ctypes.data_as(_DP), int(x.size), out.ctypes.data_as(_DP))
+    if rc:
+        raise SimError(SIM_ECUDA, f"simplets_recip_check failed ({rc})")
+    return out[0::2].copy(), out[1::2].copy()
 
 
 class _CudaArray:

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "simplets_probe.h"
+#include "stg_common.cuh"
 
 namespace {
 
@@ -66,4 +67,22 @@ extern "C" int simplets_alu_peak(int kind, double millis, void *stream, double *
     if (!gflops || !(millis >= 1.0) || (kind != 0 && kind != 1)) return 1;
     cudaStream_t st = (cudaStream_t)stream;
     return kind == 0 ? run<double>(millis, st, gflops) : run<float>(millis, st, gflops);
+}
+
+extern "C" int simplets_recip_check(const double *host_x, int n, double *host_out)
+{
+    if (n < 0 || (n > 0 && (!host_x || !host_out))) return 1;
+    if (n == 0) return 0;
+    double *d = nullptr;
+    if (cudaMalloc(&d, 3 * (size_t)n * sizeof(double)) != cudaSuccess) return 3;
+    int rc = 0;
+    if (cudaMemcpy(d, host_x, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) rc = 3;
+    if (!rc) {
+        stg::launch_recip_check(d, d + n, n, nullptr);
+        if (cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(host_out, d + n, 2 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = 3;
+    }
+    cudaFree(d);
+    return rc;
 }

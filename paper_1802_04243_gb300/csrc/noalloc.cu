@@ -331,6 +331,7 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
             for (int j = 0; j < ny; j++) uref = std::fmax(uref, std::fabs(bc->inflow_u[j]));
         k.dt = cfl * dmin / (uref + std::sqrt(gm / 2.0));
     }
+    k.hrdt = 0.5 / k.dt;
 
     // --------------------------------------------------- carve the scratch
     void *base = nullptr;
@@ -340,7 +341,7 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     const size_t nelem = (size_t)pitch * (ny + 2 * G + 1);
     const int mx = nx + 2 * G + 1, my = ny + 2 * G + 1;
     Carver cv{(unsigned char *)base};
-    double *pool = cv.take<double>(31 * nelem);
+    double *pool = cv.take<double>(34 * nelem);
     uint16_t *flag = cv.take<uint16_t>(nelem);
     uint8_t *kind = cv.take<uint8_t>(nelem);
     uint8_t *side = cv.take<uint8_t>(nelem);
@@ -365,7 +366,7 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     if (bc->inflow_p) NA_TRY(cudaMemcpyAsync(cin + 2 * ny, bc->inflow_p, ny * sizeof(double), cudaMemcpyHostToDevice, s));
     if (bc->n_rect) NA_TRY(cudaMemcpyAsync(crect, bc->rect, 4 * bc->n_rect * sizeof(int), cudaMemcpyHostToDevice, s));
     // the scratch keeps the previous call's contents: clear the work arrays
-    NA_TRY(cudaMemsetAsync(pool + 18 * nelem, 0, 13 * nelem * sizeof(double), s));
+    NA_TRY(cudaMemsetAsync(pool + 18 * nelem, 0, 16 * nelem * sizeof(double), s));
 
     Setup su{};
     su.nx = nx; su.ny = ny; su.pitch = pitch;
@@ -393,7 +394,8 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     }
     Work w{};
     w.rho_u = q; q += nelem; w.rho_v = q; q += nelem;
-    w.Fx = q; q += nelem; w.Fy = q; q += nelem; w.hx = q; q += nelem; w.hy = q; q += nelem;
+    w.Fx = q; q += nelem; w.Fy = q; q += nelem; w.DTx = q; q += nelem; w.DTy = q; q += nelem;
+    w.Bgc = q; q += nelem; w.Bgx = q; q += nelem; w.Bgy = q; q += nelem;
     w.uhat = q; q += nelem; w.du = q; q += nelem;
     w.vhat = q; q += nelem; w.dv = q; q += nelem; w.uexp = q; q += nelem; w.vexp = q; q += nelem;
     w.Texp = q;

@@ -216,6 +216,7 @@ sim_status read_problem(const sim_grid *gr, const sim_gas *gas, const sim_bc *bc
             for (int j = 0; j < pb.ny; j++) uref = std::fmax(uref, std::fabs(bc->inflow_u[j]));
         pb.k.dt = cfl * dmin / (uref + std::sqrt(pb.gamma / 2.0));
     }
+    pb.k.hrdt = 0.5 / pb.k.dt;
     return SIM_OK;
 }
 
@@ -539,8 +540,8 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
     std::vector<uint16_t> flags = make_flags(h);
     std::vector<double> ax = make_axis(pb.dx), ay = make_axis(pb.dy);
 
-    // one pool for 3 levels x 6 fields + 13 work arrays
-    const size_t nfields = 3 * 6 + 13;
+    // one pool for 3 levels x 6 fields + 16 work arrays
+    const size_t nfields = 3 * 6 + 16;
     cudaError_t e = cudaMalloc(&s->d_pool, nfields * s->nelem * sizeof(double));
     if (e != cudaSuccess) {
         sim_destroy(s);
@@ -561,8 +562,11 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
     w.rho_v = q; q += s->nelem;
     w.Fx = q; q += s->nelem;
     w.Fy = q; q += s->nelem;
-    w.hx = q; q += s->nelem;
-    w.hy = q; q += s->nelem;
+    w.DTx = q; q += s->nelem;
+    w.DTy = q; q += s->nelem;
+    w.Bgc = q; q += s->nelem;
+    w.Bgx = q; q += s->nelem;
+    w.Bgy = q; q += s->nelem;
     w.uhat = q; q += s->nelem;
     w.du = q; q += s->nelem;
     w.vhat = q; q += s->nelem;
@@ -593,7 +597,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
 
     s->mixed = pb.precision == SIM_MIXED;
     if (s->mixed) {
-        if (cudaMalloc(&s->d_pool32, 31 * s->nelem * sizeof(float)) != cudaSuccess ||
+        if (cudaMalloc(&s->d_pool32, 34 * s->nelem * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&s->d_axis32, (nax + nay) * sizeof(float)) != cudaSuccess) {
             sim_destroy(s);
             return SIM_ENOMEM;
@@ -613,8 +617,11 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         w32.rho_v = p32; p32 += s->nelem;
         w32.Fx = p32; p32 += s->nelem;
         w32.Fy = p32; p32 += s->nelem;
-        w32.hx = p32; p32 += s->nelem;
-        w32.hy = p32; p32 += s->nelem;
+        w32.DTx = p32; p32 += s->nelem;
+        w32.DTy = p32; p32 += s->nelem;
+        w32.Bgc = p32; p32 += s->nelem;
+        w32.Bgx = p32; p32 += s->nelem;
+        w32.Bgy = p32; p32 += s->nelem;
         w32.uhat = p32; p32 += s->nelem;
         w32.du = p32; p32 += s->nelem;
         w32.vhat = p32; p32 += s->nelem;
@@ -631,12 +638,12 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         s->mx.g.y = AxisT<float>{fy, fy + my, fy + 2 * my, fy + 3 * my, fy + 4 * my};
         const Coef &k = pb.k;
         s->mx.k = CoefT<float>{(float)k.A, (float)k.B, (float)k.CT1f, (float)k.CT2f, (float)k.CT3f,
-                               (float)k.omega, (float)k.dt, (float)k.gx, (float)k.gy};
+                               (float)k.omega, (float)k.dt, (float)k.gx, (float)k.gy, (float)k.hrdt};
         std::vector<float> a32(nax + nay);
         for (size_t q = 0; q < nax; q++) a32[q] = (float)ax[q];
         for (size_t q = 0; q < nay; q++) a32[nax + q] = (float)ay[q];
         CUDA_TRY(s, cudaMemcpy(s->d_axis32, a32.data(), a32.size() * sizeof(float), cudaMemcpyHostToDevice));
-        CUDA_TRY(s, cudaMemsetAsync(s->mx.w.rho_u, 0, 13 * s->nelem * sizeof(float), s->stream));
+        CUDA_TRY(s, cudaMemsetAsync(s->mx.w.rho_u, 0, 16 * s->nelem * sizeof(float), s->stream));
     }
 
     std::vector<double> f[6];
@@ -646,7 +653,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
     CUDA_TRY(s, cudaMemcpyAsync(s->d_flag, flags.data(), flags.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(s, cudaMemcpyAsync(s->d_axis, ax.data(), nax * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(s, cudaMemcpyAsync(s->d_axis + nax, ay.data(), nay * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    CUDA_TRY(s, cudaMemsetAsync(s->d_pool + 18 * s->nelem, 0, 13 * s->nelem * sizeof(double), s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(s->d_pool + 18 * s->nelem, 0, 16 * s->nelem * sizeof(double), s->stream));
     CUDA_TRY(s, cudaMemsetAsync(w.res, 0, 4 * sizeof(unsigned long long), s->stream));
     for (int l = 0; l < 3; l++)
         for (int k = 0; k < 6; k++)

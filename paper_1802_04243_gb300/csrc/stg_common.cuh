@@ -55,6 +55,7 @@ struct GeoT {
 template <typename R>
 struct CoefT {
     R A, B, CT1f, CT2f, CT3f, omega, dt, gx, gy;
+    R hrdt;               // 0.5 / dt
 };
 
 // One state level: u, v at faces; p, T, rho, Gamma at cell centres.
@@ -68,7 +69,9 @@ template <typename R>
 struct WorkT {
     R *rho_u, *rho_v;              // face densities (Eqs. pl10, pl11)
     R *Fx, *Fy;                    // mass fluxes F^x = rho^u u dy, F^y = rho^v v dx (Eqs. pl8, pl9)
-    R *hx, *hy;                    // harmonic-mean Gamma^lambda at x and y faces (Eq. pl33)
+    R *DTx, *DTy;                  // T conductances of x and y faces, C^T1_f Gamma_harm dy / dx_c (Eqs. pl32, pl33)
+    R *Bgc;                        // B Gamma at the corner (x^f_i, y^f_j), bilinear in the four cells
+    R *Bgx, *Bgy;                  // B Gamma dy/dx and B Gamma dx/dy of cell (i,j): normal-stress conductances
     R *uhat, *du, *vhat, *dv;      // pseudo velocities and d (Eqs. pl14, pl20, pl21)
     R *uexp, *vexp, *Texp;         // explicit convective terms (Eqs. pl15_11, pl31_1)
 };
@@ -149,5 +152,9 @@ void launch_derive(const Geo &g, const Coef &c, const Level &lv, void *stream);
 void launch_scatter(const Geo &g, int field, const double *src, const Level &lv, void *stream);
 void launch_gather(const Geo &g, int field, const Level &lv, double *dst, void *stream);
 void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, size_t nelem, void *stream);
+
+// The FP64 reciprocal of the sweep (Newton-Raphson from an FP32 seed) and the
+// IEEE quotient 1/x of each x[q], interleaved in out[2q], out[2q+1].
+void launch_recip_check(const double *x, double *out, int n, void *stream);
 
 }  // namespace stg

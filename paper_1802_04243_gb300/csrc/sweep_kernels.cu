@@ -37,6 +37,12 @@ struct Ix {
 template <typename R>
 __device__ __forceinline__ R at(const R *a, int i) { return a[i + G]; }
 
+// vel > 0 from the bit pattern: a positive double (float) is a positive
+// 64-bit (32-bit) integer, so the test runs on the integer pipe instead of
+// GB300's narrow FP64 pipe.  (NaN inputs may take either branch.)
+__device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool positive(float x) { return __float_as_int(x) > 0; }
+
 // ---------------------------------------------------------------- limiter
 
 // Van Leer psi(r) = (r + |r|)/(1 + r) for r = num/den; 0 unless num and den
@@ -52,7 +58,7 @@ __device__ __forceinline__ R van_leer(R num, R den)
 template <typename R>
 __device__ __forceinline__ R psi_surface(R f1, R f2, R f3, R f4, R d1, R d2, R d3, R d4, R vel)
 {
-    if (vel > R(0))
+    if (positive(vel))
         return d2 / (d2 + d3) * van_leer((d2 + d3) * (f2 - f1), (d1 + d2) * (f3 - f2));
     return -d3 / (d2 + d3) * van_leer((d2 + d3) * (f4 - f3), (d3 + d4) * (f3 - f2));
 }
@@ -61,15 +67,15 @@ __device__ __forceinline__ R psi_surface(R f1, R f2, R f3, R f4, R d1, R d2, R d
 template <typename R>
 __device__ __forceinline__ R psi_centre(R f1, R f2, R f3, R f4, R d1, R d2, R d3, R vel)
 {
-    if (vel > R(0))
+    if (positive(vel))
         return R(0.5) * van_leer(d2 * (f2 - f1), d1 * (f3 - f2));
     return R(-0.5) * van_leer(d2 * (f4 - f3), d3 * (f3 - f2));
 }
 
 template <typename R>
-__device__ __forceinline__ R upwind(R a, R b, R vel) { return vel > R(0) ? a : b; }
+__device__ __forceinline__ R upwind(R a, R b, R vel) { return positive(vel) ? a : b; }
 template <typename R>
-__device__ __forceinline__ R pos(R x) { return fmax(R(0), x); }
+__device__ __forceinline__ R pos(R x) { return positive(x) ? x : R(0); }
 
 // Value of node m seen from node a: reflected about the stored wall value when
 // the flag of m carries `wall_bit`.
@@ -92,14 +98,6 @@ __device__ __forceinline__ R gamma_corner(const GeoT<R> &g, const R *gam, int c,
     R lo = at(g.x.wlo, i) * gam[c - P - 1] + at(g.x.whi, i) * gam[c - P];
     R hi = at(g.x.wlo, i) * gam[c - 1] + at(g.x.whi, i) * gam[c];
     return at(g.y.wlo, j) * lo + at(g.y.whi, j) * hi;
-}
-
-// Eq. pl33: distance-weighted harmonic mean of Gamma^lambda across a face
-// between a node of size da and one of size db.
-template <typename R>
-__device__ __forceinline__ R harmonic(R ga, R gb, R da, R db)
-{
-    return (da + db) * ga * gb / (da * gb + db * ga);
 }
 
 // ------------------------------------------------------ residual reduction
@@ -200,38 +198,60 @@ __device__ __forceinline__ double recip(double a)
     return r;
 }
 
+// T conductance of the face between a node of size da and one of size db
+// (Eq. pl32): c_area Gamma_f / (0.5 (da + db)) with the distance-weighted
+// harmonic mean Gamma_f = (da + db) ga gb / (da gb + db ga) of Eq. pl33,
+// i.e. 2 c_area ga gb / (da gb + db ga).  c_area = C^T1_f times the face area.
+template <typename R>
+__device__ __forceinline__ R conductance(R ga, R gb, R da, R db, R c_area)
+{
+    return R(2) * c_area * (ga * gb) * recip(fma(da, gb, db * ga));
+}
+
 // ------------------------------------------------------- face densities
 
-// rho^u at u face (i,j) and rho^v at v face (i,j), Eqs. pl10, pl11, written as
-// the upwind value plus psi_s times the difference across the face.
+// Per-position face quantities of one state level, stored for the kernels
+// that follow: rho^u at u face (i,j) and rho^v at v face (i,j) (Eqs. pl10,
+// pl11, the upwind value plus psi_s times the difference across the face),
+// the mass fluxes through them (Eqs. pl8, pl9), the T conductances of the x
+// and y faces (Eq. pl32 with the harmonic mean Eq. pl33), B Gamma at the
+// corner (x^f_i, y^f_j), and the normal-stress conductances B Gamma dy/dx,
+// B Gamma dx/dy of cell (i,j).  Each is used by two to four neighbours in the
+// assembly, which would otherwise recompute it each time.
 template <typename R, bool TVD>
-__device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const R *__restrict__ u, const R *__restrict__ v,
-                                                    const R *__restrict__ rho, const R *__restrict__ gam,
-                                                    const WorkT<R> &w, int i, int j)
+__device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const CoefT<R> &k, const R *__restrict__ u,
+                                                    const R *__restrict__ v, const R *__restrict__ rho,
+                                                    const R *__restrict__ gam, const WorkT<R> &w, int i, int j)
 {
-    R *__restrict__ rho_u = w.rho_u;
-    R *__restrict__ rho_v = w.rho_v;
     const int P = g.pitch;
     const int c = Ix{P}(i, j);
-    if (i <= g.nx && j < g.ny) {
+    if (i > g.nx || j > g.ny) return;
+    const R dxi = at(g.x.d, i), dyj = at(g.y.d, j);
+    if (j < g.ny) {
         const R vel = u[c], rl = rho[c - 1], rr = rho[c];
         R val = upwind(rl, rr, vel);
         if (TVD && (g.flag[c] & F_TCX))
             val += psi_surface(rho[c - 2], rl, rr, rho[c + 1], at(g.x.d, i - 2), at(g.x.d, i - 1),
-                               at(g.x.d, i), at(g.x.d, i + 1), vel) * (rr - rl);
-        rho_u[c] = val;
-        w.Fx[c] = val * vel * at(g.y.d, j);
-        w.hx[c] = harmonic(gam[c - 1], gam[c], at(g.x.d, i - 1), at(g.x.d, i));
+                               dxi, at(g.x.d, i + 1), vel) * (rr - rl);
+        w.rho_u[c] = val;
+        w.Fx[c] = val * vel * dyj;
+        w.DTx[c] = conductance(gam[c - 1], gam[c], at(g.x.d, i - 1), dxi, k.CT1f * dyj);
     }
-    if (i < g.nx && j <= g.ny) {
+    if (i < g.nx) {
         const R vel = v[c], rb = rho[c - P], rt = rho[c];
         R val = upwind(rb, rt, vel);
         if (TVD && (g.flag[c] & F_TCY))
             val += psi_surface(rho[c - 2 * P], rb, rt, rho[c + P], at(g.y.d, j - 2), at(g.y.d, j - 1),
-                               at(g.y.d, j), at(g.y.d, j + 1), vel) * (rt - rb);
-        rho_v[c] = val;
-        w.Fy[c] = val * vel * at(g.x.d, i);
-        w.hy[c] = harmonic(gam[c - P], gam[c], at(g.y.d, j - 1), at(g.y.d, j));
+                               dyj, at(g.y.d, j + 1), vel) * (rt - rb);
+        w.rho_v[c] = val;
+        w.Fy[c] = val * vel * dxi;
+        w.DTy[c] = conductance(gam[c - P], gam[c], at(g.y.d, j - 1), dyj, k.CT1f * dxi);
+    }
+    w.Bgc[c] = k.B * gamma_corner(g, gam, c, i, j);
+    if (i < g.nx && j < g.ny) {
+        const R bg = k.B * gam[c];
+        w.Bgx[c] = bg * dyj * at(g.x.rd, i);
+        w.Bgy[c] = bg * dxi * at(g.y.rd, j);
     }
 }
 
@@ -407,10 +427,7 @@ __device__ R temperature(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     const R Ts = seen<R, WALLS>(T, fl, c, c - P, F_WALL), Tn = seen<R, WALLS>(T, fl, c, c + P, F_WALL);
     const R uw = old.u[c], ue = old.u[c + 1], vs = old.v[c], vn = old.v[c + P];
     const R Fw = w.Fx[c], Fe = w.Fx[c + 1], Fs = w.Fy[c], Fn = w.Fy[c + P];
-    const R Dw = k.CT1f * w.hx[c] * dyj * at(g.x.rc, i);
-    const R De = k.CT1f * w.hx[c + 1] * dyj * at(g.x.rc, i + 1);
-    const R Ds = k.CT1f * w.hy[c] * dxi * at(g.y.rc, j);
-    const R Dn = k.CT1f * w.hy[c + P] * dxi * at(g.y.rc, j + 1);
+    const R Dw = w.DTx[c], De = w.DTx[c + 1], Ds = w.DTy[c], Dn = w.DTy[c + P];
     const R vol = dxi * dyj;
     R a1, a2, a3, a4, a0, texp;
     if (IMPL) {
@@ -460,17 +477,16 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     const R Fbw = ubw * rho[a - 1] * dyj, Fbe = ube * rho[a] * dyj;
     const R vs1 = v[a - 1], vs2 = v[a], vn1 = v[a - 1 + P], vn2 = v[a + P];
     const R Fs1 = w.Fy[a - 1], Fs2 = w.Fy[a], Fn1 = w.Fy[a - 1 + P], Fn2 = w.Fy[a + P];
-    const R gcs = gamma_corner(g, gam, a, i, j), gcn = gamma_corner(g, gam, a + P, i, j + 1);
-    const R Dxw = k.B * gam[a - 1] * dyj * at(g.x.rd, i - 1);
-    const R Dxe = k.B * gam[a] * dyj * at(g.x.rd, i);
+    const R gcs = w.Bgc[a], gcn = w.Bgc[a + P];      // B Gamma at the corners (i, j), (i, j+1)
+    const R Dxw = w.Bgx[a - 1], Dxe = w.Bgx[a];
     const R wsum = dxp + dxw;
-    const R Dys = k.B * gcs * wsum * (R(0.5) * at(g.y.rc, j));
-    const R Dyn = k.B * gcn * wsum * (R(0.5) * at(g.y.rc, j + 1));
-    const R r2dt = R(0.5) / k.dt;
+    const R Dys = gcs * wsum * (R(0.5) * at(g.y.rc, j));
+    const R Dyn = gcn * wsum * (R(0.5) * at(g.y.rc, j + 1));
+    const R r2dt = k.hrdt;
     const R trans = (rho[a] * dxp + rho[a - 1] * dxw) * dyj * r2dt;
     const R b = (prev.rho[a] * dxp + prev.rho[a - 1] * dxw) * dyj * r2dt * prev.u[a]
-                     + k.B * (gcn * (vn2 - vn1) - gcs * (vs2 - vs1)
-                              - R(2.0 / 3.0) * gam[a] * (vn2 - vs2) + R(2.0 / 3.0) * gam[a - 1] * (vn1 - vs1))
+                     + (gcn * (vn2 - vn1) - gcs * (vs2 - vs1))
+                     + k.B * (R(2.0 / 3.0) * gam[a - 1] * (vn1 - vs1) - R(2.0 / 3.0) * gam[a] * (vn2 - vs2))
                      + k.gx * (rho[a] * dxp + rho[a - 1] * dxw) * dyj * R(0.5);
     R a1, a2, a3, a4, a0, uexp;
     if (IMPL) {
@@ -526,17 +542,16 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     const R Fbs = vbs * rho[b - P] * dxi, Fbn = vbn * rho[b] * dxi;
     const R uw1 = u[b - P], uw2 = u[b], ue1 = u[b + 1 - P], ue2 = u[b + 1];
     const R Fw1 = w.Fx[b - P], Fw2 = w.Fx[b], Fe1 = w.Fx[b + 1 - P], Fe2 = w.Fx[b + 1];
-    const R gcw = gamma_corner(g, gam, b, i, j), gce = gamma_corner(g, gam, b + 1, i + 1, j);
+    const R gcw = w.Bgc[b], gce = w.Bgc[b + 1];      // B Gamma at the corners (i, j), (i+1, j)
     const R hsum = dyp + dys;
-    const R Dxw = k.B * gcw * hsum * (R(0.5) * at(g.x.rc, i));
-    const R Dxe = k.B * gce * hsum * (R(0.5) * at(g.x.rc, i + 1));
-    const R Dys = k.B * gam[b - P] * dxi * at(g.y.rd, j - 1);
-    const R Dyn = k.B * gam[b] * dxi * at(g.y.rd, j);
-    const R r2dt = R(0.5) / k.dt;
+    const R Dxw = gcw * hsum * (R(0.5) * at(g.x.rc, i));
+    const R Dxe = gce * hsum * (R(0.5) * at(g.x.rc, i + 1));
+    const R Dys = w.Bgy[b - P], Dyn = w.Bgy[b];
+    const R r2dt = k.hrdt;
     const R trans = (rho[b] * dyp + rho[b - P] * dys) * dxi * r2dt;
     const R bsrc = (prev.rho[b] * dyp + prev.rho[b - P] * dys) * dxi * r2dt * prev.v[b]
-                        + k.B * (gce * (ue2 - ue1) - gcw * (uw2 - uw1)
-                                 - R(2.0 / 3.0) * gam[b] * (ue2 - uw2) + R(2.0 / 3.0) * gam[b - P] * (ue1 - uw1))
+                        + (gce * (ue2 - ue1) - gcw * (uw2 - uw1))
+                        + k.B * (R(2.0 / 3.0) * gam[b - P] * (ue1 - uw1) - R(2.0 / 3.0) * gam[b] * (ue2 - uw2))
                         + k.gy * (rho[b] * dyp + rho[b - P] * dys) * dxi * R(0.5);
     R a1, a2, a3, a4, a0, vexp;
     if (IMPL) {
@@ -630,7 +645,8 @@ __device__ __forceinline__ void assemble_body(const GeoT<R> &g, const CoefT<R> &
 // ---------------------------------------------------------------- pressure
 
 // Eqs. pl23, pl24 with the new T (point Jacobi in p^old), then rho = p/T
-// (Eq. pl5) and Gamma = T^omega, with the p and T residual maxima.
+// (Eq. pl5) and Gamma = T^omega, with the p and T residual maxima.  The
+// divisions by T and a^p_0 use the Newton-Raphson reciprocal.
 __device__ __forceinline__ void pressure_body(const Geo &g, const Coef &k, const Level &prev, const Level &old,
                                               const Level &nw, const Work &w, int i, int j)
 {
@@ -645,14 +661,14 @@ __device__ __forceinline__ void pressure_body(const Geo &g, const Coef &k, const
             const double aps = rv_s * w.dv[c] * dxi, apn = rv_n * w.dv[c + P] * dxi;
             const double bpw = ru_w * w.uhat[c] * dyj, bpe = ru_e * w.uhat[c + 1] * dyj;
             const double bps = rv_s * w.vhat[c] * dxi, bpn = rv_n * w.vhat[c + P] * dxi;
-            const double Tn = nw.T[c];
+            const double Tn = nw.T[c], inv_T = recip(Tn);
             const double vol = dxi * dyj;
-            const double ap0 = vol / Tn + (apw + ape + aps + apn) * k.dt;
+            const double ap0 = vol * inv_T + (apw + ape + aps + apn) * k.dt;
             const double bp = prev.rho[c] * vol - (bpe - bpw + bpn - bps) * k.dt;
             const double pn = ((apw * old.p[c - 1] + ape * old.p[c + 1] + aps * old.p[c - P] + apn * old.p[c + P]) * k.dt
-                               + bp) / ap0;
+                               + bp) * recip(ap0);
             nw.p[c] = pn;
-            nw.rho[c] = pn / Tn;
+            nw.rho[c] = pn * inv_T;
             nw.gam[c] = (k.omega == 0.5) ? sqrt(Tn) : pow(Tn, k.omega);
             rp = ordered(pn - old.p[c]);
             rT = ordered(Tn - old.T[c]);
@@ -959,10 +975,10 @@ __global__ void __launch_bounds__(256) k_faces(const __grid_constant__ BatchPlan
     for_tiles(bp, [&](const Inst &I, int i, int j) {
         if constexpr (MIXED) {
             const LevelT<float> &L = I.lv32[level];
-            face_densities_body<float, TVD>(I.g32, L.u, L.v, L.rho, L.gam, I.w32, i, j);
+            face_densities_body<float, TVD>(I.g32, I.k32, L.u, L.v, L.rho, L.gam, I.w32, i, j);
         } else {
             const Level &L = I.lv[level];
-            face_densities_body<double, TVD>(I.g, L.u, L.v, L.rho, L.gam, I.w, i, j);
+            face_densities_body<double, TVD>(I.g, I.k, L.u, L.v, L.rho, L.gam, I.w, i, j);
         }
     });
 }
@@ -1015,7 +1031,9 @@ __global__ void __launch_bounds__(256) k_velocity(const __grid_constant__ BatchP
 
 // ----------------------------------------------------- state maintenance
 
-// rho = p/T and Gamma = T^omega of every fluid cell.
+// rho = p/T and Gamma = T^omega of every fluid cell, evaluated exactly as
+// the pressure kernel evaluates them (so a state written out and set again
+// continues bit for bit).
 __global__ void k_derive(Geo g, Coef k, Level L)
 {
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
@@ -1023,7 +1041,7 @@ __global__ void k_derive(Geo g, Coef k, Level L)
     const int c = Ix{g.pitch}(i, j);
     if (!(g.flag[c] & F_FLUID)) return;
     const double T = L.T[c];
-    L.rho[c] = L.p[c] / T;
+    L.rho[c] = L.p[c] * recip(T);
     L.gam[c] = (k.omega == 0.5) ? sqrt(T) : pow(T, k.omega);
 }
 
@@ -1061,6 +1079,15 @@ __global__ void k_gather(Geo g, int field, Level L, double *dst)
     const int w = field == 0 ? nx + 1 : nx, h = field == 1 ? ny + 1 : ny;
     if (i >= w || j >= h) return;
     dst[(size_t)j * w + i] = field_of(L, field)[Ix{g.pitch}(i, j)];
+}
+
+// recip(x) next to the IEEE quotient 1/x, for the check of the reciprocal.
+__global__ void k_recip_check(const double *x, double *out, int n)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    out[2 * q] = recip(x[q]);
+    out[2 * q + 1] = 1.0 / x[q];
 }
 
 template <typename R>
@@ -1110,6 +1137,11 @@ void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, siz
     (void)g;
     const int blocks = (int)((nelem + 255) / 256 < 4096 ? (nelem + 255) / 256 : 4096);
     k_shadow<<<blocks, 256, 0, (cudaStream_t)stream>>>(lv, lv32, nelem);
+}
+
+void launch_recip_check(const double *x, double *out, int n, void *stream)
+{
+    if (n > 0) k_recip_check<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, out, n);
 }
 
 void launch_derive(const Geo &g, const Coef &c, const Level &lv, void *stream)

@@ -1,0 +1,44 @@
+"""The FP64 reciprocal of the sweep against CUDA's IEEE division.
+
+The sweep divides by a^0 (Eqs. pl15, pl20, pl21, pl30) and by T and a^p_0
+(Eqs. pl23, pl5) with a Newton-Raphson reciprocal, r <- r (2 - x r), two steps
+from the FP32 reciprocal of x, instead of IEEE division.  Two steps take the
+FP32 seed's relative error (about 2^-23) to below the FP64 rounding, so the
+result must stay within one unit in the last place of the IEEE quotient."""
+import numpy as np
+import pytest
+
+import paper_1802_04243_gb300 as sim
+from paper_1802_04243_gb300 import build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+    sim.load()
+
+
+def test_reciprocal_within_one_ulp_of_ieee_division():
+    rng = np.random.default_rng(11)
+    mags = 10.0 ** rng.uniform(-300, 300, 200_000)
+    x = np.concatenate([
+        mags * rng.choice([-1.0, 1.0], mags.size),
+        rng.uniform(0.5, 2.0, 100_000),                              # the typical magnitudes of a^0
+        np.nextafter(1.0, 2.0) * 2.0 ** np.arange(-120, 121),        # both sides of the FP32-seed range
+        np.nextafter(2.0, 1.0) * 2.0 ** np.arange(-120, 121),
+        [1.0, -1.0, 2.0, 0.5, 3.0, 1.0 / 3.0, 7.0, 1e-310, -1e-310, 1e308, 2.0 ** -100, 2.0 ** 100],
+    ])
+    ours, ieee = sim.recip_check(x)
+    assert np.all(np.isfinite(ours) == np.isfinite(ieee))
+    fin = np.isfinite(ieee)
+    ulps = np.abs(ours[fin] - ieee[fin]) / np.spacing(np.abs(ieee[fin]))
+    print("max ulp", ulps.max(), "exact", float(np.mean(ulps == 0)))
+    assert ulps.max() <= 1.0
+
+
+def test_reciprocal_of_exact_cases():
+    x = np.array([1.0, 2.0, 4.0, 0.25, -8.0, 2.0 ** 60, 2.0 ** -60])
+    ours, ieee = sim.recip_check(x)
+    assert np.array_equal(ours, ieee)                                # powers of two are exact
