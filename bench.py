@@ -31,19 +31,32 @@ if ROOT not in sys.path:
 METRIC = "Mcell-steps/s FP64 vs FP32/FP64 mixed at stated error; % of HBM roofline"
 UNIT = "Mcell-steps/s"
 
-# Algorithmic traffic of the assembly kernel per cell and loop-2 iteration:
-# reads u, v, p, T, rho, Gamma of the previous iterate, rho^u, rho^v, and
-# u, v, T, rho of level n-1 (12 doubles); writes T, u^, d^u, v^, d^v (5 doubles).
-ASSEMBLE_BYTES_PER_CELL = 17 * 8
-# FP64 flops the assembly kernel executes per cell and iteration (implicit
-# upwind): 2 * DFMA + DMUL + DADD thread instructions of one k_assemble launch
-# counted by ncu on the 2048x512 channel (151.6 M, 160.9 M, 91.8 M), divided by
-# its 1,048,576 cells.
-ASSEMBLE_FP64_FLOPS_PER_CELL = 530.2
-# DRAM bytes of that launch per cell (69.1 MB read + 11.1 MB written).
-ASSEMBLE_DRAM_BYTES_PER_CELL = 76.5
-# ncu: sm__pipe_fp64_cycles_active of that launch, percent of peak.
-ASSEMBLE_FP64_PIPE_ACTIVE = 0.864
+# The dominant kernel, k_assemble (FP64, implicit upwind), is bound by GB300's
+# FP64 pipe.  Its work per cell and loop-2 iteration is counted by ncu on one
+# launch for the 2048x512 channel (1,048,576 cells): DFMA, DADD and DMUL thread
+# instructions 67.04 M, 65.51 M, 81.47 M.
+ASSEMBLE_FP64_INST_PER_CELL = {"dfma": 63.93, "dadd": 62.48, "dmul": 77.70}
+# DRAM bytes of that launch per cell (110.7 MB read + 19.3 MB written).
+ASSEMBLE_DRAM_BYTES_PER_CELL = 124.0
+# ncu: sm__pipe_fp64_cycles_active of that launch, fraction of peak.
+ASSEMBLE_FP64_PIPE_ACTIVE = 0.859
+# Algorithmic HBM traffic of the kernel per cell: reads u, v, p, T, rho, Gamma of
+# the previous iterate, u, v, T, rho of level n-1 and the face arrays F^x, F^y,
+# D^T_x, D^T_y, B Gamma (corner), B Gamma dy/dx, B Gamma dx/dy (17 doubles);
+# writes T, u^, d^u, v^, d^v (5 doubles).
+ASSEMBLE_BYTES_PER_CELL = 22 * 8
+# GB300 FP64 pipe: 2 FP64 thread instructions per cycle per SM (ncu's
+# peak_sustained for DFMA), 152 SMs.
+FP64_INST_PER_CYCLE_PER_SM = 2
+
+
+def hbm_peak_gbs() -> float:
+    """Measured HBM copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
 
 
 def parse():
@@ -365,23 +378,28 @@ def run_ours(args, rank, world, local_rank):
 
     asm_ms, asm_n = prof["assemble"]
     asm_avg_s = asm_ms / max(asm_n, 1) * 1e-3
-    if ASSEMBLE_FP64_FLOPS_PER_CELL:
-        ach = ASSEMBLE_FP64_FLOPS_PER_CELL * case.cells / asm_avg_s / 1e12
-        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak_fp64 / 1e3, 4), "unit": "TFLOP/s",
-                "frac": round(ach / (peak_fp64 / 1e3), 4),
-                "traffic": round(ASSEMBLE_DRAM_BYTES_PER_CELL * case.cells),
-                "kernel": "k_assemble", "peak_source": "FP64 FMA probe measured in this run (simplets_alu_peak), "
-                                                        "2 flops per DFMA at full issue rate",
-                "fp64_pipe_active_ncu": ASSEMBLE_FP64_PIPE_ACTIVE,
-                "traffic_source": "ncu dram bytes of one launch on the 2048x512 channel, scaled by cells"}
-    else:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
-        ach = ASSEMBLE_BYTES_PER_CELL * case.cells / asm_avg_s / 1e9
-        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": None, "kernel": "k_assemble"}
+    csum = clocks.summary()
+    sm_mhz = csum.get("sm_mhz") or csum.get("sm_max_mhz") or 2070.0
+    n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    inst = sum(ASSEMBLE_FP64_INST_PER_CELL.values()) * case.cells            # per launch
+    flops = (2 * ASSEMBLE_FP64_INST_PER_CELL["dfma"] + ASSEMBLE_FP64_INST_PER_CELL["dadd"]
+             + ASSEMBLE_FP64_INST_PER_CELL["dmul"]) * case.cells
+    peak_inst = FP64_INST_PER_CYCLE_PER_SM * n_sm * sm_mhz * 1e6                 # per second
+    ach = inst / asm_avg_s
+    roof = {"bound": "alu", "achieved": round(ach / 1e9, 2), "peak": round(peak_inst / 1e9, 2),
+            "unit": "G FP64 inst/s", "frac": round(ach / peak_inst, 4),
+            "traffic": round(ASSEMBLE_DRAM_BYTES_PER_CELL * case.cells), "kernel": "k_assemble",
+            "peak_source": f"{FP64_INST_PER_CYCLE_PER_SM} FP64 instructions/cycle/SM x {n_sm} SMs x "
+                           f"{sm_mhz:.0f} MHz (median SM clock sampled in the timed region)",
+            "work_source": "ncu DFMA+DADD+DMUL thread instructions per cell of one launch (2048x512 channel)",
+            "traffic_source": "ncu dram bytes of that launch, scaled by cells",
+            "fp64_pipe_active_ncu": ASSEMBLE_FP64_PIPE_ACTIVE,
+            "flops": {"achieved_tflops": round(flops / asm_avg_s / 1e12, 4),
+                      "peak_tflops": round(2 * peak_inst / 1e12, 4),
+                      "probe_tflops": round(peak_fp64 / 1e3, 4)},
+            "hbm": {"algorithmic_gbs": round(ASSEMBLE_BYTES_PER_CELL * case.cells / asm_avg_s / 1e9, 1),
+                    "peak_gbs": hbm_peak_gbs()}}
     roof["kernel_ms_avg"] = round(asm_avg_s * 1e3, 5)
-    roof["fp64_peak_gflops_measured"] = round(peak_fp64, 1)
 
     batched = None if args.no_batch else run_batch(args, stream)
 
@@ -402,7 +420,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": int(launches),
             "kernel_ms_avg": {k: round(ms / n, 5) for k, (ms, n) in prof.items() if n},
             "kernel_timing": f"separate pass of {prof_steps} steps with per-launch CUDA events",
-            "roofline": roof, "mixed": mixed, "batched": batched, "cpu_baseline": cpu, "clocks": clocks.summary(),
+            "roofline": roof, "mixed": mixed, "batched": batched, "cpu_baseline": cpu, "clocks": csum,
             "residuals_last_step": [float(x) for x in res], "impl": "ours"}
     print(json.dumps(line), flush=True)
     if dist:

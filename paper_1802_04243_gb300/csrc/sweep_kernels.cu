@@ -442,10 +442,17 @@ __device__ R temperature(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
             if (fl[c + P] & F_TCY)
                 pn = psi_surface(Ts, Tp, Tn, T[c + 2 * P], dys, dyj, dyn, at(g.y.d, j + 2), vn);
         }
-        a1 = pos(Fw) - Fw * pw + Dw;
-        a2 = pos(-Fe) - Fe * pe + De;
-        a3 = pos(Fs) - Fs * ps + Ds;
-        a4 = pos(-Fn) - Fn * pn + Dn;
+        if constexpr (TVD) {
+            a1 = pos(Fw) - Fw * pw + Dw;
+            a2 = pos(-Fe) - Fe * pe + De;
+            a3 = pos(Fs) - Fs * ps + Ds;
+            a4 = pos(-Fn) - Fn * pn + Dn;
+        } else {                                   // upwind: psi = 0
+            a1 = pos(Fw) + Dw;
+            a2 = pos(-Fe) + De;
+            a3 = pos(Fs) + Ds;
+            a4 = pos(-Fn) + Dn;
+        }
         a0 = k.dt * (a1 + a2 + a3 + a4 + Fe - Fw + Fn - Fs) + old.rho[c] * vol;
         texp = R(0);
     } else {
@@ -454,7 +461,9 @@ __device__ R temperature(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
         texp = w.Texp[c];
     }
     const R sc = energy_source<R, WALLS>(g, k, old, c, i, j);
-    const R rhs = k.dt * (a1 * Tw + a2 * Te + a3 * Ts + a4 * Tn + sc + texp) + prev.rho[c] * prev.T[c] * vol;
+    R src = a1 * Tw + a2 * Te + a3 * Ts + a4 * Tn + sc;
+    if constexpr (!IMPL) src += texp;
+    const R rhs = k.dt * src + prev.rho[c] * prev.T[c] * vol;
     return rhs * recip(a0);
 }
 
@@ -509,10 +518,17 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
                 pn2 = psi_surface(uS, uP, uN, f4, d1, dyj, d3, d4, vn2);
             }
         }
-        a1 = pos(Fbw) - Fbw * pw + R(4.0 / 3.0) * Dxw;
-        a2 = pos(-Fbe) - Fbe * pe + R(4.0 / 3.0) * Dxe;
-        a3 = R(0.5) * (pos(Fs1) - Fs1 * ps1 + pos(Fs2) - Fs2 * ps2) + Dys;
-        a4 = R(0.5) * (pos(-Fn1) - Fn1 * pn1 + pos(-Fn2) - Fn2 * pn2) + Dyn;
+        if constexpr (TVD) {
+            a1 = pos(Fbw) - Fbw * pw + R(4.0 / 3.0) * Dxw;
+            a2 = pos(-Fbe) - Fbe * pe + R(4.0 / 3.0) * Dxe;
+            a3 = R(0.5) * (pos(Fs1) - Fs1 * ps1 + pos(Fs2) - Fs2 * ps2) + Dys;
+            a4 = R(0.5) * (pos(-Fn1) - Fn1 * pn1 + pos(-Fn2) - Fn2 * pn2) + Dyn;
+        } else {                                   // upwind: psi = 0
+            a1 = pos(Fbw) + R(4.0 / 3.0) * Dxw;
+            a2 = pos(-Fbe) + R(4.0 / 3.0) * Dxe;
+            a3 = R(0.5) * (pos(Fs1) + pos(Fs2)) + Dys;
+            a4 = R(0.5) * (pos(-Fn1) + pos(-Fn2)) + Dyn;
+        }
         a0 = a1 + a2 + a3 + a4 + R(0.5) * (Fn2 - Fs2 + Fn1 - Fs1) + Fbe - Fbw + trans;
         uexp = R(0);
     } else {
@@ -521,7 +537,9 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
         uexp = w.uexp[a];
     }
     const R r = recip(a0);
-    uhat = (a1 * uW + a2 * uE + a3 * uS + a4 * uN + b + uexp) * r;
+    R src = a1 * uW + a2 * uE + a3 * uS + a4 * uN + b;
+    if constexpr (!IMPL) src += uexp;
+    uhat = src * r;
     du = k.A * dyj * r;
 }
 
@@ -574,10 +592,17 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
             if (fl[b + P] & F_TVY)
                 pn = psi_centre(vS, vP, vN, v[b + 2 * P], dys, dyp, at(g.y.d, j + 1), vbn);
         }
-        a1 = R(0.5) * (pos(Fw2) - Fw2 * pw2 + pos(Fw1) - Fw1 * pw1) + Dxw;
-        a2 = R(0.5) * (pos(-Fe2) - Fe2 * pe2 + pos(-Fe1) - Fe1 * pe1) + Dxe;
-        a3 = pos(Fbs) - Fbs * ps + R(4.0 / 3.0) * Dys;
-        a4 = pos(-Fbn) - Fbn * pn + R(4.0 / 3.0) * Dyn;
+        if constexpr (TVD) {
+            a1 = R(0.5) * (pos(Fw2) - Fw2 * pw2 + pos(Fw1) - Fw1 * pw1) + Dxw;
+            a2 = R(0.5) * (pos(-Fe2) - Fe2 * pe2 + pos(-Fe1) - Fe1 * pe1) + Dxe;
+            a3 = pos(Fbs) - Fbs * ps + R(4.0 / 3.0) * Dys;
+            a4 = pos(-Fbn) - Fbn * pn + R(4.0 / 3.0) * Dyn;
+        } else {                                   // upwind: psi = 0
+            a1 = R(0.5) * (pos(Fw2) + pos(Fw1)) + Dxw;
+            a2 = R(0.5) * (pos(-Fe2) + pos(-Fe1)) + Dxe;
+            a3 = pos(Fbs) + R(4.0 / 3.0) * Dys;
+            a4 = pos(-Fbn) + R(4.0 / 3.0) * Dyn;
+        }
         a0 = a1 + a2 + a3 + a4 + R(0.5) * (Fe2 - Fw2 + Fe1 - Fw1) + Fbn - Fbs + trans;
         vexp = R(0);
     } else {
@@ -586,7 +611,9 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
         vexp = w.vexp[b];
     }
     const R r = recip(a0);
-    vhat = (a1 * vW + a2 * vE + a3 * vS + a4 * vN + bsrc + vexp) * r;
+    R src = a1 * vW + a2 * vE + a3 * vS + a4 * vN + bsrc;
+    if constexpr (!IMPL) src += vexp;
+    vhat = src * r;
     dv = k.A * dxi * r;
 }
 
