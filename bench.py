@@ -318,32 +318,38 @@ def run_ours(args, rank, world, local_rank):
     prof = s.profile_read()
     s.profile(False)
 
-    # the same workload and timing protocol with the mixed-precision sweep
-    # (FP32 assembly and relaxation; FP64 pressure accumulation, EOS and
-    # residuals), and its per-field error against the FP64 path after the
-    # same number of steps from the same start
+    # the same workload and timing protocol with the other precisions of the
+    # sweep, and their per-field error against the FP64 path after the same
+    # number of steps from the same start
     import workloads as W
-    sm = sim.Simulation(case.replace(precision=W.MIXED), stream=stream.cuda_stream)
-    for _ in range(args.warmup):
-        sm.step(1)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    mixed_ms = timed_steps(sm, args.steps, stream, flush, starts, ends)
-    mixed_state = sm.fields()
-    sm.profile(True, timing=True)
-    timed_steps(sm, prof_steps, stream, flush, starts, ends)
-    mprof = sm.profile_read()
-    sm.profile(False)
-    sm.close()
-    mixed_ms = reduce_max(mixed_ms, dist, "cuda")
-    mixed_err = {k: float(np.abs(mixed_state[k] - fp64_state[k]).max() / np.abs(fp64_state[k]).max())
-                 for k in ("u", "v", "p", "T")}
-    mixed = {"value": round(throughput(case.cells, args.steps, world, mixed_ms * 1e-3), 3),
-             "ms_per_step": round(mixed_ms / args.steps, 5), "dtype": "f32 assembly / f64 pressure, EOS, residuals",
-             "max_rel_err_vs_fp64": {k: float(f"{v:.3e}") for k, v in mixed_err.items()},
-             "error_after_steps": args.warmup + args.steps,
-             "kernel_ms_avg": {k: round(ms / n, 5) for k, (ms, n) in mprof.items() if n}}
+
+    def variant(precision, dtype):
+        sv = sim.Simulation(case.replace(precision=precision), stream=stream.cuda_stream)
+        for _ in range(args.warmup):
+            sv.step(1)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        v_ms = timed_steps(sv, args.steps, stream, flush, starts, ends)
+        v_state = sv.fields()
+        sv.profile(True, timing=True)
+        timed_steps(sv, prof_steps, stream, flush, starts, ends)
+        vprof = sv.profile_read()
+        sv.profile(False)
+        sv.close()
+        v_ms = reduce_max(v_ms, dist, "cuda")
+        err = {k: float(np.abs(v_state[k] - fp64_state[k]).max() / np.abs(fp64_state[k]).max())
+               for k in ("u", "v", "p", "T")}
+        return {"value": round(throughput(case.cells, args.steps, world, v_ms * 1e-3), 3),
+                "ms_per_step": round(v_ms / args.steps, 5), "dtype": dtype,
+                "max_rel_err_vs_fp64": {k: float(f"{x:.3e}") for k, x in err.items()},
+                "error_after_steps": args.warmup + args.steps,
+                "kernel_ms_avg": {k: round(ms / n, 5) for k, (ms, n) in vprof.items() if n}}
+
+    # FP32 assembly and relaxation; FP64 pressure accumulation, EOS and residuals
+    mixed = variant(W.MIXED, "f32 assembly / f64 pressure, EOS, residuals")
+    # every kernel in double-float (pairs of floats) on the FP32 pipe
+    df64 = variant(W.DF64, "df64 (float pairs, about 48 bits) in every kernel; f64 state on read-out")
 
     # end to end through the C ABI with host buffers: every step uploads its
     # input state from pinned host memory and reads the new state and the
@@ -420,7 +426,7 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": int(launches),
             "kernel_ms_avg": {k: round(ms / n, 5) for k, (ms, n) in prof.items() if n},
             "kernel_timing": f"separate pass of {prof_steps} steps with per-launch CUDA events",
-            "roofline": roof, "mixed": mixed, "batched": batched, "cpu_baseline": cpu, "clocks": csum,
+            "roofline": roof, "mixed": mixed, "df64": df64, "batched": batched, "cpu_baseline": cpu, "clocks": csum,
             "residuals_last_step": [float(x) for x in res], "impl": "ours"}
     print(json.dumps(line), flush=True)
     if dist:

@@ -58,7 +58,7 @@ enum { SIM_GAS_IDEAL_RE = 0, SIM_GAS_HARD_SPHERE_KN = 1 };
 /* scheme flags for sim_step: time treatment of convection | spatial scheme */
 enum { SIM_EXPLICIT = 0, SIM_IMPLICIT = 1, SIM_UPWIND = 0, SIM_TVD = 2 };
 /* arithmetic of the sweep */
-enum { SIM_FP64 = 0, SIM_MIXED = 1 };
+enum { SIM_FP64 = 0, SIM_MIXED = 1, SIM_DF64 = 2 };
 /* field ids */
 enum { SIM_FIELD_U = 0, SIM_FIELD_V = 1, SIM_FIELD_P = 2, SIM_FIELD_T = 3,
        SIM_FIELD_RHO = 4, SIM_FIELD_GAMMA = 5 };
@@ -103,7 +103,11 @@ typedef struct {
  * seed, perturb: start state = inflow state of the row (rest when W is not an
  *   inflow) times (1 + perturb xi), xi in [-1, 1) from splitmix64 of
  *   (seed ^ (field<<40 + j<<20 + i)); v = perturb U_in xi.
- * precision: SIM_FP64 or SIM_MIXED. */
+ * precision: SIM_FP64; SIM_MIXED (FP32 assembly and relaxation, FP64
+ *   pressure accumulation, equation of state and residuals); SIM_DF64 (every
+ *   kernel of the iteration in double-float arithmetic -- pairs of floats,
+ *   about 48 significant bits -- on the FP32 pipe; the FP64 state is filled
+ *   from it when read, and the residual maxima carry FP32 precision). */
 typedef struct {
     int side_kind[4];
     double side_vel[4];
@@ -145,7 +149,10 @@ sim_status sim_fields(sim_t sim, int field, double *host_dst, size_t n);
 /* Borrow the device array of one field of the current state.  *dev receives
  * the address of element (i, j) = (0, 0); element (i, j) is at
  * dev[j * (*pitch) + i] for -2 <= i, j (two ghost layers).  Valid until the
- * next sim_step, sim_set_fields or sim_destroy.  Errors: SIM_EINVAL. */
+ * next sim_step, sim_set_fields or sim_destroy.  SIM_DF64: the FP64 array is
+ * refreshed from the double-float state by work queued on the handle's
+ * stream; synchronise with that stream before reading it elsewhere.
+ * Errors: SIM_EINVAL. */
 sim_status sim_field_ptr(sim_t sim, int field, void **dev, size_t *pitch);
 
 /* Overwrite the unknowns of one field (u, v, p or T; logical shape) of the

@@ -26,7 +26,7 @@ SIM_W, SIM_E, SIM_S, SIM_N = range(4)
 SIM_BC_WALL, SIM_BC_SYMMETRY, SIM_BC_INFLOW, SIM_BC_OUTFLOW = range(4)
 SIM_GAS_IDEAL_RE, SIM_GAS_HARD_SPHERE_KN = range(2)
 SIM_EXPLICIT, SIM_IMPLICIT, SIM_UPWIND, SIM_TVD = 0, 1, 0, 2
-SIM_FP64, SIM_MIXED = 0, 1
+SIM_FP64, SIM_MIXED, SIM_DF64 = 0, 1, 2
 FIELDS = {"u": 0, "v": 1, "p": 2, "T": 3, "rho": 4, "gamma": 5}
 KERNELS = {"faces": 0, "assemble": 1, "pressure": 2, "velocity": 3, "ghosts": 4, "explicit": 5}
 STATUS = {0: "SIM_OK", 1: "SIM_EINVAL", 2: "SIM_ENOMEM", 3: "SIM_ECUDA", 4: "SIM_EDIVERGED",

@@ -57,6 +57,13 @@ struct sim_s {
     Mixed mx{};
     float *d_pool32 = nullptr;
     float *d_axis32 = nullptr;
+    // double-float precision: working levels, scratch and grid factors; the
+    // FP64 levels are refreshed from them when the state is read out
+    bool df = false;
+    bool df_dirty = false;                     // the FP64 levels lag behind the double-float ones
+    DoubleFloat dfm{};
+    df64 *d_pooldf = nullptr;
+    df64 *d_axisdf = nullptr;
     // the one-problem tile list the equation kernels walk (32 x 8 tiles)
     Inst *d_inst = nullptr;
     int *d_tiles = nullptr;
@@ -187,7 +194,8 @@ sim_status read_problem(const sim_grid *gr, const sim_gas *gas, const sim_bc *bc
     }
     if (bc->iters < 1) return fail(err, SIM_EINVAL, "iters must be >= 1");
     if (!(bc->tol >= 0.0)) return fail(err, SIM_EINVAL, "tol must be >= 0");
-    if (bc->precision != SIM_FP64 && bc->precision != SIM_MIXED) return fail(err, SIM_EINVAL, "unknown precision");
+    if (bc->precision != SIM_FP64 && bc->precision != SIM_MIXED && bc->precision != SIM_DF64)
+        return fail(err, SIM_EINVAL, "unknown precision");
     pb.iters = bc->iters;
     pb.tol = bc->tol;
     pb.seed = bc->seed;
@@ -409,10 +417,39 @@ Inst inst_of(const sim_s *s, int tx, int tile0)
     }
     I.w = s->work;
     I.w32 = s->mx.w;
+    I.gdf = s->dfm.g;
+    I.kdf = s->dfm.k;
+    for (int l = 0; l < 3; l++) I.lvdf[l] = s->dfm.lv[l];
+    I.wdf = s->dfm.w;
     I.east_outflow = s->pb.side_kind[SIM_E] == SIM_BC_OUTFLOW;
     I.tiles_x = (s->pb.nx + 1 + tx - 1) / tx;
     I.tile0 = tile0;
     return I;
+}
+
+int prec_of(const sim_s *s) { return s->mixed ? PREC_MIXED : s->df ? PREC_DF64 : PREC_FP64; }
+
+// Carve three state levels and the iteration scratch out of one pool.
+template <typename R>
+R *carve_levels(R *q, size_t nelem, LevelT<R> lv[3], WorkT<R> &w)
+{
+    for (int l = 0; l < 3; l++) {
+        R **f[6] = {&lv[l].u, &lv[l].v, &lv[l].p, &lv[l].T, &lv[l].rho, &lv[l].gam};
+        for (R **x : f) { *x = q; q += nelem; }
+    }
+    R **a[16] = {&w.rho_u, &w.rho_v, &w.Fx, &w.Fy, &w.DTx, &w.DTy, &w.Bgc, &w.Bgx, &w.Bgy,
+                 &w.uhat, &w.du, &w.vhat, &w.dv, &w.uexp, &w.vexp, &w.Texp};
+    for (R **x : a) { *x = q; q += nelem; }
+    return q;
+}
+
+// The FP64 levels of the current state, brought up to date in DF64 mode.
+void sync_out(sim_t s)
+{
+    if (s->df && s->df_dirty) {
+        launch_join(s->dfm.lv[s->cur], s->lv[s->cur], s->nelem, s->stream);
+        s->df_dirty = false;
+    }
 }
 
 int tiles_of(const sim_s *s, int tx, int ty)
@@ -468,8 +505,8 @@ struct Launch {
 // (explicit scheme only, once per step).  counts != nullptr: capture mode.
 void enqueue_explicit(sim_t s, int prev, bool tvd, cudaStream_t st, long long *counts)
 {
-    { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, s->mixed, prev, tvd, st); }
-    { Launch l(s, SIM_K_EXPLICIT, st, counts); launch_explicit(s->plan, s->mixed, prev, tvd, st); }
+    { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, prec_of(s), prev, tvd, st); }
+    { Launch l(s, SIM_K_EXPLICIT, st, counts); launch_explicit(s->plan, prec_of(s), prev, tvd, st); }
 }
 
 // One loop-2 iteration from level `old` (level `prev` holds n-1) into the
@@ -480,14 +517,19 @@ int enqueue_iteration(sim_t s, int prev, int old, bool implicit, bool tvd, cudaS
     if (nw == prev) nw = (nw + 1) % 3;
     const int ng = ghost_kernels(s->sides, true);
     cudaMemsetAsync(s->work.res, 0, 4 * sizeof(unsigned long long), st);
-    { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, s->mixed, old, tvd, st); }
-    { Launch l(s, SIM_K_ASSEMBLE, st, counts); launch_assemble(s->plan, s->mixed, prev, old, nw, implicit, tvd, st); }
-    { Launch l(s, SIM_K_PRESSURE, st, counts); launch_pressure(s->plan, s->mixed, prev, old, nw, st); }
-    { Launch l(s, SIM_K_VELOCITY, st, counts); launch_velocity(s->plan, s->mixed, old, nw, st); }
+    const int prec = prec_of(s);
+    { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, prec, old, tvd, st); }
+    { Launch l(s, SIM_K_ASSEMBLE, st, counts); launch_assemble(s->plan, prec, prev, old, nw, implicit, tvd, st); }
+    { Launch l(s, SIM_K_PRESSURE, st, counts); launch_pressure(s->plan, prec, prev, old, nw, st); }
+    { Launch l(s, SIM_K_VELOCITY, st, counts); launch_velocity(s->plan, prec, old, nw, st); }
     if (ng) {
         Launch l(s, SIM_K_GHOSTS, st, counts, s->mixed ? 2 * ng : ng);
-        launch_ghosts(s->geo, s->sides, s->lv[nw], true, st);
-        if (s->mixed) launch_ghosts_f32(s->mx, s->sides, nw, true, st);
+        if (s->df) {
+            launch_ghosts_df(s->dfm, s->sides, nw, true, st);
+        } else {
+            launch_ghosts(s->geo, s->sides, s->lv[nw], true, st);
+            if (s->mixed) launch_ghosts_f32(s->mx, s->sides, nw, true, st);
+        }
     }
     return nw;
 }
@@ -646,6 +688,32 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         CUDA_TRY(s, cudaMemsetAsync(s->mx.w.rho_u, 0, 16 * s->nelem * sizeof(float), s->stream));
     }
 
+    s->df = pb.precision == SIM_DF64;
+    if (s->df) {
+        if (cudaMalloc(&s->d_pooldf, 34 * s->nelem * sizeof(df64)) != cudaSuccess ||
+            cudaMalloc(&s->d_axisdf, (nax + nay) * sizeof(df64)) != cudaSuccess) {
+            sim_destroy(s);
+            return SIM_ENOMEM;
+        }
+        carve_levels(s->d_pooldf, s->nelem, s->dfm.lv, s->dfm.w);
+        const df64 *fx = s->d_axisdf, *fy = s->d_axisdf + nax;
+        s->dfm.g.nx = pb.nx;
+        s->dfm.g.ny = pb.ny;
+        s->dfm.g.pitch = s->pitch;
+        s->dfm.g.flag = s->d_flag;
+        s->dfm.g.x = AxisT<df64>{fx, fx + mx, fx + 2 * mx, fx + 3 * mx, fx + 4 * mx};
+        s->dfm.g.y = AxisT<df64>{fy, fy + my, fy + 2 * my, fy + 3 * my, fy + 4 * my};
+        const Coef &k = pb.k;
+        s->dfm.k = CoefT<df64>{dfl::split_host(k.A), dfl::split_host(k.B), dfl::split_host(k.CT1f), dfl::split_host(k.CT2f),
+                               dfl::split_host(k.CT3f), dfl::split_host(k.omega), dfl::split_host(k.dt), dfl::split_host(k.gx),
+                               dfl::split_host(k.gy), dfl::split_host(k.hrdt)};
+        std::vector<df64> adf(nax + nay);
+        for (size_t q = 0; q < nax; q++) adf[q] = dfl::split_host(ax[q]);
+        for (size_t q = 0; q < nay; q++) adf[nax + q] = dfl::split_host(ay[q]);
+        CUDA_TRY(s, cudaMemcpy(s->d_axisdf, adf.data(), adf.size() * sizeof(df64), cudaMemcpyHostToDevice));
+        CUDA_TRY(s, cudaMemsetAsync(s->dfm.w.rho_u, 0, 16 * s->nelem * sizeof(df64), s->stream));
+    }
+
     std::vector<double> f[6];
     for (auto &a : f) a.assign(s->nelem, 0.0);
     build_start_level(pb, h, f);
@@ -663,6 +731,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         launch_derive(s->geo, pb.k, s->lv[l], s->stream);
         launch_ghosts(s->geo, s->sides, s->lv[l], false, s->stream);
         if (s->mixed) launch_shadow(s->geo, s->lv[l], s->mx.lv[l], s->nelem, s->stream);
+        if (s->df) launch_split(s->lv[l], s->dfm.lv[l], s->nelem, s->stream);
     }
     const Inst one = inst_of(s, 32, 0);
     const int ntiles = tiles_of(s, 32, 8);
@@ -687,6 +756,7 @@ extern "C" sim_status sim_step(sim_t s, int n_steps, int scheme)
     if (n_steps < 0 || (scheme & ~3)) return fail(s, SIM_EINVAL, "bad n_steps %d or scheme %d", n_steps, scheme);
     const bool implicit = scheme & SIM_IMPLICIT, tvd = scheme & SIM_TVD;
     const Problem &pb = s->pb;
+    if (n_steps > 0 && s->df) s->df_dirty = true;
 
     // Fixed loop-2 length and no event timing: replay one captured graph per
     // step (the three state levels rotate, so a step graph exists for each
@@ -764,6 +834,7 @@ extern "C" sim_status sim_fields(sim_t s, int field, double *host_dst, size_t n)
     if (field < 0 || field > 5 || !host_dst) return fail(s, SIM_EINVAL, "bad field %d or null destination", field);
     const size_t need = field_count(s->pb, field);
     if (n != need) return fail(s, SIM_EINVAL, "field %d has %zu elements, got %zu", field, need, n);
+    sync_out(s);
     launch_gather(s->geo, field, s->lv[s->cur], s->d_stage, s->stream);
     CUDA_TRY(s, cudaGetLastError());
     CUDA_TRY(s, cudaMemcpyAsync(host_dst, s->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -775,6 +846,7 @@ extern "C" sim_status sim_field_ptr(sim_t s, int field, void **dev, size_t *pitc
 {
     if (!s) return SIM_EINVAL;
     if (field < 0 || field > 5 || !dev || !pitch) return fail(s, SIM_EINVAL, "bad field %d or null output", field);
+    sync_out(s);
     *dev = level_field(s->lv[s->cur], field) + (size_t)G * s->pitch + G;
     *pitch = (size_t)s->pitch;
     return SIM_OK;
@@ -789,12 +861,14 @@ extern "C" sim_status sim_set_fields(sim_t s, int field, const double *host_src,
     for (size_t q = 0; q < n; q++)
         if (!std::isfinite(host_src[q]) || ((field == SIM_FIELD_T || field == SIM_FIELD_P) && !(host_src[q] > 0.0)))
             return fail(s, SIM_EINVAL, "field %d: value %zu is not admissible", field, q);
+    sync_out(s);
     const Level &L = s->lv[s->cur];
     CUDA_TRY(s, cudaMemcpyAsync(s->d_stage, host_src, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     launch_scatter(s->geo, field, s->d_stage, L, s->stream);
     launch_derive(s->geo, s->pb.k, L, s->stream);
     launch_ghosts(s->geo, s->sides, L, false, s->stream);
     if (s->mixed) launch_shadow(s->geo, L, s->mx.lv[s->cur], s->nelem, s->stream);
+    if (s->df) launch_split(L, s->dfm.lv[s->cur], s->nelem, s->stream);
     CUDA_TRY(s, cudaGetLastError());
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
     if (s->diverged) {
@@ -885,6 +959,8 @@ extern "C" void sim_destroy(sim_t s)
     cudaFree(s->d_axis32);
     cudaFree(s->d_inst);
     cudaFree(s->d_tiles);
+    cudaFree(s->d_pooldf);
+    cudaFree(s->d_axisdf);
     if (s->h_res) cudaFreeHost(s->h_res);
     for (auto &m : s->marks) {
         cudaEventDestroy(m.e0);
@@ -904,6 +980,7 @@ struct sim_batch_s {
     std::vector<sim_t> inst;
     cudaStream_t stream = nullptr;
     bool mixed = false;
+    int prec = PREC_FP64;
     int iters = 1;
     Inst *d_inst = nullptr;
     int *d_tiles = nullptr;
@@ -980,23 +1057,27 @@ int enqueue_batch_step(sim_batch_t b, int prev, bool implicit, bool tvd, cudaStr
 {
     const BatchPlan &bp = b->plan;
     if (!implicit) {
-        launch_faces(bp, b->mixed, prev, tvd, st);
-        launch_explicit(bp, b->mixed, prev, tvd, st);
+        launch_faces(bp, b->prec, prev, tvd, st);
+        launch_explicit(bp, b->prec, prev, tvd, st);
     }
     int old = prev;
     for (int it = 1; it <= b->iters; it++) {
         int nw = (old + 1) % 3;
         if (nw == prev) nw = (nw + 1) % 3;
         launch_zero_res(bp, st);
-        launch_faces(bp, b->mixed, old, tvd, st);
-        launch_assemble(bp, b->mixed, prev, old, nw, implicit, tvd, st);
-        launch_pressure(bp, b->mixed, prev, old, nw, st);
-        launch_velocity(bp, b->mixed, old, nw, st);
+        launch_faces(bp, b->prec, old, tvd, st);
+        launch_assemble(bp, b->prec, prev, old, nw, implicit, tvd, st);
+        launch_pressure(bp, b->prec, prev, old, nw, st);
+        launch_velocity(bp, b->prec, old, nw, st);
         if (b->ghosts)
             for (sim_t s : b->inst)
                 if (ghost_kernels(s->sides, true)) {
-                    launch_ghosts(s->geo, s->sides, s->lv[nw], true, st);
-                    if (b->mixed) launch_ghosts_f32(s->mx, s->sides, nw, true, st);
+                    if (s->df) {
+                        launch_ghosts_df(s->dfm, s->sides, nw, true, st);
+                    } else {
+                        launch_ghosts(s->geo, s->sides, s->lv[nw], true, st);
+                        if (b->mixed) launch_ghosts_f32(s->mx, s->sides, nw, true, st);
+                    }
                 }
         old = nw;
     }
@@ -1009,6 +1090,7 @@ void set_levels(sim_batch_t b, int cur)
     for (sim_t s : b->inst) {
         s->cur = cur;
         s->last_iters = b->iters;
+        if (s->df) s->df_dirty = true;
     }
 }
 
@@ -1028,6 +1110,7 @@ extern "C" sim_status sim_batch_create(int n, const sim_grid *grids, const sim_g
     if (!b) return SIM_ENOMEM;
     b->stream = (cudaStream_t)stream;
     b->mixed = bcs[0].precision == SIM_MIXED;
+    b->prec = b->mixed ? PREC_MIXED : bcs[0].precision == SIM_DF64 ? PREC_DF64 : PREC_FP64;
     b->iters = bcs[0].iters;
     for (int q = 0; q < n; q++) {
         sim_t s = nullptr;
@@ -1095,7 +1178,8 @@ extern "C" sim_status sim_batch_tune(sim_batch_t b, int scheme, int out[3])
     // keep a copy of every problem's current level (FP64 and FP32 shadow) and
     // residual words, so that tuning leaves the simulation where it was
     size_t total = 0;
-    for (sim_t s : b->inst) total += 6 * s->nelem * (sizeof(double) + (b->mixed ? sizeof(float) : 0)) + 32;
+    const size_t shadow = b->mixed ? sizeof(float) : b->prec == PREC_DF64 ? sizeof(df64) : 0;
+    for (sim_t s : b->inst) total += 6 * s->nelem * (sizeof(double) + shadow) + 32;
     unsigned char *save = nullptr;
     if (cudaMalloc(&save, total) != cudaSuccess) return bfail(b, SIM_ENOMEM, "no memory for the tuning copy");
     const int start = b->cur;
@@ -1116,6 +1200,15 @@ extern "C" sim_status sim_batch_tune(sim_batch_t b, int scheme, int out[3])
                                 : cudaMemcpyAsync(f32, p, n32, cudaMemcpyDeviceToDevice, b->stream);
                     if (e != cudaSuccess) return e;
                     p += n32;
+                }
+                if (b->prec == PREC_DF64) {
+                    const LevelT<df64> &L = s->dfm.lv[start];
+                    df64 *fd = f == 0 ? L.u : f == 1 ? L.v : f == 2 ? L.p : f == 3 ? L.T : f == 4 ? L.rho : L.gam;
+                    const size_t nd = s->nelem * sizeof(df64);
+                    e = to_save ? cudaMemcpyAsync(p, fd, nd, cudaMemcpyDeviceToDevice, b->stream)
+                                : cudaMemcpyAsync(fd, p, nd, cudaMemcpyDeviceToDevice, b->stream);
+                    if (e != cudaSuccess) return e;
+                    p += nd;
                 }
             }
             cudaError_t e = to_save ? cudaMemcpyAsync(p, s->work.res, 32, cudaMemcpyDeviceToDevice, b->stream)

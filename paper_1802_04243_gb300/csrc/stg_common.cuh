@@ -11,7 +11,11 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "df64.cuh"
+
 namespace stg {
+
+using dfl::df64;
 
 constexpr int G = 2;
 
@@ -95,16 +99,33 @@ struct Mixed {
     WorkT<float> w;
 };
 
+// Double-float side of the DF64 sweep: grid factors, coefficients, the three
+// working state levels and the iteration scratch, all double-float.  The FP64
+// levels are filled from them only when the state is read out.
+struct DoubleFloat {
+    GeoT<df64> g;
+    CoefT<df64> k;
+    LevelT<df64> lv[3];
+    WorkT<df64> w;
+};
+
+// Arithmetic of the equation kernels.
+enum { PREC_FP64 = 0, PREC_MIXED = 1, PREC_DF64 = 2 };
+
 // One problem of a tile list, as the equation kernels see it (device resident).
 struct Inst {
     Geo g;
     Coef k;
     GeoT<float> g32;
     CoefT<float> k32;
+    GeoT<df64> gdf;
+    CoefT<df64> kdf;
     Level lv[3];
     LevelT<float> lv32[3];
+    LevelT<df64> lvdf[3];
     Work w;
     WorkT<float> w32;
+    WorkT<df64> wdf;
     int east_outflow;
     int tiles_x;          // tiles along x for the batch's tile shape
     int tile0;            // index of this problem's first tile in the batch
@@ -131,20 +152,22 @@ enum { BC_WALL = 0, BC_SYMMETRY = 1, BC_INFLOW = 2, BC_OUTFLOW = 3 };
 // Launch wrappers (sweep_kernels.cu).  All are asynchronous on `stream`.
 //
 // Equation kernels: one launch per phase over a tile list (one problem or a
-// batch).  `mixed` selects the FP32 assembly of the mixed-precision path;
-// levels are indices into Inst::lv / Inst::lv32.
+// batch).  `prec` (PREC_*) selects the arithmetic: FP64; the FP32 assembly
+// of the mixed-precision path; double-float.  Levels are indices into
+// Inst::lv / lv32 / lvdf.
 void launch_zero_res(const BatchPlan &bp, void *stream);
-void launch_faces(const BatchPlan &bp, bool mixed, int level, bool tvd, void *stream);
-void launch_explicit(const BatchPlan &bp, bool mixed, int prev, bool tvd, void *stream);
-void launch_assemble(const BatchPlan &bp, bool mixed, int prev, int old, int nw, bool implicit, bool tvd,
+void launch_faces(const BatchPlan &bp, int prec, int level, bool tvd, void *stream);
+void launch_explicit(const BatchPlan &bp, int prec, int prev, bool tvd, void *stream);
+void launch_assemble(const BatchPlan &bp, int prec, int prev, int old, int nw, bool implicit, bool tvd,
                      void *stream);
-void launch_pressure(const BatchPlan &bp, bool mixed, int prev, int old, int nw, void *stream);
-void launch_velocity(const BatchPlan &bp, bool mixed, int old, int nw, void *stream);
+void launch_pressure(const BatchPlan &bp, int prec, int prev, int old, int nw, void *stream);
+void launch_velocity(const BatchPlan &bp, int prec, int old, int nw, void *stream);
 
 // Ghost copies of outflow and symmetry sides.  after_velocity: the velocity
 // kernel has already copied the outflow side, only symmetry sides remain.
 void launch_ghosts(const Geo &g, const Sides &s, const Level &lv, bool after_velocity, void *stream);
 void launch_ghosts_f32(const Mixed &m, const Sides &s, int level, bool after_velocity, void *stream);
+void launch_ghosts_df(const DoubleFloat &d, const Sides &s, int level, bool after_velocity, void *stream);
 int ghost_kernels(const Sides &s, bool after_velocity);
 
 // State maintenance.
@@ -152,6 +175,9 @@ void launch_derive(const Geo &g, const Coef &c, const Level &lv, void *stream);
 void launch_scatter(const Geo &g, int field, const double *src, const Level &lv, void *stream);
 void launch_gather(const Geo &g, int field, const Level &lv, double *dst, void *stream);
 void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, size_t nelem, void *stream);
+// Whole-level conversions between FP64 and double-float (ghosts included).
+void launch_split(const Level &lv, const LevelT<df64> &d, size_t nelem, void *stream);
+void launch_join(const LevelT<df64> &d, const Level &lv, size_t nelem, void *stream);
 
 // The FP64 reciprocal of the sweep (Newton-Raphson from an FP32 seed) and the
 // IEEE quotient 1/x of each x[q], interleaved in out[2q], out[2q+1].

@@ -2,7 +2,9 @@
 // (K. S. Shterev, arXiv:1802.04243, Sections 3.1 and 3.2) for sm_103a.
 // The equation kernels are templated on the arithmetic type: double for the
 // FP64 path, float for the FP32 assembly of the mixed-precision path (whose
-// pressure accumulation, equation of state and residuals stay FP64).
+// pressure accumulation, equation of state and residuals stay FP64), and
+// df64 (double-float, df64.cuh) for the DF64 path, which runs the whole
+// iteration on the FP32 pipe.
 //
 // One loop-2 iteration (Section 3.1, Figs. 1 and 2, GPU column) runs as
 //   k_faces      rho^u, rho^v, mass fluxes and conductivities of every face (Eqs. pl8-pl11, pl33)
@@ -21,6 +23,8 @@
 // where the flag of the face says all four stencil nodes are unknowns.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <type_traits>
 
 #include "stg_common.cuh"
 
@@ -42,6 +46,7 @@ __device__ __forceinline__ R at(const R *a, int i) { return a[i + G]; }
 // GB300's narrow FP64 pipe.  (NaN inputs may take either branch.)
 __device__ __forceinline__ bool positive(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool positive(float x) { return __float_as_int(x) > 0; }
+__device__ __forceinline__ bool positive(df64 x) { return x.hi > 0.0f; }    // normalised: lo is 0 when hi is
 
 // ---------------------------------------------------------------- limiter
 
@@ -196,6 +201,20 @@ __device__ __forceinline__ double recip(double a)
     r = fma(r, fma(-a, r, 1.0), r);
     r = fma(r, fma(-a, r, 1.0), r);
     return r;
+}
+
+// Residual key |d| of a difference held in the compute precision (a
+// double-float difference is keyed by its leading float).
+__device__ __forceinline__ unsigned long long res_key(double d) { return ordered(d); }
+__device__ __forceinline__ unsigned long long res_key(df64 d) { return ordered_bits(widen(d.hi)); }
+
+// Gamma = T^omega (power-law transport coefficients): the square root for
+// omega = 1/2, the general power otherwise (double-float: through FP64).
+__device__ __forceinline__ double gamma_of(double T, double omega) { return omega == 0.5 ? sqrt(T) : pow(T, omega); }
+__device__ __forceinline__ df64 gamma_of(df64 T, df64 omega)
+{
+    if (omega.hi == 0.5f && omega.lo == 0.0f) return sqrt(T);
+    return dfl::split_dev(pow(dfl::join(T), dfl::join(omega)));
 }
 
 // T conductance of the face between a node of size da and one of size db
@@ -619,18 +638,15 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
 
 template <typename R, bool IMPL, bool TVD, bool WALLS>
 __device__ __forceinline__ void assemble_at(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev,
-                                            const LevelT<R> &old, double *__restrict__ T_out,
-                                            float *__restrict__ T32_out, const WorkT<R> &w, int c, uint16_t f,
+                                            const LevelT<R> &old, R *__restrict__ T_out,
+                                            double *__restrict__ T64_out, const WorkT<R> &w, int c, uint16_t f,
                                             int i, int j)
 {
     if (i < g.nx && j < g.ny && (f & F_FLUID)) {
         const R Tn = temperature<R, IMPL, TVD, WALLS>(g, k, prev, old, w, c, i, j);
-        if constexpr (sizeof(R) == 4) {
-            T_out[c] = widen(Tn);
-            T32_out[c] = Tn;
-        } else {
-            T_out[c] = Tn;
-        }
+        T_out[c] = Tn;
+        if constexpr (std::is_same<R, float>::value)
+            T64_out[c] = widen(Tn);
     }
     if (j < g.ny) {
         R uh = old.u[c], d = R(0);            // faces that are not unknowns: stored u, d = 0
@@ -649,12 +665,12 @@ __device__ __forceinline__ void assemble_at(const GeoT<R> &g, const CoefT<R> &k,
 }
 
 // One thread per position: T of the cell, u^/d^u of the u face, v^/d^v of
-// the v face.  The new T goes to T_out (state precision) and, for the FP32
-// assembly of the mixed path, also to T32_out (the FP32 shadow copy).
+// the v face.  The new T goes to T_out (compute precision) and, for the FP32
+// assembly of the mixed path, also to T64_out (the FP64 state).
 template <typename R, bool IMPL, bool TVD>
 __device__ __forceinline__ void assemble_body(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev,
-                                              const LevelT<R> &old, double *__restrict__ T_out,
-                                              float *__restrict__ T32_out, const WorkT<R> &w, int i, int j)
+                                              const LevelT<R> &old, R *__restrict__ T_out,
+                                              double *__restrict__ T64_out, const WorkT<R> &w, int i, int j)
 {
     if (i > g.nx || j > g.ny) return;
     const int c = Ix{g.pitch}(i, j);
@@ -664,9 +680,9 @@ __device__ __forceinline__ void assemble_body(const GeoT<R> &g, const CoefT<R> &
     // position only, never on how threads form warps, so every tiling gives
     // the same bits; with 32-wide tiles it is uniform across each warp.
     if (f & F_INTERIOR)
-        assemble_at<R, IMPL, TVD, false>(g, k, prev, old, T_out, T32_out, w, c, f, i, j);
+        assemble_at<R, IMPL, TVD, false>(g, k, prev, old, T_out, T64_out, w, c, f, i, j);
     else
-        assemble_at<R, IMPL, TVD, true>(g, k, prev, old, T_out, T32_out, w, c, f, i, j);
+        assemble_at<R, IMPL, TVD, true>(g, k, prev, old, T_out, T64_out, w, c, f, i, j);
 }
 
 // ---------------------------------------------------------------- pressure
@@ -674,34 +690,36 @@ __device__ __forceinline__ void assemble_body(const GeoT<R> &g, const CoefT<R> &
 // Eqs. pl23, pl24 with the new T (point Jacobi in p^old), then rho = p/T
 // (Eq. pl5) and Gamma = T^omega, with the p and T residual maxima.  The
 // divisions by T and a^p_0 use the Newton-Raphson reciprocal.
-__device__ __forceinline__ void pressure_body(const Geo &g, const Coef &k, const Level &prev, const Level &old,
-                                              const Level &nw, const Work &w, int i, int j)
+template <typename R>
+__device__ __forceinline__ void pressure_body(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev,
+                                              const LevelT<R> &old, const LevelT<R> &nw, const WorkT<R> &w,
+                                              unsigned long long *res, int i, int j)
 {
     const int P = g.pitch;
     unsigned long long rp = 0, rT = 0;
     if (i < g.nx && j < g.ny) {
         const int c = Ix{P}(i, j);
         if (g.flag[c] & F_FLUID) {
-            const double dxi = at(g.x.d, i), dyj = at(g.y.d, j);
-            const double ru_w = w.rho_u[c], ru_e = w.rho_u[c + 1], rv_s = w.rho_v[c], rv_n = w.rho_v[c + P];
-            const double apw = ru_w * w.du[c] * dyj, ape = ru_e * w.du[c + 1] * dyj;
-            const double aps = rv_s * w.dv[c] * dxi, apn = rv_n * w.dv[c + P] * dxi;
-            const double bpw = ru_w * w.uhat[c] * dyj, bpe = ru_e * w.uhat[c + 1] * dyj;
-            const double bps = rv_s * w.vhat[c] * dxi, bpn = rv_n * w.vhat[c + P] * dxi;
-            const double Tn = nw.T[c], inv_T = recip(Tn);
-            const double vol = dxi * dyj;
-            const double ap0 = vol * inv_T + (apw + ape + aps + apn) * k.dt;
-            const double bp = prev.rho[c] * vol - (bpe - bpw + bpn - bps) * k.dt;
-            const double pn = ((apw * old.p[c - 1] + ape * old.p[c + 1] + aps * old.p[c - P] + apn * old.p[c + P]) * k.dt
-                               + bp) * recip(ap0);
+            const R dxi = at(g.x.d, i), dyj = at(g.y.d, j);
+            const R ru_w = w.rho_u[c], ru_e = w.rho_u[c + 1], rv_s = w.rho_v[c], rv_n = w.rho_v[c + P];
+            const R apw = ru_w * w.du[c] * dyj, ape = ru_e * w.du[c + 1] * dyj;
+            const R aps = rv_s * w.dv[c] * dxi, apn = rv_n * w.dv[c + P] * dxi;
+            const R bpw = ru_w * w.uhat[c] * dyj, bpe = ru_e * w.uhat[c + 1] * dyj;
+            const R bps = rv_s * w.vhat[c] * dxi, bpn = rv_n * w.vhat[c + P] * dxi;
+            const R Tn = nw.T[c], inv_T = recip(Tn);
+            const R vol = dxi * dyj;
+            const R ap0 = vol * inv_T + (apw + ape + aps + apn) * k.dt;
+            const R bp = prev.rho[c] * vol - (bpe - bpw + bpn - bps) * k.dt;
+            const R pn = ((apw * old.p[c - 1] + ape * old.p[c + 1] + aps * old.p[c - P] + apn * old.p[c + P]) * k.dt
+                          + bp) * recip(ap0);
             nw.p[c] = pn;
             nw.rho[c] = pn * inv_T;
-            nw.gam[c] = (k.omega == 0.5) ? sqrt(Tn) : pow(Tn, k.omega);
-            rp = ordered(pn - old.p[c]);
-            rT = ordered(Tn - old.T[c]);
+            nw.gam[c] = gamma_of(Tn, k.omega);
+            rp = res_key(pn - old.p[c]);
+            rT = res_key(Tn - old.T[c]);
         }
     }
-    block_max2(rp, rT, &w.res[2], &w.res[3]);
+    block_max2(rp, rT, &res[2], &res[3]);
 }
 
 // -------------------------------------------------------------- velocity
@@ -730,8 +748,10 @@ __device__ __forceinline__ void outflow_copy(int j, int ny, int c, LevelT<R> L)
 
 // Eqs. pl18, pl19: velocities of the face unknowns from the new pressure,
 // then the outflow ghost copies of the row.
-__device__ __forceinline__ void velocity_body(const Geo &g, const Level &old, const Level &nw, const Work &w,
-                                              int east_outflow, int i, int j)
+template <typename R>
+__device__ __forceinline__ void velocity_body(const GeoT<R> &g, const LevelT<R> &old, const LevelT<R> &nw,
+                                              const WorkT<R> &w, unsigned long long *res, int east_outflow, int i,
+                                              int j)
 {
     const int P = g.pitch;
     unsigned long long ru = 0, rv = 0;
@@ -739,19 +759,19 @@ __device__ __forceinline__ void velocity_body(const Geo &g, const Level &old, co
         const int c = Ix{P}(i, j);
         const uint16_t f = g.flag[c];
         if (j < g.ny && (f & F_UACT)) {
-            const double un = w.uhat[c] - w.du[c] * (nw.p[c] - nw.p[c - 1]);
+            const R un = w.uhat[c] - w.du[c] * (nw.p[c] - nw.p[c - 1]);
             nw.u[c] = un;
-            ru = ordered(un - old.u[c]);
+            ru = res_key(un - old.u[c]);
         }
         if (i < g.nx && (f & F_VACT)) {
-            const double vn = w.vhat[c] - w.dv[c] * (nw.p[c] - nw.p[c - P]);
+            const R vn = w.vhat[c] - w.dv[c] * (nw.p[c] - nw.p[c - P]);
             nw.v[c] = vn;
-            rv = ordered(vn - old.v[c]);
+            rv = res_key(vn - old.v[c]);
         }
         if (east_outflow && i == g.nx - 1)
             outflow_copy(j, g.ny, c, nw);
     }
-    block_max2(ru, rv, &w.res[0], &w.res[1]);
+    block_max2(ru, rv, &res[0], &res[1]);
 }
 
 // ------------------------------------------------------------ ghost copies
@@ -996,13 +1016,16 @@ __global__ void k_zero_res(BatchPlan bp)
     if (q < bp.n_inst * 4) bp.inst[q >> 2].w.res[q & 3] = 0ull;
 }
 
-template <bool MIXED, bool TVD>
+template <int PREC, bool TVD>
 __global__ void __launch_bounds__(256) k_faces(const __grid_constant__ BatchPlan bp, int level)
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
-        if constexpr (MIXED) {
+        if constexpr (PREC == PREC_MIXED) {
             const LevelT<float> &L = I.lv32[level];
             face_densities_body<float, TVD>(I.g32, I.k32, L.u, L.v, L.rho, L.gam, I.w32, i, j);
+        } else if constexpr (PREC == PREC_DF64) {
+            const LevelT<df64> &L = I.lvdf[level];
+            face_densities_body<df64, TVD>(I.gdf, I.kdf, L.u, L.v, L.rho, L.gam, I.wdf, i, j);
         } else {
             const Level &L = I.lv[level];
             face_densities_body<double, TVD>(I.g, I.k, L.u, L.v, L.rho, L.gam, I.w, i, j);
@@ -1010,50 +1033,84 @@ __global__ void __launch_bounds__(256) k_faces(const __grid_constant__ BatchPlan
     });
 }
 
-template <bool MIXED, bool TVD>
+template <int PREC, bool TVD>
 __global__ void __launch_bounds__(256) k_explicit(const __grid_constant__ BatchPlan bp, int prev)
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
-        if constexpr (MIXED)
+        if constexpr (PREC == PREC_MIXED)
             explicit_terms_body<float, TVD>(I.g32, I.lv32[prev], I.w32, i, j);
+        else if constexpr (PREC == PREC_DF64)
+            explicit_terms_body<df64, TVD>(I.gdf, I.lvdf[prev], I.wdf, i, j);
         else
             explicit_terms_body<double, TVD>(I.g, I.lv[prev], I.w, i, j);
     });
 }
 
-template <bool MIXED, bool IMPL, bool TVD>
+template <int PREC, bool IMPL, bool TVD>
 __global__ void __launch_bounds__(256) k_assemble(const __grid_constant__ BatchPlan bp, int prev, int old, int nw)
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
-        if constexpr (MIXED)
-            assemble_body<float, IMPL, TVD>(I.g32, I.k32, I.lv32[prev], I.lv32[old], I.lv[nw].T, I.lv32[nw].T, I.w32,
-                                           i, j);
+        if constexpr (PREC == PREC_MIXED)
+            assemble_body<float, IMPL, TVD>(I.g32, I.k32, I.lv32[prev], I.lv32[old], I.lv32[nw].T, I.lv[nw].T,
+                                           I.w32, i, j);
+        else if constexpr (PREC == PREC_DF64)
+            assemble_body<df64, IMPL, TVD>(I.gdf, I.kdf, I.lvdf[prev], I.lvdf[old], I.lvdf[nw].T, nullptr, I.wdf,
+                                          i, j);
         else
             assemble_body<double, IMPL, TVD>(I.g, I.k, I.lv[prev], I.lv[old], I.lv[nw].T, nullptr, I.w, i, j);
     });
 }
 
-template <bool MIXED>
+template <int PREC>
 __global__ void __launch_bounds__(256) k_pressure(const __grid_constant__ BatchPlan bp, int prev, int old, int nw)
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
-        if constexpr (MIXED)
+        if constexpr (PREC == PREC_MIXED)
             pressure_mixed_body(I.g, I.k, I.g32, I.k32, I.lv[prev], I.lv[old], I.lv[nw], I.lv32[old], I.lv32[nw],
                                 I.w32, I.w.res, i, j);
+        else if constexpr (PREC == PREC_DF64)
+            pressure_body<df64>(I.gdf, I.kdf, I.lvdf[prev], I.lvdf[old], I.lvdf[nw], I.wdf, I.w.res, i, j);
         else
-            pressure_body(I.g, I.k, I.lv[prev], I.lv[old], I.lv[nw], I.w, i, j);
+            pressure_body<double>(I.g, I.k, I.lv[prev], I.lv[old], I.lv[nw], I.w, I.w.res, i, j);
     });
 }
 
-template <bool MIXED>
+template <int PREC>
 __global__ void __launch_bounds__(256) k_velocity(const __grid_constant__ BatchPlan bp, int old, int nw)
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
-        if constexpr (MIXED)
+        if constexpr (PREC == PREC_MIXED)
             velocity_mixed_body(I.g, I.lv[nw], I.lv32[old], I.lv32[nw], I.w32, I.w.res, I.east_outflow, i, j);
+        else if constexpr (PREC == PREC_DF64)
+            velocity_body<df64>(I.gdf, I.lvdf[old], I.lvdf[nw], I.wdf, I.w.res, I.east_outflow, i, j);
         else
-            velocity_body(I.g, I.lv[old], I.lv[nw], I.w, I.east_outflow, i, j);
+            velocity_body<double>(I.g, I.lv[old], I.lv[nw], I.w, I.w.res, I.east_outflow, i, j);
     });
+}
+
+// Whole-level conversions FP64 <-> double-float, ghosts included.
+__global__ void k_split(Level L, LevelT<df64> D, size_t n)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        D.u[q] = dfl::split_dev(L.u[q]);
+        D.v[q] = dfl::split_dev(L.v[q]);
+        D.p[q] = dfl::split_dev(L.p[q]);
+        D.T[q] = dfl::split_dev(L.T[q]);
+        D.rho[q] = dfl::split_dev(L.rho[q]);
+        D.gam[q] = dfl::split_dev(L.gam[q]);
+    }
+}
+
+__global__ void k_join(LevelT<df64> D, Level L, size_t n)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        L.u[q] = dfl::join(D.u[q]);
+        L.v[q] = dfl::join(D.v[q]);
+        L.p[q] = dfl::join(D.p[q]);
+        L.T[q] = dfl::join(D.T[q]);
+        L.rho[q] = dfl::join(D.rho[q]);
+        L.gam[q] = dfl::join(D.gam[q]);
+    }
 }
 
 // ----------------------------------------------------- state maintenance
@@ -1159,6 +1216,30 @@ void launch_ghosts_f32(const Mixed &m, const Sides &sd, int level, bool after_ve
         k_ghost_sn<float><<<(m.g.nx + 2 * G + 1 + 127) / 128, 128, 0, s>>>(m.g, sd, m.lv[level]);
 }
 
+void launch_ghosts_df(const DoubleFloat &d, const Sides &sd, int level, bool after_velocity, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool we = (!after_velocity && sd.kind[SIDE_E] == BC_OUTFLOW) || sd.kind[SIDE_E] == BC_SYMMETRY ||
+                    sd.kind[SIDE_W] == BC_SYMMETRY;
+    const bool sn = sd.kind[SIDE_S] == BC_SYMMETRY || sd.kind[SIDE_N] == BC_SYMMETRY;
+    if (we)
+        k_ghost_we<df64><<<(d.g.ny + 1 + 127) / 128, 128, 0, s>>>(d.g, sd, d.lv[level]);
+    if (sn)
+        k_ghost_sn<df64><<<(d.g.nx + 2 * G + 1 + 127) / 128, 128, 0, s>>>(d.g, sd, d.lv[level]);
+}
+
+void launch_split(const Level &lv, const LevelT<df64> &d, size_t nelem, void *stream)
+{
+    const int blocks = (int)((nelem + 255) / 256 < 4096 ? (nelem + 255) / 256 : 4096);
+    k_split<<<blocks, 256, 0, (cudaStream_t)stream>>>(lv, d, nelem);
+}
+
+void launch_join(const LevelT<df64> &d, const Level &lv, size_t nelem, void *stream)
+{
+    const int blocks = (int)((nelem + 255) / 256 < 4096 ? (nelem + 255) / 256 : 4096);
+    k_join<<<blocks, 256, 0, (cudaStream_t)stream>>>(d, lv, nelem);
+}
+
 void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, size_t nelem, void *stream)
 {
     (void)g;
@@ -1191,58 +1272,69 @@ void launch_zero_res(const BatchPlan &bp, void *stream)
     k_zero_res<<<(bp.n_inst * 4 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(bp);
 }
 
-void launch_faces(const BatchPlan &bp, bool mixed, int level, bool tvd, void *stream)
+void launch_faces(const BatchPlan &bp, int prec, int level, bool tvd, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
     const dim3 bl(bp.tx, bp.ty);
-    if (mixed && tvd) k_faces<true, true><<<bp.grid, bl, 0, s>>>(bp, level);
-    else if (mixed) k_faces<true, false><<<bp.grid, bl, 0, s>>>(bp, level);
-    else if (tvd) k_faces<false, true><<<bp.grid, bl, 0, s>>>(bp, level);
-    else k_faces<false, false><<<bp.grid, bl, 0, s>>>(bp, level);
-}
-
-void launch_explicit(const BatchPlan &bp, bool mixed, int prev, bool tvd, void *stream)
-{
-    cudaStream_t s = (cudaStream_t)stream;
-    const dim3 bl(bp.tx, bp.ty);
-    if (mixed && tvd) k_explicit<true, true><<<bp.grid, bl, 0, s>>>(bp, prev);
-    else if (mixed) k_explicit<true, false><<<bp.grid, bl, 0, s>>>(bp, prev);
-    else if (tvd) k_explicit<false, true><<<bp.grid, bl, 0, s>>>(bp, prev);
-    else k_explicit<false, false><<<bp.grid, bl, 0, s>>>(bp, prev);
-}
-
-void launch_assemble(const BatchPlan &bp, bool mixed, int prev, int old, int nw, bool implicit, bool tvd,
-                           void *stream)
-{
-    cudaStream_t s = (cudaStream_t)stream;
-    const dim3 bl(bp.tx, bp.ty);
-    const int code = (mixed ? 4 : 0) | (implicit ? 2 : 0) | (tvd ? 1 : 0);
-    switch (code) {
-    case 7: k_assemble<true, true, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    case 6: k_assemble<true, true, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    case 5: k_assemble<true, false, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    case 4: k_assemble<true, false, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    case 3: k_assemble<false, true, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    case 2: k_assemble<false, true, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    case 1: k_assemble<false, false, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
-    default: k_assemble<false, false, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw); break;
+    switch (prec * 2 + (tvd ? 1 : 0)) {
+    case 5: k_faces<PREC_DF64, true><<<bp.grid, bl, 0, s>>>(bp, level); break;
+    case 4: k_faces<PREC_DF64, false><<<bp.grid, bl, 0, s>>>(bp, level); break;
+    case 3: k_faces<PREC_MIXED, true><<<bp.grid, bl, 0, s>>>(bp, level); break;
+    case 2: k_faces<PREC_MIXED, false><<<bp.grid, bl, 0, s>>>(bp, level); break;
+    case 1: k_faces<PREC_FP64, true><<<bp.grid, bl, 0, s>>>(bp, level); break;
+    default: k_faces<PREC_FP64, false><<<bp.grid, bl, 0, s>>>(bp, level); break;
     }
 }
 
-void launch_pressure(const BatchPlan &bp, bool mixed, int prev, int old, int nw, void *stream)
+void launch_explicit(const BatchPlan &bp, int prec, int prev, bool tvd, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
     const dim3 bl(bp.tx, bp.ty);
-    if (mixed) k_pressure<true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
-    else k_pressure<false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+    switch (prec * 2 + (tvd ? 1 : 0)) {
+    case 5: k_explicit<PREC_DF64, true><<<bp.grid, bl, 0, s>>>(bp, prev); break;
+    case 4: k_explicit<PREC_DF64, false><<<bp.grid, bl, 0, s>>>(bp, prev); break;
+    case 3: k_explicit<PREC_MIXED, true><<<bp.grid, bl, 0, s>>>(bp, prev); break;
+    case 2: k_explicit<PREC_MIXED, false><<<bp.grid, bl, 0, s>>>(bp, prev); break;
+    case 1: k_explicit<PREC_FP64, true><<<bp.grid, bl, 0, s>>>(bp, prev); break;
+    default: k_explicit<PREC_FP64, false><<<bp.grid, bl, 0, s>>>(bp, prev); break;
+    }
 }
 
-void launch_velocity(const BatchPlan &bp, bool mixed, int old, int nw, void *stream)
+template <int PREC>
+void assemble_variant(const BatchPlan &bp, int prev, int old, int nw, bool implicit, bool tvd, cudaStream_t s)
+{
+    const dim3 bl(bp.tx, bp.ty);
+    if (implicit && tvd) k_assemble<PREC, true, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+    else if (implicit) k_assemble<PREC, true, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+    else if (tvd) k_assemble<PREC, false, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+    else k_assemble<PREC, false, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+}
+
+void launch_assemble(const BatchPlan &bp, int prec, int prev, int old, int nw, bool implicit, bool tvd,
+                     void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == PREC_DF64) assemble_variant<PREC_DF64>(bp, prev, old, nw, implicit, tvd, s);
+    else if (prec == PREC_MIXED) assemble_variant<PREC_MIXED>(bp, prev, old, nw, implicit, tvd, s);
+    else assemble_variant<PREC_FP64>(bp, prev, old, nw, implicit, tvd, s);
+}
+
+void launch_pressure(const BatchPlan &bp, int prec, int prev, int old, int nw, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
     const dim3 bl(bp.tx, bp.ty);
-    if (mixed) k_velocity<true><<<bp.grid, bl, 0, s>>>(bp, old, nw);
-    else k_velocity<false><<<bp.grid, bl, 0, s>>>(bp, old, nw);
+    if (prec == PREC_DF64) k_pressure<PREC_DF64><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+    else if (prec == PREC_MIXED) k_pressure<PREC_MIXED><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+    else k_pressure<PREC_FP64><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+}
+
+void launch_velocity(const BatchPlan &bp, int prec, int old, int nw, void *stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    const dim3 bl(bp.tx, bp.ty);
+    if (prec == PREC_DF64) k_velocity<PREC_DF64><<<bp.grid, bl, 0, s>>>(bp, old, nw);
+    else if (prec == PREC_MIXED) k_velocity<PREC_MIXED><<<bp.grid, bl, 0, s>>>(bp, old, nw);
+    else k_velocity<PREC_FP64><<<bp.grid, bl, 0, s>>>(bp, old, nw);
 }
 
 }  // namespace stg

@@ -31,7 +31,7 @@ def small_batch(n=5, precision=W.MIXED, implicit=True, tvd=False):
     return out
 
 
-@pytest.mark.parametrize("precision", [W.FP64, W.MIXED])
+@pytest.mark.parametrize("precision", [W.FP64, W.MIXED, W.DF64])
 @pytest.mark.parametrize("implicit,tvd", [(True, False), (False, True)])
 def test_batch_equals_problems_advanced_alone(precision, implicit, tvd):
     cases = small_batch(precision=precision, implicit=implicit, tvd=tvd)

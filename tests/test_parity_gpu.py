@@ -84,26 +84,31 @@ def test_parity_channel_128x32(implicit, tvd):
     np.testing.assert_allclose(gres, ores, rtol=1e-6, atol=1e-12)
 
 
+@pytest.mark.parametrize("precision", [W.FP64, W.DF64], ids=["fp64", "df64"])
 @pytest.mark.parametrize("implicit,tvd", SCHEMES)
-def test_parity_box_nonuniform_moving_walls(implicit, tvd):
+def test_parity_box_nonuniform_moving_walls(implicit, tvd, precision):
     rng = np.random.default_rng(4)
     nx, ny = 37, 29                                  # ragged: not a multiple of the 32 x 8 tile
     dx, dy = rng.uniform(0.2, 0.35, nx), rng.uniform(0.2, 0.35, ny)
     case = W.closed_box(implicit=implicit, tvd=tvd).replace(
         nx=nx, ny=ny, dx=dx, dy=dy, lx=float(dx.sum()), ly=float(dy.sum()),
-        rects=[[5, 4, 12, 9], [20, 15, 24, 25]], gx=0.01, gy=-0.02, iters=3, perturb=1e-3, seed=21)
+        rects=[[5, 4, 12, 9], [20, 15, 24, 25]], gx=0.01, gy=-0.02, iters=3, perturb=1e-3, seed=21,
+        precision=precision)
     start = oracle.init(case)
     start["u"] += 0.03 * rng.standard_normal(start["u"].shape)
     start["v"] += 0.03 * rng.standard_normal(start["v"].shape)
-    g, o, *_ = run_both(case, steps_for(implicit, tvd, 40), start=start)
+    n = (df64_steps_for if precision == W.DF64 else steps_for)(implicit, tvd, 40)
+    g, o, *_ = run_both(case, n, start=start)
     assert_parity(g, o)
 
 
+@pytest.mark.parametrize("precision", [W.FP64, W.DF64], ids=["fp64", "df64"])
 @pytest.mark.parametrize("implicit,tvd", SCHEMES)
-def test_parity_symmetry_sides_and_obstacle(implicit, tvd):
+def test_parity_symmetry_sides_and_obstacle(implicit, tvd, precision):
     case = W.uniform_flow(nx=48, ny=20, implicit=implicit, tvd=tvd).replace(
-        rects=[[10, 6, 14, 12]], perturb=1e-3, seed=8)
-    g, o, *_ = run_both(case, steps_for(implicit, tvd, 60))
+        rects=[[10, 6, 14, 12]], perturb=1e-3, seed=8, precision=precision)
+    n = (df64_steps_for if precision == W.DF64 else steps_for)(implicit, tvd, 60)
+    g, o, *_ = run_both(case, n)
     assert_parity(g, o)
 
 
@@ -248,7 +253,7 @@ def test_mixed_start_state_matches_fp64_start_state():
         assert np.array_equal(fa[k], fb[k])
 
 
-@pytest.mark.parametrize("precision", [W.FP64, W.MIXED])
+@pytest.mark.parametrize("precision", [W.FP64, W.MIXED, W.DF64])
 def test_step_graph_replay_matches_direct_launches(precision):
     # sim_step replays captured step graphs; with event timing on it launches
     # kernels one by one.  Both must give the same bits, for every start level
@@ -264,3 +269,62 @@ def test_step_graph_replay_matches_direct_launches(precision):
     for k in "uvpT":
         assert np.array_equal(a[k], b[k]), k
     assert n_direct == 12 * case.iters
+
+
+# ------------------------------------------------------------ double-float
+
+# The DF64 path runs every kernel of the iteration in double-float arithmetic
+# (pairs of floats, about 2^-48 relative precision per operation) and is held
+# to the FP64 bar against the FP64 oracle.  Its start state is the FP64 start
+# state rounded to double-float.
+
+def df64_steps_for(implicit, tvd, n):
+    # Implicit TVD amplifies rounding differences by about 1e4 over 10-20
+    # steps (test_oracle_pins.test_rounding_sensitivity_per_scheme); the
+    # double-float unit roundoff (2^-48) is 32 times FP64's, so its runs stop
+    # at 10 steps where the FP64 runs stop at 20.
+    return min(n, 10) if (implicit and tvd) else n
+
+
+@pytest.mark.parametrize("implicit,tvd", SCHEMES)
+def test_df64_parity_channel_128x32(implicit, tvd):
+    case = W.c1_small().replace(implicit=implicit, tvd=tvd, precision=W.DF64)
+    n = df64_steps_for(implicit, tvd, case.steps)
+    g, o, gres, ores, git, oit = run_both(case, n)
+    e = assert_parity(g, o, what=f"df64 {n} steps")
+    print("df64", implicit, tvd, n, e)
+    assert git == oit == case.iters
+    np.testing.assert_allclose(gres, ores, rtol=1e-6, atol=1e-12)
+
+
+def test_df64_start_state_is_the_fp64_start_rounded():
+    case = W.c1_small()
+    with sim.Simulation(case) as a, sim.Simulation(case.replace(precision=W.DF64)) as b:
+        fa, fb = a.fields(("u", "v", "p", "T", "rho")), b.fields(("u", "v", "p", "T", "rho"))
+    for k in fa:
+        rel = np.abs(fb[k] - fa[k]) / np.maximum(np.abs(fa[k]), 1e-300)
+        assert rel.max() <= 2.0 ** -47, k
+
+
+def test_df64_1024x256_implicit_100_steps():
+    case = W.c2_medium().replace(precision=W.DF64)
+    g, o, *_ = run_both(case, 100)
+    e = assert_parity(g, o)
+    print("df64 c2", e)
+
+
+def test_df64_restart_through_host_fields_continues():
+    # A DF64 state read out as FP64 and set again loses the bits beyond FP64's
+    # reach only, so the continued run stays at the FP64 bar.
+    case = W.c1_small().replace(implicit=True, tvd=False, precision=W.DF64)
+    with sim.Simulation(case) as a:
+        a.step(20)
+        full = a.fields()
+    with sim.Simulation(case) as b:
+        b.step(10)
+        mid = b.fields()
+    with sim.Simulation(case) as c:
+        c.set_fields(mid)
+        c.step(10)
+        again = c.fields()
+    assert_parity(again, full, tol=1e-12)

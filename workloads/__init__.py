@@ -25,7 +25,7 @@ import numpy as np
 W, E, S, N = 0, 1, 2, 3
 WALL, SYMMETRY, INFLOW, OUTFLOW = 0, 1, 2, 3
 GAS_IDEAL_RE, GAS_HARD_SPHERE_KN = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, DF64 = 0, 1, 2
 
 
 @dataclass
