@@ -196,7 +196,7 @@ __global__ void k_na_fill(Setup s, const double *u_in, const double *v_in, const
     } else if (tl == NK_FLUID || t == NK_FLUID) {
         u = (tl == NK_INFLOW || t == NK_INFLOW) ? uin : 0.0;
     } else if (nwall(s, i - 1, j) && nwall(s, i, j)) {
-        const int sl = nin(s, i - 1, j) ? s.side[nidx(s, i - 1, j)] : 0, sr = s.side[c];
+        const int sl = s.side[nidx(s, i - 1 < -G ? -G : i - 1, j)], sr = s.side[c];
         if (tl == NK_WALL && (sl == SIM_S || sl == SIM_N)) u = s.side_vel[sl];
         else if (t == NK_WALL && (sr == SIM_S || sr == SIM_N)) u = s.side_vel[sr];
     } else if (tl == NK_INFLOW || t == NK_INFLOW) {
@@ -209,7 +209,7 @@ __global__ void k_na_fill(Setup s, const double *u_in, const double *v_in, const
     if (tb == NK_FLUID && t == NK_FLUID) {
         v = v_in[(size_t)j * s.nx + i];
     } else if (tb != NK_FLUID && t != NK_FLUID && nwall(s, i, j - 1) && nwall(s, i, j)) {
-        const int sb = nin(s, i, j - 1) ? s.side[nidx(s, i, j - 1)] : 0, st = s.side[c];
+        const int sb = s.side[nidx(s, i, j - 1 < -G ? -G : j - 1)], st = s.side[c];
         if (tb == NK_WALL && (sb == SIM_W || sb == SIM_E)) v = s.side_vel[sb];
         else if (t == NK_WALL && (st == SIM_W || st == SIM_E)) v = s.side_vel[st];
     }

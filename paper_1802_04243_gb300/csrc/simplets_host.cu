@@ -236,6 +236,14 @@ struct HostGrid {
     int at(int i, int j) const { return (j + G) * P + (i + G); }
     bool in(int i, int j) const { return i >= -G && i <= nx + G && j >= -G && j <= ny + G; }
     int k(int i, int j) const { return in(i, j) ? kind[at(i, j)] : K_WALL; }
+    // side of the nearest position of the extended grid (lookups one layer
+    // beyond it, from the faces of the outermost ghost layer, stay inside)
+    int side_at(int i, int j) const
+    {
+        i = i < -G ? -G : (i > nx + G ? nx + G : i);
+        j = j < -G ? -G : (j > ny + G ? ny + G : j);
+        return side[at(i, j)];
+    }
     bool fluid(int i, int j) const { return k(i, j) == K_FLUID; }
     bool wall(int i, int j) const { int t = k(i, j); return t == K_SOLID || t == K_WALL; }
 };
@@ -368,7 +376,7 @@ void build_start_level(const Problem &pb, const HostGrid &h, std::vector<double>
                 u = (tl == K_INFLOW || tr == K_INFLOW) ? pb.in_u[row(j)] : 0.0;
             } else if (h.wall(i - 1, j) && h.wall(i, j)) {
                 // inside a wall: tangential wall speed behind a S/N wall, else 0
-                int sl = h.side[h.at(i - 1, j)], sr = h.side[c];
+                int sl = h.side_at(i - 1, j), sr = h.side[c];
                 if (tl == K_WALL && (sl == SIM_S || sl == SIM_N)) u = pb.side_vel[sl];
                 else if (tr == K_WALL && (sr == SIM_S || sr == SIM_N)) u = pb.side_vel[sr];
             } else if (tl == K_INFLOW || tr == K_INFLOW) {
@@ -382,7 +390,7 @@ void build_start_level(const Problem &pb, const HostGrid &h, std::vector<double>
             if (tb == K_FLUID && tt == K_FLUID) {
                 v = pb.perturb * pb.u_in * hash_uniform(pb.seed, 1, i, j);
             } else if (tb != K_FLUID && tt != K_FLUID && h.wall(i, j - 1) && h.wall(i, j)) {
-                int sb = h.side[h.at(i, j - 1)], st = h.side[c];
+                int sb = h.side_at(i, j - 1), st = h.side[c];
                 if (tb == K_WALL && (sb == SIM_W || sb == SIM_E)) v = pb.side_vel[sb];
                 else if (tt == K_WALL && (st == SIM_W || st == SIM_E)) v = pb.side_vel[st];
             }
