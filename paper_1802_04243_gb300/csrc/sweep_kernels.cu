@@ -50,22 +50,38 @@ __device__ __forceinline__ bool positive(df64 x) { return x.hi > 0.0f; }    // n
 
 // ---------------------------------------------------------------- limiter
 
-// Van Leer psi(r) = (r + |r|)/(1 + r) for r = num/den; 0 unless num and den
-// share a sign (a zero denominator falls back to first order).
+__device__ __forceinline__ float recip(float a);
+__device__ __forceinline__ double recip(double a);
+
+// Van Leer psi(r) = (r + |r|)/(1 + r) for r = num/den, i.e. 2 num/(num + den)
+// when num and den are nonzero with one sign, else 0 (a zero denominator
+// falls back to first order).  The sign test reads the sign bits, so it runs
+// on the integer pipe; the quotient uses the sweep's reciprocal.
 template <typename R>
 __device__ __forceinline__ R van_leer(R num, R den)
 {
-    return (num * den > R(0)) ? R(2) * num / (num + den) : R(0);
+    const bool same = (positive(num) && positive(den)) || (positive(-num) && positive(-den));
+    return same ? R(2) * num * recip(num + den) : R(0);
 }
 
-// Eq. pl15_2: correction at the face between nodes 2 and 3; d1..d4 are the
-// cell sizes of the four nodes.
+// Eq. pl15_2: correction at the face between nodes 2 and 3 for flow towards
+// node 3 (up) and towards node 2 (dn); d1..d4 are the sizes of the four
+// nodes, w2 = d2/(d2 + d3) and w3 = d3/(d2 + d3) the weights of the face,
+// taken from the axis tables.
 template <typename R>
-__device__ __forceinline__ R psi_surface(R f1, R f2, R f3, R f4, R d1, R d2, R d3, R d4, R vel)
+__device__ __forceinline__ R psi_s_up(R f1, R f2, R f3, R d1, R d2, R d3, R w2)
 {
-    if (positive(vel))
-        return d2 / (d2 + d3) * van_leer((d2 + d3) * (f2 - f1), (d1 + d2) * (f3 - f2));
-    return -d3 / (d2 + d3) * van_leer((d2 + d3) * (f4 - f3), (d3 + d4) * (f3 - f2));
+    return w2 * van_leer((d2 + d3) * (f2 - f1), (d1 + d2) * (f3 - f2));
+}
+template <typename R>
+__device__ __forceinline__ R psi_s_dn(R f2, R f3, R f4, R d2, R d3, R d4, R w3)
+{
+    return -(w3 * van_leer((d2 + d3) * (f4 - f3), (d3 + d4) * (f3 - f2)));
+}
+template <typename R>
+__device__ __forceinline__ R psi_surface(R f1, R f2, R f3, R f4, R d1, R d2, R d3, R d4, R w2, R w3, R vel)
+{
+    return positive(vel) ? psi_s_up(f1, f2, f3, d1, d2, d3, w2) : psi_s_dn(f2, f3, f4, d2, d3, d4, w3);
 }
 
 // Eq. pl15_1: face midway between nodes 2 and 3; d1..d3 the node distances.
@@ -251,7 +267,7 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         R val = upwind(rl, rr, vel);
         if (TVD && (g.flag[c] & F_TCX))
             val += psi_surface(rho[c - 2], rl, rr, rho[c + 1], at(g.x.d, i - 2), at(g.x.d, i - 1),
-                               dxi, at(g.x.d, i + 1), vel) * (rr - rl);
+                               dxi, at(g.x.d, i + 1), at(g.x.whi, i), at(g.x.wlo, i), vel) * (rr - rl);
         w.rho_u[c] = val;
         w.Fx[c] = val * vel * dyj;
         w.DTx[c] = conductance(gam[c - 1], gam[c], at(g.x.d, i - 1), dxi, k.CT1f * dyj);
@@ -261,7 +277,7 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         R val = upwind(rb, rt, vel);
         if (TVD && (g.flag[c] & F_TCY))
             val += psi_surface(rho[c - 2 * P], rb, rt, rho[c + P], at(g.y.d, j - 2), at(g.y.d, j - 1),
-                               dyj, at(g.y.d, j + 1), vel) * (rt - rb);
+                               dyj, at(g.y.d, j + 1), at(g.y.whi, j), at(g.y.wlo, j), vel) * (rt - rb);
         w.rho_v[c] = val;
         w.Fy[c] = val * vel * dxi;
         w.DTy[c] = conductance(gam[c - P], gam[c], at(g.y.d, j - 1), dyj, k.CT1f * dxi);
@@ -292,13 +308,17 @@ __device__ R explicit_T(const GeoT<R> &g, const LevelT<R> &L, const R *Fx, const
     R pw = 0.0, pe = 0.0, ps = 0.0, pn = 0.0;
     if (TVD) {
         if (fl[c + 1] & F_TCX)
-            pe = psi_surface(T[c - 1], Tp, Te, T[c + 2], at(g.x.d, i - 1), dxi, at(g.x.d, i + 1), at(g.x.d, i + 2), ue);
+            pe = psi_surface(T[c - 1], Tp, Te, T[c + 2], at(g.x.d, i - 1), dxi, at(g.x.d, i + 1), at(g.x.d, i + 2),
+                             at(g.x.whi, i + 1), at(g.x.wlo, i + 1), ue);
         if (fl[c] & F_TCX)
-            pw = psi_surface(T[c - 2], Tw, Tp, Te, at(g.x.d, i - 2), at(g.x.d, i - 1), dxi, at(g.x.d, i + 1), uw);
+            pw = psi_surface(T[c - 2], Tw, Tp, Te, at(g.x.d, i - 2), at(g.x.d, i - 1), dxi, at(g.x.d, i + 1),
+                             at(g.x.whi, i), at(g.x.wlo, i), uw);
         if (fl[c + P] & F_TCY)
-            pn = psi_surface(T[c - P], Tp, Tn, T[c + 2 * P], at(g.y.d, j - 1), dyj, at(g.y.d, j + 1), at(g.y.d, j + 2), vn);
+            pn = psi_surface(T[c - P], Tp, Tn, T[c + 2 * P], at(g.y.d, j - 1), dyj, at(g.y.d, j + 1), at(g.y.d, j + 2),
+                             at(g.y.whi, j + 1), at(g.y.wlo, j + 1), vn);
         if (fl[c] & F_TCY)
-            ps = psi_surface(T[c - 2 * P], Ts, Tp, Tn, at(g.y.d, j - 2), at(g.y.d, j - 1), dyj, at(g.y.d, j + 1), vs);
+            ps = psi_surface(T[c - 2 * P], Ts, Tp, Tn, at(g.y.d, j - 2), at(g.y.d, j - 1), dyj, at(g.y.d, j + 1),
+                             at(g.y.whi, j), at(g.y.wlo, j), vs);
     }
     return -Fe * (upwind(Tp, Te, ue) + (Te - Tp) * pe) + Fw * (upwind(Tw, Tp, uw) + (Tp - Tw) * pw)
            - Fn * (upwind(Tp, Tn, vn) + (Tn - Tp) * pn) + Fs * (upwind(Ts, Tp, vs) + (Tp - Ts) * ps);
@@ -322,14 +342,18 @@ __device__ R explicit_v(const GeoT<R> &g, const LevelT<R> &L, const R *Fx, int b
         if (fl[b + 1] & F_TVX) {
             const R f1 = v[b - 1], f4 = v[b + 2];
             const R d1 = at(g.x.d, i - 1), d3 = at(g.x.d, i + 1), d4 = at(g.x.d, i + 2);
-            pe1 = psi_surface(f1, vP, vE, f4, d1, dxi, d3, d4, ue1);
-            pe2 = psi_surface(f1, vP, vE, f4, d1, dxi, d3, d4, ue2);
+            const R up = psi_s_up(f1, vP, vE, d1, dxi, d3, at(g.x.whi, i + 1));
+            const R dn = psi_s_dn(vP, vE, f4, dxi, d3, d4, at(g.x.wlo, i + 1));
+            pe1 = positive(ue1) ? up : dn;
+            pe2 = positive(ue2) ? up : dn;
         }
         if (fl[b] & F_TVX) {
             const R f1 = v[b - 2];
             const R d1 = at(g.x.d, i - 2), d2 = at(g.x.d, i - 1), d4 = at(g.x.d, i + 1);
-            pw1 = psi_surface(f1, vW, vP, vE, d1, d2, dxi, d4, uw1);
-            pw2 = psi_surface(f1, vW, vP, vE, d1, d2, dxi, d4, uw2);
+            const R up = psi_s_up(f1, vW, vP, d1, d2, dxi, at(g.x.whi, i));
+            const R dn = psi_s_dn(vW, vP, vE, d2, dxi, d4, at(g.x.wlo, i));
+            pw1 = positive(uw1) ? up : dn;
+            pw2 = positive(uw2) ? up : dn;
         }
         if (fl[b + P] & F_TVY)
             pn = psi_centre(vS, vP, vN, v[b + 2 * P], dys, dyp, at(g.y.d, j + 1), vbn);
@@ -360,14 +384,18 @@ __device__ R explicit_u(const GeoT<R> &g, const LevelT<R> &L, const R *Fy, int a
         if (fl[a + P] & F_TUY) {
             const R f1 = u[a - P], f4 = u[a + 2 * P];
             const R d1 = at(g.y.d, j - 1), d3 = at(g.y.d, j + 1), d4 = at(g.y.d, j + 2);
-            pn1 = psi_surface(f1, uP, uN, f4, d1, dyj, d3, d4, vn1);
-            pn2 = psi_surface(f1, uP, uN, f4, d1, dyj, d3, d4, vn2);
+            const R up = psi_s_up(f1, uP, uN, d1, dyj, d3, at(g.y.whi, j + 1));
+            const R dn = psi_s_dn(uP, uN, f4, dyj, d3, d4, at(g.y.wlo, j + 1));
+            pn1 = positive(vn1) ? up : dn;
+            pn2 = positive(vn2) ? up : dn;
         }
         if (fl[a] & F_TUY) {
             const R f1 = u[a - 2 * P];
             const R d1 = at(g.y.d, j - 2), d2 = at(g.y.d, j - 1), d4 = at(g.y.d, j + 1);
-            ps1 = psi_surface(f1, uS, uP, uN, d1, d2, dyj, d4, vs1);
-            ps2 = psi_surface(f1, uS, uP, uN, d1, d2, dyj, d4, vs2);
+            const R up = psi_s_up(f1, uS, uP, d1, d2, dyj, at(g.y.whi, j));
+            const R dn = psi_s_dn(uS, uP, uN, d2, dyj, d4, at(g.y.wlo, j));
+            ps1 = positive(vs1) ? up : dn;
+            ps2 = positive(vs2) ? up : dn;
         }
         if (fl[a + 1] & F_TUX)
             pe = psi_centre(uW, uP, uE, u[a + 2], dxw, dxp, at(g.x.d, i + 1), ube);
@@ -453,13 +481,16 @@ __device__ R temperature(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
         R pw = 0.0, pe = 0.0, ps = 0.0, pn = 0.0;
         if (TVD) {
             if (fl[c] & F_TCX)
-                pw = psi_surface(T[c - 2], Tw, Tp, Te, at(g.x.d, i - 2), dxw, dxi, dxe, uw);
+                pw = psi_surface(T[c - 2], Tw, Tp, Te, at(g.x.d, i - 2), dxw, dxi, dxe, at(g.x.whi, i), at(g.x.wlo, i), uw);
             if (fl[c + 1] & F_TCX)
-                pe = psi_surface(Tw, Tp, Te, T[c + 2], dxw, dxi, dxe, at(g.x.d, i + 2), ue);
+                pe = psi_surface(Tw, Tp, Te, T[c + 2], dxw, dxi, dxe, at(g.x.d, i + 2), at(g.x.whi, i + 1),
+                                 at(g.x.wlo, i + 1), ue);
             if (fl[c] & F_TCY)
-                ps = psi_surface(T[c - 2 * P], Ts, Tp, Tn, at(g.y.d, j - 2), dys, dyj, dyn, vs);
+                ps = psi_surface(T[c - 2 * P], Ts, Tp, Tn, at(g.y.d, j - 2), dys, dyj, dyn, at(g.y.whi, j),
+                                 at(g.y.wlo, j), vs);
             if (fl[c + P] & F_TCY)
-                pn = psi_surface(Ts, Tp, Tn, T[c + 2 * P], dys, dyj, dyn, at(g.y.d, j + 2), vn);
+                pn = psi_surface(Ts, Tp, Tn, T[c + 2 * P], dys, dyj, dyn, at(g.y.d, j + 2), at(g.y.whi, j + 1),
+                                 at(g.y.wlo, j + 1), vn);
         }
         if constexpr (TVD) {
             a1 = pos(Fw) - Fw * pw + Dw;
@@ -527,14 +558,18 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
             if (fl[a] & F_TUY) {
                 const R f1 = u[a - 2 * P];
                 const R d1 = at(g.y.d, j - 2), d2 = at(g.y.d, j - 1), d4 = at(g.y.d, j + 1);
-                ps1 = psi_surface(f1, uS, uP, uN, d1, d2, dyj, d4, vs1);
-                ps2 = psi_surface(f1, uS, uP, uN, d1, d2, dyj, d4, vs2);
+                const R up = psi_s_up(f1, uS, uP, d1, d2, dyj, at(g.y.whi, j));
+                const R dn = psi_s_dn(uS, uP, uN, d2, dyj, d4, at(g.y.wlo, j));
+                ps1 = positive(vs1) ? up : dn;
+                ps2 = positive(vs2) ? up : dn;
             }
             if (fl[a + P] & F_TUY) {
                 const R f4 = u[a + 2 * P];
                 const R d1 = at(g.y.d, j - 1), d3 = at(g.y.d, j + 1), d4 = at(g.y.d, j + 2);
-                pn1 = psi_surface(uS, uP, uN, f4, d1, dyj, d3, d4, vn1);
-                pn2 = psi_surface(uS, uP, uN, f4, d1, dyj, d3, d4, vn2);
+                const R up = psi_s_up(uS, uP, uN, d1, dyj, d3, at(g.y.whi, j + 1));
+                const R dn = psi_s_dn(uP, uN, f4, dyj, d3, d4, at(g.y.wlo, j + 1));
+                pn1 = positive(vn1) ? up : dn;
+                pn2 = positive(vn2) ? up : dn;
             }
         }
         if constexpr (TVD) {
@@ -597,14 +632,18 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
             if (fl[b] & F_TVX) {
                 const R f1 = v[b - 2];
                 const R d1 = at(g.x.d, i - 2), d2 = at(g.x.d, i - 1), d4 = at(g.x.d, i + 1);
-                pw1 = psi_surface(f1, vW, vP, vE, d1, d2, dxi, d4, uw1);
-                pw2 = psi_surface(f1, vW, vP, vE, d1, d2, dxi, d4, uw2);
+                const R up = psi_s_up(f1, vW, vP, d1, d2, dxi, at(g.x.whi, i));
+                const R dn = psi_s_dn(vW, vP, vE, d2, dxi, d4, at(g.x.wlo, i));
+                pw1 = positive(uw1) ? up : dn;
+                pw2 = positive(uw2) ? up : dn;
             }
             if (fl[b + 1] & F_TVX) {
                 const R f4 = v[b + 2];
                 const R d1 = at(g.x.d, i - 1), d3 = at(g.x.d, i + 1), d4 = at(g.x.d, i + 2);
-                pe1 = psi_surface(vW, vP, vE, f4, d1, dxi, d3, d4, ue1);
-                pe2 = psi_surface(vW, vP, vE, f4, d1, dxi, d3, d4, ue2);
+                const R up = psi_s_up(vW, vP, vE, d1, dxi, d3, at(g.x.whi, i + 1));
+                const R dn = psi_s_dn(vP, vE, f4, dxi, d3, d4, at(g.x.wlo, i + 1));
+                pe1 = positive(ue1) ? up : dn;
+                pe2 = positive(ue2) ? up : dn;
             }
             if (fl[b] & F_TVY)
                 ps = psi_centre(v[b - 2 * P], vS, vP, vN, at(g.y.d, j - 2), dys, dyp, vbs);
