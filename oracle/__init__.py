@@ -55,6 +55,7 @@ class _Problem(ctypes.Structure):
         ("implicit", ctypes.c_int), ("tvd", ctypes.c_int),
         ("iters", ctypes.c_int), ("tol", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("perturb", ctypes.c_double),
+        ("zeta_coef", ctypes.c_double), ("tau_coef", ctypes.c_double),
     ]
 
 
@@ -130,6 +131,7 @@ class _Pinned:
         P.implicit, P.tvd = int(bool(c.implicit)), int(bool(c.tvd))
         P.iters, P.tol = c.iters, c.tol
         P.seed, P.perturb = c.seed, c.perturb
+        P.zeta_coef, P.tau_coef = c.zeta_coef, c.tau_coef
         self.P = P
 
 

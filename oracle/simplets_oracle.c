@@ -27,16 +27,19 @@
  * coefficients here are their mirror image under x<->y, u<->v, i<->j.
  *
  * Boundary treatment (the paper gives only the slip/jump forms Eqs. pl38,
- * pl39; this file takes their zeta = tau = 0 limit):
+ * pl39 for walls):
  *   - every field lives on an extended grid with two ghost layers;
  *   - ghost cells of an inflow side hold the inflow state, of an outflow side
  *     a zero-gradient copy, of a symmetry side a mirror copy (refreshed after
  *     every iteration);
  *   - wall ghost cells and obstacle cells hold the wall state (wall T, wall
  *     tangential velocity) and are never updated; a temperature or a
- *     tangential velocity read across a wall is reflected about the wall value,
- *     phi = 2 phi_wall - phi_reader, which puts the wall value half a cell
- *     from the reader;
+ *     tangential velocity read across a wall is reflected about the value at
+ *     the wall surface, phi = 2 phi_s - phi_reader, which puts phi_s half a
+ *     cell from the reader.  phi_s follows Eqs. pl38, pl39,
+ *     phi_s - phi_wall = s dphi/dn with dphi/dn = (phi_reader - phi_s)/h, h half
+ *     the reader's size normal to the wall and s = zeta or tau (coefficient
+ *     over the local density, the reader's); s = 0 gives phi_s = phi_wall;
  *   - a face between a fluid cell and a wall carries zero normal velocity;
  *   - the TVD correction of a face is applied only when all four nodes of its
  *     stencil are unknowns of the equation, otherwise the face is upwind;
@@ -557,40 +560,74 @@ static void copy_level(const orc *o, level *dst, const level *src)
 
 /* ----------------------------------------------------------- node access */
 
-/* Temperature of cell (ni,nj) as read from cell (ci,cj): reflected about the
- * wall temperature when (ni,nj) is a wall or obstacle cell. */
-static double T_at(const orc *o, const level *L, int ci, int cj, int ni, int nj)
-{
-    double Tn = L->T[CI(o, ni, nj)];
-    if (wallish(o, ni, nj))
-        return 2.0 * Tn - L->T[CI(o, ci, cj)];
-    return Tn;
-}
-
-/* u of node (mi,mj) as read from node (ai,aj): reflected about the wall
- * velocity when (mi,mj) lies inside a wall or obstacle. */
-static double u_at(const orc *o, const level *L, int ai, int aj, int mi, int mj)
-{
-    double um = L->u[UI(o, mi, mj)];
-    if (u_inwall(o, mi, mj))
-        return 2.0 * um - L->u[UI(o, ai, aj)];
-    return um;
-}
-
-static double v_at(const orc *o, const level *L, int ai, int aj, int mi, int mj)
-{
-    double vm = L->v[VI(o, mi, mj)];
-    if (v_inwall(o, mi, mj))
-        return 2.0 * vm - L->v[VI(o, ai, aj)];
-    return vm;
-}
-
 static double Tc(const orc *o, const level *L, int i, int j) { return L->T[CI(o, i, j)]; }
 static double Uc(const orc *o, const level *L, int i, int j) { return L->u[UI(o, i, j)]; }
 static double Vc(const orc *o, const level *L, int i, int j) { return L->v[VI(o, i, j)]; }
 static double RHOc(const orc *o, const level *L, int i, int j) { return L->rho[CI(o, i, j)]; }
 static double GAMc(const orc *o, const level *L, int i, int j) { return L->gam[CI(o, i, j)]; }
 static double Pc(const orc *o, const level *L, int i, int j) { return L->p[CI(o, i, j)]; }
+
+/* Value at the wall surface between a reader node (value phi_r, distance h
+ * from the surface, local density rho) and a wall (value phi_w): Eqs. pl38,
+ * pl39 with the normal derivative (phi_r - phi_s)/h solved for phi_s,
+ * phi_s = (h phi_w + s phi_r)/(h + s), s = coef/rho. */
+static double wall_surface(double phi_w, double phi_r, double h, double coef, double rho)
+{
+    double s = coef / rho;
+    return (h * phi_w + s * phi_r) / (h + s);
+}
+
+/* Temperature of cell (ni,nj) as read from cell (ci,cj): reflected about the
+ * surface temperature when (ni,nj) is a wall or obstacle cell (temperature
+ * jump, Eq. pl39, tau = tau_coef / rho of the reader cell). */
+static double T_at(const orc *o, const level *L, int ci, int cj, int ni, int nj)
+{
+    double Tn = L->T[CI(o, ni, nj)];
+    if (wallish(o, ni, nj)) {
+        double Tr = L->T[CI(o, ci, cj)];
+        if (o->P->tau_coef > 0.0) {
+            double h = 0.5 * (ni != ci ? DX(o, ci) : DY(o, cj));
+            return 2.0 * wall_surface(Tn, Tr, h, o->P->tau_coef, RHOc(o, L, ci, cj)) - Tr;
+        }
+        return 2.0 * Tn - Tr;
+    }
+    return Tn;
+}
+
+/* u of node (mi,mj) as read from node (ai,aj): reflected about the surface
+ * velocity when (mi,mj) lies inside a wall or obstacle.  Across a wall in y,
+ * u is tangential and slips (Eq. pl38, zeta = zeta_coef / rho of the reader's
+ * u control volume, the mean of its two cells); across a wall in x it is the
+ * normal component and is reflected about the wall value. */
+static double u_at(const orc *o, const level *L, int ai, int aj, int mi, int mj)
+{
+    double um = L->u[UI(o, mi, mj)];
+    if (u_inwall(o, mi, mj)) {
+        double ur = L->u[UI(o, ai, aj)];
+        if (mj != aj && o->P->zeta_coef > 0.0) {
+            double rho = 0.5 * (RHOc(o, L, ai - 1, aj) + RHOc(o, L, ai, aj));
+            return 2.0 * wall_surface(um, ur, 0.5 * DY(o, aj), o->P->zeta_coef, rho) - ur;
+        }
+        return 2.0 * um - ur;
+    }
+    return um;
+}
+
+/* v of node (mi,mj) as read from node (ai,aj): as u_at with x and y swapped. */
+static double v_at(const orc *o, const level *L, int ai, int aj, int mi, int mj)
+{
+    double vm = L->v[VI(o, mi, mj)];
+    if (v_inwall(o, mi, mj)) {
+        double vr = L->v[VI(o, ai, aj)];
+        if (mi != ai && o->P->zeta_coef > 0.0) {
+            double rho = 0.5 * (RHOc(o, L, ai, aj - 1) + RHOc(o, L, ai, aj));
+            return 2.0 * wall_surface(vm, vr, 0.5 * DX(o, ai), o->P->zeta_coef, rho) - vr;
+        }
+        return 2.0 * vm - vr;
+    }
+    return vm;
+}
+
 
 /* TVD applies on a face only when the four stencil nodes are all unknowns. */
 static int tvd_cells_x(const orc *o, int i, int j)   /* cells i-2..i+1 (face i) */

@@ -48,6 +48,10 @@ typedef struct {
     double tol;                 /* stop loop 2 when every residual <= tol (0: fixed iters) */
     uint64_t seed;
     double perturb;
+    /* velocity-slip and temperature-jump walls (Eqs. pl38, pl39):
+     * zeta = zeta_coef / rho_local, tau = tau_coef / rho_local (the paper's
+     * hard-sphere values: 1.1466 Kn and 2.1904 Kn); 0 = no slip / no jump */
+    double zeta_coef, tau_coef;
 } orc_problem;
 
 /* Non-dimensional coefficients derived from the gas description. */

@@ -44,7 +44,16 @@ MUTANTS = {
     "corner_gamma_weights": ("double wxm = DX(o, i) / (DX(o, i - 1) + DX(o, i));",
                              "double wxm = DX(o, i - 1) / (DX(o, i - 1) + DX(o, i));"),
     "dv_uses_dy": ("*dv = k->A * dxi / a0;", "*dv = k->A * dyp / a0;"),
-    "T_wall_reflection": ("return 2.0 * Tn - L->T[CI(o, ci, cj)];", "return Tn;"),
+    "T_wall_reflection": ("return 2.0 * Tn - Tr;", "return Tn;"),
+    "slip_surface_weights": ("return (h * phi_w + s * phi_r) / (h + s);",
+                             "return (h * phi_r + s * phi_w) / (h + s);"),
+    "slip_density_dropped": ("double s = coef / rho;", "double s = coef;"),
+    "slip_full_cell_distance": ("wall_surface(um, ur, 0.5 * DY(o, aj), o->P->zeta_coef, rho)",
+                                "wall_surface(um, ur, DY(o, aj), o->P->zeta_coef, rho)"),
+    "slip_on_normal_component": ("if (mj != aj && o->P->zeta_coef > 0.0) {",
+                                 "if (mi != ai && o->P->zeta_coef > 0.0) {"),
+    "jump_normal_size_swapped": ("double h = 0.5 * (ni != ci ? DX(o, ci) : DY(o, cj));",
+                                 "double h = 0.5 * (ni != ci ? DY(o, cj) : DX(o, ci));"),
     "rho_v_tvd_velocity": (
         "DY(o, j - 2), DY(o, j - 1), DY(o, j), DY(o, j + 1), vel) * (rt - rb);",
         "DY(o, j - 2), DY(o, j - 1), DY(o, j), DY(o, j + 1), -vel) * (rt - rb);"),

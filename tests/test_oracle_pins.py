@@ -191,14 +191,14 @@ def test_rounding_sensitivity_per_scheme():
 
 # ------------------------------ P3: transpose symmetry (pins the unprinted u equation)
 
-def _box_pair(implicit, tvd):
+def _box_pair(implicit, tvd, zeta_coef=0.0, tau_coef=0.0):
     rng = np.random.default_rng(11)
     nx, ny = 12, 9
     dx = rng.uniform(0.2, 0.4, nx)
     dy = rng.uniform(0.2, 0.4, ny)
     a = W.closed_box(implicit=implicit, tvd=tvd).replace(
         nx=nx, ny=ny, dx=dx, dy=dy, lx=float(dx.sum()), ly=float(dy.sum()),
-        rects=[[3, 2, 6, 5]], gx=0.02, gy=-0.03, dt=0.02, iters=3)
+        rects=[[3, 2, 6, 5]], gx=0.02, gy=-0.03, dt=0.02, iters=3, zeta_coef=zeta_coef, tau_coef=tau_coef)
     # the transposed problem: x <-> y, u <-> v, W <-> S, E <-> N
     perm = [W.S, W.N, W.W, W.E]
     b = a.replace(nx=ny, ny=nx, dx=dy, dy=dx, lx=a.ly, ly=a.lx,
@@ -215,9 +215,12 @@ def _box_pair(implicit, tvd):
     return a, b, sa, sb
 
 
+@pytest.mark.parametrize("slip", [False, True], ids=["noslip", "slip"])
 @pytest.mark.parametrize("implicit,tvd", SCHEMES)
-def test_transposed_problem_gives_transposed_fields(implicit, tvd):
-    a, b, sa, sb = _box_pair(implicit, tvd)
+def test_transposed_problem_gives_transposed_fields(implicit, tvd, slip):
+    # with slip and jump walls (Eqs. pl38, pl39): u slips across walls in y,
+    # v across walls in x, and T jumps at every wall
+    a, b, sa, sb = _box_pair(implicit, tvd, *((0.3, 0.5) if slip else (0.0, 0.0)))
     ra, _, _ = oracle.run(a, sa, nsteps=6)
     rb, _, _ = oracle.run(b, sb, nsteps=6)
     tol = 1e-12
@@ -367,6 +370,60 @@ def test_dilatation_heating_and_pressure_work():
     lin = 2 * d1 - d2 / 2                             # c2 a
     assert quad == pytest.approx(scale * k["CT2f"] * 4 / 3 * a * a, rel=1e-7)
     assert lin == pytest.approx(scale * (k["CT3f"] - 1.0) * 2 * a, rel=1e-7)
+
+
+# ------------------------- velocity slip and temperature jump (Eqs. pl38, pl39)
+
+def test_slip_couette_flow_profile():
+    # Couette flow with Maxwell slip u_s - u_w = zeta du/dn at both walls,
+    # zeta = zeta_coef / rho: the profile stays linear with a slip velocity
+    # zeta dU/(H + 2 zeta) at each wall, u = U (y + zeta) / (H + 2 zeta).  At
+    # p = 2 and T = 1 the density is 2, so zeta is half of zeta_coef.
+    ny, uw, zc, rho = 16, 0.05, 0.3, 2.0
+    zeta = zc / rho
+    y = (np.arange(ny) + 0.5) / ny
+    exact = uw * (y + zeta) / (1 + 2 * zeta)
+    c = W.couette(ny=ny, u_wall=uw, reynolds=1.0).replace(
+        inflow_u=exact, inflow_T=np.ones(ny), inflow_p=rho * np.ones(ny), dt=0.05, zeta_coef=zc)
+    s, res, _ = oracle.run(c, oracle.init(c), nsteps=1500)
+    i = c.nx - 1
+    assert np.abs(s["u"][:, i] - exact).max() < 1e-4 * uw
+    assert np.abs(exact - uw * y).max() > 0.1 * uw          # the slip is large against that bound
+    assert res.max() < 1e-9
+
+
+def _jump_conduction(ny, tc=0.2, t_top=1.02, omega=0.5):
+    # Gas at rest between walls at T = 1 and t_top with the temperature jump
+    # T_s - T_w = tau dT/dn, tau = tc / rho = tc T / p.  Steady state: the
+    # Kirchhoff variable K(T) = T^(omega+1)/(omega+1) is linear in y,
+    # K(T(y)) = K(T_0) + q y with Gamma dT/dy = q; T_0, T_H, q solve the two
+    # jump conditions and K(T_H) - K(T_0) = q H.
+    from scipy.optimize import fsolve
+    c = W.Case(name="cond", nx=4, ny=ny, lx=1.0, ly=1.0,
+               side_kind=(W.SYMMETRY, W.SYMMETRY, W.WALL, W.WALL), side_T=(1, 1, 1, t_top),
+               mach_in=0.3, reynolds=2.0, visc_exp=omega, implicit=True, perturb=0.0,
+               iters=4, dt=0.02, tau_coef=tc)
+    s, res, _ = oracle.run(c, oracle.init(c), nsteps=6000)
+    p = s["p"][:, 1].mean()
+    K = lambda T: T ** (omega + 1) / (omega + 1)
+
+    def eqs(x):
+        T0, TH, q = x
+        return [K(TH) - K(T0) - q, T0 - 1 - tc * T0 / p * q / T0 ** omega,
+                TH - t_top + tc * TH / p * q / TH ** omega]
+
+    T0, TH, q = fsolve(eqs, [1.0, t_top, t_top - 1.0], xtol=1e-14)
+    yc = (np.arange(ny) + 0.5) / ny
+    exact = ((K(T0) + q * yc) * (omega + 1)) ** (1 / (omega + 1))
+    return np.abs(s["T"][:, 1] - exact).max() / (t_top - 1), res.max(), (T0 - 1) / (t_top - 1)
+
+
+def test_temperature_jump_conduction_profile():
+    pytest.importorskip("scipy")
+    err, res, jump = _jump_conduction(16)
+    assert res < 1e-12
+    assert jump > 0.1                                       # a jump of 14 % of the wall difference
+    assert err < 1e-3
 
 
 # ----------------------- heat conduction with T-dependent Gamma^lambda (Eqs. pl32, pl33)

@@ -65,6 +65,10 @@ class Case:
     seed: int = 1
     perturb: float = 1e-3
     precision: int = FP64
+    # velocity-slip / temperature-jump walls (Eqs. pl38, pl39): zeta = zeta_coef
+    # / rho_local, tau = tau_coef / rho_local; 0 = no slip / no jump
+    zeta_coef: float = 0.0
+    tau_coef: float = 0.0
     steps: int = 1           # length of the run the case is quoted on
 
     @property
