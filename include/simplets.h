@@ -107,7 +107,13 @@ typedef struct {
  *   pressure accumulation, equation of state and residuals); SIM_DF64 (every
  *   kernel of the iteration in double-float arithmetic -- pairs of floats,
  *   about 48 significant bits -- on the FP32 pipe; the FP64 state is filled
- *   from it when read, and the residual maxima carry FP32 precision). */
+ *   from it when read, and the residual maxima carry FP32 precision).
+ * zeta_coef, tau_coef: velocity-slip and temperature-jump walls (Eqs. pl38,
+ *   pl39), u_s - u_w = zeta du/dn and T_s - T_w = tau dT/dn with
+ *   zeta = zeta_coef / rho_local and tau = tau_coef / rho_local (the paper's
+ *   hard-sphere gas: 1.1466 Kn and 2.1904 Kn).  They apply at every wall side
+ *   and obstacle; a tangential velocity slips, the normal one stays zero.
+ *   0 gives no-slip isothermal walls; negative values are rejected. */
 typedef struct {
     int side_kind[4];
     double side_vel[4];
@@ -122,6 +128,7 @@ typedef struct {
     uint64_t seed;
     double perturb;
     int precision;
+    double zeta_coef, tau_coef;
 } sim_bc;
 
 /* Validate the problem, allocate every device buffer and set the start state.

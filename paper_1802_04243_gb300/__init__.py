@@ -53,7 +53,7 @@ class sim_bc(ctypes.Structure):
                 ("inflow_u", _DP), ("inflow_T", _DP), ("inflow_p", _DP),
                 ("dt", ctypes.c_double), ("cfl", ctypes.c_double), ("iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("seed", ctypes.c_uint64), ("perturb", ctypes.c_double),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("zeta_coef", ctypes.c_double), ("tau_coef", ctypes.c_double)]
 
 
 class SimError(RuntimeError):
@@ -147,6 +147,7 @@ class _Desc:
         bc.inflow_u, bc.inflow_T, bc.inflow_p = _ptr(iu), _ptr(iT), _ptr(ip)
         bc.dt, bc.cfl, bc.iters, bc.tol = c.dt, c.cfl, c.iters, c.tol
         bc.seed, bc.perturb, bc.precision = c.seed, c.perturb, c.precision
+        bc.zeta_coef, bc.tau_coef = c.zeta_coef, c.tau_coef
         self.bc = bc
 
 

@@ -332,6 +332,11 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
         k.dt = cfl * dmin / (uref + std::sqrt(gm / 2.0));
     }
     k.hrdt = 0.5 / k.dt;
+    if (!(bc->zeta_coef >= 0.0) || !(bc->tau_coef >= 0.0) || !std::isfinite(bc->zeta_coef) ||
+        !std::isfinite(bc->tau_coef))
+        return SIM_EINVAL;
+    k.zeta = bc->zeta_coef;
+    k.tau = bc->tau_coef;
 
     // --------------------------------------------------- carve the scratch
     void *base = nullptr;

@@ -196,6 +196,9 @@ sim_status read_problem(const sim_grid *gr, const sim_gas *gas, const sim_bc *bc
     if (!(bc->tol >= 0.0)) return fail(err, SIM_EINVAL, "tol must be >= 0");
     if (bc->precision != SIM_FP64 && bc->precision != SIM_MIXED && bc->precision != SIM_DF64)
         return fail(err, SIM_EINVAL, "unknown precision");
+    if (!(bc->zeta_coef >= 0.0) || !(bc->tau_coef >= 0.0) || !std::isfinite(bc->zeta_coef) ||
+        !std::isfinite(bc->tau_coef))
+        return fail(err, SIM_EINVAL, "slip and jump coefficients must be finite and >= 0");
     pb.iters = bc->iters;
     pb.tol = bc->tol;
     pb.seed = bc->seed;
@@ -203,6 +206,8 @@ sim_status read_problem(const sim_grid *gr, const sim_gas *gas, const sim_bc *bc
     pb.precision = bc->precision;
     sim_status st = derive_coefficients(gas, pb, err);
     if (st != SIM_OK) return st;
+    pb.k.zeta = bc->zeta_coef;
+    pb.k.tau = bc->tau_coef;
     pb.in_u.resize(pb.ny);
     pb.in_T.resize(pb.ny);
     pb.in_p.resize(pb.ny);
@@ -688,7 +693,8 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         s->mx.g.y = AxisT<float>{fy, fy + my, fy + 2 * my, fy + 3 * my, fy + 4 * my};
         const Coef &k = pb.k;
         s->mx.k = CoefT<float>{(float)k.A, (float)k.B, (float)k.CT1f, (float)k.CT2f, (float)k.CT3f,
-                               (float)k.omega, (float)k.dt, (float)k.gx, (float)k.gy, (float)k.hrdt};
+                               (float)k.omega, (float)k.dt, (float)k.gx, (float)k.gy, (float)k.hrdt,
+                               (float)k.zeta, (float)k.tau};
         std::vector<float> a32(nax + nay);
         for (size_t q = 0; q < nax; q++) a32[q] = (float)ax[q];
         for (size_t q = 0; q < nay; q++) a32[nax + q] = (float)ay[q];
@@ -714,7 +720,8 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         const Coef &k = pb.k;
         s->dfm.k = CoefT<df64>{dfl::split_host(k.A), dfl::split_host(k.B), dfl::split_host(k.CT1f), dfl::split_host(k.CT2f),
                                dfl::split_host(k.CT3f), dfl::split_host(k.omega), dfl::split_host(k.dt), dfl::split_host(k.gx),
-                               dfl::split_host(k.gy), dfl::split_host(k.hrdt)};
+                               dfl::split_host(k.gy), dfl::split_host(k.hrdt), dfl::split_host(k.zeta),
+                               dfl::split_host(k.tau)};
         std::vector<df64> adf(nax + nay);
         for (size_t q = 0; q < nax; q++) adf[q] = dfl::split_host(ax[q]);
         for (size_t q = 0; q < nay; q++) adf[nax + q] = dfl::split_host(ay[q]);

@@ -60,6 +60,7 @@ template <typename R>
 struct CoefT {
     R A, B, CT1f, CT2f, CT3f, omega, dt, gx, gy;
     R hrdt;               // 0.5 / dt
+    R zeta, tau;          // slip / jump coefficients (Eqs. pl38, pl39), divided by rho_local at use; 0 = off
 };
 
 // One state level: u, v at faces; p, T, rho, Gamma at cell centres.

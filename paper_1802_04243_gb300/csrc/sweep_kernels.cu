@@ -111,6 +111,30 @@ __device__ __forceinline__ R seen(const R *f, const uint16_t *flag, int a, int m
 }
 
 
+// Value of node m seen from node a when m may lie across a wall or obstacle
+// (the flag of m carries wall_bit): reflected about the value at the wall
+// surface, phi_s = (h phi_w + s phi_a)/(h + s), Eqs. pl38, pl39 with the
+// normal derivative (phi_a - phi_s)/h; h is half the reader's size normal to
+// the wall, s = coef / rho_local with rho_local the mean of rho[r0] and
+// rho[r1] (the reader's cell, or the two cells of its u or v control volume).
+// coef = 0: the no-slip / isothermal reflection 2 phi_w - phi_a.
+template <typename R, bool WALLS = true>
+__device__ __forceinline__ R seen_s(const R *f, const uint16_t *flag, int a, int m, uint32_t wall_bit, R coef,
+                                    R size, const R *rho, int r0, int r1)
+{
+    const R fm = f[m];
+    if constexpr (!WALLS) {
+        return fm;
+    } else {
+        if (!(flag[m] & wall_bit)) return fm;
+        const R fa = f[a];
+        if (!positive(coef)) return R(2) * fm - fa;
+        const R sl = coef * recip(R(0.5) * (rho[r0] + rho[r1]));
+        const R h = R(0.5) * size;
+        return R(2) * ((h * fm + sl * fa) * recip(h + sl)) - fa;
+    }
+}
+
 // Gamma at the corner (x^f_i, y^f_j): bilinear in the four cell centres.
 template <typename R>
 __device__ __forceinline__ R gamma_corner(const GeoT<R> &g, const R *gam, int c, int i, int j)
@@ -294,15 +318,18 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
 
 // T^explicit of cell (i,j), Eq. pl31_1, all inputs at level n-1.
 template <typename R, bool TVD>
-__device__ R explicit_T(const GeoT<R> &g, const LevelT<R> &L, const R *Fx, const R *Fy, int c, int i, int j)
+__device__ R explicit_T(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, const R *Fx, const R *Fy, int c,
+                       int i, int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
     const R dxi = at(g.x.d, i), dyj = at(g.y.d, j);
     const R *T = L.T;
     const R Tp = T[c];
-    const R Tw = seen(T, fl, c, c - 1, F_WALL), Te = seen(T, fl, c, c + 1, F_WALL);
-    const R Ts = seen(T, fl, c, c - P, F_WALL), Tn = seen(T, fl, c, c + P, F_WALL);
+    const R Tw = seen_s(T, fl, c, c - 1, F_WALL, k.tau, dxi, L.rho, c, c);
+    const R Te = seen_s(T, fl, c, c + 1, F_WALL, k.tau, dxi, L.rho, c, c);
+    const R Ts = seen_s(T, fl, c, c - P, F_WALL, k.tau, dyj, L.rho, c, c);
+    const R Tn = seen_s(T, fl, c, c + P, F_WALL, k.tau, dyj, L.rho, c, c);
     const R uw = L.u[c], ue = L.u[c + 1], vs = L.v[c], vn = L.v[c + P];
     const R Fw = Fx[c], Fe = Fx[c + 1], Fs = Fy[c], Fn = Fy[c + P];
     R pw = 0.0, pe = 0.0, ps = 0.0, pn = 0.0;
@@ -326,13 +353,15 @@ __device__ R explicit_T(const GeoT<R> &g, const LevelT<R> &L, const R *Fx, const
 
 // v^explicit of v face (i,j), Eq. pl15_11, level n-1.
 template <typename R, bool TVD>
-__device__ R explicit_v(const GeoT<R> &g, const LevelT<R> &L, const R *Fx, int b, int i, int j)
+__device__ R explicit_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, const R *Fx, int b, int i, int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
     const R *v = L.v, *u = L.u;
     const R dxi = at(g.x.d, i), dys = at(g.y.d, j - 1), dyp = at(g.y.d, j);
-    const R vP = v[b], vW = seen(v, fl, b, b - 1, F_VWALL), vE = seen(v, fl, b, b + 1, F_VWALL);
+    const R vP = v[b];
+    const R vW = seen_s(v, fl, b, b - 1, F_VWALL, k.zeta, dxi, L.rho, b - P, b);
+    const R vE = seen_s(v, fl, b, b + 1, F_VWALL, k.zeta, dxi, L.rho, b - P, b);
     const R vS = v[b - P], vN = v[b + P];
     const R uw1 = u[b - P], uw2 = u[b], ue1 = u[b + 1 - P], ue2 = u[b + 1];
     const R Fw1 = Fx[b - P], Fw2 = Fx[b], Fe1 = Fx[b + 1 - P], Fe2 = Fx[b + 1];
@@ -368,13 +397,15 @@ __device__ R explicit_v(const GeoT<R> &g, const LevelT<R> &L, const R *Fx, int b
 
 // u^explicit of u face (i,j): the mirror image of Eq. pl15_11, level n-1.
 template <typename R, bool TVD>
-__device__ R explicit_u(const GeoT<R> &g, const LevelT<R> &L, const R *Fy, int a, int i, int j)
+__device__ R explicit_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, const R *Fy, int a, int i, int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
     const R *u = L.u, *v = L.v;
     const R dyj = at(g.y.d, j), dxw = at(g.x.d, i - 1), dxp = at(g.x.d, i);
-    const R uP = u[a], uS = seen(u, fl, a, a - P, F_UWALL), uN = seen(u, fl, a, a + P, F_UWALL);
+    const R uP = u[a];
+    const R uS = seen_s(u, fl, a, a - P, F_UWALL, k.zeta, dyj, L.rho, a - 1, a);
+    const R uN = seen_s(u, fl, a, a + P, F_UWALL, k.zeta, dyj, L.rho, a - 1, a);
     const R uW = u[a - 1], uE = u[a + 1];
     const R vs1 = v[a - 1], vs2 = v[a], vn1 = v[a - 1 + P], vn2 = v[a + P];
     const R Fs1 = Fy[a - 1], Fs2 = Fy[a], Fn1 = Fy[a - 1 + P], Fn2 = Fy[a + P];
@@ -409,18 +440,18 @@ __device__ R explicit_u(const GeoT<R> &g, const LevelT<R> &L, const R *Fy, int a
 }
 
 template <typename R, bool TVD>
-__device__ __forceinline__ void explicit_terms_body(const GeoT<R> &g, const LevelT<R> &prev, const WorkT<R> &w, int i,
-                                                    int j)
+__device__ __forceinline__ void explicit_terms_body(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev,
+                                                    const WorkT<R> &w, int i, int j)
 {
     const int c = Ix{g.pitch}(i, j);
     if (i > g.nx || j > g.ny) return;
     const uint16_t f = g.flag[c];
     if (i < g.nx && j < g.ny)
-        w.Texp[c] = (f & F_FLUID) ? explicit_T<R, TVD>(g, prev, w.Fx, w.Fy, c, i, j) : R(0);
+        w.Texp[c] = (f & F_FLUID) ? explicit_T<R, TVD>(g, k, prev, w.Fx, w.Fy, c, i, j) : R(0);
     if (j < g.ny)
-        w.uexp[c] = (f & F_UACT) ? explicit_u<R, TVD>(g, prev, w.Fy, c, i, j) : R(0);
+        w.uexp[c] = (f & F_UACT) ? explicit_u<R, TVD>(g, k, prev, w.Fy, c, i, j) : R(0);
     if (i < g.nx)
-        w.vexp[c] = (f & F_VACT) ? explicit_v<R, TVD>(g, prev, w.Fx, c, i, j) : R(0);
+        w.vexp[c] = (f & F_VACT) ? explicit_v<R, TVD>(g, k, prev, w.Fx, c, i, j) : R(0);
 }
 
 // ------------------------------------------------------------ temperature
@@ -441,15 +472,20 @@ __device__ R energy_source(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> 
     const R xl0 = at(g.x.wlo, i), xh0 = at(g.x.whi, i), xl1 = at(g.x.wlo, i + 1), xh1 = at(g.x.whi, i + 1);
     const R yl0 = at(g.y.wlo, j), yh0 = at(g.y.whi, j), yl1 = at(g.y.wlo, j + 1), yh1 = at(g.y.whi, j + 1);
     // v at (x^f_i, y^v_j) and (x^f_{i+1}, y^v_j)
-    const R v_w = R(0.5) * ((xl0 * seen<R, WALLS>(v, fl, c, c - 1, F_VWALL) + xh0 * v[c])
-                              + (xl0 * seen<R, WALLS>(v, fl, c + P, c + P - 1, F_VWALL) + xh0 * v[c + P]));
-    const R v_e = R(0.5) * ((xl1 * v[c] + xh1 * seen<R, WALLS>(v, fl, c, c + 1, F_VWALL))
-                              + (xl1 * v[c + P] + xh1 * seen<R, WALLS>(v, fl, c + P, c + P + 1, F_VWALL)));
+    const R *rho = L.rho;
+    const R v_w = R(0.5) * ((xl0 * seen_s<R, WALLS>(v, fl, c, c - 1, F_VWALL, k.zeta, dxi, rho, c - P, c) + xh0 * v[c])
+                              + (xl0 * seen_s<R, WALLS>(v, fl, c + P, c + P - 1, F_VWALL, k.zeta, dxi, rho, c, c + P)
+                                 + xh0 * v[c + P]));
+    const R v_e = R(0.5) * ((xl1 * v[c] + xh1 * seen_s<R, WALLS>(v, fl, c, c + 1, F_VWALL, k.zeta, dxi, rho, c - P, c))
+                              + (xl1 * v[c + P]
+                                 + xh1 * seen_s<R, WALLS>(v, fl, c + P, c + P + 1, F_VWALL, k.zeta, dxi, rho, c, c + P)));
     // u at (x^v_i, y^f_j) and (x^v_i, y^f_{j+1})
-    const R u_s = R(0.5) * ((yl0 * seen<R, WALLS>(u, fl, c, c - P, F_UWALL) + yh0 * u[c])
-                              + (yl0 * seen<R, WALLS>(u, fl, c + 1, c + 1 - P, F_UWALL) + yh0 * u[c + 1]));
-    const R u_n = R(0.5) * ((yl1 * u[c] + yh1 * seen<R, WALLS>(u, fl, c, c + P, F_UWALL))
-                              + (yl1 * u[c + 1] + yh1 * seen<R, WALLS>(u, fl, c + 1, c + 1 + P, F_UWALL)));
+    const R u_s = R(0.5) * ((yl0 * seen_s<R, WALLS>(u, fl, c, c - P, F_UWALL, k.zeta, dyj, rho, c - 1, c) + yh0 * u[c])
+                              + (yl0 * seen_s<R, WALLS>(u, fl, c + 1, c + 1 - P, F_UWALL, k.zeta, dyj, rho, c, c + 1)
+                                 + yh0 * u[c + 1]));
+    const R u_n = R(0.5) * ((yl1 * u[c] + yh1 * seen_s<R, WALLS>(u, fl, c, c + P, F_UWALL, k.zeta, dyj, rho, c - 1, c))
+                              + (yl1 * u[c + 1]
+                                 + yh1 * seen_s<R, WALLS>(u, fl, c + 1, c + 1 + P, F_UWALL, k.zeta, dyj, rho, c, c + 1)));
     const R dvdx = (v_e - v_w) * rdx, dudy = (u_n - u_s) * rdy;
     const R div = dudx + dvdy, shear = dvdx + dudy;
     const R phi = R(2) * (dudx * dudx + dvdy * dvdy) + shear * shear - R(2.0 / 3.0) * div * div;
@@ -470,8 +506,10 @@ __device__ R temperature(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     const R dxi = at(g.x.d, i), dyj = at(g.y.d, j);
     const R dxw = at(g.x.d, i - 1), dxe = at(g.x.d, i + 1), dys = at(g.y.d, j - 1), dyn = at(g.y.d, j + 1);
     const R Tp = T[c];
-    const R Tw = seen<R, WALLS>(T, fl, c, c - 1, F_WALL), Te = seen<R, WALLS>(T, fl, c, c + 1, F_WALL);
-    const R Ts = seen<R, WALLS>(T, fl, c, c - P, F_WALL), Tn = seen<R, WALLS>(T, fl, c, c + P, F_WALL);
+    const R Tw = seen_s<R, WALLS>(T, fl, c, c - 1, F_WALL, k.tau, dxi, old.rho, c, c);
+    const R Te = seen_s<R, WALLS>(T, fl, c, c + 1, F_WALL, k.tau, dxi, old.rho, c, c);
+    const R Ts = seen_s<R, WALLS>(T, fl, c, c - P, F_WALL, k.tau, dyj, old.rho, c, c);
+    const R Tn = seen_s<R, WALLS>(T, fl, c, c + P, F_WALL, k.tau, dyj, old.rho, c, c);
     const R uw = old.u[c], ue = old.u[c + 1], vs = old.v[c], vn = old.v[c + P];
     const R Fw = w.Fx[c], Fe = w.Fx[c + 1], Fs = w.Fy[c], Fn = w.Fy[c + P];
     const R Dw = w.DTx[c], De = w.DTx[c + 1], Ds = w.DTy[c], Dn = w.DTy[c + P];
@@ -531,7 +569,8 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     const R dxw = at(g.x.d, i - 1), dxp = at(g.x.d, i), dyj = at(g.y.d, j);
     const R uP = u[a];
     const R uW = seen<R, WALLS>(u, fl, a, a - 1, F_UWALL), uE = seen<R, WALLS>(u, fl, a, a + 1, F_UWALL);
-    const R uS = seen<R, WALLS>(u, fl, a, a - P, F_UWALL), uN = seen<R, WALLS>(u, fl, a, a + P, F_UWALL);
+    const R uS = seen_s<R, WALLS>(u, fl, a, a - P, F_UWALL, k.zeta, dyj, rho, a - 1, a);
+    const R uN = seen_s<R, WALLS>(u, fl, a, a + P, F_UWALL, k.zeta, dyj, rho, a - 1, a);
     const R ubw = R(0.5) * (uW + uP), ube = R(0.5) * (uP + uE);
     const R Fbw = ubw * rho[a - 1] * dyj, Fbe = ube * rho[a] * dyj;
     const R vs1 = v[a - 1], vs2 = v[a], vn1 = v[a - 1 + P], vn2 = v[a + P];
@@ -608,7 +647,8 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     const R *u = old.u, *v = old.v, *gam = old.gam, *rho = old.rho;
     const R dys = at(g.y.d, j - 1), dyp = at(g.y.d, j), dxi = at(g.x.d, i);
     const R vP = v[b];
-    const R vW = seen<R, WALLS>(v, fl, b, b - 1, F_VWALL), vE = seen<R, WALLS>(v, fl, b, b + 1, F_VWALL);
+    const R vW = seen_s<R, WALLS>(v, fl, b, b - 1, F_VWALL, k.zeta, dxi, rho, b - P, b);
+    const R vE = seen_s<R, WALLS>(v, fl, b, b + 1, F_VWALL, k.zeta, dxi, rho, b - P, b);
     const R vS = seen<R, WALLS>(v, fl, b, b - P, F_VWALL), vN = seen<R, WALLS>(v, fl, b, b + P, F_VWALL);
     const R vbs = R(0.5) * (vS + vP), vbn = R(0.5) * (vP + vN);
     const R Fbs = vbs * rho[b - P] * dxi, Fbn = vbn * rho[b] * dxi;
@@ -1077,11 +1117,11 @@ __global__ void __launch_bounds__(256) k_explicit(const __grid_constant__ BatchP
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
         if constexpr (PREC == PREC_MIXED)
-            explicit_terms_body<float, TVD>(I.g32, I.lv32[prev], I.w32, i, j);
+            explicit_terms_body<float, TVD>(I.g32, I.k32, I.lv32[prev], I.w32, i, j);
         else if constexpr (PREC == PREC_DF64)
-            explicit_terms_body<df64, TVD>(I.gdf, I.lvdf[prev], I.wdf, i, j);
+            explicit_terms_body<df64, TVD>(I.gdf, I.kdf, I.lvdf[prev], I.wdf, i, j);
         else
-            explicit_terms_body<double, TVD>(I.g, I.lv[prev], I.w, i, j);
+            explicit_terms_body<double, TVD>(I.g, I.k, I.lv[prev], I.w, i, j);
     });
 }
 

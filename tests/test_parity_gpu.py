@@ -328,3 +328,47 @@ def test_df64_restart_through_host_fields_continues():
         c.step(10)
         again = c.fields()
     assert_parity(again, full, tol=1e-12)
+
+
+# ------------------------------------------------- slip and jump walls (Eqs. pl38, pl39)
+
+def slip_case(implicit, tvd, precision=W.FP64):
+    # the paper's microchannel set-up (moving walls, square particle, hard-sphere
+    # gas) at Kn = 0.05, where the slip velocity and the temperature jump are
+    # large enough to matter at every wall and on the obstacle
+    return W.paper_channel(ny=40, nx=160, kn=0.05, side=8, inlet=24, implicit=implicit, tvd=tvd).replace(
+        perturb=1e-3, seed=13, precision=precision)
+
+
+@pytest.mark.parametrize("precision", [W.FP64, W.DF64], ids=["fp64", "df64"])
+@pytest.mark.parametrize("implicit,tvd", SCHEMES)
+def test_parity_slip_and_jump_walls(implicit, tvd, precision):
+    case = slip_case(implicit, tvd, precision)
+    n = (df64_steps_for if precision == W.DF64 else steps_for)(implicit, tvd, 40)
+    g, o, gres, ores, *_ = run_both(case, n)
+    e = assert_parity(g, o, what=f"slip {n} steps")
+    print("slip", implicit, tvd, precision, e)
+    np.testing.assert_allclose(gres, ores, rtol=1e-6, atol=1e-12)
+    # the slip and jump terms are exercised: without them the fields differ
+    o0, _, _ = oracle.run(case.replace(zeta_coef=0.0, tau_coef=0.0), None, nsteps=n)
+    assert max(rel_err(o, o0).values()) > 1e-4
+
+
+def test_mixed_precision_slip_walls_error():
+    case = slip_case(True, False, W.MIXED)
+    with sim.Simulation(case) as s:
+        start = s.fields()
+        s.step(40)
+        g = s.fields()
+    o, _, _ = oracle.run(case.replace(precision=W.FP64), start, nsteps=40)
+    e = rel_err(g, o)
+    print("mixed slip", e)
+    assert max(e.values()) <= MIXED_BOUND, e
+
+
+@pytest.mark.parametrize("implicit,tvd", [(True, False), (False, True)], ids=["implicit-upwind", "explicit-tvd"])
+def test_parity_paper_channel_4032x200(implicit, tvd):
+    # the paper's own mesh (Section 4): 4032 x 200 cells of 0.05 a, Kn 0.001, M 2.43
+    case = W.paper_channel(ny=200, implicit=implicit, tvd=tvd)
+    g, o, *_ = run_both(case, 3)
+    assert_parity(g, o)

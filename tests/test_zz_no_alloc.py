@@ -52,6 +52,7 @@ CASES = {
         nx=27, ny=21, dx=np.linspace(0.2, 0.3, 27), dy=np.linspace(0.3, 0.2, 21), lx=float(np.linspace(0.2, 0.3, 27).sum()),
         ly=float(np.linspace(0.3, 0.2, 21).sum()), perturb=1e-3, seed=31),
     "symmetry-sides": lambda: W.uniform_flow(nx=40, ny=18).replace(rects=[[9, 6, 13, 11]], perturb=1e-3),
+    "slip-jump-walls": lambda: W.paper_channel(ny=40, nx=160, kn=0.05, side=8, inlet=24).replace(perturb=1e-3),
 }
 
 
