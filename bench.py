@@ -34,12 +34,12 @@ UNIT = "Mcell-steps/s"
 # The dominant kernel, k_assemble (FP64, implicit upwind), is bound by GB300's
 # FP64 pipe.  Its work per cell and loop-2 iteration is counted by ncu on one
 # launch for the 2048x512 channel (1,048,576 cells): DFMA, DADD and DMUL thread
-# instructions 67.04 M, 65.51 M, 81.47 M.
-ASSEMBLE_FP64_INST_PER_CELL = {"dfma": 63.93, "dadd": 62.48, "dmul": 77.70}
+# instructions 67.04 M, 64.36 M, 81.47 M.
+ASSEMBLE_FP64_INST_PER_CELL = {"dfma": 63.93, "dadd": 61.38, "dmul": 77.70}
 # DRAM bytes of that launch per cell (110.7 MB read + 19.3 MB written).
 ASSEMBLE_DRAM_BYTES_PER_CELL = 124.0
 # ncu: sm__pipe_fp64_cycles_active of that launch, fraction of peak.
-ASSEMBLE_FP64_PIPE_ACTIVE = 0.859
+ASSEMBLE_FP64_PIPE_ACTIVE = 0.855
 # Algorithmic HBM traffic of the kernel per cell: reads u, v, p, T, rho, Gamma of
 # the previous iterate, u, v, T, rho of level n-1 and the face arrays F^x, F^y,
 # D^T_x, D^T_y, B Gamma (corner), B Gamma dy/dx, B Gamma dx/dy (17 doubles);
@@ -80,6 +80,8 @@ WORKLOADS = {
     "c3-explicit": lambda W: W.c3_large(implicit=False),
     "c4": lambda W: W.c4_paper_scale(),
     "profile": lambda W: W.profile_channel(),
+    "paper": lambda W: W.paper_channel(ny=400),
+    "paper-4000": lambda W: W.paper_channel(ny=4000),
 }
 _ARGS = None
 

@@ -1125,8 +1125,11 @@ __global__ void __launch_bounds__(256) k_explicit(const __grid_constant__ BatchP
     });
 }
 
+// Resident CTAs per SM: two for the FP64 assembly (bound by the FP64 pipe),
+// three for the FP32 and double-float ones, which are latency-bound.
 template <int PREC, bool IMPL, bool TVD>
-__global__ void __launch_bounds__(256) k_assemble(const __grid_constant__ BatchPlan bp, int prev, int old, int nw)
+__global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 2 : 3) k_assemble(const __grid_constant__ BatchPlan bp,
+                                                                              int prev, int old, int nw)
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
         if constexpr (PREC == PREC_MIXED)
