@@ -354,27 +354,23 @@ def run_ours(args, rank, world, local_rank):
     df64 = variant(W.DF64, "df64 (float pairs, about 48 bits) in every kernel; f64 state on read-out")
 
     # end to end through the C ABI with host buffers: every step uploads its
-    # input state from pinned host memory and reads the new state and the
-    # residuals back
+    # input state from pinned host memory (sim_set_state), advances one step
+    # and reads the new state and the residuals back (sim_get_state)
     host = {k: torch.from_numpy(v).pin_memory() for k, v in s.fields().items()}
     h2d = sum(v.numel() * 8 for v in host.values())
     d2h = h2d + 4 * 8
     views = {k: v.numpy() for k, v in host.items()}
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
     for _ in range(2):
-        s.set_fields(views); s.step(1)
-        for k in views: s.field(k, out=views[k])
-        s.residuals()
+        s.set_state(views); s.step(1); s.get_state(views)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        s.set_fields(views)
+        s.set_state(views)
         s.step(1)
-        for k in views:
-            s.field(k, out=views[k])
-        s.residuals()
+        s.get_state(views)
     e2e_s = time.perf_counter() - t0
     e2e_value = throughput(case.cells, e2e_steps, world, reduce_max(e2e_s, dist, "cuda"))
     s.close()

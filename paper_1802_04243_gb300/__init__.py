@@ -74,6 +74,8 @@ _SIGNATURES = {
     "sim_field_ptr": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
                        ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "sim_set_fields": ([ctypes.c_void_p, ctypes.c_int, _DP, ctypes.c_size_t], ctypes.c_int),
+    "sim_set_state": ([ctypes.c_void_p, _DP, _DP, _DP, _DP], ctypes.c_int),
+    "sim_get_state": ([ctypes.c_void_p, _DP, _DP, _DP, _DP, _DP], ctypes.c_int),
     "sim_residuals": ([ctypes.c_void_p, _DP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sim_coefficients": ([ctypes.c_void_p, _DP], ctypes.c_int),
     "sim_profile": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
@@ -228,6 +230,27 @@ class Simulation:
         for k in ("u", "v", "p", "T"):
             if k in state:
                 self.set_field(k, state[k])
+
+    def set_state(self, state: Dict[str, np.ndarray]):
+        """All of u, v, p, T at once (sim_set_state): one synchronisation, checks on the device."""
+        arrs = []
+        for k in ("u", "v", "p", "T"):
+            a = np.ascontiguousarray(state[k], dtype=np.float64)
+            if a.shape != self.shape(k):
+                raise ValueError(f"{k}: shape {a.shape} != {self.shape(k)}")
+            arrs.append(a)
+        self._check(self.lib.sim_set_state(self.handle, *[a.ctypes.data_as(_DP) for a in arrs]))
+
+    def get_state(self, out: Optional[Dict[str, np.ndarray]] = None):
+        """u, v, p, T and the residuals (sim_get_state), with one synchronisation.
+        Returns (fields, residuals, status)."""
+        out = out if out is not None else {k: np.empty(self.shape(k)) for k in ("u", "v", "p", "T")}
+        res = np.zeros(4)
+        st = self.lib.sim_get_state(self.handle, *[out[k].ctypes.data_as(_DP) for k in ("u", "v", "p", "T")],
+                                    res.ctypes.data_as(_DP))
+        if st not in (SIM_OK, SIM_EDIVERGED):
+            self._check(st)
+        return out, res, st
 
     def residuals(self):
         out = np.zeros(4)

@@ -52,6 +52,9 @@ struct sim_s {
     uint16_t *d_flag = nullptr;
     double *d_axis = nullptr;
     double *d_stage = nullptr;                 // logical-shape staging array
+    double *d_state = nullptr;                 // u, v, p, T staged back to back (allocated on first use)
+    unsigned *d_bad = nullptr;                 // admissibility flag of a staged state
+    unsigned *h_bad = nullptr;                 // its pinned host copy
     // mixed precision: FP32 shadow levels, FP32 scratch and grid factors
     bool mixed = false;
     Mixed mx{};
@@ -896,6 +899,98 @@ extern "C" sim_status sim_set_fields(sim_t s, int field, const double *host_src,
     return SIM_OK;
 }
 
+namespace {
+
+// Residual words -> doubles; false if one is not finite.
+bool read_residuals(const unsigned long long *bits, double out[4])
+{
+    bool ok = true;
+    for (int q = 0; q < 4; q++) {
+        std::memcpy(&out[q], &bits[q], sizeof(double));
+        if (!std::isfinite(out[q])) ok = false;
+    }
+    return ok;
+}
+
+sim_status ensure_state_stage(sim_t s)
+{
+    if (s->d_state) return SIM_OK;
+    const size_t n = 4 * (size_t)(s->pb.nx + 1) * (s->pb.ny + 1);
+    if (cudaMalloc(&s->d_state, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&s->d_bad, sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost(&s->h_bad, sizeof(unsigned)) != cudaSuccess) {
+        cudaFree(s->d_state);
+        cudaFree(s->d_bad);
+        s->d_state = nullptr;
+        s->d_bad = nullptr;
+        return fail(s, SIM_ENOMEM, "no memory for the state staging area");
+    }
+    return SIM_OK;
+}
+
+}  // namespace
+
+extern "C" sim_status sim_set_state(sim_t s, const double *u, const double *v, const double *p, const double *T)
+{
+    if (!s) return SIM_EINVAL;
+    if (!u || !v || !p || !T) return fail(s, SIM_EINVAL, "null state array");
+    sim_status st = ensure_state_stage(s);
+    if (st != SIM_OK) return st;
+    const size_t nu = field_count(s->pb, SIM_FIELD_U), nv = field_count(s->pb, SIM_FIELD_V);
+    const size_t nc = field_count(s->pb, SIM_FIELD_P);
+    const double *src[4] = {u, v, p, T};
+    const size_t off[4] = {0, nu, nu + nv, nu + nv + nc}, cnt[4] = {nu, nv, nc, nc};
+    CUDA_TRY(s, cudaMemsetAsync(s->d_bad, 0, sizeof(unsigned), s->stream));
+    for (int f = 0; f < 4; f++)
+        CUDA_TRY(s, cudaMemcpyAsync(s->d_state + off[f], src[f], cnt[f] * sizeof(double), cudaMemcpyHostToDevice,
+                                    s->stream));
+    launch_validate_state(s->d_state, nu, nv, nc, s->d_bad, s->stream);
+    CUDA_TRY(s, cudaMemcpyAsync(s->h_bad, s->d_bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    if (*s->h_bad) return fail(s, SIM_EINVAL, "state not admissible (non-finite value, or p or T <= 0)");
+    // every unknown is overwritten: the FP64 level needs no refresh from the
+    // double-float one first
+    const Level &L = s->lv[s->cur];
+    for (int f = 0; f < 4; f++) launch_scatter(s->geo, f, s->d_state + off[f], L, s->stream);
+    launch_derive(s->geo, s->pb.k, L, s->stream);
+    launch_ghosts(s->geo, s->sides, L, false, s->stream);
+    if (s->mixed) launch_shadow(s->geo, L, s->mx.lv[s->cur], s->nelem, s->stream);
+    if (s->df) launch_split(L, s->dfm.lv[s->cur], s->nelem, s->stream);
+    s->df_dirty = false;
+    CUDA_TRY(s, cudaGetLastError());
+    s->diverged = false;
+    s->set_mask = 0;
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_get_state(sim_t s, double *u, double *v, double *p, double *T, double res[4])
+{
+    if (!s) return SIM_EINVAL;
+    if (!u || !v || !p || !T) return fail(s, SIM_EINVAL, "null state array");
+    sim_status st = ensure_state_stage(s);
+    if (st != SIM_OK) return st;
+    const size_t nu = field_count(s->pb, SIM_FIELD_U), nv = field_count(s->pb, SIM_FIELD_V);
+    const size_t nc = field_count(s->pb, SIM_FIELD_P);
+    double *dst[4] = {u, v, p, T};
+    const size_t off[4] = {0, nu, nu + nv, nu + nv + nc}, cnt[4] = {nu, nv, nc, nc};
+    sync_out(s);
+    for (int f = 0; f < 4; f++) launch_gather(s->geo, f, s->lv[s->cur], s->d_state + off[f], s->stream);
+    CUDA_TRY(s, cudaGetLastError());
+    for (int f = 0; f < 4; f++)
+        CUDA_TRY(s, cudaMemcpyAsync(dst[f], s->d_state + off[f], cnt[f] * sizeof(double), cudaMemcpyDeviceToHost,
+                                    s->stream));
+    if (res)
+        CUDA_TRY(s, cudaMemcpyAsync(s->h_res, s->work.res, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                    s->stream));
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    if (res && !read_residuals(s->h_res, res)) {
+        s->diverged = true;
+        s->set_mask = 0;
+        return fail(s, SIM_EDIVERGED, "non-finite residual");
+    }
+    return SIM_OK;
+}
+
 extern "C" sim_status sim_residuals(sim_t s, double out[4], int *iters_last_step)
 {
     if (!s || !out) return SIM_EINVAL;
@@ -969,6 +1064,9 @@ extern "C" void sim_destroy(sim_t s)
     cudaFree(s->d_flag);
     cudaFree(s->d_axis);
     cudaFree(s->d_stage);
+    cudaFree(s->d_state);
+    cudaFree(s->d_bad);
+    if (s->h_bad) cudaFreeHost(s->h_bad);
     cudaFree(s->work.res);
     cudaFree(s->d_pool32);
     cudaFree(s->d_axis32);

@@ -175,6 +175,8 @@ int ghost_kernels(const Sides &s, bool after_velocity);
 void launch_derive(const Geo &g, const Coef &c, const Level &lv, void *stream);
 void launch_scatter(const Geo &g, int field, const double *src, const Level &lv, void *stream);
 void launch_gather(const Geo &g, int field, const Level &lv, double *dst, void *stream);
+// Sets *bad (|= 1) if a value of the staged u, v, p, T is not finite or p, T <= 0.
+void launch_validate_state(const double *stage, size_t nu, size_t nv, size_t nc, unsigned *bad, void *stream);
 void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, size_t nelem, void *stream);
 // Whole-level conversions between FP64 and double-float (ghosts included).
 void launch_split(const Level &lv, const LevelT<df64> &d, size_t nelem, void *stream);

@@ -1256,6 +1256,21 @@ __global__ void k_recip_check(const double *x, double *out, int n)
     out[2 * q + 1] = 1.0 / x[q];
 }
 
+// Admissibility of a staged state (u, v, p, T back to back): every value
+// finite, p and T positive.  Bit tests only.
+__global__ void k_validate_state(const double *st, size_t nu, size_t nv, size_t nc, unsigned *bad)
+{
+    const size_t n = nu + nv + 2 * nc;
+    unsigned b = 0;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long x = (unsigned long long)__double_as_longlong(st[q]);
+        const bool finite = ((x >> 52) & 0x7FFull) != 0x7FFull;
+        const bool need_positive = q >= nu + nv;
+        if (!finite || (need_positive && !positive(st[q]))) b = 1u;
+    }
+    if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+
 template <typename R>
 dim3 grid_of(const GeoT<R> &g)
 {
@@ -1332,6 +1347,13 @@ void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, siz
 void launch_recip_check(const double *x, double *out, int n, void *stream)
 {
     if (n > 0) k_recip_check<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(x, out, n);
+}
+
+void launch_validate_state(const double *stage, size_t nu, size_t nv, size_t nc, unsigned *bad, void *stream)
+{
+    const size_t n = nu + nv + 2 * nc;
+    const int blocks = (int)((n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048);
+    k_validate_state<<<blocks, 256, 0, (cudaStream_t)stream>>>(stage, nu, nv, nc, bad);
 }
 
 void launch_derive(const Geo &g, const Coef &c, const Level &lv, void *stream)

@@ -67,6 +67,8 @@ def _create(case):
     dict(tol=-1.0),
     dict(precision=7),
     dict(side_T=(1.0, 1.0, 0.0, 1.0)),
+    dict(zeta_coef=-0.1),
+    dict(tau_coef=float("nan")),
 ])
 def test_invalid_descriptions_are_rejected_on_the_host(lib, bad):
     case = W.c1_small().replace(**bad)
@@ -88,5 +90,7 @@ def test_batch_rejects_inconsistent_descriptions_on_the_host(lib):
 
 def test_null_arguments(lib):
     assert lib.sim_create(None, None, None, None, None) == sim.SIM_EINVAL
+    assert lib.sim_set_state(None, None, None, None, None) == sim.SIM_EINVAL
+    assert lib.sim_get_state(None, None, None, None, None, None) == sim.SIM_EINVAL
     lib.sim_destroy(None)
     assert lib.sim_last_error(None) == b"null handle"

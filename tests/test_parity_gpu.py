@@ -372,3 +372,56 @@ def test_parity_paper_channel_4032x200(implicit, tvd):
     case = W.paper_channel(ny=200, implicit=implicit, tvd=tvd)
     g, o, *_ = run_both(case, 3)
     assert_parity(g, o)
+
+
+# ------------------------------------------------- whole-state calls
+
+@pytest.mark.parametrize("precision", [W.FP64, W.MIXED, W.DF64], ids=["fp64", "mixed", "df64"])
+def test_state_calls_match_field_calls(precision):
+    # sim_set_state / sim_get_state (one synchronisation each) give the bits of
+    # four sim_set_fields / sim_fields calls
+    case = W.c1_small().replace(precision=precision)
+    with sim.Simulation(case) as a, sim.Simulation(case) as b:
+        a.step(3)
+        mid = a.fields()
+        b.set_fields(mid)
+        a.set_state(mid)
+        a.step(4)
+        b.step(4)
+        got, res, st = a.get_state()
+        ref = b.fields()
+        rres, _, _ = b.residuals()
+    assert st == sim.SIM_OK
+    for k in "uvpT":
+        assert np.array_equal(got[k], ref[k]), k
+    assert np.array_equal(res, rres)
+
+
+def test_set_state_rejects_inadmissible_values_and_changes_nothing():
+    case = W.c1_small()
+    with sim.Simulation(case) as s:
+        s.step(2)
+        before = s.fields()
+        bad = {k: v.copy() for k, v in before.items()}
+        bad["T"][3, 5] = -1.0
+        with pytest.raises(sim.SimError) as e:
+            s.set_state(bad)
+        assert e.value.status == sim.SIM_EINVAL
+        bad = {k: v.copy() for k, v in before.items()}
+        bad["u"][0, 0] = np.nan
+        with pytest.raises(sim.SimError):
+            s.set_state(bad)
+        after = s.fields()
+    for k in "uvpT":
+        assert np.array_equal(before[k], after[k]), k
+
+
+def test_set_state_clears_a_diverged_handle():
+    case = W.c1_small().replace(implicit=True, tvd=False, cfl=3.0)
+    with sim.Simulation(case) as s:
+        start = s.fields()
+        s.step(200)
+        _, _, st = s.residuals()
+        assert st == sim.SIM_EDIVERGED
+        s.set_state(start)
+        s.step(1)
