@@ -427,6 +427,7 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+            "mcell_iterations_per_s": round(value * case.iters, 3),
             "gpu_launches": int(launches),
             "kernel_ms_avg": {k: round(ms / n, 5) for k, (ms, n) in prof.items() if n},
             "kernel_timing": f"separate pass of {prof_steps} steps with per-launch CUDA events",
