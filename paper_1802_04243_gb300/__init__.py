@@ -199,6 +199,7 @@ class Simulation:
         if st != SIM_OK:
             raise SimError(st, "sim_create failed (invalid description or no device)")
         self.handle = h
+        self._stream = stream or 0
         self.scheme = scheme_of(case.implicit, case.tvd)
 
     def _check(self, st: int):
@@ -272,6 +273,10 @@ class Simulation:
         dev = ctypes.c_void_p()
         pitch = ctypes.c_size_t()
         self._check(self.lib.sim_field_ptr(self.handle, FIELDS[name], ctypes.byref(dev), ctypes.byref(pitch)))
+        if self._stream:
+            # the handle's stream may still be filling the array (double-float
+            # state): torch's current stream waits for it
+            torch.cuda.current_stream().wait_stream(torch.cuda.ExternalStream(self._stream))
         ny, nx = self.shape(name)
         base = dev.value - (2 * pitch.value + 2) * 8
         arr = _CudaArray(base, (ny + 4, nx + 4), (pitch.value * 8, 8))
