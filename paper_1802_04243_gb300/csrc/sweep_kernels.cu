@@ -19,8 +19,10 @@
 //
 // Boundary rules: wall ghost and obstacle cells hold the wall state; a
 // temperature or tangential velocity read across a wall is reflected about
-// the stored wall value (2 phi_wall - phi_reader); TVD corrections apply only
-// where the flag of the face says all four stencil nodes are unknowns.
+// the value at the wall surface (2 phi_s - phi_reader): the wall value, or
+// with velocity slip / temperature jump the value of Eqs. pl38, pl39 (seen_s);
+// TVD corrections apply only where the flag of the face says all four stencil
+// nodes are unknowns.
 #include <cuda_runtime.h>
 #include <math.h>
 
