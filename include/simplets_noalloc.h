@@ -26,7 +26,7 @@ extern "C" {
 
 /* Size of the static scratch in MiB.  Every GPU that loads the library holds
  * this much device memory until the process exits. */
-#define SIM_NOALLOC_SCRATCH_MB 72
+#define SIM_NOALLOC_SCRATCH_MB 96
 
 /* Advance the state held in the caller's device arrays by n_steps time steps,
  * exactly as sim_create + sim_step (FP64) would, without allocating anything:
@@ -45,10 +45,10 @@ extern "C" {
  *   loop-2 iteration (max |du|, |dv|, |dp|, |dT|); when given, the call waits
  *   for the stream.
  *
- * Scratch: one static 72 MiB device array holds three state levels, the
+ * Scratch: one static 96 MiB device array holds three state levels, the
  * scratch of the sweep, the geometry tables and the residual words, about
- * 276 bytes per element of the padded grid (pitch x (ny + 5), pitch =
- * nx + 5 rounded up to a multiple of 8): up to about 273,000 elements,
+ * 340 bytes per element of the padded grid (pitch x (ny + 5), pitch =
+ * nx + 5 rounded up to a multiple of 8): up to about 296,000 elements,
  * e.g. 1024 x 256 or 512 x 512 cells.  A larger problem returns SIM_ENOMEM
  * before any work is queued.
  *

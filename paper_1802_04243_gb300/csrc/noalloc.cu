@@ -346,7 +346,7 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     const size_t nelem = (size_t)pitch * (ny + 2 * G + 1);
     const int mx = nx + 2 * G + 1, my = ny + 2 * G + 1;
     Carver cv{(unsigned char *)base};
-    double *pool = cv.take<double>(34 * nelem);
+    double *pool = cv.take<double>(42 * nelem);
     uint16_t *flag = cv.take<uint16_t>(nelem);
     uint8_t *kind = cv.take<uint8_t>(nelem);
     uint8_t *side = cv.take<uint8_t>(nelem);
@@ -371,7 +371,7 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     if (bc->inflow_p) NA_TRY(cudaMemcpyAsync(cin + 2 * ny, bc->inflow_p, ny * sizeof(double), cudaMemcpyHostToDevice, s));
     if (bc->n_rect) NA_TRY(cudaMemcpyAsync(crect, bc->rect, 4 * bc->n_rect * sizeof(int), cudaMemcpyHostToDevice, s));
     // the scratch keeps the previous call's contents: clear the work arrays
-    NA_TRY(cudaMemsetAsync(pool + 18 * nelem, 0, 16 * nelem * sizeof(double), s));
+    NA_TRY(cudaMemsetAsync(pool + 18 * nelem, 0, 24 * nelem * sizeof(double), s));
 
     Setup su{};
     su.nx = nx; su.ny = ny; su.pitch = pitch;
@@ -404,6 +404,9 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     w.uhat = q; q += nelem; w.du = q; q += nelem;
     w.vhat = q; q += nelem; w.dv = q; q += nelem; w.uexp = q; q += nelem; w.vexp = q; q += nelem;
     w.Texp = q;
+    q += nelem;
+    double **lim[8] = {&w.psTx, &w.psTy, &w.psUx, &w.psUyU, &w.psUyD, &w.psVy, &w.psVxU, &w.psVxD};
+    for (double **x : lim) { *x = q; q += nelem; }
     w.res = res;
 
     Geo g{};
@@ -448,17 +451,17 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
         const int prev = cur;
         int old = prev;
         if (!implicit) {
-            launch_faces(plan, false, prev, tvd, s);
-            launch_explicit(plan, false, prev, tvd, s);
+            launch_faces(plan, PREC_FP64, prev, tvd, true, s);
+            launch_explicit(plan, PREC_FP64, prev, tvd, s);
         }
         for (int it = 0; it < bc->iters; it++) {
             int nw = (old + 1) % 3;
             if (nw == prev) nw = (nw + 1) % 3;
             NA_TRY(cudaMemsetAsync(res, 0, 4 * sizeof(unsigned long long), s));
-            launch_faces(plan, false, old, tvd, s);
-            launch_assemble(plan, false, prev, old, nw, implicit, tvd, s);
-            launch_pressure(plan, false, prev, old, nw, s);
-            launch_velocity(plan, false, old, nw, s);
+            launch_faces(plan, PREC_FP64, old, tvd, implicit, s);
+            launch_assemble(plan, PREC_FP64, prev, old, nw, implicit, tvd, s);
+            launch_pressure(plan, PREC_FP64, prev, old, nw, s);
+            launch_velocity(plan, PREC_FP64, old, nw, s);
             launch_ghosts(g, sides, lv[nw], true, s);
             old = nw;
         }

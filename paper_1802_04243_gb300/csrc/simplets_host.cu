@@ -445,6 +445,11 @@ Inst inst_of(const sim_s *s, int tx, int tile0)
 
 int prec_of(const sim_s *s) { return s->mixed ? PREC_MIXED : s->df ? PREC_DF64 : PREC_FP64; }
 
+// Arrays of one pool: three levels of six fields, then the iteration
+// scratch (WorkT), which starts at rho_u and is cleared at creation.
+constexpr int kWorkArrays = 24;
+constexpr int kPoolArrays = 3 * 6 + kWorkArrays;
+
 // Carve three state levels and the iteration scratch out of one pool.
 template <typename R>
 R *carve_levels(R *q, size_t nelem, LevelT<R> lv[3], WorkT<R> &w)
@@ -453,8 +458,9 @@ R *carve_levels(R *q, size_t nelem, LevelT<R> lv[3], WorkT<R> &w)
         R **f[6] = {&lv[l].u, &lv[l].v, &lv[l].p, &lv[l].T, &lv[l].rho, &lv[l].gam};
         for (R **x : f) { *x = q; q += nelem; }
     }
-    R **a[16] = {&w.rho_u, &w.rho_v, &w.Fx, &w.Fy, &w.DTx, &w.DTy, &w.Bgc, &w.Bgx, &w.Bgy,
-                 &w.uhat, &w.du, &w.vhat, &w.dv, &w.uexp, &w.vexp, &w.Texp};
+    R **a[kWorkArrays] = {&w.rho_u, &w.rho_v, &w.Fx, &w.Fy, &w.DTx, &w.DTy, &w.Bgc, &w.Bgx, &w.Bgy,
+                          &w.uhat, &w.du, &w.vhat, &w.dv, &w.uexp, &w.vexp, &w.Texp,
+                          &w.psTx, &w.psTy, &w.psUx, &w.psUyU, &w.psUyD, &w.psVy, &w.psVxU, &w.psVxD};
     for (R **x : a) { *x = q; q += nelem; }
     return q;
 }
@@ -521,7 +527,7 @@ struct Launch {
 // (explicit scheme only, once per step).  counts != nullptr: capture mode.
 void enqueue_explicit(sim_t s, int prev, bool tvd, cudaStream_t st, long long *counts)
 {
-    { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, prec_of(s), prev, tvd, st); }
+    { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, prec_of(s), prev, tvd, true, st); }
     { Launch l(s, SIM_K_EXPLICIT, st, counts); launch_explicit(s->plan, prec_of(s), prev, tvd, st); }
 }
 
@@ -534,7 +540,7 @@ int enqueue_iteration(sim_t s, int prev, int old, bool implicit, bool tvd, cudaS
     const int ng = ghost_kernels(s->sides, true);
     cudaMemsetAsync(s->work.res, 0, 4 * sizeof(unsigned long long), st);
     const int prec = prec_of(s);
-    { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, prec, old, tvd, st); }
+    { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, prec, old, tvd, implicit, st); }
     { Launch l(s, SIM_K_ASSEMBLE, st, counts); launch_assemble(s->plan, prec, prev, old, nw, implicit, tvd, st); }
     { Launch l(s, SIM_K_PRESSURE, st, counts); launch_pressure(s->plan, prec, prev, old, nw, st); }
     { Launch l(s, SIM_K_VELOCITY, st, counts); launch_velocity(s->plan, prec, old, nw, st); }
@@ -598,40 +604,14 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
     std::vector<uint16_t> flags = make_flags(h);
     std::vector<double> ax = make_axis(pb.dx), ay = make_axis(pb.dy);
 
-    // one pool for 3 levels x 6 fields + 16 work arrays
-    const size_t nfields = 3 * 6 + 16;
-    cudaError_t e = cudaMalloc(&s->d_pool, nfields * s->nelem * sizeof(double));
+    // one pool for 3 levels x 6 fields + the work arrays
+    cudaError_t e = cudaMalloc(&s->d_pool, kPoolArrays * s->nelem * sizeof(double));
     if (e != cudaSuccess) {
         sim_destroy(s);
         return e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA;
     }
-    double *q = s->d_pool;
-    for (int l = 0; l < 3; l++) {
-        Level &L = s->lv[l];
-        L.u = q; q += s->nelem;
-        L.v = q; q += s->nelem;
-        L.p = q; q += s->nelem;
-        L.T = q; q += s->nelem;
-        L.rho = q; q += s->nelem;
-        L.gam = q; q += s->nelem;
-    }
     Work &w = s->work;
-    w.rho_u = q; q += s->nelem;
-    w.rho_v = q; q += s->nelem;
-    w.Fx = q; q += s->nelem;
-    w.Fy = q; q += s->nelem;
-    w.DTx = q; q += s->nelem;
-    w.DTy = q; q += s->nelem;
-    w.Bgc = q; q += s->nelem;
-    w.Bgx = q; q += s->nelem;
-    w.Bgy = q; q += s->nelem;
-    w.uhat = q; q += s->nelem;
-    w.du = q; q += s->nelem;
-    w.vhat = q; q += s->nelem;
-    w.dv = q; q += s->nelem;
-    w.uexp = q; q += s->nelem;
-    w.vexp = q; q += s->nelem;
-    w.Texp = q; q += s->nelem;
+    carve_levels(s->d_pool, s->nelem, s->lv, static_cast<WorkT<double> &>(w));
     const size_t nax = ax.size(), nay = ay.size();
     const size_t stage = (size_t)(pb.nx + 1) * (pb.ny + 1);
     if (cudaMalloc(&s->d_flag, flags.size() * sizeof(uint16_t)) != cudaSuccess ||
@@ -655,38 +635,12 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
 
     s->mixed = pb.precision == SIM_MIXED;
     if (s->mixed) {
-        if (cudaMalloc(&s->d_pool32, 34 * s->nelem * sizeof(float)) != cudaSuccess ||
+        if (cudaMalloc(&s->d_pool32, kPoolArrays * s->nelem * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&s->d_axis32, (nax + nay) * sizeof(float)) != cudaSuccess) {
             sim_destroy(s);
             return SIM_ENOMEM;
         }
-        float *p32 = s->d_pool32;
-        for (int l = 0; l < 3; l++) {
-            LevelT<float> &L = s->mx.lv[l];
-            L.u = p32; p32 += s->nelem;
-            L.v = p32; p32 += s->nelem;
-            L.p = p32; p32 += s->nelem;
-            L.T = p32; p32 += s->nelem;
-            L.rho = p32; p32 += s->nelem;
-            L.gam = p32; p32 += s->nelem;
-        }
-        WorkT<float> &w32 = s->mx.w;
-        w32.rho_u = p32; p32 += s->nelem;
-        w32.rho_v = p32; p32 += s->nelem;
-        w32.Fx = p32; p32 += s->nelem;
-        w32.Fy = p32; p32 += s->nelem;
-        w32.DTx = p32; p32 += s->nelem;
-        w32.DTy = p32; p32 += s->nelem;
-        w32.Bgc = p32; p32 += s->nelem;
-        w32.Bgx = p32; p32 += s->nelem;
-        w32.Bgy = p32; p32 += s->nelem;
-        w32.uhat = p32; p32 += s->nelem;
-        w32.du = p32; p32 += s->nelem;
-        w32.vhat = p32; p32 += s->nelem;
-        w32.dv = p32; p32 += s->nelem;
-        w32.uexp = p32; p32 += s->nelem;
-        w32.vexp = p32; p32 += s->nelem;
-        w32.Texp = p32;
+        carve_levels(s->d_pool32, s->nelem, s->mx.lv, s->mx.w);
         const float *fx = s->d_axis32, *fy = s->d_axis32 + nax;
         s->mx.g.nx = pb.nx;
         s->mx.g.ny = pb.ny;
@@ -702,12 +656,12 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         for (size_t q = 0; q < nax; q++) a32[q] = (float)ax[q];
         for (size_t q = 0; q < nay; q++) a32[nax + q] = (float)ay[q];
         CUDA_TRY(s, cudaMemcpy(s->d_axis32, a32.data(), a32.size() * sizeof(float), cudaMemcpyHostToDevice));
-        CUDA_TRY(s, cudaMemsetAsync(s->mx.w.rho_u, 0, 16 * s->nelem * sizeof(float), s->stream));
+        CUDA_TRY(s, cudaMemsetAsync(s->mx.w.rho_u, 0, kWorkArrays * s->nelem * sizeof(float), s->stream));
     }
 
     s->df = pb.precision == SIM_DF64;
     if (s->df) {
-        if (cudaMalloc(&s->d_pooldf, 34 * s->nelem * sizeof(df64)) != cudaSuccess ||
+        if (cudaMalloc(&s->d_pooldf, kPoolArrays * s->nelem * sizeof(df64)) != cudaSuccess ||
             cudaMalloc(&s->d_axisdf, (nax + nay) * sizeof(df64)) != cudaSuccess) {
             sim_destroy(s);
             return SIM_ENOMEM;
@@ -729,7 +683,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         for (size_t q = 0; q < nax; q++) adf[q] = dfl::split_host(ax[q]);
         for (size_t q = 0; q < nay; q++) adf[nax + q] = dfl::split_host(ay[q]);
         CUDA_TRY(s, cudaMemcpy(s->d_axisdf, adf.data(), adf.size() * sizeof(df64), cudaMemcpyHostToDevice));
-        CUDA_TRY(s, cudaMemsetAsync(s->dfm.w.rho_u, 0, 16 * s->nelem * sizeof(df64), s->stream));
+        CUDA_TRY(s, cudaMemsetAsync(s->dfm.w.rho_u, 0, kWorkArrays * s->nelem * sizeof(df64), s->stream));
     }
 
     std::vector<double> f[6];
@@ -739,7 +693,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
     CUDA_TRY(s, cudaMemcpyAsync(s->d_flag, flags.data(), flags.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(s, cudaMemcpyAsync(s->d_axis, ax.data(), nax * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(s, cudaMemcpyAsync(s->d_axis + nax, ay.data(), nay * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    CUDA_TRY(s, cudaMemsetAsync(s->d_pool + 18 * s->nelem, 0, 16 * s->nelem * sizeof(double), s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(s->work.rho_u, 0, kWorkArrays * s->nelem * sizeof(double), s->stream));
     CUDA_TRY(s, cudaMemsetAsync(w.res, 0, 4 * sizeof(unsigned long long), s->stream));
     for (int l = 0; l < 3; l++)
         for (int k = 0; k < 6; k++)
@@ -1170,7 +1124,7 @@ int enqueue_batch_step(sim_batch_t b, int prev, bool implicit, bool tvd, cudaStr
 {
     const BatchPlan &bp = b->plan;
     if (!implicit) {
-        launch_faces(bp, b->prec, prev, tvd, st);
+        launch_faces(bp, b->prec, prev, tvd, true, st);
         launch_explicit(bp, b->prec, prev, tvd, st);
     }
     int old = prev;
@@ -1178,7 +1132,7 @@ int enqueue_batch_step(sim_batch_t b, int prev, bool implicit, bool tvd, cudaStr
         int nw = (old + 1) % 3;
         if (nw == prev) nw = (nw + 1) % 3;
         launch_zero_res(bp, st);
-        launch_faces(bp, b->prec, old, tvd, st);
+        launch_faces(bp, b->prec, old, tvd, implicit, st);
         launch_assemble(bp, b->prec, prev, old, nw, implicit, tvd, st);
         launch_pressure(bp, b->prec, prev, old, nw, st);
         launch_velocity(bp, b->prec, old, nw, st);

@@ -78,6 +78,11 @@ struct WorkT {
     R *Bgc;                        // B Gamma at the corner (x^f_i, y^f_j), bilinear in the four cells
     R *Bgx, *Bgy;                  // B Gamma dy/dx and B Gamma dx/dy of cell (i,j): normal-stress conductances
     R *uhat, *du, *vhat, *dv;      // pseudo velocities and d (Eqs. pl14, pl20, pl21)
+    // TVD limiters of one level, one evaluation per face (Eqs. pl15_1, pl15_2;
+    // 0 where the face's stencil is not all unknowns): T on the x and y faces;
+    // u on the x face of its control volume (at the centre of cell i-1) and
+    // on the y face below node (i,j) for flow up (U) and down (D); v likewise
+    R *psTx, *psTy, *psUx, *psUyU, *psUyD, *psVy, *psVxU, *psVxD;
     R *uexp, *vexp, *Texp;         // explicit convective terms (Eqs. pl15_11, pl31_1)
 };
 
@@ -157,7 +162,9 @@ enum { BC_WALL = 0, BC_SYMMETRY = 1, BC_INFLOW = 2, BC_OUTFLOW = 3 };
 // of the mixed-precision path; double-float.  Levels are indices into
 // Inst::lv / lv32 / lvdf.
 void launch_zero_res(const BatchPlan &bp, void *stream);
-void launch_faces(const BatchPlan &bp, int prec, int level, bool tvd, void *stream);
+// limiters: also store the TVD limiters of the level (tvd only; the kernels
+// that read them are the implicit-TVD assembly and the explicit terms).
+void launch_faces(const BatchPlan &bp, int prec, int level, bool tvd, bool limiters, void *stream);
 void launch_explicit(const BatchPlan &bp, int prec, int prev, bool tvd, void *stream);
 void launch_assemble(const BatchPlan &bp, int prec, int prev, int old, int nw, bool implicit, bool tvd,
                      void *stream);

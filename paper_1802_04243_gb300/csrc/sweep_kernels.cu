@@ -271,6 +271,53 @@ __device__ __forceinline__ R conductance(R ga, R gb, R da, R db, R c_area)
 
 // ------------------------------------------------------- face densities
 
+// The TVD limiters of position (i,j) (WorkT::psTx ... psVxD), each from the
+// level's own fields and written as 0 where the flag says the four stencil
+// nodes are not all unknowns (so no wall value enters a limiter).
+template <typename R>
+__device__ __forceinline__ void face_limiters(const GeoT<R> &g, const R *__restrict__ u, const R *__restrict__ v,
+                                              const R *__restrict__ T, const WorkT<R> &w, int c, int i, int j)
+{
+    const int P = g.pitch;
+    const uint16_t f = g.flag[c];
+    const R zero = R(0);
+    // T on the x face i and the y face j (Eq. pl15_2)
+    w.psTx[c] = (f & F_TCX) ? psi_surface(T[c - 2], T[c - 1], T[c], T[c + 1], at(g.x.d, i - 2), at(g.x.d, i - 1),
+                                          at(g.x.d, i), at(g.x.d, i + 1), at(g.x.whi, i), at(g.x.wlo, i), u[c])
+                            : zero;
+    w.psTy[c] = (f & F_TCY) ? psi_surface(T[c - 2 * P], T[c - P], T[c], T[c + P], at(g.y.d, j - 2), at(g.y.d, j - 1),
+                                          at(g.y.d, j), at(g.y.d, j + 1), at(g.y.whi, j), at(g.y.wlo, j), v[c])
+                            : zero;
+    // u node (i,j): x face of its control volume at the centre of cell i-1
+    // (Eq. pl15_1, velocity the mean of the two u nodes), and the y face
+    // between u nodes (i,j-1) and (i,j) (Eq. pl15_2, both flow directions)
+    w.psUx[c] = (f & F_TUX) ? psi_centre(u[c - 2], u[c - 1], u[c], u[c + 1], at(g.x.d, i - 2), at(g.x.d, i - 1),
+                                         at(g.x.d, i), R(0.5) * (u[c - 1] + u[c]))
+                            : zero;
+    if (f & F_TUY) {
+        w.psUyU[c] = psi_s_up(u[c - 2 * P], u[c - P], u[c], at(g.y.d, j - 2), at(g.y.d, j - 1), at(g.y.d, j),
+                              at(g.y.whi, j));
+        w.psUyD[c] = psi_s_dn(u[c - P], u[c], u[c + P], at(g.y.d, j - 1), at(g.y.d, j), at(g.y.d, j + 1),
+                              at(g.y.wlo, j));
+    } else {
+        w.psUyU[c] = zero;
+        w.psUyD[c] = zero;
+    }
+    // v node (i,j): the mirror image
+    w.psVy[c] = (f & F_TVY) ? psi_centre(v[c - 2 * P], v[c - P], v[c], v[c + P], at(g.y.d, j - 2), at(g.y.d, j - 1),
+                                         at(g.y.d, j), R(0.5) * (v[c - P] + v[c]))
+                            : zero;
+    if (f & F_TVX) {
+        w.psVxU[c] = psi_s_up(v[c - 2], v[c - 1], v[c], at(g.x.d, i - 2), at(g.x.d, i - 1), at(g.x.d, i),
+                              at(g.x.whi, i));
+        w.psVxD[c] = psi_s_dn(v[c - 1], v[c], v[c + 1], at(g.x.d, i - 1), at(g.x.d, i), at(g.x.d, i + 1),
+                              at(g.x.wlo, i));
+    } else {
+        w.psVxU[c] = zero;
+        w.psVxD[c] = zero;
+    }
+}
+
 // Per-position face quantities of one state level, stored for the kernels
 // that follow: rho^u at u face (i,j) and rho^v at v face (i,j) (Eqs. pl10,
 // pl11, the upwind value plus psi_s times the difference across the face),
@@ -279,10 +326,14 @@ __device__ __forceinline__ R conductance(R ga, R gb, R da, R db, R c_area)
 // corner (x^f_i, y^f_j), and the normal-stress conductances B Gamma dy/dx,
 // B Gamma dx/dy of cell (i,j).  Each is used by two to four neighbours in the
 // assembly, which would otherwise recompute it each time.
+// With `limiters` (TVD only) it also evaluates the Van Leer limiters of the
+// level once per face for the temperature and momentum equations, which
+// would otherwise be evaluated by both control volumes sharing the face.
 template <typename R, bool TVD>
 __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const CoefT<R> &k, const R *__restrict__ u,
                                                     const R *__restrict__ v, const R *__restrict__ rho,
-                                                    const R *__restrict__ gam, const WorkT<R> &w, int i, int j)
+                                                    const R *__restrict__ gam, const R *__restrict__ T,
+                                                    bool limiters, const WorkT<R> &w, int i, int j)
 {
     const int P = g.pitch;
     const int c = Ix{P}(i, j);
@@ -314,14 +365,17 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         w.Bgx[c] = bg * dyj * at(g.x.rd, i);
         w.Bgy[c] = bg * dxi * at(g.y.rd, j);
     }
+    if constexpr (TVD) {
+        if (limiters) face_limiters(g, u, v, T, w, c, i, j);
+    }
 }
 
 // ------------------------------------------------------- explicit terms
 
 // T^explicit of cell (i,j), Eq. pl31_1, all inputs at level n-1.
 template <typename R, bool TVD>
-__device__ R explicit_T(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, const R *Fx, const R *Fy, int c,
-                       int i, int j)
+__device__ R explicit_T(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, const WorkT<R> &w, int c, int i,
+                       int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
@@ -333,21 +387,13 @@ __device__ R explicit_T(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L,
     const R Ts = seen_s(T, fl, c, c - P, F_WALL, k.tau, dyj, L.rho, c, c);
     const R Tn = seen_s(T, fl, c, c + P, F_WALL, k.tau, dyj, L.rho, c, c);
     const R uw = L.u[c], ue = L.u[c + 1], vs = L.v[c], vn = L.v[c + P];
-    const R Fw = Fx[c], Fe = Fx[c + 1], Fs = Fy[c], Fn = Fy[c + P];
+    const R Fw = w.Fx[c], Fe = w.Fx[c + 1], Fs = w.Fy[c], Fn = w.Fy[c + P];
     R pw = 0.0, pe = 0.0, ps = 0.0, pn = 0.0;
-    if (TVD) {
-        if (fl[c + 1] & F_TCX)
-            pe = psi_surface(T[c - 1], Tp, Te, T[c + 2], at(g.x.d, i - 1), dxi, at(g.x.d, i + 1), at(g.x.d, i + 2),
-                             at(g.x.whi, i + 1), at(g.x.wlo, i + 1), ue);
-        if (fl[c] & F_TCX)
-            pw = psi_surface(T[c - 2], Tw, Tp, Te, at(g.x.d, i - 2), at(g.x.d, i - 1), dxi, at(g.x.d, i + 1),
-                             at(g.x.whi, i), at(g.x.wlo, i), uw);
-        if (fl[c + P] & F_TCY)
-            pn = psi_surface(T[c - P], Tp, Tn, T[c + 2 * P], at(g.y.d, j - 1), dyj, at(g.y.d, j + 1), at(g.y.d, j + 2),
-                             at(g.y.whi, j + 1), at(g.y.wlo, j + 1), vn);
-        if (fl[c] & F_TCY)
-            ps = psi_surface(T[c - 2 * P], Ts, Tp, Tn, at(g.y.d, j - 2), at(g.y.d, j - 1), dyj, at(g.y.d, j + 1),
-                             at(g.y.whi, j), at(g.y.wlo, j), vs);
+    if (TVD) {                                     // limiters of level n-1, one per face
+        pe = w.psTx[c + 1];
+        pw = w.psTx[c];
+        pn = w.psTy[c + P];
+        ps = w.psTy[c];
     }
     return -Fe * (upwind(Tp, Te, ue) + (Te - Tp) * pe) + Fw * (upwind(Tw, Tp, uw) + (Tp - Tw) * pw)
            - Fn * (upwind(Tp, Tn, vn) + (Tn - Tp) * pn) + Fs * (upwind(Ts, Tp, vs) + (Tp - Ts) * ps);
@@ -355,7 +401,8 @@ __device__ R explicit_T(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L,
 
 // v^explicit of v face (i,j), Eq. pl15_11, level n-1.
 template <typename R, bool TVD>
-__device__ R explicit_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, const R *Fx, int b, int i, int j)
+__device__ R explicit_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, const WorkT<R> &w, int b, int i,
+                       int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
@@ -366,30 +413,16 @@ __device__ R explicit_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L,
     const R vE = seen_s(v, fl, b, b + 1, F_VWALL, k.zeta, dxi, L.rho, b - P, b);
     const R vS = v[b - P], vN = v[b + P];
     const R uw1 = u[b - P], uw2 = u[b], ue1 = u[b + 1 - P], ue2 = u[b + 1];
-    const R Fw1 = Fx[b - P], Fw2 = Fx[b], Fe1 = Fx[b + 1 - P], Fe2 = Fx[b + 1];
+    const R Fw1 = w.Fx[b - P], Fw2 = w.Fx[b], Fe1 = w.Fx[b + 1 - P], Fe2 = w.Fx[b + 1];
     const R vbs = R(0.5) * (vS + vP), vbn = R(0.5) * (vP + vN);
     R pw1 = 0, pw2 = 0, pe1 = 0, pe2 = 0, ps = 0, pn = 0;
-    if (TVD) {
-        if (fl[b + 1] & F_TVX) {
-            const R f1 = v[b - 1], f4 = v[b + 2];
-            const R d1 = at(g.x.d, i - 1), d3 = at(g.x.d, i + 1), d4 = at(g.x.d, i + 2);
-            const R up = psi_s_up(f1, vP, vE, d1, dxi, d3, at(g.x.whi, i + 1));
-            const R dn = psi_s_dn(vP, vE, f4, dxi, d3, d4, at(g.x.wlo, i + 1));
-            pe1 = positive(ue1) ? up : dn;
-            pe2 = positive(ue2) ? up : dn;
-        }
-        if (fl[b] & F_TVX) {
-            const R f1 = v[b - 2];
-            const R d1 = at(g.x.d, i - 2), d2 = at(g.x.d, i - 1), d4 = at(g.x.d, i + 1);
-            const R up = psi_s_up(f1, vW, vP, d1, d2, dxi, at(g.x.whi, i));
-            const R dn = psi_s_dn(vW, vP, vE, d2, dxi, d4, at(g.x.wlo, i));
-            pw1 = positive(uw1) ? up : dn;
-            pw2 = positive(uw2) ? up : dn;
-        }
-        if (fl[b + P] & F_TVY)
-            pn = psi_centre(vS, vP, vN, v[b + 2 * P], dys, dyp, at(g.y.d, j + 1), vbn);
-        if (fl[b] & F_TVY)
-            ps = psi_centre(v[b - 2 * P], vS, vP, vN, at(g.y.d, j - 2), dys, dyp, vbs);
+    if (TVD) {                                     // limiters of level n-1, one per face
+        pe1 = positive(ue1) ? w.psVxU[b + 1] : w.psVxD[b + 1];
+        pe2 = positive(ue2) ? w.psVxU[b + 1] : w.psVxD[b + 1];
+        pw1 = positive(uw1) ? w.psVxU[b] : w.psVxD[b];
+        pw2 = positive(uw2) ? w.psVxU[b] : w.psVxD[b];
+        pn = w.psVy[b + P];
+        ps = w.psVy[b];
     }
     return R(-0.5) * (Fe1 * (upwind(vP, vE, ue1) + (vE - vP) * pe1) + Fe2 * (upwind(vP, vE, ue2) + (vE - vP) * pe2))
            + R(0.5) * (Fw1 * (upwind(vW, vP, uw1) + (vP - vW) * pw1) + Fw2 * (upwind(vW, vP, uw2) + (vP - vW) * pw2))
@@ -399,7 +432,8 @@ __device__ R explicit_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L,
 
 // u^explicit of u face (i,j): the mirror image of Eq. pl15_11, level n-1.
 template <typename R, bool TVD>
-__device__ R explicit_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, const R *Fy, int a, int i, int j)
+__device__ R explicit_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, const WorkT<R> &w, int a, int i,
+                       int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
@@ -410,30 +444,16 @@ __device__ R explicit_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L,
     const R uN = seen_s(u, fl, a, a + P, F_UWALL, k.zeta, dyj, L.rho, a - 1, a);
     const R uW = u[a - 1], uE = u[a + 1];
     const R vs1 = v[a - 1], vs2 = v[a], vn1 = v[a - 1 + P], vn2 = v[a + P];
-    const R Fs1 = Fy[a - 1], Fs2 = Fy[a], Fn1 = Fy[a - 1 + P], Fn2 = Fy[a + P];
+    const R Fs1 = w.Fy[a - 1], Fs2 = w.Fy[a], Fn1 = w.Fy[a - 1 + P], Fn2 = w.Fy[a + P];
     const R ubw = R(0.5) * (uW + uP), ube = R(0.5) * (uP + uE);
     R pn1 = 0, pn2 = 0, ps1 = 0, ps2 = 0, pe = 0, pw = 0;
-    if (TVD) {
-        if (fl[a + P] & F_TUY) {
-            const R f1 = u[a - P], f4 = u[a + 2 * P];
-            const R d1 = at(g.y.d, j - 1), d3 = at(g.y.d, j + 1), d4 = at(g.y.d, j + 2);
-            const R up = psi_s_up(f1, uP, uN, d1, dyj, d3, at(g.y.whi, j + 1));
-            const R dn = psi_s_dn(uP, uN, f4, dyj, d3, d4, at(g.y.wlo, j + 1));
-            pn1 = positive(vn1) ? up : dn;
-            pn2 = positive(vn2) ? up : dn;
-        }
-        if (fl[a] & F_TUY) {
-            const R f1 = u[a - 2 * P];
-            const R d1 = at(g.y.d, j - 2), d2 = at(g.y.d, j - 1), d4 = at(g.y.d, j + 1);
-            const R up = psi_s_up(f1, uS, uP, d1, d2, dyj, at(g.y.whi, j));
-            const R dn = psi_s_dn(uS, uP, uN, d2, dyj, d4, at(g.y.wlo, j));
-            ps1 = positive(vs1) ? up : dn;
-            ps2 = positive(vs2) ? up : dn;
-        }
-        if (fl[a + 1] & F_TUX)
-            pe = psi_centre(uW, uP, uE, u[a + 2], dxw, dxp, at(g.x.d, i + 1), ube);
-        if (fl[a] & F_TUX)
-            pw = psi_centre(u[a - 2], uW, uP, uE, at(g.x.d, i - 2), dxw, dxp, ubw);
+    if (TVD) {                                     // limiters of level n-1, one per face
+        pn1 = positive(vn1) ? w.psUyU[a + P] : w.psUyD[a + P];
+        pn2 = positive(vn2) ? w.psUyU[a + P] : w.psUyD[a + P];
+        ps1 = positive(vs1) ? w.psUyU[a] : w.psUyD[a];
+        ps2 = positive(vs2) ? w.psUyU[a] : w.psUyD[a];
+        pe = w.psUx[a + 1];
+        pw = w.psUx[a];
     }
     return R(-0.5) * (Fn1 * (upwind(uP, uN, vn1) + (uN - uP) * pn1) + Fn2 * (upwind(uP, uN, vn2) + (uN - uP) * pn2))
            + R(0.5) * (Fs1 * (upwind(uS, uP, vs1) + (uP - uS) * ps1) + Fs2 * (upwind(uS, uP, vs2) + (uP - uS) * ps2))
@@ -449,11 +469,11 @@ __device__ __forceinline__ void explicit_terms_body(const GeoT<R> &g, const Coef
     if (i > g.nx || j > g.ny) return;
     const uint16_t f = g.flag[c];
     if (i < g.nx && j < g.ny)
-        w.Texp[c] = (f & F_FLUID) ? explicit_T<R, TVD>(g, k, prev, w.Fx, w.Fy, c, i, j) : R(0);
+        w.Texp[c] = (f & F_FLUID) ? explicit_T<R, TVD>(g, k, prev, w, c, i, j) : R(0);
     if (j < g.ny)
-        w.uexp[c] = (f & F_UACT) ? explicit_u<R, TVD>(g, k, prev, w.Fy, c, i, j) : R(0);
+        w.uexp[c] = (f & F_UACT) ? explicit_u<R, TVD>(g, k, prev, w, c, i, j) : R(0);
     if (i < g.nx)
-        w.vexp[c] = (f & F_VACT) ? explicit_v<R, TVD>(g, k, prev, w.Fx, c, i, j) : R(0);
+        w.vexp[c] = (f & F_VACT) ? explicit_v<R, TVD>(g, k, prev, w, c, i, j) : R(0);
 }
 
 // ------------------------------------------------------------ temperature
@@ -519,18 +539,11 @@ __device__ R temperature(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     R a1, a2, a3, a4, a0, texp;
     if (IMPL) {
         R pw = 0.0, pe = 0.0, ps = 0.0, pn = 0.0;
-        if (TVD) {
-            if (fl[c] & F_TCX)
-                pw = psi_surface(T[c - 2], Tw, Tp, Te, at(g.x.d, i - 2), dxw, dxi, dxe, at(g.x.whi, i), at(g.x.wlo, i), uw);
-            if (fl[c + 1] & F_TCX)
-                pe = psi_surface(Tw, Tp, Te, T[c + 2], dxw, dxi, dxe, at(g.x.d, i + 2), at(g.x.whi, i + 1),
-                                 at(g.x.wlo, i + 1), ue);
-            if (fl[c] & F_TCY)
-                ps = psi_surface(T[c - 2 * P], Ts, Tp, Tn, at(g.y.d, j - 2), dys, dyj, dyn, at(g.y.whi, j),
-                                 at(g.y.wlo, j), vs);
-            if (fl[c + P] & F_TCY)
-                pn = psi_surface(Ts, Tp, Tn, T[c + 2 * P], dys, dyj, dyn, at(g.y.d, j + 2), at(g.y.whi, j + 1),
-                                 at(g.y.wlo, j + 1), vn);
+        if (TVD) {                                 // limiters of the level, one per face
+            pw = w.psTx[c];
+            pe = w.psTx[c + 1];
+            ps = w.psTy[c];
+            pn = w.psTy[c + P];
         }
         if constexpr (TVD) {
             a1 = pos(Fw) - Fw * pw + Dw;
@@ -591,27 +604,13 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     R a1, a2, a3, a4, a0, uexp;
     if (IMPL) {
         R pw = 0, pe = 0, ps1 = 0, ps2 = 0, pn1 = 0, pn2 = 0;
-        if (TVD) {
-            if (fl[a] & F_TUX)
-                pw = psi_centre(u[a - 2], uW, uP, uE, at(g.x.d, i - 2), dxw, dxp, ubw);
-            if (fl[a + 1] & F_TUX)
-                pe = psi_centre(uW, uP, uE, u[a + 2], dxw, dxp, at(g.x.d, i + 1), ube);
-            if (fl[a] & F_TUY) {
-                const R f1 = u[a - 2 * P];
-                const R d1 = at(g.y.d, j - 2), d2 = at(g.y.d, j - 1), d4 = at(g.y.d, j + 1);
-                const R up = psi_s_up(f1, uS, uP, d1, d2, dyj, at(g.y.whi, j));
-                const R dn = psi_s_dn(uS, uP, uN, d2, dyj, d4, at(g.y.wlo, j));
-                ps1 = positive(vs1) ? up : dn;
-                ps2 = positive(vs2) ? up : dn;
-            }
-            if (fl[a + P] & F_TUY) {
-                const R f4 = u[a + 2 * P];
-                const R d1 = at(g.y.d, j - 1), d3 = at(g.y.d, j + 1), d4 = at(g.y.d, j + 2);
-                const R up = psi_s_up(uS, uP, uN, d1, dyj, d3, at(g.y.whi, j + 1));
-                const R dn = psi_s_dn(uP, uN, f4, dyj, d3, d4, at(g.y.wlo, j + 1));
-                pn1 = positive(vn1) ? up : dn;
-                pn2 = positive(vn2) ? up : dn;
-            }
+        if (TVD) {                                 // limiters of the level, one per face
+            pw = w.psUx[a];
+            pe = w.psUx[a + 1];
+            ps1 = positive(vs1) ? w.psUyU[a] : w.psUyD[a];
+            ps2 = positive(vs2) ? w.psUyU[a] : w.psUyD[a];
+            pn1 = positive(vn1) ? w.psUyU[a + P] : w.psUyD[a + P];
+            pn2 = positive(vn2) ? w.psUyU[a + P] : w.psUyD[a + P];
         }
         if constexpr (TVD) {
             a1 = pos(Fbw) - Fbw * pw + R(4.0 / 3.0) * Dxw;
@@ -670,27 +669,13 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     R a1, a2, a3, a4, a0, vexp;
     if (IMPL) {
         R pw1 = 0, pw2 = 0, pe1 = 0, pe2 = 0, ps = 0, pn = 0;
-        if (TVD) {
-            if (fl[b] & F_TVX) {
-                const R f1 = v[b - 2];
-                const R d1 = at(g.x.d, i - 2), d2 = at(g.x.d, i - 1), d4 = at(g.x.d, i + 1);
-                const R up = psi_s_up(f1, vW, vP, d1, d2, dxi, at(g.x.whi, i));
-                const R dn = psi_s_dn(vW, vP, vE, d2, dxi, d4, at(g.x.wlo, i));
-                pw1 = positive(uw1) ? up : dn;
-                pw2 = positive(uw2) ? up : dn;
-            }
-            if (fl[b + 1] & F_TVX) {
-                const R f4 = v[b + 2];
-                const R d1 = at(g.x.d, i - 1), d3 = at(g.x.d, i + 1), d4 = at(g.x.d, i + 2);
-                const R up = psi_s_up(vW, vP, vE, d1, dxi, d3, at(g.x.whi, i + 1));
-                const R dn = psi_s_dn(vP, vE, f4, dxi, d3, d4, at(g.x.wlo, i + 1));
-                pe1 = positive(ue1) ? up : dn;
-                pe2 = positive(ue2) ? up : dn;
-            }
-            if (fl[b] & F_TVY)
-                ps = psi_centre(v[b - 2 * P], vS, vP, vN, at(g.y.d, j - 2), dys, dyp, vbs);
-            if (fl[b + P] & F_TVY)
-                pn = psi_centre(vS, vP, vN, v[b + 2 * P], dys, dyp, at(g.y.d, j + 1), vbn);
+        if (TVD) {                                 // limiters of the level, one per face
+            pw1 = positive(uw1) ? w.psVxU[b] : w.psVxD[b];
+            pw2 = positive(uw2) ? w.psVxU[b] : w.psVxD[b];
+            pe1 = positive(ue1) ? w.psVxU[b + 1] : w.psVxD[b + 1];
+            pe2 = positive(ue2) ? w.psVxU[b + 1] : w.psVxD[b + 1];
+            ps = w.psVy[b];
+            pn = w.psVy[b + P];
         }
         if constexpr (TVD) {
             a1 = R(0.5) * (pos(Fw2) - Fw2 * pw2 + pos(Fw1) - Fw1 * pw1) + Dxw;
@@ -1098,18 +1083,18 @@ __global__ void k_zero_res(BatchPlan bp)
 }
 
 template <int PREC, bool TVD>
-__global__ void __launch_bounds__(256) k_faces(const __grid_constant__ BatchPlan bp, int level)
+__global__ void __launch_bounds__(256) k_faces(const __grid_constant__ BatchPlan bp, int level, int limiters)
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
         if constexpr (PREC == PREC_MIXED) {
             const LevelT<float> &L = I.lv32[level];
-            face_densities_body<float, TVD>(I.g32, I.k32, L.u, L.v, L.rho, L.gam, I.w32, i, j);
+            face_densities_body<float, TVD>(I.g32, I.k32, L.u, L.v, L.rho, L.gam, L.T, limiters, I.w32, i, j);
         } else if constexpr (PREC == PREC_DF64) {
             const LevelT<df64> &L = I.lvdf[level];
-            face_densities_body<df64, TVD>(I.gdf, I.kdf, L.u, L.v, L.rho, L.gam, I.wdf, i, j);
+            face_densities_body<df64, TVD>(I.gdf, I.kdf, L.u, L.v, L.rho, L.gam, L.T, limiters, I.wdf, i, j);
         } else {
             const Level &L = I.lv[level];
-            face_densities_body<double, TVD>(I.g, I.k, L.u, L.v, L.rho, L.gam, I.w, i, j);
+            face_densities_body<double, TVD>(I.g, I.k, L.u, L.v, L.rho, L.gam, L.T, limiters, I.w, i, j);
         }
     });
 }
@@ -1378,17 +1363,18 @@ void launch_zero_res(const BatchPlan &bp, void *stream)
     k_zero_res<<<(bp.n_inst * 4 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(bp);
 }
 
-void launch_faces(const BatchPlan &bp, int prec, int level, bool tvd, void *stream)
+void launch_faces(const BatchPlan &bp, int prec, int level, bool tvd, bool limiters, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
     const dim3 bl(bp.tx, bp.ty);
+    const int lim = tvd && limiters;
     switch (prec * 2 + (tvd ? 1 : 0)) {
-    case 5: k_faces<PREC_DF64, true><<<bp.grid, bl, 0, s>>>(bp, level); break;
-    case 4: k_faces<PREC_DF64, false><<<bp.grid, bl, 0, s>>>(bp, level); break;
-    case 3: k_faces<PREC_MIXED, true><<<bp.grid, bl, 0, s>>>(bp, level); break;
-    case 2: k_faces<PREC_MIXED, false><<<bp.grid, bl, 0, s>>>(bp, level); break;
-    case 1: k_faces<PREC_FP64, true><<<bp.grid, bl, 0, s>>>(bp, level); break;
-    default: k_faces<PREC_FP64, false><<<bp.grid, bl, 0, s>>>(bp, level); break;
+    case 5: k_faces<PREC_DF64, true><<<bp.grid, bl, 0, s>>>(bp, level, lim); break;
+    case 4: k_faces<PREC_DF64, false><<<bp.grid, bl, 0, s>>>(bp, level, 0); break;
+    case 3: k_faces<PREC_MIXED, true><<<bp.grid, bl, 0, s>>>(bp, level, lim); break;
+    case 2: k_faces<PREC_MIXED, false><<<bp.grid, bl, 0, s>>>(bp, level, 0); break;
+    case 1: k_faces<PREC_FP64, true><<<bp.grid, bl, 0, s>>>(bp, level, lim); break;
+    default: k_faces<PREC_FP64, false><<<bp.grid, bl, 0, s>>>(bp, level, 0); break;
     }
 }
 
