@@ -80,6 +80,9 @@ WORKLOADS = {
     "c3-explicit": lambda W: W.c3_large(implicit=False),
     "c4": lambda W: W.c4_paper_scale(),
     "profile": lambda W: W.profile_channel(),
+    "c2-implicit-tvd": lambda W: W.c2_medium().replace(tvd=True, name="c2_1024x256_implicit_tvd"),
+    "c2-explicit-upwind": lambda W: W.c2_medium().replace(implicit=False, name="c2_1024x256_explicit_upwind"),
+    "c2-explicit-tvd": lambda W: W.c2_medium().replace(implicit=False, tvd=True, name="c2_1024x256_explicit_tvd"),
     "paper": lambda W: W.paper_channel(ny=400),
     "paper-4000": lambda W: W.paper_channel(ny=4000),
 }
