@@ -294,27 +294,29 @@ __device__ __forceinline__ void face_limiters(const GeoT<R> &g, const R *__restr
     w.psUx[c] = (f & F_TUX) ? psi_centre(u[c - 2], u[c - 1], u[c], u[c + 1], at(g.x.d, i - 2), at(g.x.d, i - 1),
                                          at(g.x.d, i), R(0.5) * (u[c - 1] + u[c]))
                             : zero;
-    if (f & F_TUY) {
-        w.psUyU[c] = psi_s_up(u[c - 2 * P], u[c - P], u[c], at(g.y.d, j - 2), at(g.y.d, j - 1), at(g.y.d, j),
-                              at(g.y.whi, j));
-        w.psUyD[c] = psi_s_dn(u[c - P], u[c], u[c + P], at(g.y.d, j - 1), at(g.y.d, j), at(g.y.d, j + 1),
-                              at(g.y.wlo, j));
-    } else {
-        w.psUyU[c] = zero;
-        w.psUyD[c] = zero;
+    // (a branch is evaluated only if one of the two v faces that select it,
+    // v(i-1,j) and v(i,j), points its way)
+    {
+        const bool t = (f & F_TUY) != 0, p0 = positive(v[c - 1]), p1 = positive(v[c]);
+        w.psUyU[c] = (t && (p0 || p1)) ? psi_s_up(u[c - 2 * P], u[c - P], u[c], at(g.y.d, j - 2), at(g.y.d, j - 1),
+                                                  at(g.y.d, j), at(g.y.whi, j))
+                                       : zero;
+        w.psUyD[c] = (t && !(p0 && p1)) ? psi_s_dn(u[c - P], u[c], u[c + P], at(g.y.d, j - 1), at(g.y.d, j),
+                                                   at(g.y.d, j + 1), at(g.y.wlo, j))
+                                        : zero;
     }
     // v node (i,j): the mirror image
     w.psVy[c] = (f & F_TVY) ? psi_centre(v[c - 2 * P], v[c - P], v[c], v[c + P], at(g.y.d, j - 2), at(g.y.d, j - 1),
                                          at(g.y.d, j), R(0.5) * (v[c - P] + v[c]))
                             : zero;
-    if (f & F_TVX) {
-        w.psVxU[c] = psi_s_up(v[c - 2], v[c - 1], v[c], at(g.x.d, i - 2), at(g.x.d, i - 1), at(g.x.d, i),
-                              at(g.x.whi, i));
-        w.psVxD[c] = psi_s_dn(v[c - 1], v[c], v[c + 1], at(g.x.d, i - 1), at(g.x.d, i), at(g.x.d, i + 1),
-                              at(g.x.wlo, i));
-    } else {
-        w.psVxU[c] = zero;
-        w.psVxD[c] = zero;
+    {
+        const bool t = (f & F_TVX) != 0, p0 = positive(u[c - P]), p1 = positive(u[c]);
+        w.psVxU[c] = (t && (p0 || p1)) ? psi_s_up(v[c - 2], v[c - 1], v[c], at(g.x.d, i - 2), at(g.x.d, i - 1),
+                                                  at(g.x.d, i), at(g.x.whi, i))
+                                       : zero;
+        w.psVxD[c] = (t && !(p0 && p1)) ? psi_s_dn(v[c - 1], v[c], v[c + 1], at(g.x.d, i - 1), at(g.x.d, i),
+                                                   at(g.x.d, i + 1), at(g.x.wlo, i))
+                                        : zero;
     }
 }
 
