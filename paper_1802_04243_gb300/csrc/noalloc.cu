@@ -78,8 +78,9 @@ __device__ __forceinline__ bool nwall(const Setup &s, int i, int j)
 }
 
 // Grid factor tables of one axis (the layout of stg::Axis): cell size,
-// inverse, the two interpolation weights of face i and the inverse centre
-// distance across face i; ghost sizes mirror the boundary cells.
+// inverse, the two interpolation weights of face i, the inverse centre
+// distance across face i and the three derivative weights of cell i; ghost
+// sizes mirror the boundary cells.
 __global__ void k_na_axis(int n, const double *dl, double len, double *out)
 {
     const int m = n + 2 * G + 1;
@@ -92,11 +93,21 @@ __global__ void k_na_axis(int n, const double *dl, double len, double *out)
         return dl ? dl[s] : len / n;
     };
     const double di = size_at(q), dm = q > 0 ? size_at(q - 1) : di;
+    const double rd = 1.0 / di, wlo = di / (dm + di), whi = dm / (dm + di);
     out[q] = di;
-    out[m + q] = 1.0 / di;
-    out[2 * m + q] = di / (dm + di);
-    out[3 * m + q] = dm / (dm + di);
+    out[m + q] = rd;
+    out[2 * m + q] = wlo;
+    out[3 * m + q] = whi;
     out[4 * m + q] = 1.0 / (0.5 * (dm + di));
+    out[8 * m + q] = 0.5 * (dm + di);
+    // derivative weights: the interpolation weights of face q+1 (of face q
+    // itself for the last entry, which no cell uses)
+    const double dn = q + 1 < m ? size_at(q + 1) : di, dc = q + 1 < m ? di : dm;
+    const double wlo_n = dn / (dc + dn), whi_n = dc / (dc + dn);
+    const double h = 0.5 * rd;
+    out[5 * m + q] = h * wlo;
+    out[6 * m + q] = h * (wlo_n - whi);
+    out[7 * m + q] = h * whi_n;
 }
 
 // Cell kinds of the extended grid: S/N ghost rows own the corners.
@@ -346,12 +357,12 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     const size_t nelem = (size_t)pitch * (ny + 2 * G + 1);
     const int mx = nx + 2 * G + 1, my = ny + 2 * G + 1;
     Carver cv{(unsigned char *)base};
-    double *pool = cv.take<double>(42 * nelem);
+    double *pool = cv.take<double>(kPoolArrays * nelem);
     uint16_t *flag = cv.take<uint16_t>(nelem);
     uint8_t *kind = cv.take<uint8_t>(nelem);
     uint8_t *side = cv.take<uint8_t>(nelem);
-    double *axx = cv.take<double>(5 * (size_t)mx);
-    double *axy = cv.take<double>(5 * (size_t)my);
+    double *axx = cv.take<double>(kAxisTables * (size_t)mx);
+    double *axy = cv.take<double>(kAxisTables * (size_t)my);
     double *cdx = grid->dx ? cv.take<double>(nx) : nullptr;
     double *cdy = grid->dy ? cv.take<double>(ny) : nullptr;
     double *cin = cv.take<double>(3 * (size_t)ny);
@@ -371,7 +382,7 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     if (bc->inflow_p) NA_TRY(cudaMemcpyAsync(cin + 2 * ny, bc->inflow_p, ny * sizeof(double), cudaMemcpyHostToDevice, s));
     if (bc->n_rect) NA_TRY(cudaMemcpyAsync(crect, bc->rect, 4 * bc->n_rect * sizeof(int), cudaMemcpyHostToDevice, s));
     // the scratch keeps the previous call's contents: clear the work arrays
-    NA_TRY(cudaMemsetAsync(pool + 18 * nelem, 0, 24 * nelem * sizeof(double), s));
+    NA_TRY(cudaMemsetAsync(pool + 18 * nelem, 0, kWorkArrays * nelem * sizeof(double), s));
 
     Setup su{};
     su.nx = nx; su.ny = ny; su.pitch = pitch;
@@ -398,9 +409,10 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
         lv[l].T = q; q += nelem; lv[l].rho = q; q += nelem; lv[l].gam = q; q += nelem;
     }
     Work w{};
-    w.rho_u = q; q += nelem; w.rho_v = q; q += nelem;
+    w.ru_dy = q; q += nelem; w.rv_dx = q; q += nelem;
     w.Fx = q; q += nelem; w.Fy = q; q += nelem; w.DTx = q; q += nelem; w.DTy = q; q += nelem;
     w.Bgc = q; q += nelem; w.Bgx = q; q += nelem; w.Bgy = q; q += nelem;
+    w.Fbu = q; q += nelem; w.Fbv = q; q += nelem;
     w.uhat = q; q += nelem; w.du = q; q += nelem;
     w.vhat = q; q += nelem; w.dv = q; q += nelem; w.uexp = q; q += nelem; w.vexp = q; q += nelem;
     w.Texp = q;
@@ -411,8 +423,8 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
 
     Geo g{};
     g.nx = nx; g.ny = ny; g.pitch = pitch; g.flag = flag;
-    g.x = Axis{axx, axx + mx, axx + 2 * mx, axx + 3 * mx, axx + 4 * mx};
-    g.y = Axis{axy, axy + my, axy + 2 * my, axy + 3 * my, axy + 4 * my};
+    g.x = axis_view<double>(axx, mx);
+    g.y = axis_view<double>(axy, my);
     Sides sides{};
     for (int t = 0; t < 4; t++) sides.kind[t] = bc->side_kind[t];
 
@@ -458,7 +470,8 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
             int nw = (old + 1) % 3;
             if (nw == prev) nw = (nw + 1) % 3;
             NA_TRY(cudaMemsetAsync(res, 0, 4 * sizeof(unsigned long long), s));
-            launch_faces(plan, PREC_FP64, old, tvd, implicit, s);
+            if (implicit || it > 0)     // an explicit step's first iteration reuses the faces of n-1
+                launch_faces(plan, PREC_FP64, old, tvd, implicit, s);
             launch_assemble(plan, PREC_FP64, prev, old, nw, implicit, tvd, s);
             launch_pressure(plan, PREC_FP64, prev, old, nw, s);
             launch_velocity(plan, PREC_FP64, old, nw, s);

@@ -322,11 +322,11 @@ std::vector<uint16_t> make_flags(const HostGrid &h)
     return f;
 }
 
-// Axis factor table: 5 arrays of n + 2G + 1 entries over [-2, n+2].
+// Axis factor table: kAxisTables arrays of n + 2G + 1 entries over [-2, n+2].
 std::vector<double> make_axis(const std::vector<double> &dl)
 {
     const int n = (int)dl.size(), m = n + 2 * G + 1;
-    std::vector<double> d(m), out(5 * (size_t)m, 0.0);
+    std::vector<double> d(m), out(kAxisTables * (size_t)m, 0.0);
     for (int i = -G; i <= n + G; i++) {
         int s = i;
         if (s < 0) s = -s - 1;                  // mirror about the west / south side
@@ -340,6 +340,14 @@ std::vector<double> make_axis(const std::vector<double> &dl)
         out[2 * m + q] = di / (dm + di);
         out[3 * m + q] = dm / (dm + di);
         out[4 * m + q] = 1.0 / (0.5 * (dm + di));
+        out[8 * m + q] = 0.5 * (dm + di);
+    }
+    for (int q = 0; q < m; q++) {
+        const int qn = q + 1 < m ? q + 1 : q;
+        const double h = 0.5 * out[m + q];
+        out[5 * m + q] = h * out[2 * m + q];
+        out[6 * m + q] = h * (out[2 * m + qn] - out[3 * m + q]);
+        out[7 * m + q] = h * out[3 * m + qn];
     }
     return out;
 }
@@ -445,10 +453,9 @@ Inst inst_of(const sim_s *s, int tx, int tile0)
 
 int prec_of(const sim_s *s) { return s->mixed ? PREC_MIXED : s->df ? PREC_DF64 : PREC_FP64; }
 
-// Arrays of one pool: three levels of six fields, then the iteration
-// scratch (WorkT), which starts at rho_u and is cleared at creation.
-constexpr int kWorkArrays = 24;
-constexpr int kPoolArrays = 3 * 6 + kWorkArrays;
+// A pool holds three levels of six fields, then the iteration scratch
+// (WorkT, kWorkArrays arrays), which starts at ru_dy and is cleared at
+// creation.
 
 // Carve three state levels and the iteration scratch out of one pool.
 template <typename R>
@@ -458,8 +465,8 @@ R *carve_levels(R *q, size_t nelem, LevelT<R> lv[3], WorkT<R> &w)
         R **f[6] = {&lv[l].u, &lv[l].v, &lv[l].p, &lv[l].T, &lv[l].rho, &lv[l].gam};
         for (R **x : f) { *x = q; q += nelem; }
     }
-    R **a[kWorkArrays] = {&w.rho_u, &w.rho_v, &w.Fx, &w.Fy, &w.DTx, &w.DTy, &w.Bgc, &w.Bgx, &w.Bgy,
-                          &w.uhat, &w.du, &w.vhat, &w.dv, &w.uexp, &w.vexp, &w.Texp,
+    R **a[kWorkArrays] = {&w.ru_dy, &w.rv_dx, &w.Fx, &w.Fy, &w.DTx, &w.DTy, &w.Bgc, &w.Bgx, &w.Bgy,
+                          &w.Fbu, &w.Fbv, &w.uhat, &w.du, &w.vhat, &w.dv, &w.uexp, &w.vexp, &w.Texp,
                           &w.psTx, &w.psTy, &w.psUx, &w.psUyU, &w.psUyD, &w.psVy, &w.psVxU, &w.psVxD};
     for (R **x : a) { *x = q; q += nelem; }
     return q;
@@ -532,15 +539,19 @@ void enqueue_explicit(sim_t s, int prev, bool tvd, cudaStream_t st, long long *c
 }
 
 // One loop-2 iteration from level `old` (level `prev` holds n-1) into the
-// third level, which is returned.
-int enqueue_iteration(sim_t s, int prev, int old, bool implicit, bool tvd, cudaStream_t st, long long *counts)
+// third level, which is returned.  faces_ready: the face quantities of `old`
+// are already in the scratch (the first iteration of an explicit step, whose
+// explicit terms were computed from the same level), so the face kernel is
+// not launched again.
+int enqueue_iteration(sim_t s, int prev, int old, bool implicit, bool tvd, bool faces_ready, cudaStream_t st,
+                      long long *counts)
 {
     int nw = (old + 1) % 3;
     if (nw == prev) nw = (nw + 1) % 3;
     const int ng = ghost_kernels(s->sides, true);
     cudaMemsetAsync(s->work.res, 0, 4 * sizeof(unsigned long long), st);
     const int prec = prec_of(s);
-    { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, prec, old, tvd, implicit, st); }
+    if (!faces_ready) { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, prec, old, tvd, implicit, st); }
     { Launch l(s, SIM_K_ASSEMBLE, st, counts); launch_assemble(s->plan, prec, prev, old, nw, implicit, tvd, st); }
     { Launch l(s, SIM_K_PRESSURE, st, counts); launch_pressure(s->plan, prec, prev, old, nw, st); }
     { Launch l(s, SIM_K_VELOCITY, st, counts); launch_velocity(s->plan, prec, old, nw, st); }
@@ -563,7 +574,7 @@ int enqueue_step(sim_t s, int prev, bool implicit, bool tvd, cudaStream_t st, lo
     if (!implicit) enqueue_explicit(s, prev, tvd, st, counts);
     int old = prev;
     for (int it = 1; it <= s->pb.iters; it++)
-        old = enqueue_iteration(s, prev, old, implicit, tvd, st, counts);
+        old = enqueue_iteration(s, prev, old, implicit, tvd, !implicit && it == 1, st, counts);
     return old;
 }
 
@@ -629,8 +640,8 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
     s->geo.flag = s->d_flag;
     const int mx = pb.nx + 2 * G + 1, my = pb.ny + 2 * G + 1;
     const double *dax = s->d_axis, *day = s->d_axis + nax;
-    s->geo.x = Axis{dax, dax + mx, dax + 2 * mx, dax + 3 * mx, dax + 4 * mx};
-    s->geo.y = Axis{day, day + my, day + 2 * my, day + 3 * my, day + 4 * my};
+    s->geo.x = axis_view(dax, mx);
+    s->geo.y = axis_view(day, my);
     for (int k = 0; k < 4; k++) s->sides.kind[k] = pb.side_kind[k];
 
     s->mixed = pb.precision == SIM_MIXED;
@@ -646,8 +657,8 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         s->mx.g.ny = pb.ny;
         s->mx.g.pitch = s->pitch;
         s->mx.g.flag = s->d_flag;
-        s->mx.g.x = AxisT<float>{fx, fx + mx, fx + 2 * mx, fx + 3 * mx, fx + 4 * mx};
-        s->mx.g.y = AxisT<float>{fy, fy + my, fy + 2 * my, fy + 3 * my, fy + 4 * my};
+        s->mx.g.x = axis_view(fx, mx);
+        s->mx.g.y = axis_view(fy, my);
         const Coef &k = pb.k;
         s->mx.k = CoefT<float>{(float)k.A, (float)k.B, (float)k.CT1f, (float)k.CT2f, (float)k.CT3f,
                                (float)k.omega, (float)k.dt, (float)k.gx, (float)k.gy, (float)k.hrdt,
@@ -656,7 +667,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         for (size_t q = 0; q < nax; q++) a32[q] = (float)ax[q];
         for (size_t q = 0; q < nay; q++) a32[nax + q] = (float)ay[q];
         CUDA_TRY(s, cudaMemcpy(s->d_axis32, a32.data(), a32.size() * sizeof(float), cudaMemcpyHostToDevice));
-        CUDA_TRY(s, cudaMemsetAsync(s->mx.w.rho_u, 0, kWorkArrays * s->nelem * sizeof(float), s->stream));
+        CUDA_TRY(s, cudaMemsetAsync(s->mx.w.ru_dy, 0, kWorkArrays * s->nelem * sizeof(float), s->stream));
     }
 
     s->df = pb.precision == SIM_DF64;
@@ -672,8 +683,8 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         s->dfm.g.ny = pb.ny;
         s->dfm.g.pitch = s->pitch;
         s->dfm.g.flag = s->d_flag;
-        s->dfm.g.x = AxisT<df64>{fx, fx + mx, fx + 2 * mx, fx + 3 * mx, fx + 4 * mx};
-        s->dfm.g.y = AxisT<df64>{fy, fy + my, fy + 2 * my, fy + 3 * my, fy + 4 * my};
+        s->dfm.g.x = axis_view(fx, mx);
+        s->dfm.g.y = axis_view(fy, my);
         const Coef &k = pb.k;
         s->dfm.k = CoefT<df64>{dfl::split_host(k.A), dfl::split_host(k.B), dfl::split_host(k.CT1f), dfl::split_host(k.CT2f),
                                dfl::split_host(k.CT3f), dfl::split_host(k.omega), dfl::split_host(k.dt), dfl::split_host(k.gx),
@@ -683,7 +694,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         for (size_t q = 0; q < nax; q++) adf[q] = dfl::split_host(ax[q]);
         for (size_t q = 0; q < nay; q++) adf[nax + q] = dfl::split_host(ay[q]);
         CUDA_TRY(s, cudaMemcpy(s->d_axisdf, adf.data(), adf.size() * sizeof(df64), cudaMemcpyHostToDevice));
-        CUDA_TRY(s, cudaMemsetAsync(s->dfm.w.rho_u, 0, kWorkArrays * s->nelem * sizeof(df64), s->stream));
+        CUDA_TRY(s, cudaMemsetAsync(s->dfm.w.ru_dy, 0, kWorkArrays * s->nelem * sizeof(df64), s->stream));
     }
 
     std::vector<double> f[6];
@@ -693,7 +704,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
     CUDA_TRY(s, cudaMemcpyAsync(s->d_flag, flags.data(), flags.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(s, cudaMemcpyAsync(s->d_axis, ax.data(), nax * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(s, cudaMemcpyAsync(s->d_axis + nax, ay.data(), nay * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    CUDA_TRY(s, cudaMemsetAsync(s->work.rho_u, 0, kWorkArrays * s->nelem * sizeof(double), s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(s->work.ru_dy, 0, kWorkArrays * s->nelem * sizeof(double), s->stream));
     CUDA_TRY(s, cudaMemsetAsync(w.res, 0, 4 * sizeof(unsigned long long), s->stream));
     for (int l = 0; l < 3; l++)
         for (int k = 0; k < 6; k++)
@@ -772,7 +783,7 @@ extern "C" sim_status sim_step(sim_t s, int n_steps, int scheme)
         int old = prev, it = 0;
         if (!implicit) enqueue_explicit(s, prev, tvd, s->stream, nullptr);
         for (it = 1; it <= pb.iters; it++) {
-            old = enqueue_iteration(s, prev, old, implicit, tvd, s->stream, nullptr);
+            old = enqueue_iteration(s, prev, old, implicit, tvd, !implicit && it == 1, s->stream, nullptr);
             CUDA_TRY(s, cudaMemcpyAsync(s->h_res, s->work.res, 4 * sizeof(unsigned long long),
                                         cudaMemcpyDeviceToHost, s->stream));
             CUDA_TRY(s, cudaStreamSynchronize(s->stream));
@@ -1132,7 +1143,8 @@ int enqueue_batch_step(sim_batch_t b, int prev, bool implicit, bool tvd, cudaStr
         int nw = (old + 1) % 3;
         if (nw == prev) nw = (nw + 1) % 3;
         launch_zero_res(bp, st);
-        launch_faces(bp, b->prec, old, tvd, implicit, st);
+        if (implicit || it > 1)         // an explicit step's first iteration reuses the faces of n-1
+            launch_faces(bp, b->prec, old, tvd, implicit, st);
         launch_assemble(bp, b->prec, prev, old, nw, implicit, tvd, st);
         launch_pressure(bp, b->prec, prev, old, nw, st);
         launch_velocity(bp, b->prec, old, nw, st);

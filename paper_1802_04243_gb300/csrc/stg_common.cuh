@@ -46,7 +46,25 @@ struct AxisT {
     const R *wlo;    // d_i / (d_{i-1} + d_i): weight of index i-1 at face i
     const R *whi;    // d_{i-1} / (d_{i-1} + d_i): weight of index i at face i
     const R *rc;     // 1 / (0.5 (d_{i-1} + d_i)): inverse centre distance across face i
+    // Weights of the derivative across cell i of a quantity interpolated to
+    // faces i and i+1 and averaged over two rows: with a pair sum S(k) of the
+    // two rows' values at index k, (f_{i+1} - f_i) / d_i equals
+    // qlo * -S(i-1) + qmid * S(i) + qhi * S(i+1).
+    const R *qlo;    // wlo_i / (2 d_i)
+    const R *qmid;   // (wlo_{i+1} - whi_i) / (2 d_i)
+    const R *qhi;    // whi_{i+1} / (2 d_i)
+    const R *dc;     // 0.5 (d_{i-1} + d_i): centre distance across face i
 };
+
+// Number of per-index arrays of an axis table, stored one after another.
+constexpr int kAxisTables = 9;
+
+// The arrays of an axis table of m entries per array starting at t.
+template <typename R>
+inline AxisT<R> axis_view(const R *t, int m)
+{
+    return AxisT<R>{t, t + m, t + 2 * m, t + 3 * m, t + 4 * m, t + 5 * m, t + 6 * m, t + 7 * m, t + 8 * m};
+}
 
 template <typename R>
 struct GeoT {
@@ -69,14 +87,17 @@ struct LevelT {
     R *u, *v, *p, *T, *rho, *gam;
 };
 
-// Scratch of one loop-2 iteration (all extended-indexed).
+// Scratch of one loop-2 iteration (all extended-indexed).  The arrays are
+// carved one after another in this order; kWorkArrays counts them.
 template <typename R>
 struct WorkT {
-    R *rho_u, *rho_v;              // face densities (Eqs. pl10, pl11)
+    R *ru_dy, *rv_dx;              // face densities (Eqs. pl10, pl11) times the face area: rho^u dy, rho^v dx
     R *Fx, *Fy;                    // mass fluxes F^x = rho^u u dy, F^y = rho^v v dx (Eqs. pl8, pl9)
     R *DTx, *DTy;                  // T conductances of x and y faces, C^T1_f Gamma_harm dy / dx_c (Eqs. pl32, pl33)
     R *Bgc;                        // B Gamma at the corner (x^f_i, y^f_j), bilinear in the four cells
     R *Bgx, *Bgy;                  // B Gamma dy/dx and B Gamma dx/dy of cell (i,j): normal-stress conductances
+    R *Fbu, *Fbv;                  // mass fluxes through the centre of cell (i,j) between the u (v) control
+                                   // volumes: rho 0.5 (u_i + u_{i+1}) dy and rho 0.5 (v_j + v_{j+1}) dx
     R *uhat, *du, *vhat, *dv;      // pseudo velocities and d (Eqs. pl14, pl20, pl21)
     // TVD limiters of one level, one evaluation per face (Eqs. pl15_1, pl15_2;
     // 0 where the face's stencil is not all unknowns): T on the x and y faces;
@@ -85,6 +106,10 @@ struct WorkT {
     R *psTx, *psTy, *psUx, *psUyU, *psUyD, *psVy, *psVxU, *psVxD;
     R *uexp, *vexp, *Texp;         // explicit convective terms (Eqs. pl15_11, pl31_1)
 };
+
+constexpr int kWorkArrays = 26;
+// Arrays of one pool: three levels of six fields, then the scratch.
+constexpr int kPoolArrays = 3 * 6 + kWorkArrays;
 
 using Axis = AxisT<double>;
 using Geo = GeoT<double>;

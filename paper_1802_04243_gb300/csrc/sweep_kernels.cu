@@ -321,9 +321,10 @@ __device__ __forceinline__ void face_limiters(const GeoT<R> &g, const R *__restr
 }
 
 // Per-position face quantities of one state level, stored for the kernels
-// that follow: rho^u at u face (i,j) and rho^v at v face (i,j) (Eqs. pl10,
-// pl11, the upwind value plus psi_s times the difference across the face),
-// the mass fluxes through them (Eqs. pl8, pl9), the T conductances of the x
+// that follow: rho^u dy at u face (i,j) and rho^v dx at v face (i,j) (the
+// face densities of Eqs. pl10, pl11 -- the upwind value plus psi_s times the
+// difference across the face -- times the face area), the mass fluxes
+// through them (Eqs. pl8, pl9), the T conductances of the x
 // and y faces (Eq. pl32 with the harmonic mean Eq. pl33), B Gamma at the
 // corner (x^f_i, y^f_j), and the normal-stress conductances B Gamma dy/dx,
 // B Gamma dx/dy of cell (i,j).  Each is used by two to four neighbours in the
@@ -347,8 +348,9 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         if (TVD && (g.flag[c] & F_TCX))
             val += psi_surface(rho[c - 2], rl, rr, rho[c + 1], at(g.x.d, i - 2), at(g.x.d, i - 1),
                                dxi, at(g.x.d, i + 1), at(g.x.whi, i), at(g.x.wlo, i), vel) * (rr - rl);
-        w.rho_u[c] = val;
-        w.Fx[c] = val * vel * dyj;
+        const R rdy = val * dyj;
+        w.ru_dy[c] = rdy;
+        w.Fx[c] = rdy * vel;
         w.DTx[c] = conductance(gam[c - 1], gam[c], at(g.x.d, i - 1), dxi, k.CT1f * dyj);
     }
     if (i < g.nx) {
@@ -357,8 +359,9 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         if (TVD && (g.flag[c] & F_TCY))
             val += psi_surface(rho[c - 2 * P], rb, rt, rho[c + P], at(g.y.d, j - 2), at(g.y.d, j - 1),
                                dyj, at(g.y.d, j + 1), at(g.y.whi, j), at(g.y.wlo, j), vel) * (rt - rb);
-        w.rho_v[c] = val;
-        w.Fy[c] = val * vel * dxi;
+        const R rdx = val * dxi;
+        w.rv_dx[c] = rdx;
+        w.Fy[c] = rdx * vel;
         w.DTy[c] = conductance(gam[c - P], gam[c], at(g.y.d, j - 1), dyj, k.CT1f * dxi);
     }
     w.Bgc[c] = k.B * gamma_corner(g, gam, c, i, j);
@@ -366,6 +369,11 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         const R bg = k.B * gam[c];
         w.Bgx[c] = bg * dyj * at(g.x.rd, i);
         w.Bgy[c] = bg * dxi * at(g.y.rd, j);
+        // mass fluxes through the cell centre, the face between the u (v)
+        // control volumes of faces i and i+1 (j and j+1), with the mean
+        // velocity of the two faces
+        w.Fbu[c] = (u[c] + u[c + 1]) * (R(0.5) * dyj) * rho[c];
+        w.Fbv[c] = (v[c] + v[c + P]) * (R(0.5) * dxi) * rho[c];
     }
     if constexpr (TVD) {
         if (limiters) face_limiters(g, u, v, T, w, c, i, j);
@@ -416,7 +424,7 @@ __device__ R explicit_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L,
     const R vS = v[b - P], vN = v[b + P];
     const R uw1 = u[b - P], uw2 = u[b], ue1 = u[b + 1 - P], ue2 = u[b + 1];
     const R Fw1 = w.Fx[b - P], Fw2 = w.Fx[b], Fe1 = w.Fx[b + 1 - P], Fe2 = w.Fx[b + 1];
-    const R vbs = R(0.5) * (vS + vP), vbn = R(0.5) * (vP + vN);
+    const R Fbs = w.Fbv[b - P], Fbn = w.Fbv[b];     // mass fluxes through the centres of cells j-1, j
     R pw1 = 0, pw2 = 0, pe1 = 0, pe2 = 0, ps = 0, pn = 0;
     if (TVD) {                                     // limiters of level n-1, one per face
         pe1 = positive(ue1) ? w.psVxU[b + 1] : w.psVxD[b + 1];
@@ -428,8 +436,8 @@ __device__ R explicit_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L,
     }
     return R(-0.5) * (Fe1 * (upwind(vP, vE, ue1) + (vE - vP) * pe1) + Fe2 * (upwind(vP, vE, ue2) + (vE - vP) * pe2))
            + R(0.5) * (Fw1 * (upwind(vW, vP, uw1) + (vP - vW) * pw1) + Fw2 * (upwind(vW, vP, uw2) + (vP - vW) * pw2))
-           - dxi * L.rho[b] * vbn * (upwind(vP, vN, vbn) + (vN - vP) * pn)
-           + dxi * L.rho[b - P] * vbs * (upwind(vS, vP, vbs) + (vP - vS) * ps);
+           - Fbn * (upwind(vP, vN, Fbn) + (vN - vP) * pn)
+           + Fbs * (upwind(vS, vP, Fbs) + (vP - vS) * ps);
 }
 
 // u^explicit of u face (i,j): the mirror image of Eq. pl15_11, level n-1.
@@ -447,7 +455,7 @@ __device__ R explicit_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L,
     const R uW = u[a - 1], uE = u[a + 1];
     const R vs1 = v[a - 1], vs2 = v[a], vn1 = v[a - 1 + P], vn2 = v[a + P];
     const R Fs1 = w.Fy[a - 1], Fs2 = w.Fy[a], Fn1 = w.Fy[a - 1 + P], Fn2 = w.Fy[a + P];
-    const R ubw = R(0.5) * (uW + uP), ube = R(0.5) * (uP + uE);
+    const R Fbw = w.Fbu[a - 1], Fbe = w.Fbu[a];     // mass fluxes through the centres of cells i-1, i
     R pn1 = 0, pn2 = 0, ps1 = 0, ps2 = 0, pe = 0, pw = 0;
     if (TVD) {                                     // limiters of level n-1, one per face
         pn1 = positive(vn1) ? w.psUyU[a + P] : w.psUyD[a + P];
@@ -459,8 +467,8 @@ __device__ R explicit_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L,
     }
     return R(-0.5) * (Fn1 * (upwind(uP, uN, vn1) + (uN - uP) * pn1) + Fn2 * (upwind(uP, uN, vn2) + (uN - uP) * pn2))
            + R(0.5) * (Fs1 * (upwind(uS, uP, vs1) + (uP - uS) * ps1) + Fs2 * (upwind(uS, uP, vs2) + (uP - uS) * ps2))
-           - dyj * L.rho[a] * ube * (upwind(uP, uE, ube) + (uE - uP) * pe)
-           + dyj * L.rho[a - 1] * ubw * (upwind(uW, uP, ubw) + (uP - uW) * pw);
+           - Fbe * (upwind(uP, uE, Fbe) + (uE - uP) * pe)
+           + Fbw * (upwind(uW, uP, Fbw) + (uP - uW) * pw);
 }
 
 template <typename R, bool TVD>
@@ -493,26 +501,26 @@ __device__ R energy_source(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> 
     const R rdx = at(g.x.rd, i), rdy = at(g.y.rd, j);
     const R dudx = (u[c + 1] - u[c]) * rdx;
     const R dvdy = (v[c + P] - v[c]) * rdy;
-    const R xl0 = at(g.x.wlo, i), xh0 = at(g.x.whi, i), xl1 = at(g.x.wlo, i + 1), xh1 = at(g.x.whi, i + 1);
-    const R yl0 = at(g.y.wlo, j), yh0 = at(g.y.whi, j), yl1 = at(g.y.wlo, j + 1), yh1 = at(g.y.whi, j + 1);
-    // v at (x^f_i, y^v_j) and (x^f_{i+1}, y^v_j)
+    // dv/dx and du/dy of the cell from the bilinear corner values: v at
+    // (x^f_i, y^v_j) and (x^f_{i+1}, y^v_j), u at (x^v_i, y^f_j) and
+    // (x^v_i, y^f_{j+1}), each the mean of the two face interpolations, with
+    // the values across walls reflected.  With the interpolation weights
+    // summing to one per face, (v_e - v_w) / dx reduces to three weighted pair
+    // sums whose weights the axis tables hold (qlo, qmid, qhi).
     const R *rho = L.rho;
-    const R v_w = R(0.5) * ((xl0 * seen_s<R, WALLS>(v, fl, c, c - 1, F_VWALL, k.zeta, dxi, rho, c - P, c) + xh0 * v[c])
-                              + (xl0 * seen_s<R, WALLS>(v, fl, c + P, c + P - 1, F_VWALL, k.zeta, dxi, rho, c, c + P)
-                                 + xh0 * v[c + P]));
-    const R v_e = R(0.5) * ((xl1 * v[c] + xh1 * seen_s<R, WALLS>(v, fl, c, c + 1, F_VWALL, k.zeta, dxi, rho, c - P, c))
-                              + (xl1 * v[c + P]
-                                 + xh1 * seen_s<R, WALLS>(v, fl, c + P, c + P + 1, F_VWALL, k.zeta, dxi, rho, c, c + P)));
-    // u at (x^v_i, y^f_j) and (x^v_i, y^f_{j+1})
-    const R u_s = R(0.5) * ((yl0 * seen_s<R, WALLS>(u, fl, c, c - P, F_UWALL, k.zeta, dyj, rho, c - 1, c) + yh0 * u[c])
-                              + (yl0 * seen_s<R, WALLS>(u, fl, c + 1, c + 1 - P, F_UWALL, k.zeta, dyj, rho, c, c + 1)
-                                 + yh0 * u[c + 1]));
-    const R u_n = R(0.5) * ((yl1 * u[c] + yh1 * seen_s<R, WALLS>(u, fl, c, c + P, F_UWALL, k.zeta, dyj, rho, c - 1, c))
-                              + (yl1 * u[c + 1]
-                                 + yh1 * seen_s<R, WALLS>(u, fl, c + 1, c + 1 + P, F_UWALL, k.zeta, dyj, rho, c, c + 1)));
-    const R dvdx = (v_e - v_w) * rdx, dudy = (u_n - u_s) * rdy;
+    const R vW0 = seen_s<R, WALLS>(v, fl, c, c - 1, F_VWALL, k.zeta, dxi, rho, c - P, c);
+    const R vW1 = seen_s<R, WALLS>(v, fl, c + P, c + P - 1, F_VWALL, k.zeta, dxi, rho, c, c + P);
+    const R vE0 = seen_s<R, WALLS>(v, fl, c, c + 1, F_VWALL, k.zeta, dxi, rho, c - P, c);
+    const R vE1 = seen_s<R, WALLS>(v, fl, c + P, c + P + 1, F_VWALL, k.zeta, dxi, rho, c, c + P);
+    const R uS0 = seen_s<R, WALLS>(u, fl, c, c - P, F_UWALL, k.zeta, dyj, rho, c - 1, c);
+    const R uS1 = seen_s<R, WALLS>(u, fl, c + 1, c + 1 - P, F_UWALL, k.zeta, dyj, rho, c, c + 1);
+    const R uN0 = seen_s<R, WALLS>(u, fl, c, c + P, F_UWALL, k.zeta, dyj, rho, c - 1, c);
+    const R uN1 = seen_s<R, WALLS>(u, fl, c + 1, c + 1 + P, F_UWALL, k.zeta, dyj, rho, c, c + 1);
+    const R dvdx = at(g.x.qmid, i) * (v[c] + v[c + P]) + at(g.x.qhi, i) * (vE0 + vE1) - at(g.x.qlo, i) * (vW0 + vW1);
+    const R dudy = at(g.y.qmid, j) * (u[c] + u[c + 1]) + at(g.y.qhi, j) * (uN0 + uN1) - at(g.y.qlo, j) * (uS0 + uS1);
     const R div = dudx + dvdy, shear = dvdx + dudy;
-    const R phi = R(2) * (dudx * dudx + dvdy * dvdy) + shear * shear - R(2.0 / 3.0) * div * div;
+    // 2 (dudx^2 + dvdy^2) - 2/3 div^2 = 4/3 (dudx^2 - dudx dvdy + dvdy^2)
+    const R phi = R(4.0 / 3.0) * (dudx * (dudx - dvdy) + dvdy * dvdy) + shear * shear;
     const R vol = dxi * dyj;
     return (k.CT2f * L.gam[c] * phi + k.CT3f * L.p[c] * div) * vol;
 }
@@ -588,21 +596,23 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     const R uW = seen<R, WALLS>(u, fl, a, a - 1, F_UWALL), uE = seen<R, WALLS>(u, fl, a, a + 1, F_UWALL);
     const R uS = seen_s<R, WALLS>(u, fl, a, a - P, F_UWALL, k.zeta, dyj, rho, a - 1, a);
     const R uN = seen_s<R, WALLS>(u, fl, a, a + P, F_UWALL, k.zeta, dyj, rho, a - 1, a);
-    const R ubw = R(0.5) * (uW + uP), ube = R(0.5) * (uP + uE);
-    const R Fbw = ubw * rho[a - 1] * dyj, Fbe = ube * rho[a] * dyj;
+    const R Fbw = w.Fbu[a - 1], Fbe = w.Fbu[a];     // mass fluxes through the centres of cells i-1, i
     const R vs1 = v[a - 1], vs2 = v[a], vn1 = v[a - 1 + P], vn2 = v[a + P];
     const R Fs1 = w.Fy[a - 1], Fs2 = w.Fy[a], Fn1 = w.Fy[a - 1 + P], Fn2 = w.Fy[a + P];
     const R gcs = w.Bgc[a], gcn = w.Bgc[a + P];      // B Gamma at the corners (i, j), (i, j+1)
     const R Dxw = w.Bgx[a - 1], Dxe = w.Bgx[a];
-    const R wsum = dxp + dxw;
-    const R Dys = gcs * wsum * (R(0.5) * at(g.y.rc, j));
-    const R Dyn = gcn * wsum * (R(0.5) * at(g.y.rc, j + 1));
-    const R r2dt = k.hrdt;
-    const R trans = (rho[a] * dxp + rho[a - 1] * dxw) * dyj * r2dt;
-    const R b = (prev.rho[a] * dxp + prev.rho[a - 1] * dxw) * dyj * r2dt * prev.u[a]
-                     + (gcn * (vn2 - vn1) - gcs * (vs2 - vs1))
-                     + k.B * (R(2.0 / 3.0) * gam[a - 1] * (vn1 - vs1) - R(2.0 / 3.0) * gam[a] * (vn2 - vs2))
-                     + k.gx * (rho[a] * dxp + rho[a - 1] * dxw) * dyj * R(0.5);
+    const R cx = at(g.x.dc, i);                      // centre distance of cells i-1, i: half the CV width
+    const R Dys = gcs * cx * at(g.y.rc, j);
+    const R Dyn = gcn * cx * at(g.y.rc, j + 1);
+    const R vdt = dyj * k.hrdt;
+    const R mass = rho[a] * dxp + rho[a - 1] * dxw;  // twice the CV mass over dy
+    const R trans = mass * vdt;
+    const R B23 = R(2.0 / 3.0) * k.B;
+    R b = (prev.rho[a] * dxp + prev.rho[a - 1] * dxw) * vdt * prev.u[a]
+               + (gcn * (vn2 - vn1) - gcs * (vs2 - vs1))
+               + B23 * (gam[a - 1] * (vn1 - vs1) - gam[a] * (vn2 - vs2));
+    if (positive(k.gx) || positive(-k.gx))       // body force (uniform branch: zero in most flows)
+        b += k.gx * mass * dyj * R(0.5);
     R a1, a2, a3, a4, a0, uexp;
     if (IMPL) {
         R pw = 0, pe = 0, ps1 = 0, ps2 = 0, pn1 = 0, pn2 = 0;
@@ -653,21 +663,23 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     const R vW = seen_s<R, WALLS>(v, fl, b, b - 1, F_VWALL, k.zeta, dxi, rho, b - P, b);
     const R vE = seen_s<R, WALLS>(v, fl, b, b + 1, F_VWALL, k.zeta, dxi, rho, b - P, b);
     const R vS = seen<R, WALLS>(v, fl, b, b - P, F_VWALL), vN = seen<R, WALLS>(v, fl, b, b + P, F_VWALL);
-    const R vbs = R(0.5) * (vS + vP), vbn = R(0.5) * (vP + vN);
-    const R Fbs = vbs * rho[b - P] * dxi, Fbn = vbn * rho[b] * dxi;
+    const R Fbs = w.Fbv[b - P], Fbn = w.Fbv[b];     // mass fluxes through the centres of cells j-1, j
     const R uw1 = u[b - P], uw2 = u[b], ue1 = u[b + 1 - P], ue2 = u[b + 1];
     const R Fw1 = w.Fx[b - P], Fw2 = w.Fx[b], Fe1 = w.Fx[b + 1 - P], Fe2 = w.Fx[b + 1];
     const R gcw = w.Bgc[b], gce = w.Bgc[b + 1];      // B Gamma at the corners (i, j), (i+1, j)
-    const R hsum = dyp + dys;
-    const R Dxw = gcw * hsum * (R(0.5) * at(g.x.rc, i));
-    const R Dxe = gce * hsum * (R(0.5) * at(g.x.rc, i + 1));
+    const R cy = at(g.y.dc, j);                      // centre distance of cells j-1, j: half the CV height
+    const R Dxw = gcw * cy * at(g.x.rc, i);
+    const R Dxe = gce * cy * at(g.x.rc, i + 1);
     const R Dys = w.Bgy[b - P], Dyn = w.Bgy[b];
-    const R r2dt = k.hrdt;
-    const R trans = (rho[b] * dyp + rho[b - P] * dys) * dxi * r2dt;
-    const R bsrc = (prev.rho[b] * dyp + prev.rho[b - P] * dys) * dxi * r2dt * prev.v[b]
-                        + (gce * (ue2 - ue1) - gcw * (uw2 - uw1))
-                        + k.B * (R(2.0 / 3.0) * gam[b - P] * (ue1 - uw1) - R(2.0 / 3.0) * gam[b] * (ue2 - uw2))
-                        + k.gy * (rho[b] * dyp + rho[b - P] * dys) * dxi * R(0.5);
+    const R vdt = dxi * k.hrdt;
+    const R mass = rho[b] * dyp + rho[b - P] * dys;  // twice the CV mass over dx
+    const R trans = mass * vdt;
+    const R B23 = R(2.0 / 3.0) * k.B;
+    R bsrc = (prev.rho[b] * dyp + prev.rho[b - P] * dys) * vdt * prev.v[b]
+                  + (gce * (ue2 - ue1) - gcw * (uw2 - uw1))
+                  + B23 * (gam[b - P] * (ue1 - uw1) - gam[b] * (ue2 - uw2));
+    if (positive(k.gy) || positive(-k.gy))       // body force (uniform branch: zero in most flows)
+        bsrc += k.gy * mass * dxi * R(0.5);
     R a1, a2, a3, a4, a0, vexp;
     if (IMPL) {
         R pw1 = 0, pw2 = 0, pe1 = 0, pe2 = 0, ps = 0, pn = 0;
@@ -769,11 +781,12 @@ __device__ __forceinline__ void pressure_body(const GeoT<R> &g, const CoefT<R> &
         const int c = Ix{P}(i, j);
         if (g.flag[c] & F_FLUID) {
             const R dxi = at(g.x.d, i), dyj = at(g.y.d, j);
-            const R ru_w = w.rho_u[c], ru_e = w.rho_u[c + 1], rv_s = w.rho_v[c], rv_n = w.rho_v[c + P];
-            const R apw = ru_w * w.du[c] * dyj, ape = ru_e * w.du[c + 1] * dyj;
-            const R aps = rv_s * w.dv[c] * dxi, apn = rv_n * w.dv[c + P] * dxi;
-            const R bpw = ru_w * w.uhat[c] * dyj, bpe = ru_e * w.uhat[c + 1] * dyj;
-            const R bps = rv_s * w.vhat[c] * dxi, bpn = rv_n * w.vhat[c + P] * dxi;
+            // rho^u dy and rho^v dx of the four faces (stored by the face kernel)
+            const R ru_w = w.ru_dy[c], ru_e = w.ru_dy[c + 1], rv_s = w.rv_dx[c], rv_n = w.rv_dx[c + P];
+            const R apw = ru_w * w.du[c], ape = ru_e * w.du[c + 1];
+            const R aps = rv_s * w.dv[c], apn = rv_n * w.dv[c + P];
+            const R bpw = ru_w * w.uhat[c], bpe = ru_e * w.uhat[c + 1];
+            const R bps = rv_s * w.vhat[c], bpn = rv_n * w.vhat[c + P];
             const R Tn = nw.T[c], inv_T = recip(Tn);
             const R vol = dxi * dyj;
             const R ap0 = vol * inv_T + (apw + ape + aps + apn) * k.dt;
@@ -955,11 +968,11 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
         const int c = Ix{P}(i, j);
         if (g.flag[c] & F_FLUID) {
             const float dxi = at(g32.x.d, i), dyj = at(g32.y.d, j);
-            const float ru_w = w.rho_u[c], ru_e = w.rho_u[c + 1], rv_s = w.rho_v[c], rv_n = w.rho_v[c + P];
-            const float apw = ru_w * w.du[c] * dyj, ape = ru_e * w.du[c + 1] * dyj;
-            const float aps = rv_s * w.dv[c] * dxi, apn = rv_n * w.dv[c + P] * dxi;
-            const float bpw = ru_w * w.uhat[c] * dyj, bpe = ru_e * w.uhat[c + 1] * dyj;
-            const float bps = rv_s * w.vhat[c] * dxi, bpn = rv_n * w.vhat[c + P] * dxi;
+            const float ru_w = w.ru_dy[c], ru_e = w.ru_dy[c + 1], rv_s = w.rv_dx[c], rv_n = w.rv_dx[c + P];
+            const float apw = ru_w * w.du[c], ape = ru_e * w.du[c + 1];
+            const float aps = rv_s * w.dv[c], apn = rv_n * w.dv[c + P];
+            const float bpw = ru_w * w.uhat[c], bpe = ru_e * w.uhat[c + 1];
+            const float bps = rv_s * w.vhat[c], bpn = rv_n * w.vhat[c + P];
             const float T32 = nw32.T[c];
             const double Tn = widen(T32);
             const float ap0 = dxi * dyj / T32 + (apw + ape + aps + apn) * k32.dt;
