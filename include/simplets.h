@@ -172,8 +172,11 @@ sim_status sim_set_fields(sim_t sim, int field, const double *host_src, size_t n
  * arrays in the logical shapes (u: (nx+1) x ny, v: nx x (ny+1), p, T: nx x ny;
  * row-major, x fastest), as four sim_set_fields calls would, with one
  * synchronisation: the values are copied to the device and checked there
- * (finite; p, T > 0) before anything changes.  On return the host arrays may
- * be reused; the update itself is queued on the handle's stream.  Clears the
+ * (finite; p, T > 0) before anything changes.  Arrays wholly in page-locked
+ * host memory that the device addresses (cudaHostAlloc, cudaHostRegister)
+ * are read by one kernel over the host link; other arrays are copied with
+ * cudaMemcpyAsync.  On return the host arrays may be reused; the update
+ * itself is queued on the handle's stream.  Clears the
  * error state of a diverged handle.  Errors: SIM_EINVAL (null array, or a
  * value not admissible: nothing is changed), SIM_ENOMEM, SIM_ECUDA. */
 sim_status sim_set_state(sim_t sim, const double *u, const double *v, const double *p, const double *T);
@@ -181,6 +184,8 @@ sim_status sim_set_state(sim_t sim, const double *u, const double *v, const doub
 /* Copy all four fields of the current state into host arrays (logical shapes,
  * boundary values included) and, if res is not NULL, the residuals of the
  * last loop-2 iteration (as sim_residuals), with one synchronisation.
+ * Page-locked destination arrays are written by the gather kernel directly;
+ * others receive cudaMemcpyAsync copies of a device staging array.
  * Errors: SIM_EINVAL (null array), SIM_ECUDA; SIM_EDIVERGED if a residual is
  * not finite (the fields are copied all the same). */
 sim_status sim_get_state(sim_t sim, double *u, double *v, double *p, double *T, double res[4]);

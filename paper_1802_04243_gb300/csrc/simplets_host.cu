@@ -877,6 +877,30 @@ bool read_residuals(const unsigned long long *bits, double out[4])
     return ok;
 }
 
+// Device address of a host array of `bytes` bytes when its first and last
+// bytes lie in page-locked memory that the device addresses, mapped as one
+// range; nullptr otherwise (pageable memory, or memory CUDA does not know),
+// and the caller copies with cudaMemcpyAsync instead.
+const void *mapped_view(const void *p, size_t bytes)
+{
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    const char *last = (const char *)p + (bytes - 1);
+    if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (b.type != cudaMemoryTypeHost || !b.devicePointer ||
+        (const char *)b.devicePointer - (const char *)a.devicePointer != (std::ptrdiff_t)(bytes - 1))
+        return nullptr;
+    return a.devicePointer;
+}
+
 sim_status ensure_state_stage(sim_t s)
 {
     if (s->d_state) return SIM_OK;
@@ -906,18 +930,29 @@ extern "C" sim_status sim_set_state(sim_t s, const double *u, const double *v, c
     const double *src[4] = {u, v, p, T};
     const size_t off[4] = {0, nu, nu + nv, nu + nv + nc}, cnt[4] = {nu, nv, nc, nc};
     CUDA_TRY(s, cudaMemsetAsync(s->d_bad, 0, sizeof(unsigned), s->stream));
-    for (int f = 0; f < 4; f++)
-        CUDA_TRY(s, cudaMemcpyAsync(s->d_state + off[f], src[f], cnt[f] * sizeof(double), cudaMemcpyHostToDevice,
-                                    s->stream));
-    launch_validate_state(s->d_state, nu, nv, nc, s->d_bad, s->stream);
+    // page-locked arrays: one kernel reads them over the host link, stages and
+    // checks them; otherwise four copies and the check
+    StateSrc view{};
+    bool mapped = true;
+    for (int f = 0; f < 4 && mapped; f++) {
+        view.f[f] = (const double *)mapped_view(src[f], cnt[f] * sizeof(double));
+        mapped = view.f[f] != nullptr;
+    }
+    if (mapped) {
+        launch_stage_state(view, nu, nv, nc, s->d_state, s->d_bad, s->stream);
+    } else {
+        for (int f = 0; f < 4; f++)
+            CUDA_TRY(s, cudaMemcpyAsync(s->d_state + off[f], src[f], cnt[f] * sizeof(double),
+                                        cudaMemcpyHostToDevice, s->stream));
+        launch_validate_state(s->d_state, nu, nv, nc, s->d_bad, s->stream);
+    }
     CUDA_TRY(s, cudaMemcpyAsync(s->h_bad, s->d_bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
     if (*s->h_bad) return fail(s, SIM_EINVAL, "state not admissible (non-finite value, or p or T <= 0)");
     // every unknown is overwritten: the FP64 level needs no refresh from the
     // double-float one first
     const Level &L = s->lv[s->cur];
-    for (int f = 0; f < 4; f++) launch_scatter(s->geo, f, s->d_state + off[f], L, s->stream);
-    launch_derive(s->geo, s->pb.k, L, s->stream);
+    launch_scatter_state(s->geo, s->pb.k, s->d_state, L, s->stream);
     launch_ghosts(s->geo, s->sides, L, false, s->stream);
     if (s->mixed) launch_shadow(s->geo, L, s->mx.lv[s->cur], s->nelem, s->stream);
     if (s->df) launch_split(L, s->dfm.lv[s->cur], s->nelem, s->stream);
@@ -939,11 +974,21 @@ extern "C" sim_status sim_get_state(sim_t s, double *u, double *v, double *p, do
     double *dst[4] = {u, v, p, T};
     const size_t off[4] = {0, nu, nu + nv, nu + nv + nc}, cnt[4] = {nu, nv, nc, nc};
     sync_out(s);
-    for (int f = 0; f < 4; f++) launch_gather(s->geo, f, s->lv[s->cur], s->d_state + off[f], s->stream);
+    // page-locked arrays: the gather kernel writes them over the host link;
+    // otherwise it writes the staging array, copied out field by field
+    StatePtrs view{}, stage{};
+    bool mapped = true;
+    for (int f = 0; f < 4 && mapped; f++) {
+        view.f[f] = (double *)mapped_view(dst[f], cnt[f] * sizeof(double));
+        mapped = view.f[f] != nullptr;
+    }
+    for (int f = 0; f < 4; f++) stage.f[f] = s->d_state + off[f];
+    launch_gather_state(s->geo, s->lv[s->cur], mapped ? view : stage, s->stream);
     CUDA_TRY(s, cudaGetLastError());
-    for (int f = 0; f < 4; f++)
-        CUDA_TRY(s, cudaMemcpyAsync(dst[f], s->d_state + off[f], cnt[f] * sizeof(double), cudaMemcpyDeviceToHost,
-                                    s->stream));
+    if (!mapped)
+        for (int f = 0; f < 4; f++)
+            CUDA_TRY(s, cudaMemcpyAsync(dst[f], s->d_state + off[f], cnt[f] * sizeof(double),
+                                        cudaMemcpyDeviceToHost, s->stream));
     if (res)
         CUDA_TRY(s, cudaMemcpyAsync(s->h_res, s->work.res, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                     s->stream));

@@ -207,6 +207,22 @@ int ghost_kernels(const Sides &s, bool after_velocity);
 void launch_derive(const Geo &g, const Coef &c, const Level &lv, void *stream);
 void launch_scatter(const Geo &g, int field, const double *src, const Level &lv, void *stream);
 void launch_gather(const Geo &g, int field, const Level &lv, double *dst, void *stream);
+// The four state fields u, v, p, T as separate arrays in their logical shapes.
+struct StatePtrs {
+    double *f[4];
+};
+struct StateSrc {
+    const double *f[4];
+};
+// All four fields in one launch.  The scatter reads them back to back from
+// the staging array and derives rho and Gamma as launch_derive does; the
+// gather writes four arrays (device memory, or page-locked host memory the
+// device addresses); the staging copy reads four such arrays into the
+// staging array and checks them as launch_validate_state does.
+void launch_scatter_state(const Geo &g, const Coef &c, const double *stage, const Level &lv, void *stream);
+void launch_gather_state(const Geo &g, const Level &lv, const StatePtrs &dst, void *stream);
+void launch_stage_state(const StateSrc &src, size_t nu, size_t nv, size_t nc, double *stage, unsigned *bad,
+                        void *stream);
 // Sets *bad (|= 1) if a value of the staged u, v, p, T is not finite or p, T <= 0.
 void launch_validate_state(const double *stage, size_t nu, size_t nv, size_t nc, unsigned *bad, void *stream);
 void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, size_t nelem, void *stream);

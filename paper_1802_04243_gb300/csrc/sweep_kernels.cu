@@ -1249,6 +1249,68 @@ __global__ void k_gather(Geo g, int field, Level L, double *dst)
     dst[(size_t)j * w + i] = field_of(L, field)[Ix{g.pitch}(i, j)];
 }
 
+// All four fields of a staged state (u, v, p, T back to back in their
+// logical shapes) into the unknowns of a level, with rho and Gamma derived
+// as k_derive derives them; one thread per position.
+__global__ void k_scatter_state(Geo g, Coef k, const double *st, Level L)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    const int nx = g.nx, ny = g.ny;
+    if (i > nx || j > ny) return;
+    const size_t nu = (size_t)(nx + 1) * ny, nv = (size_t)nx * (ny + 1), nc = (size_t)nx * ny;
+    const int c = Ix{g.pitch}(i, j);
+    const uint16_t f = g.flag[c];
+    if (j < ny && (f & F_UACT)) L.u[c] = st[(size_t)j * (nx + 1) + i];
+    if (i < nx && (f & F_VACT)) L.v[c] = st[nu + (size_t)j * nx + i];
+    if (i < nx && j < ny && (f & F_FLUID)) {
+        const size_t q = (size_t)j * nx + i;
+        const double p = st[nu + nv + q], T = st[nu + nv + nc + q];
+        L.p[c] = p;
+        L.T[c] = T;
+        L.rho[c] = p * recip(T);
+        L.gam[c] = (k.omega == 0.5) ? sqrt(T) : pow(T, k.omega);
+    }
+}
+
+// All four fields of a level into four arrays in their logical shapes
+// (device memory, or page-locked host memory the device addresses),
+// boundary values included.
+__global__ void k_gather_state(Geo g, Level L, StatePtrs dst)
+{
+    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    const int nx = g.nx, ny = g.ny;
+    if (i > nx || j > ny) return;
+    const int c = Ix{g.pitch}(i, j);
+    if (j < ny) dst.f[0][(size_t)j * (nx + 1) + i] = L.u[c];
+    if (i < nx) dst.f[1][(size_t)j * nx + i] = L.v[c];
+    if (i < nx && j < ny) {
+        const size_t q = (size_t)j * nx + i;
+        dst.f[2][q] = L.p[c];
+        dst.f[3][q] = L.T[c];
+    }
+}
+
+// Copy of a state from four arrays the device addresses (u, v, p, T in their
+// logical shapes, e.g. page-locked host memory) into the staging array, with
+// the admissibility check of k_validate_state.
+__global__ void k_stage_state(StateSrc src, size_t nu, size_t nv, size_t nc, double *stage, unsigned *bad)
+{
+    const size_t n = nu + nv + 2 * nc;
+    unsigned b = 0;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        double x;
+        if (q < nu) x = src.f[0][q];
+        else if (q < nu + nv) x = src.f[1][q - nu];
+        else if (q < nu + nv + nc) x = src.f[2][q - nu - nv];
+        else x = src.f[3][q - nu - nv - nc];
+        stage[q] = x;
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+        const bool finite = ((bits >> 52) & 0x7FFull) != 0x7FFull;
+        if (!finite || (q >= nu + nv && !positive(x))) b = 1u;
+    }
+    if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+}
+
 // recip(x) next to the IEEE quotient 1/x, for the check of the reciprocal.
 __global__ void k_recip_check(const double *x, double *out, int n)
 {
@@ -1361,6 +1423,24 @@ void launch_validate_state(const double *stage, size_t nu, size_t nv, size_t nc,
 void launch_derive(const Geo &g, const Coef &c, const Level &lv, void *stream)
 {
     k_derive<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, c, lv);
+}
+
+void launch_scatter_state(const Geo &g, const Coef &c, const double *stage, const Level &lv, void *stream)
+{
+    k_scatter_state<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, c, stage, lv);
+}
+
+void launch_gather_state(const Geo &g, const Level &lv, const StatePtrs &dst, void *stream)
+{
+    k_gather_state<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, lv, dst);
+}
+
+void launch_stage_state(const StateSrc &src, size_t nu, size_t nv, size_t nc, double *stage, unsigned *bad,
+                        void *stream)
+{
+    const size_t n = nu + nv + 2 * nc;
+    const int blocks = (int)((n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048);
+    k_stage_state<<<blocks, 256, 0, (cudaStream_t)stream>>>(src, nu, nv, nc, stage, bad);
 }
 
 void launch_scatter(const Geo &g, int field, const double *src, const Level &lv, void *stream)

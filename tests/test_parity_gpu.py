@@ -376,19 +376,35 @@ def test_parity_paper_channel_4032x200(implicit, tvd):
 
 # ------------------------------------------------- whole-state calls
 
+def _page_locked(state, keep):
+    # numpy views of page-locked copies (the library reads and writes these
+    # directly from its kernels); `keep` holds the owning tensors
+    import torch
+    out = {}
+    for k, v in state.items():
+        t = torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+        keep.append(t)
+        out[k] = t.numpy()
+    return out
+
+
+@pytest.mark.parametrize("pinned", [False, True], ids=["pageable", "page-locked"])
 @pytest.mark.parametrize("precision", [W.FP64, W.MIXED, W.DF64], ids=["fp64", "mixed", "df64"])
-def test_state_calls_match_field_calls(precision):
+def test_state_calls_match_field_calls(precision, pinned):
     # sim_set_state / sim_get_state (one synchronisation each) give the bits of
-    # four sim_set_fields / sim_fields calls
+    # four sim_set_fields / sim_fields calls, from and into pageable arrays
+    # (copies) and page-locked arrays (read and written by the kernels)
     case = W.c1_small().replace(precision=precision)
+    keep = []
     with sim.Simulation(case) as a, sim.Simulation(case) as b:
         a.step(3)
         mid = a.fields()
         b.set_fields(mid)
-        a.set_state(mid)
+        a.set_state(_page_locked(mid, keep) if pinned else mid)
         a.step(4)
         b.step(4)
-        got, res, st = a.get_state()
+        out = _page_locked({k: np.full(a.shape(k), np.nan) for k in "uvpT"}, keep) if pinned else None
+        got, res, st = a.get_state(out)
         ref = b.fields()
         rres, _, _ = b.residuals()
     assert st == sim.SIM_OK
@@ -397,20 +413,26 @@ def test_state_calls_match_field_calls(precision):
     assert np.array_equal(res, rres)
 
 
-def test_set_state_rejects_inadmissible_values_and_changes_nothing():
+@pytest.mark.parametrize("pinned", [False, True], ids=["pageable", "page-locked"])
+def test_set_state_rejects_inadmissible_values_and_changes_nothing(pinned):
     case = W.c1_small()
+    keep = []
     with sim.Simulation(case) as s:
         s.step(2)
         before = s.fields()
         bad = {k: v.copy() for k, v in before.items()}
         bad["T"][3, 5] = -1.0
         with pytest.raises(sim.SimError) as e:
-            s.set_state(bad)
+            s.set_state(_page_locked(bad, keep) if pinned else bad)
         assert e.value.status == sim.SIM_EINVAL
         bad = {k: v.copy() for k, v in before.items()}
         bad["u"][0, 0] = np.nan
         with pytest.raises(sim.SimError):
-            s.set_state(bad)
+            s.set_state(_page_locked(bad, keep) if pinned else bad)
+        bad = {k: v.copy() for k, v in before.items()}
+        bad["p"][-1, -1] = 0.0                       # the last value of the staged state
+        with pytest.raises(sim.SimError):
+            s.set_state(_page_locked(bad, keep) if pinned else bad)
         after = s.fields()
     for k in "uvpT":
         assert np.array_equal(before[k], after[k]), k
