@@ -24,8 +24,9 @@ extern "C" {
 int simplets_alu_peak(int kind, double millis, void *stream, double *gflops);
 
 /* Check of the FP64 reciprocal the sweep uses in place of IEEE division
- * (Newton-Raphson iteration r <- r (2 - x r), two steps from the FP32
- * reciprocal of x; IEEE division for |x| outside [2^-100, 2^100]).
+ * (from the FP32 reciprocal r of x, one step r <- r + r (e + e^2) with
+ * e = 1 - x r, the geometric series of 1/x = r / (1 - e) to third order;
+ * IEEE division for |x| outside [2^-100, 2^100]).
  * host_x: n doubles (host memory).  host_out: 2n doubles (host memory)
  * receiving, for each x[q], the sweep's reciprocal in host_out[2q] and the
  * IEEE quotient 1/x[q] in host_out[2q+1], both computed on the device.

@@ -230,7 +230,7 @@ void launch_shadow(const Geo &g, const Level &lv, const LevelT<float> &lv32, siz
 void launch_split(const Level &lv, const LevelT<df64> &d, size_t nelem, void *stream);
 void launch_join(const LevelT<df64> &d, const Level &lv, size_t nelem, void *stream);
 
-// The FP64 reciprocal of the sweep (Newton-Raphson from an FP32 seed) and the
+// The FP64 reciprocal of the sweep (a series step from the FP32 reciprocal) and the
 // IEEE quotient 1/x of each x[q], interleaved in out[2q], out[2q+1].
 void launch_recip_check(const double *x, double *out, int n, void *stream);
 

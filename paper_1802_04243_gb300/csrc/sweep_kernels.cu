@@ -228,21 +228,22 @@ __device__ __forceinline__ void block_max2(unsigned long long a, unsigned long l
     __syncthreads();       // the shared slots are reused by the block's next call
 }
 
-// 1/a.  FP64: Newton-Raphson reciprocal iteration r <- r (2 - a r) (two
-// steps, written as fused multiply-adds) from the FP32 reciprocal of a; it
-// replaces the longer IEEE division sequence on GB300's slow FP64 pipe and
-// is within a few ulp of 1/a.  Magnitudes outside [2^-100, 2^100] fall back
-// to the IEEE division.  FP32: the IEEE division.
+// 1/a.  FP64: from the FP32 reciprocal r of a (relative error e = 1 - a r
+// below about 2^-23), one third-order step of the geometric series
+// 1/a = r / (1 - e) = r (1 + e + e^2 + ...), r <- r + r (e + e^2), three
+// fused multiply-adds; the truncation leaves about e^3 < 2^-69, so the result
+// is within one ulp of 1/a.  It replaces the longer IEEE division sequence on
+// GB300's slow FP64 pipe.  Magnitudes outside [2^-100, 2^100] fall back to the
+// IEEE division.  FP32: the IEEE division.
 __device__ __forceinline__ float recip(float a) { return 1.0f / a; }
 __device__ __forceinline__ double recip(double a)
 {
-    const unsigned e = ((unsigned)__double2hiint(a) >> 20) & 0x7FFu;
-    if (e < 1023u - 100u || e > 1023u + 100u)
+    const unsigned ex = ((unsigned)__double2hiint(a) >> 20) & 0x7FFu;
+    if (ex < 1023u - 100u || ex > 1023u + 100u)
         return 1.0 / a;
-    double r = widen(1.0f / narrow(a));
-    r = fma(r, fma(-a, r, 1.0), r);
-    r = fma(r, fma(-a, r, 1.0), r);
-    return r;
+    const double r = widen(1.0f / narrow(a));
+    const double e = fma(-a, r, 1.0);
+    return fma(r, fma(e, e, e), r);
 }
 
 // Residual key |d| of a difference held in the compute precision (a
@@ -769,7 +770,7 @@ __device__ __forceinline__ void assemble_body(const GeoT<R> &g, const CoefT<R> &
 
 // Eqs. pl23, pl24 with the new T (point Jacobi in p^old), then rho = p/T
 // (Eq. pl5) and Gamma = T^omega, with the p and T residual maxima.  The
-// divisions by T and a^p_0 use the Newton-Raphson reciprocal.
+// divisions by T and a^p_0 use the sweep's reciprocal.
 template <typename R>
 __device__ __forceinline__ void pressure_body(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev,
                                               const LevelT<R> &old, const LevelT<R> &nw, const WorkT<R> &w,

@@ -1,10 +1,11 @@
 """The FP64 reciprocal of the sweep against CUDA's IEEE division.
 
 The sweep divides by a^0 (Eqs. pl15, pl20, pl21, pl30) and by T and a^p_0
-(Eqs. pl23, pl5) with a Newton-Raphson reciprocal, r <- r (2 - x r), two steps
-from the FP32 reciprocal of x, instead of IEEE division.  Two steps take the
-FP32 seed's relative error (about 2^-23) to below the FP64 rounding, so the
-result must stay within one unit in the last place of the IEEE quotient."""
+(Eqs. pl23, pl5) with its own reciprocal instead of IEEE division: from the
+FP32 reciprocal r of x, with e = 1 - x r (about 2^-23), one step
+r + r (e + e^2) of the geometric series of r / (1 - e).  The truncation error
+e^3 is far below the FP64 rounding, so the result must stay within one unit
+in the last place of the IEEE quotient."""
 import numpy as np
 import pytest
 

@@ -63,7 +63,7 @@ def test_start_state_is_bitwise_identical(case):
     o = oracle.init(case)
     for k in "uvpT":
         assert np.array_equal(g[k], o[k]), k
-    # rho = p/T (Eq. pl5) with the sweep's Newton-Raphson reciprocal of T:
+    # rho = p/T (Eq. pl5) with the sweep's own reciprocal of T:
     # within two units in the last place of the IEEE quotient
     q = o["p"] / o["T"]
     assert np.all(np.abs(g["rho"] - q) <= 2 * np.spacing(np.abs(q)))
