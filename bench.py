@@ -71,6 +71,11 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=40)
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2",
                     help="c2 (default, the benchmark line); the others are for profiling and sweeps")
+    ap.add_argument("--sweep", choices=["paper"], default=None,
+                    help="paper: the paper's experiment (Section 4) -- the four schemes on the 4032 x "
+                         "{200, 400, 2000, 4000} meshes with 1, 2, 10, 20 particles, FP64, against the "
+                         "oracle on one core, and the tile-height sweep that stands in for its rows per "
+                         "work-group")
     return ap.parse_args()
 
 
@@ -273,6 +278,85 @@ def oracle_throughput(case, target_s: float = 12.0, max_steps: int = 400):
     oracle.run(case, state, nsteps=n)
     dt = time.perf_counter() - t0
     return case.cells * n / dt / 1e6, n, dt
+
+
+# ------------------------------------------------------------ paper sweep
+
+PAPER_HEIGHTS = (200, 400, 2000, 4000)
+PAPER_SCHEMES = (("explicit-tvd", False, True), ("explicit-upwind", False, False),
+                 ("implicit-tvd", True, True), ("implicit-upwind", True, False))
+PAPER_TILES = ((256, 1), (128, 2), (64, 4), (32, 8), (16, 16))
+
+
+def run_paper_sweep(args, local_rank):
+    """The paper's experiment (Section 4): every scheme on the four meshes of
+    its test case, FP64 Mcell-steps/s and the speedup over the serial oracle on
+    one host core on the same case; then, for the implicit upwind scheme, the
+    throughput of every tile shape of 256 threads (tile height 1 to 16 rows),
+    which plays the part of the paper's rows per work-group."""
+    import torch
+
+    import paper_1802_04243_gb300 as sim
+    import workloads as W
+    from paper_1802_04243_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    steps = max(1, args.steps)
+
+    def timed(step_fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            step_fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    rows, tiles = [], []
+    with ClockSampler(local_rank) as clocks:
+        for ny in PAPER_HEIGHTS:
+            base = W.paper_channel(ny=ny)
+            for name, implicit, tvd in PAPER_SCHEMES:
+                case = base.replace(implicit=implicit, tvd=tvd)
+                with sim.Simulation(case, stream=stream.cuda_stream) as s:
+                    for _ in range(args.warmup):
+                        s.step(1)
+                    ms = timed(lambda: s.step(1), steps)
+                v = throughput(case.cells, steps, 1, ms * 1e-3)
+                row = {"ny": ny, "particles": len(case.rects), "scheme": name, "fp64": round(v, 2)}
+                if not args.no_cpu_baseline:
+                    # one time step of the serial oracle on the same case
+                    import oracle
+                    state = oracle.init(case)
+                    t0 = time.perf_counter()
+                    oracle.run(case, state, nsteps=1)
+                    dt = time.perf_counter() - t0
+                    o = case.cells / dt / 1e6
+                    row.update({"oracle_1core": round(o, 3), "speedup": round(v / o, 1),
+                                "oracle_sample": f"1 step, {dt:.1f} s"})
+                rows.append(row)
+            case = base.replace(implicit=True, tvd=False)
+            with sim.Batch([case], stream=stream.cuda_stream) as b:
+                for tx, ty in PAPER_TILES:
+                    b.set_tiles(tx, ty, 0)
+                    for _ in range(max(2, args.warmup)):
+                        b.step(1)
+                    ms = timed(lambda: b.step(1), steps)
+                    tiles.append({"ny": ny, "tile": [tx, ty],
+                                  "fp64": round(throughput(case.cells, steps, 1, ms * 1e-3), 2)})
+    top = next(r for r in rows if r["ny"] == PAPER_HEIGHTS[-1] and r["scheme"] == "implicit-upwind")
+    line = {"metric": METRIC, "value": top["fp64"], "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "paper sweep: 4032 x {200, 400, 2000, 4000} channels with 1, 2, 10, 20 "
+                                   "square particles (side 20 cells, one per 10 a of height), hard-sphere gas "
+                                   "Kn 0.001, Mach 2.43, moving slip/jump walls; value = 4032x4000 implicit "
+                                   "upwind",
+                       "l2": "state larger than L2 on every mesh", "parallelism": "single GPU"},
+            "sweep": rows, "tiles": tiles, "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------- ours
@@ -480,6 +564,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.sweep == "paper":
+        if rank == 0:
+            run_paper_sweep(args, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

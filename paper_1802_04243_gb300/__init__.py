@@ -90,6 +90,7 @@ _SIGNATURES = {
     "sim_batch_fields": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _DP, ctypes.c_size_t], ctypes.c_int),
     "sim_batch_residuals": ([ctypes.c_void_p, ctypes.c_int, _DP], ctypes.c_int),
     "sim_batch_tune": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "sim_batch_set_tiles": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "sim_batch_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "sim_batch_destroy": ([ctypes.c_void_p], None),
     "sim_step_noalloc": ([ctypes.POINTER(sim_grid), ctypes.POINTER(sim_gas), ctypes.POINTER(sim_bc), ctypes.c_int,
@@ -346,6 +347,10 @@ class Batch:
         out = (ctypes.c_int * 3)()
         self._check(self.lib.sim_batch_tune(self.handle, self.scheme if scheme is None else int(scheme), out))
         return tuple(out)
+
+    def set_tiles(self, tile_x: int, tile_y: int, ctas: int = 0):
+        """Tiles of tile_x x tile_y threads walked by `ctas` CTAs (0: one per tile), sim_batch_set_tiles."""
+        self._check(self.lib.sim_batch_set_tiles(self.handle, int(tile_x), int(tile_y), int(ctas)))
 
     def field(self, instance: int, name: str) -> np.ndarray:
         c = self.cases[instance]

@@ -1398,6 +1398,17 @@ extern "C" sim_status sim_batch_tune(sim_batch_t b, int scheme, int out[3])
     return SIM_OK;
 }
 
+extern "C" sim_status sim_batch_set_tiles(sim_batch_t b, int tx, int ty, int ctas)
+{
+    if (!b) return SIM_EINVAL;
+    const bool shape = (tx == 16 || tx == 32 || tx == 64 || tx == 128 || tx == 256) && tx * ty == 256;
+    if (!shape || ctas < 0)
+        return bfail(b, SIM_EINVAL, "tile %d x %d with %d CTAs: want 256 threads, tile x in {16, ..., 256}, CTAs >= 0",
+                     tx, ty, ctas);
+    BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
+    return plan_tiles(b, tx, ty, ctas);
+}
+
 extern "C" const char *sim_batch_last_error(sim_batch_t b)
 {
     return b ? b->err : "null batch";

@@ -92,5 +92,6 @@ def test_null_arguments(lib):
     assert lib.sim_create(None, None, None, None, None) == sim.SIM_EINVAL
     assert lib.sim_set_state(None, None, None, None, None) == sim.SIM_EINVAL
     assert lib.sim_get_state(None, None, None, None, None, None) == sim.SIM_EINVAL
+    assert lib.sim_batch_set_tiles(None, 32, 8, 0) == sim.SIM_EINVAL
     lib.sim_destroy(None)
     assert lib.sim_last_error(None) == b"null handle"

@@ -76,6 +76,29 @@ def test_tuning_keeps_the_state_and_the_results():
                 assert np.array_equal(fa[k], fb[k]), (q, k)
 
 
+@pytest.mark.parametrize("shape", [(16, 16, 0), (64, 4, 0), (128, 2, 304), (256, 1, 0), (32, 8, 152)])
+def test_every_tile_shape_gives_the_same_bits(shape):
+    # sim_batch_set_tiles: any distribution of the positions over threads and
+    # CTAs gives the bits of the default one (32 x 8, one CTA per tile)
+    cases = small_batch(n=3, precision=W.FP64)
+    with sim.Batch(cases) as a, sim.Batch(cases) as b:
+        b.set_tiles(*shape)
+        a.step(5)
+        b.step(5)
+        for q in range(len(cases)):
+            fa, fb = a.fields(q), b.fields(q)
+            for k in "uvpT":
+                assert np.array_equal(fa[k], fb[k]), (q, k)
+
+
+def test_set_tiles_rejects_other_shapes():
+    with sim.Batch(small_batch(n=1)) as b:
+        for bad in [(32, 4, 0), (8, 32, 0), (512, 1, 0), (32, 8, -1)]:
+            with pytest.raises(sim.SimError) as e:
+                b.set_tiles(*bad)
+            assert e.value.status == sim.SIM_EINVAL
+
+
 def test_batch_rejects_mixed_loop2_lengths():
     cases = small_batch(n=2)
     cases[1] = cases[1].replace(iters=3)

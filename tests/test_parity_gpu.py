@@ -366,10 +366,12 @@ def test_mixed_precision_slip_walls_error():
     assert max(e.values()) <= MIXED_BOUND, e
 
 
+@pytest.mark.parametrize("ny", [200, 400], ids=["4032x200-1-particle", "4032x400-2-particles"])
 @pytest.mark.parametrize("implicit,tvd", [(True, False), (False, True)], ids=["implicit-upwind", "explicit-tvd"])
-def test_parity_paper_channel_4032x200(implicit, tvd):
-    # the paper's own mesh (Section 4): 4032 x 200 cells of 0.05 a, Kn 0.001, M 2.43
-    case = W.paper_channel(ny=200, implicit=implicit, tvd=tvd)
+def test_parity_paper_channel(implicit, tvd, ny):
+    # the paper's own meshes (Section 4): 4032 x 200 and 4032 x 400 cells of
+    # 0.05 a with one particle per 10 a of height, Kn 0.001, M 2.43
+    case = W.paper_channel(ny=ny, implicit=implicit, tvd=tvd)
     g, o, *_ = run_both(case, 3)
     assert_parity(g, o)
 

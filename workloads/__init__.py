@@ -156,19 +156,26 @@ def c5_batch(n: int = 64, precision: int = MIXED) -> List[Case]:
 
 def paper_channel(ny: int = 200, nx: int = 4032, kn: float = 0.001, mach: float = 2.43,
                   side: int = 20, inlet: int = 110, implicit: bool = True, tvd: bool = False,
-                  seed: int = 9) -> Case:
-    """The paper's test case (Section 4): a square particle of side a in a
-    microchannel, seen from the particle, so the gas enters at Mach 2.43 and the
-    channel walls move with the inflow speed; hard-sphere gas at Kn = 0.001
+                  seed: int = 9, n_squares: Optional[int] = None) -> Case:
+    """The paper's test case (Section 4): square particles of side a in a
+    microchannel, seen from the particles, so the gas enters at Mach 2.43 and
+    the channel walls move with the inflow speed; hard-sphere gas at Kn = 0.001
     (Eqs. pl35-pl37) with velocity-slip and temperature-jump walls (Eqs. pl38,
     pl39: zeta = 1.1466 Kn / rho, tau = 2.1904 Kn / rho).  Uniform cells of
     0.05 a (side = 20 cells); channel length 201.6 a (4032 cells), inlet length
-    5.5 a (110 cells); the paper's heights are 10 to 200 a (200 to 4000 cells)."""
+    5.5 a (110 cells); the paper's heights are 10, 20, 100 and 200 a (200 to
+    4000 cells) with 1, 2, 10 and 20 particles, i.e. one per 10 a of height
+    (n_squares None); each sits at the centre of its 10 a band, all at the same
+    distance from the inlet."""
     u_in = mach * math.sqrt((5.0 / 3.0) / 2.0)
-    j0 = ny // 2 - side // 2
+    n = max(1, ny // (10 * side)) if n_squares is None else n_squares
+    rects = []
+    for k in range(n):
+        j0 = int(math.floor((k + 0.5) * ny / n - side / 2.0 + 0.5))
+        rects.append([inlet, j0, inlet + side, j0 + side])
     return Case(name=f"paper_{nx}x{ny}", nx=nx, ny=ny, lx=nx / side, ly=ny / side,
                 side_kind=(INFLOW, OUTFLOW, WALL, WALL), side_vel=(0.0, 0.0, u_in, u_in),
-                rects=[[inlet, j0, inlet + side, j0 + side]],
+                rects=rects,
                 gas_model=GAS_HARD_SPHERE_KN, kn=kn, mach_in=mach,
                 zeta_coef=1.1466 * kn, tau_coef=2.1904 * kn,
                 implicit=implicit, tvd=tvd, seed=seed, steps=1000)
