@@ -256,9 +256,9 @@ sim_status sim_batch_tune(sim_batch_t batch, int scheme, int out[3]);
 
 /* Set the work distribution of the batched kernels explicitly: tiles of
  * tile_x x tile_y threads (tile_x one of 16, 32, 64, 128, 256 and
- * tile_x * tile_y = 256) walked by `ctas` CTAs (0: one CTA per tile).  Every
- * distribution gives the same bits.  Synchronous.  Errors: SIM_EINVAL (null
- * batch, another shape, ctas < 0), SIM_ECUDA. */
+ * tile_x * tile_y one of 32, 64, 128, 256) walked by `ctas` CTAs (0: one CTA
+ * per tile).  Every distribution gives the same bits.  Synchronous.
+ * Errors: SIM_EINVAL (null batch, another shape, ctas < 0), SIM_ECUDA. */
 sim_status sim_batch_set_tiles(sim_batch_t batch, int tile_x, int tile_y, int ctas);
 
 /* Text of the last error on this batch (never NULL). */

@@ -1401,9 +1401,12 @@ extern "C" sim_status sim_batch_tune(sim_batch_t b, int scheme, int out[3])
 extern "C" sim_status sim_batch_set_tiles(sim_batch_t b, int tx, int ty, int ctas)
 {
     if (!b) return SIM_EINVAL;
-    const bool shape = (tx == 16 || tx == 32 || tx == 64 || tx == 128 || tx == 256) && tx * ty == 256;
+    const int threads = tx * ty;
+    const bool shape = (tx == 16 || tx == 32 || tx == 64 || tx == 128 || tx == 256) && ty >= 1 &&
+                       (threads == 32 || threads == 64 || threads == 128 || threads == 256);
     if (!shape || ctas < 0)
-        return bfail(b, SIM_EINVAL, "tile %d x %d with %d CTAs: want 256 threads, tile x in {16, ..., 256}, CTAs >= 0",
+        return bfail(b, SIM_EINVAL,
+                     "tile %d x %d with %d CTAs: want 32, 64, 128 or 256 threads, tile x in {16, ..., 256}, CTAs >= 0",
                      tx, ty, ctas);
     BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
     return plan_tiles(b, tx, ty, ctas);

@@ -76,7 +76,8 @@ def test_tuning_keeps_the_state_and_the_results():
                 assert np.array_equal(fa[k], fb[k]), (q, k)
 
 
-@pytest.mark.parametrize("shape", [(16, 16, 0), (64, 4, 0), (128, 2, 304), (256, 1, 0), (32, 8, 152)])
+@pytest.mark.parametrize("shape", [(16, 16, 0), (64, 4, 0), (128, 2, 304), (256, 1, 0), (32, 8, 152), (32, 2, 0),
+                                   (32, 1, 0), (16, 4, 0)])
 def test_every_tile_shape_gives_the_same_bits(shape):
     # sim_batch_set_tiles: any distribution of the positions over threads and
     # CTAs gives the bits of the default one (32 x 8, one CTA per tile)
@@ -93,7 +94,7 @@ def test_every_tile_shape_gives_the_same_bits(shape):
 
 def test_set_tiles_rejects_other_shapes():
     with sim.Batch(small_batch(n=1)) as b:
-        for bad in [(32, 4, 0), (8, 32, 0), (512, 1, 0), (32, 8, -1)]:
+        for bad in [(32, 3, 0), (8, 32, 0), (512, 1, 0), (32, 8, -1), (64, 8, 0)]:
             with pytest.raises(sim.SimError) as e:
                 b.set_tiles(*bad)
             assert e.value.status == sim.SIM_EINVAL
