@@ -85,6 +85,8 @@ def _load():
         lib.orc_psi_c.restype = ctypes.c_double
         lib.orc_splitmix_uniform.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.orc_splitmix_uniform.restype = ctypes.c_double
+        lib.orc_gam_harmonic.argtypes = [ctypes.c_double] * 4
+        lib.orc_gam_harmonic.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -191,6 +193,10 @@ def psi_s(f1, f2, f3, f4, d1, d2, d3, d4, vel) -> float:
 
 def psi_c(f1, f2, f3, f4, d1, d2, d3, vel) -> float:
     return _load().orc_psi_c(f1, f2, f3, f4, d1, d2, d3, vel)
+
+
+def gam_harmonic(ga: float, gb: float, da: float, db: float) -> float:
+    return _load().orc_gam_harmonic(ga, gb, da, db)
 
 
 def splitmix_uniform(seed: int, field: int, i: int, j: int) -> float:

@@ -669,8 +669,8 @@ static double gam_corner(const orc *o, const level *L, int i, int j)
 }
 
 /* Harmonic mean of Gamma^lambda at the face between cells a (size da) and b
- * (size db), Eq. pl33. */
-static double gam_harmonic(double ga, double gb, double da, double db)
+ * (size db), Eq. pl33 (exported for the closed-form check). */
+double orc_gam_harmonic(double ga, double gb, double da, double db)
 {
     return (da + db) * ga * gb / (da * gb + db * ga);
 }
@@ -881,10 +881,10 @@ static double temperature(const orc *o, const level *prev, const level *old, int
     double Fw = o->Fx[FU(o, i, j)], Fe = o->Fx[FU(o, i + 1, j)];
     double Fs = o->Fy[FV(o, i, j)], Fn = o->Fy[FV(o, i, j + 1)];
     double gp = GAMc(o, old, i, j);
-    double gw = gam_harmonic(GAMc(o, old, i - 1, j), gp, DX(o, i - 1), dxi);
-    double ge = gam_harmonic(gp, GAMc(o, old, i + 1, j), dxi, DX(o, i + 1));
-    double gs = gam_harmonic(GAMc(o, old, i, j - 1), gp, DY(o, j - 1), dyj);
-    double gn = gam_harmonic(gp, GAMc(o, old, i, j + 1), dyj, DY(o, j + 1));
+    double gw = orc_gam_harmonic(GAMc(o, old, i - 1, j), gp, DX(o, i - 1), dxi);
+    double ge = orc_gam_harmonic(gp, GAMc(o, old, i + 1, j), dxi, DX(o, i + 1));
+    double gs = orc_gam_harmonic(GAMc(o, old, i, j - 1), gp, DY(o, j - 1), dyj);
+    double gn = orc_gam_harmonic(gp, GAMc(o, old, i, j + 1), dyj, DY(o, j + 1));
     double Dw = k->CT1f * gw * dyj / (0.5 * (dxi + DX(o, i - 1)));
     double De = k->CT1f * ge * dyj / (0.5 * (DX(o, i + 1) + dxi));
     double Ds = k->CT1f * gs * dxi / (0.5 * (dyj + DY(o, j - 1)));

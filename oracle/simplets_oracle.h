@@ -77,6 +77,7 @@ double orc_psi_s(double f1, double f2, double f3, double f4,
 double orc_psi_c(double f1, double f2, double f3, double f4,
                  double d1, double d2, double d3, double vel);
 double orc_splitmix_uniform(uint64_t seed, int field, int i, int j);
+double orc_gam_harmonic(double ga, double gb, double da, double db);
 
 #ifdef __cplusplus
 }

@@ -41,6 +41,8 @@ MUTANTS = {
     "u_tvd_south_velocity": (
         "ps1 = orc_psi_s(f1, uS, uP, uN, DY(o, j - 2), DY(o, j - 1), dyj, DY(o, j + 1), Vc(o, old, i - 1, j));",
         "ps1 = orc_psi_s(f1, uS, uP, uN, DY(o, j - 2), DY(o, j - 1), dyj, DY(o, j + 1), Vc(o, old, i, j));"),
+    "harmonic_mean_weights": ("return (da + db) * ga * gb / (da * gb + db * ga);",
+                              "return (da + db) * ga * gb / (da * ga + db * gb);"),
     "corner_gamma_weights": ("double wxm = DX(o, i) / (DX(o, i - 1) + DX(o, i));",
                              "double wxm = DX(o, i - 1) / (DX(o, i - 1) + DX(o, i));"),
     "dv_uses_dy": ("*dv = k->A * dxi / a0;", "*dv = k->A * dyp / a0;"),

@@ -443,6 +443,24 @@ def _steady_conduction(ny, ratio=4.0, omega=2.0, t_top=3.0):
     return np.abs(s["T"][:, 1] - exact).max(), res.max()
 
 
+def test_face_conductance_is_two_half_cells_in_series():
+    # Eq. pl32 divides the face value of Gamma (Eq. pl33) by the centre
+    # distance 0.5 (da + db).  Between two cells of sizes da, db and
+    # conductivities ga, gb that must be the conductance of the two half-cells
+    # in series, 1 / (da / (2 ga) + db / (2 gb)), which fixes which size
+    # weights which Gamma in the harmonic mean.
+    rng = np.random.default_rng(3)
+    for _ in range(2000):
+        ga, gb = 10.0 ** rng.uniform(-2, 2, 2)
+        da, db = 10.0 ** rng.uniform(-2, 1, 2)
+        got = oracle.gam_harmonic(ga, gb, da, db) / (0.5 * (da + db))
+        want = 1.0 / (da / (2.0 * ga) + db / (2.0 * gb))
+        assert got == pytest.approx(want, rel=1e-13)
+    # equal sizes: the plain harmonic mean; equal conductivities: that value
+    assert oracle.gam_harmonic(2.0, 6.0, 0.3, 0.3) == pytest.approx(3.0, rel=1e-15)
+    assert oracle.gam_harmonic(1.7, 1.7, 0.1, 0.9) == pytest.approx(1.7, rel=1e-15)
+
+
 def test_steady_conduction_converges_to_kirchhoff_solution():
     # Gas at rest between walls at T = 1 and 3, Gamma^lambda = T^2, and a grid
     # whose spacing jumps by 4x at mid height.
