@@ -549,7 +549,9 @@ int enqueue_iteration(sim_t s, int prev, int old, bool implicit, bool tvd, bool 
     int nw = (old + 1) % 3;
     if (nw == prev) nw = (nw + 1) % 3;
     const int ng = ghost_kernels(s->sides, true);
-    cudaMemsetAsync(s->work.res, 0, 4 * sizeof(unsigned long long), st);
+    // residual words to 0 with a kernel rather than a memset: inside the step
+    // graph a memset node between two kernels delays the next kernel's launch
+    { Launch l(s, SIM_K_GHOSTS, st, counts); launch_zero_res(s->plan, st); }
     const int prec = prec_of(s);
     if (!faces_ready) { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, prec, old, tvd, implicit, st); }
     { Launch l(s, SIM_K_ASSEMBLE, st, counts); launch_assemble(s->plan, prec, prev, old, nw, implicit, tvd, st); }
