@@ -200,8 +200,7 @@ sim_status sim_residuals(sim_t sim, double out[4], int *iters_last_step);
  * C^T3_f, omega, U_in, dt, cells.  Errors: SIM_EINVAL. */
 sim_status sim_coefficients(sim_t sim, double out[9]);
 
-/* Kernel classes of the sweep, for sim_profile_read (SIM_K_GHOSTS: the
- * ghost copies of symmetry sides and the reset of the residual words). */
+/* Kernel classes of the sweep, for sim_profile_read. */
 enum { SIM_K_FACES = 0, SIM_K_ASSEMBLE = 1, SIM_K_PRESSURE = 2, SIM_K_VELOCITY = 3, SIM_K_GHOSTS = 4,
        SIM_K_EXPLICIT = 5, SIM_K_COUNT = 6 };
 

@@ -469,7 +469,6 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
         for (int it = 0; it < bc->iters; it++) {
             int nw = (old + 1) % 3;
             if (nw == prev) nw = (nw + 1) % 3;
-            launch_zero_res(plan, s);
             if (implicit || it > 0)     // an explicit step's first iteration reuses the faces of n-1
                 launch_faces(plan, PREC_FP64, old, tvd, implicit, s);
             launch_assemble(plan, PREC_FP64, prev, old, nw, implicit, tvd, s);

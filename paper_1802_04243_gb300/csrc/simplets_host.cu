@@ -549,9 +549,6 @@ int enqueue_iteration(sim_t s, int prev, int old, bool implicit, bool tvd, bool 
     int nw = (old + 1) % 3;
     if (nw == prev) nw = (nw + 1) % 3;
     const int ng = ghost_kernels(s->sides, true);
-    // residual words to 0 with a kernel rather than a memset: inside the step
-    // graph a memset node between two kernels delays the next kernel's launch
-    { Launch l(s, SIM_K_GHOSTS, st, counts); launch_zero_res(s->plan, st); }
     const int prec = prec_of(s);
     if (!faces_ready) { Launch l(s, SIM_K_FACES, st, counts); launch_faces(s->plan, prec, old, tvd, implicit, st); }
     { Launch l(s, SIM_K_ASSEMBLE, st, counts); launch_assemble(s->plan, prec, prev, old, nw, implicit, tvd, st); }
@@ -1189,7 +1186,6 @@ int enqueue_batch_step(sim_batch_t b, int prev, bool implicit, bool tvd, cudaStr
     for (int it = 1; it <= b->iters; it++) {
         int nw = (old + 1) % 3;
         if (nw == prev) nw = (nw + 1) % 3;
-        launch_zero_res(bp, st);
         if (implicit || it > 1)         // an explicit step's first iteration reuses the faces of n-1
             launch_faces(bp, b->prec, old, tvd, implicit, st);
         launch_assemble(bp, b->prec, prev, old, nw, implicit, tvd, st);

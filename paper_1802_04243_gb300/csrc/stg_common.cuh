@@ -186,7 +186,8 @@ enum { BC_WALL = 0, BC_SYMMETRY = 1, BC_INFLOW = 2, BC_OUTFLOW = 3 };
 // batch).  `prec` (PREC_*) selects the arithmetic: FP64; the FP32 assembly
 // of the mixed-precision path; double-float.  Levels are indices into
 // Inst::lv / lv32 / lvdf.
-void launch_zero_res(const BatchPlan &bp, void *stream);
+// The face kernel also resets the residual words of every problem of the
+// list (its first CTA), since it opens every loop-2 iteration.
 // limiters: also store the TVD limiters of the level (tvd only; the kernels
 // that read them are the implicit-TVD assembly and the explicit terms).
 void launch_faces(const BatchPlan &bp, int prec, int level, bool tvd, bool limiters, void *stream);

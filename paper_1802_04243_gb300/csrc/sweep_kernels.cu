@@ -1092,15 +1092,23 @@ __device__ __forceinline__ void for_tiles(const BatchPlan &bp, F &&f)
     }
 }
 
-__global__ void k_zero_res(BatchPlan bp)
+// The residual words of every problem of the list to 0.  The face kernel
+// does this in its first CTA: it runs at the start of every loop-2 iteration
+// (for the first iteration of an explicit step, as part of the explicit
+// terms), before the pressure and velocity kernels accumulate the maxima, and
+// after the previous iteration's velocity kernel has finished.  (A separate
+// memset or kernel for it costs a node of the step graph.)
+__device__ __forceinline__ void reset_residuals(const BatchPlan &bp)
 {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < bp.n_inst * 4) bp.inst[q >> 2].w.res[q & 3] = 0ull;
+    if (blockIdx.x != 0) return;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+    for (int q = tid; q < bp.n_inst * 4; q += nthr) bp.inst[q >> 2].w.res[q & 3] = 0ull;
 }
 
 template <int PREC, bool TVD>
 __global__ void __launch_bounds__(256) k_faces(const __grid_constant__ BatchPlan bp, int level, int limiters)
 {
+    reset_residuals(bp);
     for_tiles(bp, [&](const Inst &I, int i, int j) {
         if constexpr (PREC == PREC_MIXED) {
             const LevelT<float> &L = I.lv32[level];
@@ -1452,11 +1460,6 @@ void launch_scatter(const Geo &g, int field, const double *src, const Level &lv,
 void launch_gather(const Geo &g, int field, const Level &lv, double *dst, void *stream)
 {
     k_gather<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, field, lv, dst);
-}
-
-void launch_zero_res(const BatchPlan &bp, void *stream)
-{
-    k_zero_res<<<(bp.n_inst * 4 + 127) / 128, 128, 0, (cudaStream_t)stream>>>(bp);
 }
 
 void launch_faces(const BatchPlan &bp, int prec, int level, bool tvd, bool limiters, void *stream)
