@@ -50,6 +50,20 @@ __device__ __forceinline__ bool positive(double x) { return __double_as_longlong
 __device__ __forceinline__ bool positive(float x) { return __float_as_int(x) > 0; }
 __device__ __forceinline__ bool positive(df64 x) { return x.hi > 0.0f; }    // normalised: lo is 0 when hi is
 
+// x < 0, the same test as positive(-x) without forming -x (-0 is not below
+// zero): sign bit set and a nonzero rest.
+__device__ __forceinline__ bool below_zero(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) != 0 && (b << 1) != 0;
+}
+__device__ __forceinline__ bool below_zero(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    return (b >> 31) != 0 && (b << 1) != 0;
+}
+__device__ __forceinline__ bool below_zero(df64 x) { return positive(-x); }
+
 // ---------------------------------------------------------------- limiter
 
 __device__ __forceinline__ float recip(float a);
@@ -62,7 +76,7 @@ __device__ __forceinline__ double recip(double a);
 template <typename R>
 __device__ __forceinline__ R van_leer(R num, R den)
 {
-    const bool same = (positive(num) && positive(den)) || (positive(-num) && positive(-den));
+    const bool same = (positive(num) && positive(den)) || (below_zero(num) && below_zero(den));
     return same ? R(2) * num * recip(num + den) : R(0);
 }
 
@@ -99,6 +113,20 @@ template <typename R>
 __device__ __forceinline__ R upwind(R a, R b, R vel) { return positive(vel) ? a : b; }
 template <typename R>
 __device__ __forceinline__ R pos(R x) { return positive(x) ? x : R(0); }
+
+// max(0, -x), the same bits as pos(-x): the sign test reads the sign bit and
+// the FP64 negation flips it on the integer pipe.
+__device__ __forceinline__ bool negative(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool negative(float x) { return __float_as_int(x) < 0; }
+__device__ __forceinline__ bool negative(df64 x) { return positive(-x); }
+__device__ __forceinline__ double flip_sign(double x)
+{
+    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000u, __double2loint(x));
+}
+__device__ __forceinline__ float flip_sign(float x) { return -x; }
+__device__ __forceinline__ df64 flip_sign(df64 x) { return -x; }
+template <typename R>
+__device__ __forceinline__ R neg_part(R x) { return negative(x) ? flip_sign(x) : R(0); }
 
 // Value of node m seen from node a: reflected about the stored wall value when
 // the flag of m carries `wall_bit`.
@@ -558,14 +586,14 @@ __device__ R temperature(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
         }
         if constexpr (TVD) {
             a1 = pos(Fw) - Fw * pw + Dw;
-            a2 = pos(-Fe) - Fe * pe + De;
+            a2 = neg_part(Fe) - Fe * pe + De;
             a3 = pos(Fs) - Fs * ps + Ds;
-            a4 = pos(-Fn) - Fn * pn + Dn;
+            a4 = neg_part(Fn) - Fn * pn + Dn;
         } else {                                   // upwind: psi = 0
             a1 = pos(Fw) + Dw;
-            a2 = pos(-Fe) + De;
+            a2 = neg_part(Fe) + De;
             a3 = pos(Fs) + Ds;
-            a4 = pos(-Fn) + Dn;
+            a4 = neg_part(Fn) + Dn;
         }
         a0 = k.dt * (a1 + a2 + a3 + a4 + Fe - Fw + Fn - Fs) + old.rho[c] * vol;
         texp = R(0);
@@ -627,14 +655,14 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
         }
         if constexpr (TVD) {
             a1 = pos(Fbw) - Fbw * pw + R(4.0 / 3.0) * Dxw;
-            a2 = pos(-Fbe) - Fbe * pe + R(4.0 / 3.0) * Dxe;
+            a2 = neg_part(Fbe) - Fbe * pe + R(4.0 / 3.0) * Dxe;
             a3 = R(0.5) * (pos(Fs1) - Fs1 * ps1 + pos(Fs2) - Fs2 * ps2) + Dys;
-            a4 = R(0.5) * (pos(-Fn1) - Fn1 * pn1 + pos(-Fn2) - Fn2 * pn2) + Dyn;
+            a4 = R(0.5) * (neg_part(Fn1) - Fn1 * pn1 + neg_part(Fn2) - Fn2 * pn2) + Dyn;
         } else {                                   // upwind: psi = 0
             a1 = pos(Fbw) + R(4.0 / 3.0) * Dxw;
-            a2 = pos(-Fbe) + R(4.0 / 3.0) * Dxe;
+            a2 = neg_part(Fbe) + R(4.0 / 3.0) * Dxe;
             a3 = R(0.5) * (pos(Fs1) + pos(Fs2)) + Dys;
-            a4 = R(0.5) * (pos(-Fn1) + pos(-Fn2)) + Dyn;
+            a4 = R(0.5) * (neg_part(Fn1) + neg_part(Fn2)) + Dyn;
         }
         a0 = a1 + a2 + a3 + a4 + R(0.5) * (Fn2 - Fs2 + Fn1 - Fs1) + Fbe - Fbw + trans;
         uexp = R(0);
@@ -694,14 +722,14 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
         }
         if constexpr (TVD) {
             a1 = R(0.5) * (pos(Fw2) - Fw2 * pw2 + pos(Fw1) - Fw1 * pw1) + Dxw;
-            a2 = R(0.5) * (pos(-Fe2) - Fe2 * pe2 + pos(-Fe1) - Fe1 * pe1) + Dxe;
+            a2 = R(0.5) * (neg_part(Fe2) - Fe2 * pe2 + neg_part(Fe1) - Fe1 * pe1) + Dxe;
             a3 = pos(Fbs) - Fbs * ps + R(4.0 / 3.0) * Dys;
-            a4 = pos(-Fbn) - Fbn * pn + R(4.0 / 3.0) * Dyn;
+            a4 = neg_part(Fbn) - Fbn * pn + R(4.0 / 3.0) * Dyn;
         } else {                                   // upwind: psi = 0
             a1 = R(0.5) * (pos(Fw2) + pos(Fw1)) + Dxw;
-            a2 = R(0.5) * (pos(-Fe2) + pos(-Fe1)) + Dxe;
+            a2 = R(0.5) * (neg_part(Fe2) + neg_part(Fe1)) + Dxe;
             a3 = pos(Fbs) + R(4.0 / 3.0) * Dys;
-            a4 = pos(-Fbn) + R(4.0 / 3.0) * Dyn;
+            a4 = neg_part(Fbn) + R(4.0 / 3.0) * Dyn;
         }
         a0 = a1 + a2 + a3 + a4 + R(0.5) * (Fe2 - Fw2 + Fe1 - Fw1) + Fbn - Fbs + trans;
         vexp = R(0);
