@@ -64,6 +64,11 @@ __device__ __forceinline__ bool below_zero(float x)
 }
 __device__ __forceinline__ bool below_zero(df64 x) { return positive(-x); }
 
+// x != 0 (either sign of zero counts as zero), from the bits.
+__device__ __forceinline__ bool nonzero(double x) { return ((unsigned long long)__double_as_longlong(x) << 1) != 0; }
+__device__ __forceinline__ bool nonzero(float x) { return (__float_as_uint(x) << 1) != 0; }
+__device__ __forceinline__ bool nonzero(df64 x) { return x.hi != 0.0f; }
+
 // ---------------------------------------------------------------- limiter
 
 __device__ __forceinline__ float recip(float a);
@@ -177,13 +182,8 @@ __device__ __forceinline__ R gamma_corner(const GeoT<R> &g, const R *gam, int c,
 
 // ------------------------------------------------------ residual reduction
 
-__device__ __forceinline__ unsigned long long ordered(double x)
-{
-    // |x| as an unsigned integer: ordered like the value, NaN above infinity
-    return (unsigned long long)__double_as_longlong(fabs(x));
-}
-
-// Ordered key of |x| for an FP64 value held as bits (integer pipe only).
+// Ordered key of |x|: the bits of an FP64 value without its sign, ordered like
+// |x| as unsigned integers, NaN above infinity (integer pipe only).
 __device__ __forceinline__ unsigned long long ordered_bits(double x)
 {
     return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
@@ -276,7 +276,7 @@ __device__ __forceinline__ double recip(double a)
 
 // Residual key |d| of a difference held in the compute precision (a
 // double-float difference is keyed by its leading float).
-__device__ __forceinline__ unsigned long long res_key(double d) { return ordered(d); }
+__device__ __forceinline__ unsigned long long res_key(double d) { return ordered_bits(d); }
 __device__ __forceinline__ unsigned long long res_key(df64 d) { return ordered_bits(widen(d.hi)); }
 
 // Gamma = T^omega (power-law transport coefficients): the square root for
@@ -640,7 +640,7 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     R b = (prev.rho[a] * dxp + prev.rho[a - 1] * dxw) * vdt * prev.u[a]
                + (gcn * (vn2 - vn1) - gcs * (vs2 - vs1))
                + B23 * (gam[a - 1] * (vn1 - vs1) - gam[a] * (vn2 - vs2));
-    if (positive(k.gx) || positive(-k.gx))       // body force (uniform branch: zero in most flows)
+    if (nonzero(k.gx))                           // body force (uniform branch: zero in most flows)
         b += k.gx * mass * dyj * R(0.5);
     R a1, a2, a3, a4, a0, uexp;
     if (IMPL) {
@@ -707,7 +707,7 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     R bsrc = (prev.rho[b] * dyp + prev.rho[b - P] * dys) * vdt * prev.v[b]
                   + (gce * (ue2 - ue1) - gcw * (uw2 - uw1))
                   + B23 * (gam[b - P] * (ue1 - uw1) - gam[b] * (ue2 - uw2));
-    if (positive(k.gy) || positive(-k.gy))       // body force (uniform branch: zero in most flows)
+    if (nonzero(k.gy))                           // body force (uniform branch: zero in most flows)
         bsrc += k.gy * mass * dxi * R(0.5);
     R a1, a2, a3, a4, a0, vexp;
     if (IMPL) {
