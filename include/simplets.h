@@ -133,6 +133,8 @@ typedef struct {
 
 /* Validate the problem, allocate every device buffer and set the start state.
  * stream: a cudaStream_t (may be NULL).  On success *out owns the handle.
+ * Grids: 4 <= nx, ny < 2^20 and at most 2^31 - 1 elements in the padded grid
+ * ((nx + 5) rounded up to a multiple of 8, times ny + 5).
  * Errors: SIM_EINVAL (bad description), SIM_ENOMEM, SIM_ECUDA. */
 sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const sim_bc *bc,
                       void *stream, sim_t *out);

@@ -167,6 +167,11 @@ sim_status read_problem(const sim_grid *gr, const sim_gas *gas, const sim_bc *bc
         return fail(err, SIM_EINVAL, "null description");
     if (gr->nx < 4 || gr->ny < 4 || gr->nx >= (1 << 20) || gr->ny >= (1 << 20))
         return fail(err, SIM_EINVAL, "grid %d x %d outside [4, 2^20)", gr->nx, gr->ny);
+    // the kernels index the padded grid with 32-bit integers
+    const long long padded = ((long long)(gr->nx + 2 * G + 1) + 7) / 8 * 8 * (gr->ny + 2 * G + 1);
+    if (padded > 0x7FFFFFFFLL)
+        return fail(err, SIM_EINVAL, "grid %d x %d: %lld padded elements exceed 32-bit indexing", gr->nx, gr->ny,
+                    padded);
     pb.nx = gr->nx;
     pb.ny = gr->ny;
     pb.dx.resize(pb.nx);

@@ -56,6 +56,7 @@ def _create(case):
 @pytest.mark.parametrize("bad", [
     dict(nx=3),
     dict(ny=2),
+    dict(nx=60000, ny=60000),                # padded grid beyond 32-bit indexing
     dict(rects=[[1, 10, 9, 18]]),            # touches the inflow ghost band
     dict(rects=[[30, 10, 31, 20]]),          # one cell wide
     dict(rects=[[30, 10, 40, 31]]),          # reaches the north wall
