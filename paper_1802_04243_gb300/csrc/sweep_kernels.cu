@@ -69,6 +69,20 @@ __device__ __forceinline__ bool nonzero(double x) { return ((unsigned long long)
 __device__ __forceinline__ bool nonzero(float x) { return (__float_as_uint(x) << 1) != 0; }
 __device__ __forceinline__ bool nonzero(df64 x) { return x.hi != 0.0f; }
 
+// max(0, -x), the same bits as pos(-x): the sign test reads the sign bit and
+// the FP64 negation flips it on the integer pipe.
+__device__ __forceinline__ bool negative(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool negative(float x) { return __float_as_int(x) < 0; }
+__device__ __forceinline__ bool negative(df64 x) { return positive(-x); }
+__device__ __forceinline__ double flip_sign(double x)
+{
+    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000u, __double2loint(x));
+}
+__device__ __forceinline__ float flip_sign(float x) { return -x; }
+__device__ __forceinline__ df64 flip_sign(df64 x) { return -x; }
+template <typename R>
+__device__ __forceinline__ R neg_part(R x) { return negative(x) ? flip_sign(x) : R(0); }
+
 // ---------------------------------------------------------------- limiter
 
 __device__ __forceinline__ float recip(float a);
@@ -86,32 +100,45 @@ __device__ __forceinline__ R van_leer(R num, R den)
 }
 
 // Eq. pl15_2: correction at the face between nodes 2 and 3 for flow towards
-// node 3 (up) and towards node 2 (dn); d1..d4 are the sizes of the four
-// nodes, w2 = d2/(d2 + d3) and w3 = d3/(d2 + d3) the weights of the face,
-// taken from the axis tables.
+// node 3 (up) and towards node 2 (dn), with d1..d4 the sizes of the four
+// nodes: psi = w2 VanLeer((d2 + d3)(f2 - f1), (d1 + d2)(f3 - f2)) and its
+// mirror, w2 = d2/(d2 + d3), w3 = d3/(d2 + d3).  Van Leer's quotient is
+// unchanged when both arguments are halved, so the sums of two sizes enter
+// as the centre distances c12 = (d1 + d2)/2, c23, c34 of the axis tables
+// (the same bits: halving is exact).
 template <typename R>
-__device__ __forceinline__ R psi_s_up(R f1, R f2, R f3, R d1, R d2, R d3, R w2)
+__device__ __forceinline__ R psi_s_up(R f1, R f2, R f3, R c12, R c23, R w2)
 {
-    return w2 * van_leer((d2 + d3) * (f2 - f1), (d1 + d2) * (f3 - f2));
+    return w2 * van_leer(c23 * (f2 - f1), c12 * (f3 - f2));
 }
 template <typename R>
-__device__ __forceinline__ R psi_s_dn(R f2, R f3, R f4, R d2, R d3, R d4, R w3)
+__device__ __forceinline__ R psi_s_dn(R f2, R f3, R f4, R c23, R c34, R w3)
 {
-    return -(w3 * van_leer((d2 + d3) * (f4 - f3), (d3 + d4) * (f3 - f2)));
+    return -(w3 * van_leer(c23 * (f4 - f3), c34 * (f3 - f2)));
 }
 template <typename R>
-__device__ __forceinline__ R psi_surface(R f1, R f2, R f3, R f4, R d1, R d2, R d3, R d4, R w2, R w3, R vel)
+__device__ __forceinline__ R psi_surface(R f1, R f2, R f3, R f4, R c12, R c23, R c34, R w2, R w3, R vel)
 {
-    return positive(vel) ? psi_s_up(f1, f2, f3, d1, d2, d3, w2) : psi_s_dn(f2, f3, f4, d2, d3, d4, w3);
+    return positive(vel) ? psi_s_up(f1, f2, f3, c12, c23, w2) : psi_s_dn(f2, f3, f4, c23, c34, w3);
 }
 
-// Eq. pl15_1: face midway between nodes 2 and 3; d1..d3 the node distances.
+// Half of Van Leer's psi, num/(num + den) under the same sign test: the same
+// bits as 0.5 van_leer(num, den), since scaling by 2 and by 1/2 is exact.
+template <typename R>
+__device__ __forceinline__ R van_leer_half(R num, R den)
+{
+    const bool same = (positive(num) && positive(den)) || (below_zero(num) && below_zero(den));
+    return same ? num * recip(num + den) : R(0);
+}
+
+// Eq. pl15_1: face midway between nodes 2 and 3; d1..d3 the node distances;
+// psi = +-0.5 VanLeer(...).
 template <typename R>
 __device__ __forceinline__ R psi_centre(R f1, R f2, R f3, R f4, R d1, R d2, R d3, R vel)
 {
     if (positive(vel))
-        return R(0.5) * van_leer(d2 * (f2 - f1), d1 * (f3 - f2));
-    return R(-0.5) * van_leer(d2 * (f4 - f3), d3 * (f3 - f2));
+        return van_leer_half(d2 * (f2 - f1), d1 * (f3 - f2));
+    return flip_sign(van_leer_half(d2 * (f4 - f3), d3 * (f3 - f2)));
 }
 
 template <typename R>
@@ -119,19 +146,6 @@ __device__ __forceinline__ R upwind(R a, R b, R vel) { return positive(vel) ? a 
 template <typename R>
 __device__ __forceinline__ R pos(R x) { return positive(x) ? x : R(0); }
 
-// max(0, -x), the same bits as pos(-x): the sign test reads the sign bit and
-// the FP64 negation flips it on the integer pipe.
-__device__ __forceinline__ bool negative(double x) { return __double_as_longlong(x) < 0; }
-__device__ __forceinline__ bool negative(float x) { return __float_as_int(x) < 0; }
-__device__ __forceinline__ bool negative(df64 x) { return positive(-x); }
-__device__ __forceinline__ double flip_sign(double x)
-{
-    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000u, __double2loint(x));
-}
-__device__ __forceinline__ float flip_sign(float x) { return -x; }
-__device__ __forceinline__ df64 flip_sign(df64 x) { return -x; }
-template <typename R>
-__device__ __forceinline__ R neg_part(R x) { return negative(x) ? flip_sign(x) : R(0); }
 
 // Value of node m seen from node a: reflected about the stored wall value when
 // the flag of m carries `wall_bit`.
@@ -311,11 +325,11 @@ __device__ __forceinline__ void face_limiters(const GeoT<R> &g, const R *__restr
     const uint16_t f = g.flag[c];
     const R zero = R(0);
     // T on the x face i and the y face j (Eq. pl15_2)
-    w.psTx[c] = (f & F_TCX) ? psi_surface(T[c - 2], T[c - 1], T[c], T[c + 1], at(g.x.d, i - 2), at(g.x.d, i - 1),
-                                          at(g.x.d, i), at(g.x.d, i + 1), at(g.x.whi, i), at(g.x.wlo, i), u[c])
+    w.psTx[c] = (f & F_TCX) ? psi_surface(T[c - 2], T[c - 1], T[c], T[c + 1], at(g.x.dc, i - 1), at(g.x.dc, i),
+                                          at(g.x.dc, i + 1), at(g.x.whi, i), at(g.x.wlo, i), u[c])
                             : zero;
-    w.psTy[c] = (f & F_TCY) ? psi_surface(T[c - 2 * P], T[c - P], T[c], T[c + P], at(g.y.d, j - 2), at(g.y.d, j - 1),
-                                          at(g.y.d, j), at(g.y.d, j + 1), at(g.y.whi, j), at(g.y.wlo, j), v[c])
+    w.psTy[c] = (f & F_TCY) ? psi_surface(T[c - 2 * P], T[c - P], T[c], T[c + P], at(g.y.dc, j - 1), at(g.y.dc, j),
+                                          at(g.y.dc, j + 1), at(g.y.whi, j), at(g.y.wlo, j), v[c])
                             : zero;
     // u node (i,j): x face of its control volume at the centre of cell i-1
     // (Eq. pl15_1, velocity the mean of the two u nodes), and the y face
@@ -327,11 +341,11 @@ __device__ __forceinline__ void face_limiters(const GeoT<R> &g, const R *__restr
     // v(i-1,j) and v(i,j), points its way)
     {
         const bool t = (f & F_TUY) != 0, p0 = positive(v[c - 1]), p1 = positive(v[c]);
-        w.psUyU[c] = (t && (p0 || p1)) ? psi_s_up(u[c - 2 * P], u[c - P], u[c], at(g.y.d, j - 2), at(g.y.d, j - 1),
-                                                  at(g.y.d, j), at(g.y.whi, j))
+        w.psUyU[c] = (t && (p0 || p1)) ? psi_s_up(u[c - 2 * P], u[c - P], u[c], at(g.y.dc, j - 1), at(g.y.dc, j),
+                                                  at(g.y.whi, j))
                                        : zero;
-        w.psUyD[c] = (t && !(p0 && p1)) ? psi_s_dn(u[c - P], u[c], u[c + P], at(g.y.d, j - 1), at(g.y.d, j),
-                                                   at(g.y.d, j + 1), at(g.y.wlo, j))
+        w.psUyD[c] = (t && !(p0 && p1)) ? psi_s_dn(u[c - P], u[c], u[c + P], at(g.y.dc, j), at(g.y.dc, j + 1),
+                                                   at(g.y.wlo, j))
                                         : zero;
     }
     // v node (i,j): the mirror image
@@ -340,11 +354,11 @@ __device__ __forceinline__ void face_limiters(const GeoT<R> &g, const R *__restr
                             : zero;
     {
         const bool t = (f & F_TVX) != 0, p0 = positive(u[c - P]), p1 = positive(u[c]);
-        w.psVxU[c] = (t && (p0 || p1)) ? psi_s_up(v[c - 2], v[c - 1], v[c], at(g.x.d, i - 2), at(g.x.d, i - 1),
-                                                  at(g.x.d, i), at(g.x.whi, i))
+        w.psVxU[c] = (t && (p0 || p1)) ? psi_s_up(v[c - 2], v[c - 1], v[c], at(g.x.dc, i - 1), at(g.x.dc, i),
+                                                  at(g.x.whi, i))
                                        : zero;
-        w.psVxD[c] = (t && !(p0 && p1)) ? psi_s_dn(v[c - 1], v[c], v[c + 1], at(g.x.d, i - 1), at(g.x.d, i),
-                                                   at(g.x.d, i + 1), at(g.x.wlo, i))
+        w.psVxD[c] = (t && !(p0 && p1)) ? psi_s_dn(v[c - 1], v[c], v[c + 1], at(g.x.dc, i), at(g.x.dc, i + 1),
+                                                   at(g.x.wlo, i))
                                         : zero;
     }
 }
@@ -375,8 +389,8 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         const R vel = u[c], rl = rho[c - 1], rr = rho[c];
         R val = upwind(rl, rr, vel);
         if (TVD && (g.flag[c] & F_TCX))
-            val += psi_surface(rho[c - 2], rl, rr, rho[c + 1], at(g.x.d, i - 2), at(g.x.d, i - 1),
-                               dxi, at(g.x.d, i + 1), at(g.x.whi, i), at(g.x.wlo, i), vel) * (rr - rl);
+            val += psi_surface(rho[c - 2], rl, rr, rho[c + 1], at(g.x.dc, i - 1), at(g.x.dc, i), at(g.x.dc, i + 1),
+                               at(g.x.whi, i), at(g.x.wlo, i), vel) * (rr - rl);
         const R rdy = val * dyj;
         w.ru_dy[c] = rdy;
         w.Fx[c] = rdy * vel;
@@ -386,8 +400,8 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         const R vel = v[c], rb = rho[c - P], rt = rho[c];
         R val = upwind(rb, rt, vel);
         if (TVD && (g.flag[c] & F_TCY))
-            val += psi_surface(rho[c - 2 * P], rb, rt, rho[c + P], at(g.y.d, j - 2), at(g.y.d, j - 1),
-                               dyj, at(g.y.d, j + 1), at(g.y.whi, j), at(g.y.wlo, j), vel) * (rt - rb);
+            val += psi_surface(rho[c - 2 * P], rb, rt, rho[c + P], at(g.y.dc, j - 1), at(g.y.dc, j),
+                               at(g.y.dc, j + 1), at(g.y.whi, j), at(g.y.wlo, j), vel) * (rt - rb);
         const R rdx = val * dxi;
         w.rv_dx[c] = rdx;
         w.Fy[c] = rdx * vel;
