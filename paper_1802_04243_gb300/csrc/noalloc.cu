@@ -100,6 +100,8 @@ __global__ void k_na_axis(int n, const double *dl, double len, double *out)
     out[3 * m + q] = whi;
     out[4 * m + q] = 1.0 / (0.5 * (dm + di));
     out[8 * m + q] = 0.5 * (dm + di);
+    out[9 * m + q] = 2.0 * wlo;
+    out[10 * m + q] = 2.0 * whi;
     // derivative weights: the interpolation weights of face q+1 (of face q
     // itself for the last entry, which no cell uses)
     const double dn = q + 1 < m ? size_at(q + 1) : di, dc = q + 1 < m ? di : dm;

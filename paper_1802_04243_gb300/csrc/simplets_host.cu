@@ -346,6 +346,8 @@ std::vector<double> make_axis(const std::vector<double> &dl)
         out[3 * m + q] = dm / (dm + di);
         out[4 * m + q] = 1.0 / (0.5 * (dm + di));
         out[8 * m + q] = 0.5 * (dm + di);
+        out[9 * m + q] = 2.0 * out[2 * m + q];
+        out[10 * m + q] = 2.0 * out[3 * m + q];
     }
     for (int q = 0; q < m; q++) {
         const int qn = q + 1 < m ? q + 1 : q;

@@ -90,13 +90,15 @@ __device__ __forceinline__ double recip(double a);
 
 // Van Leer psi(r) = (r + |r|)/(1 + r) for r = num/den, i.e. 2 num/(num + den)
 // when num and den are nonzero with one sign, else 0 (a zero denominator
-// falls back to first order).  The sign test reads the sign bits, so it runs
-// on the integer pipe; the quotient uses the sweep's reciprocal.
+// falls back to first order).  Its half, num/(num + den), is what the
+// corrections below use (the factor 2 is folded into their weights; scaling
+// by a power of two is exact).  The sign test reads the sign bits, so it
+// runs on the integer pipe; the quotient uses the sweep's reciprocal.
 template <typename R>
-__device__ __forceinline__ R van_leer(R num, R den)
+__device__ __forceinline__ R van_leer_half(R num, R den)
 {
     const bool same = (positive(num) && positive(den)) || (below_zero(num) && below_zero(den));
-    return same ? R(2) * num * recip(num + den) : R(0);
+    return same ? num * recip(num + den) : R(0);
 }
 
 // Eq. pl15_2: correction at the face between nodes 2 and 3 for flow towards
@@ -104,31 +106,23 @@ __device__ __forceinline__ R van_leer(R num, R den)
 // nodes: psi = w2 VanLeer((d2 + d3)(f2 - f1), (d1 + d2)(f3 - f2)) and its
 // mirror, w2 = d2/(d2 + d3), w3 = d3/(d2 + d3).  Van Leer's quotient is
 // unchanged when both arguments are halved, so the sums of two sizes enter
-// as the centre distances c12 = (d1 + d2)/2, c23, c34 of the axis tables
-// (the same bits: halving is exact).
+// as the centre distances c12 = (d1 + d2)/2, c23, c34 of the axis tables, and
+// w2 VanLeer = (2 w2) VanLeer/2 with 2 w2 tabulated (the same bits: every
+// rescaling is by a power of two).
 template <typename R>
-__device__ __forceinline__ R psi_s_up(R f1, R f2, R f3, R c12, R c23, R w2)
+__device__ __forceinline__ R psi_s_up(R f1, R f2, R f3, R c12, R c23, R w2x2)
 {
-    return w2 * van_leer(c23 * (f2 - f1), c12 * (f3 - f2));
+    return w2x2 * van_leer_half(c23 * (f2 - f1), c12 * (f3 - f2));
 }
 template <typename R>
-__device__ __forceinline__ R psi_s_dn(R f2, R f3, R f4, R c23, R c34, R w3)
+__device__ __forceinline__ R psi_s_dn(R f2, R f3, R f4, R c23, R c34, R w3x2)
 {
-    return -(w3 * van_leer(c23 * (f4 - f3), c34 * (f3 - f2)));
+    return -(w3x2 * van_leer_half(c23 * (f4 - f3), c34 * (f3 - f2)));
 }
 template <typename R>
-__device__ __forceinline__ R psi_surface(R f1, R f2, R f3, R f4, R c12, R c23, R c34, R w2, R w3, R vel)
+__device__ __forceinline__ R psi_surface(R f1, R f2, R f3, R f4, R c12, R c23, R c34, R w2x2, R w3x2, R vel)
 {
-    return positive(vel) ? psi_s_up(f1, f2, f3, c12, c23, w2) : psi_s_dn(f2, f3, f4, c23, c34, w3);
-}
-
-// Half of Van Leer's psi, num/(num + den) under the same sign test: the same
-// bits as 0.5 van_leer(num, den), since scaling by 2 and by 1/2 is exact.
-template <typename R>
-__device__ __forceinline__ R van_leer_half(R num, R den)
-{
-    const bool same = (positive(num) && positive(den)) || (below_zero(num) && below_zero(den));
-    return same ? num * recip(num + den) : R(0);
+    return positive(vel) ? psi_s_up(f1, f2, f3, c12, c23, w2x2) : psi_s_dn(f2, f3, f4, c23, c34, w3x2);
 }
 
 // Eq. pl15_1: face midway between nodes 2 and 3; d1..d3 the node distances;
@@ -326,10 +320,10 @@ __device__ __forceinline__ void face_limiters(const GeoT<R> &g, const R *__restr
     const R zero = R(0);
     // T on the x face i and the y face j (Eq. pl15_2)
     w.psTx[c] = (f & F_TCX) ? psi_surface(T[c - 2], T[c - 1], T[c], T[c + 1], at(g.x.dc, i - 1), at(g.x.dc, i),
-                                          at(g.x.dc, i + 1), at(g.x.whi, i), at(g.x.wlo, i), u[c])
+                                          at(g.x.dc, i + 1), at(g.x.whi2, i), at(g.x.wlo2, i), u[c])
                             : zero;
     w.psTy[c] = (f & F_TCY) ? psi_surface(T[c - 2 * P], T[c - P], T[c], T[c + P], at(g.y.dc, j - 1), at(g.y.dc, j),
-                                          at(g.y.dc, j + 1), at(g.y.whi, j), at(g.y.wlo, j), v[c])
+                                          at(g.y.dc, j + 1), at(g.y.whi2, j), at(g.y.wlo2, j), v[c])
                             : zero;
     // u node (i,j): x face of its control volume at the centre of cell i-1
     // (Eq. pl15_1, velocity the mean of the two u nodes), and the y face
@@ -342,10 +336,10 @@ __device__ __forceinline__ void face_limiters(const GeoT<R> &g, const R *__restr
     {
         const bool t = (f & F_TUY) != 0, p0 = positive(v[c - 1]), p1 = positive(v[c]);
         w.psUyU[c] = (t && (p0 || p1)) ? psi_s_up(u[c - 2 * P], u[c - P], u[c], at(g.y.dc, j - 1), at(g.y.dc, j),
-                                                  at(g.y.whi, j))
+                                                  at(g.y.whi2, j))
                                        : zero;
         w.psUyD[c] = (t && !(p0 && p1)) ? psi_s_dn(u[c - P], u[c], u[c + P], at(g.y.dc, j), at(g.y.dc, j + 1),
-                                                   at(g.y.wlo, j))
+                                                   at(g.y.wlo2, j))
                                         : zero;
     }
     // v node (i,j): the mirror image
@@ -355,10 +349,10 @@ __device__ __forceinline__ void face_limiters(const GeoT<R> &g, const R *__restr
     {
         const bool t = (f & F_TVX) != 0, p0 = positive(u[c - P]), p1 = positive(u[c]);
         w.psVxU[c] = (t && (p0 || p1)) ? psi_s_up(v[c - 2], v[c - 1], v[c], at(g.x.dc, i - 1), at(g.x.dc, i),
-                                                  at(g.x.whi, i))
+                                                  at(g.x.whi2, i))
                                        : zero;
         w.psVxD[c] = (t && !(p0 && p1)) ? psi_s_dn(v[c - 1], v[c], v[c + 1], at(g.x.dc, i), at(g.x.dc, i + 1),
-                                                   at(g.x.wlo, i))
+                                                   at(g.x.wlo2, i))
                                         : zero;
     }
 }
@@ -390,7 +384,7 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         R val = upwind(rl, rr, vel);
         if (TVD && (g.flag[c] & F_TCX))
             val += psi_surface(rho[c - 2], rl, rr, rho[c + 1], at(g.x.dc, i - 1), at(g.x.dc, i), at(g.x.dc, i + 1),
-                               at(g.x.whi, i), at(g.x.wlo, i), vel) * (rr - rl);
+                               at(g.x.whi2, i), at(g.x.wlo2, i), vel) * (rr - rl);
         const R rdy = val * dyj;
         w.ru_dy[c] = rdy;
         w.Fx[c] = rdy * vel;
@@ -401,7 +395,7 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         R val = upwind(rb, rt, vel);
         if (TVD && (g.flag[c] & F_TCY))
             val += psi_surface(rho[c - 2 * P], rb, rt, rho[c + P], at(g.y.dc, j - 1), at(g.y.dc, j),
-                               at(g.y.dc, j + 1), at(g.y.whi, j), at(g.y.wlo, j), vel) * (rt - rb);
+                               at(g.y.dc, j + 1), at(g.y.whi2, j), at(g.y.wlo2, j), vel) * (rt - rb);
         const R rdx = val * dxi;
         w.rv_dx[c] = rdx;
         w.Fy[c] = rdx * vel;
