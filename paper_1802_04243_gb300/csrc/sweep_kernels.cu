@@ -328,8 +328,9 @@ __device__ __forceinline__ void face_limiters(const GeoT<R> &g, const R *__restr
     // u node (i,j): x face of its control volume at the centre of cell i-1
     // (Eq. pl15_1, velocity the mean of the two u nodes), and the y face
     // between u nodes (i,j-1) and (i,j) (Eq. pl15_2, both flow directions)
+    // (only the sign of the mean velocity selects the branch: the sum has it)
     w.psUx[c] = (f & F_TUX) ? psi_centre(u[c - 2], u[c - 1], u[c], u[c + 1], at(g.x.d, i - 2), at(g.x.d, i - 1),
-                                         at(g.x.d, i), R(0.5) * (u[c - 1] + u[c]))
+                                         at(g.x.d, i), u[c - 1] + u[c])
                             : zero;
     // (a branch is evaluated only if one of the two v faces that select it,
     // v(i-1,j) and v(i,j), points its way)
@@ -344,7 +345,7 @@ __device__ __forceinline__ void face_limiters(const GeoT<R> &g, const R *__restr
     }
     // v node (i,j): the mirror image
     w.psVy[c] = (f & F_TVY) ? psi_centre(v[c - 2 * P], v[c - P], v[c], v[c + P], at(g.y.d, j - 2), at(g.y.d, j - 1),
-                                         at(g.y.d, j), R(0.5) * (v[c - P] + v[c]))
+                                         at(g.y.d, j), v[c - P] + v[c])
                             : zero;
     {
         const bool t = (f & F_TVX) != 0, p0 = positive(u[c - P]), p1 = positive(u[c]);
