@@ -420,6 +420,18 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
 
 // ------------------------------------------------------- explicit terms
 
+// Face value of Eqs. pl15_11, pl31_1: the upwind node value plus psi times
+// the difference across the face.  The upwind scheme (psi = 0) skips the
+// correction, which IEEE arithmetic cannot drop by itself.
+template <typename R, bool TVD>
+__device__ __forceinline__ R face_value(R a, R b, R vel, R psi)
+{
+    if constexpr (TVD)
+        return upwind(a, b, vel) + (b - a) * psi;
+    else
+        return upwind(a, b, vel);
+}
+
 // T^explicit of cell (i,j), Eq. pl31_1, all inputs at level n-1.
 template <typename R, bool TVD>
 __device__ R explicit_T(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, const WorkT<R> &w, int c, int i,
@@ -443,8 +455,8 @@ __device__ R explicit_T(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L,
         pn = w.psTy[c + P];
         ps = w.psTy[c];
     }
-    return -Fe * (upwind(Tp, Te, ue) + (Te - Tp) * pe) + Fw * (upwind(Tw, Tp, uw) + (Tp - Tw) * pw)
-           - Fn * (upwind(Tp, Tn, vn) + (Tn - Tp) * pn) + Fs * (upwind(Ts, Tp, vs) + (Tp - Ts) * ps);
+    return -Fe * face_value<R, TVD>(Tp, Te, ue, pe) + Fw * face_value<R, TVD>(Tw, Tp, uw, pw)
+           - Fn * face_value<R, TVD>(Tp, Tn, vn, pn) + Fs * face_value<R, TVD>(Ts, Tp, vs, ps);
 }
 
 // v^explicit of v face (i,j), Eq. pl15_11, level n-1.
@@ -472,10 +484,10 @@ __device__ R explicit_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L,
         pn = w.psVy[b + P];
         ps = w.psVy[b];
     }
-    return R(-0.5) * (Fe1 * (upwind(vP, vE, ue1) + (vE - vP) * pe1) + Fe2 * (upwind(vP, vE, ue2) + (vE - vP) * pe2))
-           + R(0.5) * (Fw1 * (upwind(vW, vP, uw1) + (vP - vW) * pw1) + Fw2 * (upwind(vW, vP, uw2) + (vP - vW) * pw2))
-           - Fbn * (upwind(vP, vN, Fbn) + (vN - vP) * pn)
-           + Fbs * (upwind(vS, vP, Fbs) + (vP - vS) * ps);
+    return R(-0.5) * (Fe1 * face_value<R, TVD>(vP, vE, ue1, pe1) + Fe2 * face_value<R, TVD>(vP, vE, ue2, pe2))
+           + R(0.5) * (Fw1 * face_value<R, TVD>(vW, vP, uw1, pw1) + Fw2 * face_value<R, TVD>(vW, vP, uw2, pw2))
+           - Fbn * face_value<R, TVD>(vP, vN, Fbn, pn)
+           + Fbs * face_value<R, TVD>(vS, vP, Fbs, ps);
 }
 
 // u^explicit of u face (i,j): the mirror image of Eq. pl15_11, level n-1.
@@ -503,10 +515,10 @@ __device__ R explicit_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L,
         pe = w.psUx[a + 1];
         pw = w.psUx[a];
     }
-    return R(-0.5) * (Fn1 * (upwind(uP, uN, vn1) + (uN - uP) * pn1) + Fn2 * (upwind(uP, uN, vn2) + (uN - uP) * pn2))
-           + R(0.5) * (Fs1 * (upwind(uS, uP, vs1) + (uP - uS) * ps1) + Fs2 * (upwind(uS, uP, vs2) + (uP - uS) * ps2))
-           - Fbe * (upwind(uP, uE, Fbe) + (uE - uP) * pe)
-           + Fbw * (upwind(uW, uP, Fbw) + (uP - uW) * pw);
+    return R(-0.5) * (Fn1 * face_value<R, TVD>(uP, uN, vn1, pn1) + Fn2 * face_value<R, TVD>(uP, uN, vn2, pn2))
+           + R(0.5) * (Fs1 * face_value<R, TVD>(uS, uP, vs1, ps1) + Fs2 * face_value<R, TVD>(uS, uP, vs2, ps2))
+           - Fbe * face_value<R, TVD>(uP, uE, Fbe, pe)
+           + Fbw * face_value<R, TVD>(uW, uP, Fbw, pw);
 }
 
 template <typename R, bool TVD>
