@@ -34,10 +34,10 @@ UNIT = "Mcell-steps/s"
 # The dominant kernel, k_assemble (FP64, implicit upwind), is bound by GB300's
 # FP64 pipe.  Its work per cell and loop-2 iteration is counted by ncu on one
 # launch for the 2048x512 channel (1,048,576 cells): DFMA, DADD and DMUL thread
-# instructions 53.62 M, 54.05 M, 46.41 M.
-ASSEMBLE_FP64_INST_PER_CELL = {"dfma": 51.14, "dadd": 51.55, "dmul": 44.26}
-# DRAM bytes of that launch per cell (127.4 MB read + 21.3 MB written).
-ASSEMBLE_DRAM_BYTES_PER_CELL = 141.8
+# instructions 53.62 M, 54.05 M, 44.34 M.
+ASSEMBLE_FP64_INST_PER_CELL = {"dfma": 51.14, "dadd": 51.55, "dmul": 42.29}
+# DRAM bytes of that launch per cell (127.4 MB read + 20.9 MB written).
+ASSEMBLE_DRAM_BYTES_PER_CELL = 141.4
 # ncu: sm__pipe_fp64_cycles_active of that launch, fraction of peak.
 ASSEMBLE_FP64_PIPE_ACTIVE = 0.852
 # Algorithmic HBM traffic of the kernel per cell: reads u, v, p, T, rho, Gamma of

@@ -102,6 +102,7 @@ __global__ void k_na_axis(int n, const double *dl, double len, double *out)
     out[8 * m + q] = 0.5 * (dm + di);
     out[9 * m + q] = 2.0 * wlo;
     out[10 * m + q] = 2.0 * whi;
+    out[11 * m + q] = 0.5 * di;
     // derivative weights: the interpolation weights of face q+1 (of face q
     // itself for the last entry, which no cell uses)
     const double dn = q + 1 < m ? size_at(q + 1) : di, dc = q + 1 < m ? di : dm;
@@ -263,7 +264,7 @@ struct Carver {
 bool coefficients(const sim_gas *gas, Coef &k, double &u_in, double &gm)
 {
     double ct1, ct2, ct3;
-    k.A = 0.5;
+    k.A = 0.5;                 // for every gas model; the FP64 kernels take A dy as the tabulated half height
     if (gas->model == SIM_GAS_HARD_SPHERE_KN) {
         const double pi = 3.14159265358979323846;
         gm = 5.0 / 3.0;

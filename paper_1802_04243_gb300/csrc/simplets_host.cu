@@ -129,7 +129,7 @@ sim_status derive_coefficients(const sim_gas *gas, Problem &pb, sim_t err)
 {
     double ct1, ct2, ct3, gm;
     Coef &k = pb.k;
-    k.A = 0.5;
+    k.A = 0.5;                 // for every gas model; the FP64 kernels take A dy as the tabulated half height
     if (gas->model == SIM_GAS_HARD_SPHERE_KN) {
         const double pi = 3.14159265358979323846;
         gm = 5.0 / 3.0;
@@ -348,6 +348,7 @@ std::vector<double> make_axis(const std::vector<double> &dl)
         out[8 * m + q] = 0.5 * (dm + di);
         out[9 * m + q] = 2.0 * out[2 * m + q];
         out[10 * m + q] = 2.0 * out[3 * m + q];
+        out[11 * m + q] = 0.5 * di;
     }
     for (int q = 0; q < m; q++) {
         const int qn = q + 1 < m ? q + 1 : q;

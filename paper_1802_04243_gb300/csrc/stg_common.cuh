@@ -56,17 +56,18 @@ struct AxisT {
     const R *dc;     // 0.5 (d_{i-1} + d_i): centre distance across face i
     const R *wlo2;   // 2 wlo (exact): the TVD face corrections take twice the weight
     const R *whi2;   // 2 whi
+    const R *hd;     // 0.5 d_i (exact)
 };
 
 // Number of per-index arrays of an axis table, stored one after another.
-constexpr int kAxisTables = 11;
+constexpr int kAxisTables = 12;
 
 // The arrays of an axis table of m entries per array starting at t.
 template <typename R>
 inline AxisT<R> axis_view(const R *t, int m)
 {
-    return AxisT<R>{t,         t + m,     t + 2 * m, t + 3 * m, t + 4 * m, t + 5 * m,
-                    t + 6 * m, t + 7 * m, t + 8 * m, t + 9 * m, t + 10 * m};
+    return AxisT<R>{t,         t + m,     t + 2 * m, t + 3 * m, t + 4 * m,  t + 5 * m,
+                    t + 6 * m, t + 7 * m, t + 8 * m, t + 9 * m, t + 10 * m, t + 11 * m};
 }
 
 template <typename R>

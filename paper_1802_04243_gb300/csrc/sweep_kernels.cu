@@ -289,7 +289,21 @@ __device__ __forceinline__ unsigned long long res_key(df64 d) { return ordered_b
 
 // Gamma = T^omega (power-law transport coefficients): the square root for
 // omega = 1/2, the general power otherwise (double-float: through FP64).
-__device__ __forceinline__ double gamma_of(double T, double omega) { return omega == 0.5 ? sqrt(T) : pow(T, omega); }
+// (omega == 1/2 is tested on the bits, keeping the comparison off the FP64 pipe)
+__device__ __forceinline__ bool is_half(double omega) { return __double_as_longlong(omega) == 0x3FE0000000000000LL; }
+
+// d/2 of index i: from the half-size table in FP64 (a load instead of an
+// FP64 multiply); the FP32 and double-float sweeps, bound by latency rather
+// than by arithmetic, multiply (the same value: halving is exact).
+template <typename R>
+__device__ __forceinline__ R half_size(const AxisT<R> &ax, int i, R d)
+{
+    if constexpr (std::is_same<R, double>::value)
+        return ax.hd[i + G];
+    else
+        return R(0.5) * d;
+}
+__device__ __forceinline__ double gamma_of(double T, double omega) { return is_half(omega) ? sqrt(T) : pow(T, omega); }
 __device__ __forceinline__ df64 gamma_of(df64 T, df64 omega)
 {
     if (omega.hi == 0.5f && omega.lo == 0.0f) return sqrt(T);
@@ -299,11 +313,12 @@ __device__ __forceinline__ df64 gamma_of(df64 T, df64 omega)
 // T conductance of the face between a node of size da and one of size db
 // (Eq. pl32): c_area Gamma_f / (0.5 (da + db)) with the distance-weighted
 // harmonic mean Gamma_f = (da + db) ga gb / (da gb + db ga) of Eq. pl33,
-// i.e. 2 c_area ga gb / (da gb + db ga).  c_area = C^T1_f times the face area.
+// i.e. 2 c_area ga gb / (da gb + db ga).  c2_area = 2 C^T1_f times the face
+// area (the caller doubles C^T1_f once for both faces; doubling is exact).
 template <typename R>
-__device__ __forceinline__ R conductance(R ga, R gb, R da, R db, R c_area)
+__device__ __forceinline__ R conductance(R ga, R gb, R da, R db, R c2_area)
 {
-    return R(2) * c_area * (ga * gb) * recip(fma(da, gb, db * ga));
+    return c2_area * (ga * gb) * recip(fma(da, gb, db * ga));
 }
 
 // ------------------------------------------------------- face densities
@@ -380,6 +395,7 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
     const int c = Ix{P}(i, j);
     if (i > g.nx || j > g.ny) return;
     const R dxi = at(g.x.d, i), dyj = at(g.y.d, j);
+    const R ct1f2 = R(2) * k.CT1f;
     if (j < g.ny) {
         const R vel = u[c], rl = rho[c - 1], rr = rho[c];
         R val = upwind(rl, rr, vel);
@@ -389,7 +405,7 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         const R rdy = val * dyj;
         w.ru_dy[c] = rdy;
         w.Fx[c] = rdy * vel;
-        w.DTx[c] = conductance(gam[c - 1], gam[c], at(g.x.d, i - 1), dxi, k.CT1f * dyj);
+        w.DTx[c] = conductance(gam[c - 1], gam[c], at(g.x.d, i - 1), dxi, ct1f2 * dyj);
     }
     if (i < g.nx) {
         const R vel = v[c], rb = rho[c - P], rt = rho[c];
@@ -400,7 +416,7 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         const R rdx = val * dxi;
         w.rv_dx[c] = rdx;
         w.Fy[c] = rdx * vel;
-        w.DTy[c] = conductance(gam[c - P], gam[c], at(g.y.d, j - 1), dyj, k.CT1f * dxi);
+        w.DTy[c] = conductance(gam[c - P], gam[c], at(g.y.d, j - 1), dyj, ct1f2 * dxi);
     }
     w.Bgc[c] = k.B * gamma_corner(g, gam, c, i, j);
     if (i < g.nx && j < g.ny) {
@@ -410,8 +426,8 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         // mass fluxes through the cell centre, the face between the u (v)
         // control volumes of faces i and i+1 (j and j+1), with the mean
         // velocity of the two faces
-        w.Fbu[c] = (u[c] + u[c + 1]) * (R(0.5) * dyj) * rho[c];
-        w.Fbv[c] = (v[c] + v[c + P]) * (R(0.5) * dxi) * rho[c];
+        w.Fbu[c] = (u[c] + u[c + 1]) * half_size(g.y, j, dyj) * rho[c];
+        w.Fbv[c] = (v[c] + v[c + P]) * half_size(g.x, i, dxi) * rho[c];
     }
     if constexpr (TVD) {
         if (limiters) face_limiters(g, u, v, T, w, c, i, j);
@@ -696,7 +712,14 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     R src = a1 * uW + a2 * uE + a3 * uS + a4 * uN + b;
     if constexpr (!IMPL) src += uexp;
     uhat = src * r;
-    du = k.A * dyj * r;
+    // A = 1/2 for every gas model of this solver (Eq. pl37, reading R6): in
+    // FP64 A dy is the tabulated half height (the same value, no multiply)
+    R Ady;
+    if constexpr (std::is_same<R, double>::value)
+        Ady = half_size(g.y, j, dyj);
+    else
+        Ady = k.A * dyj;
+    du = Ady * r;
 }
 
 // v^ and d^v of v face (i,j) between fluid cells, Eqs. pl14-pl16, pl21
@@ -763,7 +786,12 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     R src = a1 * vW + a2 * vE + a3 * vS + a4 * vN + bsrc;
     if constexpr (!IMPL) src += vexp;
     vhat = src * r;
-    dv = k.A * dxi * r;
+    R Adx;
+    if constexpr (std::is_same<R, double>::value)
+        Adx = half_size(g.x, i, dxi);
+    else
+        Adx = k.A * dxi;
+    dv = Adx * r;
 }
 
 template <typename R, bool IMPL, bool TVD, bool WALLS>
@@ -1268,7 +1296,7 @@ __global__ void k_derive(Geo g, Coef k, Level L)
     if (!(g.flag[c] & F_FLUID)) return;
     const double T = L.T[c];
     L.rho[c] = L.p[c] * recip(T);
-    L.gam[c] = (k.omega == 0.5) ? sqrt(T) : pow(T, k.omega);
+    L.gam[c] = gamma_of(T, k.omega);
 }
 
 __device__ __forceinline__ double *field_of(const Level &L, int f)
@@ -1326,7 +1354,7 @@ __global__ void k_scatter_state(Geo g, Coef k, const double *st, Level L)
         L.p[c] = p;
         L.T[c] = T;
         L.rho[c] = p * recip(T);
-        L.gam[c] = (k.omega == 0.5) ? sqrt(T) : pow(T, k.omega);
+        L.gam[c] = gamma_of(T, k.omega);
     }
 }
 
