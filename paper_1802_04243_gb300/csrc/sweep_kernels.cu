@@ -1214,9 +1214,12 @@ __global__ void __launch_bounds__(256) k_explicit(const __grid_constant__ BatchP
 }
 
 // Resident CTAs per SM: two for the FP64 assembly (bound by the FP64 pipe),
-// three for the FP32 and double-float ones, which are latency-bound.
+// four for the FP32 and double-float ones, which are latency-bound
+// (measured against three: FP32 at 64 registers with a few bytes of spills
+// 5-6 % faster, double-float up to 2.5 % despite its spills; five CTAs were
+// slower for FP32).
 template <int PREC, bool IMPL, bool TVD>
-__global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 2 : 3) k_assemble(const __grid_constant__ BatchPlan bp,
+__global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 2 : 4) k_assemble(const __grid_constant__ BatchPlan bp,
                                                                               int prev, int old, int nw)
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
