@@ -34,6 +34,13 @@ int simplets_alu_peak(int kind, double millis, void *stream, double *gflops);
  * allocates and frees its own device buffers. */
 int simplets_recip_check(const double *host_x, int n, double *host_out);
 
+/* Check of the FP64 square root the sweep uses for Gamma = T^(1/2) (two
+ * Newton-Raphson steps s <- s + (x - s^2) y/2 from s = x y, y the FP32
+ * reciprocal square root of x; the library's sqrt for |x| outside
+ * [2^-100, 2^100]).  Same arguments and returns as simplets_recip_check, with
+ * the sweep's root in host_out[2q] and the IEEE root in host_out[2q+1]. */
+int simplets_sqrt_check(const double *host_x, int n, double *host_out);
+
 #ifdef __cplusplus
 }
 #endif

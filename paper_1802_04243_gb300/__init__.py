@@ -83,6 +83,7 @@ _SIGNATURES = {
     "sim_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "simplets_alu_peak": ([ctypes.c_int, ctypes.c_double, ctypes.c_void_p, _DP], ctypes.c_int),
     "simplets_recip_check": ([_DP, ctypes.c_int, _DP], ctypes.c_int),
+    "simplets_sqrt_check": ([_DP, ctypes.c_int, _DP], ctypes.c_int),
     "sim_destroy": ([ctypes.c_void_p], None),
     "sim_batch_create": ([ctypes.c_int, ctypes.POINTER(sim_grid), ctypes.POINTER(sim_gas), ctypes.POINTER(sim_bc),
                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
@@ -176,6 +177,17 @@ def recip_check(x) -> "tuple[np.ndarray, np.ndarray]":
     rc = load().simplets_recip_check(x.ctypes.data_as(_DP), int(x.size), out.ctypes.data_as(_DP))
     if rc:
         raise SimError(SIM_ECUDA, f"simplets_recip_check failed ({rc})")
+    return out[0::2].copy(), out[1::2].copy()
+
+
+def sqrt_check(x) -> "tuple[np.ndarray, np.ndarray]":
+    """The sweep's FP64 square root of each x (Gamma for omega = 1/2) and the
+    IEEE root, both computed on the device (include/simplets_probe.h)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    out = np.empty(2 * x.size)
+    rc = load().simplets_sqrt_check(x.ctypes.data_as(_DP), int(x.size), out.ctypes.data_as(_DP))
+    if rc:
+        raise SimError(SIM_ECUDA, f"simplets_sqrt_check failed ({rc})")
     return out[0::2].copy(), out[1::2].copy()
 
 

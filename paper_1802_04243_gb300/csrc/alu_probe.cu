@@ -69,7 +69,8 @@ extern "C" int simplets_alu_peak(int kind, double millis, void *stream, double *
     return kind == 0 ? run<double>(millis, st, gflops) : run<float>(millis, st, gflops);
 }
 
-extern "C" int simplets_recip_check(const double *host_x, int n, double *host_out)
+// Both checks: copy x in, run one of the check kernels, copy the pairs out.
+static int run_check(const double *host_x, int n, double *host_out, bool root)
 {
     if (n < 0 || (n > 0 && (!host_x || !host_out))) return 1;
     if (n == 0) return 0;
@@ -78,11 +79,24 @@ extern "C" int simplets_recip_check(const double *host_x, int n, double *host_ou
     int rc = 0;
     if (cudaMemcpy(d, host_x, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) rc = 3;
     if (!rc) {
-        stg::launch_recip_check(d, d + n, n, nullptr);
+        if (root)
+            stg::launch_sqrt_check(d, d + n, n, nullptr);
+        else
+            stg::launch_recip_check(d, d + n, n, nullptr);
         if (cudaDeviceSynchronize() != cudaSuccess ||
             cudaMemcpy(host_out, d + n, 2 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
             rc = 3;
     }
     cudaFree(d);
     return rc;
+}
+
+extern "C" int simplets_recip_check(const double *host_x, int n, double *host_out)
+{
+    return run_check(host_x, n, host_out, false);
+}
+
+extern "C" int simplets_sqrt_check(const double *host_x, int n, double *host_out)
+{
+    return run_check(host_x, n, host_out, true);
 }

@@ -238,5 +238,8 @@ void launch_join(const LevelT<df64> &d, const Level &lv, size_t nelem, void *str
 // The FP64 reciprocal of the sweep (a series step from the FP32 reciprocal) and the
 // IEEE quotient 1/x of each x[q], interleaved in out[2q], out[2q+1].
 void launch_recip_check(const double *x, double *out, int n, void *stream);
+// The FP64 square root of the sweep (Gamma = T^1/2: two Newton steps from the
+// FP32 reciprocal square root) and the IEEE root of each x[q], interleaved.
+void launch_sqrt_check(const double *x, double *out, int n, void *stream);
 
 }  // namespace stg

@@ -1,4 +1,5 @@
-"""The FP64 reciprocal of the sweep against CUDA's IEEE division.
+"""The FP64 reciprocal and square root of the sweep against CUDA's IEEE
+division and square root.
 
 The sweep divides by a^0 (Eqs. pl15, pl20, pl21, pl30) and by T and a^p_0
 (Eqs. pl23, pl5) with its own reciprocal instead of IEEE division: from the
@@ -43,3 +44,23 @@ def test_reciprocal_of_exact_cases():
     x = np.array([1.0, 2.0, 4.0, 0.25, -8.0, 2.0 ** 60, 2.0 ** -60])
     ours, ieee = sim.recip_check(x)
     assert np.array_equal(ours, ieee)                                # powers of two are exact
+
+
+def test_square_root_within_one_ulp_of_ieee_sqrt():
+    # Gamma = T^(1/2) (Eq. pl37): two Newton-Raphson steps for s^2 = x from
+    # the FP32 reciprocal square root take its error of about 2^-22 to about
+    # 2^-65, so the root must stay within one ulp of the correctly rounded one
+    rng = np.random.default_rng(13)
+    x = np.concatenate([
+        10.0 ** rng.uniform(-300, 300, 200_000),
+        rng.uniform(0.2, 20.0, 200_000),                           # the temperatures of the workloads
+        np.nextafter(1.0, 2.0) * 2.0 ** np.arange(-120, 121),      # both sides of the FP32-seed range
+        np.nextafter(2.0, 1.0) * 2.0 ** np.arange(-120, 121),
+        np.arange(1.0, 2000.0) ** 2,                               # perfect squares
+        [1.0, 2.0, 0.5, 3.0, 1e-310, 1e308, 2.0 ** -100, 2.0 ** 100, 0.0],
+    ])
+    ours, ieee = sim.sqrt_check(x)
+    ulps = np.abs(ours - ieee) / np.spacing(np.abs(ieee))
+    print("max ulp", ulps.max(), "exact", float(np.mean(ulps == 0)))
+    assert ulps.max() <= 1.0
+    assert np.isnan(sim.sqrt_check(np.array([-1.0]))[0][0])
