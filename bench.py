@@ -36,10 +36,10 @@ UNIT = "Mcell-steps/s"
 # launch for the 2048x512 channel (1,048,576 cells): DFMA, DADD and DMUL thread
 # instructions 53.62 M, 54.05 M, 44.34 M.
 ASSEMBLE_FP64_INST_PER_CELL = {"dfma": 51.14, "dadd": 51.55, "dmul": 42.29}
-# DRAM bytes of that launch per cell (127.4 MB read + 20.9 MB written).
-ASSEMBLE_DRAM_BYTES_PER_CELL = 141.4
+# DRAM bytes of that launch per cell (127.4 MB read + 20.8 MB written).
+ASSEMBLE_DRAM_BYTES_PER_CELL = 141.3
 # ncu: sm__pipe_fp64_cycles_active of that launch, fraction of peak.
-ASSEMBLE_FP64_PIPE_ACTIVE = 0.852
+ASSEMBLE_FP64_PIPE_ACTIVE = 0.854
 # Algorithmic HBM traffic of the kernel per cell: reads u, v, p, T, rho, Gamma of
 # the previous iterate, u, v, T, rho of level n-1 and the face arrays F^x, F^y,
 # D^T_x, D^T_y, B Gamma (corner), B Gamma dy/dx, B Gamma dx/dy and the two
