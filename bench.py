@@ -265,19 +265,35 @@ def run_batch(args, stream):
 
 # ------------------------------------------------------------- cpu baseline
 
-def oracle_throughput(case, target_s: float = 12.0, max_steps: int = 400):
-    """Time the reference oracle (serial FP64 C) on the host on a bounded
+def oracle_throughput(case, target_s: float = 12.0, max_steps: int = 400, rows: bool = False):
+    """Time the reference oracle (serial FP64 C, or with rows=True its
+    row-parallel OpenMP build on all host threads) on the host on a bounded
     number of time steps of the same workload; returns (Mcell-steps/s, steps, seconds)."""
     import oracle
     state = oracle.init(case)
     t0 = time.perf_counter()
-    state = oracle.run(case, state, nsteps=1)[0]
+    state = oracle.run(case, state, nsteps=1, rows=rows)[0]
     t1 = time.perf_counter() - t0
     n = max(1, min(max_steps, int(target_s / max(t1, 1e-6))))
     t0 = time.perf_counter()
-    oracle.run(case, state, nsteps=n)
+    oracle.run(case, state, nsteps=n, rows=rows)
     dt = time.perf_counter() - t0
     return case.cells * n / dt / 1e6, n, dt
+
+
+def cpu_rows_baseline(case):
+    """The same oracle source built with OpenMP: its row loops split across
+    all host threads (same bits as the serial build).  A second, multi-core
+    CPU figure beside the one-core baseline."""
+    import oracle
+    try:
+        v, n, secs = oracle_throughput(case, target_s=6.0, rows=True)
+        cores = oracle.threads(rows=True)
+    except (OSError, subprocess.CalledProcessError) as e:
+        return {"unavailable": f"row-parallel oracle build failed: {e}".splitlines()[0]}
+    return {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle, row-parallel (OpenMP)",
+            "sample": f"{n} time steps of the same {case.nx}x{case.ny} channel from its seeded start "
+                      f"({secs:.1f} s on {cores} threads)"}
 
 
 # ------------------------------------------------------------ paper sweep
@@ -500,12 +516,13 @@ def run_ours(args, rank, world, local_rank):
 
     batched = None if args.no_batch else run_batch(args, stream)
 
-    cpu = None
+    cpu = cpu_rows = None
     if not args.no_cpu_baseline:
         v, n, secs = oracle_throughput(case)
         cpu = {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{n} time steps of the same {case.nx}x{case.ny} channel from its seeded start "
                          f"({secs:.1f} s, serial FP64 C oracle)"}
+        cpu_rows = cpu_rows_baseline(case)
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
@@ -518,7 +535,8 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": int(launches),
             "kernel_ms_avg": {k: round(ms / n, 5) for k, (ms, n) in prof.items() if n},
             "kernel_timing": f"separate pass of {prof_steps} steps with per-launch CUDA events",
-            "roofline": roof, "mixed": mixed, "df64": df64, "batched": batched, "cpu_baseline": cpu, "clocks": csum,
+            "roofline": roof, "mixed": mixed, "df64": df64, "batched": batched, "cpu_baseline": cpu,
+            "cpu_baseline_rows": cpu_rows, "clocks": csum,
             "residuals_last_step": [float(x) for x in res], "impl": "ours"}
     print(json.dumps(line), flush=True)
     if dist:

@@ -21,19 +21,25 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "simplets_oracle.c")
 _HDR = os.path.join(_HERE, "simplets_oracle.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_ROWS = os.path.join(_HERE, "liboracle_rows.so")
 
 CFLAGS = ["-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-Wall"]
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so next to the source (plain gcc, no FMA contraction)."""
-    stale = (not os.path.exists(_LIB)
-             or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+def build(force: bool = False, rows: bool = False) -> str:
+    """Compile liboracle.so next to the source (plain gcc, no FMA contraction).
+
+    rows=True compiles the same source with -fopenmp into liboracle_rows.so,
+    whose row loops run on all host threads (the multi-core CPU baseline);
+    it gives the same bits as the serial build."""
+    lib = _LIB_ROWS if rows else _LIB
+    stale = (not os.path.exists(lib)
+             or os.path.getmtime(lib) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
     if force or stale:
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, *(["-fopenmp"] if rows else []), "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, lib)
+    return lib
 
 
 class _Problem(ctypes.Structure):
@@ -63,16 +69,16 @@ class _Coeffs(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("A", "B", "CT1f", "CT2f", "CT3f", "omega", "u_in", "dt")]
 
 
-_lib = None
+_libs: Dict[bool, ctypes.CDLL] = {}
 _DP = ctypes.POINTER(ctypes.c_double)
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        # SIMPLETS_ORACLE_LIB points the binding at another build of the same
-        # source (the mutation test compiles deliberately broken copies)
-        lib = ctypes.CDLL(os.environ.get("SIMPLETS_ORACLE_LIB") or build())
+def _load(rows: bool = False):
+    if rows not in _libs:
+        # SIMPLETS_ORACLE_LIB points the serial binding at another build of the
+        # same source (the mutation test compiles deliberately broken copies)
+        path = build(rows=True) if rows else (os.environ.get("SIMPLETS_ORACLE_LIB") or build())
+        lib = ctypes.CDLL(path)
         lib.orc_coefficients.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(_Coeffs)]
         lib.orc_init.argtypes = [ctypes.POINTER(_Problem), _DP, _DP, _DP, _DP]
         lib.orc_run.argtypes = [ctypes.POINTER(_Problem), _DP, _DP, _DP, _DP, ctypes.c_int,
@@ -87,8 +93,10 @@ def _load():
         lib.orc_splitmix_uniform.restype = ctypes.c_double
         lib.orc_gam_harmonic.argtypes = [ctypes.c_double] * 4
         lib.orc_gam_harmonic.restype = ctypes.c_double
-        _lib = lib
-    return _lib
+        lib.orc_threads.argtypes = []
+        lib.orc_threads.restype = ctypes.c_int
+        _libs[rows] = lib
+    return _libs[rows]
 
 
 def _dptr(a: Optional[np.ndarray]):
@@ -165,9 +173,10 @@ def init(case) -> Dict[str, np.ndarray]:
 
 
 def run(case, state: Optional[Dict[str, np.ndarray]] = None, nsteps: int = 1,
-        allow_diverged: bool = False) -> Tuple[Dict[str, np.ndarray], np.ndarray, int]:
-    """Advance `nsteps` time steps.  Returns (state, residuals[u, v, p, T], iterations of last step)."""
-    lib = _load()
+        allow_diverged: bool = False, rows: bool = False) -> Tuple[Dict[str, np.ndarray], np.ndarray, int]:
+    """Advance `nsteps` time steps.  Returns (state, residuals[u, v, p, T], iterations of last step).
+    rows=True runs the row-parallel build (same bits, all host threads)."""
+    lib = _load(rows)
     pin = _Pinned(case)
     s = init(case) if state is None else {k: np.array(v, dtype=np.float64, copy=True) for k, v in state.items()}
     for k in ("u", "v", "p", "T"):
@@ -201,3 +210,8 @@ def gam_harmonic(ga: float, gb: float, da: float, db: float) -> float:
 
 def splitmix_uniform(seed: int, field: int, i: int, j: int) -> float:
     return _load().orc_splitmix_uniform(seed, field, i, j)
+
+
+def threads(rows: bool = False) -> int:
+    """Threads the row loops of a run use (1 for the serial build)."""
+    return _load(rows).orc_threads()

@@ -51,8 +51,22 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define G 2                  /* ghost layers on each side */
+
+/* Row loops whose iterations write disjoint elements and read only what an
+ * earlier pass wrote.  The plain build runs them serially.  The row-parallel
+ * build (-fopenmp, the multi-core CPU baseline) splits the rows across
+ * threads; each element takes the same arithmetic in the same order in both
+ * builds, so they give the same bits.  The residual maxima stay serial. */
+#ifdef _OPENMP
+#define ROWS _Pragma("omp parallel for private(i) schedule(static)")
+#else
+#define ROWS
+#endif
 
 enum { C_FLUID = 0, C_SOLID, C_WALL, C_SYMM, C_INFLOW, C_OUTFLOW };
 
@@ -708,12 +722,14 @@ static void compute_fluxes(const orc *o, const level *L, double *rho_u, double *
                            double *Fx, double *Fy)
 {
     int i, j;
+    ROWS
     for (j = 0; j < o->ny; j++)
         for (i = 0; i <= o->nx; i++) {
             double r = face_rho_u(o, L, i, j);
             if (rho_u) rho_u[FU(o, i, j)] = r;
             Fx[FU(o, i, j)] = r * Uc(o, L, i, j) * DY(o, j);
         }
+    ROWS
     for (j = 0; j <= o->ny; j++)
         for (i = 0; i < o->nx; i++) {
             double r = face_rho_v(o, L, i, j);
@@ -826,12 +842,15 @@ static void explicit_terms(orc *o, const level *prev)
 {
     int i, j;
     compute_fluxes(o, prev, NULL, NULL, o->Fx_prev, o->Fy_prev);
+    ROWS
     for (j = 0; j < o->ny; j++)
         for (i = 0; i < o->nx; i++)
             o->Texp[FC(o, i, j)] = fluid(o, i, j) ? T_explicit(o, prev, o->Fx_prev, o->Fy_prev, i, j) : 0.0;
+    ROWS
     for (j = 0; j < o->ny; j++)
         for (i = 0; i <= o->nx; i++)
             o->Uexp[FU(o, i, j)] = u_active(o, i, j) ? u_explicit(o, prev, o->Fy_prev, i, j) : 0.0;
+    ROWS
     for (j = 0; j <= o->ny; j++)
         for (i = 0; i < o->nx; i++)
             o->Vexp[FV(o, i, j)] = v_active(o, i, j) ? v_explicit(o, prev, o->Fx_prev, i, j) : 0.0;
@@ -1074,6 +1093,7 @@ static void iterate(orc *o, const level *prev, const level *old, level *nw, doub
     compute_fluxes(o, old, o->rho_u, o->rho_v, o->Fx, o->Fy);
 
     /* energy */
+    ROWS
     for (j = 0; j < ny; j++)
         for (i = 0; i < nx; i++)
             if (fluid(o, i, j))
@@ -1081,6 +1101,7 @@ static void iterate(orc *o, const level *prev, const level *old, level *nw, doub
 
     /* pseudo velocities; faces that are not unknowns keep their stored
      * velocity and d = 0 */
+    ROWS
     for (j = 0; j < ny; j++)
         for (i = 0; i <= nx; i++) {
             int f = FU(o, i, j);
@@ -1091,6 +1112,7 @@ static void iterate(orc *o, const level *prev, const level *old, level *nw, doub
                 o->du[f] = 0.0;
             }
         }
+    ROWS
     for (j = 0; j <= ny; j++)
         for (i = 0; i < nx; i++) {
             int f = FV(o, i, j);
@@ -1103,18 +1125,21 @@ static void iterate(orc *o, const level *prev, const level *old, level *nw, doub
         }
 
     /* pressure */
+    ROWS
     for (j = 0; j < ny; j++)
         for (i = 0; i < nx; i++)
             if (fluid(o, i, j))
                 nw->p[CI(o, i, j)] = pressure(o, prev, old, nw->T[CI(o, i, j)], i, j);
 
     /* velocity corrections, Eqs. pl18, pl19 */
+    ROWS
     for (j = 0; j < ny; j++)
         for (i = 0; i <= nx; i++)
             if (u_active(o, i, j)) {
                 int f = FU(o, i, j);
                 nw->u[UI(o, i, j)] = o->uhat[f] - o->du[f] * (Pc(o, nw, i, j) - Pc(o, nw, i - 1, j));
             }
+    ROWS
     for (j = 0; j <= ny; j++)
         for (i = 0; i < nx; i++)
             if (v_active(o, i, j)) {
@@ -1123,6 +1148,7 @@ static void iterate(orc *o, const level *prev, const level *old, level *nw, doub
             }
 
     /* equation of state and diffusion coefficient */
+    ROWS
     for (j = 0; j < ny; j++)
         for (i = 0; i < nx; i++)
             if (fluid(o, i, j)) {
@@ -1243,4 +1269,13 @@ int orc_run(const orc_problem *P, double *u, double *v, double *p, double *T,
     if (iters_last) *iters_last = it;
     orc_free(&o);
     return 0;
+}
+
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

@@ -79,6 +79,10 @@ double orc_psi_c(double f1, double f2, double f3, double f4,
 double orc_splitmix_uniform(uint64_t seed, int field, int i, int j);
 double orc_gam_harmonic(double ga, double gb, double da, double db);
 
+/* Threads the row loops of orc_run use: 1 in the plain build, the OpenMP
+ * thread count in the row-parallel build (-fopenmp). */
+int orc_threads(void);
+
 #ifdef __cplusplus
 }
 #endif
