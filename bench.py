@@ -99,6 +99,22 @@ def workload():
     return WORKLOADS[_ARGS.workload if _ARGS else "c2"](W)
 
 
+def small_case():
+    import workloads as W
+    return W.c1_small()
+
+
+def device_bytes_of(make):
+    """(object, device bytes its creation took): the drop in the driver's
+    free-memory count around make(), which allocates through cudaMalloc."""
+    import torch
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    obj = make()
+    torch.cuda.synchronize()
+    return obj, free0 - torch.cuda.mem_get_info()[0]
+
+
 def config_of(case, flush: str):
     scheme = ("implicit" if case.implicit else "explicit") + ("-tvd" if case.tvd else "-upwind")
     return {"workload": f"{case.name}: {case.nx}x{case.ny} channel, {len(case.rects)} square obstacle(s), "
@@ -393,7 +409,8 @@ def run_ours(args, rank, world, local_rank):
 
     case = workload()
     stream = torch.cuda.current_stream()
-    s = sim.Simulation(case, stream=stream.cuda_stream)
+    sim.Simulation(small_case(), stream=stream.cuda_stream).close()   # loads the GPU code first
+    s, dev_bytes = device_bytes_of(lambda: sim.Simulation(case, stream=stream.cuda_stream))
     for _ in range(args.warmup):
         s.step(1)
     peak_fp64 = sim.alu_peak_gflops("fp64", 30.0, stream.cuda_stream)
@@ -429,7 +446,8 @@ def run_ours(args, rank, world, local_rank):
     import workloads as W
 
     def variant(precision, dtype):
-        sv = sim.Simulation(case.replace(precision=precision), stream=stream.cuda_stream)
+        sv, v_bytes = device_bytes_of(lambda: sim.Simulation(case.replace(precision=precision),
+                                                             stream=stream.cuda_stream))
         for _ in range(args.warmup):
             sv.step(1)
         if dist:
@@ -449,6 +467,7 @@ def run_ours(args, rank, world, local_rank):
                 "ms_per_step": round(v_ms / args.steps, 5), "dtype": dtype,
                 "max_rel_err_vs_fp64": {k: float(f"{x:.3e}") for k, x in err.items()},
                 "error_after_steps": args.warmup + args.steps,
+                "device_bytes_per_cell": round(v_bytes / case.cells, 1),
                 "kernel_ms_avg": {k: round(ms / n, 5) for k, (ms, n) in vprof.items() if n}}
 
     # FP32 assembly and relaxation; FP64 pressure accumulation, EOS and residuals
@@ -532,6 +551,7 @@ def run_ours(args, rank, world, local_rank):
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps},
             "mcell_iterations_per_s": round(value * case.iters, 3),
+            "device_bytes_per_cell": round(dev_bytes / case.cells, 1),
             "gpu_launches": int(launches),
             "kernel_ms_avg": {k: round(ms / n, 5) for k, (ms, n) in prof.items() if n},
             "kernel_timing": f"separate pass of {prof_steps} steps with per-launch CUDA events",
