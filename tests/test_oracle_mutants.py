@@ -56,6 +56,7 @@ MUTANTS = {
                                  "if (mi != ai && o->P->zeta_coef > 0.0) {"),
     "jump_normal_size_swapped": ("double h = 0.5 * (ni != ci ? DX(o, ci) : DY(o, cj));",
                                  "double h = 0.5 * (ni != ci ? DY(o, cj) : DX(o, ci));"),
+    "rho_u_downwind": ("    double val = upwind(rl, rr, vel);\n", "    double val = upwind(rr, rl, vel);\n"),
     "rho_v_tvd_velocity": (
         "DY(o, j - 2), DY(o, j - 1), DY(o, j), DY(o, j + 1), vel) * (rt - rb);",
         "DY(o, j - 2), DY(o, j - 1), DY(o, j), DY(o, j + 1), -vel) * (rt - rb);"),

@@ -297,6 +297,81 @@ def test_mass_conservation_at_loop2_convergence(implicit, tvd):
     assert abs((mass1 - mass0) - dt * (f_in - f_out)) < 1e-10 * dt * f_in
 
 
+# ------------------------------- P7: continuity cell by cell at the loop-2 fixed point
+
+def _fluid_mask(c):
+    fluid = np.ones((c.ny, c.nx), dtype=bool)
+    for i0, j0, i1, j1 in c.rects:
+        fluid[j0:j1, i0:i1] = False
+    return fluid
+
+
+@pytest.mark.parametrize("implicit", [False, True])
+def test_continuity_holds_in_every_cell_at_loop2_convergence(implicit):
+    # What Eqs. pl23, pl24 with the corrections of Eqs. pl18, pl19 solve,
+    # restated independently: at a fixed point of loop 2 every fluid cell
+    # satisfies discrete continuity, its mass change over dt plus the net
+    # outflow through its faces of the upwind fluxes F^x = rho^u u dy,
+    # F^y = rho^v v dx (Eqs. pl8-pl11 with psi = 0), with rho = p/T (Eq. pl5)
+    # and the face densities of the converged iterate (R10).  The global mass
+    # balance above is the sum of these; this check sees every cell and face.
+    c = W.channel(48, 16, 4, mach_in=1.5, reynolds=50.0, implicit=implicit, tvd=False, seed=9)
+    s, _, _ = oracle.run(c, nsteps=5)
+    s1, res, it = oracle.run(c.replace(iters=400, tol=1e-14), s, nsteps=1)
+    assert res.max() < 1e-12 and it < 400
+    dt = oracle.coefficients(c)["dt"]
+    dx, dy = c.lx / c.nx, c.ly / c.ny
+    rho0, rho = s["p"] / s["T"], s1["p"] / s1["T"]
+    # x faces: the inflow ghost holds p = T = 1, the outflow ghost a copy
+    rx = np.concatenate([np.ones((c.ny, 1)), rho, rho[:, -1:]], axis=1)
+    ry = np.concatenate([rho[:1], rho, rho[-1:]], axis=0)       # wall faces carry v = 0
+    u, v = s1["u"], s1["v"]
+    Fx = np.where(u > 0, rx[:, :-1], rx[:, 1:]) * u * dy
+    Fy = np.where(v > 0, ry[:-1], ry[1:]) * v * dx
+    assert np.all(v[0] == 0) and np.all(v[-1] == 0)
+    resid = (rho - rho0) * dx * dy / dt + (Fx[:, 1:] - Fx[:, :-1]) + (Fy[1:] - Fy[:-1])
+    scale = oracle.coefficients(c)["u_in"] * dy
+    assert np.abs(resid[_fluid_mask(c)]).max() < 1e-10 * scale
+    # and the check is not empty: the flow is unsteady and crosses the cells
+    assert np.abs((rho - rho0)[_fluid_mask(c)]).max() * dx * dy / dt > 1e-4 * scale
+
+
+# ------------------------------ P10: TVD with every limiter zero is upwind
+
+@pytest.mark.parametrize("implicit", [False, True])
+def test_tvd_is_upwind_bit_for_bit_when_every_limiter_is_zero(implicit):
+    # With every field alternating in sign from node to node (a checkerboard
+    # about a mean), each ratio of successive differences is negative, so the
+    # Van Leer limiter (Eq. pl15_2, reading R2) is 0 on every face.  One
+    # loop-2 iteration of one step then evaluates every limiter on that state
+    # (the fluxes, the explicit terms of level n-1 and the coefficient forms),
+    # and the TVD forms of Eqs. pl10, pl11, pl15, pl15_11, pl31, pl31_1 must
+    # give the upwind scheme's bits.  From a smooth state they must not.
+    n = 8
+
+    def run(tvd, start):
+        c = W.closed_box(n=n, implicit=implicit, tvd=tvd).replace(rects=[], iters=1)
+        s = oracle.init(c)
+        jc, ic = np.mgrid[0:n, 0:n]
+        ju, iu = np.mgrid[0:n, 0:n + 1]
+        jv, iv = np.mgrid[0:n + 1, 0:n]
+        if start == "checkerboard":
+            f = lambda j, i: (-1.0) ** (i + j)
+        else:
+            f = lambda j, i: np.sin(0.7 * i + 0.3) * np.cos(0.5 * j - 0.2)
+        s["T"] = 1.0 + 0.1 * f(jc, ic)
+        s["p"] = 1.0 + 0.05 * f(jc, ic)
+        s["u"][:, 1:n] = 0.2 + 0.05 * f(ju, iu)[:, 1:n]
+        s["v"][1:n, :] = -0.1 + 0.05 * f(jv, iv)[1:n, :]
+        return oracle.run(c, s, nsteps=1)[0]
+
+    a, b = run(True, "checkerboard"), run(False, "checkerboard")
+    for k in "uvpT":
+        assert np.array_equal(a[k], b[k]), k
+    a, b = run(True, "smooth"), run(False, "smooth")
+    assert max(np.abs(a[k] - b[k]).max() for k in "uvpT") > 1e-8
+
+
 # ---------------- P10: explicit and implicit convection agree to first order in dt
 
 @pytest.mark.parametrize("tvd", [False, True])
