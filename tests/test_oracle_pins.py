@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 import workloads as W
+from discrete_checks import continuity_residual, fluid_mask
 
 SCHEMES = [(False, False), (False, True), (True, False), (True, True)]   # (implicit, tvd)
 
@@ -299,41 +300,26 @@ def test_mass_conservation_at_loop2_convergence(implicit, tvd):
 
 # ------------------------------- P7: continuity cell by cell at the loop-2 fixed point
 
-def _fluid_mask(c):
-    fluid = np.ones((c.ny, c.nx), dtype=bool)
-    for i0, j0, i1, j1 in c.rects:
-        fluid[j0:j1, i0:i1] = False
-    return fluid
-
-
 @pytest.mark.parametrize("implicit", [False, True])
 def test_continuity_holds_in_every_cell_at_loop2_convergence(implicit):
     # What Eqs. pl23, pl24 with the corrections of Eqs. pl18, pl19 solve,
-    # restated independently: at a fixed point of loop 2 every fluid cell
-    # satisfies discrete continuity, its mass change over dt plus the net
-    # outflow through its faces of the upwind fluxes F^x = rho^u u dy,
-    # F^y = rho^v v dx (Eqs. pl8-pl11 with psi = 0), with rho = p/T (Eq. pl5)
-    # and the face densities of the converged iterate (R10).  The global mass
-    # balance above is the sum of these; this check sees every cell and face.
+    # restated independently (tests/discrete_checks.py): at a fixed point of
+    # loop 2 every fluid cell satisfies discrete continuity with the upwind
+    # face densities of the converged iterate (R10) and rho = p/T (Eq. pl5).
+    # The global mass balance above is the sum of these; this sees every face.
     c = W.channel(48, 16, 4, mach_in=1.5, reynolds=50.0, implicit=implicit, tvd=False, seed=9)
     s, _, _ = oracle.run(c, nsteps=5)
     s1, res, it = oracle.run(c.replace(iters=400, tol=1e-14), s, nsteps=1)
     assert res.max() < 1e-12 and it < 400
-    dt = oracle.coefficients(c)["dt"]
-    dx, dy = c.lx / c.nx, c.ly / c.ny
+    assert np.all(s1["v"][0] == 0) and np.all(s1["v"][-1] == 0)
+    coef = oracle.coefficients(c)
     rho0, rho = s["p"] / s["T"], s1["p"] / s1["T"]
-    # x faces: the inflow ghost holds p = T = 1, the outflow ghost a copy
-    rx = np.concatenate([np.ones((c.ny, 1)), rho, rho[:, -1:]], axis=1)
-    ry = np.concatenate([rho[:1], rho, rho[-1:]], axis=0)       # wall faces carry v = 0
-    u, v = s1["u"], s1["v"]
-    Fx = np.where(u > 0, rx[:, :-1], rx[:, 1:]) * u * dy
-    Fy = np.where(v > 0, ry[:-1], ry[1:]) * v * dx
-    assert np.all(v[0] == 0) and np.all(v[-1] == 0)
-    resid = (rho - rho0) * dx * dy / dt + (Fx[:, 1:] - Fx[:, :-1]) + (Fy[1:] - Fy[:-1])
-    scale = oracle.coefficients(c)["u_in"] * dy
-    assert np.abs(resid[_fluid_mask(c)]).max() < 1e-10 * scale
+    resid = continuity_residual(c, rho0, rho, s1["u"], s1["v"], coef["dt"])
+    scale = coef["u_in"] * c.ly / c.ny
+    fluid = fluid_mask(c)
+    assert np.abs(resid[fluid]).max() < 1e-10 * scale
     # and the check is not empty: the flow is unsteady and crosses the cells
-    assert np.abs((rho - rho0)[_fluid_mask(c)]).max() * dx * dy / dt > 1e-4 * scale
+    assert np.abs((rho - rho0)[fluid]).max() * (c.lx / c.nx) * (c.ly / c.ny) / coef["dt"] > 1e-4 * scale
 
 
 # ------------------------------ P10: TVD with every limiter zero is upwind

@@ -11,6 +11,7 @@ import pytest
 import oracle
 import paper_1802_04243_gb300 as sim
 import workloads as W
+from discrete_checks import continuity_residual, fluid_mask
 from paper_1802_04243_gb300 import build
 
 pytestmark = pytest.mark.gpu
@@ -190,6 +191,46 @@ def test_field_view_is_zero_copy_and_matches_host_copy():
         assert np.array_equal(t[2:-2, 2:-2].cpu().numpy(), host)
 
 
+# --------------------------------------- TVD with every Van Leer limiter zero
+
+def _alternating_start(case, n):
+    """A state in which every field alternates in sign about its mean from
+    node to node, so every ratio of successive differences is negative and
+    every Van Leer limiter (Eq. pl15_2) is 0."""
+    s = oracle.init(case)
+    jc, ic = np.mgrid[0:n, 0:n]
+    ju, iu = np.mgrid[0:n, 0:n + 1]
+    jv, iv = np.mgrid[0:n + 1, 0:n]
+    s["T"] = 1.0 + 0.1 * (-1.0) ** (ic + jc)
+    s["p"] = 1.0 + 0.05 * (-1.0) ** (ic + jc)
+    s["u"][:, 1:n] = (0.2 + 0.05 * (-1.0) ** (iu + ju))[:, 1:n]
+    s["v"][1:n, :] = (-0.1 + 0.05 * (-1.0) ** (iv + jv))[1:n, :]
+    return s
+
+
+@pytest.mark.parametrize("precision", [W.FP64, W.MIXED, W.DF64], ids=["fp64", "mixed", "df64"])
+@pytest.mark.parametrize("implicit", [False, True])
+def test_tvd_with_every_limiter_zero_gives_the_upwind_bits(implicit, precision):
+    # One loop-2 iteration of one step from the alternating state evaluates
+    # every limiter (face densities, explicit terms of level n-1, coefficient
+    # forms) on that state: the TVD kernels must give the upwind kernels' bits,
+    # and the FP64 result the oracle's TVD result
+    n = 8
+    case = W.closed_box(n=n, implicit=implicit, tvd=True).replace(rects=[], iters=1, precision=precision)
+    start = _alternating_start(case, n)
+    out = {}
+    for tvd in (True, False):
+        with sim.Simulation(case.replace(tvd=tvd)) as s:
+            s.set_fields(start)
+            s.step(1)
+            out[tvd] = s.fields()
+    for k in "uvpT":
+        assert np.array_equal(out[True][k], out[False][k]), k
+    if precision == W.FP64:
+        o, _, _ = oracle.run(case, start, nsteps=1)
+        assert_parity(out[True], o, what="alternating start, TVD")
+
+
 # ------------------------------------------------------------ full sizes
 
 def test_parity_1024x256_implicit_100_steps():
@@ -204,6 +245,33 @@ def test_parity_full_size_one_step(make):
     case = make()
     g, o, *_ = run_both(case, 1)
     assert_parity(g, o)
+
+
+@pytest.mark.parametrize("make", [W.c2_medium, W.c4_paper_scale], ids=["c2", "c4"])
+def test_continuity_in_every_cell_at_the_loop2_fixed_point_full_size(make):
+    # A property that holds at any size, checked on the GPU's own FP64 result
+    # at the full sizes: with loop 2 iterated to its fixed point, every fluid
+    # cell satisfies discrete continuity (what Eqs. pl23, pl24 with the
+    # corrections of Eqs. pl18, pl19 solve, with the upwind fluxes of Eqs.
+    # pl8-pl11), restated in numpy in tests/discrete_checks.py
+    case = make()
+    with sim.Simulation(case) as s:
+        s.step(3)                                  # leave the start state
+        start = s.fields()
+    with sim.Simulation(case.replace(iters=1000, tol=1e-13)) as s:
+        s.set_fields(start)
+        rho0 = s.fields(("rho",))["rho"]
+        s.step(1)
+        g = s.fields(("u", "v", "p", "T", "rho"))
+        res, it, st = s.residuals()
+        coef = s.coefficients()
+    assert st == sim.SIM_OK and it < 1000, (res, it)
+    assert np.all(g["v"][0] == 0) and np.all(g["v"][-1] == 0)
+    resid = continuity_residual(case, rho0, g["rho"], g["u"], g["v"], coef["dt"])
+    scale = coef["u_in"] * case.ly / case.ny
+    fluid = fluid_mask(case)
+    assert np.abs(resid[fluid]).max() < 1e-10 * scale
+    assert np.abs((g["rho"] - rho0)[fluid]).max() * case.lx / case.nx * case.ly / case.ny / coef["dt"] > 1e-6 * scale
 
 
 # ------------------------------------------------------------ mixed precision
