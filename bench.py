@@ -34,17 +34,18 @@ UNIT = "Mcell-steps/s"
 # The dominant kernel, k_assemble (FP64, implicit upwind), is bound by GB300's
 # FP64 pipe.  Its work per cell and loop-2 iteration is counted by ncu on one
 # launch for the 2048x512 channel (1,048,576 cells): DFMA, DADD and DMUL thread
-# instructions 53.62 M, 54.05 M, 44.34 M.
-ASSEMBLE_FP64_INST_PER_CELL = {"dfma": 51.14, "dadd": 51.55, "dmul": 42.29}
-# DRAM bytes of that launch per cell (127.4 MB read + 20.8 MB written).
-ASSEMBLE_DRAM_BYTES_PER_CELL = 141.3
+# instructions 53.62 M, 48.16 M, 44.34 M.
+ASSEMBLE_FP64_INST_PER_CELL = {"dfma": 51.14, "dadd": 45.93, "dmul": 42.29}
+# DRAM bytes of that launch per cell (143.3 MB read + 23.6 MB written).
+ASSEMBLE_DRAM_BYTES_PER_CELL = 159.2
 # ncu: sm__pipe_fp64_cycles_active of that launch, fraction of peak.
-ASSEMBLE_FP64_PIPE_ACTIVE = 0.854
+ASSEMBLE_FP64_PIPE_ACTIVE = 0.852
 # Algorithmic HBM traffic of the kernel per cell: reads u, v, p, T, rho, Gamma of
 # the previous iterate, u, v, T, rho of level n-1 and the face arrays F^x, F^y,
-# D^T_x, D^T_y, B Gamma (corner), B Gamma dy/dx, B Gamma dx/dy and the two
-# cell-centre mass fluxes (19 doubles); writes T, u^, d^u, v^, d^v (5 doubles).
-ASSEMBLE_BYTES_PER_CELL = 24 * 8
+# D^T_x, D^T_y, B Gamma (corner), B Gamma dy/dx, B Gamma dx/dy, the two
+# cell-centre mass fluxes and the two cell pair sums u_i + u_{i+1}, v_j + v_{j+1}
+# (21 doubles); writes T, u^, d^u, v^, d^v (5 doubles).
+ASSEMBLE_BYTES_PER_CELL = 26 * 8
 # GB300 FP64 pipe: 2 FP64 thread instructions per cycle per SM (ncu's
 # peak_sustained for DFMA), 152 SMs.
 FP64_INST_PER_CYCLE_PER_SM = 2

@@ -416,6 +416,7 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     w.Fx = q; q += nelem; w.Fy = q; q += nelem; w.DTx = q; q += nelem; w.DTy = q; q += nelem;
     w.Bgc = q; q += nelem; w.Bgx = q; q += nelem; w.Bgy = q; q += nelem;
     w.Fbu = q; q += nelem; w.Fbv = q; q += nelem;
+    w.Su = q; q += nelem; w.Sv = q; q += nelem;
     w.uhat = q; q += nelem; w.du = q; q += nelem;
     w.vhat = q; q += nelem; w.dv = q; q += nelem; w.uexp = q; q += nelem; w.vexp = q; q += nelem;
     w.Texp = q;

@@ -474,7 +474,7 @@ R *carve_levels(R *q, size_t nelem, LevelT<R> lv[3], WorkT<R> &w)
         for (R **x : f) { *x = q; q += nelem; }
     }
     R **a[kWorkArrays] = {&w.ru_dy, &w.rv_dx, &w.Fx, &w.Fy, &w.DTx, &w.DTy, &w.Bgc, &w.Bgx, &w.Bgy,
-                          &w.Fbu, &w.Fbv, &w.uhat, &w.du, &w.vhat, &w.dv, &w.uexp, &w.vexp, &w.Texp,
+                          &w.Fbu, &w.Fbv, &w.Su, &w.Sv, &w.uhat, &w.du, &w.vhat, &w.dv, &w.uexp, &w.vexp, &w.Texp,
                           &w.psTx, &w.psTy, &w.psUx, &w.psUyU, &w.psUyD, &w.psVy, &w.psVxU, &w.psVxD};
     for (R **x : a) { *x = q; q += nelem; }
     return q;

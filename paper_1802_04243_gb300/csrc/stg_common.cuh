@@ -102,6 +102,8 @@ struct WorkT {
     R *Bgx, *Bgy;                  // B Gamma dy/dx and B Gamma dx/dy of cell (i,j): normal-stress conductances
     R *Fbu, *Fbv;                  // mass fluxes through the centre of cell (i,j) between the u (v) control
                                    // volumes: rho 0.5 (u_i + u_{i+1}) dy and rho 0.5 (v_j + v_{j+1}) dx
+    R *Su, *Sv;                    // u_i + u_{i+1} and v_j + v_{j+1} of cell (i,j), the pair sums of the
+                                   // energy source's dv/dx, du/dy (stored by the FP64 sweep only)
     R *uhat, *du, *vhat, *dv;      // pseudo velocities and d (Eqs. pl14, pl20, pl21)
     // TVD limiters of one level, one evaluation per face (Eqs. pl15_1, pl15_2;
     // 0 where the face's stencil is not all unknowns): T on the x and y faces;
@@ -111,7 +113,7 @@ struct WorkT {
     R *uexp, *vexp, *Texp;         // explicit convective terms (Eqs. pl15_11, pl31_1)
 };
 
-constexpr int kWorkArrays = 26;
+constexpr int kWorkArrays = 28;
 // Arrays of one pool: three levels of six fields, then the scratch.
 constexpr int kPoolArrays = 3 * 6 + kWorkArrays;
 

@@ -444,8 +444,13 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         // mass fluxes through the cell centre, the face between the u (v)
         // control volumes of faces i and i+1 (j and j+1), with the mean
         // velocity of the two faces
-        w.Fbu[c] = (u[c] + u[c + 1]) * half_size(g.y, j, dyj) * rho[c];
-        w.Fbv[c] = (v[c] + v[c + P]) * half_size(g.x, i, dxi) * rho[c];
+        const R su = u[c] + u[c + 1], sv = v[c] + v[c + P];
+        w.Fbu[c] = su * half_size(g.y, j, dyj) * rho[c];
+        w.Fbv[c] = sv * half_size(g.x, i, dxi) * rho[c];
+        if constexpr (std::is_same<R, double>::value) {
+            w.Su[c] = su;                       // the energy source's pair sums (FP64 sweep)
+            w.Sv[c] = sv;
+        }
     }
     if constexpr (TVD) {
         if (limiters) face_limiters(g, u, v, T, w, c, i, j);
@@ -576,7 +581,8 @@ __device__ __forceinline__ void explicit_terms_body(const GeoT<R> &g, const Coef
 // viscous dissipation (Eq. pl7) and pressure work; velocities off their
 // nodes are bilinear interpolations, reflected across walls.
 template <typename R, bool WALLS>
-__device__ R energy_source(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, int c, int i, int j)
+__device__ R energy_source(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &L, const WorkT<R> &w, int c,
+                           int i, int j)
 {
     const int P = g.pitch;
     const uint16_t *fl = g.flag;
@@ -591,17 +597,26 @@ __device__ R energy_source(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> 
     // the values across walls reflected.  With the interpolation weights
     // summing to one per face, (v_e - v_w) / dx reduces to three weighted pair
     // sums whose weights the axis tables hold (qlo, qmid, qhi).
-    const R *rho = L.rho;
-    const R vW0 = seen_s<R, WALLS>(v, fl, c, c - 1, F_VWALL, k.zeta, dxi, rho, c - P, c);
-    const R vW1 = seen_s<R, WALLS>(v, fl, c + P, c + P - 1, F_VWALL, k.zeta, dxi, rho, c, c + P);
-    const R vE0 = seen_s<R, WALLS>(v, fl, c, c + 1, F_VWALL, k.zeta, dxi, rho, c - P, c);
-    const R vE1 = seen_s<R, WALLS>(v, fl, c + P, c + P + 1, F_VWALL, k.zeta, dxi, rho, c, c + P);
-    const R uS0 = seen_s<R, WALLS>(u, fl, c, c - P, F_UWALL, k.zeta, dyj, rho, c - 1, c);
-    const R uS1 = seen_s<R, WALLS>(u, fl, c + 1, c + 1 - P, F_UWALL, k.zeta, dyj, rho, c, c + 1);
-    const R uN0 = seen_s<R, WALLS>(u, fl, c, c + P, F_UWALL, k.zeta, dyj, rho, c - 1, c);
-    const R uN1 = seen_s<R, WALLS>(u, fl, c + 1, c + 1 + P, F_UWALL, k.zeta, dyj, rho, c, c + 1);
-    const R dvdx = at(g.x.qmid, i) * (v[c] + v[c + P]) + at(g.x.qhi, i) * (vE0 + vE1) - at(g.x.qlo, i) * (vW0 + vW1);
-    const R dudy = at(g.y.qmid, j) * (u[c] + u[c + 1]) + at(g.y.qhi, j) * (uN0 + uN1) - at(g.y.qlo, j) * (uS0 + uS1);
+    R dvdx, dudy;
+    if constexpr (!WALLS && std::is_same<R, double>::value) {
+        // no wall in reach: the pair sums of the neighbouring cells are their
+        // own v_j + v_{j+1} and u_i + u_{i+1}, which the face kernel stored
+        // (the same operands in the same order, so the same bits)
+        dvdx = at(g.x.qmid, i) * w.Sv[c] + at(g.x.qhi, i) * w.Sv[c + 1] - at(g.x.qlo, i) * w.Sv[c - 1];
+        dudy = at(g.y.qmid, j) * w.Su[c] + at(g.y.qhi, j) * w.Su[c + P] - at(g.y.qlo, j) * w.Su[c - P];
+    } else {
+        const R *rho = L.rho;
+        const R vW0 = seen_s<R, WALLS>(v, fl, c, c - 1, F_VWALL, k.zeta, dxi, rho, c - P, c);
+        const R vW1 = seen_s<R, WALLS>(v, fl, c + P, c + P - 1, F_VWALL, k.zeta, dxi, rho, c, c + P);
+        const R vE0 = seen_s<R, WALLS>(v, fl, c, c + 1, F_VWALL, k.zeta, dxi, rho, c - P, c);
+        const R vE1 = seen_s<R, WALLS>(v, fl, c + P, c + P + 1, F_VWALL, k.zeta, dxi, rho, c, c + P);
+        const R uS0 = seen_s<R, WALLS>(u, fl, c, c - P, F_UWALL, k.zeta, dyj, rho, c - 1, c);
+        const R uS1 = seen_s<R, WALLS>(u, fl, c + 1, c + 1 - P, F_UWALL, k.zeta, dyj, rho, c, c + 1);
+        const R uN0 = seen_s<R, WALLS>(u, fl, c, c + P, F_UWALL, k.zeta, dyj, rho, c - 1, c);
+        const R uN1 = seen_s<R, WALLS>(u, fl, c + 1, c + 1 + P, F_UWALL, k.zeta, dyj, rho, c, c + 1);
+        dvdx = at(g.x.qmid, i) * (v[c] + v[c + P]) + at(g.x.qhi, i) * (vE0 + vE1) - at(g.x.qlo, i) * (vW0 + vW1);
+        dudy = at(g.y.qmid, j) * (u[c] + u[c + 1]) + at(g.y.qhi, j) * (uN0 + uN1) - at(g.y.qlo, j) * (uS0 + uS1);
+    }
     const R div = dudx + dvdy, shear = dvdx + dudy;
     // 2 (dudx^2 + dvdy^2) - 2/3 div^2 = 4/3 (dudx^2 - dudx dvdy + dvdy^2)
     const R phi = R(4.0 / 3.0) * (dudx * (dudx - dvdy) + dvdy * dvdy) + shear * shear;
@@ -657,7 +672,7 @@ __device__ R temperature(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
         a0 = k.dt * (a1 + a2 + a3 + a4) + old.rho[c] * vol;
         texp = w.Texp[c];
     }
-    const R sc = energy_source<R, WALLS>(g, k, old, c, i, j);
+    const R sc = energy_source<R, WALLS>(g, k, old, w, c, i, j);
     R src = a1 * Tw + a2 * Te + a3 * Ts + a4 * Tn + sc;
     if constexpr (!IMPL) src += texp;
     const R rhs = k.dt * src + prev.rho[c] * prev.T[c] * vol;
