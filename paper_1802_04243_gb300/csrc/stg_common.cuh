@@ -103,7 +103,7 @@ struct WorkT {
     R *Fbu, *Fbv;                  // mass fluxes through the centre of cell (i,j) between the u (v) control
                                    // volumes: rho 0.5 (u_i + u_{i+1}) dy and rho 0.5 (v_j + v_{j+1}) dx
     R *Su, *Sv;                    // u_i + u_{i+1} and v_j + v_{j+1} of cell (i,j), the pair sums of the
-                                   // energy source's dv/dx, du/dy (stored by the FP64 sweep only)
+                                   // energy source's dv/dx, du/dy (stored by the FP64 and DF64 sweeps)
     R *uhat, *du, *vhat, *dv;      // pseudo velocities and d (Eqs. pl14, pl20, pl21)
     // TVD limiters of one level, one evaluation per face (Eqs. pl15_1, pl15_2;
     // 0 where the face's stencil is not all unknowns): T on the x and y faces;

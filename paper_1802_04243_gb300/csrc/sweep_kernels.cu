@@ -447,8 +447,8 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         const R su = u[c] + u[c + 1], sv = v[c] + v[c + P];
         w.Fbu[c] = su * half_size(g.y, j, dyj) * rho[c];
         w.Fbv[c] = sv * half_size(g.x, i, dxi) * rho[c];
-        if constexpr (std::is_same<R, double>::value) {
-            w.Su[c] = su;                       // the energy source's pair sums (FP64 sweep)
+        if constexpr (!std::is_same<R, float>::value) {
+            w.Su[c] = su;                       // the energy source's pair sums (FP64, DF64)
             w.Sv[c] = sv;
         }
     }
@@ -598,7 +598,7 @@ __device__ R energy_source(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> 
     // summing to one per face, (v_e - v_w) / dx reduces to three weighted pair
     // sums whose weights the axis tables hold (qlo, qmid, qhi).
     R dvdx, dudy;
-    if constexpr (!WALLS && std::is_same<R, double>::value) {
+    if constexpr (!WALLS && !std::is_same<R, float>::value) {
         // no wall in reach: the pair sums of the neighbouring cells are their
         // own v_j + v_{j+1} and u_i + u_{i+1}, which the face kernel stored
         // (the same operands in the same order, so the same bits)
