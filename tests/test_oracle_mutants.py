@@ -57,6 +57,13 @@ MUTANTS = {
     "jump_normal_size_swapped": ("double h = 0.5 * (ni != ci ? DX(o, ci) : DY(o, cj));",
                                  "double h = 0.5 * (ni != ci ? DY(o, cj) : DX(o, ci));"),
     "rho_u_downwind": ("    double val = upwind(rl, rr, vel);\n", "    double val = upwind(rr, rl, vel);\n"),
+    # both face densities anti-upwinded in the same way keeps the x/y symmetry:
+    # only the observed order of the TVD scheme sees it
+    "rho_tvd_difference_sign_both_axes": [
+        ("DX(o, i - 2), DX(o, i - 1), DX(o, i), DX(o, i + 1), vel) * (rr - rl);",
+         "DX(o, i - 2), DX(o, i - 1), DX(o, i), DX(o, i + 1), vel) * (rl - rr);"),
+        ("DY(o, j - 2), DY(o, j - 1), DY(o, j), DY(o, j + 1), vel) * (rt - rb);",
+         "DY(o, j - 2), DY(o, j - 1), DY(o, j), DY(o, j + 1), vel) * (rb - rt);")],
     "rho_v_tvd_velocity": (
         "DY(o, j - 2), DY(o, j - 1), DY(o, j), DY(o, j + 1), vel) * (rt - rb);",
         "DY(o, j - 2), DY(o, j - 1), DY(o, j), DY(o, j + 1), -vel) * (rt - rb);"),
@@ -71,11 +78,16 @@ def source():
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_planted_mistake_is_caught(name, source, tmp_path):
-    before, after = MUTANTS[name]
-    assert source.count(before) == 1, f"mutation site of {name} not found once"
+    edits = MUTANTS[name]
+    if isinstance(edits, tuple):
+        edits = [edits]
+    mutated = source
+    for before, after in edits:
+        assert source.count(before) == 1, f"mutation site of {name} not found once"
+        mutated = mutated.replace(before, after)
     shutil.copy(HDR, tmp_path)
     csrc = tmp_path / "mutant.c"
-    csrc.write_text(source.replace(before, after))
+    csrc.write_text(mutated)
     lib = tmp_path / "libmutant.so"
     subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
                            "-o", str(lib), str(csrc), "-lm"])

@@ -322,6 +322,63 @@ def test_continuity_holds_in_every_cell_at_loop2_convergence(implicit):
     assert np.abs((rho - rho0)[fluid]).max() * (c.lx / c.nx) * (c.ly / c.ny) / coef["dt"] > 1e-4 * scale
 
 
+# ------------------------------------ P8: observed order of the convection schemes
+
+def _graded_channel(n, tvd, implicit, dt):
+    """Channel of 2n x n cells, inflow profiles u = 1.5 U 4y(1-y),
+    T = 1 + 0.2 sin(pi y), walls at T = 1, low Mach and Re 20; loop 2 is
+    iterated to its fixed point every step."""
+    ny = n
+    y = (np.arange(ny) + 0.5) / ny
+    mach = 0.3
+    u_scale = mach * math.sqrt(1.4 / 2.0)
+    return W.Case(name="graded", nx=2 * n, ny=ny, lx=2.0, ly=1.0, mach_in=mach, reynolds=20.0,
+                  side_kind=(W.INFLOW, W.OUTFLOW, W.WALL, W.WALL), implicit=implicit, tvd=tvd,
+                  inflow_u=1.5 * u_scale * 4 * y * (1 - y), inflow_T=1.0 + 0.2 * np.sin(math.pi * y),
+                  inflow_p=np.ones(ny), perturb=0.0, iters=300, tol=1e-12, dt=dt)
+
+
+def _smooth_start(c):
+    """The inflow profiles carried through the channel, T modulated along x."""
+    s = oracle.init(c)
+    y = (np.arange(c.ny) + 0.5) / c.ny
+    x = (np.arange(c.nx) + 0.5) * c.lx / c.nx
+    s["u"] = np.repeat(c.inflow_u[:, None], c.nx + 1, axis=1)
+    s["v"][:] = 0.0
+    s["p"][:] = 1.0
+    s["T"] = 1.0 + 0.2 * np.sin(math.pi * y)[:, None] * (1.0 + 0.5 * np.sin(2 * math.pi * x / c.lx))[None, :]
+    return s
+
+
+def _observed_order(tvd, implicit, dt_power, t_end=0.4):
+    # T at t_end on 16x8, 32x16 and 64x32 cells with dt proportional to
+    # h^dt_power; fine solutions averaged 2x2 onto the coarser cells; order
+    # from the ratio of successive differences (L1 norm)
+    sols = []
+    for n in (8, 16, 32):
+        nsteps = 8 * (n // 8) ** dt_power
+        c = _graded_channel(n, tvd, implicit, t_end / nsteps)
+        s, res, _ = oracle.run(c, _smooth_start(c), nsteps=nsteps)
+        assert res.max() < 1e-11
+        sols.append(s["T"])
+    coarsen = lambda a: 0.25 * (a[0::2, 0::2] + a[1::2, 0::2] + a[0::2, 1::2] + a[1::2, 1::2])
+    a, b, c = sols[0], coarsen(sols[1]), coarsen(coarsen(sols[2]))
+    return math.log2(np.abs(a - b).mean() / np.abs(b - c).mean())
+
+
+@pytest.mark.parametrize("implicit", [True, False])
+def test_observed_order_of_upwind_and_tvd_convection(implicit):
+    # Upwind faces (Eqs. pl15, pl31 with psi = 0; pl15_11, pl31_1) are first
+    # order in space; Van Leer faces (Eqs. pl15_1, pl15_2) second order on
+    # smooth data away from extrema and boundaries (R9 makes them upwind next
+    # to walls and the inflow), so refined with dt ~ h^2 their observed order
+    # is well above one.  Diffusion and sources are central in both.
+    p_up = _observed_order(False, implicit, 1)
+    p_tvd = _observed_order(True, implicit, 2)
+    assert 0.6 < p_up < 1.3, p_up
+    assert p_tvd > 1.4 and p_tvd > p_up + 0.4, (p_up, p_tvd)
+
+
 # ------------------------------ P10: TVD with every limiter zero is upwind
 
 @pytest.mark.parametrize("implicit", [False, True])
