@@ -322,6 +322,68 @@ def test_continuity_holds_in_every_cell_at_loop2_convergence(implicit):
     assert np.abs((rho - rho0)[fluid]).max() * (c.lx / c.nx) * (c.ly / c.ny) / coef["dt"] > 1e-4 * scale
 
 
+# ------------------------- P9: one cell's energy equation written out by hand
+
+def test_temperature_of_interior_cells_from_the_printed_equations():
+    # Eqs. pl28-pl33 for the implicit upwind scheme on a uniform 10 x 8 box,
+    # evaluated here term by term for every cell two or more cells from the
+    # walls (no reflection in reach), after one loop-2 iteration of one step
+    # from a random state (old = level n):
+    #   F^x = rho^u u dy with the upwind rho^u (Eqs. pl8, pl10), F^y likewise;
+    #   D = C^T1_f Gamma_h dy / dx, Gamma_h the harmonic mean (Eqs. pl32, pl33);
+    #   a_W = max(0, F_w) + D_w, a_E = max(0, -F_e) + D_e, ... (Eq. pl31);
+    #   a_0 = dt (sum a + F_e - F_w + F_n - F_s) + rho dV;
+    #   S_c = (C^T2_f Gamma Phi + C^T3_f p div u) dV (Eq. pl29, reading R5),
+    #   Phi of Eq. pl7 with dv/dx, du/dy from the corner means of four nodes;
+    #   T = [dt (sum a T_nb + S_c) + rho^n T^n dV] / a_0 (Eq. pl30).
+    n_x, n_y = 10, 8
+    c = W.closed_box(n=8).replace(nx=n_x, ny=n_y, lx=2.5, ly=2.0, rects=[], implicit=True, tvd=False,
+                                  iters=1, perturb=0.0)
+    rng = np.random.default_rng(11)
+    s = oracle.init(c)
+    s["u"][:, 1:n_x] = 0.3 * rng.standard_normal((n_y, n_x - 1))
+    s["v"][1:n_y, :] = 0.3 * rng.standard_normal((n_y - 1, n_x))
+    s["T"] = 1.0 + 0.3 * rng.random((n_y, n_x))
+    s["p"] = 1.0 + 0.3 * rng.random((n_y, n_x))
+    new, _, _ = oracle.run(c, s, nsteps=1)
+    k = oracle.coefficients(c)
+    dt, dx, dy = k["dt"], c.lx / n_x, c.ly / n_y
+    u, v, T, p = s["u"], s["v"], s["T"], s["p"]
+    rho, gam = p / T, T ** k["omega"]
+    harm = lambda a, b: 2.0 * a * b / (a + b)
+    checked = 0
+    for j in range(2, n_y - 2):
+        for i in range(2, n_x - 2):
+            Fw = (rho[j, i - 1] if u[j, i] > 0 else rho[j, i]) * u[j, i] * dy
+            Fe = (rho[j, i] if u[j, i + 1] > 0 else rho[j, i + 1]) * u[j, i + 1] * dy
+            Fs = (rho[j - 1, i] if v[j, i] > 0 else rho[j, i]) * v[j, i] * dx
+            Fn = (rho[j, i] if v[j + 1, i] > 0 else rho[j + 1, i]) * v[j + 1, i] * dx
+            Dw = k["CT1f"] * harm(gam[j, i - 1], gam[j, i]) * dy / dx
+            De = k["CT1f"] * harm(gam[j, i], gam[j, i + 1]) * dy / dx
+            Ds = k["CT1f"] * harm(gam[j - 1, i], gam[j, i]) * dx / dy
+            Dn = k["CT1f"] * harm(gam[j, i], gam[j + 1, i]) * dx / dy
+            aw, ae = max(0.0, Fw) + Dw, max(0.0, -Fe) + De
+            as_, an = max(0.0, Fs) + Ds, max(0.0, -Fn) + Dn
+            dV = dx * dy
+            a0 = dt * (aw + ae + as_ + an + Fe - Fw + Fn - Fs) + rho[j, i] * dV
+            ux = (u[j, i + 1] - u[j, i]) / dx
+            vy = (v[j + 1, i] - v[j, i]) / dy
+            v_w = 0.25 * (v[j, i - 1] + v[j, i] + v[j + 1, i - 1] + v[j + 1, i])
+            v_e = 0.25 * (v[j, i] + v[j, i + 1] + v[j + 1, i] + v[j + 1, i + 1])
+            u_s = 0.25 * (u[j - 1, i] + u[j, i] + u[j - 1, i + 1] + u[j, i + 1])
+            u_n = 0.25 * (u[j, i] + u[j + 1, i] + u[j, i + 1] + u[j + 1, i + 1])
+            vx, uy = (v_e - v_w) / dx, (u_n - u_s) / dy
+            div = ux + vy
+            phi = 2.0 * (ux * ux + vy * vy) + (vx + uy) ** 2 - 2.0 / 3.0 * div * div
+            Sc = (k["CT2f"] * gam[j, i] * phi + k["CT3f"] * p[j, i] * div) * dV
+            rhs = dt * (aw * T[j, i - 1] + ae * T[j, i + 1] + as_ * T[j - 1, i] + an * T[j + 1, i] + Sc) \
+                + rho[j, i] * T[j, i] * dV
+            assert new["T"][j, i] == pytest.approx(rhs / a0, rel=1e-13), (i, j)
+            checked += 1
+    assert checked == 24
+    assert np.abs(new["T"] - T).max() > 1e-3          # the step did change T
+
+
 # ------------------------------------ P8: observed order of the convection schemes
 
 def _graded_channel(n, tvd, implicit, dt):
