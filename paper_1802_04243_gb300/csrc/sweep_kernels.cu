@@ -745,8 +745,9 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     R src = a1 * uW + a2 * uE + a3 * uS + a4 * uN + b;
     if constexpr (!IMPL) src += uexp;
     uhat = src * r;
-    // A = 1/2 for every gas model of this solver (Eq. pl37, reading R6): in
-    // FP64 A dy is the tabulated half height (the same value, no multiply)
+    // A = 1/2 for every gas model of this solver (Eq. pl37, and the ideal-gas
+    // mapping of the coefficients): in FP64 A dy is the tabulated half height
+    // (the same value, no multiply)
     R Ady;
     if constexpr (std::is_same<R, double>::value)
         Ady = half_size(g.y, j, dyj);

@@ -43,7 +43,7 @@ def hard_sphere_case(kn):
 @pytest.mark.parametrize("kn", [PAPER["Kn"][0], 0.05])
 def test_hard_sphere_coefficients_are_the_printed_ones(kn):
     # Eq. pl37 as printed; the discrete energy equation takes C^T1..3 in the
-    # c_v form (times gamma, the C^T3 work term with its sign: reading R5)
+    # c_v form (times gamma, the C^T3 work term with its sign, -(gamma - 1))
     k = oracle.coefficients(hard_sphere_case(kn))
     gam = PAPER["gamma"][0]
     assert k["A"] == PAPER["A"][0]

@@ -139,7 +139,7 @@ def test_ideal_gas_mapping_reduces_to_hard_sphere_constants():
     assert hs["CT3f"] == pytest.approx(-(gam - 1.0), rel=1e-14)
 
 
-# ------------------------------------------------- P1: uniform flow is steady
+# ------------------------------------------------- uniform flow is steady
 
 @pytest.mark.parametrize("implicit,tvd", SCHEMES)
 def test_uniform_flow_is_preserved(implicit, tvd):
@@ -153,7 +153,7 @@ def test_uniform_flow_is_preserved(implicit, tvd):
     assert res.max() < 1e-13
 
 
-# ------------------------------------------------- P2: mirror symmetry in y
+# ------------------------------------------------- mirror symmetry in y
 
 @pytest.mark.parametrize("implicit,tvd", SCHEMES)
 def test_mirror_symmetry_about_mid_height(implicit, tvd):
@@ -190,7 +190,7 @@ def test_rounding_sensitivity_per_scheme():
     assert _growth(c.replace(implicit=True, tvd=True), 40) > 1e-8
 
 
-# ------------------------------ P3: transpose symmetry (pins the unprinted u equation)
+# ------------------------------ transpose symmetry (pins the unprinted u equation)
 
 def _box_pair(implicit, tvd, zeta_coef=0.0, tau_coef=0.0):
     rng = np.random.default_rng(11)
@@ -233,7 +233,7 @@ def test_transposed_problem_gives_transposed_fields(implicit, tvd, slip):
     assert np.abs(ra["u"] - sa["u"]).max() > 1e-2
 
 
-# ------------------------------------------------- P4: plane Couette flow
+# ------------------------------------------------- plane Couette flow
 
 def test_couette_flow_profile():
     # Fully developed compressible Couette flow between isothermal walls at
@@ -255,7 +255,7 @@ def test_couette_flow_profile():
     assert res.max() < 1e-9
 
 
-# ------------------------------------------------- P5: plane Poiseuille flow
+# ------------------------------------------------- plane Poiseuille flow
 
 def test_poiseuille_flow_profile():
     # Body-force driven flow (rho g_x in Eq. pl2, added to b^u) between resting
@@ -276,7 +276,7 @@ def test_poiseuille_flow_profile():
     assert res.max() < 1e-6
 
 
-# ------------------------------------------------- P6: global mass conservation
+# ------------------------------------------------- global mass conservation
 
 @pytest.mark.parametrize("implicit,tvd", SCHEMES)
 def test_mass_conservation_at_loop2_convergence(implicit, tvd):
@@ -298,14 +298,15 @@ def test_mass_conservation_at_loop2_convergence(implicit, tvd):
     assert abs((mass1 - mass0) - dt * (f_in - f_out)) < 1e-10 * dt * f_in
 
 
-# ------------------------------- P7: continuity cell by cell at the loop-2 fixed point
+# ------------------------------- continuity cell by cell at the loop-2 fixed point
 
 @pytest.mark.parametrize("implicit", [False, True])
 def test_continuity_holds_in_every_cell_at_loop2_convergence(implicit):
     # What Eqs. pl23, pl24 with the corrections of Eqs. pl18, pl19 solve,
     # restated independently (tests/discrete_checks.py): at a fixed point of
     # loop 2 every fluid cell satisfies discrete continuity with the upwind
-    # face densities of the converged iterate (R10) and rho = p/T (Eq. pl5).
+    # face densities of the converged iterate (the pressure equation takes them
+    # from the previous iterate) and rho = p/T (Eq. pl5).
     # The global mass balance above is the sum of these; this sees every face.
     c = W.channel(48, 16, 4, mach_in=1.5, reynolds=50.0, implicit=implicit, tvd=False, seed=9)
     s, _, _ = oracle.run(c, nsteps=5)
@@ -322,7 +323,7 @@ def test_continuity_holds_in_every_cell_at_loop2_convergence(implicit):
     assert np.abs((rho - rho0)[fluid]).max() * (c.lx / c.nx) * (c.ly / c.ny) / coef["dt"] > 1e-4 * scale
 
 
-# ------------------------- P9: one cell's energy equation written out by hand
+# ------------------------- one cell's energy equation written out by hand
 
 def test_temperature_of_interior_cells_from_the_printed_equations():
     # Eqs. pl28-pl33 for the implicit upwind scheme on a uniform 10 x 8 box,
@@ -333,7 +334,7 @@ def test_temperature_of_interior_cells_from_the_printed_equations():
     #   D = C^T1_f Gamma_h dy / dx, Gamma_h the harmonic mean (Eqs. pl32, pl33);
     #   a_W = max(0, F_w) + D_w, a_E = max(0, -F_e) + D_e, ... (Eq. pl31);
     #   a_0 = dt (sum a + F_e - F_w + F_n - F_s) + rho dV;
-    #   S_c = (C^T2_f Gamma Phi + C^T3_f p div u) dV (Eq. pl29, reading R5),
+    #   S_c = (C^T2_f Gamma Phi + C^T3_f p div u) dV (Eq. pl29, C^T3_f = -(gamma - 1)),
     #   Phi of Eq. pl7 with dv/dx, du/dy from the corner means of four nodes;
     #   T = [dt (sum a T_nb + S_c) + rho^n T^n dV] / a_0 (Eq. pl30).
     n_x, n_y = 10, 8
@@ -384,7 +385,7 @@ def test_temperature_of_interior_cells_from_the_printed_equations():
     assert np.abs(new["T"] - T).max() > 1e-3          # the step did change T
 
 
-# ------------------------------------ P8: observed order of the convection schemes
+# ------------------------------------ observed order of the convection schemes
 
 def _graded_channel(n, tvd, implicit, dt):
     """Channel of 2n x n cells, inflow profiles u = 1.5 U 4y(1-y),
@@ -432,8 +433,9 @@ def _observed_order(tvd, implicit, dt_power, t_end=0.4):
 def test_observed_order_of_upwind_and_tvd_convection(implicit):
     # Upwind faces (Eqs. pl15, pl31 with psi = 0; pl15_11, pl31_1) are first
     # order in space; Van Leer faces (Eqs. pl15_1, pl15_2) second order on
-    # smooth data away from extrema and boundaries (R9 makes them upwind next
-    # to walls and the inflow), so refined with dt ~ h^2 their observed order
+    # smooth data away from extrema and boundaries (a face whose four-node
+    # stencil is not all unknowns stays upwind, so next to walls and the
+    # inflow they are), so refined with dt ~ h^2 their observed order
     # is well above one.  Diffusion and sources are central in both.
     p_up = _observed_order(False, implicit, 1)
     p_tvd = _observed_order(True, implicit, 2)
@@ -441,14 +443,15 @@ def test_observed_order_of_upwind_and_tvd_convection(implicit):
     assert p_tvd > 1.4 and p_tvd > p_up + 0.4, (p_up, p_tvd)
 
 
-# ------------------------------ P10: TVD with every limiter zero is upwind
+# ------------------------------ TVD with every limiter zero is upwind
 
 @pytest.mark.parametrize("implicit", [False, True])
 def test_tvd_is_upwind_bit_for_bit_when_every_limiter_is_zero(implicit):
     # With every field alternating in sign from node to node (a checkerboard
     # about a mean), each ratio of successive differences is negative, so the
-    # Van Leer limiter (Eq. pl15_2, reading R2) is 0 on every face.  One
-    # loop-2 iteration of one step then evaluates every limiter on that state
+    # Van Leer limiter (Eq. pl15_2, 0 unless both differences have one sign)
+    # is 0 on every face.  One loop-2 iteration of one step then evaluates
+    # every limiter on that state
     # (the fluxes, the explicit terms of level n-1 and the coefficient forms),
     # and the TVD forms of Eqs. pl10, pl11, pl15, pl15_11, pl31, pl31_1 must
     # give the upwind scheme's bits.  From a smooth state they must not.
@@ -477,7 +480,7 @@ def test_tvd_is_upwind_bit_for_bit_when_every_limiter_is_zero(implicit):
     assert max(np.abs(a[k] - b[k]).max() for k in "uvpT") > 1e-8
 
 
-# ---------------- P10: explicit and implicit convection agree to first order in dt
+# ---------------- explicit and implicit convection agree to first order in dt
 
 @pytest.mark.parametrize("tvd", [False, True])
 def test_explicit_and_implicit_agree_to_first_order_in_dt(tvd):

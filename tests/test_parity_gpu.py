@@ -278,8 +278,9 @@ def test_continuity_in_every_cell_at_the_loop2_fixed_point_full_size(make):
 
 # Stated per-field bound of the FP32-assembly path against the FP64 oracle for
 # the explicit schemes and implicit upwind (measured: <= 3e-6 after 100 steps).
-# Implicit TVD amplifies rounding differences (R15): FP32 rounding
-# reaches ~4e-4 after 10 steps, so it has its own, looser bound.
+# Implicit TVD amplifies rounding differences (the limiter's upwind switch in
+# the coefficients depends on differences that are not small inside loop 2):
+# FP32 rounding reaches ~4e-4 after 10 steps, so it has its own, looser bound.
 MIXED_BOUND = 1e-5
 MIXED_BOUND_IMPLICIT_TVD = 2e-3
 
