@@ -338,7 +338,7 @@ def test_temperature_of_interior_cells_from_the_printed_equations():
     #   Phi of Eq. pl7 with dv/dx, du/dy from the corner means of four nodes;
     #   T = [dt (sum a T_nb + S_c) + rho^n T^n dV] / a_0 (Eq. pl30).
     n_x, n_y = 10, 8
-    c = W.closed_box(n=8).replace(nx=n_x, ny=n_y, lx=2.5, ly=2.0, rects=[], implicit=True, tvd=False,
+    c = W.closed_box(n=8).replace(nx=n_x, ny=n_y, lx=2.5, ly=1.6, rects=[], implicit=True, tvd=False,
                                   iters=1, perturb=0.0)
     rng = np.random.default_rng(11)
     s = oracle.init(c)
@@ -383,6 +383,108 @@ def test_temperature_of_interior_cells_from_the_printed_equations():
             checked += 1
     assert checked == 24
     assert np.abs(new["T"] - T).max() > 1e-3          # the step did change T
+
+
+# ------------- momentum, pressure and corrections of interior cells written out
+
+def _uniform_box_step(seed):
+    """One implicit-upwind loop-2 iteration of one step on a uniform 12 x 10
+    box of 0.25 x 0.2 cells from a random state; returns (case, start,
+    result, coefficients)."""
+    nx, ny = 12, 10
+    c = W.closed_box(n=8).replace(nx=nx, ny=ny, lx=3.0, ly=2.0, rects=[], implicit=True, tvd=False,
+                                  iters=1, perturb=0.0)
+    rng = np.random.default_rng(seed)
+    s = oracle.init(c)
+    s["u"][:, 1:nx] = 0.3 * rng.standard_normal((ny, nx - 1))
+    s["v"][1:ny, :] = 0.3 * rng.standard_normal((ny - 1, nx))
+    s["T"] = 1.0 + 0.3 * rng.random((ny, nx))
+    s["p"] = 1.0 + 0.3 * rng.random((ny, nx))
+    new, _, _ = oracle.run(c, s, nsteps=1)
+    return c, s, new, oracle.coefficients(c)
+
+
+def test_momentum_pressure_and_corrections_of_interior_cells_from_the_printed_equations():
+    # Eqs. pl14-pl16 (implicit upwind) with pl20, pl21 for the v faces and
+    # their mirror image for the u faces, the pressure equation Eqs. pl23,
+    # pl24 with the new T, and the corrections Eqs. pl18, pl19, evaluated
+    # here term by term on a uniform grid for every cell two or more cells
+    # from the walls, then compared with one loop-2 iteration of the oracle.
+    # Level n is the start state and the previous iterate (first iteration).
+    c, s, new, k = _uniform_box_step(5)
+    nx, ny = c.nx, c.ny
+    dt, dx, dy, B, A = k["dt"], c.lx / nx, c.ly / ny, k["B"], k["A"]
+    u, v, T, p = s["u"], s["v"], s["T"], s["p"]
+    rho, gam = p / T, T ** k["omega"]
+    up = lambda a, b, vel: a if vel > 0 else b
+
+    def Fx(i, j):                                  # Eqs. pl8, pl10, upwind
+        return up(rho[j, i - 1], rho[j, i], u[j, i]) * u[j, i] * dy
+
+    def Fy(i, j):                                  # Eqs. pl9, pl11, upwind
+        return up(rho[j - 1, i], rho[j, i], v[j, i]) * v[j, i] * dx
+
+    def gc(i, j):                                  # Gamma at the corner (x_i, y_j)
+        return 0.25 * (gam[j - 1, i - 1] + gam[j - 1, i] + gam[j, i - 1] + gam[j, i])
+
+    def v_face(i, j):                              # v^ and d^v, Eqs. pl14-pl16, pl21
+        Fbs = 0.5 * (v[j - 1, i] + v[j, i]) * rho[j - 1, i] * dx
+        Fbn = 0.5 * (v[j, i] + v[j + 1, i]) * rho[j, i] * dx
+        Fw1, Fw2, Fe1, Fe2 = Fx(i, j - 1), Fx(i, j), Fx(i + 1, j - 1), Fx(i + 1, j)
+        Dw, De = B * gc(i, j) * dy / dx, B * gc(i + 1, j) * dy / dx
+        Ds, Dn = B * gam[j - 1, i] * dx / dy, B * gam[j, i] * dx / dy
+        trans = (rho[j, i] + rho[j - 1, i]) * dy * dx / (2 * dt)
+        b = trans * v[j, i] + B * (gc(i + 1, j) * (u[j, i + 1] - u[j - 1, i + 1]) - gc(i, j) * (u[j, i] - u[j - 1, i])
+                                   - 2 / 3 * gam[j, i] * (u[j, i + 1] - u[j, i])
+                                   + 2 / 3 * gam[j - 1, i] * (u[j - 1, i + 1] - u[j - 1, i]))
+        a1 = 0.5 * (max(0.0, Fw2) + max(0.0, Fw1)) + Dw
+        a2 = 0.5 * (max(0.0, -Fe2) + max(0.0, -Fe1)) + De
+        a3 = max(0.0, Fbs) + 4 / 3 * Ds
+        a4 = max(0.0, -Fbn) + 4 / 3 * Dn
+        a0 = a1 + a2 + a3 + a4 + 0.5 * (Fe2 - Fw2 + Fe1 - Fw1) + Fbn - Fbs + trans
+        vh = (a1 * v[j, i - 1] + a2 * v[j, i + 1] + a3 * v[j - 1, i] + a4 * v[j + 1, i] + b) / a0
+        return vh, A * dx / a0
+
+    def u_face(i, j):                              # the mirror image: u^ and d^u, Eq. pl20
+        Fbw = 0.5 * (u[j, i - 1] + u[j, i]) * rho[j, i - 1] * dy
+        Fbe = 0.5 * (u[j, i] + u[j, i + 1]) * rho[j, i] * dy
+        Fs1, Fs2, Fn1, Fn2 = Fy(i - 1, j), Fy(i, j), Fy(i - 1, j + 1), Fy(i, j + 1)
+        Ds, Dn = B * gc(i, j) * dx / dy, B * gc(i, j + 1) * dx / dy
+        Dw, De = B * gam[j, i - 1] * dy / dx, B * gam[j, i] * dy / dx
+        trans = (rho[j, i] + rho[j, i - 1]) * dx * dy / (2 * dt)
+        b = trans * u[j, i] + B * (gc(i, j + 1) * (v[j + 1, i] - v[j + 1, i - 1]) - gc(i, j) * (v[j, i] - v[j, i - 1])
+                                   - 2 / 3 * gam[j, i] * (v[j + 1, i] - v[j, i])
+                                   + 2 / 3 * gam[j, i - 1] * (v[j + 1, i - 1] - v[j, i - 1]))
+        a1 = max(0.0, Fbw) + 4 / 3 * Dw
+        a2 = max(0.0, -Fbe) + 4 / 3 * De
+        a3 = 0.5 * (max(0.0, Fs2) + max(0.0, Fs1)) + Ds
+        a4 = 0.5 * (max(0.0, -Fn2) + max(0.0, -Fn1)) + Dn
+        a0 = a1 + a2 + a3 + a4 + 0.5 * (Fn2 - Fs2 + Fn1 - Fs1) + Fbe - Fbw + trans
+        uh = (a1 * u[j, i - 1] + a2 * u[j, i + 1] + a3 * u[j - 1, i] + a4 * u[j + 1, i] + b) / a0
+        return uh, A * dy / a0
+
+    checked = 0
+    for j in range(2, ny - 2):
+        for i in range(2, nx - 2):
+            (uw, dw), (ue, de) = u_face(i, j), u_face(i + 1, j)
+            (vs, ds), (vn, dn) = v_face(i, j), v_face(i, j + 1)
+            rw, re_ = up(rho[j, i - 1], rho[j, i], u[j, i]), up(rho[j, i], rho[j, i + 1], u[j, i + 1])
+            rs, rn = up(rho[j - 1, i], rho[j, i], v[j, i]), up(rho[j, i], rho[j + 1, i], v[j + 1, i])
+            aw, ae, as_, an = rw * dw * dy, re_ * de * dy, rs * ds * dx, rn * dn * dx     # Eq. pl24
+            ap0 = dx * dy / new["T"][j, i] + dt * (aw + ae + as_ + an)
+            bp = rho[j, i] * dx * dy - dt * (re_ * ue * dy - rw * uw * dy + rn * vn * dx - rs * vs * dx)
+            p_new = (dt * (aw * p[j, i - 1] + ae * p[j, i + 1] + as_ * p[j - 1, i] + an * p[j + 1, i]) + bp) / ap0
+            assert new["p"][j, i] == pytest.approx(p_new, rel=1e-12), (i, j)
+            # the corrections of the west and south faces, Eqs. pl18, pl19
+            if i > 2:
+                assert new["u"][j, i] == pytest.approx(uw - dw * (new["p"][j, i] - new["p"][j, i - 1]),
+                                                       rel=1e-12, abs=1e-14), (i, j)
+            if j > 2:
+                assert new["v"][j, i] == pytest.approx(vs - ds * (new["p"][j, i] - new["p"][j - 1, i]),
+                                                       rel=1e-12, abs=1e-14), (i, j)
+            checked += 1
+    assert checked == 48
+    assert np.abs(new["p"] - p).max() > 1e-3
 
 
 # ------------------------------------ observed order of the convection schemes
