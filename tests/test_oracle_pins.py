@@ -325,20 +325,36 @@ def test_continuity_holds_in_every_cell_at_loop2_convergence(implicit):
 
 # ------------------------- one cell's energy equation written out by hand
 
-def test_temperature_of_interior_cells_from_the_printed_equations():
-    # Eqs. pl28-pl33 for the implicit upwind scheme on a uniform 10 x 8 box,
+def _van_leer_face(f1, f2, f3, f4, vel):
+    """Face value on a uniform grid between nodes f2 and f3 (f1, f4 their
+    outer neighbours): the upwind node plus half Van Leer's psi(r) times the
+    difference across the face, r the ratio of the upwind-side difference to
+    the difference across the face (Eqs. pl10, pl15_1, pl15_2; psi = 0 unless
+    both differences have one sign)."""
+    def psi(num, den):
+        return 2.0 * num / (num + den) if num * den > 0 else 0.0
+    if vel > 0:
+        return f2 + 0.5 * psi(f2 - f1, f3 - f2) * (f3 - f2)
+    return f3 - 0.5 * psi(f4 - f3, f3 - f2) * (f3 - f2)
+
+
+@pytest.mark.parametrize("tvd", [False, True], ids=["upwind", "van-leer"])
+def test_temperature_of_interior_cells_from_the_printed_equations(tvd):
+    # Eqs. pl28-pl33 for the implicit scheme on a uniform 10 x 8 box,
     # evaluated here term by term for every cell two or more cells from the
-    # walls (no reflection in reach), after one loop-2 iteration of one step
-    # from a random state (old = level n):
-    #   F^x = rho^u u dy with the upwind rho^u (Eqs. pl8, pl10), F^y likewise;
+    # walls (no reflection in reach, every face stencil complete), after one
+    # loop-2 iteration of one step from a random state (old = level n):
+    #   F^x = rho^u u dy, rho^u the upwind density or its Van Leer face value
+    #   (Eqs. pl8, pl10), F^y likewise;
     #   D = C^T1_f Gamma_h dy / dx, Gamma_h the harmonic mean (Eqs. pl32, pl33);
-    #   a_W = max(0, F_w) + D_w, a_E = max(0, -F_e) + D_e, ... (Eq. pl31);
+    #   a_W = max(0, F_w) - F_w psi_w + D_w, a_E = max(0, -F_e) - F_e psi_e + D_e,
+    #   ... (Eq. pl31), psi the Van Leer weight of T's face value (0 upwind);
     #   a_0 = dt (sum a + F_e - F_w + F_n - F_s) + rho dV;
     #   S_c = (C^T2_f Gamma Phi + C^T3_f p div u) dV (Eq. pl29, C^T3_f = -(gamma - 1)),
     #   Phi of Eq. pl7 with dv/dx, du/dy from the corner means of four nodes;
     #   T = [dt (sum a T_nb + S_c) + rho^n T^n dV] / a_0 (Eq. pl30).
     n_x, n_y = 10, 8
-    c = W.closed_box(n=8).replace(nx=n_x, ny=n_y, lx=2.5, ly=1.6, rects=[], implicit=True, tvd=False,
+    c = W.closed_box(n=8).replace(nx=n_x, ny=n_y, lx=2.5, ly=1.6, rects=[], implicit=True, tvd=tvd,
                                   iters=1, perturb=0.0)
     rng = np.random.default_rng(11)
     s = oracle.init(c)
@@ -352,19 +368,38 @@ def test_temperature_of_interior_cells_from_the_printed_equations():
     u, v, T, p = s["u"], s["v"], s["T"], s["p"]
     rho, gam = p / T, T ** k["omega"]
     harm = lambda a, b: 2.0 * a * b / (a + b)
+
+    def weight(f1, f2, f3, f4, vel):
+        # psi of a face value written upwind + psi (f3 - f2)
+        if not tvd or f3 == f2:
+            return 0.0
+        return (_van_leer_face(f1, f2, f3, f4, vel) - (f2 if vel > 0 else f3)) / (f3 - f2)
+
+    def face_rho_x(i, j):
+        if tvd:
+            return _van_leer_face(rho[j, i - 2], rho[j, i - 1], rho[j, i], rho[j, i + 1], u[j, i])
+        return rho[j, i - 1] if u[j, i] > 0 else rho[j, i]
+
+    def face_rho_y(i, j):
+        if tvd:
+            return _van_leer_face(rho[j - 2, i], rho[j - 1, i], rho[j, i], rho[j + 1, i], v[j, i])
+        return rho[j - 1, i] if v[j, i] > 0 else rho[j, i]
+
     checked = 0
     for j in range(2, n_y - 2):
         for i in range(2, n_x - 2):
-            Fw = (rho[j, i - 1] if u[j, i] > 0 else rho[j, i]) * u[j, i] * dy
-            Fe = (rho[j, i] if u[j, i + 1] > 0 else rho[j, i + 1]) * u[j, i + 1] * dy
-            Fs = (rho[j - 1, i] if v[j, i] > 0 else rho[j, i]) * v[j, i] * dx
-            Fn = (rho[j, i] if v[j + 1, i] > 0 else rho[j + 1, i]) * v[j + 1, i] * dx
+            Fw, Fe = face_rho_x(i, j) * u[j, i] * dy, face_rho_x(i + 1, j) * u[j, i + 1] * dy
+            Fs, Fn = face_rho_y(i, j) * v[j, i] * dx, face_rho_y(i, j + 1) * v[j + 1, i] * dx
+            pw = weight(T[j, i - 2], T[j, i - 1], T[j, i], T[j, i + 1], u[j, i])
+            pe = weight(T[j, i - 1], T[j, i], T[j, i + 1], T[j, i + 2], u[j, i + 1])
+            ps = weight(T[j - 2, i], T[j - 1, i], T[j, i], T[j + 1, i], v[j, i])
+            pn = weight(T[j - 1, i], T[j, i], T[j + 1, i], T[j + 2, i], v[j + 1, i])
             Dw = k["CT1f"] * harm(gam[j, i - 1], gam[j, i]) * dy / dx
             De = k["CT1f"] * harm(gam[j, i], gam[j, i + 1]) * dy / dx
             Ds = k["CT1f"] * harm(gam[j - 1, i], gam[j, i]) * dx / dy
             Dn = k["CT1f"] * harm(gam[j, i], gam[j + 1, i]) * dx / dy
-            aw, ae = max(0.0, Fw) + Dw, max(0.0, -Fe) + De
-            as_, an = max(0.0, Fs) + Ds, max(0.0, -Fn) + Dn
+            aw, ae = max(0.0, Fw) - Fw * pw + Dw, max(0.0, -Fe) - Fe * pe + De
+            as_, an = max(0.0, Fs) - Fs * ps + Ds, max(0.0, -Fn) - Fn * pn + Dn
             dV = dx * dy
             a0 = dt * (aw + ae + as_ + an + Fe - Fw + Fn - Fs) + rho[j, i] * dV
             ux = (u[j, i + 1] - u[j, i]) / dx
@@ -379,7 +414,7 @@ def test_temperature_of_interior_cells_from_the_printed_equations():
             Sc = (k["CT2f"] * gam[j, i] * phi + k["CT3f"] * p[j, i] * div) * dV
             rhs = dt * (aw * T[j, i - 1] + ae * T[j, i + 1] + as_ * T[j - 1, i] + an * T[j + 1, i] + Sc) \
                 + rho[j, i] * T[j, i] * dV
-            assert new["T"][j, i] == pytest.approx(rhs / a0, rel=1e-13), (i, j)
+            assert new["T"][j, i] == pytest.approx(rhs / a0, rel=1e-12), (i, j)
             checked += 1
     assert checked == 24
     assert np.abs(new["T"] - T).max() > 1e-3          # the step did change T
