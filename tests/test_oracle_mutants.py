@@ -56,6 +56,8 @@ MUTANTS = {
                                  "if (mi != ai && o->P->zeta_coef > 0.0) {"),
     "jump_normal_size_swapped": ("double h = 0.5 * (ni != ci ? DX(o, ci) : DY(o, cj));",
                                  "double h = 0.5 * (ni != ci ? DY(o, cj) : DX(o, ci));"),
+    "T_explicit_west_limiter": ("           + Fw * (upwind(Tw, Tp, uw) + (Tp - Tw) * pw)\n",
+                                "           + Fw * (upwind(Tw, Tp, uw) + (Tp - Tw) * pe)\n"),
     "rho_u_downwind": ("    double val = upwind(rl, rr, vel);\n", "    double val = upwind(rr, rl, vel);\n"),
     # both face densities anti-upwinded in the same way keeps the x/y symmetry:
     # only the observed order of the TVD scheme sees it

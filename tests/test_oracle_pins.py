@@ -339,8 +339,9 @@ def _van_leer_face(f1, f2, f3, f4, vel):
 
 
 @pytest.mark.parametrize("tvd", [False, True], ids=["upwind", "van-leer"])
-def test_temperature_of_interior_cells_from_the_printed_equations(tvd):
-    # Eqs. pl28-pl33 for the implicit scheme on a uniform 10 x 8 box,
+@pytest.mark.parametrize("implicit", [True, False], ids=["implicit", "explicit"])
+def test_temperature_of_interior_cells_from_the_printed_equations(implicit, tvd):
+    # Eqs. pl28-pl33 (and pl31_1 for the explicit scheme) on a uniform 10 x 8 box,
     # evaluated here term by term for every cell two or more cells from the
     # walls (no reflection in reach, every face stencil complete), after one
     # loop-2 iteration of one step from a random state (old = level n):
@@ -353,8 +354,11 @@ def test_temperature_of_interior_cells_from_the_printed_equations(tvd):
     #   S_c = (C^T2_f Gamma Phi + C^T3_f p div u) dV (Eq. pl29, C^T3_f = -(gamma - 1)),
     #   Phi of Eq. pl7 with dv/dx, du/dy from the corner means of four nodes;
     #   T = [dt (sum a T_nb + S_c) + rho^n T^n dV] / a_0 (Eq. pl30).
+    # The explicit scheme (Eq. pl31_1) keeps a_k = D_k, drops the flux terms
+    # from a_0 and adds T^exp = F_w T_w - F_e T_e + F_s T_s - F_n T_n with the
+    # face values of level n-1 (here the start state) to the right-hand side.
     n_x, n_y = 10, 8
-    c = W.closed_box(n=8).replace(nx=n_x, ny=n_y, lx=2.5, ly=1.6, rects=[], implicit=True, tvd=tvd,
+    c = W.closed_box(n=8).replace(nx=n_x, ny=n_y, lx=2.5, ly=1.6, rects=[], implicit=implicit, tvd=tvd,
                                   iters=1, perturb=0.0)
     rng = np.random.default_rng(11)
     s = oracle.init(c)
@@ -398,10 +402,21 @@ def test_temperature_of_interior_cells_from_the_printed_equations(tvd):
             De = k["CT1f"] * harm(gam[j, i], gam[j, i + 1]) * dy / dx
             Ds = k["CT1f"] * harm(gam[j - 1, i], gam[j, i]) * dx / dy
             Dn = k["CT1f"] * harm(gam[j, i], gam[j + 1, i]) * dx / dy
-            aw, ae = max(0.0, Fw) - Fw * pw + Dw, max(0.0, -Fe) - Fe * pe + De
-            as_, an = max(0.0, Fs) - Fs * ps + Ds, max(0.0, -Fn) - Fn * pn + Dn
             dV = dx * dy
-            a0 = dt * (aw + ae + as_ + an + Fe - Fw + Fn - Fs) + rho[j, i] * dV
+            if implicit:
+                aw, ae = max(0.0, Fw) - Fw * pw + Dw, max(0.0, -Fe) - Fe * pe + De
+                as_, an = max(0.0, Fs) - Fs * ps + Ds, max(0.0, -Fn) - Fn * pn + Dn
+                a0 = dt * (aw + ae + as_ + an + Fe - Fw + Fn - Fs) + rho[j, i] * dV
+                Texp = 0.0
+            else:
+                aw, ae, as_, an = Dw, De, Ds, Dn
+                a0 = dt * (aw + ae + as_ + an) + rho[j, i] * dV
+                face = lambda f1, f2, f3, f4, vel: (_van_leer_face(f1, f2, f3, f4, vel) if tvd
+                                                    else (f2 if vel > 0 else f3))
+                Texp = (Fw * face(T[j, i - 2], T[j, i - 1], T[j, i], T[j, i + 1], u[j, i])
+                        - Fe * face(T[j, i - 1], T[j, i], T[j, i + 1], T[j, i + 2], u[j, i + 1])
+                        + Fs * face(T[j - 2, i], T[j - 1, i], T[j, i], T[j + 1, i], v[j, i])
+                        - Fn * face(T[j - 1, i], T[j, i], T[j + 1, i], T[j + 2, i], v[j + 1, i]))
             ux = (u[j, i + 1] - u[j, i]) / dx
             vy = (v[j + 1, i] - v[j, i]) / dy
             v_w = 0.25 * (v[j, i - 1] + v[j, i] + v[j + 1, i - 1] + v[j + 1, i])
@@ -412,7 +427,7 @@ def test_temperature_of_interior_cells_from_the_printed_equations(tvd):
             div = ux + vy
             phi = 2.0 * (ux * ux + vy * vy) + (vx + uy) ** 2 - 2.0 / 3.0 * div * div
             Sc = (k["CT2f"] * gam[j, i] * phi + k["CT3f"] * p[j, i] * div) * dV
-            rhs = dt * (aw * T[j, i - 1] + ae * T[j, i + 1] + as_ * T[j - 1, i] + an * T[j + 1, i] + Sc) \
+            rhs = dt * (aw * T[j, i - 1] + ae * T[j, i + 1] + as_ * T[j - 1, i] + an * T[j + 1, i] + Sc + Texp) \
                 + rho[j, i] * T[j, i] * dV
             assert new["T"][j, i] == pytest.approx(rhs / a0, rel=1e-12), (i, j)
             checked += 1
