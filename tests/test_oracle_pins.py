@@ -437,12 +437,12 @@ def test_temperature_of_interior_cells_from_the_printed_equations(implicit, tvd)
 
 # ------------- momentum, pressure and corrections of interior cells written out
 
-def _uniform_box_step(seed):
-    """One implicit-upwind loop-2 iteration of one step on a uniform 12 x 10
-    box of 0.25 x 0.2 cells from a random state; returns (case, start,
-    result, coefficients)."""
+def _uniform_box_step(seed, implicit, tvd):
+    """One loop-2 iteration of one step on a uniform 12 x 10 box of
+    0.25 x 0.2 cells from a random state; returns (case, start, result,
+    coefficients)."""
     nx, ny = 12, 10
-    c = W.closed_box(n=8).replace(nx=nx, ny=ny, lx=3.0, ly=2.0, rects=[], implicit=True, tvd=False,
+    c = W.closed_box(n=8).replace(nx=nx, ny=ny, lx=3.0, ly=2.0, rects=[], implicit=implicit, tvd=tvd,
                                   iters=1, perturb=0.0)
     rng = np.random.default_rng(seed)
     s = oracle.init(c)
@@ -454,63 +454,126 @@ def _uniform_box_step(seed):
     return c, s, new, oracle.coefficients(c)
 
 
-def test_momentum_pressure_and_corrections_of_interior_cells_from_the_printed_equations():
-    # Eqs. pl14-pl16 (implicit upwind) with pl20, pl21 for the v faces and
-    # their mirror image for the u faces, the pressure equation Eqs. pl23,
-    # pl24 with the new T, and the corrections Eqs. pl18, pl19, evaluated
-    # here term by term on a uniform grid for every cell two or more cells
-    # from the walls, then compared with one loop-2 iteration of the oracle.
-    # Level n is the start state and the previous iterate (first iteration).
-    c, s, new, k = _uniform_box_step(5)
+@pytest.mark.parametrize("tvd", [False, True], ids=["upwind", "van-leer"])
+@pytest.mark.parametrize("implicit", [True, False], ids=["implicit", "explicit"])
+def test_momentum_pressure_and_corrections_of_interior_cells_from_the_printed_equations(implicit, tvd):
+    # Eqs. pl14-pl16 (implicit) or pl15_11 (explicit) with pl20, pl21 for the
+    # v faces and their mirror image for the u faces, the pressure equation
+    # Eqs. pl23, pl24 with the new T, and the corrections Eqs. pl18, pl19,
+    # evaluated here term by term on a uniform grid for every cell two or more
+    # cells from the walls, then compared with one loop-2 iteration of the
+    # oracle.  Level n is the start state and the previous iterate.  The
+    # Van Leer weight of a face applies only where all four nodes of its
+    # stencil are unknowns; the v faces through cell centres take the mean
+    # velocity of the cell (F^y bar = rho 0.5 (v_j + v_{j+1}) dx) to pick the
+    # upwind side, the faces through corners the velocities of the two
+    # neighbouring u faces, each for half of the face.
+    c, s, new, k = _uniform_box_step(5, implicit, tvd)
     nx, ny = c.nx, c.ny
     dt, dx, dy, B, A = k["dt"], c.lx / nx, c.ly / ny, k["B"], k["A"]
     u, v, T, p = s["u"], s["v"], s["T"], s["p"]
     rho, gam = p / T, T ** k["omega"]
-    up = lambda a, b, vel: a if vel > 0 else b
 
-    def Fx(i, j):                                  # Eqs. pl8, pl10, upwind
-        return up(rho[j, i - 1], rho[j, i], u[j, i]) * u[j, i] * dy
+    fluid = lambda i, j: 0 <= i < nx and 0 <= j < ny
+    ua = lambda i, j: 1 <= i <= nx - 1 and 0 <= j <= ny - 1      # u unknowns
+    va = lambda i, j: 0 <= i <= nx - 1 and 1 <= j <= ny - 1      # v unknowns
+    span = lambda ok, i, j, di, dj: tvd and all(ok(i + q * di, j + q * dj) for q in (-2, -1, 0, 1))
 
-    def Fy(i, j):                                  # Eqs. pl9, pl11, upwind
-        return up(rho[j - 1, i], rho[j, i], v[j, i]) * v[j, i] * dx
+    def face(f1, f2, f3, f4, vel, complete):      # face value, upwind + psi (f3 - f2)
+        if complete:
+            return _van_leer_face(f1, f2, f3, f4, vel)
+        return f2 if vel > 0 else f3
+
+    def psi(f1, f2, f3, f4, vel, complete):       # the psi of that face value
+        if not complete or f3 == f2:
+            return 0.0
+        return (face(f1, f2, f3, f4, vel, True) - (f2 if vel > 0 else f3)) / (f3 - f2)
+
+    def Fx(i, j):                                  # Eqs. pl8, pl10
+        r = face(rho[j, i - 2] if i >= 2 else 0, rho[j, i - 1], rho[j, i], rho[j, i + 1] if i + 1 < nx else 0,
+                 u[j, i], span(fluid, i, j, 1, 0))
+        return r * u[j, i] * dy, r
+
+    def Fy(i, j):                                  # Eqs. pl9, pl11
+        r = face(rho[j - 2, i] if j >= 2 else 0, rho[j - 1, i], rho[j, i], rho[j + 1, i] if j + 1 < ny else 0,
+                 v[j, i], span(fluid, i, j, 0, 1))
+        return r * v[j, i] * dx, r
 
     def gc(i, j):                                  # Gamma at the corner (x_i, y_j)
         return 0.25 * (gam[j - 1, i - 1] + gam[j - 1, i] + gam[j, i - 1] + gam[j, i])
 
-    def v_face(i, j):                              # v^ and d^v, Eqs. pl14-pl16, pl21
-        Fbs = 0.5 * (v[j - 1, i] + v[j, i]) * rho[j - 1, i] * dx
-        Fbn = 0.5 * (v[j, i] + v[j + 1, i]) * rho[j, i] * dx
-        Fw1, Fw2, Fe1, Fe2 = Fx(i, j - 1), Fx(i, j), Fx(i + 1, j - 1), Fx(i + 1, j)
+    def v_face(i, j):                              # v^ and d^v, Eqs. pl14-pl16, pl15_11, pl21
+        vP, vW, vE, vS, vN = v[j, i], v[j, i - 1], v[j, i + 1], v[j - 1, i], v[j + 1, i]
+        vb_s, vb_n = 0.5 * (vS + vP), 0.5 * (vP + vN)
+        Fbs, Fbn = vb_s * rho[j - 1, i] * dx, vb_n * rho[j, i] * dx
+        (Fw1, _), (Fw2, _) = Fx(i, j - 1), Fx(i, j)
+        (Fe1, _), (Fe2, _) = Fx(i + 1, j - 1), Fx(i + 1, j)
+        uw1, uw2, ue1, ue2 = u[j - 1, i], u[j, i], u[j - 1, i + 1], u[j, i + 1]
+        cw, ce = span(va, i, j, 1, 0), span(va, i + 1, j, 1, 0)
+        cs, cn = span(va, i, j, 0, 1), span(va, i, j + 1, 0, 1)
+        vWW = v[j, i - 2] if cw else 0.0
+        vEE = v[j, i + 2] if ce else 0.0
+        vSS = v[j - 2, i] if cs else 0.0
+        vNN = v[j + 2, i] if cn else 0.0
         Dw, De = B * gc(i, j) * dy / dx, B * gc(i + 1, j) * dy / dx
         Ds, Dn = B * gam[j - 1, i] * dx / dy, B * gam[j, i] * dx / dy
         trans = (rho[j, i] + rho[j - 1, i]) * dy * dx / (2 * dt)
-        b = trans * v[j, i] + B * (gc(i + 1, j) * (u[j, i + 1] - u[j - 1, i + 1]) - gc(i, j) * (u[j, i] - u[j - 1, i])
-                                   - 2 / 3 * gam[j, i] * (u[j, i + 1] - u[j, i])
-                                   + 2 / 3 * gam[j - 1, i] * (u[j - 1, i + 1] - u[j - 1, i]))
-        a1 = 0.5 * (max(0.0, Fw2) + max(0.0, Fw1)) + Dw
-        a2 = 0.5 * (max(0.0, -Fe2) + max(0.0, -Fe1)) + De
-        a3 = max(0.0, Fbs) + 4 / 3 * Ds
-        a4 = max(0.0, -Fbn) + 4 / 3 * Dn
-        a0 = a1 + a2 + a3 + a4 + 0.5 * (Fe2 - Fw2 + Fe1 - Fw1) + Fbn - Fbs + trans
-        vh = (a1 * v[j, i - 1] + a2 * v[j, i + 1] + a3 * v[j - 1, i] + a4 * v[j + 1, i] + b) / a0
+        b = trans * vP + B * (gc(i + 1, j) * (ue2 - ue1) - gc(i, j) * (uw2 - uw1)
+                              - 2 / 3 * gam[j, i] * (ue2 - uw2) + 2 / 3 * gam[j - 1, i] * (ue1 - uw1))
+        if implicit:
+            pw1, pw2 = psi(vWW, vW, vP, vE, uw1, cw), psi(vWW, vW, vP, vE, uw2, cw)
+            pe1, pe2 = psi(vW, vP, vE, vEE, ue1, ce), psi(vW, vP, vE, vEE, ue2, ce)
+            ps, pn = psi(vSS, vS, vP, vN, vb_s, cs), psi(vS, vP, vN, vNN, vb_n, cn)
+            a1 = 0.5 * (max(0.0, Fw2) - Fw2 * pw2 + max(0.0, Fw1) - Fw1 * pw1) + Dw
+            a2 = 0.5 * (max(0.0, -Fe2) - Fe2 * pe2 + max(0.0, -Fe1) - Fe1 * pe1) + De
+            a3 = max(0.0, Fbs) - Fbs * ps + 4 / 3 * Ds
+            a4 = max(0.0, -Fbn) - Fbn * pn + 4 / 3 * Dn
+            a0 = a1 + a2 + a3 + a4 + 0.5 * (Fe2 - Fw2 + Fe1 - Fw1) + Fbn - Fbs + trans
+            vexp = 0.0
+        else:
+            a1, a2, a3, a4 = Dw, De, 4 / 3 * Ds, 4 / 3 * Dn
+            a0 = a1 + a2 + a3 + a4 + trans
+            vexp = (0.5 * (Fw1 * face(vWW, vW, vP, vE, uw1, cw) + Fw2 * face(vWW, vW, vP, vE, uw2, cw))
+                    - 0.5 * (Fe1 * face(vW, vP, vE, vEE, ue1, ce) + Fe2 * face(vW, vP, vE, vEE, ue2, ce))
+                    + Fbs * face(vSS, vS, vP, vN, vb_s, cs) - Fbn * face(vS, vP, vN, vNN, vb_n, cn))
+        vh = (a1 * vW + a2 * vE + a3 * vS + a4 * vN + b + vexp) / a0
         return vh, A * dx / a0
 
     def u_face(i, j):                              # the mirror image: u^ and d^u, Eq. pl20
-        Fbw = 0.5 * (u[j, i - 1] + u[j, i]) * rho[j, i - 1] * dy
-        Fbe = 0.5 * (u[j, i] + u[j, i + 1]) * rho[j, i] * dy
-        Fs1, Fs2, Fn1, Fn2 = Fy(i - 1, j), Fy(i, j), Fy(i - 1, j + 1), Fy(i, j + 1)
+        uP, uW, uE, uS, uN = u[j, i], u[j, i - 1], u[j, i + 1], u[j - 1, i], u[j + 1, i]
+        ub_w, ub_e = 0.5 * (uW + uP), 0.5 * (uP + uE)
+        Fbw, Fbe = ub_w * rho[j, i - 1] * dy, ub_e * rho[j, i] * dy
+        (Fs1, _), (Fs2, _) = Fy(i - 1, j), Fy(i, j)
+        (Fn1, _), (Fn2, _) = Fy(i - 1, j + 1), Fy(i, j + 1)
+        vs1, vs2, vn1, vn2 = v[j, i - 1], v[j, i], v[j + 1, i - 1], v[j + 1, i]
+        cw, ce = span(ua, i, j, 1, 0), span(ua, i + 1, j, 1, 0)
+        cs, cn = span(ua, i, j, 0, 1), span(ua, i, j + 1, 0, 1)
+        uWW = u[j, i - 2] if cw else 0.0
+        uEE = u[j, i + 2] if ce else 0.0
+        uSS = u[j - 2, i] if cs else 0.0
+        uNN = u[j + 2, i] if cn else 0.0
         Ds, Dn = B * gc(i, j) * dx / dy, B * gc(i, j + 1) * dx / dy
         Dw, De = B * gam[j, i - 1] * dy / dx, B * gam[j, i] * dy / dx
         trans = (rho[j, i] + rho[j, i - 1]) * dx * dy / (2 * dt)
-        b = trans * u[j, i] + B * (gc(i, j + 1) * (v[j + 1, i] - v[j + 1, i - 1]) - gc(i, j) * (v[j, i] - v[j, i - 1])
-                                   - 2 / 3 * gam[j, i] * (v[j + 1, i] - v[j, i])
-                                   + 2 / 3 * gam[j, i - 1] * (v[j + 1, i - 1] - v[j, i - 1]))
-        a1 = max(0.0, Fbw) + 4 / 3 * Dw
-        a2 = max(0.0, -Fbe) + 4 / 3 * De
-        a3 = 0.5 * (max(0.0, Fs2) + max(0.0, Fs1)) + Ds
-        a4 = 0.5 * (max(0.0, -Fn2) + max(0.0, -Fn1)) + Dn
-        a0 = a1 + a2 + a3 + a4 + 0.5 * (Fn2 - Fs2 + Fn1 - Fs1) + Fbe - Fbw + trans
-        uh = (a1 * u[j, i - 1] + a2 * u[j, i + 1] + a3 * u[j - 1, i] + a4 * u[j + 1, i] + b) / a0
+        b = trans * uP + B * (gc(i, j + 1) * (vn2 - vn1) - gc(i, j) * (vs2 - vs1)
+                              - 2 / 3 * gam[j, i] * (vn2 - vs2) + 2 / 3 * gam[j, i - 1] * (vn1 - vs1))
+        if implicit:
+            pw, pe = psi(uWW, uW, uP, uE, ub_w, cw), psi(uW, uP, uE, uEE, ub_e, ce)
+            ps1, ps2 = psi(uSS, uS, uP, uN, vs1, cs), psi(uSS, uS, uP, uN, vs2, cs)
+            pn1, pn2 = psi(uS, uP, uN, uNN, vn1, cn), psi(uS, uP, uN, uNN, vn2, cn)
+            a1 = max(0.0, Fbw) - Fbw * pw + 4 / 3 * Dw
+            a2 = max(0.0, -Fbe) - Fbe * pe + 4 / 3 * De
+            a3 = 0.5 * (max(0.0, Fs2) - Fs2 * ps2 + max(0.0, Fs1) - Fs1 * ps1) + Ds
+            a4 = 0.5 * (max(0.0, -Fn2) - Fn2 * pn2 + max(0.0, -Fn1) - Fn1 * pn1) + Dn
+            a0 = a1 + a2 + a3 + a4 + 0.5 * (Fn2 - Fs2 + Fn1 - Fs1) + Fbe - Fbw + trans
+            uexp = 0.0
+        else:
+            a1, a2, a3, a4 = 4 / 3 * Dw, 4 / 3 * De, Ds, Dn
+            a0 = a1 + a2 + a3 + a4 + trans
+            uexp = (0.5 * (Fs1 * face(uSS, uS, uP, uN, vs1, cs) + Fs2 * face(uSS, uS, uP, uN, vs2, cs))
+                    - 0.5 * (Fn1 * face(uS, uP, uN, uNN, vn1, cn) + Fn2 * face(uS, uP, uN, uNN, vn2, cn))
+                    + Fbw * face(uWW, uW, uP, uE, ub_w, cw) - Fbe * face(uW, uP, uE, uEE, ub_e, ce))
+        uh = (a1 * uW + a2 * uE + a3 * uS + a4 * uN + b + uexp) / a0
         return uh, A * dy / a0
 
     checked = 0
@@ -518,8 +581,8 @@ def test_momentum_pressure_and_corrections_of_interior_cells_from_the_printed_eq
         for i in range(2, nx - 2):
             (uw, dw), (ue, de) = u_face(i, j), u_face(i + 1, j)
             (vs, ds), (vn, dn) = v_face(i, j), v_face(i, j + 1)
-            rw, re_ = up(rho[j, i - 1], rho[j, i], u[j, i]), up(rho[j, i], rho[j, i + 1], u[j, i + 1])
-            rs, rn = up(rho[j - 1, i], rho[j, i], v[j, i]), up(rho[j, i], rho[j + 1, i], v[j + 1, i])
+            rw, re_ = Fx(i, j)[1], Fx(i + 1, j)[1]
+            rs, rn = Fy(i, j)[1], Fy(i, j + 1)[1]
             aw, ae, as_, an = rw * dw * dy, re_ * de * dy, rs * ds * dx, rn * dn * dx     # Eq. pl24
             ap0 = dx * dy / new["T"][j, i] + dt * (aw + ae + as_ + an)
             bp = rho[j, i] * dx * dy - dt * (re_ * ue * dy - rw * uw * dy + rn * vn * dx - rs * vs * dx)
