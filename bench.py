@@ -4,11 +4,15 @@
 One benchmark step = one time step of the whole hot path: loop-2 iterations
 of face densities, energy, pseudo velocities, pressure, velocity correction,
 equation of state and residual reduction (plus the explicit convective terms
-for the explicit scheme), on the 1024 x 256 supersonic channel with one
-square obstacle (implicit upwind, FP64, Mach 2.5, Re 200, 2 loop-2
-iterations per step).  Metric: Mcell-steps/s = nx * ny * steps / second.
+for the explicit scheme).  The default workload is the paper-scale channel:
+4864 x 1216 cells (5.9 M control volumes, the size the paper fits in 1 GB,
+Section 5) with one square obstacle, implicit upwind, Mach 2, Re 300, 2
+loop-2 iterations per step; `value` is its FP64 throughput and the same line
+carries the mixed-precision and double-float runs of the same workload with
+their error against FP64.  Metric: Mcell-steps/s = nx * ny * steps / second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--precision fp64|mixed|df64] [--only-main]
 
 Under torchrun (N > 1) every rank advances its own replica of the channel
 (the method needs no exchange between independent problems): weak scaling.
@@ -31,21 +35,33 @@ if ROOT not in sys.path:
 METRIC = "Mcell-steps/s FP64 vs FP32/FP64 mixed at stated error; % of HBM roofline"
 UNIT = "Mcell-steps/s"
 
-# The dominant kernel, k_assemble (FP64, implicit upwind), is bound by GB300's
-# FP64 pipe.  Its work per cell and loop-2 iteration is counted by ncu on one
-# launch for the 2048x512 channel (1,048,576 cells): DFMA, DADD and DMUL thread
-# instructions 53.62 M, 48.16 M, 44.34 M.
-ASSEMBLE_FP64_INST_PER_CELL = {"dfma": 51.14, "dadd": 45.93, "dmul": 42.29}
-# DRAM bytes of that launch per cell (143.3 MB read + 23.6 MB written).
-ASSEMBLE_DRAM_BYTES_PER_CELL = 159.2
-# ncu: sm__pipe_fp64_cycles_active of that launch, fraction of peak.
-ASSEMBLE_FP64_PIPE_ACTIVE = 0.852
-# Algorithmic HBM traffic of the kernel per cell: reads u, v, p, T, rho, Gamma of
-# the previous iterate, u, v, T, rho of level n-1 and the face arrays F^x, F^y,
+# The dominant kernel of every FP64 scheme, k_assemble, is bound by GB300's
+# FP64 pipe.  Its work per cell and loop-2 iteration is the number of FP64
+# arithmetic thread instructions (DFMA, DADD, DMUL) ncu counts on one launch,
+# divided by the cells of that launch; its DRAM traffic per cell likewise
+# (dram__bytes_read.sum + dram__bytes_write.sum).  Each entry names the case
+# it was counted on; the bench scales it by the cells of its own workload.
+# The commands are in profiles/.
+ASSEMBLE_FP64_COUNTS = {
+    "implicit-upwind": {"dfma": 51.14, "dadd": 45.93, "dmul": 42.29, "dram_bytes": 159.2, "fp64_pipe": 0.852,
+                        "case": "2048x512 channel, one square (1,048,576 cells)"},
+}
+# Algorithmic HBM bytes of k_assemble per cell: the previous iterate's u, v,
+# p, T, rho, Gamma, level n-1's u, v, T, rho, and the face arrays F^x, F^y,
 # D^T_x, D^T_y, B Gamma (corner), B Gamma dy/dx, B Gamma dx/dy, the two
-# cell-centre mass fluxes and the two cell pair sums u_i + u_{i+1}, v_j + v_{j+1}
-# (21 doubles); writes T, u^, d^u, v^, d^v (5 doubles).
+# cell-centre mass fluxes and the two cell pair sums (21 doubles read); T,
+# u^, d^u, v^, d^v written (5 doubles).
 ASSEMBLE_BYTES_PER_CELL = 26 * 8
+# Algorithmic HBM bytes of the method per cell (the sweep's own minimum with
+# perfect neighbour reuse): each loop-2 iteration reads u, v, p, T of the
+# previous iterate and of level n-1 and writes u, v, p, T (12 doubles); the
+# explicit scheme reads its three explicit terms as well (15 doubles) and
+# computes them once per step from 4 reads and 3 writes (7 doubles).
+def method_bytes_per_step(case) -> int:
+    per_iter = 15 * 8 if not case.implicit else 12 * 8
+    return case.cells * (case.iters * per_iter + (0 if case.implicit else 7 * 8))
+
+
 # GB300 FP64 pipe: 2 FP64 thread instructions per cycle per SM (ncu's
 # peak_sustained for DFMA), 152 SMs.
 FP64_INST_PER_CYCLE_PER_SM = 2
@@ -63,21 +79,46 @@ def hbm_peak_gbs() -> float:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched measurement")
     ap.add_argument("--batch-steps", type=int, default=40)
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2",
-                    help="c2 (default, the benchmark line); the others are for profiling and sweeps")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c4",
+                    help="c4 (default: the paper-scale 4864x1216 channel, the benchmark line); the others "
+                         "are for profiling and sweeps")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "df64"], default="fp64",
+                    help="arithmetic of the main timed run (default fp64, the bench value)")
+    ap.add_argument("--only-main", action="store_true",
+                    help="time the main run only (no per-kernel pass, no other precisions, no e2e, batch or "
+                         "CPU baseline): the command the profiler captures")
     ap.add_argument("--sweep", choices=["paper"], default=None,
                     help="paper: the paper's experiment (Section 4) -- the four schemes on the 4032 x "
                          "{200, 400, 2000, 4000} meshes with 1, 2, 10, 20 particles, FP64, against the "
                          "oracle on one core, and the tile-height sweep that stands in for its rows per "
                          "work-group")
     return ap.parse_args()
+
+
+def _c4_half(W):
+    """The paper-scale channel at half resolution (2432x608, square of side
+    152 at a quarter of the length): the C4 geometry on a case small enough
+    for a detailed profiler capture, with a state (about 0.6 GB FP64) well
+    above L2."""
+    return W.channel(2432, 608, 152, name="c4half_2432x608_implicit_upwind", mach_in=2.0, reynolds=300.0,
+                     implicit=True, tvd=False, seed=4, steps=2000)
+
+
+_SCHEMES = {"implicit-upwind": (True, False), "implicit-tvd": (True, True), "explicit-upwind": (False, False),
+            "explicit-tvd": (False, True)}
+
+
+def _with_scheme(case, scheme):
+    implicit, tvd = _SCHEMES[scheme]
+    name = case.name.rsplit("_", 2)[0] + "_" + scheme.replace("-", "_")
+    return case.replace(implicit=implicit, tvd=tvd, name=name)
 
 
 WORKLOADS = {
@@ -91,13 +132,15 @@ WORKLOADS = {
     "c2-explicit-tvd": lambda W: W.c2_medium().replace(implicit=False, tvd=True, name="c2_1024x256_explicit_tvd"),
     "paper": lambda W: W.paper_channel(ny=400),
     "paper-4000": lambda W: W.paper_channel(ny=4000),
+    **{f"c4-{s}": (lambda s: lambda W: _with_scheme(W.c4_paper_scale(), s))(s) for s in _SCHEMES if s != "implicit-upwind"},
+    **{f"c4half-{s}": (lambda s: lambda W: _with_scheme(_c4_half(W), s))(s) for s in _SCHEMES},
 }
 _ARGS = None
 
 
 def workload():
     import workloads as W
-    return WORKLOADS[_ARGS.workload if _ARGS else "c2"](W)
+    return WORKLOADS[_ARGS.workload if _ARGS else "c4"](W)
 
 
 def small_case():
@@ -116,13 +159,17 @@ def device_bytes_of(make):
     return obj, free0 - torch.cuda.mem_get_info()[0]
 
 
-def config_of(case, flush: str):
+def config_of(case):
+    """The workload description, identical in both arms of the benchmark."""
     scheme = ("implicit" if case.implicit else "explicit") + ("-tvd" if case.tvd else "-upwind")
+    state_mb = case.cells * 3 * 6 * 8 / 1e6       # three FP64 levels of six fields
+    l2 = ("state larger than L2" if state_mb > 126 else "state smaller than L2") + \
+         f" ({state_mb:.0f} MB of FP64 levels vs 126 MB); the GPU arm also writes 256 MB between timed steps"
     return {"workload": f"{case.name}: {case.nx}x{case.ny} channel, {len(case.rects)} square obstacle(s), "
                         f"{scheme}, Mach {case.mach_in}, Re {case.reynolds:g}, "
                         f"{case.iters} loop-2 iterations per step",
             "nx": case.nx, "ny": case.ny, "cells": case.cells, "scheme": scheme,
-            "loop2_iters": case.iters, "l2": flush}
+            "loop2_iters": case.iters, "l2": l2}
 
 
 # ------------------------------------------------------------------ clocks
@@ -394,11 +441,103 @@ def run_paper_sweep(args, local_rank):
 
 # ------------------------------------------------------------------- ours
 
+PRECISIONS = {"fp64": 0, "mixed": 1, "df64": 2}
+DTYPE_OF = {"fp64": "f64",
+            "mixed": "f32 assembly / f64 pressure, EOS, residuals",
+            "df64": "df64 (float pairs, about 48 bits) in every kernel; f64 state on read-out"}
+
+
+def scheme_key(case) -> str:
+    return ("implicit" if case.implicit else "explicit") + ("-tvd" if case.tvd else "-upwind")
+
+
+def fp64_roofline(case, asm_avg_s, clocks, n_sm, probe_gflops):
+    """Roofline of k_assemble, FP64: achieved FP64 instructions per second
+    (ncu's per-cell count for the scheme x cells / event-timed launch) against
+    the FP64 pipe's peak at the sampled clock; None when the scheme has no
+    count."""
+    cnt = ASSEMBLE_FP64_COUNTS.get(scheme_key(case))
+    if cnt is None:
+        return None
+    sm_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    per_cell = cnt["dfma"] + cnt["dadd"] + cnt["dmul"]
+    inst = per_cell * case.cells                                               # per launch
+    flops = (2 * cnt["dfma"] + cnt["dadd"] + cnt["dmul"]) * case.cells
+    peak_inst = FP64_INST_PER_CYCLE_PER_SM * n_sm * sm_mhz * 1e6              # per second
+    ach = inst / asm_avg_s
+    return {"bound": "alu", "achieved": round(ach / 1e9, 2), "peak": round(peak_inst / 1e9, 2),
+            "unit": "G FP64 inst/s", "frac": round(ach / peak_inst, 4),
+            "traffic": round(cnt["dram_bytes"] * case.cells), "kernel": "k_assemble",
+            "kernel_ms_avg": round(asm_avg_s * 1e3, 5),
+            "peak_source": f"{FP64_INST_PER_CYCLE_PER_SM} FP64 instructions/cycle/SM x {n_sm} SMs x "
+                           f"{sm_mhz:.0f} MHz (median SM clock sampled in the timed region)",
+            "work_source": f"ncu DFMA+DADD+DMUL thread instructions per cell of one {scheme_key(case)} "
+                           f"k_assemble launch on the {cnt['case']}: {per_cell:.1f} per cell, x {case.cells} cells",
+            "traffic_source": f"ncu dram__bytes_read.sum + dram__bytes_write.sum of that launch, "
+                              f"{cnt['dram_bytes']:.1f} B per cell, scaled to {case.cells} cells",
+            "time_source": "mean event-timed k_assemble launch of the per-kernel pass",
+            "fp64_pipe_active_ncu": cnt["fp64_pipe"],
+            "flops": {"achieved_tflops": round(flops / asm_avg_s / 1e12, 4),
+                      "peak_tflops": round(2 * peak_inst / 1e12, 4),
+                      "probe_tflops": round(probe_gflops / 1e3, 4)},
+            "hbm": {"algorithmic_gbs": round(ASSEMBLE_BYTES_PER_CELL * case.cells / asm_avg_s / 1e9, 1),
+                    "peak_gbs": hbm_peak_gbs(), "unit": "GB/s"}}
+
+
+def step_hbm(case, ms_per_step):
+    """The whole step against HBM: the method's algorithmic bytes per step
+    (method_bytes_per_step) over the graph-timed step."""
+    b = method_bytes_per_step(case)
+    ach = b / (ms_per_step * 1e-3) / 1e9
+    peak = hbm_peak_gbs()
+    return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+            "bytes_per_step": b,
+            "bytes_source": ("12 doubles per cell and loop-2 iteration (u, v, p, T of the previous iterate and "
+                             "of level n-1 read, u, v, p, T written)" if case.implicit else
+                             "15 doubles per cell and loop-2 iteration (12 plus the three explicit terms) and "
+                             "7 per step for the explicit terms"),
+            "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+
+
+# ncu figures of the mixed path's loop-2 kernels (one launch each, one
+# kernel per capture, implicit upwind): pipe and occupancy percentages and
+# DRAM bytes per cell, from the case named; the commands are in profiles/.
+MIXED_KERNEL_NCU = {
+    "case": "2048x512 channel, one square (1,048,576 cells), ncu --set full",
+    "faces": {"fma_pct": 17.0, "lsu_pct": 40.9, "fp64_pct": 0.0, "warps_active_pct": 64.0, "dram_bytes": 16.5},
+    "assemble": {"fma_pct": 18.7, "lsu_pct": 55.3, "fp64_pct": 0.0, "warps_active_pct": 44.0, "dram_bytes": 66.7},
+    "pressure": {"fma_pct": 12.4, "lsu_pct": 26.6, "fp64_pct": 75.0, "warps_active_pct": 69.0, "dram_bytes": 52.8},
+    "velocity": {"fma_pct": 12.1, "lsu_pct": 36.1, "fp64_pct": 35.3, "warps_active_pct": 84.0, "dram_bytes": 34.4},
+}
+
+
+def mixed_roofline(case, ms_per_step, kernel_ms):
+    """Roofline block of the mixed path: the step against HBM (the method's
+    bytes, and the DRAM bytes ncu counted), and per kernel its measured time
+    and the pipe that bounds it."""
+    r = step_hbm(case, ms_per_step)
+    dram = sum(MIXED_KERNEL_NCU[k]["dram_bytes"] for k in ("faces", "assemble", "pressure", "velocity"))
+    r["traffic"] = round(dram * case.cells * case.iters)
+    r["traffic_source"] = (f"sum of the four kernels' ncu DRAM bytes per cell ({dram:.1f} B) x cells x loop-2 "
+                           f"iterations; counted on the {MIXED_KERNEL_NCU['case']}")
+    per = {}
+    for k in ("faces", "assemble", "pressure", "velocity"):
+        n = MIXED_KERNEL_NCU[k]
+        pipes = {"fma": n["fma_pct"], "lsu": n["lsu_pct"], "fp64": n["fp64_pct"]}
+        top = max(pipes, key=pipes.get)
+        per[k] = {**n, "ms_avg": kernel_ms.get(k),
+                  "bound": ("fp64 pipe" if top == "fp64" and pipes["fp64"] > 60 else
+                            "latency (no pipe above 60 %, LSU the busiest)" if top == "lsu" else f"{top} pipe")}
+    r["kernels"] = per
+    return r
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
 
     import paper_1802_04243_gb300 as sim
+    import workloads as W
     from paper_1802_04243_gb300 import build
 
     build.build()
@@ -408,16 +547,18 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    case = workload()
+    base = workload()
+    case = base.replace(precision=PRECISIONS[args.precision])
     stream = torch.cuda.current_stream()
     sim.Simulation(small_case(), stream=stream.cuda_stream).close()   # loads the GPU code first
     s, dev_bytes = device_bytes_of(lambda: sim.Simulation(case, stream=stream.cuda_stream))
     for _ in range(args.warmup):
         s.step(1)
-    peak_fp64 = sim.alu_peak_gflops("fp64", 30.0, stream.cuda_stream)
+    peak_fp64 = 0.0 if args.only_main else sim.alu_peak_gflops("fp64", 30.0, stream.cuda_stream)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2 (126 MB)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    n_ev = max(args.steps, 1)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
 
     s.profile(True, timing=False)                  # count launches; step graphs stay on
     if dist:
@@ -431,50 +572,72 @@ def run_ours(args, rank, world, local_rank):
     res, iters, st = s.residuals()
     total_ms = reduce_max(total_ms, dist, "cuda")
     value = throughput(case.cells, args.steps, world, total_ms * 1e-3)
-    fp64_state = s.fields()
+    ms_per_step = total_ms / args.steps
+    csum = clocks.summary()
+
+    if args.only_main:
+        s.close()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                              "dtype": DTYPE_OF[args.precision], "data": "synthetic", "config": config_of(case),
+                              "gpu_launches": int(launches), "clocks": csum, "impl": "ours",
+                              "note": "--only-main: the main timed run alone (profiling command)"}), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    main_state = s.fields()
 
     # per-kernel durations: the same steps again, kernels launched one by one
     # between CUDA events on the same stream
     prof_steps = min(args.steps, 50)
-    s.profile(True, timing=True)
-    timed_steps(s, prof_steps, stream, flush, starts, ends)
-    prof = s.profile_read()
-    s.profile(False)
+
+    def kernel_pass(h):
+        h.profile(True, timing=True)
+        timed_steps(h, prof_steps, stream, flush, starts, ends)
+        p = h.profile_read()
+        h.profile(False)
+        return p
+
+    prof = kernel_pass(s)
+    kernel_ms = {k: ms / n for k, (ms, n) in prof.items() if n}
+    event_ms_per_step = sum(ms for ms, _ in prof.values()) / prof_steps
 
     # the same workload and timing protocol with the other precisions of the
-    # sweep, and their per-field error against the FP64 path after the same
+    # sweep, and their per-field error against the main run after the same
     # number of steps from the same start
-    import workloads as W
-
-    def variant(precision, dtype):
-        sv, v_bytes = device_bytes_of(lambda: sim.Simulation(case.replace(precision=precision),
+    def variant(prec_name):
+        sv, v_bytes = device_bytes_of(lambda: sim.Simulation(base.replace(precision=PRECISIONS[prec_name]),
                                                              stream=stream.cuda_stream))
         for _ in range(args.warmup):
             sv.step(1)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        v_ms = timed_steps(sv, args.steps, stream, flush, starts, ends)
+        with ClockSampler(local_rank) as vclocks:
+            v_ms = timed_steps(sv, args.steps, stream, flush, starts, ends)
         v_state = sv.fields()
-        sv.profile(True, timing=True)
-        timed_steps(sv, prof_steps, stream, flush, starts, ends)
-        vprof = sv.profile_read()
-        sv.profile(False)
+        vprof = kernel_pass(sv)
         sv.close()
         v_ms = reduce_max(v_ms, dist, "cuda")
-        err = {k: float(np.abs(v_state[k] - fp64_state[k]).max() / np.abs(fp64_state[k]).max())
+        err = {k: float(np.abs(v_state[k] - main_state[k]).max() / np.abs(main_state[k]).max())
                for k in ("u", "v", "p", "T")}
-        return {"value": round(throughput(case.cells, args.steps, world, v_ms * 1e-3), 3),
-                "ms_per_step": round(v_ms / args.steps, 5), "dtype": dtype,
-                "max_rel_err_vs_fp64": {k: float(f"{x:.3e}") for k, x in err.items()},
-                "error_after_steps": args.warmup + args.steps,
-                "device_bytes_per_cell": round(v_bytes / case.cells, 1),
-                "kernel_ms_avg": {k: round(ms / n, 5) for k, (ms, n) in vprof.items() if n}}
+        vk = {k: ms / n for k, (ms, n) in vprof.items() if n}
+        out = {"value": round(throughput(case.cells, args.steps, world, v_ms * 1e-3), 3),
+               "ms_per_step": round(v_ms / args.steps, 5), "dtype": DTYPE_OF[prec_name],
+               f"max_rel_err_vs_{args.precision}": {k: float(f"{x:.3e}") for k, x in err.items()},
+               "error_after_steps": args.warmup + args.steps,
+               "device_bytes_per_cell": round(v_bytes / case.cells, 1),
+               "kernel_ms_avg": {k: round(x, 5) for k, x in vk.items()}, "clocks": vclocks.summary()}
+        if prec_name == "mixed":
+            out["roofline"] = mixed_roofline(case, v_ms / args.steps, vk)
+        else:
+            out["step_hbm"] = step_hbm(case, v_ms / args.steps)
+        return out
 
-    # FP32 assembly and relaxation; FP64 pressure accumulation, EOS and residuals
-    mixed = variant(W.MIXED, "f32 assembly / f64 pressure, EOS, residuals")
-    # every kernel in double-float (pairs of floats) on the FP32 pipe
-    df64 = variant(W.DF64, "df64 (float pairs, about 48 bits) in every kernel; f64 state on read-out")
+    others = {p: variant(p) for p in ("fp64", "mixed", "df64") if p != args.precision}
 
     # end to end through the C ABI with host buffers: every step uploads its
     # input state from pinned host memory (sim_set_state), advances one step
@@ -503,36 +666,12 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
 
-    asm_ms, asm_n = prof["assemble"]
-    asm_avg_s = asm_ms / max(asm_n, 1) * 1e-3
-    csum = clocks.summary()
-    # the per-cell instruction counts were taken for the implicit-upwind
-    # assembly; other schemes get no roofline line
-    measured_scheme = case.implicit and not case.tvd
-    sm_mhz = csum.get("sm_mhz") or csum.get("sm_max_mhz") or 2070.0
     n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    inst = sum(ASSEMBLE_FP64_INST_PER_CELL.values()) * case.cells            # per launch
-    flops = (2 * ASSEMBLE_FP64_INST_PER_CELL["dfma"] + ASSEMBLE_FP64_INST_PER_CELL["dadd"]
-             + ASSEMBLE_FP64_INST_PER_CELL["dmul"]) * case.cells
-    peak_inst = FP64_INST_PER_CYCLE_PER_SM * n_sm * sm_mhz * 1e6                 # per second
-    ach = inst / asm_avg_s
-    roof = {"bound": "alu", "achieved": round(ach / 1e9, 2), "peak": round(peak_inst / 1e9, 2),
-            "unit": "G FP64 inst/s", "frac": round(ach / peak_inst, 4),
-            "traffic": round(ASSEMBLE_DRAM_BYTES_PER_CELL * case.cells), "kernel": "k_assemble",
-            "peak_source": f"{FP64_INST_PER_CYCLE_PER_SM} FP64 instructions/cycle/SM x {n_sm} SMs x "
-                           f"{sm_mhz:.0f} MHz (median SM clock sampled in the timed region)",
-            "work_source": "ncu DFMA+DADD+DMUL thread instructions per cell of one launch (2048x512 channel)",
-            "traffic_source": "ncu dram bytes of that launch, scaled by cells",
-            "fp64_pipe_active_ncu": ASSEMBLE_FP64_PIPE_ACTIVE,
-            "flops": {"achieved_tflops": round(flops / asm_avg_s / 1e12, 4),
-                      "peak_tflops": round(2 * peak_inst / 1e12, 4),
-                      "probe_tflops": round(peak_fp64 / 1e3, 4)},
-            "hbm": {"algorithmic_gbs": round(ASSEMBLE_BYTES_PER_CELL * case.cells / asm_avg_s / 1e9, 1),
-                    "peak_gbs": hbm_peak_gbs()}}
-    if not measured_scheme:
-        roof = None
-    if roof is not None:
-        roof["kernel_ms_avg"] = round(asm_avg_s * 1e3, 5)
+    roof = None
+    if args.precision == "fp64" and "assemble" in kernel_ms:
+        roof = fp64_roofline(case, kernel_ms["assemble"] * 1e-3, csum, n_sm, peak_fp64)
+    elif args.precision == "mixed":
+        roof = mixed_roofline(case, ms_per_step, kernel_ms)
 
     batched = None if args.no_batch else run_batch(args, stream)
 
@@ -541,22 +680,34 @@ def run_ours(args, rank, world, local_rank):
         v, n, secs = oracle_throughput(case)
         cpu = {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{n} time steps of the same {case.nx}x{case.ny} channel from its seeded start "
-                         f"({secs:.1f} s, serial FP64 C oracle)"}
+                         f"({secs:.1f} s, serial FP64 C oracle); Mcell-steps/s = cells x steps / seconds"}
         cpu_rows = cpu_rows_baseline(case)
 
+    steps_per_iter_kernels = {k: n / (prof_steps * case.iters) for k, (_, n) in prof.items() if n}
     line = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {**config_of(case, "flushed between timed steps (256 MB write)"),
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_OF[args.precision], "data": "synthetic",
+            "config": config_of(case),
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                    "path": "sim_set_state (pinned host -> device), sim_step, sim_get_state (device -> pinned "
+                            "host, residuals)"},
             "mcell_iterations_per_s": round(value * case.iters, 3),
             "device_bytes_per_cell": round(dev_bytes / case.cells, 1),
             "gpu_launches": int(launches),
-            "kernel_ms_avg": {k: round(ms / n, 5) for k, (ms, n) in prof.items() if n},
-            "kernel_timing": f"separate pass of {prof_steps} steps with per-launch CUDA events",
-            "roofline": roof, "mixed": mixed, "df64": df64, "batched": batched, "cpu_baseline": cpu,
+            "roofline": roof, "step_hbm": step_hbm(case, ms_per_step),
+            "kernel_ms_avg": {k: round(x, 5) for k, x in kernel_ms.items()},
+            "kernel_timing": {
+                "how": f"separate pass of {prof_steps} steps, every kernel launched on its own between two "
+                       "CUDA events on the library's stream (the timed steps replay one CUDA graph per step, "
+                       "which has no per-kernel events)",
+                "event_pass_ms_per_step": round(event_ms_per_step, 5), "graph_ms_per_step": round(ms_per_step, 5),
+                "note": "the per-launch events and the direct launches add overhead, so the event pass's sum "
+                        "exceeds the graph-timed step; shares between kernels and each kernel's mean are what "
+                        "it gives (the roofline's k_assemble time comes from it)",
+                "launches_per_iteration": {k: round(x, 3) for k, x in steps_per_iter_kernels.items()}},
+            **others, "batched": batched, "cpu_baseline": cpu,
             "cpu_baseline_rows": cpu_rows, "clocks": csum,
             "residuals_last_step": [float(x) for x in res], "impl": "ours"}
     print(json.dumps(line), flush=True)
@@ -588,7 +739,7 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(secs / n * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(case, "not applicable (host)"), "impl": "reference",
+            "config": config_of(case), "parallelism": "host, one core", "impl": "reference",
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "kind": "oracle", "cores": 1, "sample": sample},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

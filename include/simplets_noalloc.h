@@ -5,12 +5,12 @@
  * The paper has no counterpart to this entry point; it is a property of this
  * library.  sim_create allocates every buffer a problem needs with cudaMalloc.
  * Some callers cannot do that at the moment they want to run the solver:
- *   - code that runs while a CUDA stream is being captured into a graph, where
- *     the runtime refuses cudaMalloc (global capture mode);
  *   - applications that reserve their GPU memory once at start-up (their own
  *     pool or a fixed budget) and forbid allocations afterwards;
  *   - loops that cannot afford the device-wide synchronisation that
- *     cudaMalloc and cudaFree imply.
+ *     cudaMalloc and cudaFree imply;
+ *   - plug-ins called from a host framework that owns the device memory and
+ *     hands them only the arrays to work on.
  * sim_step_noalloc serves them: it takes the problem description and the
  * caller's own device arrays, and carves everything else it needs out of one
  * static device array that is part of the library itself.
@@ -53,8 +53,15 @@ extern "C" {
  * before any work is queued.
  *
  * First call on a device: it looks up the device address of the static
- * array once (cudaGetSymbolAddress), which can load the library's GPU code.
- * Make the first call on each device before any stream capture begins.
+ * array once (cudaGetSymbolAddress, with that device current), which can load
+ * the library's GPU code.  Make the first call on each device before any
+ * stream capture begins.  The address is kept per device and CUDA context:
+ * a call from another context (for instance after cudaDeviceReset) looks it
+ * up again.
+ *
+ * Host arrays of the description (grid->dx, grid->dy, bc->rect and the inflow
+ * profiles) are copied to the scratch with cudaMemcpyAsync on `stream`; keep
+ * them unchanged until the stream has reached the call's work.
  *
  * Sharing: all calls on a device use the same array, which keeps the last
  * call's contents; the call clears what must start at zero.  Two calls that

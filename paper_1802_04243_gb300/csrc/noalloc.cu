@@ -7,12 +7,14 @@
 // and the residual words -- is carved out of one file-scope device array.
 // The sweep itself runs through the same kernels as sim_step, over a
 // one-problem tile list that also lives in the array.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstring>
 #include <mutex>
 
+#include "problem_rules.h"
 #include "simplets.h"
 #include "simplets_noalloc.h"
 #include "stg_common.cuh"
@@ -30,24 +32,68 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_lock;
-void *g_scratch_dev[kMaxDevices] = {nullptr};
 
-// Device address of the scratch for the current device, looked up once per
-// device (the lookup may load the module, so it must not run inside a
-// stream capture).
+// The device address of the scratch is looked up once per device and CUDA
+// context (cudaGetSymbolAddress, with that device current), and looked up
+// again when the caller's current context is another one -- after
+// cudaDeviceReset, say, the module is loaded anew and the old address is
+// stale.  The context is identified by cuCtxGetId, reached through the
+// runtime's driver entry points (no link against the driver library).
+struct ScratchSlot {
+    unsigned long long ctx_id = 0;
+    void *ptr = nullptr;
+};
+ScratchSlot g_slot[kMaxDevices];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context; false if there is none
+// or the driver cannot say.
+bool current_context_id(unsigned long long *id)
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)f;
+    });
+    CUcontext ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of the scratch in the current device's current context.
+// The first call on a device (or in a new context) looks it up, which can
+// load the library's GPU code; later calls in the same context reuse it.
+// When the context cannot be identified the address is looked up every call.
 sim_status scratch_address(void **out)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return SIM_ECUDA;
     std::lock_guard<std::mutex> g(g_lock);
-    if (!g_scratch_dev[dev]) {
+    unsigned long long id = 0;
+    const bool known = current_context_id(&id);
+    ScratchSlot &s = g_slot[dev];
+    if (!known || !s.ptr || s.ctx_id != id) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p)
             return SIM_ECUDA;
-        g_scratch_dev[dev] = p;
+        // the lookup makes the device's primary context current if none was
+        unsigned long long id2 = 0;
+        s.ptr = p;
+        s.ctx_id = current_context_id(&id2) ? id2 : 0;
     }
-    *out = g_scratch_dev[dev];
+    *out = s.ptr;
     return SIM_OK;
 }
 
@@ -259,41 +305,6 @@ struct Carver {
     }
 };
 
-// Non-dimensional coefficients of the gas description (Section 4 scaling,
-// Eq. pl37 for the hard-sphere gas, c_v-form energy constants).
-bool coefficients(const sim_gas *gas, Coef &k, double &u_in, double &gm)
-{
-    double ct1, ct2, ct3;
-    k.A = 0.5;                 // for every gas model; the FP64 kernels take A dy as the tabulated half height
-    if (gas->model == SIM_GAS_HARD_SPHERE_KN) {
-        const double pi = 3.14159265358979323846;
-        gm = 5.0 / 3.0;
-        k.omega = 0.5;
-        u_in = gas->mach_in * std::sqrt(gm / 2.0);
-        k.B = 5.0 * std::sqrt(pi) * gas->kn / 16.0;
-        ct1 = gas->kn * std::sqrt(pi * 225.0 / 1024.0);
-        ct2 = std::sqrt(pi) * gas->kn / 4.0;
-        ct3 = 2.0 / 5.0;
-    } else if (gas->model == SIM_GAS_IDEAL_RE) {
-        if (!(gas->reynolds > 0.0) || !(gas->gamma > 1.0) || !(gas->prandtl > 0.0)) return false;
-        gm = gas->gamma;
-        k.omega = gas->visc_exp;
-        u_in = gas->mach_in * std::sqrt(gm / 2.0);
-        k.B = u_in / gas->reynolds;
-        ct1 = k.B / gas->prandtl;
-        ct2 = 2.0 * k.B * (gm - 1.0) / gm;
-        ct3 = (gm - 1.0) / gm;
-    } else {
-        return false;
-    }
-    k.CT1f = gm * ct1;
-    k.CT2f = gm * ct2;
-    k.CT3f = -gm * ct3;
-    k.gx = gas->gx;
-    k.gy = gas->gy;
-    return true;
-}
-
 #define NA_TRY(call)                                   \
     do {                                               \
         if ((call) != cudaSuccess) return SIM_ECUDA;   \
@@ -331,20 +342,11 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     if (bc->iters < 1 || bc->tol != 0.0 || bc->precision != SIM_FP64) return SIM_EINVAL;
     if (bc->inflow_T)
         for (int j = 0; j < ny; j++) if (!(bc->inflow_T[j] > 0.0)) return SIM_EINVAL;
+    // the coefficients and the time step by the rules sim_create applies
     Coef k{};
     double u_in = 0.0, gm = 0.0;
-    if (!coefficients(gas, k, u_in, gm)) return SIM_EINVAL;
-    if (bc->dt > 0.0) {
-        k.dt = bc->dt;
-    } else {
-        double cfl = bc->cfl > 0.0 ? bc->cfl : 0.2, dmin = 1e300, uref = std::fabs(u_in);
-        for (int i = 0; i < nx; i++) dmin = std::fmin(dmin, grid->dx ? grid->dx[i] : grid->lx / nx);
-        for (int j = 0; j < ny; j++) dmin = std::fmin(dmin, grid->dy ? grid->dy[j] : grid->ly / ny);
-        for (int s = 0; s < 4; s++) uref = std::fmax(uref, std::fabs(bc->side_vel[s]));
-        if (bc->inflow_u)
-            for (int j = 0; j < ny; j++) uref = std::fmax(uref, std::fabs(bc->inflow_u[j]));
-        k.dt = cfl * dmin / (uref + std::sqrt(gm / 2.0));
-    }
+    if (!gas_coefficients(gas, k, u_in, gm)) return SIM_EINVAL;
+    k.dt = time_step(grid, bc, u_in, gm);
     k.hrdt = 0.5 / k.dt;
     if (!(bc->zeta_coef >= 0.0) || !(bc->tau_coef >= 0.0) || !std::isfinite(bc->zeta_coef) ||
         !std::isfinite(bc->tau_coef))

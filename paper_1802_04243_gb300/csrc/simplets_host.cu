@@ -12,6 +12,7 @@
 #include <new>
 #include <vector>
 
+#include "problem_rules.h"
 #include "simplets.h"
 #include "stg_common.cuh"
 
@@ -123,41 +124,14 @@ double hash_uniform(uint64_t seed, int field, int i, int j)
 }
 
 // Non-dimensional parameters (Section 4 scaling; Eq. pl37 for the hard-sphere
-// gas).  The energy constants are the c_v-form C^Tk_f = gamma C^Tk (C^T3_f
-// with a minus sign), the form Eq. pl29 uses.
+// gas), by the rules of problem_rules.h.
 sim_status derive_coefficients(const sim_gas *gas, Problem &pb, sim_t err)
 {
-    double ct1, ct2, ct3, gm;
-    Coef &k = pb.k;
-    k.A = 0.5;                 // for every gas model; the FP64 kernels take A dy as the tabulated half height
-    if (gas->model == SIM_GAS_HARD_SPHERE_KN) {
-        const double pi = 3.14159265358979323846;
-        gm = 5.0 / 3.0;
-        k.omega = 0.5;
-        pb.u_in = gas->mach_in * std::sqrt(gm / 2.0);
-        k.B = 5.0 * std::sqrt(pi) * gas->kn / 16.0;
-        ct1 = gas->kn * std::sqrt(pi * 225.0 / 1024.0);
-        ct2 = std::sqrt(pi) * gas->kn / 4.0;
-        ct3 = 2.0 / 5.0;
-    } else if (gas->model == SIM_GAS_IDEAL_RE) {
-        if (!(gas->reynolds > 0.0) || !(gas->gamma > 1.0) || !(gas->prandtl > 0.0))
+    if (!gas_coefficients(gas, pb.k, pb.u_in, pb.gamma)) {
+        if (gas->model == SIM_GAS_IDEAL_RE)
             return fail(err, SIM_EINVAL, "ideal gas needs reynolds > 0, gamma > 1, prandtl > 0");
-        gm = gas->gamma;
-        k.omega = gas->visc_exp;
-        pb.u_in = gas->mach_in * std::sqrt(gm / 2.0);
-        k.B = pb.u_in / gas->reynolds;
-        ct1 = k.B / gas->prandtl;
-        ct2 = 2.0 * k.B * (gm - 1.0) / gm;
-        ct3 = (gm - 1.0) / gm;
-    } else {
         return fail(err, SIM_EINVAL, "unknown gas model %d", gas->model);
     }
-    pb.gamma = gm;
-    k.CT1f = gm * ct1;
-    k.CT2f = gm * ct2;
-    k.CT3f = -gm * ct3;
-    k.gx = gas->gx;
-    k.gy = gas->gy;
     return SIM_OK;
 }
 
@@ -226,17 +200,7 @@ sim_status read_problem(const sim_grid *gr, const sim_gas *gas, const sim_bc *bc
         if (!(pb.in_T[j] > 0.0)) return fail(err, SIM_EINVAL, "inflow temperature must be positive");
     }
     // time step: given, or cfl * min cell size / (U_ref + sound speed)
-    if (bc->dt > 0.0) {
-        pb.k.dt = bc->dt;
-    } else {
-        double cfl = bc->cfl > 0.0 ? bc->cfl : 0.2, dmin = 1e300, uref = std::fabs(pb.u_in);
-        for (double d : pb.dx) dmin = std::fmin(dmin, d);
-        for (double d : pb.dy) dmin = std::fmin(dmin, d);
-        for (int s = 0; s < 4; s++) uref = std::fmax(uref, std::fabs(pb.side_vel[s]));
-        if (bc->inflow_u)
-            for (int j = 0; j < pb.ny; j++) uref = std::fmax(uref, std::fabs(bc->inflow_u[j]));
-        pb.k.dt = cfl * dmin / (uref + std::sqrt(pb.gamma / 2.0));
-    }
+    pb.k.dt = time_step(gr, bc, pb.u_in, pb.gamma);
     pb.k.hrdt = 0.5 / pb.k.dt;
     return SIM_OK;
 }

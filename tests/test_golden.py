@@ -71,6 +71,13 @@ def test_paper_workloads_use_the_printed_test_case():
         assert c.gas_model == W.GAS_HARD_SPHERE_KN
         assert c.zeta_coef == pytest.approx(PAPER["zeta_per_Kn"][0] * c.kn, rel=1e-15)
         assert c.tau_coef == pytest.approx(PAPER["tau_per_Kn"][0] * c.kn, rel=1e-15)
+        # seen from the particle the channel walls move with the gas at the
+        # inlet (Section 4): both wall speeds are the inlet speed the oracle
+        # derives from the case itself, M sqrt(gamma / 2) in units of V0
+        u_in = oracle.coefficients(c)["u_in"]
+        assert c.side_kind[W.S] == W.WALL and c.side_kind[W.N] == W.WALL
+        assert c.side_vel[W.S] == u_in and c.side_vel[W.N] == u_in
+        assert c.side_vel[W.W] == 0.0 and c.side_vel[W.E] == 0.0
 
 
 def test_splitmix64_first_outputs():

@@ -2,8 +2,9 @@
 points.
 
 sim_step_noalloc is for callers that cannot allocate device memory when they
-run the solver (inside a stream capture, under a fixed memory budget, or
-where the synchronisation of cudaMalloc is unacceptable).  It advances state
+run the solver (under a fixed memory budget, inside a host framework that owns
+the device memory, or where the synchronisation of cudaMalloc is
+unacceptable).  It advances state
 that lives in the caller's own device arrays and keeps all its working
 memory in a static array of the library.  These tests give it device arrays
 (allocated here by the test, as such a caller would beforehand), call it
@@ -53,7 +54,19 @@ CASES = {
         ly=float(np.linspace(0.3, 0.2, 21).sum()), perturb=1e-3, seed=31),
     "symmetry-sides": lambda: W.uniform_flow(nx=40, ny=18).replace(rects=[[9, 6, 13, 11]], perturb=1e-3),
     "slip-jump-walls": lambda: W.paper_channel(ny=40, nx=160, kn=0.05, side=8, inlet=24).replace(perturb=1e-3),
+    "inflow-profile-body-force-hard-sphere": lambda: _profile_case(),
 }
+
+
+def _profile_case():
+    # inflow u, T and p profiles (the start state's inflow rows and the inflow
+    # ghosts come from them), moving and heated walls, a body force
+    ny = 24
+    y = (np.arange(ny) + 0.5) / ny
+    return W.Case(name="hs", nx=40, ny=ny, lx=40 / 24, ly=1.0, gas_model=W.GAS_HARD_SPHERE_KN, kn=0.01,
+                  mach_in=1.2, side_vel=(0, 0, 0.1, -0.2), side_T=(1, 1, 1.1, 0.9), gx=0.05,
+                  inflow_u=0.8 * 4 * y * (1 - y), inflow_T=1 + 0.1 * y, inflow_p=np.ones(ny) * 1.05,
+                  rects=[[10, 8, 14, 14]], implicit=True, tvd=False, perturb=1e-3, seed=17)
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
