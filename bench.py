@@ -42,9 +42,16 @@ UNIT = "Mcell-steps/s"
 # (dram__bytes_read.sum + dram__bytes_write.sum).  Each entry names the case
 # it was counted on; the bench scales it by the cells of its own workload.
 # The commands are in profiles/.
+_C4HALF = "2432x608 channel (the 4864x1216 channel at half resolution, 1,478,656 cells)"
 ASSEMBLE_FP64_COUNTS = {
-    "implicit-upwind": {"dfma": 51.14, "dadd": 45.93, "dmul": 42.29, "dram_bytes": 159.2, "fp64_pipe": 0.852,
-                        "case": "2048x512 channel, one square (1,048,576 cells)"},
+    "implicit-upwind": {"dfma": 51.15, "dadd": 45.79, "dmul": 42.30, "dram_bytes": 165.2, "fp64_pipe": 0.856,
+                        "case": _C4HALF},
+    "implicit-tvd": {"dfma": 66.88, "dadd": 45.79, "dmul": 42.30, "dram_bytes": 223.5, "fp64_pipe": 0.862,
+                     "case": _C4HALF},
+    "explicit-upwind": {"dfma": 41.31, "dadd": 27.10, "dmul": 46.23, "dram_bytes": 156.6, "fp64_pipe": 0.854,
+                        "case": _C4HALF},
+    "explicit-tvd": {"dfma": 41.31, "dadd": 27.10, "dmul": 46.23, "dram_bytes": 156.5, "fp64_pipe": 0.854,
+                     "case": _C4HALF},
 }
 # Algorithmic HBM bytes of k_assemble per cell: the previous iterate's u, v,
 # p, T, rho, Gamma, level n-1's u, v, T, rho, and the face arrays F^x, F^y,
@@ -503,11 +510,11 @@ def step_hbm(case, ms_per_step):
 # kernel per capture, implicit upwind): pipe and occupancy percentages and
 # DRAM bytes per cell, from the case named; the commands are in profiles/.
 MIXED_KERNEL_NCU = {
-    "case": "2048x512 channel, one square (1,048,576 cells), ncu --set full",
-    "faces": {"fma_pct": 17.0, "lsu_pct": 40.9, "fp64_pct": 0.0, "warps_active_pct": 64.0, "dram_bytes": 16.5},
-    "assemble": {"fma_pct": 18.7, "lsu_pct": 55.3, "fp64_pct": 0.0, "warps_active_pct": 44.0, "dram_bytes": 66.7},
-    "pressure": {"fma_pct": 12.4, "lsu_pct": 26.6, "fp64_pct": 75.0, "warps_active_pct": 69.0, "dram_bytes": 52.8},
-    "velocity": {"fma_pct": 12.1, "lsu_pct": 36.1, "fp64_pct": 35.3, "warps_active_pct": 84.0, "dram_bytes": 34.4},
+    "case": _C4HALF + ", ncu --metrics (one kernel per capture)",
+    "faces": {"fma_pct": 17.9, "lsu_pct": 43.1, "fp64_pct": 0.0, "warps_active_pct": 64.5, "dram_bytes": 20.6},
+    "assemble": {"fma_pct": 18.6, "lsu_pct": 54.8, "fp64_pct": 0.0, "warps_active_pct": 44.5, "dram_bytes": 73.2},
+    "pressure": {"fma_pct": 12.8, "lsu_pct": 27.4, "fp64_pct": 77.5, "warps_active_pct": 69.5, "dram_bytes": 60.8},
+    "velocity": {"fma_pct": 12.8, "lsu_pct": 38.1, "fp64_pct": 37.5, "warps_active_pct": 88.7, "dram_bytes": 35.6},
 }
 
 
