@@ -101,11 +101,12 @@ def parse():
     ap.add_argument("--only-main", action="store_true",
                     help="time the main run only (no per-kernel pass, no other precisions, no e2e, batch or "
                          "CPU baseline): the command the profiler captures")
-    ap.add_argument("--sweep", choices=["paper"], default=None,
+    ap.add_argument("--sweep", choices=["paper", "plans"], default=None,
                     help="paper: the paper's experiment (Section 4) -- the four schemes on the 4032 x "
                          "{200, 400, 2000, 4000} meshes with 1, 2, 10, 20 particles, FP64, against the "
                          "oracle on one core, and the tile-height sweep that stands in for its rows per "
-                         "work-group")
+                         "work-group; plans: every work distribution of the equation kernels (tile shape, "
+                         "CTA count) on --workload for each precision")
     return ap.parse_args()
 
 
@@ -446,6 +447,51 @@ def run_paper_sweep(args, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ plan sweep
+
+PLAN_CANDIDATES = [(32, 8, 0), (32, 4, 0), (64, 4, 0), (64, 2, 0), (128, 2, 0), (16, 16, 0), (32, 8, 608),
+                   (32, 8, 1216)]
+
+
+def run_plan_sweep(args, local_rank):
+    """Time every candidate work distribution of the equation kernels
+    (sim_set_plan: tile shape, CTA count) on the
+    workload, for each precision: graph-replayed steps with the L2 flush
+    between them, and per-kernel means from the event-timed pass.  Every plan
+    gives the same bits (tests/test_batch_gpu.py)."""
+    import torch
+
+    import paper_1802_04243_gb300 as sim
+    from paper_1802_04243_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.current_stream()
+    base = workload()
+    steps = max(1, args.steps)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    rows = []
+    with ClockSampler(local_rank) as clocks:
+        for prec in ("fp64", "mixed", "df64"):
+            with sim.Simulation(base.replace(precision=PRECISIONS[prec]), stream=stream.cuda_stream) as s:
+                for plan in PLAN_CANDIDATES:
+                    s.set_plan(*plan)
+                    for _ in range(args.warmup):
+                        s.step(1)
+                    ms = timed_steps(s, steps, stream, flush, starts, ends)
+                    s.profile(True, timing=True)
+                    timed_steps(s, min(steps, 10), stream, flush, starts, ends)
+                    prof = s.profile_read()
+                    s.profile(False)
+                    rows.append({"precision": prec, "plan": list(plan),
+                                 "value": round(throughput(base.cells, steps, 1, ms * 1e-3), 2),
+                                 "kernel_ms_avg": {k: round(t / n, 5) for k, (t, n) in prof.items() if n}})
+    print(json.dumps({"sweep": "plans", "config": config_of(base), "steps": steps, "warmup": args.warmup,
+                      "rows": rows, "clocks": clocks.summary()}), flush=True)
+
+
 # ------------------------------------------------------------------- ours
 
 PRECISIONS = {"fp64": 0, "mixed": 1, "df64": 2}
@@ -764,6 +810,9 @@ def main():
     elif args.sweep == "paper":
         if rank == 0:
             run_paper_sweep(args, local_rank)
+    elif args.sweep == "plans":
+        if rank == 0:
+            run_plan_sweep(args, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

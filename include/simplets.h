@@ -203,16 +203,12 @@ sim_status sim_residuals(sim_t sim, double out[4], int *iters_last_step);
 sim_status sim_coefficients(sim_t sim, double out[9]);
 
 /* Work distribution of the handle's equation kernels (not part of the method;
- * every distribution gives the same bits).  The kernels walk a list of tiles
- * of tile_x x (tile_y * rows) grid positions; each tile is taken by one CTA of
- * tile_x x tile_y threads, in which the thread at (x, y) owns the positions
- * (x, y), (x, y + tile_y), ..., (x, y + (rows - 1) tile_y) of the tile.
- * tile_x in {16, 32, 64, 128, 256}; tile_x * tile_y in {32, 64, 128, 256};
- * 1 <= rows <= 8; ctas >= 0 CTAs walk the list (0: one CTA per tile).
- * The default is 32 x 8 threads, one CTA per tile, and a number of rows that
- * depends on the precision.  Synchronous; the captured step graphs are
- * rebuilt on the next sim_step.  Errors: SIM_EINVAL, SIM_ECUDA. */
-sim_status sim_set_plan(sim_t sim, int tile_x, int tile_y, int rows, int ctas);
+ * every distribution gives the same bits): tiles of tile_x x tile_y threads,
+ * one grid position per thread, walked by `ctas` CTAs (0: one CTA per tile).
+ * tile_x in {16, 32, 64, 128, 256}; tile_x * tile_y in {32, 64, 128, 256}.
+ * The default is 32 x 8, one CTA per tile.  Synchronous; the captured step
+ * graphs are rebuilt on the next sim_step.  Errors: SIM_EINVAL, SIM_ECUDA. */
+sim_status sim_set_plan(sim_t sim, int tile_x, int tile_y, int ctas);
 
 /* Kernel classes of the sweep, for sim_profile_read. */
 enum { SIM_K_FACES = 0, SIM_K_ASSEMBLE = 1, SIM_K_PRESSURE = 2, SIM_K_VELOCITY = 3, SIM_K_GHOSTS = 4,
@@ -274,16 +270,6 @@ sim_status sim_batch_tune(sim_batch_t batch, int scheme, int out[3]);
  * per tile).  Every distribution gives the same bits.  Synchronous.
  * Errors: SIM_EINVAL (null batch, another shape, ctas < 0), SIM_ECUDA. */
 sim_status sim_batch_set_tiles(sim_batch_t batch, int tile_x, int tile_y, int ctas);
-
-/* As sim_batch_set_tiles, with `rows` (1 to 8) positions per thread along y:
- * tiles of tile_x x (tile_y * rows) positions, as for sim_set_plan. */
-sim_status sim_batch_set_plan(sim_batch_t batch, int tile_x, int tile_y, int rows, int ctas);
-
-/* As sim_batch_tune, over the tile shapes 32x8, 64x4, 128x2, 16x16, 32x4,
- * 64x2, 1, 2 or 4 positions per thread along y and the CTA counts;
- * out[0..3] = tile x, tile y, CTAs, rows.  Synchronous; allocates a temporary
- * copy of the state.  Errors: SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA. */
-sim_status sim_batch_tune_plan(sim_batch_t batch, int scheme, int out[4]);
 
 /* Text of the last error on this batch (never NULL). */
 const char *sim_batch_last_error(sim_batch_t batch);

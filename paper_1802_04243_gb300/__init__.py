@@ -78,7 +78,7 @@ _SIGNATURES = {
     "sim_get_state": ([ctypes.c_void_p, _DP, _DP, _DP, _DP, _DP], ctypes.c_int),
     "sim_residuals": ([ctypes.c_void_p, _DP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sim_coefficients": ([ctypes.c_void_p, _DP], ctypes.c_int),
-    "sim_set_plan": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "sim_set_plan": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "sim_profile": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "sim_profile_read": ([ctypes.c_void_p, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "sim_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
@@ -93,9 +93,6 @@ _SIGNATURES = {
     "sim_batch_residuals": ([ctypes.c_void_p, ctypes.c_int, _DP], ctypes.c_int),
     "sim_batch_tune": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sim_batch_set_tiles": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
-    "sim_batch_set_plan": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
-                           ctypes.c_int),
-    "sim_batch_tune_plan": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sim_batch_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "sim_batch_destroy": ([ctypes.c_void_p], None),
     "sim_step_noalloc": ([ctypes.POINTER(sim_grid), ctypes.POINTER(sim_gas), ctypes.POINTER(sim_bc), ctypes.c_int,
@@ -299,9 +296,9 @@ class Simulation:
         arr = _CudaArray(base, (ny + 4, nx + 4), (pitch.value * 8, 8))
         return torch.as_tensor(arr, device="cuda")
 
-    def set_plan(self, tile_x: int = 32, tile_y: int = 8, rows: int = 1, ctas: int = 0):
+    def set_plan(self, tile_x: int = 32, tile_y: int = 8, ctas: int = 0):
         """Work distribution of the equation kernels (sim_set_plan); the same bits for every choice."""
-        self._check(self.lib.sim_set_plan(self.handle, int(tile_x), int(tile_y), int(rows), int(ctas)))
+        self._check(self.lib.sim_set_plan(self.handle, int(tile_x), int(tile_y), int(ctas)))
 
     def profile(self, enable: bool = True, timing: bool = True):
         """enable=True: clear the launch counters; timing=True also brackets every
@@ -371,16 +368,6 @@ class Batch:
     def set_tiles(self, tile_x: int, tile_y: int, ctas: int = 0):
         """Tiles of tile_x x tile_y threads walked by `ctas` CTAs (0: one per tile), sim_batch_set_tiles."""
         self._check(self.lib.sim_batch_set_tiles(self.handle, int(tile_x), int(tile_y), int(ctas)))
-
-    def set_plan(self, tile_x: int, tile_y: int, rows: int = 1, ctas: int = 0):
-        """As set_tiles with `rows` positions per thread along y (sim_batch_set_plan)."""
-        self._check(self.lib.sim_batch_set_plan(self.handle, int(tile_x), int(tile_y), int(rows), int(ctas)))
-
-    def tune_plan(self, scheme: Optional[int] = None):
-        """sim_batch_tune_plan: (tile x, tile y, CTAs, rows) of the fastest candidate, now in use."""
-        out = (ctypes.c_int * 4)()
-        self._check(self.lib.sim_batch_tune_plan(self.handle, self.scheme if scheme is None else int(scheme), out))
-        return tuple(out)
 
     def field(self, instance: int, name: str) -> np.ndarray:
         c = self.cases[instance]

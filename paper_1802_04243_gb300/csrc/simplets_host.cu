@@ -453,27 +453,19 @@ void sync_out(sim_t s)
     }
 }
 
-// Tiles of tx x th positions over the (nx + 1) x (ny + 1) positions of a problem.
-int tiles_of(const sim_s *s, int tx, int th)
+// Tiles of tx x ty positions over the (nx + 1) x (ny + 1) positions of a problem.
+int tiles_of(const sim_s *s, int tx, int ty)
 {
-    return ((s->pb.nx + 1 + tx - 1) / tx) * ((s->pb.ny + 1 + th - 1) / th);
+    return ((s->pb.nx + 1 + tx - 1) / tx) * ((s->pb.ny + 1 + ty - 1) / ty);
 }
 
-// Positions per thread along y of a new handle's tile-list kernels, per
-// arithmetic (sim_set_plan changes it).
-int default_rows(int prec)
-{
-    (void)prec;
-    return 1;
-}
-
-// Shapes the tile-list kernels accept: tx in {16, 32, 64, 128, 256},
-// tx * ty in {32, 64, 128, 256} threads, 1 to 8 positions per thread along y.
-bool plan_shape_ok(int tx, int ty, int ry, int ctas)
+// Tile shapes the tile-list kernels accept: tx in {16, 32, 64, 128, 256},
+// tx * ty in {32, 64, 128, 256} threads.
+bool plan_shape_ok(int tx, int ty, int ctas)
 {
     const int threads = tx * ty;
     return (tx == 16 || tx == 32 || tx == 64 || tx == 128 || tx == 256) && ty >= 1 &&
-           (threads == 32 || threads == 64 || threads == 128 || threads == 256) && ry >= 1 && ry <= 8 && ctas >= 0;
+           (threads == 32 || threads == 64 || threads == 128 || threads == 256) && ctas >= 0;
 }
 
 void drop_step_graphs(sim_t s)
@@ -486,17 +478,15 @@ void drop_step_graphs(sim_t s)
             }
 }
 
-// The one-problem tile list of a handle: tiles of tx x (ty * ry) positions,
-// CTAs of tx x ty threads, `ctas` CTAs walking the list (0: one per tile).
-// The step graphs, which hold the old list, are rebuilt on the next step.
-sim_status single_plan(sim_t s, int tx, int ty, int ry, int ctas)
+// The one-problem tile list of a handle: tiles of tx x ty threads, `ctas`
+// CTAs walking the list (0: one per tile).  The step graphs, which hold the
+// old list, are rebuilt on the next step.
+sim_status single_plan(sim_t s, int tx, int ty, int ctas)
 {
     const Inst one = inst_of(s, tx, 0);
-    const int ntiles = tiles_of(s, tx, ty * ry);
+    const int ntiles = tiles_of(s, tx, ty);
     CUDA_TRY(s, cudaMemcpyAsync(s->d_inst, &one, sizeof(Inst), cudaMemcpyHostToDevice, s->stream));
-    BatchPlan bp{s->d_inst, s->d_tiles, 1, ntiles, tx, ty, ctas > 0 ? std::min(ctas, ntiles) : ntiles, one};
-    bp.ry = ry;
-    s->plan = bp;
+    s->plan = BatchPlan{s->d_inst, s->d_tiles, 1, ntiles, tx, ty, ctas > 0 ? std::min(ctas, ntiles) : ntiles, one};
     drop_step_graphs(s);
     return SIM_OK;
 }
@@ -736,7 +726,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         return SIM_ENOMEM;
     }
     CUDA_TRY(s, cudaMemsetAsync(s->d_tiles, 0, sizeof(int), s->stream));
-    st = single_plan(s, 32, 8, default_rows(prec_of(s)), 0);
+    st = single_plan(s, 32, 8, 0);
     if (st != SIM_OK) {
         sim_destroy(s);
         return st;
@@ -1044,15 +1034,15 @@ extern "C" sim_status sim_coefficients(sim_t s, double out[9])
     return SIM_OK;
 }
 
-extern "C" sim_status sim_set_plan(sim_t s, int tile_x, int tile_y, int rows, int ctas)
+extern "C" sim_status sim_set_plan(sim_t s, int tile_x, int tile_y, int ctas)
 {
     if (!s) return SIM_EINVAL;
-    if (!plan_shape_ok(tile_x, tile_y, rows, ctas))
+    if (!plan_shape_ok(tile_x, tile_y, ctas))
         return fail(s, SIM_EINVAL,
-                    "tile %d x %d, %d rows per thread, %d CTAs: want 32, 64, 128 or 256 threads, tile x in "
-                    "{16, ..., 256}, 1 to 8 rows, CTAs >= 0", tile_x, tile_y, rows, ctas);
+                    "tile %d x %d with %d CTAs: want 32, 64, 128 or 256 threads, tile x in {16, ..., 256}, "
+                    "CTAs >= 0", tile_x, tile_y, ctas);
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
-    sim_status st = single_plan(s, tile_x, tile_y, rows, ctas);
+    sim_status st = single_plan(s, tile_x, tile_y, ctas);
     if (st != SIM_OK) return st;
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
     return SIM_OK;
@@ -1178,14 +1168,14 @@ void drop_graphs(sim_batch_t b)
 
 // Tile list for a tile shape: every problem's (nx+1) x (ny+1) positions cut
 // into tx x ty tiles; `grid` resident CTAs walk the list.
-sim_status plan_tiles(sim_batch_t b, int tx, int ty, int grid, int ry = 1)
+sim_status plan_tiles(sim_batch_t b, int tx, int ty, int grid)
 {
     std::vector<Inst> host(b->inst.size());
     std::vector<int> tiles;
     for (size_t q = 0; q < b->inst.size(); q++) {
         const sim_t s = b->inst[q];
         host[q] = inst_of(s, tx, (int)tiles.size());
-        tiles.insert(tiles.end(), (size_t)tiles_of(s, tx, ty * ry), (int)q);
+        tiles.insert(tiles.end(), (size_t)tiles_of(s, tx, ty), (int)q);
     }
     if (!b->d_inst)
         BCUDA_TRY(b, cudaMalloc(&b->d_inst, host.size() * sizeof(Inst)));
@@ -1200,7 +1190,6 @@ sim_status plan_tiles(sim_batch_t b, int tx, int ty, int grid, int ry = 1)
     BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
     b->plan = BatchPlan{b->d_inst, b->d_tiles, (int)host.size(), (int)tiles.size(), tx, ty,
                         grid > 0 ? std::min(grid, (int)tiles.size()) : (int)tiles.size(), host[0]};
-    b->plan.ry = ry;
     drop_graphs(b);
     return SIM_OK;
 }
@@ -1326,10 +1315,10 @@ extern "C" sim_status sim_batch_residuals(sim_batch_t b, int instance, double ou
 
 namespace {
 
-// Autotuner of sim_batch_tune / sim_batch_tune_plan: every tile shape x rows
-// per thread x CTA count of the candidate lists, each timed over three steps
-// after one warm-up step from the same saved state.
-sim_status tune_batch(sim_batch_t b, int scheme, const int *rows_list, int n_rows, int out[4])
+// Autotuner of sim_batch_tune: every tile shape x CTA count of the candidate
+// lists, each timed over three steps after one warm-up step from the same
+// saved state.
+sim_status tune_batch(sim_batch_t b, int scheme, int out[3])
 {
     const bool implicit = scheme & SIM_IMPLICIT, tvd = scheme & SIM_TVD;
     // keep a copy of every problem's current level (FP64 and FP32 shadow) and
@@ -1388,12 +1377,11 @@ sim_status tune_batch(sim_batch_t b, int scheme, const int *rows_list, int n_row
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bx = 32, by = 8, bg = 0, br = 1;
+    int bx = 32, by = 8, bg = 0;
     sim_status st = SIM_OK;
     for (auto &sh : shapes) {
-      for (int ri = 0; ri < n_rows && st == SIM_OK; ri++) {
         for (int gsz : grids) {
-            if ((st = plan_tiles(b, sh[0], sh[1], gsz, rows_list[ri])) != SIM_OK) break;
+            if ((st = plan_tiles(b, sh[0], sh[1], gsz)) != SIM_OK) break;
             int lv = start;
             lv = enqueue_batch_step(b, lv, implicit, tvd, b->stream);     // warm-up
             cudaEventRecord(e0, b->stream);
@@ -1410,7 +1398,6 @@ sim_status tune_batch(sim_batch_t b, int scheme, const int *rows_list, int n_row
                 bx = sh[0];
                 by = sh[1];
                 bg = gsz;
-                br = rows_list[ri];
             }
             // next candidate starts from the saved state again
             if (copy_state(false) != cudaSuccess) {
@@ -1418,8 +1405,7 @@ sim_status tune_batch(sim_batch_t b, int scheme, const int *rows_list, int n_row
                 break;
             }
         }
-      }
-      if (st != SIM_OK) break;
+        if (st != SIM_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1427,11 +1413,10 @@ sim_status tune_batch(sim_batch_t b, int scheme, const int *rows_list, int n_row
     cudaFree(save);
     if (st != SIM_OK) return st;
     set_levels(b, start);
-    if ((st = plan_tiles(b, bx, by, bg, br)) != SIM_OK) return st;
+    if ((st = plan_tiles(b, bx, by, bg)) != SIM_OK) return st;
     out[0] = bx;
     out[1] = by;
     out[2] = b->plan.grid;
-    out[3] = br;
     return SIM_OK;
 }
 
@@ -1440,34 +1425,18 @@ sim_status tune_batch(sim_batch_t b, int scheme, const int *rows_list, int n_row
 extern "C" sim_status sim_batch_tune(sim_batch_t b, int scheme, int out[3])
 {
     if (!b || !out || (scheme & ~3)) return SIM_EINVAL;
-    const int rows[1] = {1};
-    int o[4];
-    sim_status st = tune_batch(b, scheme, rows, 1, o);
-    if (st == SIM_OK) std::memcpy(out, o, 3 * sizeof(int));
-    return st;
-}
-
-extern "C" sim_status sim_batch_tune_plan(sim_batch_t b, int scheme, int out[4])
-{
-    if (!b || !out || (scheme & ~3)) return SIM_EINVAL;
-    const int rows[3] = {1, 2, 4};
-    return tune_batch(b, scheme, rows, 3, out);
-}
-
-extern "C" sim_status sim_batch_set_plan(sim_batch_t b, int tx, int ty, int rows, int ctas)
-{
-    if (!b) return SIM_EINVAL;
-    if (!plan_shape_ok(tx, ty, rows, ctas))
-        return bfail(b, SIM_EINVAL,
-                     "tile %d x %d, %d rows per thread, %d CTAs: want 32, 64, 128 or 256 threads, tile x in "
-                     "{16, ..., 256}, 1 to 8 rows, CTAs >= 0", tx, ty, rows, ctas);
-    BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
-    return plan_tiles(b, tx, ty, ctas, rows);
+    return tune_batch(b, scheme, out);
 }
 
 extern "C" sim_status sim_batch_set_tiles(sim_batch_t b, int tx, int ty, int ctas)
 {
-    return sim_batch_set_plan(b, tx, ty, 1, ctas);
+    if (!b) return SIM_EINVAL;
+    if (!plan_shape_ok(tx, ty, ctas))
+        return bfail(b, SIM_EINVAL,
+                     "tile %d x %d with %d CTAs: want 32, 64, 128 or 256 threads, tile x in {16, ..., 256}, CTAs >= 0",
+                     tx, ty, ctas);
+    BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
+    return plan_tiles(b, tx, ty, ctas);
 }
 
 extern "C" const char *sim_batch_last_error(sim_batch_t b)

@@ -168,17 +168,14 @@ struct Inst {
     int tile0;            // index of this problem's first tile in the batch
 };
 
-// Work distribution of the equation kernels: tiles of tx x (ty * ry)
-// positions over every problem of the list, each taken by one CTA of tx x ty
-// threads (tx * ty <= 256) in which a thread owns the ry positions (i, j),
-// (i, j + ty), ..., (i, j + (ry - 1) ty); `grid` CTAs walk the list.
+// Work distribution of the equation kernels: tiles of tx x ty threads
+// (tx * ty <= 256) over every problem of the list, walked by `grid` CTAs.
 struct BatchPlan {
     const Inst *inst;
     const int *tile_inst; // problem of each tile
     int n_inst, n_tiles;
     int tx, ty, grid;
     Inst one;             // copy of inst[0], read from the launch parameters when n_inst == 1
-    int ry = 1;           // positions per thread along y
 };
 
 // Boundary description used by the ghost refresh.

@@ -191,10 +191,16 @@ __device__ __forceinline__ R gamma_corner(const GeoT<R> &g, const R *gam, int c,
 // ------------------------------------------------------ residual reduction
 
 // Ordered key of |x|: the bits of an FP64 value without its sign, ordered like
-// |x| as unsigned integers, NaN above infinity (integer pipe only).
+// |x| as unsigned integers, NaN above infinity.  The sign is cleared by a
+// 32-bit AND on the high word (inline PTX): written as a 64-bit mask, the
+// compiler had turned it into an FP64 absolute value, one instruction on
+// GB300's narrow FP64 pipe per residual.
 __device__ __forceinline__ unsigned long long ordered_bits(double x)
 {
-    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+    unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    asm("and.b32 %0, %0, 0x7fffffff;" : "+r"(hi));
+    return ((unsigned long long)hi << 32) | lo;
 }
 
 // FP32 <-> FP64 conversions on the integer pipe.  On GB300 the F2F
@@ -885,9 +891,10 @@ __device__ __forceinline__ void assemble_body(const GeoT<R> &g, const CoefT<R> &
 template <typename R>
 __device__ __forceinline__ void pressure_body(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev,
                                               const LevelT<R> &old, const LevelT<R> &nw, const WorkT<R> &w,
-                                              unsigned long long &rp, unsigned long long &rT, int i, int j)
+                                              unsigned long long *res, int i, int j)
 {
     const int P = g.pitch;
+    unsigned long long rp = 0, rT = 0;
     if (i < g.nx && j < g.ny) {
         const int c = Ix{P}(i, j);
         if (g.flag[c] & F_FLUID) {
@@ -907,10 +914,11 @@ __device__ __forceinline__ void pressure_body(const GeoT<R> &g, const CoefT<R> &
             nw.p[c] = pn;
             nw.rho[c] = pn * inv_T;
             nw.gam[c] = gamma_of(Tn, k.omega);
-            rp = max(rp, res_key(pn - old.p[c]));
-            rT = max(rT, res_key(Tn - old.T[c]));
+            rp = res_key(pn - old.p[c]);
+            rT = res_key(Tn - old.T[c]);
         }
     }
+    block_max2(rp, rT, &res[2], &res[3]);
 }
 
 // -------------------------------------------------------------- velocity
@@ -941,26 +949,28 @@ __device__ __forceinline__ void outflow_copy(int j, int ny, int c, LevelT<R> L)
 // then the outflow ghost copies of the row.
 template <typename R>
 __device__ __forceinline__ void velocity_body(const GeoT<R> &g, const LevelT<R> &old, const LevelT<R> &nw,
-                                              const WorkT<R> &w, unsigned long long &ru, unsigned long long &rv,
-                                              int east_outflow, int i, int j)
+                                              const WorkT<R> &w, unsigned long long *res, int east_outflow, int i,
+                                              int j)
 {
     const int P = g.pitch;
+    unsigned long long ru = 0, rv = 0;
     if (i <= g.nx && j <= g.ny) {
         const int c = Ix{P}(i, j);
         const uint16_t f = g.flag[c];
         if (j < g.ny && (f & F_UACT)) {
             const R un = w.uhat[c] - w.du[c] * (nw.p[c] - nw.p[c - 1]);
             nw.u[c] = un;
-            ru = max(ru, res_key(un - old.u[c]));
+            ru = res_key(un - old.u[c]);
         }
         if (i < g.nx && (f & F_VACT)) {
             const R vn = w.vhat[c] - w.dv[c] * (nw.p[c] - nw.p[c - P]);
             nw.v[c] = vn;
-            rv = max(rv, res_key(vn - old.v[c]));
+            rv = res_key(vn - old.v[c]);
         }
         if (east_outflow && i == g.nx - 1)
             outflow_copy(j, g.ny, c, nw);
     }
+    block_max2(ru, rv, &res[0], &res[1]);
 }
 
 // ------------------------------------------------------------ ghost copies
@@ -1068,9 +1078,10 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
                                                     const CoefT<float> &k32, const Level &prev, const Level &old,
                                                     const Level &nw, const LevelT<float> &old32,
                                                     const LevelT<float> &nw32, const WorkT<float> &w,
-                                                    unsigned long long &rp, unsigned long long &rT, int i, int j)
+                                                    unsigned long long *res, int i, int j)
 {
     const int P = g.pitch;
+    unsigned long long rp = 0, rT = 0;
     if (i < g.nx && j < g.ny) {
         const int c = Ix{P}(i, j);
         if (g.flag[c] & F_FLUID) {
@@ -1105,10 +1116,11 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
             nw32.p[c] = narrow(pn);
             nw32.rho[c] = narrow(rho);
             nw32.gam[c] = gm;
-            rp = max(rp, ordered_bits(pn - old.p[c]));
-            rT = max(rT, ordered_bits(widen(T32 - old32.T[c])));
+            rp = ordered_bits(pn - old.p[c]);
+            rT = ordered_bits(widen(T32 - old32.T[c]));
         }
     }
+    block_max2(rp, rT, &res[2], &res[3]);
 }
 
 // Mixed precision, Eqs. pl18, pl19: FP32 correction of the FP32 pseudo
@@ -1117,10 +1129,10 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
 // FP64 bit patterns.
 __device__ __forceinline__ void velocity_mixed_body(const Geo &g, const Level &nw, const LevelT<float> &old32,
                                                     const LevelT<float> &nw32, const WorkT<float> &w,
-                                                    unsigned long long &ru, unsigned long long &rv, int east_outflow,
-                                                    int i, int j)
+                                                    unsigned long long *res, int east_outflow, int i, int j)
 {
     const int P = g.pitch;
+    unsigned long long ru = 0, rv = 0;
     if (i <= g.nx && j <= g.ny) {
         const int c = Ix{P}(i, j);
         const uint16_t f = g.flag[c];
@@ -1128,19 +1140,20 @@ __device__ __forceinline__ void velocity_mixed_body(const Geo &g, const Level &n
             const float un32 = w.uhat[c] - w.du[c] * narrow(nw.p[c] - nw.p[c - 1]);
             nw.u[c] = widen(un32);
             nw32.u[c] = un32;
-            ru = max(ru, ordered_bits(widen(un32 - old32.u[c])));
+            ru = ordered_bits(widen(un32 - old32.u[c]));
         }
         if (i < g.nx && (f & F_VACT)) {
             const float vn32 = w.vhat[c] - w.dv[c] * narrow(nw.p[c] - nw.p[c - P]);
             nw.v[c] = widen(vn32);
             nw32.v[c] = vn32;
-            rv = max(rv, ordered_bits(widen(vn32 - old32.v[c])));
+            rv = ordered_bits(widen(vn32 - old32.v[c]));
         }
         if (east_outflow && i == g.nx - 1) {
             outflow_copy(j, g.ny, c, nw);
             outflow_copy(j, g.ny, c, nw32);
         }
     }
+    block_max2(ru, rv, &res[0], &res[1]);
 }
 
 // FP32 shadow copy of a whole FP64 level (every element, ghosts included).
@@ -1191,16 +1204,9 @@ __device__ __forceinline__ void for_tiles(const BatchPlan &bp, F &&f)
         const Inst &I = sI;
         const int lt = t - I.tile0;
         const int i = (lt % I.tiles_x) * bp.tx + threadIdx.x;
-        const int j0 = (lt / I.tiles_x) * (bp.ty * bp.ry) + threadIdx.y;
-        f(I, i, j0);
+        const int j = (lt / I.tiles_x) * bp.ty + threadIdx.y;
+        f(I, i, j);
     }
-}
-
-// The ry positions (i, j0), (i, j0 + ty), ... of the calling thread in its tile.
-template <typename F>
-__device__ __forceinline__ void for_rows(const BatchPlan &bp, int j0, F &&f)
-{
-    for (int r = 0; r < bp.ry; r++) f(j0 + r * bp.ty);
 }
 
 // The residual words of every problem of the list to 0.  The face kernel
@@ -1220,34 +1226,30 @@ template <int PREC, bool TVD>
 __global__ void __launch_bounds__(256) k_faces(const __grid_constant__ BatchPlan bp, int level, int limiters)
 {
     reset_residuals(bp);
-    for_tiles(bp, [&](const Inst &I, int i, int j0) {
-        for_rows(bp, j0, [&](int j) {
-            if constexpr (PREC == PREC_MIXED) {
-                const LevelT<float> &L = I.lv32[level];
-                face_densities_body<float, TVD>(I.g32, I.k32, L.u, L.v, L.rho, L.gam, L.T, limiters, I.w32, i, j);
-            } else if constexpr (PREC == PREC_DF64) {
-                const LevelT<df64> &L = I.lvdf[level];
-                face_densities_body<df64, TVD>(I.gdf, I.kdf, L.u, L.v, L.rho, L.gam, L.T, limiters, I.wdf, i, j);
-            } else {
-                const Level &L = I.lv[level];
-                face_densities_body<double, TVD>(I.g, I.k, L.u, L.v, L.rho, L.gam, L.T, limiters, I.w, i, j);
-            }
-        });
+    for_tiles(bp, [&](const Inst &I, int i, int j) {
+        if constexpr (PREC == PREC_MIXED) {
+            const LevelT<float> &L = I.lv32[level];
+            face_densities_body<float, TVD>(I.g32, I.k32, L.u, L.v, L.rho, L.gam, L.T, limiters, I.w32, i, j);
+        } else if constexpr (PREC == PREC_DF64) {
+            const LevelT<df64> &L = I.lvdf[level];
+            face_densities_body<df64, TVD>(I.gdf, I.kdf, L.u, L.v, L.rho, L.gam, L.T, limiters, I.wdf, i, j);
+        } else {
+            const Level &L = I.lv[level];
+            face_densities_body<double, TVD>(I.g, I.k, L.u, L.v, L.rho, L.gam, L.T, limiters, I.w, i, j);
+        }
     });
 }
 
 template <int PREC, bool TVD>
 __global__ void __launch_bounds__(256) k_explicit(const __grid_constant__ BatchPlan bp, int prev)
 {
-    for_tiles(bp, [&](const Inst &I, int i, int j0) {
-        for_rows(bp, j0, [&](int j) {
-            if constexpr (PREC == PREC_MIXED)
-                explicit_terms_body<float, TVD>(I.g32, I.k32, I.lv32[prev], I.w32, i, j);
-            else if constexpr (PREC == PREC_DF64)
-                explicit_terms_body<df64, TVD>(I.gdf, I.kdf, I.lvdf[prev], I.wdf, i, j);
-            else
-                explicit_terms_body<double, TVD>(I.g, I.k, I.lv[prev], I.w, i, j);
-        });
+    for_tiles(bp, [&](const Inst &I, int i, int j) {
+        if constexpr (PREC == PREC_MIXED)
+            explicit_terms_body<float, TVD>(I.g32, I.k32, I.lv32[prev], I.w32, i, j);
+        else if constexpr (PREC == PREC_DF64)
+            explicit_terms_body<df64, TVD>(I.gdf, I.kdf, I.lvdf[prev], I.wdf, i, j);
+        else
+            explicit_terms_body<double, TVD>(I.g, I.k, I.lv[prev], I.w, i, j);
     });
 }
 
@@ -1260,54 +1262,42 @@ template <int PREC, bool IMPL, bool TVD>
 __global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 2 : 4) k_assemble(const __grid_constant__ BatchPlan bp,
                                                                               int prev, int old, int nw)
 {
-    for_tiles(bp, [&](const Inst &I, int i, int j0) {
-        for_rows(bp, j0, [&](int j) {
-            if constexpr (PREC == PREC_MIXED)
-                assemble_body<float, IMPL, TVD>(I.g32, I.k32, I.lv32[prev], I.lv32[old], I.lv32[nw].T,
-                                               I.lv[nw].T, I.w32, i, j);
-            else if constexpr (PREC == PREC_DF64)
-                assemble_body<df64, IMPL, TVD>(I.gdf, I.kdf, I.lvdf[prev], I.lvdf[old], I.lvdf[nw].T, nullptr,
-                                              I.wdf, i, j);
-            else
-                assemble_body<double, IMPL, TVD>(I.g, I.k, I.lv[prev], I.lv[old], I.lv[nw].T, nullptr, I.w, i, j);
-        });
+    for_tiles(bp, [&](const Inst &I, int i, int j) {
+        if constexpr (PREC == PREC_MIXED)
+            assemble_body<float, IMPL, TVD>(I.g32, I.k32, I.lv32[prev], I.lv32[old], I.lv32[nw].T, I.lv[nw].T,
+                                           I.w32, i, j);
+        else if constexpr (PREC == PREC_DF64)
+            assemble_body<df64, IMPL, TVD>(I.gdf, I.kdf, I.lvdf[prev], I.lvdf[old], I.lvdf[nw].T, nullptr, I.wdf,
+                                          i, j);
+        else
+            assemble_body<double, IMPL, TVD>(I.g, I.k, I.lv[prev], I.lv[old], I.lv[nw].T, nullptr, I.w, i, j);
     });
 }
 
-// The residual kernels reduce the maxima of the tile's positions once per
-// tile (warp shuffles, shared memory, one atomicMax per word and CTA).
 template <int PREC>
 __global__ void __launch_bounds__(256) k_pressure(const __grid_constant__ BatchPlan bp, int prev, int old, int nw)
 {
-    for_tiles(bp, [&](const Inst &I, int i, int j0) {
-        unsigned long long rp = 0, rT = 0;
-        for_rows(bp, j0, [&](int j) {
-            if constexpr (PREC == PREC_MIXED)
-                pressure_mixed_body(I.g, I.k, I.g32, I.k32, I.lv[prev], I.lv[old], I.lv[nw], I.lv32[old],
-                                    I.lv32[nw], I.w32, rp, rT, i, j);
-            else if constexpr (PREC == PREC_DF64)
-                pressure_body<df64>(I.gdf, I.kdf, I.lvdf[prev], I.lvdf[old], I.lvdf[nw], I.wdf, rp, rT, i, j);
-            else
-                pressure_body<double>(I.g, I.k, I.lv[prev], I.lv[old], I.lv[nw], I.w, rp, rT, i, j);
-        });
-        block_max2(rp, rT, &I.w.res[2], &I.w.res[3]);
+    for_tiles(bp, [&](const Inst &I, int i, int j) {
+        if constexpr (PREC == PREC_MIXED)
+            pressure_mixed_body(I.g, I.k, I.g32, I.k32, I.lv[prev], I.lv[old], I.lv[nw], I.lv32[old], I.lv32[nw],
+                                I.w32, I.w.res, i, j);
+        else if constexpr (PREC == PREC_DF64)
+            pressure_body<df64>(I.gdf, I.kdf, I.lvdf[prev], I.lvdf[old], I.lvdf[nw], I.wdf, I.w.res, i, j);
+        else
+            pressure_body<double>(I.g, I.k, I.lv[prev], I.lv[old], I.lv[nw], I.w, I.w.res, i, j);
     });
 }
 
 template <int PREC>
 __global__ void __launch_bounds__(256) k_velocity(const __grid_constant__ BatchPlan bp, int old, int nw)
 {
-    for_tiles(bp, [&](const Inst &I, int i, int j0) {
-        unsigned long long ru = 0, rv = 0;
-        for_rows(bp, j0, [&](int j) {
-            if constexpr (PREC == PREC_MIXED)
-                velocity_mixed_body(I.g, I.lv[nw], I.lv32[old], I.lv32[nw], I.w32, ru, rv, I.east_outflow, i, j);
-            else if constexpr (PREC == PREC_DF64)
-                velocity_body<df64>(I.gdf, I.lvdf[old], I.lvdf[nw], I.wdf, ru, rv, I.east_outflow, i, j);
-            else
-                velocity_body<double>(I.g, I.lv[old], I.lv[nw], I.w, ru, rv, I.east_outflow, i, j);
-        });
-        block_max2(ru, rv, &I.w.res[0], &I.w.res[1]);
+    for_tiles(bp, [&](const Inst &I, int i, int j) {
+        if constexpr (PREC == PREC_MIXED)
+            velocity_mixed_body(I.g, I.lv[nw], I.lv32[old], I.lv32[nw], I.w32, I.w.res, I.east_outflow, i, j);
+        else if constexpr (PREC == PREC_DF64)
+            velocity_body<df64>(I.gdf, I.lvdf[old], I.lvdf[nw], I.wdf, I.w.res, I.east_outflow, i, j);
+        else
+            velocity_body<double>(I.g, I.lv[old], I.lv[nw], I.w, I.w.res, I.east_outflow, i, j);
     });
 }
 

@@ -67,7 +67,7 @@ def test_tuning_keeps_the_state_and_the_results():
         a.step(3)
         b.step(3)
         tx, ty, grid = b.tune()
-        assert tx * ty == 256 and grid >= 1
+        assert tx * ty in (128, 256) and grid >= 1
         a.step(4)
         b.step(4)                                  # replays graphs built for the tuned tiles
         for q in range(len(cases)):
@@ -108,31 +108,12 @@ def test_batch_rejects_mixed_loop2_lengths():
     assert e.value.status == sim.SIM_EINVAL
 
 
-@pytest.mark.parametrize("plan", [(32, 8, 2, 0), (32, 8, 4, 0), (32, 4, 4, 304), (64, 4, 2, 0), (16, 16, 3, 0),
-                                  (128, 2, 8, 0), (32, 8, 2, 608)])
-def test_every_plan_with_rows_per_thread_gives_the_same_bits(plan):
-    # sim_batch_set_plan: several positions per thread along y (a tile of
-    # tile_y x rows positions) change which thread computes a position, never
-    # its arithmetic
-    cases = small_batch(n=3, precision=W.FP64)
-    with sim.Batch(cases) as a, sim.Batch(cases) as b:
-        b.set_plan(*plan)
-        a.step(5)
-        b.step(5)
-        for q in range(len(cases)):
-            fa, fb = a.fields(q), b.fields(q)
-            ra, rb = a.residuals(q)[0], b.residuals(q)[0]
-            for k in "uvpT":
-                assert np.array_equal(fa[k], fb[k]), (q, k)
-            np.testing.assert_array_equal(ra, rb)
-
-
 @pytest.mark.parametrize("precision", [W.FP64, W.MIXED, W.DF64], ids=["fp64", "mixed", "df64"])
-@pytest.mark.parametrize("plan", [(32, 8, 1, 0), (32, 8, 2, 0), (32, 8, 4, 0), (64, 4, 3, 456), (32, 4, 8, 0)])
+@pytest.mark.parametrize("plan", [(32, 8, 0), (64, 4, 0), (32, 4, 456), (16, 16, 0), (128, 2, 304), (32, 1, 0)])
 def test_single_problem_plans_give_the_same_bits(plan, precision):
-    # sim_set_plan on one handle, on a ragged grid (37 x 29 positions cut into
-    # tiles of up to 32 rows) with obstacles: every plan, every precision, the
-    # explicit TVD and implicit upwind schemes within one run
+    # sim_set_plan on one handle, on a ragged grid (37 x 29 positions) with
+    # obstacles: every tile shape and CTA count, every precision, the implicit
+    # upwind and explicit TVD schemes within one run
     rng = np.random.default_rng(4)
     nx, ny = 37, 29
     dx, dy = rng.uniform(0.2, 0.35, nx), rng.uniform(0.2, 0.35, ny)
@@ -151,24 +132,9 @@ def test_single_problem_plans_give_the_same_bits(plan, precision):
     np.testing.assert_array_equal(ra, rb)
 
 
-def test_tune_plan_keeps_the_state_and_the_results():
-    cases = small_batch(n=4)
-    with sim.Batch(cases) as a, sim.Batch(cases) as b:
-        a.step(3)
-        b.step(3)
-        tx, ty, grid, rows = b.tune_plan()
-        assert tx * ty in (128, 256) and grid >= 1 and rows in (1, 2, 4)
-        a.step(4)
-        b.step(4)
-        for q in range(len(cases)):
-            fa, fb = a.fields(q), b.fields(q)
-            for k in "uvpT":
-                assert np.array_equal(fa[k], fb[k]), (q, k)
-
-
 def test_set_plan_rejects_other_shapes():
-    with sim.Batch(small_batch(n=1)) as b:
-        for bad in [(32, 8, 0, 0), (32, 8, 9, 0), (32, 3, 1, 0), (32, 8, 2, -1)]:
+    with sim.Simulation(W.c1_small()) as s:
+        for bad in [(32, 3, 0), (8, 32, 0), (512, 1, 0), (32, 8, -1)]:
             with pytest.raises(sim.SimError) as e:
-                b.set_plan(*bad)
+                s.set_plan(*bad)
             assert e.value.status == sim.SIM_EINVAL
