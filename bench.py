@@ -449,8 +449,8 @@ def run_paper_sweep(args, local_rank):
 
 # ------------------------------------------------------------ plan sweep
 
-PLAN_CANDIDATES = [(32, 8, 0), (32, 4, 0), (64, 4, 0), (64, 2, 0), (128, 2, 0), (16, 16, 0), (32, 8, 608),
-                   (32, 8, 1216)]
+PLAN_CANDIDATES = [(32, 8, 0, 0), (32, 4, 0, 0), (64, 2, 0, 0), (32, 4, 0, 608), (32, 4, 0, 1216),
+                   (32, 4, 0, 304), (32, 8, 0, 608), (32, 2, 0, 0), (32, 2, 0, 608)]
 
 
 def run_plan_sweep(args, local_rank):

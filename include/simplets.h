@@ -204,11 +204,14 @@ sim_status sim_coefficients(sim_t sim, double out[9]);
 
 /* Work distribution of the handle's equation kernels (not part of the method;
  * every distribution gives the same bits): tiles of tile_x x tile_y threads,
- * one grid position per thread, walked by `ctas` CTAs (0: one CTA per tile).
+ * one grid position per thread, walked by `ctas` CTAs (0: one CTA per tile);
+ * the assembly kernel by `asm_ctas` CTAs (0: as the others).
  * tile_x in {16, 32, 64, 128, 256}; tile_x * tile_y in {32, 64, 128, 256}.
- * The default is 32 x 8, one CTA per tile.  Synchronous; the captured step
- * graphs are rebuilt on the next sim_step.  Errors: SIM_EINVAL, SIM_ECUDA. */
-sim_status sim_set_plan(sim_t sim, int tile_x, int tile_y, int ctas);
+ * Defaults (measured on the 4864x1216 channel): 32 x 4 tiles, one CTA per
+ * tile, the mixed path's assembly on 4 CTAs per SM; 32 x 8 for SIM_DF64.
+ * Synchronous; the captured step graphs are rebuilt on the next sim_step.
+ * Errors: SIM_EINVAL, SIM_ECUDA. */
+sim_status sim_set_plan(sim_t sim, int tile_x, int tile_y, int ctas, int asm_ctas);
 
 /* Kernel classes of the sweep, for sim_profile_read. */
 enum { SIM_K_FACES = 0, SIM_K_ASSEMBLE = 1, SIM_K_PRESSURE = 2, SIM_K_VELOCITY = 3, SIM_K_GHOSTS = 4,

@@ -78,7 +78,7 @@ _SIGNATURES = {
     "sim_get_state": ([ctypes.c_void_p, _DP, _DP, _DP, _DP, _DP], ctypes.c_int),
     "sim_residuals": ([ctypes.c_void_p, _DP, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sim_coefficients": ([ctypes.c_void_p, _DP], ctypes.c_int),
-    "sim_set_plan": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "sim_set_plan": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "sim_profile": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "sim_profile_read": ([ctypes.c_void_p, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "sim_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
@@ -296,9 +296,9 @@ class Simulation:
         arr = _CudaArray(base, (ny + 4, nx + 4), (pitch.value * 8, 8))
         return torch.as_tensor(arr, device="cuda")
 
-    def set_plan(self, tile_x: int = 32, tile_y: int = 8, ctas: int = 0):
+    def set_plan(self, tile_x: int = 32, tile_y: int = 8, ctas: int = 0, asm_ctas: int = 0):
         """Work distribution of the equation kernels (sim_set_plan); the same bits for every choice."""
-        self._check(self.lib.sim_set_plan(self.handle, int(tile_x), int(tile_y), int(ctas)))
+        self._check(self.lib.sim_set_plan(self.handle, int(tile_x), int(tile_y), int(ctas), int(asm_ctas)))
 
     def profile(self, enable: bool = True, timing: bool = True):
         """enable=True: clear the launch counters; timing=True also brackets every

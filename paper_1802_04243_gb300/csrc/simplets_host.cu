@@ -479,16 +479,37 @@ void drop_step_graphs(sim_t s)
 }
 
 // The one-problem tile list of a handle: tiles of tx x ty threads, `ctas`
-// CTAs walking the list (0: one per tile).  The step graphs, which hold the
-// old list, are rebuilt on the next step.
-sim_status single_plan(sim_t s, int tx, int ty, int ctas)
+// CTAs walking the list (0: one per tile), the assembly kernel `asm_ctas`
+// (0: as the others).  The step graphs, which hold the old list, are rebuilt
+// on the next step.
+sim_status single_plan(sim_t s, int tx, int ty, int ctas, int asm_ctas)
 {
     const Inst one = inst_of(s, tx, 0);
     const int ntiles = tiles_of(s, tx, ty);
     CUDA_TRY(s, cudaMemcpyAsync(s->d_inst, &one, sizeof(Inst), cudaMemcpyHostToDevice, s->stream));
-    s->plan = BatchPlan{s->d_inst, s->d_tiles, 1, ntiles, tx, ty, ctas > 0 ? std::min(ctas, ntiles) : ntiles, one};
+    s->plan = BatchPlan{s->d_inst, s->d_tiles, 1, ntiles, tx, ty, ctas > 0 ? std::min(ctas, ntiles) : ntiles, one,
+                        asm_ctas > 0 ? std::min(asm_ctas, ntiles) : 0};
     drop_step_graphs(s);
     return SIM_OK;
+}
+
+// The measured best distribution per arithmetic on the 4864x1216 channel
+// (bench.py --sweep plans): FP64 and mixed tiles of 32 x 4 threads, one CTA
+// per tile, and for the mixed path's FP32 assembly four resident CTAs per SM
+// walking the tiles (the descriptor each CTA stages is then read once per
+// CTA instead of once per tile); double-float 32 x 8, one CTA per tile.
+sim_status default_plan(sim_t s)
+{
+    const int prec = prec_of(s);
+    if (prec == PREC_DF64) return single_plan(s, 32, 8, 0, 0);
+    int asm_ctas = 0;
+    if (prec == PREC_MIXED) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            asm_ctas = 4 * sms;
+    }
+    return single_plan(s, 32, 4, 0, asm_ctas);
 }
 
 size_t field_count(const Problem &pb, int f)
@@ -726,7 +747,7 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         return SIM_ENOMEM;
     }
     CUDA_TRY(s, cudaMemsetAsync(s->d_tiles, 0, sizeof(int), s->stream));
-    st = single_plan(s, 32, 8, 0);
+    st = default_plan(s);
     if (st != SIM_OK) {
         sim_destroy(s);
         return st;
@@ -1034,15 +1055,15 @@ extern "C" sim_status sim_coefficients(sim_t s, double out[9])
     return SIM_OK;
 }
 
-extern "C" sim_status sim_set_plan(sim_t s, int tile_x, int tile_y, int ctas)
+extern "C" sim_status sim_set_plan(sim_t s, int tile_x, int tile_y, int ctas, int asm_ctas)
 {
     if (!s) return SIM_EINVAL;
-    if (!plan_shape_ok(tile_x, tile_y, ctas))
+    if (!plan_shape_ok(tile_x, tile_y, ctas) || asm_ctas < 0)
         return fail(s, SIM_EINVAL,
-                    "tile %d x %d with %d CTAs: want 32, 64, 128 or 256 threads, tile x in {16, ..., 256}, "
-                    "CTAs >= 0", tile_x, tile_y, ctas);
+                    "tile %d x %d with %d / %d CTAs: want 32, 64, 128 or 256 threads, tile x in {16, ..., 256}, "
+                    "CTAs >= 0", tile_x, tile_y, ctas, asm_ctas);
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
-    sim_status st = single_plan(s, tile_x, tile_y, ctas);
+    sim_status st = single_plan(s, tile_x, tile_y, ctas, asm_ctas);
     if (st != SIM_OK) return st;
     CUDA_TRY(s, cudaStreamSynchronize(s->stream));
     return SIM_OK;
@@ -1189,7 +1210,7 @@ sim_status plan_tiles(sim_batch_t b, int tx, int ty, int grid)
     BCUDA_TRY(b, cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
     b->plan = BatchPlan{b->d_inst, b->d_tiles, (int)host.size(), (int)tiles.size(), tx, ty,
-                        grid > 0 ? std::min(grid, (int)tiles.size()) : (int)tiles.size(), host[0]};
+                        grid > 0 ? std::min(grid, (int)tiles.size()) : (int)tiles.size(), host[0], 0};
     drop_graphs(b);
     return SIM_OK;
 }

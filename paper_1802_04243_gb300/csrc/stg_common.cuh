@@ -169,13 +169,15 @@ struct Inst {
 };
 
 // Work distribution of the equation kernels: tiles of tx x ty threads
-// (tx * ty <= 256) over every problem of the list, walked by `grid` CTAs.
+// (tx * ty <= 256) over every problem of the list, walked by `grid` CTAs
+// (the assembly kernel by `grid_asm` CTAs when that is positive).
 struct BatchPlan {
     const Inst *inst;
     const int *tile_inst; // problem of each tile
     int n_inst, n_tiles;
     int tx, ty, grid;
     Inst one;             // copy of inst[0], read from the launch parameters when n_inst == 1
+    int grid_asm;         // CTAs of the assembly kernel; 0: grid
 };
 
 // Boundary description used by the ghost refresh.

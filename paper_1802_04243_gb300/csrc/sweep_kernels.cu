@@ -1629,10 +1629,11 @@ template <int PREC>
 void assemble_variant(const BatchPlan &bp, int prev, int old, int nw, bool implicit, bool tvd, cudaStream_t s)
 {
     const dim3 bl(bp.tx, bp.ty);
-    if (implicit && tvd) k_assemble<PREC, true, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
-    else if (implicit) k_assemble<PREC, true, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
-    else if (tvd) k_assemble<PREC, false, true><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
-    else k_assemble<PREC, false, false><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+    const int g = bp.grid_asm > 0 ? bp.grid_asm : bp.grid;
+    if (implicit && tvd) k_assemble<PREC, true, true><<<g, bl, 0, s>>>(bp, prev, old, nw);
+    else if (implicit) k_assemble<PREC, true, false><<<g, bl, 0, s>>>(bp, prev, old, nw);
+    else if (tvd) k_assemble<PREC, false, true><<<g, bl, 0, s>>>(bp, prev, old, nw);
+    else k_assemble<PREC, false, false><<<g, bl, 0, s>>>(bp, prev, old, nw);
 }
 
 void launch_assemble(const BatchPlan &bp, int prec, int prev, int old, int nw, bool implicit, bool tvd,

@@ -109,7 +109,8 @@ def test_batch_rejects_mixed_loop2_lengths():
 
 
 @pytest.mark.parametrize("precision", [W.FP64, W.MIXED, W.DF64], ids=["fp64", "mixed", "df64"])
-@pytest.mark.parametrize("plan", [(32, 8, 0), (64, 4, 0), (32, 4, 456), (16, 16, 0), (128, 2, 304), (32, 1, 0)])
+@pytest.mark.parametrize("plan", [(32, 8, 0, 0), (64, 4, 0, 0), (32, 4, 456, 0), (16, 16, 0, 0), (128, 2, 304, 0),
+                                  (32, 1, 0, 0), (32, 4, 0, 608), (32, 8, 0, 7)])
 def test_single_problem_plans_give_the_same_bits(plan, precision):
     # sim_set_plan on one handle, on a ragged grid (37 x 29 positions) with
     # obstacles: every tile shape and CTA count, every precision, the implicit
@@ -134,7 +135,7 @@ def test_single_problem_plans_give_the_same_bits(plan, precision):
 
 def test_set_plan_rejects_other_shapes():
     with sim.Simulation(W.c1_small()) as s:
-        for bad in [(32, 3, 0), (8, 32, 0), (512, 1, 0), (32, 8, -1)]:
+        for bad in [(32, 3, 0, 0), (8, 32, 0, 0), (512, 1, 0, 0), (32, 8, -1, 0), (32, 8, 0, -1)]:
             with pytest.raises(sim.SimError) as e:
                 s.set_plan(*bad)
             assert e.value.status == sim.SIM_EINVAL
