@@ -283,6 +283,54 @@ void sim_batch_destroy(sim_batch_t batch);
 /* Release every resource of the handle (NULL is a no-op). */
 void sim_destroy(sim_t sim);
 
+/* ------------------------------------------------------------------------
+ * x-strips: one problem decomposed into strips along x (the paper's
+ * decomposition axis for several devices, Section 5), advanced on one device.
+ * Each strip owns the cell columns [own0, own1) of a nearly equal split and
+ * stores its own arrays for the columns it computes: its owned columns and a
+ * halo of SIM_STRIP_HALO columns on each side that faces another strip.  Per
+ * loop-2 iteration every strip runs the sweep's kernels over its owned
+ * columns and its halo (recomputing the halo from the previous iterate), then
+ * one kernel copies the new level's halo columns of every field from the
+ * strip that owns them; the residual maxima count each strip's owned columns
+ * only and are reduced over the strips.  Every owned value is computed by the
+ * same arithmetic as in a whole-problem handle, so the fields and residuals
+ * equal sim_create + sim_step bit for bit.  tol must be 0.
+ * ------------------------------------------------------------------------ */
+#define SIM_STRIP_HALO 4
+typedef struct sim_strips_s *sim_strips_t;
+
+/* Layout of strip `strip` of `n_strips` over nx cells (host only, no device
+ * call): out[0..5] = own0, own1 (owned cell columns [own0, own1)), store0,
+ * store1 (stored columns of the extended grid, [store0, store1)), comp0,
+ * comp1 (computed grid positions, [comp0, comp1)).  1 <= n_strips <= 64 and
+ * nx >= 2 * SIM_STRIP_HALO * n_strips.  Errors: SIM_EINVAL. */
+sim_status sim_strips_layout(int nx, int n_strips, int strip, int out[6]);
+
+/* Create the strips of one problem (as for sim_create) on one stream.
+ * Errors: SIM_EINVAL (bad description, tol != 0, a layout outside the limits
+ * above), SIM_ENOMEM, SIM_ECUDA. */
+sim_status sim_strips_create(const sim_grid *grid, const sim_gas *gas, const sim_bc *bc, int n_strips,
+                             void *stream, sim_strips_t *out);
+
+/* Advance n_steps time steps with `scheme` (as sim_step); each step is one
+ * captured CUDA graph.  Asynchronous.  Errors: SIM_EINVAL, SIM_ECUDA. */
+sim_status sim_strips_step(sim_strips_t strips, int n_steps, int scheme);
+
+/* One field of the whole problem, gathered from the strips' owned columns
+ * (as sim_fields).  Synchronous.  Errors: SIM_EINVAL, SIM_ECUDA. */
+sim_status sim_strips_fields(sim_strips_t strips, int field, double *host_dst, size_t n);
+
+/* Residuals of the last loop-2 iteration over the whole problem (as
+ * sim_residuals).  Synchronous.  SIM_EDIVERGED if one is not finite. */
+sim_status sim_strips_residuals(sim_strips_t strips, double out[4]);
+
+/* Text of the last error (never NULL). */
+const char *sim_strips_last_error(sim_strips_t strips);
+
+/* Release the strips (NULL is a no-op). */
+void sim_strips_destroy(sim_strips_t strips);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,14 @@ _SIGNATURES = {
     "sim_batch_set_tiles": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "sim_batch_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
     "sim_batch_destroy": ([ctypes.c_void_p], None),
+    "sim_strips_layout": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "sim_strips_create": ([ctypes.POINTER(sim_grid), ctypes.POINTER(sim_gas), ctypes.POINTER(sim_bc), ctypes.c_int,
+                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "sim_strips_step": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "sim_strips_fields": ([ctypes.c_void_p, ctypes.c_int, _DP, ctypes.c_size_t], ctypes.c_int),
+    "sim_strips_residuals": ([ctypes.c_void_p, _DP], ctypes.c_int),
+    "sim_strips_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
+    "sim_strips_destroy": ([ctypes.c_void_p], None),
     "sim_step_noalloc": ([ctypes.POINTER(sim_grid), ctypes.POINTER(sim_gas), ctypes.POINTER(sim_bc), ctypes.c_int,
                           ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                           ctypes.c_void_p, _DP], ctypes.c_int),
@@ -393,6 +401,79 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             self.lib.sim_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+STRIP_HALO = 4
+
+
+def strips_layout(nx: int, n_strips: int, strip: int) -> Dict[str, tuple]:
+    """Columns of one strip of an x-decomposed problem (sim_strips_layout, host
+    only): owned cell columns, stored columns of the extended grid, computed
+    positions, each as a half-open range."""
+    out = (ctypes.c_int * 6)()
+    st = load().sim_strips_layout(int(nx), int(n_strips), int(strip), out)
+    if st != SIM_OK:
+        raise SimError(st, f"no layout for strip {strip} of {n_strips} over {nx} columns")
+    return {"own": (out[0], out[1]), "store": (out[2], out[3]), "compute": (out[4], out[5])}
+
+
+class Strips:
+    """One problem decomposed into x-strips with halo exchange (sim_strips_*),
+    advanced on one device; results equal a whole-problem Simulation's."""
+
+    def __init__(self, case, n_strips: int, stream: Optional[int] = None):
+        self.lib = load()
+        self.case = case
+        self._desc = _Desc(case)
+        h = ctypes.c_void_p()
+        st = self.lib.sim_strips_create(ctypes.byref(self._desc.grid), ctypes.byref(self._desc.gas),
+                                        ctypes.byref(self._desc.bc), int(n_strips), ctypes.c_void_p(stream or 0),
+                                        ctypes.byref(h))
+        if st != SIM_OK:
+            raise SimError(st, "sim_strips_create failed")
+        self.handle = h
+        self.scheme = scheme_of(case.implicit, case.tvd)
+
+    def _check(self, st: int):
+        if st != SIM_OK:
+            raise SimError(st, self.lib.sim_strips_last_error(self.handle).decode())
+
+    def step(self, n: int = 1, scheme: Optional[int] = None):
+        self._check(self.lib.sim_strips_step(self.handle, int(n), self.scheme if scheme is None else int(scheme)))
+
+    def field(self, name: str) -> np.ndarray:
+        c = self.case
+        shape = {"u": (c.ny, c.nx + 1), "v": (c.ny + 1, c.nx)}.get(name, (c.ny, c.nx))
+        a = np.empty(shape)
+        self._check(self.lib.sim_strips_fields(self.handle, FIELDS[name], a.ctypes.data_as(_DP), a.size))
+        return a
+
+    def fields(self, names: Sequence[str] = ("u", "v", "p", "T")) -> Dict[str, np.ndarray]:
+        return {k: self.field(k) for k in names}
+
+    def residuals(self):
+        out = np.zeros(4)
+        st = self.lib.sim_strips_residuals(self.handle, out.ctypes.data_as(_DP))
+        if st not in (SIM_OK, SIM_EDIVERGED):
+            self._check(st)
+        return out, st
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.sim_strips_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -44,6 +44,15 @@ struct sim_s {
     Problem pb;
     int pitch = 0;
     size_t nelem = 0;                          // elements of one extended field
+    // x-window of the handle: it stores the columns [win_L, win_R) of the
+    // extended grid (a whole problem: [-2, nx + 3)) and computes the positions
+    // of the columns [win_L + 2, win_R - 2); a strip of an x-decomposed
+    // problem (sim_strips_create) stores a window.  The device arrays the
+    // kernels see are the allocations moved back by `shift` elements, so that
+    // element (i, j) keeps its whole-problem index (j + 2) pitch + (i + 2).
+    int win_L = -G, win_R = 0;
+    long shift = 0;
+    int own0 = 0, own_stop = 0;                // columns whose residuals count (own_stop 0: no limit)
     cudaStream_t stream = nullptr;
     Geo geo{};
     Sides sides{};
@@ -417,9 +426,14 @@ Inst inst_of(const sim_s *s, int tx, int tile0)
     I.kdf = s->dfm.k;
     for (int l = 0; l < 3; l++) I.lvdf[l] = s->dfm.lv[l];
     I.wdf = s->dfm.w;
-    I.east_outflow = s->pb.side_kind[SIM_E] == SIM_BC_OUTFLOW;
-    I.tiles_x = (s->pb.nx + 1 + tx - 1) / tx;
+    I.east_outflow = s->sides.kind[SIDE_E] == BC_OUTFLOW;
+    const int c0 = s->win_L + G, c1 = s->win_R - G;
+    I.tiles_x = (c1 - c0 + tx - 1) / tx;
     I.tile0 = tile0;
+    I.x0 = c0;
+    I.x_stop = c1 < s->pb.nx + 1 ? c1 : 0;
+    I.own0 = s->own0;
+    I.own_stop = s->own_stop;
     return I;
 }
 
@@ -444,6 +458,29 @@ R *carve_levels(R *q, size_t nelem, LevelT<R> lv[3], WorkT<R> &w)
     return q;
 }
 
+// The arrays of a level and of the iteration scratch as kernel views: each
+// pointer moved back by d elements (see sim_s::shift); d = 0 for a whole
+// problem.
+template <typename R>
+void shift_views(LevelT<R> lv[3], WorkT<R> &w, long d)
+{
+    for (int l = 0; l < 3; l++) {
+        R **f[6] = {&lv[l].u, &lv[l].v, &lv[l].p, &lv[l].T, &lv[l].rho, &lv[l].gam};
+        for (R **x : f) *x -= d;
+    }
+    R **a[kWorkArrays] = {&w.ru_dy, &w.rv_dx, &w.Fx, &w.Fy, &w.DTx, &w.DTy, &w.Bgc, &w.Bgx, &w.Bgy,
+                          &w.Fbu, &w.Fbv, &w.Su, &w.Sv, &w.uhat, &w.du, &w.vhat, &w.dv, &w.uexp, &w.vexp, &w.Texp,
+                          &w.psTx, &w.psTy, &w.psUx, &w.psUyU, &w.psUyD, &w.psVy, &w.psVxU, &w.psVxD};
+    for (R **x : a) *x -= d;
+}
+
+// A kernel view of a level back to its allocation (whole-array operations).
+template <typename R>
+LevelT<R> alloc_of(const LevelT<R> &v, long d)
+{
+    return LevelT<R>{v.u + d, v.v + d, v.p + d, v.T + d, v.rho + d, v.gam + d};
+}
+
 // The FP64 levels of the current state, brought up to date in DF64 mode.
 void sync_out(sim_t s)
 {
@@ -453,10 +490,12 @@ void sync_out(sim_t s)
     }
 }
 
-// Tiles of tx x ty positions over the (nx + 1) x (ny + 1) positions of a problem.
+// Tiles of tx x ty positions over the positions a handle computes: the
+// (nx + 1) x (ny + 1) positions of a problem, the columns of a strip's window.
 int tiles_of(const sim_s *s, int tx, int ty)
 {
-    return ((s->pb.nx + 1 + tx - 1) / tx) * ((s->pb.ny + 1 + ty - 1) / ty);
+    const int w = s->win_R - s->win_L - 2 * G;
+    return ((w + tx - 1) / tx) * ((s->pb.ny + 1 + ty - 1) / ty);
 }
 
 // Tile shapes the tile-list kernels accept: tx in {16, 32, 64, 128, 256},
@@ -614,6 +653,186 @@ sim_status check_live(sim_t s)
 
 // ====================================================================== ABI
 
+namespace {
+
+// Host-side set-up of a whole problem, shared by every handle built from it
+// (one for sim_create, one per strip for sim_strips_create): the geometry
+// flags, the axis tables and the start state over the extended grid with the
+// whole problem's row pitch gP.
+struct Template {
+    int gP = 0;
+    HostGrid h;
+    std::vector<uint16_t> flags;
+    std::vector<double> ax, ay;
+    std::vector<double> f[6];                  // u v p T rho gam
+};
+
+void make_template(const Problem &pb, Template &t)
+{
+    t.gP = ((pb.nx + 2 * G + 1) + 7) / 8 * 8;
+    t.h.nx = pb.nx;
+    t.h.ny = pb.ny;
+    t.h.P = t.gP;
+    classify(pb, t.h);
+    t.flags = make_flags(t.h);
+    t.ax = make_axis(pb.dx);
+    t.ay = make_axis(pb.dy);
+    const size_t n = (size_t)t.gP * (pb.ny + 2 * G + 1);
+    for (auto &a : t.f) a.assign(n, 0.0);
+    build_start_level(pb, t.h, t.f);
+}
+
+// Allocate and fill the device side of a handle whose problem (s->pb) and
+// stream are set: the columns [L, R) of the extended grid (a whole problem:
+// L = -2, R = nx + 3), with the window's slices of the template's flags and
+// start state, the whole axis tables, rho and Gamma derived on the device,
+// ghosts refreshed, shadow levels of the mixed and double-float paths.  On
+// failure the caller destroys s.
+sim_status build_handle(sim_t s, const Template &t, int L, int R)
+{
+    const Problem &pb = s->pb;
+    s->win_L = L;
+    s->win_R = R;
+    s->shift = L + G;
+    s->pitch = ((R - L) + 7) / 8 * 8;
+    const int rows = pb.ny + 2 * G + 1;
+    s->nelem = (size_t)s->pitch * rows;
+    const bool whole = L == -G && R == pb.nx + G + 1;
+
+    // the window's slices (the whole arrays for a whole problem)
+    std::vector<uint16_t> wflags;
+    std::vector<double> wf[6];
+    const std::vector<uint16_t> *flags = &t.flags;
+    const std::vector<double> *f = t.f;
+    if (!whole) {
+        wflags.assign(s->nelem, 0);
+        for (auto &a : wf) a.assign(s->nelem, 0.0);
+        for (int r = 0; r < rows; r++)
+            for (int i = L; i < R; i++) {
+                const size_t gq = (size_t)r * t.gP + (i + G), lq = (size_t)r * s->pitch + (i - L);
+                wflags[lq] = t.flags[gq];
+                for (int k = 0; k < 6; k++) wf[k][lq] = t.f[k][gq];
+            }
+        flags = &wflags;
+        f = wf;
+    }
+
+    // one pool for 3 levels x 6 fields + the work arrays
+    cudaError_t e = cudaMalloc(&s->d_pool, kPoolArrays * s->nelem * sizeof(double));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA;
+    Work &w = s->work;
+    carve_levels(s->d_pool, s->nelem, s->lv, static_cast<WorkT<double> &>(w));
+    const size_t nax = t.ax.size(), nay = t.ay.size();
+    const size_t stage = (size_t)(pb.nx + 1) * (pb.ny + 1);
+    if (cudaMalloc(&s->d_flag, s->nelem * sizeof(uint16_t)) != cudaSuccess ||
+        cudaMalloc(&s->d_axis, (nax + nay) * sizeof(double)) != cudaSuccess ||
+        (whole && cudaMalloc(&s->d_stage, stage * sizeof(double)) != cudaSuccess) ||
+        cudaMalloc(&w.res, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&s->h_res, 4 * sizeof(unsigned long long)) != cudaSuccess)
+        return SIM_ENOMEM;
+
+    s->geo.nx = pb.nx;
+    s->geo.ny = pb.ny;
+    s->geo.pitch = s->pitch;
+    s->geo.flag = s->d_flag - s->shift;
+    const int mx = pb.nx + 2 * G + 1, my = pb.ny + 2 * G + 1;
+    const double *dax = s->d_axis, *day = s->d_axis + nax;
+    s->geo.x = axis_view(dax, mx);
+    s->geo.y = axis_view(day, my);
+    for (int k = 0; k < 4; k++) s->sides.kind[k] = pb.side_kind[k];
+    if (!whole) {
+        if (L > -G) s->sides.kind[SIDE_W] = BC_INTERFACE;
+        if (R < pb.nx + G + 1) s->sides.kind[SIDE_E] = BC_INTERFACE;
+        s->sides.col0 = L;
+        s->sides.col1 = R;
+    }
+
+    s->mixed = pb.precision == SIM_MIXED;
+    if (s->mixed) {
+        if (cudaMalloc(&s->d_pool32, kPoolArrays * s->nelem * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&s->d_axis32, (nax + nay) * sizeof(float)) != cudaSuccess)
+            return SIM_ENOMEM;
+        carve_levels(s->d_pool32, s->nelem, s->mx.lv, s->mx.w);
+        const float *fx = s->d_axis32, *fy = s->d_axis32 + nax;
+        s->mx.g.nx = pb.nx;
+        s->mx.g.ny = pb.ny;
+        s->mx.g.pitch = s->pitch;
+        s->mx.g.flag = s->geo.flag;
+        s->mx.g.x = axis_view(fx, mx);
+        s->mx.g.y = axis_view(fy, my);
+        const Coef &k = pb.k;
+        s->mx.k = CoefT<float>{(float)k.A, (float)k.B, (float)k.CT1f, (float)k.CT2f, (float)k.CT3f,
+                               (float)k.omega, (float)k.dt, (float)k.gx, (float)k.gy, (float)k.hrdt,
+                               (float)k.zeta, (float)k.tau};
+        std::vector<float> a32(nax + nay);
+        for (size_t q = 0; q < nax; q++) a32[q] = (float)t.ax[q];
+        for (size_t q = 0; q < nay; q++) a32[nax + q] = (float)t.ay[q];
+        CUDA_TRY(s, cudaMemcpy(s->d_axis32, a32.data(), a32.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CUDA_TRY(s, cudaMemsetAsync(s->mx.w.ru_dy, 0, kWorkArrays * s->nelem * sizeof(float), s->stream));
+    }
+
+    s->df = pb.precision == SIM_DF64;
+    if (s->df) {
+        if (cudaMalloc(&s->d_pooldf, kPoolArrays * s->nelem * sizeof(df64)) != cudaSuccess ||
+            cudaMalloc(&s->d_axisdf, (nax + nay) * sizeof(df64)) != cudaSuccess)
+            return SIM_ENOMEM;
+        carve_levels(s->d_pooldf, s->nelem, s->dfm.lv, s->dfm.w);
+        const df64 *fx = s->d_axisdf, *fy = s->d_axisdf + nax;
+        s->dfm.g.nx = pb.nx;
+        s->dfm.g.ny = pb.ny;
+        s->dfm.g.pitch = s->pitch;
+        s->dfm.g.flag = s->geo.flag;
+        s->dfm.g.x = axis_view(fx, mx);
+        s->dfm.g.y = axis_view(fy, my);
+        const Coef &k = pb.k;
+        s->dfm.k = CoefT<df64>{dfl::split_host(k.A), dfl::split_host(k.B), dfl::split_host(k.CT1f), dfl::split_host(k.CT2f),
+                               dfl::split_host(k.CT3f), dfl::split_host(k.omega), dfl::split_host(k.dt), dfl::split_host(k.gx),
+                               dfl::split_host(k.gy), dfl::split_host(k.hrdt), dfl::split_host(k.zeta),
+                               dfl::split_host(k.tau)};
+        std::vector<df64> adf(nax + nay);
+        for (size_t q = 0; q < nax; q++) adf[q] = dfl::split_host(t.ax[q]);
+        for (size_t q = 0; q < nay; q++) adf[nax + q] = dfl::split_host(t.ay[q]);
+        CUDA_TRY(s, cudaMemcpy(s->d_axisdf, adf.data(), adf.size() * sizeof(df64), cudaMemcpyHostToDevice));
+        CUDA_TRY(s, cudaMemsetAsync(s->dfm.w.ru_dy, 0, kWorkArrays * s->nelem * sizeof(df64), s->stream));
+    }
+
+    CUDA_TRY(s, cudaMemcpyAsync(s->d_flag, flags->data(), s->nelem * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                                s->stream));
+    CUDA_TRY(s, cudaMemcpyAsync(s->d_axis, t.ax.data(), nax * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(s, cudaMemcpyAsync(s->d_axis + nax, t.ay.data(), nay * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(s->work.ru_dy, 0, kWorkArrays * s->nelem * sizeof(double), s->stream));
+    CUDA_TRY(s, cudaMemsetAsync(w.res, 0, 4 * sizeof(unsigned long long), s->stream));
+    for (int l = 0; l < 3; l++)
+        for (int k = 0; k < 6; k++)
+            CUDA_TRY(s, cudaMemcpyAsync(level_field(s->lv[l], k), f[k].data(), s->nelem * sizeof(double),
+                                        cudaMemcpyHostToDevice, s->stream));
+    // from here on the level and scratch pointers are kernel views
+    shift_views<double>(s->lv, s->work, s->shift);
+    if (s->mixed) shift_views<float>(s->mx.lv, s->mx.w, s->shift);
+    if (s->df) shift_views<df64>(s->dfm.lv, s->dfm.w, s->shift);
+    for (int l = 0; l < 3; l++) {
+        if (whole)
+            launch_derive(s->geo, pb.k, s->lv[l], s->stream);
+        else
+            launch_derive_cols(s->geo, pb.k, s->lv[l], L < 0 ? 0 : L, R, s->stream);
+        launch_ghosts(s->geo, s->sides, s->lv[l], false, s->stream);
+        if (s->mixed)
+            launch_shadow(s->geo, alloc_of(s->lv[l], s->shift), alloc_of(s->mx.lv[l], s->shift), s->nelem,
+                          s->stream);
+        if (s->df) launch_split(alloc_of(s->lv[l], s->shift), alloc_of(s->dfm.lv[l], s->shift), s->nelem, s->stream);
+    }
+    if (cudaMalloc(&s->d_inst, sizeof(Inst)) != cudaSuccess || cudaMalloc(&s->d_tiles, sizeof(int)) != cudaSuccess)
+        return SIM_ENOMEM;
+    CUDA_TRY(s, cudaMemsetAsync(s->d_tiles, 0, sizeof(int), s->stream));
+    sim_status st = default_plan(s);
+    if (st != SIM_OK) return st;
+    CUDA_TRY(s, cudaGetLastError());
+    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+}  // namespace
+
 extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const sim_bc *bc, void *stream,
                                  sim_t *out)
 {
@@ -626,134 +845,14 @@ extern "C" sim_status sim_create(const sim_grid *grid, const sim_gas *gas, const
         sim_destroy(s);
         return st;
     }
-    const Problem &pb = s->pb;
     s->stream = (cudaStream_t)stream;
-    s->pitch = ((pb.nx + 2 * G + 1) + 7) / 8 * 8;
-    const int rows = pb.ny + 2 * G + 1;
-    s->nelem = (size_t)s->pitch * rows;
-
-    HostGrid h;
-    h.nx = pb.nx;
-    h.ny = pb.ny;
-    h.P = s->pitch;
-    classify(pb, h);
-    std::vector<uint16_t> flags = make_flags(h);
-    std::vector<double> ax = make_axis(pb.dx), ay = make_axis(pb.dy);
-
-    // one pool for 3 levels x 6 fields + the work arrays
-    cudaError_t e = cudaMalloc(&s->d_pool, kPoolArrays * s->nelem * sizeof(double));
-    if (e != cudaSuccess) {
-        sim_destroy(s);
-        return e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA;
-    }
-    Work &w = s->work;
-    carve_levels(s->d_pool, s->nelem, s->lv, static_cast<WorkT<double> &>(w));
-    const size_t nax = ax.size(), nay = ay.size();
-    const size_t stage = (size_t)(pb.nx + 1) * (pb.ny + 1);
-    if (cudaMalloc(&s->d_flag, flags.size() * sizeof(uint16_t)) != cudaSuccess ||
-        cudaMalloc(&s->d_axis, (nax + nay) * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&s->d_stage, stage * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&w.res, 4 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMallocHost(&s->h_res, 4 * sizeof(unsigned long long)) != cudaSuccess) {
-        sim_destroy(s);
-        return SIM_ENOMEM;
-    }
-
-    s->geo.nx = pb.nx;
-    s->geo.ny = pb.ny;
-    s->geo.pitch = s->pitch;
-    s->geo.flag = s->d_flag;
-    const int mx = pb.nx + 2 * G + 1, my = pb.ny + 2 * G + 1;
-    const double *dax = s->d_axis, *day = s->d_axis + nax;
-    s->geo.x = axis_view(dax, mx);
-    s->geo.y = axis_view(day, my);
-    for (int k = 0; k < 4; k++) s->sides.kind[k] = pb.side_kind[k];
-
-    s->mixed = pb.precision == SIM_MIXED;
-    if (s->mixed) {
-        if (cudaMalloc(&s->d_pool32, kPoolArrays * s->nelem * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&s->d_axis32, (nax + nay) * sizeof(float)) != cudaSuccess) {
-            sim_destroy(s);
-            return SIM_ENOMEM;
-        }
-        carve_levels(s->d_pool32, s->nelem, s->mx.lv, s->mx.w);
-        const float *fx = s->d_axis32, *fy = s->d_axis32 + nax;
-        s->mx.g.nx = pb.nx;
-        s->mx.g.ny = pb.ny;
-        s->mx.g.pitch = s->pitch;
-        s->mx.g.flag = s->d_flag;
-        s->mx.g.x = axis_view(fx, mx);
-        s->mx.g.y = axis_view(fy, my);
-        const Coef &k = pb.k;
-        s->mx.k = CoefT<float>{(float)k.A, (float)k.B, (float)k.CT1f, (float)k.CT2f, (float)k.CT3f,
-                               (float)k.omega, (float)k.dt, (float)k.gx, (float)k.gy, (float)k.hrdt,
-                               (float)k.zeta, (float)k.tau};
-        std::vector<float> a32(nax + nay);
-        for (size_t q = 0; q < nax; q++) a32[q] = (float)ax[q];
-        for (size_t q = 0; q < nay; q++) a32[nax + q] = (float)ay[q];
-        CUDA_TRY(s, cudaMemcpy(s->d_axis32, a32.data(), a32.size() * sizeof(float), cudaMemcpyHostToDevice));
-        CUDA_TRY(s, cudaMemsetAsync(s->mx.w.ru_dy, 0, kWorkArrays * s->nelem * sizeof(float), s->stream));
-    }
-
-    s->df = pb.precision == SIM_DF64;
-    if (s->df) {
-        if (cudaMalloc(&s->d_pooldf, kPoolArrays * s->nelem * sizeof(df64)) != cudaSuccess ||
-            cudaMalloc(&s->d_axisdf, (nax + nay) * sizeof(df64)) != cudaSuccess) {
-            sim_destroy(s);
-            return SIM_ENOMEM;
-        }
-        carve_levels(s->d_pooldf, s->nelem, s->dfm.lv, s->dfm.w);
-        const df64 *fx = s->d_axisdf, *fy = s->d_axisdf + nax;
-        s->dfm.g.nx = pb.nx;
-        s->dfm.g.ny = pb.ny;
-        s->dfm.g.pitch = s->pitch;
-        s->dfm.g.flag = s->d_flag;
-        s->dfm.g.x = axis_view(fx, mx);
-        s->dfm.g.y = axis_view(fy, my);
-        const Coef &k = pb.k;
-        s->dfm.k = CoefT<df64>{dfl::split_host(k.A), dfl::split_host(k.B), dfl::split_host(k.CT1f), dfl::split_host(k.CT2f),
-                               dfl::split_host(k.CT3f), dfl::split_host(k.omega), dfl::split_host(k.dt), dfl::split_host(k.gx),
-                               dfl::split_host(k.gy), dfl::split_host(k.hrdt), dfl::split_host(k.zeta),
-                               dfl::split_host(k.tau)};
-        std::vector<df64> adf(nax + nay);
-        for (size_t q = 0; q < nax; q++) adf[q] = dfl::split_host(ax[q]);
-        for (size_t q = 0; q < nay; q++) adf[nax + q] = dfl::split_host(ay[q]);
-        CUDA_TRY(s, cudaMemcpy(s->d_axisdf, adf.data(), adf.size() * sizeof(df64), cudaMemcpyHostToDevice));
-        CUDA_TRY(s, cudaMemsetAsync(s->dfm.w.ru_dy, 0, kWorkArrays * s->nelem * sizeof(df64), s->stream));
-    }
-
-    std::vector<double> f[6];
-    for (auto &a : f) a.assign(s->nelem, 0.0);
-    build_start_level(pb, h, f);
-
-    CUDA_TRY(s, cudaMemcpyAsync(s->d_flag, flags.data(), flags.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s->stream));
-    CUDA_TRY(s, cudaMemcpyAsync(s->d_axis, ax.data(), nax * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    CUDA_TRY(s, cudaMemcpyAsync(s->d_axis + nax, ay.data(), nay * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    CUDA_TRY(s, cudaMemsetAsync(s->work.ru_dy, 0, kWorkArrays * s->nelem * sizeof(double), s->stream));
-    CUDA_TRY(s, cudaMemsetAsync(w.res, 0, 4 * sizeof(unsigned long long), s->stream));
-    for (int l = 0; l < 3; l++)
-        for (int k = 0; k < 6; k++)
-            CUDA_TRY(s, cudaMemcpyAsync(level_field(s->lv[l], k), f[k].data(), s->nelem * sizeof(double),
-                                        cudaMemcpyHostToDevice, s->stream));
-    for (int l = 0; l < 3; l++) {
-        launch_derive(s->geo, pb.k, s->lv[l], s->stream);
-        launch_ghosts(s->geo, s->sides, s->lv[l], false, s->stream);
-        if (s->mixed) launch_shadow(s->geo, s->lv[l], s->mx.lv[l], s->nelem, s->stream);
-        if (s->df) launch_split(s->lv[l], s->dfm.lv[l], s->nelem, s->stream);
-    }
-    if (cudaMalloc(&s->d_inst, sizeof(Inst)) != cudaSuccess ||
-        cudaMalloc(&s->d_tiles, sizeof(int)) != cudaSuccess) {
-        sim_destroy(s);
-        return SIM_ENOMEM;
-    }
-    CUDA_TRY(s, cudaMemsetAsync(s->d_tiles, 0, sizeof(int), s->stream));
-    st = default_plan(s);
+    Template t;
+    make_template(s->pb, t);
+    st = build_handle(s, t, -G, s->pb.nx + G + 1);
     if (st != SIM_OK) {
         sim_destroy(s);
         return st;
     }
-    CUDA_TRY(s, cudaGetLastError());
-    CUDA_TRY(s, cudaStreamSynchronize(s->stream));
     *out = s;
     return SIM_OK;
 }
@@ -1475,4 +1574,293 @@ extern "C" void sim_batch_destroy(sim_batch_t b)
     cudaFree(b->d_tiles);
     for (sim_t s : b->inst) sim_destroy(s);
     delete b;
+}
+
+// =================================================================== x-strips
+
+struct sim_strips_s {
+    Problem pb;
+    std::vector<sim_t> strip;                 // one windowed handle per strip
+    std::vector<int> own0, own1;              // owned cell columns [own0, own1)
+    cudaStream_t stream = nullptr;
+    HaloCopy *d_copies = nullptr;             // 3 x n_copies: the halo copies of each level
+    int n_copies = 0, max_words = 0;
+    double *d_stage = nullptr;                // logical-shape staging array of the whole problem
+    unsigned long long *h_res = nullptr;      // pinned: 4 residual words per strip
+    struct Graph { cudaGraphExec_t exec = nullptr; int result = 0; };
+    Graph graphs[3][4];
+    cudaStream_t cap_stream = nullptr;
+    int cur = 0;
+    char err[256] = {0};
+};
+
+namespace {
+
+// Columns of a halo: the strips exchange this many columns of every field on
+// each side once per loop-2 iteration.  A position's face quantities read the
+// previous iterate two columns away, the assembly reads face quantities one
+// column away, the pressure reads the assembly's d and u^ one column east and
+// the velocity correction the pressure one column west: the owned columns'
+// new values need the previous iterate four columns beyond them.
+constexpr int kStripHalo = 4;
+constexpr int kMaxStrips = 64;
+
+// Strip k of n over nx cells: owned columns [a, b) (nearly equal widths of at
+// least two halos), computed positions [c0, c1) = [a - halo rounded down to a
+// multiple of 32 (the warps keep the whole problem's 32-wide row segments),
+// b + halo) clipped to [0, nx + 1), stored columns [c0 - 2, c1 + 2).
+bool strip_layout(int nx, int n, int k, int out[6])
+{
+    if (n < 1 || n > kMaxStrips || k < 0 || k >= n || nx < 2 * kStripHalo * n) return false;
+    const int a = (int)((long long)k * nx / n), b = (int)((long long)(k + 1) * nx / n);
+    int c0 = a - kStripHalo;
+    if (c0 < 0) c0 = 0;
+    c0 = c0 / 32 * 32;
+    const int c1 = k == n - 1 ? nx + 1 : b + kStripHalo;
+    out[0] = a;
+    out[1] = b;
+    out[2] = c0 - G;
+    out[3] = c1 + G;
+    out[4] = c0;
+    out[5] = c1;
+    return true;
+}
+
+sim_status sfail(sim_strips_t h, sim_status st, const char *fmt, ...)
+{
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof h->err, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define SCUDA_TRY(h, call)                                                          \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            return sfail(h, SIM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+// The device arrays (kernel views) of level l that carry the state of the
+// strip's arithmetic, with their element sizes.
+int level_arrays(const sim_s *s, int l, void *ptr[12], int bytes[12])
+{
+    int n = 0;
+    auto add6 = [&](void *u, void *v, void *p, void *T, void *rho, void *gam, int b) {
+        void *a[6] = {u, v, p, T, rho, gam};
+        for (void *x : a) {
+            ptr[n] = x;
+            bytes[n++] = b;
+        }
+    };
+    if (s->df) {
+        const LevelT<df64> &L = s->dfm.lv[l];
+        add6(L.u, L.v, L.p, L.T, L.rho, L.gam, (int)sizeof(df64));
+    } else {
+        const Level &L = s->lv[l];
+        add6(L.u, L.v, L.p, L.T, L.rho, L.gam, (int)sizeof(double));
+        if (s->mixed) {
+            const LevelT<float> &M = s->mx.lv[l];
+            add6(M.u, M.v, M.p, M.T, M.rho, M.gam, (int)sizeof(float));
+        }
+    }
+    return n;
+}
+
+// One time step of every strip from level `prev`: the explicit terms (explicit
+// scheme), then per loop-2 iteration each strip's four kernels and ghost
+// refresh, then one launch that copies every halo of the new level from the
+// strip owning it.  Returns the result level.
+int enqueue_strips_step(sim_strips_t h, int prev, bool implicit, bool tvd, cudaStream_t st)
+{
+    long long counts[SIM_K_COUNT] = {0};
+    if (!implicit)
+        for (sim_t s : h->strip) enqueue_explicit(s, prev, tvd, st, counts);
+    int old = prev;
+    for (int it = 1; it <= h->pb.iters; it++) {
+        int nw = old;
+        for (sim_t s : h->strip) nw = enqueue_iteration(s, prev, old, implicit, tvd, !implicit && it == 1, st, counts);
+        launch_halo_copies(h->d_copies + (size_t)nw * h->n_copies, h->n_copies, h->max_words, st);
+        old = nw;
+    }
+    return old;
+}
+
+}  // namespace
+
+extern "C" sim_status sim_strips_layout(int nx, int n_strips, int strip, int out[6])
+{
+    if (!out || !strip_layout(nx, n_strips, strip, out)) return SIM_EINVAL;
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_strips_create(const sim_grid *grid, const sim_gas *gas, const sim_bc *bc, int n_strips,
+                                        void *stream, sim_strips_t *out)
+{
+    if (!out) return SIM_EINVAL;
+    *out = nullptr;
+    sim_strips_t h = new (std::nothrow) sim_strips_s;
+    if (!h) return SIM_ENOMEM;
+    h->stream = (cudaStream_t)stream;
+    sim_status st = read_problem(grid, gas, bc, h->pb, nullptr);
+    int lay[6];
+    if (st == SIM_OK && (bc->tol != 0.0 || !strip_layout(h->pb.nx, n_strips, 0, lay))) st = SIM_EINVAL;
+    if (st != SIM_OK) {
+        sim_strips_destroy(h);
+        return st;
+    }
+    Template t;
+    make_template(h->pb, t);
+    for (int k = 0; k < n_strips; k++) {
+        strip_layout(h->pb.nx, n_strips, k, lay);
+        sim_t s = new (std::nothrow) sim_s;
+        if (!s) {
+            sim_strips_destroy(h);
+            return SIM_ENOMEM;
+        }
+        s->pb = h->pb;
+        s->stream = h->stream;
+        s->own0 = lay[0];
+        s->own_stop = k == n_strips - 1 ? 0 : lay[1];
+        st = build_handle(s, t, lay[2], lay[3]);
+        if (st != SIM_OK) {
+            sim_destroy(s);
+            sim_strips_destroy(h);
+            return st;
+        }
+        h->strip.push_back(s);
+        h->own0.push_back(lay[0]);
+        h->own1.push_back(lay[1]);
+    }
+    // the halo copies of each level: at the boundary X between strips k and
+    // k + 1, the columns [X - halo, X) of strip k go to strip k + 1 and the
+    // columns [X, X + halo) of strip k + 1 go to strip k, every row of the
+    // extended grid, every field of the arithmetic's levels
+    const int rows = h->pb.ny + 2 * G + 1;
+    std::vector<HaloCopy> copies;
+    for (int l = 0; l < 3; l++) {
+        for (int k = 0; k + 1 < n_strips; k++) {
+            sim_t a = h->strip[k], b = h->strip[k + 1];
+            const int X = h->own1[k];
+            void *pa[12], *pb[12];
+            int ba[12], bb[12];
+            const int n = level_arrays(a, l, pa, ba);
+            level_arrays(b, l, pb, bb);
+            for (int f = 0; f < n; f++) {
+                const int e = ba[f];
+                auto at = [&](void *base, int i) { return (unsigned *)((char *)base + (size_t)(i + G) * e); };
+                const int wpitch_a = a->pitch * e / 4, wpitch_b = b->pitch * e / 4, words = kStripHalo * e / 4;
+                copies.push_back(HaloCopy{at(pa[f], X - kStripHalo), at(pb[f], X - kStripHalo), wpitch_a, wpitch_b,
+                                          words, rows});
+                copies.push_back(HaloCopy{at(pb[f], X), at(pa[f], X), wpitch_b, wpitch_a, words, rows});
+                h->max_words = std::max(h->max_words, words * rows);
+            }
+        }
+        if (l == 0) h->n_copies = (int)copies.size();
+    }
+    const size_t stage = (size_t)(h->pb.nx + 1) * (h->pb.ny + 1);
+    if ((!copies.empty() && cudaMalloc(&h->d_copies, copies.size() * sizeof(HaloCopy)) != cudaSuccess) ||
+        cudaMalloc(&h->d_stage, stage * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&h->h_res, 4 * sizeof(unsigned long long) * n_strips) != cudaSuccess) {
+        sim_strips_destroy(h);
+        return SIM_ENOMEM;
+    }
+    if (!copies.empty() && cudaMemcpy(h->d_copies, copies.data(), copies.size() * sizeof(HaloCopy),
+                                      cudaMemcpyHostToDevice) != cudaSuccess) {
+        sim_strips_destroy(h);
+        return SIM_ECUDA;
+    }
+    *out = h;
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_strips_step(sim_strips_t h, int n_steps, int scheme)
+{
+    if (!h) return SIM_EINVAL;
+    if (n_steps < 0 || (scheme & ~3)) return sfail(h, SIM_EINVAL, "bad n_steps %d or scheme %d", n_steps, scheme);
+    const bool implicit = scheme & SIM_IMPLICIT, tvd = scheme & SIM_TVD;
+    for (int step = 0; step < n_steps; step++) {
+        sim_strips_s::Graph &g = h->graphs[h->cur][scheme];
+        if (!g.exec) {
+            if (!h->cap_stream)
+                SCUDA_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            SCUDA_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+            g.result = enqueue_strips_step(h, h->cur, implicit, tvd, h->cap_stream);
+            SCUDA_TRY(h, cudaStreamEndCapture(h->cap_stream, &graph));
+            cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                g.exec = nullptr;
+                return sfail(h, SIM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+            }
+        }
+        SCUDA_TRY(h, cudaGraphLaunch(g.exec, h->stream));
+        h->cur = g.result;
+        for (sim_t s : h->strip) {
+            s->cur = h->cur;
+            s->last_iters = h->pb.iters;
+        }
+    }
+    SCUDA_TRY(h, cudaGetLastError());
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_strips_fields(sim_strips_t h, int field, double *host_dst, size_t n)
+{
+    if (!h) return SIM_EINVAL;
+    if (field < 0 || field > 5 || !host_dst) return sfail(h, SIM_EINVAL, "bad field %d or null destination", field);
+    const size_t need = field_count(h->pb, field);
+    if (n != need) return sfail(h, SIM_EINVAL, "field %d has %zu elements, got %zu", field, need, n);
+    const int ns = (int)h->strip.size();
+    for (int k = 0; k < ns; k++) {
+        sim_t s = h->strip[k];
+        if (s->df)
+            launch_join(alloc_of(s->dfm.lv[h->cur], s->shift), alloc_of(s->lv[h->cur], s->shift), s->nelem, h->stream);
+        launch_gather_cols(s->geo, field, s->lv[h->cur], h->d_stage, h->own0[k], k == ns - 1 ? h->pb.nx + 1 : h->own1[k],
+                           h->stream);
+    }
+    SCUDA_TRY(h, cudaGetLastError());
+    SCUDA_TRY(h, cudaMemcpyAsync(host_dst, h->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    SCUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_strips_residuals(sim_strips_t h, double out[4])
+{
+    if (!h || !out) return SIM_EINVAL;
+    const int ns = (int)h->strip.size();
+    for (int k = 0; k < ns; k++)
+        SCUDA_TRY(h, cudaMemcpyAsync(h->h_res + 4 * k, h->strip[k]->work.res, 4 * sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, h->stream));
+    SCUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    // the maxima over the strips: the same ordered keys the kernels reduce
+    unsigned long long m[4] = {0, 0, 0, 0};
+    for (int k = 0; k < ns; k++)
+        for (int q = 0; q < 4; q++) m[q] = std::max(m[q], h->h_res[4 * k + q]);
+    if (!read_residuals(m, out)) return sfail(h, SIM_EDIVERGED, "non-finite residual");
+    return SIM_OK;
+}
+
+extern "C" const char *sim_strips_last_error(sim_strips_t h)
+{
+    return h ? h->err : "null handle";
+}
+
+extern "C" void sim_strips_destroy(sim_strips_t h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (auto &row : h->graphs)
+        for (auto &g : row)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    cudaFree(h->d_copies);
+    cudaFree(h->d_stage);
+    if (h->h_res) cudaFreeHost(h->h_res);
+    for (sim_t s : h->strip) sim_destroy(s);
+    delete h;
 }

@@ -166,6 +166,11 @@ struct Inst {
     int east_outflow;
     int tiles_x;          // tiles along x for the batch's tile shape
     int tile0;            // index of this problem's first tile in the batch
+    // One strip of a problem decomposed along x (all 0 for a whole problem):
+    // the tiles start at column x0; positions of columns >= x_stop (when
+    // x_stop > 0) are skipped; the residual maxima take only the columns in
+    // [own0, own_stop) (own_stop 0: no upper limit).
+    int x0, x_stop, own0, own_stop;
 };
 
 // Work distribution of the equation kernels: tiles of tx x ty threads
@@ -183,10 +188,13 @@ struct BatchPlan {
 // Boundary description used by the ghost refresh.
 struct Sides {
     int kind[4];          // W, E, S, N
+    int col0, col1;       // columns [col0, col1) the S/N refresh covers; col1 = 0: [-2, nx + 2]
 };
 
 enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
-enum { BC_WALL = 0, BC_SYMMETRY = 1, BC_INFLOW = 2, BC_OUTFLOW = 3 };
+// BC_INTERFACE: the side of an x-strip that faces another strip (its halo is
+// copied from the neighbour, no ghost rule applies)
+enum { BC_WALL = 0, BC_SYMMETRY = 1, BC_INFLOW = 2, BC_OUTFLOW = 3, BC_INTERFACE = 4 };
 
 // Launch wrappers (sweep_kernels.cu).  All are asynchronous on `stream`.
 //
@@ -212,10 +220,23 @@ void launch_ghosts_f32(const Mixed &m, const Sides &s, int level, bool after_vel
 void launch_ghosts_df(const DoubleFloat &d, const Sides &s, int level, bool after_velocity, void *stream);
 int ghost_kernels(const Sides &s, bool after_velocity);
 
-// State maintenance.
+// State maintenance.  The _cols variants cover the columns [i0, i1) only.
 void launch_derive(const Geo &g, const Coef &c, const Level &lv, void *stream);
+void launch_derive_cols(const Geo &g, const Coef &c, const Level &lv, int i0, int i1, void *stream);
 void launch_scatter(const Geo &g, int field, const double *src, const Level &lv, void *stream);
 void launch_gather(const Geo &g, int field, const Level &lv, double *dst, void *stream);
+void launch_gather_cols(const Geo &g, int field, const Level &lv, double *dst, int i0, int i1, void *stream);
+
+// Halo exchange of an x-decomposed problem: n copies of a block of `rows`
+// rows x `words` 4-byte words between two arrays (row pitches in words),
+// one launch for every copy of a loop-2 iteration.
+struct HaloCopy {
+    const unsigned *src;
+    unsigned *dst;
+    int spitch, dpitch;   // words per row
+    int words, rows;      // block width in words, rows
+};
+void launch_halo_copies(const HaloCopy *copies, int n, int max_words, void *stream);
 // The four state fields u, v, p, T as separate arrays in their logical shapes.
 struct StatePtrs {
     double *f[4];

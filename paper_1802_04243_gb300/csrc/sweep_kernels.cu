@@ -891,7 +891,7 @@ __device__ __forceinline__ void assemble_body(const GeoT<R> &g, const CoefT<R> &
 template <typename R>
 __device__ __forceinline__ void pressure_body(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev,
                                               const LevelT<R> &old, const LevelT<R> &nw, const WorkT<R> &w,
-                                              unsigned long long *res, int i, int j)
+                                              unsigned long long *res, int i, int j, bool own)
 {
     const int P = g.pitch;
     unsigned long long rp = 0, rT = 0;
@@ -918,6 +918,7 @@ __device__ __forceinline__ void pressure_body(const GeoT<R> &g, const CoefT<R> &
             rT = res_key(Tn - old.T[c]);
         }
     }
+    if (!own) rp = rT = 0;
     block_max2(rp, rT, &res[2], &res[3]);
 }
 
@@ -950,7 +951,7 @@ __device__ __forceinline__ void outflow_copy(int j, int ny, int c, LevelT<R> L)
 template <typename R>
 __device__ __forceinline__ void velocity_body(const GeoT<R> &g, const LevelT<R> &old, const LevelT<R> &nw,
                                               const WorkT<R> &w, unsigned long long *res, int east_outflow, int i,
-                                              int j)
+                                              int j, bool own)
 {
     const int P = g.pitch;
     unsigned long long ru = 0, rv = 0;
@@ -970,6 +971,7 @@ __device__ __forceinline__ void velocity_body(const GeoT<R> &g, const LevelT<R> 
         if (east_outflow && i == g.nx - 1)
             outflow_copy(j, g.ny, c, nw);
     }
+    if (!own) ru = rv = 0;
     block_max2(ru, rv, &res[0], &res[1]);
 }
 
@@ -1030,8 +1032,8 @@ __global__ void k_ghost_we(GeoT<R> g, Sides s, LevelT<R> L)
 template <typename R>
 __global__ void k_ghost_sn(GeoT<R> g, Sides s, LevelT<R> L)
 {
-    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) - G;
-    if (i > g.nx + G) return;
+    const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x) + (s.col1 > 0 ? s.col0 : -G);
+    if (i > g.nx + G || (s.col1 > 0 && i >= s.col1)) return;
     const Ix ix{g.pitch};
     const int ny = g.ny;
     R *sc[4] = {L.p, L.T, L.rho, L.gam};
@@ -1078,7 +1080,7 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
                                                     const CoefT<float> &k32, const Level &prev, const Level &old,
                                                     const Level &nw, const LevelT<float> &old32,
                                                     const LevelT<float> &nw32, const WorkT<float> &w,
-                                                    unsigned long long *res, int i, int j)
+                                                    unsigned long long *res, int i, int j, bool own)
 {
     const int P = g.pitch;
     unsigned long long rp = 0, rT = 0;
@@ -1120,6 +1122,7 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
             rT = ordered_bits(widen(T32 - old32.T[c]));
         }
     }
+    if (!own) rp = rT = 0;
     block_max2(rp, rT, &res[2], &res[3]);
 }
 
@@ -1129,7 +1132,8 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
 // FP64 bit patterns.
 __device__ __forceinline__ void velocity_mixed_body(const Geo &g, const Level &nw, const LevelT<float> &old32,
                                                     const LevelT<float> &nw32, const WorkT<float> &w,
-                                                    unsigned long long *res, int east_outflow, int i, int j)
+                                                    unsigned long long *res, int east_outflow, int i, int j,
+                                                    bool own)
 {
     const int P = g.pitch;
     unsigned long long ru = 0, rv = 0;
@@ -1153,6 +1157,7 @@ __device__ __forceinline__ void velocity_mixed_body(const Geo &g, const Level &n
             outflow_copy(j, g.ny, c, nw32);
         }
     }
+    if (!own) ru = rv = 0;
     block_max2(ru, rv, &res[0], &res[1]);
 }
 
@@ -1203,10 +1208,18 @@ __device__ __forceinline__ void for_tiles(const BatchPlan &bp, F &&f)
         }
         const Inst &I = sI;
         const int lt = t - I.tile0;
-        const int i = (lt % I.tiles_x) * bp.tx + threadIdx.x;
+        int i = I.x0 + (lt % I.tiles_x) * bp.tx + threadIdx.x;
         const int j = (lt / I.tiles_x) * bp.ty + threadIdx.y;
+        if (I.x_stop > 0 && i >= I.x_stop) i = I.g.nx + 1;   // beyond every body's range
         f(I, i, j);
     }
+}
+
+// Whether column i counts for the residual maxima of the descriptor's problem
+// (every column of a whole problem; the owned columns of an x-strip).
+__device__ __forceinline__ bool owns(const Inst &I, int i)
+{
+    return i >= I.own0 && (I.own_stop == 0 || i < I.own_stop);
 }
 
 // The residual words of every problem of the list to 0.  The face kernel
@@ -1280,11 +1293,12 @@ __global__ void __launch_bounds__(256) k_pressure(const __grid_constant__ BatchP
     for_tiles(bp, [&](const Inst &I, int i, int j) {
         if constexpr (PREC == PREC_MIXED)
             pressure_mixed_body(I.g, I.k, I.g32, I.k32, I.lv[prev], I.lv[old], I.lv[nw], I.lv32[old], I.lv32[nw],
-                                I.w32, I.w.res, i, j);
+                                I.w32, I.w.res, i, j, owns(I, i));
         else if constexpr (PREC == PREC_DF64)
-            pressure_body<df64>(I.gdf, I.kdf, I.lvdf[prev], I.lvdf[old], I.lvdf[nw], I.wdf, I.w.res, i, j);
+            pressure_body<df64>(I.gdf, I.kdf, I.lvdf[prev], I.lvdf[old], I.lvdf[nw], I.wdf, I.w.res, i, j,
+                                owns(I, i));
         else
-            pressure_body<double>(I.g, I.k, I.lv[prev], I.lv[old], I.lv[nw], I.w, I.w.res, i, j);
+            pressure_body<double>(I.g, I.k, I.lv[prev], I.lv[old], I.lv[nw], I.w, I.w.res, i, j, owns(I, i));
     });
 }
 
@@ -1293,11 +1307,12 @@ __global__ void __launch_bounds__(256) k_velocity(const __grid_constant__ BatchP
 {
     for_tiles(bp, [&](const Inst &I, int i, int j) {
         if constexpr (PREC == PREC_MIXED)
-            velocity_mixed_body(I.g, I.lv[nw], I.lv32[old], I.lv32[nw], I.w32, I.w.res, I.east_outflow, i, j);
+            velocity_mixed_body(I.g, I.lv[nw], I.lv32[old], I.lv32[nw], I.w32, I.w.res, I.east_outflow, i, j,
+                                owns(I, i));
         else if constexpr (PREC == PREC_DF64)
-            velocity_body<df64>(I.gdf, I.lvdf[old], I.lvdf[nw], I.wdf, I.w.res, I.east_outflow, i, j);
+            velocity_body<df64>(I.gdf, I.lvdf[old], I.lvdf[nw], I.wdf, I.w.res, I.east_outflow, i, j, owns(I, i));
         else
-            velocity_body<double>(I.g, I.lv[old], I.lv[nw], I.w, I.w.res, I.east_outflow, i, j);
+            velocity_body<double>(I.g, I.lv[old], I.lv[nw], I.w, I.w.res, I.east_outflow, i, j, owns(I, i));
     });
 }
 
@@ -1331,10 +1346,10 @@ __global__ void k_join(LevelT<df64> D, Level L, size_t n)
 // rho = p/T and Gamma = T^omega of every fluid cell, evaluated exactly as
 // the pressure kernel evaluates them (so a state written out and set again
 // continues bit for bit).
-__global__ void k_derive(Geo g, Coef k, Level L)
+__global__ void k_derive(Geo g, Coef k, Level L, int i0, int i1)
 {
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
+    const int i = i0 + blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i >= i1 || i >= g.nx || j >= g.ny) return;
     const int c = Ix{g.pitch}(i, j);
     if (!(g.flag[c] & F_FLUID)) return;
     const double T = L.T[c];
@@ -1368,14 +1383,25 @@ __global__ void k_scatter(Geo g, int field, const double *src, Level L)
         field_of(L, field)[c] = src[(size_t)j * w + i];
 }
 
-// Read one field into a logical-shape array (boundary values included).
-__global__ void k_gather(Geo g, int field, Level L, double *dst)
+// Read one field into a logical-shape array (boundary values included), the
+// columns [i0, i1) of it.
+__global__ void k_gather(Geo g, int field, Level L, double *dst, int i0, int i1)
 {
-    const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    const int i = i0 + blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
     const int nx = g.nx, ny = g.ny;
     const int w = field == 0 ? nx + 1 : nx, h = field == 1 ? ny + 1 : ny;
-    if (i >= w || j >= h) return;
+    if (i >= w || i >= i1 || j >= h) return;
     dst[(size_t)j * w + i] = field_of(L, field)[Ix{g.pitch}(i, j)];
+}
+
+// One 4-byte word of each halo block per thread; blockIdx.y picks the block.
+__global__ void k_halo_copies(const HaloCopy *copies, int n)
+{
+    const HaloCopy c = copies[blockIdx.y];
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= c.words * c.rows) return;
+    const int r = q / c.words, x = q - r * c.words;
+    c.dst[(size_t)r * c.dpitch + x] = c.src[(size_t)r * c.spitch + x];
 }
 
 // All four fields of a staged state (u, v, p, T back to back in their
@@ -1565,7 +1591,14 @@ void launch_validate_state(const double *stage, size_t nu, size_t nv, size_t nc,
 
 void launch_derive(const Geo &g, const Coef &c, const Level &lv, void *stream)
 {
-    k_derive<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, c, lv);
+    k_derive<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, c, lv, 0, g.nx);
+}
+
+void launch_derive_cols(const Geo &g, const Coef &c, const Level &lv, int i0, int i1, void *stream)
+{
+    if (i1 <= i0) return;
+    const dim3 grid((unsigned)((i1 - i0 + BX - 1) / BX), (unsigned)((g.ny + BY - 1) / BY));
+    k_derive<<<grid, dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, c, lv, i0, i1);
 }
 
 void launch_scatter_state(const Geo &g, const Coef &c, const double *stage, const Level &lv, void *stream)
@@ -1593,7 +1626,20 @@ void launch_scatter(const Geo &g, int field, const double *src, const Level &lv,
 
 void launch_gather(const Geo &g, int field, const Level &lv, double *dst, void *stream)
 {
-    k_gather<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, field, lv, dst);
+    k_gather<<<grid_of(g), dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, field, lv, dst, 0, g.nx + 1);
+}
+
+void launch_gather_cols(const Geo &g, int field, const Level &lv, double *dst, int i0, int i1, void *stream)
+{
+    if (i1 <= i0) return;
+    const dim3 grid((unsigned)((i1 - i0 + BX - 1) / BX), (unsigned)((g.ny + 1 + BY - 1) / BY));
+    k_gather<<<grid, dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, field, lv, dst, i0, i1);
+}
+
+void launch_halo_copies(const HaloCopy *copies, int n, int max_words, void *stream)
+{
+    if (n <= 0 || max_words <= 0) return;
+    k_halo_copies<<<dim3((unsigned)((max_words + 255) / 256), (unsigned)n), 256, 0, (cudaStream_t)stream>>>(copies, n);
 }
 
 void launch_faces(const BatchPlan &bp, int prec, int level, bool tvd, bool limiters, void *stream)
