@@ -274,6 +274,22 @@ sim_status sim_batch_tune(sim_batch_t batch, int scheme, int out[3]);
  * Errors: SIM_EINVAL (null batch, another shape, ctas < 0), SIM_ECUDA. */
 sim_status sim_batch_set_tiles(sim_batch_t batch, int tile_x, int tile_y, int ctas);
 
+/* Run each time step of the batch as one persistent kernel (on != 0) instead
+ * of one launch per phase: a cooperative launch of as many CTAs as stay
+ * resident walks the tile list through every phase of the step (explicit
+ * terms, face densities, assembly, pressure, velocity correction), with a
+ * grid-wide barrier between the phases.  The phases run the same code as the
+ * per-phase kernels.  Each barrier wait is bounded (2 s): a wait that runs out
+ * ends the step, and the next sim_batch_fields or sim_batch_residuals returns
+ * SIM_ETIMEOUT.  Not available when a problem has a symmetry side (its ghost
+ * refresh is a separate kernel).  sim_batch_tune also times this mode.
+ * Synchronous.  Errors: SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA. */
+sim_status sim_batch_set_persistent(sim_batch_t batch, int on);
+
+/* The batch's work distribution: out[0..3] = tile x, tile y, CTAs of the
+ * per-phase kernels, 1 if each step is one persistent kernel. */
+sim_status sim_batch_plan_info(sim_batch_t batch, int out[4]);
+
 /* Text of the last error on this batch (never NULL). */
 const char *sim_batch_last_error(sim_batch_t batch);
 

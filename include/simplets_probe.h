@@ -41,6 +41,17 @@ int simplets_recip_check(const double *host_x, int n, double *host_out);
  * the sweep's root in host_out[2q] and the IEEE root in host_out[2q+1]. */
 int simplets_sqrt_check(const double *host_x, int n, double *host_out);
 
+/* Check of the grid barrier of the persistent batch step (sim_batch_set_persistent):
+ * a cooperative launch of all resident CTAs of a 256-thread kernel crosses
+ * `rounds` barriers, each expecting gridDim.x + extra_blocks CTAs.  With
+ * extra_blocks = 0 every barrier completes; with extra_blocks > 0 no barrier
+ * can complete, every wait runs out after its 2 s limit, the kernel ends and
+ * *err_out is set.  *err_out receives the barrier's error word (0: every
+ * barrier completed), *ctas_out the CTAs launched.  Returns 0 on success, 1 on
+ * a bad argument, 3 on a CUDA error.  Synchronous; allocates and frees its own
+ * device buffer. */
+int simplets_barrier_check(int extra_blocks, int rounds, int *err_out, int *ctas_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,8 @@ _SIGNATURES = {
     "simplets_alu_peak": ([ctypes.c_int, ctypes.c_double, ctypes.c_void_p, _DP], ctypes.c_int),
     "simplets_recip_check": ([_DP, ctypes.c_int, _DP], ctypes.c_int),
     "simplets_sqrt_check": ([_DP, ctypes.c_int, _DP], ctypes.c_int),
+    "simplets_barrier_check": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                               ctypes.c_int),
     "sim_destroy": ([ctypes.c_void_p], None),
     "sim_batch_create": ([ctypes.c_int, ctypes.POINTER(sim_grid), ctypes.POINTER(sim_gas), ctypes.POINTER(sim_bc),
                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
@@ -94,6 +96,8 @@ _SIGNATURES = {
     "sim_batch_tune": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sim_batch_set_tiles": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "sim_batch_last_error": ([ctypes.c_void_p], ctypes.c_char_p),
+    "sim_batch_set_persistent": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "sim_batch_plan_info": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sim_batch_destroy": ([ctypes.c_void_p], None),
     "sim_strips_layout": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "sim_strips_create": ([ctypes.POINTER(sim_grid), ctypes.POINTER(sim_gas), ctypes.POINTER(sim_bc), ctypes.c_int,
@@ -198,6 +202,17 @@ def sqrt_check(x) -> "tuple[np.ndarray, np.ndarray]":
     if rc:
         raise SimError(SIM_ECUDA, f"simplets_sqrt_check failed ({rc})")
     return out[0::2].copy(), out[1::2].copy()
+
+
+def barrier_check(extra_blocks: int = 0, rounds: int = 10) -> "tuple[int, int]":
+    """(error word, CTAs) of simplets_barrier_check: the persistent step's grid
+    barrier crossed `rounds` times by every resident CTA, each barrier expecting
+    `extra_blocks` CTAs more than were launched (include/simplets_probe.h)."""
+    err, ctas = ctypes.c_int(), ctypes.c_int()
+    rc = load().simplets_barrier_check(int(extra_blocks), int(rounds), ctypes.byref(err), ctypes.byref(ctas))
+    if rc:
+        raise SimError(SIM_ECUDA, f"simplets_barrier_check failed ({rc})")
+    return err.value, ctas.value
 
 
 class _CudaArray:
@@ -376,6 +391,16 @@ class Batch:
     def set_tiles(self, tile_x: int, tile_y: int, ctas: int = 0):
         """Tiles of tile_x x tile_y threads walked by `ctas` CTAs (0: one per tile), sim_batch_set_tiles."""
         self._check(self.lib.sim_batch_set_tiles(self.handle, int(tile_x), int(tile_y), int(ctas)))
+
+    def set_persistent(self, on: bool = True):
+        """Each step as one persistent cooperative kernel (sim_batch_set_persistent)."""
+        self._check(self.lib.sim_batch_set_persistent(self.handle, 1 if on else 0))
+
+    def plan_info(self):
+        """(tile x, tile y, CTAs, persistent) of the batch's work distribution."""
+        out = (ctypes.c_int * 4)()
+        self._check(self.lib.sim_batch_plan_info(self.handle, out))
+        return tuple(out)
 
     def field(self, instance: int, name: str) -> np.ndarray:
         c = self.cases[instance]

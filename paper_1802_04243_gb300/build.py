@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsimplets.so")
-SOURCES = ["sweep_kernels.cu", "simplets_host.cu", "alu_probe.cu", "noalloc.cu"]
+SOURCES = ["sweep_kernels.cu", "persistent.cu", "simplets_host.cu", "alu_probe.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

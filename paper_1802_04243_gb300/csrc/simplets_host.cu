@@ -534,21 +534,23 @@ sim_status single_plan(sim_t s, int tx, int ty, int ctas, int asm_ctas)
 
 // The measured best distribution per arithmetic on the 4864x1216 channel
 // (bench.py --sweep plans): FP64 and mixed tiles of 32 x 4 threads, one CTA
-// per tile, and for the mixed path's FP32 assembly four resident CTAs per SM
-// walking the tiles (the descriptor each CTA stages is then read once per
-// CTA instead of once per tile); double-float 32 x 8, one CTA per tile.
+// per tile, and for the mixed path's FP32 assembly as many CTAs as stay
+// resident (1024 threads per SM at its 64 registers) walking the tiles: the
+// descriptor each CTA stages is then read once per CTA instead of once per
+// tile; double-float 32 x 8, one CTA per tile.
 sim_status default_plan(sim_t s)
 {
     const int prec = prec_of(s);
     if (prec == PREC_DF64) return single_plan(s, 32, 8, 0, 0);
+    const int tx = 32, ty = 4;
     int asm_ctas = 0;
     if (prec == PREC_MIXED) {
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-            asm_ctas = 4 * sms;
+            asm_ctas = 1024 / (tx * ty) * sms;
     }
-    return single_plan(s, 32, 4, 0, asm_ctas);
+    return single_plan(s, tx, ty, 0, asm_ctas);
 }
 
 size_t field_count(const Problem &pb, int f)
@@ -1249,6 +1251,10 @@ struct sim_batch_s {
     size_t tiles_cap = 0;
     BatchPlan plan{};
     bool ghosts = false;                      // some problem has a symmetry side
+    // persistent step: one cooperative kernel per time step (persistent.cu)
+    bool persistent = false;
+    GridBarrier *d_bar = nullptr;
+    unsigned *h_err = nullptr;                // pinned copy of the barrier's error word
     struct Graph { cudaGraphExec_t exec = nullptr; int result = 0; };
     Graph graphs[3][4];
     cudaStream_t cap_stream = nullptr;
@@ -1257,6 +1263,8 @@ struct sim_batch_s {
 };
 
 namespace {
+
+sim_status batch_barrier_status(sim_batch_t b);
 
 sim_status bfail(sim_batch_t b, sim_status st, const char *fmt, ...)
 {
@@ -1314,10 +1322,48 @@ sim_status plan_tiles(sim_batch_t b, int tx, int ty, int grid)
     return SIM_OK;
 }
 
-// One time step of every problem from level `prev`; returns the result level.
+// The phases of one time step from level `prev` for the persistent kernel,
+// in the order the per-phase launches take; returns the result level.
+int step_phases(sim_batch_t b, int prev, bool implicit, bool tvd, PhaseList &ph)
+{
+    ph.n = 0;
+    auto add = [&](int kind, int a, int bb, int c) {
+        ph.kind[ph.n] = (unsigned char)kind;
+        ph.a[ph.n] = (unsigned char)a;
+        ph.b[ph.n] = (unsigned char)bb;
+        ph.c[ph.n] = (unsigned char)c;
+        ph.n++;
+    };
+    if (!implicit) {
+        add(PH_FACES, prev, tvd ? 1 : 0, 0);
+        add(PH_EXPLICIT, prev, 0, 0);
+    }
+    int old = prev;
+    for (int it = 1; it <= b->iters; it++) {
+        int nw = (old + 1) % 3;
+        if (nw == prev) nw = (nw + 1) % 3;
+        if (implicit || it > 1) add(PH_FACES, old, (tvd && implicit) ? 1 : 0, 0);
+        add(PH_ASSEMBLE, prev, old, nw);
+        add(PH_PRESSURE, prev, old, nw);
+        add(PH_VELOCITY, old, nw, 0);
+        old = nw;
+    }
+    return old;
+}
+
+// One time step of every problem from level `prev`; returns the result level
+// (-1 if the persistent kernel could not be launched).
 int enqueue_batch_step(sim_batch_t b, int prev, bool implicit, bool tvd, cudaStream_t st)
 {
     const BatchPlan &bp = b->plan;
+    if (b->persistent) {
+        PhaseList ph{};
+        const int result = step_phases(b, prev, implicit, tvd, ph);
+        const int ctas = std::min(persistent_ctas(b->prec, implicit, tvd, bp.tx * bp.ty), bp.n_tiles);
+        if (ctas < 1 || launch_step_persistent(bp, ph, b->d_bar, b->prec, implicit, tvd, ctas, st) != cudaSuccess)
+            return -1;
+        return result;
+    }
     if (!implicit) {
         launch_faces(bp, b->prec, prev, tvd, true, st);
         launch_explicit(bp, b->prec, prev, tvd, st);
@@ -1398,6 +1444,15 @@ extern "C" sim_status sim_batch_step(sim_batch_t b, int n_steps, int scheme)
     if (!b) return SIM_EINVAL;
     if (n_steps < 0 || (scheme & ~3)) return bfail(b, SIM_EINVAL, "bad n_steps %d or scheme %d", n_steps, scheme);
     const bool implicit = scheme & SIM_IMPLICIT, tvd = scheme & SIM_TVD;
+    if (b->persistent) {                      // one cooperative launch per step
+        for (int step = 0; step < n_steps; step++) {
+            const int result = enqueue_batch_step(b, b->cur, implicit, tvd, b->stream);
+            if (result < 0) return bfail(b, SIM_ECUDA, "persistent step launch failed: %s",
+                                         cudaGetErrorString(cudaGetLastError()));
+            set_levels(b, result);
+        }
+        return SIM_OK;
+    }
     for (int step = 0; step < n_steps; step++) {
         sim_batch_s::Graph &g = b->graphs[b->cur][scheme];
         if (!g.exec) {
@@ -1421,16 +1476,62 @@ extern "C" sim_status sim_batch_step(sim_batch_t b, int n_steps, int scheme)
     return SIM_OK;
 }
 
+namespace {
+
+// SIM_ETIMEOUT if a grid barrier of the persistent step ran out of time since
+// the barrier was last cleared (the results of that step are not valid).
+sim_status batch_barrier_status(sim_batch_t b)
+{
+    if (!b->d_bar) return SIM_OK;
+    BCUDA_TRY(b, cudaMemcpyAsync(b->h_err, &b->d_bar->err, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
+    BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
+    if (*b->h_err) return bfail(b, SIM_ETIMEOUT, "a grid barrier of the persistent step timed out");
+    return SIM_OK;
+}
+
+}  // namespace
+
 extern "C" sim_status sim_batch_fields(sim_batch_t b, int instance, int field, double *host_dst, size_t n)
 {
     if (!b || instance < 0 || instance >= (int)b->inst.size()) return SIM_EINVAL;
+    sim_status st = batch_barrier_status(b);
+    if (st != SIM_OK) return st;
     return sim_fields(b->inst[instance], field, host_dst, n);
 }
 
 extern "C" sim_status sim_batch_residuals(sim_batch_t b, int instance, double out[4])
 {
     if (!b || instance < 0 || instance >= (int)b->inst.size()) return SIM_EINVAL;
+    sim_status st = batch_barrier_status(b);
+    if (st != SIM_OK) return st;
     return sim_residuals(b->inst[instance], out, nullptr);
+}
+
+extern "C" sim_status sim_batch_set_persistent(sim_batch_t b, int on)
+{
+    if (!b) return SIM_EINVAL;
+    if (on && b->ghosts)
+        return bfail(b, SIM_EINVAL, "the persistent step does not run the ghost kernels of symmetry sides");
+    BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
+    if (on && !b->d_bar) {
+        if (cudaMalloc(&b->d_bar, sizeof(GridBarrier)) != cudaSuccess ||
+            cudaMallocHost(&b->h_err, sizeof(unsigned)) != cudaSuccess)
+            return bfail(b, SIM_ENOMEM, "no memory for the grid barrier");
+        BCUDA_TRY(b, cudaMemset(b->d_bar, 0, sizeof(GridBarrier)));
+    }
+    b->persistent = on != 0;
+    drop_graphs(b);
+    return SIM_OK;
+}
+
+extern "C" sim_status sim_batch_plan_info(sim_batch_t b, int out[4])
+{
+    if (!b || !out) return SIM_EINVAL;
+    out[0] = b->plan.tx;
+    out[1] = b->plan.ty;
+    out[2] = b->plan.grid;
+    out[3] = b->persistent ? 1 : 0;
+    return SIM_OK;
 }
 
 namespace {
@@ -1492,32 +1593,45 @@ sim_status tune_batch(sim_batch_t b, int scheme, int out[3])
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int shapes[6][2] = {{32, 8}, {64, 4}, {128, 2}, {16, 16}, {32, 4}, {64, 2}};
-    const int grids[3] = {2 * sms, 4 * sms, 0};       // 0: one CTA per tile
+    // CTA counts: 2 or 4 per SM walking the tiles, one CTA per tile (0), and
+    // the persistent step kernel (-1; not with symmetry sides)
+    const int grids[4] = {2 * sms, 4 * sms, 0, -1};
+    const int n_grids = b->ghosts ? 3 : 4;
+    if (!b->ghosts && sim_batch_set_persistent(b, 0) != SIM_OK) {
+        cudaFree(save);
+        return SIM_ECUDA;
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
     int bx = 32, by = 8, bg = 0;
+    bool bpers = false;
     sim_status st = SIM_OK;
     for (auto &sh : shapes) {
-        for (int gsz : grids) {
-            if ((st = plan_tiles(b, sh[0], sh[1], gsz)) != SIM_OK) break;
+        for (int gi = 0; gi < n_grids; gi++) {
+            const int gsz = grids[gi];
+            if ((st = plan_tiles(b, sh[0], sh[1], gsz < 0 ? 0 : gsz)) != SIM_OK) break;
+            b->persistent = gsz < 0;
+            if (b->persistent && (st = sim_batch_set_persistent(b, 1)) != SIM_OK) break;
             int lv = start;
-            lv = enqueue_batch_step(b, lv, implicit, tvd, b->stream);     // warm-up
+            bool ok = (lv = enqueue_batch_step(b, lv, implicit, tvd, b->stream)) >= 0;     // warm-up
             cudaEventRecord(e0, b->stream);
-            for (int r = 0; r < 3; r++) lv = enqueue_batch_step(b, lv, implicit, tvd, b->stream);
+            for (int r = 0; r < 3 && ok; r++) ok = (lv = enqueue_batch_step(b, lv, implicit, tvd, b->stream)) >= 0;
             cudaEventRecord(e1, b->stream);
             if (cudaEventSynchronize(e1) != cudaSuccess) {
                 st = bfail(b, SIM_ECUDA, "tuning run failed");
                 break;
             }
+            if (b->persistent && ok) ok = batch_barrier_status(b) == SIM_OK;
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
+            if (ok && ms < best) {
                 best = ms;
                 bx = sh[0];
                 by = sh[1];
-                bg = gsz;
+                bg = gsz < 0 ? 0 : gsz;
+                bpers = gsz < 0;
             }
             // next candidate starts from the saved state again
             if (copy_state(false) != cudaSuccess) {
@@ -1531,9 +1645,11 @@ sim_status tune_batch(sim_batch_t b, int scheme, int out[3])
     cudaEventDestroy(e1);
     cudaStreamSynchronize(b->stream);
     cudaFree(save);
+    b->persistent = false;
     if (st != SIM_OK) return st;
     set_levels(b, start);
     if ((st = plan_tiles(b, bx, by, bg)) != SIM_OK) return st;
+    if (bpers && (st = sim_batch_set_persistent(b, 1)) != SIM_OK) return st;
     out[0] = bx;
     out[1] = by;
     out[2] = b->plan.grid;
@@ -1572,6 +1688,8 @@ extern "C" void sim_batch_destroy(sim_batch_t b)
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     cudaFree(b->d_inst);
     cudaFree(b->d_tiles);
+    cudaFree(b->d_bar);
+    if (b->h_err) cudaFreeHost(b->h_err);
     for (sim_t s : b->inst) sim_destroy(s);
     delete b;
 }

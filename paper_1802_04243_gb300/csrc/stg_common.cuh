@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cstddef>
+#include <cuda_runtime.h>
 #include <cstdint>
 
 #include "df64.cuh"
@@ -212,6 +213,24 @@ void launch_assemble(const BatchPlan &bp, int prec, int prev, int old, int nw, b
                      void *stream);
 void launch_pressure(const BatchPlan &bp, int prec, int prev, int old, int nw, void *stream);
 void launch_velocity(const BatchPlan &bp, int prec, int old, int nw, void *stream);
+
+// Persistent step of a batch (persistent.cu): one cooperative kernel runs a
+// list of phases over the tile list, a grid barrier between each two.
+enum { PH_FACES = 0, PH_EXPLICIT = 1, PH_ASSEMBLE = 2, PH_PRESSURE = 3, PH_VELOCITY = 4 };
+constexpr int kMaxPhases = 64;
+struct PhaseList {
+    int n;
+    unsigned char kind[kMaxPhases];
+    unsigned char a[kMaxPhases], b[kMaxPhases], c[kMaxPhases];   // the phase's level arguments
+};
+struct GridBarrier {
+    unsigned count, gen, err, pad;   // err != 0: a barrier wait ran out of time
+};
+// CTAs of the persistent kernel that stay resident together (0 on error).
+int persistent_ctas(int prec, bool implicit, bool tvd, int threads);
+// Clears the barrier and launches one step (cooperative launch, `ctas` CTAs).
+cudaError_t launch_step_persistent(const BatchPlan &bp, const PhaseList &ph, GridBarrier *bar, int prec, bool implicit,
+                                   bool tvd, int ctas, void *stream);
 
 // Ghost copies of outflow and symmetry sides.  after_velocity: the velocity
 // kernel has already copied the outflow side, only symmetry sides remain.

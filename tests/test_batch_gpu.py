@@ -110,7 +110,7 @@ def test_batch_rejects_mixed_loop2_lengths():
 
 @pytest.mark.parametrize("precision", [W.FP64, W.MIXED, W.DF64], ids=["fp64", "mixed", "df64"])
 @pytest.mark.parametrize("plan", [(32, 8, 0, 0), (64, 4, 0, 0), (32, 4, 456, 0), (16, 16, 0, 0), (128, 2, 304, 0),
-                                  (32, 1, 0, 0), (32, 4, 0, 608), (32, 8, 0, 7)])
+                                  (32, 1, 0, 0), (32, 4, 0, 1216), (32, 8, 0, 7)])
 def test_single_problem_plans_give_the_same_bits(plan, precision):
     # sim_set_plan on one handle, on a ragged grid (37 x 29 positions) with
     # obstacles: every tile shape and CTA count, every precision, the implicit
@@ -139,3 +139,64 @@ def test_set_plan_rejects_other_shapes():
             with pytest.raises(sim.SimError) as e:
                 s.set_plan(*bad)
             assert e.value.status == sim.SIM_EINVAL
+
+
+# ------------------------------------------------------- persistent step
+
+@pytest.mark.parametrize("precision", [W.FP64, W.MIXED, W.DF64], ids=["fp64", "mixed", "df64"])
+@pytest.mark.parametrize("implicit,tvd", [(True, False), (False, True), (True, True)])
+def test_persistent_step_equals_the_per_phase_launches(precision, implicit, tvd):
+    # one cooperative kernel per step, phases separated by grid barriers, runs
+    # the same phase bodies over the same tile list as the per-phase kernels
+    cases = small_batch(precision=precision, implicit=implicit, tvd=tvd)
+    with sim.Batch(cases) as a, sim.Batch(cases) as b:
+        b.set_persistent(True)
+        assert b.plan_info()[3] == 1
+        a.step(6)
+        b.step(6)
+        for q in range(len(cases)):
+            fa, fb = a.fields(q), b.fields(q)
+            ra, (rb, st) = a.residuals(q)[0], b.residuals(q)
+            assert st == sim.SIM_OK
+            for k in "uvpT":
+                assert np.array_equal(fa[k], fb[k]), (q, k)
+            np.testing.assert_array_equal(ra, rb)
+
+
+def test_persistent_step_with_other_tiles_and_the_tuner():
+    cases = small_batch(n=4, precision=W.FP64)
+    with sim.Batch(cases) as a, sim.Batch(cases) as b:
+        b.set_tiles(32, 4, 0)
+        b.set_persistent(True)
+        a.step(3)
+        b.step(3)
+        b.tune()                                   # may keep either mode; the state is restored
+        a.step(3)
+        b.step(3)
+        for q in range(len(cases)):
+            fa, fb = a.fields(q), b.fields(q)
+            for k in "uvpT":
+                assert np.array_equal(fa[k], fb[k]), (q, k)
+
+
+def test_persistent_step_refused_with_symmetry_sides():
+    cases = [W.uniform_flow(nx=48, ny=20).replace(rects=[[10, 6, 14, 12]], perturb=1e-3)]
+    with sim.Batch(cases) as b:
+        with pytest.raises(sim.SimError) as e:
+            b.set_persistent(True)
+        assert e.value.status == sim.SIM_EINVAL
+
+
+def test_grid_barrier_completes_and_a_wait_that_cannot_complete_ends_with_an_error():
+    # every resident CTA crosses 50 barriers; then a barrier that expects one
+    # CTA more than were launched: each wait gives up after its limit, the
+    # error word is set, the kernel ends, and the device stays usable
+    err, ctas = sim.barrier_check(0, 50)
+    assert err == 0 and ctas >= 152
+    err, _ = sim.barrier_check(1, 3)
+    assert err == 1
+    cases = small_batch(n=2, precision=W.FP64)
+    with sim.Batch(cases) as b:
+        b.set_persistent(True)
+        b.step(2)
+        assert b.residuals(0)[1] == sim.SIM_OK
