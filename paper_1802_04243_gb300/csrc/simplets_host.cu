@@ -1316,8 +1316,17 @@ sim_status plan_tiles(sim_batch_t b, int tx, int ty, int grid)
     BCUDA_TRY(b, cudaMemcpyAsync(b->d_inst, host.data(), host.size() * sizeof(Inst), cudaMemcpyHostToDevice, b->stream));
     BCUDA_TRY(b, cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
+    // one CTA per tile: the mixed path's FP32 assembly walks the tiles with its
+    // resident CTAs instead (as for a single problem, default_plan)
+    int grid_asm = 0;
+    if (grid == 0 && b->prec == PREC_MIXED) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            grid_asm = std::min((int)tiles.size(), 1024 / (tx * ty) * sms);
+    }
     b->plan = BatchPlan{b->d_inst, b->d_tiles, (int)host.size(), (int)tiles.size(), tx, ty,
-                        grid > 0 ? std::min(grid, (int)tiles.size()) : (int)tiles.size(), host[0], 0};
+                        grid > 0 ? std::min(grid, (int)tiles.size()) : (int)tiles.size(), host[0], grid_asm};
     drop_graphs(b);
     return SIM_OK;
 }
