@@ -44,6 +44,7 @@ inline bool gas_coefficients(const sim_gas *gas, Coef &k, double &u_in, double &
     k.CT1f = gm * ct1;
     k.CT2f = gm * ct2;
     k.CT3f = -gm * ct3;
+    k.B23 = (2.0 / 3.0) * k.B;
     k.gx = gas->gx;
     k.gy = gas->gy;
     return true;

@@ -300,8 +300,9 @@ std::vector<uint16_t> make_flags(const HostGrid &h)
     return f;
 }
 
-// Axis factor table: kAxisTables arrays of n + 2G + 1 entries over [-2, n+2].
-std::vector<double> make_axis(const std::vector<double> &dl)
+// Axis factor table: kAxisTables arrays of n + 2G + 1 entries over [-2, n+2];
+// hrdt = 1 / (2 dt).
+std::vector<double> make_axis(const std::vector<double> &dl, double hrdt)
 {
     const int n = (int)dl.size(), m = n + 2 * G + 1;
     std::vector<double> d(m), out(kAxisTables * (size_t)m, 0.0);
@@ -322,6 +323,7 @@ std::vector<double> make_axis(const std::vector<double> &dl)
         out[9 * m + q] = 2.0 * out[2 * m + q];
         out[10 * m + q] = 2.0 * out[3 * m + q];
         out[11 * m + q] = 0.5 * di;
+        out[12 * m + q] = di * hrdt;
     }
     for (int q = 0; q < m; q++) {
         const int qn = q + 1 < m ? q + 1 : q;
@@ -677,8 +679,8 @@ void make_template(const Problem &pb, Template &t)
     t.h.P = t.gP;
     classify(pb, t.h);
     t.flags = make_flags(t.h);
-    t.ax = make_axis(pb.dx);
-    t.ay = make_axis(pb.dy);
+    t.ax = make_axis(pb.dx, pb.k.hrdt);
+    t.ay = make_axis(pb.dy, pb.k.hrdt);
     const size_t n = (size_t)t.gP * (pb.ny + 2 * G + 1);
     for (auto &a : t.f) a.assign(n, 0.0);
     build_start_level(pb, t.h, t.f);
@@ -765,7 +767,7 @@ sim_status build_handle(sim_t s, const Template &t, int L, int R)
         const Coef &k = pb.k;
         s->mx.k = CoefT<float>{(float)k.A, (float)k.B, (float)k.CT1f, (float)k.CT2f, (float)k.CT3f,
                                (float)k.omega, (float)k.dt, (float)k.gx, (float)k.gy, (float)k.hrdt,
-                               (float)k.zeta, (float)k.tau};
+                               (float)k.zeta, (float)k.tau, (float)k.B23};
         std::vector<float> a32(nax + nay);
         for (size_t q = 0; q < nax; q++) a32[q] = (float)t.ax[q];
         for (size_t q = 0; q < nay; q++) a32[nax + q] = (float)t.ay[q];
@@ -790,7 +792,7 @@ sim_status build_handle(sim_t s, const Template &t, int L, int R)
         s->dfm.k = CoefT<df64>{dfl::split_host(k.A), dfl::split_host(k.B), dfl::split_host(k.CT1f), dfl::split_host(k.CT2f),
                                dfl::split_host(k.CT3f), dfl::split_host(k.omega), dfl::split_host(k.dt), dfl::split_host(k.gx),
                                dfl::split_host(k.gy), dfl::split_host(k.hrdt), dfl::split_host(k.zeta),
-                               dfl::split_host(k.tau)};
+                               dfl::split_host(k.tau), dfl::split_host(k.B23)};
         std::vector<df64> adf(nax + nay);
         for (size_t q = 0; q < nax; q++) adf[q] = dfl::split_host(t.ax[q]);
         for (size_t q = 0; q < nay; q++) adf[nax + q] = dfl::split_host(t.ay[q]);

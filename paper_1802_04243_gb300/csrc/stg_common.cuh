@@ -58,17 +58,18 @@ struct AxisT {
     const R *wlo2;   // 2 wlo (exact): the TVD face corrections take twice the weight
     const R *whi2;   // 2 whi
     const R *hd;     // 0.5 d_i (exact)
+    const R *ddt;    // d_i / (2 dt): the transient factor of the momentum control volumes
 };
 
 // Number of per-index arrays of an axis table, stored one after another.
-constexpr int kAxisTables = 12;
+constexpr int kAxisTables = 13;
 
 // The arrays of an axis table of m entries per array starting at t.
 template <typename R>
 inline AxisT<R> axis_view(const R *t, int m)
 {
-    return AxisT<R>{t,         t + m,     t + 2 * m, t + 3 * m, t + 4 * m,  t + 5 * m,
-                    t + 6 * m, t + 7 * m, t + 8 * m, t + 9 * m, t + 10 * m, t + 11 * m};
+    return AxisT<R>{t,         t + m,     t + 2 * m, t + 3 * m, t + 4 * m,  t + 5 * m,  t + 6 * m,
+                    t + 7 * m, t + 8 * m, t + 9 * m, t + 10 * m, t + 11 * m, t + 12 * m};
 }
 
 template <typename R>
@@ -84,6 +85,7 @@ struct CoefT {
     R A, B, CT1f, CT2f, CT3f, omega, dt, gx, gy;
     R hrdt;               // 0.5 / dt
     R zeta, tau;          // slip / jump coefficients (Eqs. pl38, pl39), divided by rho_local at use; 0 = off
+    R B23;                // 2/3 B, the factor of the normal-stress cross terms of Eqs. pl14, pl16
 };
 
 // One state level: u, v at faces; p, T, rho, Gamma at cell centres.
