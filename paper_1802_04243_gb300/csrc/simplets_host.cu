@@ -1318,8 +1318,10 @@ sim_status plan_tiles(sim_batch_t b, int tx, int ty, int grid)
     BCUDA_TRY(b, cudaMemcpyAsync(b->d_inst, host.data(), host.size() * sizeof(Inst), cudaMemcpyHostToDevice, b->stream));
     BCUDA_TRY(b, cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BCUDA_TRY(b, cudaStreamSynchronize(b->stream));
-    // one CTA per tile: the mixed path's FP32 assembly walks the tiles with its
-    // resident CTAs instead (as for a single problem, default_plan)
+    // one CTA per tile (a count of CTAs at least the tiles' is the same): the
+    // mixed path's FP32 assembly walks the tiles with its resident CTAs
+    // instead (as for a single problem, default_plan)
+    if (grid >= (int)tiles.size()) grid = 0;
     int grid_asm = 0;
     if (grid == 0 && b->prec == PREC_MIXED) {
         int dev = 0, sms = 0;
