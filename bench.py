@@ -710,6 +710,22 @@ def run_ours(args, rank, world, local_rank):
 
     others = {p: variant(p) for p in ("fp64", "mixed", "df64") if p != args.precision}
 
+    # the same workload decomposed into x-strips on this device (halo of 4
+    # columns recomputed per loop-2 iteration, one halo-copy kernel per
+    # iteration): the cost of the decomposition against the whole problem
+    strips = {}
+    for n_strips in (2, 4):
+        with sim.Strips(case, n_strips, stream=stream.cuda_stream) as sp:
+            for _ in range(args.warmup):
+                sp.step(1)
+            torch.cuda.synchronize()
+            sp_ms = timed_steps(sp, min(args.steps, 50), stream, flush, starts, ends)
+            sp_ms = reduce_max(sp_ms, dist, "cuda")
+            nst = min(args.steps, 50)
+            strips[str(n_strips)] = {"value": round(throughput(case.cells, nst, world, sp_ms * 1e-3), 3),
+                                     "ms_per_step": round(sp_ms / nst, 5),
+                                     "vs_whole": round((total_ms / args.steps) / (sp_ms / nst), 4)}
+
     # end to end through the C ABI with host buffers: every step uploads its
     # input state from pinned host memory (sim_set_state), advances one step
     # and reads the new state and the residuals back (sim_get_state)
@@ -778,7 +794,9 @@ def run_ours(args, rank, world, local_rank):
                         "exceeds the graph-timed step; shares between kernels and each kernel's mean are what "
                         "it gives (the roofline's k_assemble time comes from it)",
                 "launches_per_iteration": {k: round(x, 3) for k, x in steps_per_iter_kernels.items()}},
-            **others, "batched": batched, "cpu_baseline": cpu,
+            **others, "strips": {"note": "the same workload as x-strips on this device, value and ratio to the "
+                                         "whole-problem step time", **strips},
+            "batched": batched, "cpu_baseline": cpu,
             "cpu_baseline_rows": cpu_rows, "clocks": csum,
             "residuals_last_step": [float(x) for x in res], "impl": "ours"}
     print(json.dumps(line), flush=True)

@@ -127,7 +127,7 @@ __device__ __forceinline__ bool nwall(const Setup &s, int i, int j)
 // inverse, the two interpolation weights of face i, the inverse centre
 // distance across face i and the three derivative weights of cell i; ghost
 // sizes mirror the boundary cells.
-__global__ void k_na_axis(int n, const double *dl, double len, double hrdt, double *out)
+__global__ void k_na_axis(int n, const double *dl, double len, double hrdt, double ct1f, double *out)
 {
     const int m = n + 2 * G + 1;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -150,6 +150,8 @@ __global__ void k_na_axis(int n, const double *dl, double len, double hrdt, doub
     out[10 * m + q] = 2.0 * whi;
     out[11 * m + q] = 0.5 * di;
     out[12 * m + q] = di * hrdt;
+    out[13 * m + q] = (2.0 * ct1f) * di;
+    out[14 * m + q] = di * (2.0 * hrdt);
     // derivative weights: the interpolation weights of face q+1 (of face q
     // itself for the last entry, which no cell uses)
     const double dn = q + 1 < m ? size_at(q + 1) : di, dc = q + 1 < m ? di : dm;
@@ -436,8 +438,8 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     for (int t = 0; t < 4; t++) sides.kind[t] = bc->side_kind[t];
 
     // -------------------------------------------------------- set-up kernels
-    k_na_axis<<<(mx + 127) / 128, 128, 0, s>>>(nx, cdx, grid->lx, k.hrdt, axx);
-    k_na_axis<<<(my + 127) / 128, 128, 0, s>>>(ny, cdy, grid->ly, k.hrdt, axy);
+    k_na_axis<<<(mx + 127) / 128, 128, 0, s>>>(nx, cdx, grid->lx, k.hrdt, k.CT1f, axx);
+    k_na_axis<<<(my + 127) / 128, 128, 0, s>>>(ny, cdy, grid->ly, k.hrdt, k.CT1f, axy);
     const dim3 bl(32, 8), gr((mx + 31) / 32, (my + 7) / 8);
     k_na_kind<<<gr, bl, 0, s>>>(su);
     k_na_flags<<<gr, bl, 0, s>>>(su, flag);

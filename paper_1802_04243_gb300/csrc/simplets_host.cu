@@ -301,8 +301,8 @@ std::vector<uint16_t> make_flags(const HostGrid &h)
 }
 
 // Axis factor table: kAxisTables arrays of n + 2G + 1 entries over [-2, n+2];
-// hrdt = 1 / (2 dt).
-std::vector<double> make_axis(const std::vector<double> &dl, double hrdt)
+// hrdt = 1 / (2 dt), ct1f = C^T1_f.
+std::vector<double> make_axis(const std::vector<double> &dl, double hrdt, double ct1f)
 {
     const int n = (int)dl.size(), m = n + 2 * G + 1;
     std::vector<double> d(m), out(kAxisTables * (size_t)m, 0.0);
@@ -324,6 +324,8 @@ std::vector<double> make_axis(const std::vector<double> &dl, double hrdt)
         out[10 * m + q] = 2.0 * out[3 * m + q];
         out[11 * m + q] = 0.5 * di;
         out[12 * m + q] = di * hrdt;
+        out[13 * m + q] = (2.0 * ct1f) * di;
+        out[14 * m + q] = di * (2.0 * hrdt);      // 2 hrdt = 1 / dt exactly
     }
     for (int q = 0; q < m; q++) {
         const int qn = q + 1 < m ? q + 1 : q;
@@ -679,8 +681,8 @@ void make_template(const Problem &pb, Template &t)
     t.h.P = t.gP;
     classify(pb, t.h);
     t.flags = make_flags(t.h);
-    t.ax = make_axis(pb.dx, pb.k.hrdt);
-    t.ay = make_axis(pb.dy, pb.k.hrdt);
+    t.ax = make_axis(pb.dx, pb.k.hrdt, pb.k.CT1f);
+    t.ay = make_axis(pb.dy, pb.k.hrdt, pb.k.CT1f);
     const size_t n = (size_t)t.gP * (pb.ny + 2 * G + 1);
     for (auto &a : t.f) a.assign(n, 0.0);
     build_start_level(pb, t.h, t.f);

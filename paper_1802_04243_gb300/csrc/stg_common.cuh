@@ -59,17 +59,19 @@ struct AxisT {
     const R *whi2;   // 2 whi
     const R *hd;     // 0.5 d_i (exact)
     const R *ddt;    // d_i / (2 dt): the transient factor of the momentum control volumes
+    const R *ct2d;   // 2 C^T1_f d_i: twice the conductance factor of a face of length d_i (Eq. pl32)
+    const R *dt1;    // d_i / dt: with the other axis's d, a cell's volume per unit time
 };
 
 // Number of per-index arrays of an axis table, stored one after another.
-constexpr int kAxisTables = 13;
+constexpr int kAxisTables = 15;
 
 // The arrays of an axis table of m entries per array starting at t.
 template <typename R>
 inline AxisT<R> axis_view(const R *t, int m)
 {
     return AxisT<R>{t,         t + m,     t + 2 * m, t + 3 * m, t + 4 * m,  t + 5 * m,  t + 6 * m,
-                    t + 7 * m, t + 8 * m, t + 9 * m, t + 10 * m, t + 11 * m, t + 12 * m};
+                    t + 7 * m, t + 8 * m, t + 9 * m, t + 10 * m, t + 11 * m, t + 12 * m, t + 13 * m, t + 14 * m};
 }
 
 template <typename R>

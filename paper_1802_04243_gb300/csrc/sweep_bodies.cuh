@@ -172,6 +172,19 @@ __device__ __forceinline__ R gamma_corner(const GeoT<R> &g, const R *gam, int c,
     return at(g.y.wlo, j) * lo + at(g.y.whi, j) * hi;
 }
 
+// Volume of cell (i,j) per unit time, dx_i dy_j / dt: the factor of the
+// transient terms of Eqs. pl30 and pl24 once those equations are divided by
+// dt (as the momentum equations Eqs. pl14-pl16 are written).  FP64 takes
+// dy_j / dt from the axis table.
+template <typename R>
+__device__ __forceinline__ R vol_per_dt(const GeoT<R> &g, const CoefT<R> &k, int j, R dxi, R dyj)
+{
+    if constexpr (std::is_same<R, double>::value)
+        return dxi * at(g.y.dt1, j);
+    else
+        return dxi * (dyj * (R(2) * k.hrdt));
+}
+
 // ------------------------------------------------------ residual reduction
 
 // Ordered key of |x|: the bits of an FP64 value without its sign, ordered like
@@ -403,7 +416,17 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
     const int c = Ix{P}(i, j);
     if (i > g.nx || j > g.ny) return;
     const R dxi = at(g.x.d, i), dyj = at(g.y.d, j);
-    const R ct1f2 = R(2) * k.CT1f;
+    // 2 C^T1_f times the face area: tabulated in FP64 (a load instead of two
+    // FP64 multiplies), formed here by the FP32 and double-float sweeps
+    R ct2_dy, ct2_dx;
+    if constexpr (std::is_same<R, double>::value) {
+        ct2_dy = at(g.y.ct2d, j);
+        ct2_dx = at(g.x.ct2d, i);
+    } else {
+        const R ct1f2 = R(2) * k.CT1f;
+        ct2_dy = ct1f2 * dyj;
+        ct2_dx = ct1f2 * dxi;
+    }
     if (j < g.ny) {
         const R vel = u[c], rl = rho[c - 1], rr = rho[c];
         R val = upwind(rl, rr, vel);
@@ -413,7 +436,7 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         const R rdy = val * dyj;
         w.ru_dy[c] = rdy;
         w.Fx[c] = rdy * vel;
-        w.DTx[c] = conductance(gam[c - 1], gam[c], at(g.x.d, i - 1), dxi, ct1f2 * dyj);
+        w.DTx[c] = conductance(gam[c - 1], gam[c], at(g.x.d, i - 1), dxi, ct2_dy);
     }
     if (i < g.nx) {
         const R vel = v[c], rb = rho[c - P], rt = rho[c];
@@ -424,7 +447,7 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         const R rdx = val * dxi;
         w.rv_dx[c] = rdx;
         w.Fy[c] = rdx * vel;
-        w.DTy[c] = conductance(gam[c - P], gam[c], at(g.y.d, j - 1), dyj, ct1f2 * dxi);
+        w.DTy[c] = conductance(gam[c - P], gam[c], at(g.y.d, j - 1), dyj, ct2_dx);
     }
     w.Bgc[c] = k.B * gamma_corner(g, gam, c, i, j);
     if (i < g.nx && j < g.ny) {
@@ -634,7 +657,9 @@ __device__ R temperature(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     const R uw = old.u[c], ue = old.u[c + 1], vs = old.v[c], vn = old.v[c + P];
     const R Fw = w.Fx[c], Fe = w.Fx[c + 1], Fs = w.Fy[c], Fn = w.Fy[c + P];
     const R Dw = w.DTx[c], De = w.DTx[c + 1], Ds = w.DTy[c], Dn = w.DTy[c + P];
-    const R vol = dxi * dyj;
+    // the equation divided by dt: the transient coefficients take the cell's
+    // volume per unit time, the fluxes and conductances stay as they are
+    const R vdt = vol_per_dt(g, k, j, dxi, dyj);
     R a1, a2, a3, a4, a0, texp;
     if (IMPL) {
         R pw = 0.0, pe = 0.0, ps = 0.0, pn = 0.0;
@@ -655,17 +680,17 @@ __device__ R temperature(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
             a3 = pos(Fs) + Ds;
             a4 = neg_part(Fn) + Dn;
         }
-        a0 = k.dt * (a1 + a2 + a3 + a4 + Fe - Fw + Fn - Fs) + old.rho[c] * vol;
+        a0 = (a1 + a2 + a3 + a4 + Fe - Fw + Fn - Fs) + old.rho[c] * vdt;
         texp = R(0);
     } else {
         a1 = Dw; a2 = De; a3 = Ds; a4 = Dn;
-        a0 = k.dt * (a1 + a2 + a3 + a4) + old.rho[c] * vol;
+        a0 = (a1 + a2 + a3 + a4) + old.rho[c] * vdt;
         texp = w.Texp[c];
     }
     const R sc = energy_source<R, WALLS>(g, k, old, w, c, i, j);
     R src = a1 * Tw + a2 * Te + a3 * Ts + a4 * Tn + sc;
     if constexpr (!IMPL) src += texp;
-    const R rhs = k.dt * src + prev.rho[c] * prev.T[c] * vol;
+    const R rhs = src + prev.rho[c] * prev.T[c] * vdt;
     return rhs * recip(a0);
 }
 
@@ -921,11 +946,14 @@ __device__ __forceinline__ void pressure_body(const GeoT<R> &g, const CoefT<R> &
             const R bpw = ru_w * w.uhat[c], bpe = ru_e * w.uhat[c + 1];
             const R bps = rv_s * w.vhat[c], bpn = rv_n * w.vhat[c + P];
             const R Tn = nw.T[c], inv_T = recip(Tn);
-            const R vol = dxi * dyj;
-            const R ap0 = vol * inv_T + (apw + ape + aps + apn) * k.dt;
-            const R bp = prev.rho[c] * vol - (bpe - bpw + bpn - bps) * k.dt;
-            const R pn = ((apw * old.p[c - 1] + ape * old.p[c + 1] + aps * old.p[c - P] + apn * old.p[c + P]) * k.dt
-                          + bp) * recip(ap0);
+            // Eqs. pl23, pl24 divided by dt (the transient terms take the
+            // cell's volume per unit time): the neighbour sum accumulates
+            // onto the source
+            const R vdt = vol_per_dt(g, k, j, dxi, dyj);
+            const R ap0 = vdt * inv_T + (apw + ape + aps + apn);
+            const R bp = prev.rho[c] * vdt - (bpe - bpw + bpn - bps);
+            const R pn = ((((bp + apw * old.p[c - 1]) + ape * old.p[c + 1]) + aps * old.p[c - P]) + apn * old.p[c + P])
+                         * recip(ap0);
             nw.p[c] = pn;
             nw.rho[c] = pn * inv_T;
             nw.gam[c] = gamma_of(Tn, k.omega);
@@ -973,15 +1001,33 @@ __device__ __forceinline__ void velocity_body(const GeoT<R> &g, const LevelT<R> 
     if (i <= g.nx && j <= g.ny) {
         const int c = Ix{P}(i, j);
         const uint16_t f = g.flag[c];
-        if (j < g.ny && (f & F_UACT)) {
-            const R un = w.uhat[c] - w.du[c] * (nw.p[c] - nw.p[c - 1]);
-            nw.u[c] = un;
-            ru = res_key(un - old.u[c]);
-        }
-        if (i < g.nx && (f & F_VACT)) {
-            const R vn = w.vhat[c] - w.dv[c] * (nw.p[c] - nw.p[c - P]);
-            nw.v[c] = vn;
-            rv = res_key(vn - old.v[c]);
+        if constexpr (std::is_same<R, double>::value) {
+            // FP64: every operand loaded before the flag decides what is
+            // stored, so the loads do not wait for it (-5 % on this kernel;
+            // the double-float sweep, slower with it, keeps the loads behind)
+            const R uh = w.uhat[c], du = w.du[c], vh = w.vhat[c], dv = w.dv[c], uo = old.u[c], vo = old.v[c];
+            const R pc = nw.p[c], pw = nw.p[c - 1], ps = nw.p[c - P];
+            if (j < g.ny && (f & F_UACT)) {
+                const R un = uh - du * (pc - pw);
+                nw.u[c] = un;
+                ru = res_key(un - uo);
+            }
+            if (i < g.nx && (f & F_VACT)) {
+                const R vn = vh - dv * (pc - ps);
+                nw.v[c] = vn;
+                rv = res_key(vn - vo);
+            }
+        } else {
+            if (j < g.ny && (f & F_UACT)) {
+                const R un = w.uhat[c] - w.du[c] * (nw.p[c] - nw.p[c - 1]);
+                nw.u[c] = un;
+                ru = res_key(un - old.u[c]);
+            }
+            if (i < g.nx && (f & F_VACT)) {
+                const R vn = w.vhat[c] - w.dv[c] * (nw.p[c] - nw.p[c - P]);
+                nw.v[c] = vn;
+                rv = res_key(vn - old.v[c]);
+            }
         }
         if (east_outflow && i == g.nx - 1)
             outflow_copy(j, g.ny, c, nw);
@@ -1010,7 +1056,10 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
     unsigned long long rp = 0, rT = 0;
     if (i < g.nx && j < g.ny) {
         const int c = Ix{P}(i, j);
-        if (g.flag[c] & F_FLUID) {
+        // evaluated for every cell, the flag deciding only what is stored, so
+        // the loads do not wait for it (-3 % on this kernel)
+        const bool fluid = (g.flag[c] & F_FLUID) != 0;
+        {
             const float dxi = at(g32.x.d, i), dyj = at(g32.y.d, j);
             const float ru_w = w.ru_dy[c], ru_e = w.ru_dy[c + 1], rv_s = w.rv_dx[c], rv_n = w.rv_dx[c + P];
             const float apw = ru_w * w.du[c], ape = ru_e * w.du[c + 1];
@@ -1019,15 +1068,16 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
             const float bps = rv_s * w.vhat[c], bpn = rv_n * w.vhat[c + P];
             const float T32 = nw32.T[c];
             const double Tn = widen(T32);
-            const float ap0 = dxi * dyj / T32 + (apw + ape + aps + apn) * k32.dt;
+            // divided by dt, as the FP64 pressure kernel: the cell's volume
+            // per unit time (FP64 from the axis table) in the transient terms
+            const float ap0 = dxi * at(g32.y.dt1, j) / T32 + (apw + ape + aps + apn);
             const float div = (bpe - bpw) + (bpn - bps);
-            const double vol = at(g.x.d, i) * at(g.y.d, j);
-            const double bp = fma(prev.rho[c], vol, -widen(k32.dt * div));
-            double num = widen(apw) * old.p[c - 1];
+            const double vdt = at(g.x.d, i) * at(g.y.dt1, j);
+            const double bp = fma(prev.rho[c], vdt, widen(-div));
+            double num = fma(widen(apw), old.p[c - 1], bp);
             num = fma(widen(ape), old.p[c + 1], num);
             num = fma(widen(aps), old.p[c - P], num);
             num = fma(widen(apn), old.p[c + P], num);
-            num = fma(num, k.dt, bp);
             const double a0 = widen(ap0);
             double r = widen(1.0f / ap0);
             r = fma(r, fma(-a0, r, 1.0), r);
@@ -1036,14 +1086,18 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
             rt = fma(rt, fma(-Tn, rt, 1.0), rt);
             const double rho = pn * rt;
             const float gm = (k32.omega == 0.5f) ? sqrtf(T32) : powf(T32, k32.omega);
-            nw.p[c] = pn;
-            nw.rho[c] = rho;
-            nw.gam[c] = widen(gm);
-            nw32.p[c] = narrow(pn);
-            nw32.rho[c] = narrow(rho);
-            nw32.gam[c] = gm;
-            rp = ordered_bits(pn - old.p[c]);
-            rT = ordered_bits(widen(T32 - old32.T[c]));
+            const double po = old.p[c];
+            const float To = old32.T[c];
+            if (fluid) {
+                nw.p[c] = pn;
+                nw.rho[c] = rho;
+                nw.gam[c] = widen(gm);
+                nw32.p[c] = narrow(pn);
+                nw32.rho[c] = narrow(rho);
+                nw32.gam[c] = gm;
+                rp = ordered_bits(pn - po);
+                rT = ordered_bits(widen(T32 - To));
+            }
         }
     }
     if (!own) rp = rT = 0;
@@ -1064,17 +1118,22 @@ __device__ __forceinline__ void velocity_mixed_body(const Geo &g, const Level &n
     if (i <= g.nx && j <= g.ny) {
         const int c = Ix{P}(i, j);
         const uint16_t f = g.flag[c];
+        // every operand is loaded before the flag decides what is stored, so
+        // the loads do not wait for the flag (every index is inside the
+        // padded arrays for positions up to (nx, ny)): -9 % on this kernel
+        const float uh = w.uhat[c], du = w.du[c], vh = w.vhat[c], dv = w.dv[c], uo = old32.u[c], vo = old32.v[c];
+        const double pc = nw.p[c], pw = nw.p[c - 1], ps = nw.p[c - P];
         if (j < g.ny && (f & F_UACT)) {
-            const float un32 = w.uhat[c] - w.du[c] * narrow(nw.p[c] - nw.p[c - 1]);
+            const float un32 = uh - du * narrow(pc - pw);
             nw.u[c] = widen(un32);
             nw32.u[c] = un32;
-            ru = ordered_bits(widen(un32 - old32.u[c]));
+            ru = ordered_bits(widen(un32 - uo));
         }
         if (i < g.nx && (f & F_VACT)) {
-            const float vn32 = w.vhat[c] - w.dv[c] * narrow(nw.p[c] - nw.p[c - P]);
+            const float vn32 = vh - dv * narrow(pc - ps);
             nw.v[c] = widen(vn32);
             nw32.v[c] = vn32;
-            rv = ordered_bits(widen(vn32 - old32.v[c]));
+            rv = ordered_bits(widen(vn32 - vo));
         }
         if (east_outflow && i == g.nx - 1) {
             outflow_copy(j, g.ny, c, nw);

@@ -351,6 +351,24 @@ def test_mixed_precision_1024x256_100_steps():
     assert max(e.values()) <= MIXED_BOUND, e
 
 
+def test_mixed_and_df64_at_the_paper_scale_100_steps():
+    # the bench workload (4864x1216 channel, 5.9 M cells): both added
+    # precisions against the FP64 oracle after 100 steps, mixed within its
+    # stated bound, double-float at the FP64 bar
+    case = W.c4_paper_scale()
+    o, _, _ = oracle.run(case, nsteps=100, rows=True)
+    with sim.Simulation(case.replace(precision=W.MIXED)) as s:
+        s.step(100)
+        gm = s.fields()
+    with sim.Simulation(case.replace(precision=W.DF64)) as s:
+        s.step(100)
+        gd = s.fields()
+    em, ed = rel_err(gm, o), rel_err(gd, o)
+    print("c4 mixed", em, "c4 df64", ed)
+    assert max(em.values()) <= MIXED_BOUND, em
+    assert max(ed.values()) <= TOL, ed
+
+
 def test_mixed_start_state_matches_fp64_start_state():
     case = W.c1_small()
     with sim.Simulation(case) as a, sim.Simulation(case.replace(precision=W.MIXED)) as b:
