@@ -44,13 +44,13 @@ UNIT = "Mcell-steps/s"
 # The commands are in profiles/.
 _C4HALF = "2432x608 channel (the 4864x1216 channel at half resolution, 1,478,656 cells)"
 ASSEMBLE_FP64_COUNTS = {
-    "implicit-upwind": {"dfma": 51.15, "dadd": 43.90, "dmul": 38.36, "dram_bytes": 165.1, "fp64_pipe": 0.868,
+    "implicit-upwind": {"dfma": 51.15, "dadd": 43.90, "dmul": 37.38, "dram_bytes": 165.1, "fp64_pipe": 0.869,
                         "case": _C4HALF},
-    "implicit-tvd": {"dfma": 66.88, "dadd": 44.84, "dmul": 38.36, "dram_bytes": 223.4, "fp64_pipe": 0.879,
+    "implicit-tvd": {"dfma": 66.88, "dadd": 43.90, "dmul": 37.38, "dram_bytes": 223.4, "fp64_pipe": 0.880,
                      "case": _C4HALF},
-    "explicit-upwind": {"dfma": 41.31, "dadd": 25.21, "dmul": 42.30, "dram_bytes": 156.3, "fp64_pipe": 0.871,
+    "explicit-upwind": {"dfma": 41.31, "dadd": 25.21, "dmul": 41.31, "dram_bytes": 156.3, "fp64_pipe": 0.871,
                         "case": _C4HALF},
-    "explicit-tvd": {"dfma": 41.31, "dadd": 25.21, "dmul": 42.30, "dram_bytes": 156.3, "fp64_pipe": 0.871,
+    "explicit-tvd": {"dfma": 41.31, "dadd": 25.21, "dmul": 41.31, "dram_bytes": 156.4, "fp64_pipe": 0.871,
                      "case": _C4HALF},
 }
 # Algorithmic HBM bytes of k_assemble per cell: the previous iterate's u, v,
@@ -575,10 +575,10 @@ def step_hbm(case, ms_per_step):
 # DRAM bytes per cell, from the case named; the commands are in profiles/.
 MIXED_KERNEL_NCU = {
     "case": _C4HALF + ", ncu --metrics (one kernel per capture)",
-    "faces": {"fma_pct": 18.3, "lsu_pct": 41.0, "fp64_pct": 0.0, "warps_active_pct": 64.7, "dram_bytes": 20.6},
-    "assemble": {"fma_pct": 19.8, "lsu_pct": 58.0, "fp64_pct": 0.0, "warps_active_pct": 47.3, "dram_bytes": 72.4},
-    "pressure": {"fma_pct": 14.3, "lsu_pct": 30.6, "fp64_pct": 71.4, "warps_active_pct": 68.7, "dram_bytes": 60.8},
-    "velocity": {"fma_pct": 13.4, "lsu_pct": 39.3, "fp64_pct": 17.6, "warps_active_pct": 86.5, "dram_bytes": 35.6},
+    "faces": {"fma_pct": 18.2, "lsu_pct": 41.0, "fp64_pct": 0.0, "warps_active_pct": 65.0, "dram_bytes": 20.4},
+    "assemble": {"fma_pct": 21.2, "lsu_pct": 61.3, "fp64_pct": 0.0, "warps_active_pct": 47.0, "dram_bytes": 72.7},
+    "pressure": {"fma_pct": 13.5, "lsu_pct": 30.8, "fp64_pct": 69.5, "warps_active_pct": 57.0, "dram_bytes": 61.6},
+    "velocity": {"fma_pct": 14.0, "lsu_pct": 40.1, "fp64_pct": 18.7, "warps_active_pct": 64.2, "dram_bytes": 35.7},
 }
 
 
