@@ -320,40 +320,18 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
                                        void *stream, double res_out[4])
 {
     // ---------------------------------------------------- validation (host)
+    // the checks sim_create applies, then this entry's own limits
     if (!grid || !gas || !bc || !d_u || !d_v || !d_p || !d_T) return SIM_EINVAL;
     if (n_steps < 0 || (scheme & ~3)) return SIM_EINVAL;
+    if (check_description(grid, bc, nullptr, 0) != SIM_OK) return SIM_EINVAL;
+    if (bc->n_rect > kMaxRects || bc->tol != 0.0 || bc->precision != SIM_FP64) return SIM_EINVAL;
     const int nx = grid->nx, ny = grid->ny;
-    if (nx < 4 || ny < 4 || nx >= (1 << 20) || ny >= (1 << 20)) return SIM_EINVAL;
-    if (!grid->dx && !(grid->lx > 0.0)) return SIM_EINVAL;
-    if (!grid->dy && !(grid->ly > 0.0)) return SIM_EINVAL;
-    if (grid->dx) for (int i = 0; i < nx; i++) if (!(grid->dx[i] > 0.0) || !std::isfinite(grid->dx[i])) return SIM_EINVAL;
-    if (grid->dy) for (int j = 0; j < ny; j++) if (!(grid->dy[j] > 0.0) || !std::isfinite(grid->dy[j])) return SIM_EINVAL;
-    for (int s = 0; s < 4; s++) {
-        const int kd = bc->side_kind[s];
-        if (kd < 0 || kd > 3) return SIM_EINVAL;
-        if (kd == SIM_BC_INFLOW && s != SIM_W) return SIM_EINVAL;
-        if (kd == SIM_BC_OUTFLOW && s != SIM_E) return SIM_EINVAL;
-        if (kd == SIM_BC_WALL && !(bc->side_T[s] > 0.0)) return SIM_EINVAL;
-    }
-    if (bc->n_rect < 0 || bc->n_rect > kMaxRects || (bc->n_rect > 0 && !bc->rect)) return SIM_EINVAL;
-    if (bc->n_rect > 0 && !(bc->body_T > 0.0)) return SIM_EINVAL;
-    for (int r = 0; r < bc->n_rect; r++) {
-        const int *q = bc->rect + 4 * r;
-        if (q[0] < 2 || q[1] < 2 || q[2] > nx - 2 || q[3] > ny - 2 || q[2] - q[0] < 2 || q[3] - q[1] < 2)
-            return SIM_EINVAL;
-    }
-    if (bc->iters < 1 || bc->tol != 0.0 || bc->precision != SIM_FP64) return SIM_EINVAL;
-    if (bc->inflow_T)
-        for (int j = 0; j < ny; j++) if (!(bc->inflow_T[j] > 0.0)) return SIM_EINVAL;
     // the coefficients and the time step by the rules sim_create applies
     Coef k{};
     double u_in = 0.0, gm = 0.0;
     if (!gas_coefficients(gas, k, u_in, gm)) return SIM_EINVAL;
     k.dt = time_step(grid, bc, u_in, gm);
     k.hrdt = 0.5 / k.dt;
-    if (!(bc->zeta_coef >= 0.0) || !(bc->tau_coef >= 0.0) || !std::isfinite(bc->zeta_coef) ||
-        !std::isfinite(bc->tau_coef))
-        return SIM_EINVAL;
     k.zeta = bc->zeta_coef;
     k.tau = bc->tau_coef;
 

@@ -5,11 +5,69 @@
 #pragma once
 
 #include <cmath>
+#include <cstdio>
 
 #include "simplets.h"
 #include "stg_common.cuh"
 
 namespace stg {
+
+// The checks of a problem description (include/simplets.h) that every entry
+// point applies: grid size and cell sizes, side kinds, wall, obstacle and
+// inflow temperatures, obstacle placement, loop-2 control, precision, slip
+// and jump coefficients (the gas is checked by gas_coefficients).  Returns
+// SIM_OK, or SIM_EINVAL with the reason written to msg (n bytes; msg may be
+// NULL).  Host only; nothing is allocated.
+inline sim_status check_description(const sim_grid *gr, const sim_bc *bc, char *msg, size_t n)
+{
+#define STG_BAD(...)                                       \
+    do {                                                   \
+        if (msg && n) std::snprintf(msg, n, __VA_ARGS__);  \
+        return SIM_EINVAL;                                 \
+    } while (0)
+    if (!gr || !bc) STG_BAD("null description");
+    if (gr->nx < 4 || gr->ny < 4 || gr->nx >= (1 << 20) || gr->ny >= (1 << 20))
+        STG_BAD("grid %d x %d outside [4, 2^20)", gr->nx, gr->ny);
+    // the kernels index the padded grid with 32-bit integers
+    const long long padded = ((long long)(gr->nx + 2 * G + 1) + 7) / 8 * 8 * (gr->ny + 2 * G + 1);
+    if (padded > 0x7FFFFFFFLL)
+        STG_BAD("grid %d x %d: %lld padded elements exceed 32-bit indexing", gr->nx, gr->ny, padded);
+    for (int i = 0; i < gr->nx; i++) {
+        const double d = gr->dx ? gr->dx[i] : gr->lx / gr->nx;
+        if (!(d > 0.0) || !std::isfinite(d)) STG_BAD("cell widths must be positive");
+    }
+    for (int j = 0; j < gr->ny; j++) {
+        const double d = gr->dy ? gr->dy[j] : gr->ly / gr->ny;
+        if (!(d > 0.0) || !std::isfinite(d)) STG_BAD("cell heights must be positive");
+    }
+    for (int s = 0; s < 4; s++) {
+        const int kd = bc->side_kind[s];
+        if (kd < 0 || kd > 3) STG_BAD("side %d: unknown kind %d", s, kd);
+        if (kd == SIM_BC_INFLOW && s != SIM_W) STG_BAD("inflow only on the west side");
+        if (kd == SIM_BC_OUTFLOW && s != SIM_E) STG_BAD("outflow only on the east side");
+        if (kd == SIM_BC_WALL && !(bc->side_T[s] > 0.0)) STG_BAD("wall temperature must be positive");
+    }
+    if (bc->n_rect < 0 || (bc->n_rect > 0 && !bc->rect)) STG_BAD("bad obstacle list");
+    if (bc->n_rect > 0 && !(bc->body_T > 0.0)) STG_BAD("obstacle temperature must be positive");
+    for (int r = 0; r < bc->n_rect; r++) {
+        const int *q = bc->rect + 4 * r;
+        if (q[0] < 2 || q[1] < 2 || q[2] > gr->nx - 2 || q[3] > gr->ny - 2 || q[2] - q[0] < 2 || q[3] - q[1] < 2)
+            STG_BAD("obstacle %d [%d,%d,%d,%d) must be >= 2 cells wide and >= 2 cells from the sides", r, q[0], q[1],
+                    q[2], q[3]);
+    }
+    if (bc->iters < 1) STG_BAD("iters must be >= 1");
+    if (!(bc->tol >= 0.0)) STG_BAD("tol must be >= 0");
+    if (bc->precision != SIM_FP64 && bc->precision != SIM_MIXED && bc->precision != SIM_DF64)
+        STG_BAD("unknown precision");
+    if (!(bc->zeta_coef >= 0.0) || !(bc->tau_coef >= 0.0) || !std::isfinite(bc->zeta_coef) ||
+        !std::isfinite(bc->tau_coef))
+        STG_BAD("slip and jump coefficients must be finite and >= 0");
+    if (bc->inflow_T)
+        for (int j = 0; j < gr->ny; j++)
+            if (!(bc->inflow_T[j] > 0.0)) STG_BAD("inflow temperature must be positive");
+#undef STG_BAD
+    return SIM_OK;
+}
 
 // Non-dimensional parameters (Section 4 scaling; Eq. pl37 for the hard-sphere
 // gas).  The energy constants are the c_v-form C^Tk_f = gamma C^Tk (C^T3_f

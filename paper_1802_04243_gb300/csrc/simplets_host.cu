@@ -146,50 +146,22 @@ sim_status derive_coefficients(const sim_gas *gas, Problem &pb, sim_t err)
 
 sim_status read_problem(const sim_grid *gr, const sim_gas *gas, const sim_bc *bc, Problem &pb, sim_t err)
 {
-    if (!gr || !gas || !bc)
-        return fail(err, SIM_EINVAL, "null description");
-    if (gr->nx < 4 || gr->ny < 4 || gr->nx >= (1 << 20) || gr->ny >= (1 << 20))
-        return fail(err, SIM_EINVAL, "grid %d x %d outside [4, 2^20)", gr->nx, gr->ny);
-    // the kernels index the padded grid with 32-bit integers
-    const long long padded = ((long long)(gr->nx + 2 * G + 1) + 7) / 8 * 8 * (gr->ny + 2 * G + 1);
-    if (padded > 0x7FFFFFFFLL)
-        return fail(err, SIM_EINVAL, "grid %d x %d: %lld padded elements exceed 32-bit indexing", gr->nx, gr->ny,
-                    padded);
+    if (!gas) return fail(err, SIM_EINVAL, "null description");
+    char msg[200];
+    if (check_description(gr, bc, msg, sizeof msg) != SIM_OK) return fail(err, SIM_EINVAL, "%s", msg);
     pb.nx = gr->nx;
     pb.ny = gr->ny;
     pb.dx.resize(pb.nx);
     pb.dy.resize(pb.ny);
     for (int i = 0; i < pb.nx; i++) pb.dx[i] = gr->dx ? gr->dx[i] : gr->lx / pb.nx;
     for (int j = 0; j < pb.ny; j++) pb.dy[j] = gr->dy ? gr->dy[j] : gr->ly / pb.ny;
-    for (double d : pb.dx) if (!(d > 0.0) || !std::isfinite(d)) return fail(err, SIM_EINVAL, "cell widths must be positive");
-    for (double d : pb.dy) if (!(d > 0.0) || !std::isfinite(d)) return fail(err, SIM_EINVAL, "cell heights must be positive");
     for (int s = 0; s < 4; s++) {
-        int kd = bc->side_kind[s];
-        if (kd < 0 || kd > 3) return fail(err, SIM_EINVAL, "side %d: unknown kind %d", s, kd);
-        if (kd == SIM_BC_INFLOW && s != SIM_W) return fail(err, SIM_EINVAL, "inflow only on the west side");
-        if (kd == SIM_BC_OUTFLOW && s != SIM_E) return fail(err, SIM_EINVAL, "outflow only on the east side");
-        pb.side_kind[s] = kd;
+        pb.side_kind[s] = bc->side_kind[s];
         pb.side_vel[s] = bc->side_vel[s];
         pb.side_T[s] = bc->side_T[s];
-        if (kd == SIM_BC_WALL && !(bc->side_T[s] > 0.0)) return fail(err, SIM_EINVAL, "wall temperature must be positive");
     }
     pb.body_T = bc->body_T;
-    if (bc->n_rect < 0 || (bc->n_rect > 0 && !bc->rect)) return fail(err, SIM_EINVAL, "bad obstacle list");
-    if (bc->n_rect > 0 && !(bc->body_T > 0.0)) return fail(err, SIM_EINVAL, "obstacle temperature must be positive");
-    for (int r = 0; r < bc->n_rect; r++) {
-        const int *q = bc->rect + 4 * r;
-        if (q[0] < 2 || q[1] < 2 || q[2] > pb.nx - 2 || q[3] > pb.ny - 2 || q[2] - q[0] < 2 || q[3] - q[1] < 2)
-            return fail(err, SIM_EINVAL, "obstacle %d [%d,%d,%d,%d) must be >= 2 cells wide and >= 2 cells from the sides",
-                        r, q[0], q[1], q[2], q[3]);
-        pb.rect.insert(pb.rect.end(), q, q + 4);
-    }
-    if (bc->iters < 1) return fail(err, SIM_EINVAL, "iters must be >= 1");
-    if (!(bc->tol >= 0.0)) return fail(err, SIM_EINVAL, "tol must be >= 0");
-    if (bc->precision != SIM_FP64 && bc->precision != SIM_MIXED && bc->precision != SIM_DF64)
-        return fail(err, SIM_EINVAL, "unknown precision");
-    if (!(bc->zeta_coef >= 0.0) || !(bc->tau_coef >= 0.0) || !std::isfinite(bc->zeta_coef) ||
-        !std::isfinite(bc->tau_coef))
-        return fail(err, SIM_EINVAL, "slip and jump coefficients must be finite and >= 0");
+    for (int r = 0; r < bc->n_rect; r++) pb.rect.insert(pb.rect.end(), bc->rect + 4 * r, bc->rect + 4 * r + 4);
     pb.iters = bc->iters;
     pb.tol = bc->tol;
     pb.seed = bc->seed;
@@ -206,7 +178,6 @@ sim_status read_problem(const sim_grid *gr, const sim_gas *gas, const sim_bc *bc
         pb.in_u[j] = bc->inflow_u ? bc->inflow_u[j] : pb.u_in;
         pb.in_T[j] = bc->inflow_T ? bc->inflow_T[j] : 1.0;
         pb.in_p[j] = bc->inflow_p ? bc->inflow_p[j] : 1.0;
-        if (!(pb.in_T[j] > 0.0)) return fail(err, SIM_EINVAL, "inflow temperature must be positive");
     }
     // time step: given, or cfl * min cell size / (U_ref + sound speed)
     pb.k.dt = time_step(gr, bc, pb.u_in, pb.gamma);

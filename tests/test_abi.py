@@ -25,7 +25,8 @@ def declared_functions():
     inc = os.path.join(ROOT, "include")
     for f in sorted(os.listdir(inc)):
         if f.endswith(".h"):
-            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+            with open(os.path.join(inc, f)) as fh:
+                text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
             names |= set(re.findall(r"\b((?:sim|simplets)_[a-z0-9_]+)\s*\(", text))
     return sorted(names)
 
@@ -39,7 +40,8 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_no_undeclared_sim_symbols(lib):
-    out = os.popen(f"nm -D --defined-only {sim.LIB_PATH}").read()
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", sim.LIB_PATH], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\b((?:sim|simplets)_[a-z0-9_]+)\b", out))
     assert exported <= set(declared_functions())
 
