@@ -13,8 +13,16 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsimplets.so")
-SOURCES = ["sweep_kernels.cu", "persistent.cu", "simplets_host.cu", "alu_probe.cu", "noalloc.cu"]
+SOURCES = ["phase_df64.cu", "step_df64.cu", "phase_fp64.cu", "step_fp64.cu", "phase_mixed.cu", "step_mixed.cu",
+           "sweep_kernels.cu", "persistent.cu", "simplets_host.cu", "alu_probe.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The FP32 and double-float kernels are compiled without multiply-add
+# contraction: every FP32 operation is rounded as written (the FMAs they need
+# are explicit), so each compiled form of a body -- descriptor read in place
+# or staged, per-phase or persistent -- gives the same bits.  The FP64 kernels
+# keep it: they are bound by the FP64 pipe, where each fused pair saves an
+# instruction, and all their forms stage the descriptor the same way.
+EXTRA_FLAGS = {f: ["--fmad=false"] for f in ("phase_mixed.cu", "step_mixed.cu", "phase_df64.cu", "step_df64.cu")}
 
 
 def nvcc() -> str:
@@ -44,7 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
-        cmd = [exe, *_flags(), "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [exe, *_flags(), *EXTRA_FLAGS.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -1,111 +1,25 @@
-// persistent.cu -- one kernel per time step of a batch: every phase of the
-// SIMPLE-TS iteration (arXiv:1802.04243, Section 3.1: explicit terms, then
-// per loop-2 iteration face densities, assembly, pressure, velocity
-// correction) over the batch's tile list, with a grid-wide barrier between
-// the phases instead of a kernel boundary.  The phases run the same bodies as
-// the per-phase kernels (sweep_bodies.cuh).  The kernel is launched
-// cooperatively with no more CTAs than stay resident, so every CTA reaches
-// every barrier; each barrier wait is bounded in time and a wait that runs
-// out sets an error word and ends the kernel (the host reads it as
-// SIM_ETIMEOUT).
+// persistent.cu -- launch of the persistent step kernel of a batch (k_step,
+// phase_kernels.cuh, compiled with the per-phase kernels of its arithmetic):
+// every phase of the SIMPLE-TS iteration (arXiv:1802.04243, Section 3.1:
+// explicit terms, then per loop-2 iteration face densities, assembly,
+// pressure, velocity correction) over the batch's tile list, with a
+// grid-wide barrier between the phases instead of a kernel boundary.  The
+// kernel is launched cooperatively with no more CTAs than stay resident, so
+// every CTA reaches every barrier; each barrier wait is bounded in time and a
+// wait that runs out sets an error word and ends the kernel (the host reads
+// it as SIM_ETIMEOUT).  Also the barrier's own check kernel.
 #include <cuda_runtime.h>
 
-#include "sweep_bodies.cuh"
+#include "grid_barrier.cuh"
 
 namespace stg {
 namespace {
 
-// Nanoseconds of the GPU's global timer.
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned load_acquire(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Longest wait at one barrier before the kernel gives up: far above a phase's
-// duration on any problem that fits the device.
-constexpr unsigned long long kBarrierLimitNs = 2000000000ull;
-
-// Barrier of all `nblocks` CTAs of the grid (generation counting).  Thread 0
-// of each CTA takes the CTA's arrival: it reads the generation, fences its
-// CTA's writes, counts itself in; the last CTA to arrive resets the count and
-// advances the generation, the others wait for that with acquire loads.
-// Returns false (in every thread of the CTA) once any CTA has timed out.
-__device__ bool grid_barrier(GridBarrier *b, unsigned nblocks)
-{
-    __shared__ unsigned s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        const unsigned gen = load_acquire(&b->gen);
-        __threadfence();
-        if (atomicAdd(&b->count, 1u) == nblocks - 1) {
-            atomicExch(&b->count, 0u);
-            __threadfence();
-            atomicAdd(&b->gen, 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            while (load_acquire(&b->gen) == gen) {
-                if (load_acquire(&b->err)) break;
-                if (global_ns() - t0 > kBarrierLimitNs) {
-                    atomicOr(&b->err, 1u);
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-        s_ok = load_acquire(&b->err) == 0;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-template <int PREC, bool IMPL, bool TVD>
-__global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 2 : 4)
-    k_step(const __grid_constant__ BatchPlan bp, const __grid_constant__ PhaseList ph, GridBarrier *bar)
-{
-    for (int q = 0; q < ph.n; q++) {
-        switch (ph.kind[q]) {
-        case PH_FACES: faces_phase<PREC, TVD>(bp, ph.a[q], ph.b[q]); break;
-        case PH_EXPLICIT: explicit_phase<PREC, TVD>(bp, ph.a[q]); break;
-        case PH_ASSEMBLE: assemble_phase<PREC, IMPL, TVD>(bp, ph.a[q], ph.b[q], ph.c[q]); break;
-        case PH_PRESSURE: pressure_phase<PREC>(bp, ph.a[q], ph.b[q], ph.c[q]); break;
-        default: velocity_phase<PREC>(bp, ph.a[q], ph.b[q]); break;
-        }
-        if (q + 1 < ph.n && !grid_barrier(bar, gridDim.x)) return;
-    }
-}
-
-template <int PREC, bool IMPL, bool TVD>
-void *step_kernel()
-{
-    return reinterpret_cast<void *>(&k_step<PREC, IMPL, TVD>);
-}
-
 void *step_kernel_of(int prec, bool implicit, bool tvd)
 {
-    switch (prec * 4 + (implicit ? 2 : 0) + (tvd ? 1 : 0)) {
-    case 0: return step_kernel<PREC_FP64, false, false>();
-    case 1: return step_kernel<PREC_FP64, false, true>();
-    case 2: return step_kernel<PREC_FP64, true, false>();
-    case 3: return step_kernel<PREC_FP64, true, true>();
-    case 4: return step_kernel<PREC_MIXED, false, false>();
-    case 5: return step_kernel<PREC_MIXED, false, true>();
-    case 6: return step_kernel<PREC_MIXED, true, false>();
-    case 7: return step_kernel<PREC_MIXED, true, true>();
-    case 8: return step_kernel<PREC_DF64, false, false>();
-    case 9: return step_kernel<PREC_DF64, false, true>();
-    case 10: return step_kernel<PREC_DF64, true, false>();
-    default: return step_kernel<PREC_DF64, true, true>();
-    }
+    if (prec == PREC_DF64) return step_kernel_for<PREC_DF64>(implicit, tvd);
+    if (prec == PREC_MIXED) return step_kernel_for<PREC_MIXED>(implicit, tvd);
+    return step_kernel_for<PREC_FP64>(implicit, tvd);
 }
 
 // Crosses `rounds` barriers expecting `nblocks` CTAs.

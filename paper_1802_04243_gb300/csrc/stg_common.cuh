@@ -217,6 +217,21 @@ void launch_assemble(const BatchPlan &bp, int prec, int prev, int old, int nw, b
                      void *stream);
 void launch_pressure(const BatchPlan &bp, int prec, int prev, int old, int nw, void *stream);
 void launch_velocity(const BatchPlan &bp, int prec, int old, int nw, void *stream);
+// The same for one arithmetic (PREC_*), each compiled in a translation unit
+// of its own (phase_kernels.cuh; lim: store the TVD limiters).
+template <int PREC>
+void launch_faces_of(const BatchPlan &bp, int level, bool tvd, int lim, void *stream);
+template <int PREC>
+void launch_explicit_of(const BatchPlan &bp, int prev, bool tvd, void *stream);
+template <int PREC>
+void launch_assemble_of(const BatchPlan &bp, int prev, int old, int nw, bool implicit, bool tvd, void *stream);
+template <int PREC>
+void launch_pressure_of(const BatchPlan &bp, int prev, int old, int nw, void *stream);
+template <int PREC>
+void launch_velocity_of(const BatchPlan &bp, int old, int nw, void *stream);
+// The persistent step kernel of one arithmetic (k_step, phase_kernels.cuh).
+template <int PREC>
+void *step_kernel_for(bool implicit, bool tvd);
 
 // Persistent step of a batch (persistent.cu): one cooperative kernel runs a
 // list of phases over the tile list, a grid barrier between each two.

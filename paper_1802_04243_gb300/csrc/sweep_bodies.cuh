@@ -172,6 +172,19 @@ __device__ __forceinline__ R gamma_corner(const GeoT<R> &g, const R *gam, int c,
     return at(g.y.wlo, j) * lo + at(g.y.whi, j) * hi;
 }
 
+// 2 C^T1_f times the length d of a face at index q of an axis: tabulated in
+// FP64 (a load instead of an FP64 multiply), formed in the branch that uses
+// it by the FP32 and double-float sweeps from ct1f2 = 2 C^T1_f (forming both
+// faces' factors up front made the double-float face kernel 15 % slower).
+template <typename R>
+__device__ __forceinline__ R face_ct2(const AxisT<R> &ax, int q, R ct1f2, R d)
+{
+    if constexpr (std::is_same<R, double>::value)
+        return at(ax.ct2d, q);
+    else
+        return ct1f2 * d;
+}
+
 // Volume of cell (i,j) per unit time, dx_i dy_j / dt: the factor of the
 // transient terms of Eqs. pl30 and pl24 once those equations are divided by
 // dt (as the momentum equations Eqs. pl14-pl16 are written).  FP64 takes
@@ -416,17 +429,7 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
     const int c = Ix{P}(i, j);
     if (i > g.nx || j > g.ny) return;
     const R dxi = at(g.x.d, i), dyj = at(g.y.d, j);
-    // 2 C^T1_f times the face area: tabulated in FP64 (a load instead of two
-    // FP64 multiplies), formed here by the FP32 and double-float sweeps
-    R ct2_dy, ct2_dx;
-    if constexpr (std::is_same<R, double>::value) {
-        ct2_dy = at(g.y.ct2d, j);
-        ct2_dx = at(g.x.ct2d, i);
-    } else {
-        const R ct1f2 = R(2) * k.CT1f;
-        ct2_dy = ct1f2 * dyj;
-        ct2_dx = ct1f2 * dxi;
-    }
+    const R ct1f2 = R(2) * k.CT1f;     // (unused in FP64, which reads face_ct2's table)
     if (j < g.ny) {
         const R vel = u[c], rl = rho[c - 1], rr = rho[c];
         R val = upwind(rl, rr, vel);
@@ -436,7 +439,7 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         const R rdy = val * dyj;
         w.ru_dy[c] = rdy;
         w.Fx[c] = rdy * vel;
-        w.DTx[c] = conductance(gam[c - 1], gam[c], at(g.x.d, i - 1), dxi, ct2_dy);
+        w.DTx[c] = conductance(gam[c - 1], gam[c], at(g.x.d, i - 1), dxi, face_ct2(g.y, j, ct1f2, dyj));
     }
     if (i < g.nx) {
         const R vel = v[c], rb = rho[c - P], rt = rho[c];
@@ -447,7 +450,7 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         const R rdx = val * dxi;
         w.rv_dx[c] = rdx;
         w.Fy[c] = rdx * vel;
-        w.DTy[c] = conductance(gam[c - P], gam[c], at(g.y.d, j - 1), dyj, ct2_dx);
+        w.DTy[c] = conductance(gam[c - P], gam[c], at(g.y.d, j - 1), dyj, face_ct2(g.x, i, ct1f2, dxi));
     }
     w.Bgc[c] = k.B * gamma_corner(g, gam, c, i, j);
     if (i < g.nx && j < g.ny) {
@@ -1151,36 +1154,48 @@ __device__ __forceinline__ void velocity_mixed_body(const Geo &g, const Level &n
 // resident CTAs in turn.  A single problem is a list of one; every caller
 // runs these same kernels, so a problem's arithmetic does not depend on what
 // else shares the launch or on the tile shape.
-// The descriptor of the tile's problem is staged in shared memory: from the
-// launch parameters when the list holds one problem, else from the device
-// array.  Every kernel body reads it from there, so one compiled body serves
-// both sources.
-template <typename F>
+// Where a kernel reads the descriptor of the tile's problem from (ONE):
+// - staged in shared memory (ONE false): from the launch parameters when the
+//   list holds one problem, else from the device array, once per problem a
+//   CTA meets;
+// - read in place from the launch parameters (ONE true, a list of one
+//   problem): no copy and no barrier before the first tile.
+// On the 4864 x 1216 channel the second made the FP32 (mixed) sweep 8 % and
+// the double-float sweep 12 % faster and the FP64 sweep 2 % slower, so the
+// host takes it for one problem in FP32 or double-float.  Both give the same
+// bits.
+template <bool ONE, typename F>
 __device__ __forceinline__ void for_tiles(const BatchPlan &bp, F &&f)
 {
-    static_assert(sizeof(Inst) % 8 == 0, "Inst is copied as 8-byte words");
-    constexpr int kWords = sizeof(Inst) / 8;
-    __shared__ __align__(16) Inst sI;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
-    int have = -1;
-    for (int t = blockIdx.x; t < bp.n_tiles; t += gridDim.x) {
-        const int q = bp.n_inst == 1 ? 0 : bp.tile_inst[t];
-        if (q != have) {
-            if (have >= 0) __syncthreads();           // the previous problem's tile is done
-            const unsigned long long *src = bp.n_inst == 1
-                                                ? reinterpret_cast<const unsigned long long *>(&bp.one)
-                                                : reinterpret_cast<const unsigned long long *>(bp.inst + q);
-            unsigned long long *dst = reinterpret_cast<unsigned long long *>(&sI);
-            for (int w = tid; w < kWords; w += nthr) dst[w] = src[w];
-            __syncthreads();
-            have = q;
-        }
-        const Inst &I = sI;
+    auto tile = [&](const Inst &I, int t) {
         const int lt = t - I.tile0;
         int i = I.x0 + (lt % I.tiles_x) * bp.tx + threadIdx.x;
         const int j = (lt / I.tiles_x) * bp.ty + threadIdx.y;
         if (I.x_stop > 0 && i >= I.x_stop) i = I.g.nx + 1;   // beyond every body's range
         f(I, i, j);
+    };
+    if constexpr (ONE) {
+        for (int t = blockIdx.x; t < bp.n_tiles; t += gridDim.x) tile(bp.one, t);
+    } else {
+        static_assert(sizeof(Inst) % 8 == 0, "Inst is copied as 8-byte words");
+        constexpr int kWords = sizeof(Inst) / 8;
+        __shared__ __align__(16) Inst sI;
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+        int have = -1;
+        for (int t = blockIdx.x; t < bp.n_tiles; t += gridDim.x) {
+            const int q = bp.n_inst == 1 ? 0 : bp.tile_inst[t];
+            if (q != have) {
+                if (have >= 0) __syncthreads();           // the previous problem's tile is done
+                const unsigned long long *src = bp.n_inst == 1
+                                                    ? reinterpret_cast<const unsigned long long *>(&bp.one)
+                                                    : reinterpret_cast<const unsigned long long *>(bp.inst + q);
+                unsigned long long *dst = reinterpret_cast<unsigned long long *>(&sI);
+                for (int w = tid; w < kWords; w += nthr) dst[w] = src[w];
+                __syncthreads();
+                have = q;
+            }
+            tile(sI, t);
+        }
     }
 }
 
@@ -1209,11 +1224,11 @@ __device__ __forceinline__ void reset_residuals(const BatchPlan &bp)
 // The phases of one loop-2 iteration over a tile list, each what one kernel
 // of sweep_kernels.cu runs; the persistent step kernel of persistent.cu runs
 // them one after another with a grid barrier between them.
-template <int PREC, bool TVD>
+template <int PREC, bool TVD, bool ONE = false>
 __device__ __forceinline__ void faces_phase(const BatchPlan &bp, int level, int limiters)
 {
     reset_residuals(bp);
-    for_tiles(bp, [&](const Inst &I, int i, int j) {
+    for_tiles<ONE>(bp, [&](const Inst &I, int i, int j) {
         if constexpr (PREC == PREC_MIXED) {
             const LevelT<float> &L = I.lv32[level];
             face_densities_body<float, TVD>(I.g32, I.k32, L.u, L.v, L.rho, L.gam, L.T, limiters, I.w32, i, j);
@@ -1227,10 +1242,10 @@ __device__ __forceinline__ void faces_phase(const BatchPlan &bp, int level, int 
     });
 }
 
-template <int PREC, bool TVD>
+template <int PREC, bool TVD, bool ONE = false>
 __device__ __forceinline__ void explicit_phase(const BatchPlan &bp, int prev)
 {
-    for_tiles(bp, [&](const Inst &I, int i, int j) {
+    for_tiles<ONE>(bp, [&](const Inst &I, int i, int j) {
         if constexpr (PREC == PREC_MIXED)
             explicit_terms_body<float, TVD>(I.g32, I.k32, I.lv32[prev], I.w32, i, j);
         else if constexpr (PREC == PREC_DF64)
@@ -1240,10 +1255,10 @@ __device__ __forceinline__ void explicit_phase(const BatchPlan &bp, int prev)
     });
 }
 
-template <int PREC, bool IMPL, bool TVD>
+template <int PREC, bool IMPL, bool TVD, bool ONE = false>
 __device__ __forceinline__ void assemble_phase(const BatchPlan &bp, int prev, int old, int nw)
 {
-    for_tiles(bp, [&](const Inst &I, int i, int j) {
+    for_tiles<ONE>(bp, [&](const Inst &I, int i, int j) {
         if constexpr (PREC == PREC_MIXED)
             assemble_body<float, IMPL, TVD>(I.g32, I.k32, I.lv32[prev], I.lv32[old], I.lv32[nw].T, I.lv[nw].T,
                                            I.w32, i, j);
@@ -1255,10 +1270,10 @@ __device__ __forceinline__ void assemble_phase(const BatchPlan &bp, int prev, in
     });
 }
 
-template <int PREC>
+template <int PREC, bool ONE = false>
 __device__ __forceinline__ void pressure_phase(const BatchPlan &bp, int prev, int old, int nw)
 {
-    for_tiles(bp, [&](const Inst &I, int i, int j) {
+    for_tiles<ONE>(bp, [&](const Inst &I, int i, int j) {
         if constexpr (PREC == PREC_MIXED)
             pressure_mixed_body(I.g, I.k, I.g32, I.k32, I.lv[prev], I.lv[old], I.lv[nw], I.lv32[old], I.lv32[nw],
                                 I.w32, I.w.res, i, j, owns(I, i));
@@ -1270,10 +1285,10 @@ __device__ __forceinline__ void pressure_phase(const BatchPlan &bp, int prev, in
     });
 }
 
-template <int PREC>
+template <int PREC, bool ONE = false>
 __device__ __forceinline__ void velocity_phase(const BatchPlan &bp, int old, int nw)
 {
-    for_tiles(bp, [&](const Inst &I, int i, int j) {
+    for_tiles<ONE>(bp, [&](const Inst &I, int i, int j) {
         if constexpr (PREC == PREC_MIXED)
             velocity_mixed_body(I.g, I.lv[nw], I.lv32[old], I.lv32[nw], I.w32, I.w.res, I.east_outflow, i, j,
                                 owns(I, i));

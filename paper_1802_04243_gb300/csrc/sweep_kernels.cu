@@ -15,7 +15,9 @@
 // and, once per step for the explicit scheme, k_explicit (Eqs. pl15_11,
 // pl31_1 and the u mirror).  Each thread owns one grid position (i, j) and
 // the cell, the u face and the v face with that index; the equation kernels
-// walk a list of tiles of one or more problems.
+// walk a list of tiles of one or more problems.  This file holds the ghost,
+// conversion, gather/scatter and check kernels and the launchers; the
+// equation kernels are in phase_kernels.cuh, compiled once per arithmetic.
 //
 // Boundary rules: wall ghost and obstacle cells hold the wall state; a
 // temperature or tangential velocity read across a wall is reflected about
@@ -132,43 +134,6 @@ __global__ void k_shadow(Level L, LevelT<float> S, size_t n)
     }
 }
 
-
-// One kernel per phase of the iteration (the bodies: sweep_bodies.cuh).
-template <int PREC, bool TVD>
-__global__ void __launch_bounds__(256) k_faces(const __grid_constant__ BatchPlan bp, int level, int limiters)
-{
-    faces_phase<PREC, TVD>(bp, level, limiters);
-}
-
-template <int PREC, bool TVD>
-__global__ void __launch_bounds__(256) k_explicit(const __grid_constant__ BatchPlan bp, int prev)
-{
-    explicit_phase<PREC, TVD>(bp, prev);
-}
-
-// Resident CTAs per SM: two for the FP64 assembly (bound by the FP64 pipe),
-// four for the FP32 and double-float ones, which are latency-bound
-// (measured against three: FP32 at 64 registers with a few bytes of spills
-// 5-6 % faster, double-float up to 2.5 % despite its spills; five CTAs were
-// slower for FP32).
-template <int PREC, bool IMPL, bool TVD>
-__global__ void __launch_bounds__(256, PREC == PREC_FP64 ? 2 : 4) k_assemble(const __grid_constant__ BatchPlan bp,
-                                                                              int prev, int old, int nw)
-{
-    assemble_phase<PREC, IMPL, TVD>(bp, prev, old, nw);
-}
-
-template <int PREC>
-__global__ void __launch_bounds__(256) k_pressure(const __grid_constant__ BatchPlan bp, int prev, int old, int nw)
-{
-    pressure_phase<PREC>(bp, prev, old, nw);
-}
-
-template <int PREC>
-__global__ void __launch_bounds__(256) k_velocity(const __grid_constant__ BatchPlan bp, int old, int nw)
-{
-    velocity_phase<PREC>(bp, old, nw);
-}
 
 // Whole-level conversions FP64 <-> double-float, ghosts included.
 __global__ void k_split(Level L, LevelT<df64> D, size_t n)
@@ -496,71 +461,43 @@ void launch_halo_copies(const HaloCopy *copies, int n, int max_words, void *stre
     k_halo_copies<<<dim3((unsigned)((max_words + 255) / 256), (unsigned)n), 256, 0, (cudaStream_t)stream>>>(copies, n);
 }
 
+// The equation kernels' launchers dispatch to the per-arithmetic
+// translation units (phase_fp64.cu, phase_mixed.cu, phase_df64.cu).
 void launch_faces(const BatchPlan &bp, int prec, int level, bool tvd, bool limiters, void *stream)
 {
-    cudaStream_t s = (cudaStream_t)stream;
-    const dim3 bl(bp.tx, bp.ty);
     const int lim = tvd && limiters;
-    switch (prec * 2 + (tvd ? 1 : 0)) {
-    case 5: k_faces<PREC_DF64, true><<<bp.grid, bl, 0, s>>>(bp, level, lim); break;
-    case 4: k_faces<PREC_DF64, false><<<bp.grid, bl, 0, s>>>(bp, level, 0); break;
-    case 3: k_faces<PREC_MIXED, true><<<bp.grid, bl, 0, s>>>(bp, level, lim); break;
-    case 2: k_faces<PREC_MIXED, false><<<bp.grid, bl, 0, s>>>(bp, level, 0); break;
-    case 1: k_faces<PREC_FP64, true><<<bp.grid, bl, 0, s>>>(bp, level, lim); break;
-    default: k_faces<PREC_FP64, false><<<bp.grid, bl, 0, s>>>(bp, level, 0); break;
-    }
+    if (prec == PREC_DF64) launch_faces_of<PREC_DF64>(bp, level, tvd, lim, stream);
+    else if (prec == PREC_MIXED) launch_faces_of<PREC_MIXED>(bp, level, tvd, lim, stream);
+    else launch_faces_of<PREC_FP64>(bp, level, tvd, lim, stream);
 }
 
 void launch_explicit(const BatchPlan &bp, int prec, int prev, bool tvd, void *stream)
 {
-    cudaStream_t s = (cudaStream_t)stream;
-    const dim3 bl(bp.tx, bp.ty);
-    switch (prec * 2 + (tvd ? 1 : 0)) {
-    case 5: k_explicit<PREC_DF64, true><<<bp.grid, bl, 0, s>>>(bp, prev); break;
-    case 4: k_explicit<PREC_DF64, false><<<bp.grid, bl, 0, s>>>(bp, prev); break;
-    case 3: k_explicit<PREC_MIXED, true><<<bp.grid, bl, 0, s>>>(bp, prev); break;
-    case 2: k_explicit<PREC_MIXED, false><<<bp.grid, bl, 0, s>>>(bp, prev); break;
-    case 1: k_explicit<PREC_FP64, true><<<bp.grid, bl, 0, s>>>(bp, prev); break;
-    default: k_explicit<PREC_FP64, false><<<bp.grid, bl, 0, s>>>(bp, prev); break;
-    }
-}
-
-template <int PREC>
-void assemble_variant(const BatchPlan &bp, int prev, int old, int nw, bool implicit, bool tvd, cudaStream_t s)
-{
-    const dim3 bl(bp.tx, bp.ty);
-    const int g = bp.grid_asm > 0 ? bp.grid_asm : bp.grid;
-    if (implicit && tvd) k_assemble<PREC, true, true><<<g, bl, 0, s>>>(bp, prev, old, nw);
-    else if (implicit) k_assemble<PREC, true, false><<<g, bl, 0, s>>>(bp, prev, old, nw);
-    else if (tvd) k_assemble<PREC, false, true><<<g, bl, 0, s>>>(bp, prev, old, nw);
-    else k_assemble<PREC, false, false><<<g, bl, 0, s>>>(bp, prev, old, nw);
+    if (prec == PREC_DF64) launch_explicit_of<PREC_DF64>(bp, prev, tvd, stream);
+    else if (prec == PREC_MIXED) launch_explicit_of<PREC_MIXED>(bp, prev, tvd, stream);
+    else launch_explicit_of<PREC_FP64>(bp, prev, tvd, stream);
 }
 
 void launch_assemble(const BatchPlan &bp, int prec, int prev, int old, int nw, bool implicit, bool tvd,
                      void *stream)
 {
-    cudaStream_t s = (cudaStream_t)stream;
-    if (prec == PREC_DF64) assemble_variant<PREC_DF64>(bp, prev, old, nw, implicit, tvd, s);
-    else if (prec == PREC_MIXED) assemble_variant<PREC_MIXED>(bp, prev, old, nw, implicit, tvd, s);
-    else assemble_variant<PREC_FP64>(bp, prev, old, nw, implicit, tvd, s);
+    if (prec == PREC_DF64) launch_assemble_of<PREC_DF64>(bp, prev, old, nw, implicit, tvd, stream);
+    else if (prec == PREC_MIXED) launch_assemble_of<PREC_MIXED>(bp, prev, old, nw, implicit, tvd, stream);
+    else launch_assemble_of<PREC_FP64>(bp, prev, old, nw, implicit, tvd, stream);
 }
 
 void launch_pressure(const BatchPlan &bp, int prec, int prev, int old, int nw, void *stream)
 {
-    cudaStream_t s = (cudaStream_t)stream;
-    const dim3 bl(bp.tx, bp.ty);
-    if (prec == PREC_DF64) k_pressure<PREC_DF64><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
-    else if (prec == PREC_MIXED) k_pressure<PREC_MIXED><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
-    else k_pressure<PREC_FP64><<<bp.grid, bl, 0, s>>>(bp, prev, old, nw);
+    if (prec == PREC_DF64) launch_pressure_of<PREC_DF64>(bp, prev, old, nw, stream);
+    else if (prec == PREC_MIXED) launch_pressure_of<PREC_MIXED>(bp, prev, old, nw, stream);
+    else launch_pressure_of<PREC_FP64>(bp, prev, old, nw, stream);
 }
 
 void launch_velocity(const BatchPlan &bp, int prec, int old, int nw, void *stream)
 {
-    cudaStream_t s = (cudaStream_t)stream;
-    const dim3 bl(bp.tx, bp.ty);
-    if (prec == PREC_DF64) k_velocity<PREC_DF64><<<bp.grid, bl, 0, s>>>(bp, old, nw);
-    else if (prec == PREC_MIXED) k_velocity<PREC_MIXED><<<bp.grid, bl, 0, s>>>(bp, old, nw);
-    else k_velocity<PREC_FP64><<<bp.grid, bl, 0, s>>>(bp, old, nw);
+    if (prec == PREC_DF64) launch_velocity_of<PREC_DF64>(bp, old, nw, stream);
+    else if (prec == PREC_MIXED) launch_velocity_of<PREC_MIXED>(bp, old, nw, stream);
+    else launch_velocity_of<PREC_FP64>(bp, old, nw, stream);
 }
 
 }  // namespace stg
