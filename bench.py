@@ -467,8 +467,8 @@ def run_paper_sweep(args, local_rank):
 
 # ------------------------------------------------------------ plan sweep
 
-PLAN_CANDIDATES = [(32, 8, 0, 0), (32, 4, 0, 0), (64, 2, 0, 0), (32, 4, 0, 1216), (32, 4, 0, 912),
-                   (32, 4, 0, 1824), (32, 8, 0, 608), (32, 2, 0, 0), (32, 2, 0, 2432)]
+PLAN_CANDIDATES = [(32, 8, 0, 0), (32, 4, 0, 0), (64, 2, 0, 0), (64, 4, 0, 0), (32, 4, 0, 1216), (32, 8, 0, 608),
+                   (32, 8, 0, 1216), (32, 8, 0, 912), (32, 2, 0, 0), (128, 1, 0, 0)]
 
 
 def run_plan_sweep(args, local_rank):
@@ -575,10 +575,10 @@ def step_hbm(case, ms_per_step):
 # DRAM bytes per cell, from the case named; the commands are in profiles/.
 MIXED_KERNEL_NCU = {
     "case": _C4HALF + ", ncu --metrics (one kernel per capture)",
-    "faces": {"fma_pct": 18.2, "lsu_pct": 41.0, "fp64_pct": 0.0, "warps_active_pct": 65.0, "dram_bytes": 20.4},
-    "assemble": {"fma_pct": 21.2, "lsu_pct": 61.3, "fp64_pct": 0.0, "warps_active_pct": 47.0, "dram_bytes": 72.7},
-    "pressure": {"fma_pct": 13.5, "lsu_pct": 30.8, "fp64_pct": 69.5, "warps_active_pct": 57.0, "dram_bytes": 61.6},
-    "velocity": {"fma_pct": 14.0, "lsu_pct": 40.1, "fp64_pct": 18.7, "warps_active_pct": 64.2, "dram_bytes": 35.7},
+    "faces": {"fma_pct": 19.2, "lsu_pct": 34.5, "fp64_pct": 0.0, "warps_active_pct": 85.4, "dram_bytes": 20.4},
+    "assemble": {"fma_pct": 24.9, "lsu_pct": 41.9, "fp64_pct": 0.0, "warps_active_pct": 46.5, "dram_bytes": 71.4},
+    "pressure": {"fma_pct": 12.7, "lsu_pct": 22.3, "fp64_pct": 75.6, "warps_active_pct": 70.3, "dram_bytes": 61.1},
+    "velocity": {"fma_pct": 9.4, "lsu_pct": 34.0, "fp64_pct": 24.8, "warps_active_pct": 88.4, "dram_bytes": 35.9},
 }
 
 

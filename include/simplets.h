@@ -207,8 +207,9 @@ sim_status sim_coefficients(sim_t sim, double out[9]);
  * one grid position per thread, walked by `ctas` CTAs (0: one CTA per tile);
  * the assembly kernel by `asm_ctas` CTAs (0: as the others).
  * tile_x in {16, 32, 64, 128, 256}; tile_x * tile_y in {32, 64, 128, 256}.
- * Defaults (measured on the 4864x1216 channel): 32 x 4 tiles, one CTA per
- * tile, the mixed path's assembly on 4 CTAs per SM; 32 x 8 for SIM_DF64.
+ * Defaults (measured on the 4864x1216 channel): SIM_FP64 32 x 4 tiles, one
+ * CTA per tile; SIM_MIXED 32 x 8 tiles, one CTA per tile, the assembly on 4
+ * CTAs per SM; SIM_DF64 32 x 8, one CTA per tile.
  * Synchronous; the captured step graphs are rebuilt on the next sim_step.
  * Errors: SIM_EINVAL, SIM_ECUDA. */
 sim_status sim_set_plan(sim_t sim, int tile_x, int tile_y, int ctas, int asm_ctas);

@@ -508,23 +508,24 @@ sim_status single_plan(sim_t s, int tx, int ty, int ctas, int asm_ctas)
 }
 
 // The measured best distribution per arithmetic on the 4864x1216 channel
-// (bench.py --sweep plans): FP64 and mixed tiles of 32 x 4 threads, one CTA
-// per tile, and for the mixed path's FP32 assembly as many CTAs as stay
-// resident (1024 threads per SM at its 64 registers) walking the tiles: the
-// descriptor each CTA stages is then read once per CTA instead of once per
-// tile; double-float 32 x 8, one CTA per tile.
+// (bench.py --sweep plans):
+// - FP64: tiles of 32 x 4 threads, one CTA per tile;
+// - mixed: tiles of 32 x 8, one CTA per tile, and for the FP32 assembly as
+//   many CTAs as stay resident (1024 threads per SM at its 64 registers)
+//   walking the tiles (6375 Mcell-steps/s against 6165 with 32 x 4 tiles:
+//   the velocity kernel, 0.101 -> 0.082 ms, ends half as many CTAs, each
+//   with its residual atomics);
+// - double-float: 32 x 8, one CTA per tile.
 sim_status default_plan(sim_t s)
 {
     const int prec = prec_of(s);
     if (prec == PREC_DF64) return single_plan(s, 32, 8, 0, 0);
-    const int tx = 32, ty = 4;
-    int asm_ctas = 0;
-    if (prec == PREC_MIXED) {
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-            asm_ctas = 1024 / (tx * ty) * sms;
-    }
+    if (prec == PREC_FP64) return single_plan(s, 32, 4, 0, 0);
+    const int tx = 32, ty = 8;
+    int dev = 0, sms = 0, asm_ctas = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+        asm_ctas = 1024 / (tx * ty) * sms;
     return single_plan(s, tx, ty, 0, asm_ctas);
 }
 

@@ -1072,11 +1072,13 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
             const float T32 = nw32.T[c];
             const double Tn = widen(T32);
             // divided by dt, as the FP64 pressure kernel: the cell's volume
-            // per unit time (FP64 from the axis table) in the transient terms
-            const float ap0 = dxi * at(g32.y.dt1, j) / T32 + (apw + ape + aps + apn);
+            // per unit time in the transient terms, a coefficient assembled
+            // in FP32 like the others; the source accumulates it in FP64
+            // (the FP32 product widens exactly)
+            const float vdt = dxi * at(g32.y.dt1, j);
+            const float ap0 = vdt / T32 + (apw + ape + aps + apn);
             const float div = (bpe - bpw) + (bpn - bps);
-            const double vdt = at(g.x.d, i) * at(g.y.dt1, j);
-            const double bp = fma(prev.rho[c], vdt, widen(-div));
+            const double bp = fma(prev.rho[c], widen(vdt), widen(-div));
             double num = fma(widen(apw), old.p[c - 1], bp);
             num = fma(widen(ape), old.p[c + 1], num);
             num = fma(widen(aps), old.p[c - P], num);
