@@ -2,7 +2,7 @@
 // problem validation, the non-dimensional coefficients, geometry flags, the
 // start state, device memory and the loop-1 / loop-2 driver of SIMPLE-TS
 // (arXiv:1802.04243, Section 3.1).  Every arithmetic step of the sweep runs in
-// the kernels of sweep_kernels.cu.
+// the kernels of phase_kernels.cuh and sweep_kernels.cu.
 #include <cuda_runtime.h>
 
 #include <cmath>

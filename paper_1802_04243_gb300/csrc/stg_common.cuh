@@ -201,7 +201,8 @@ enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
 // copied from the neighbour, no ghost rule applies)
 enum { BC_WALL = 0, BC_SYMMETRY = 1, BC_INFLOW = 2, BC_OUTFLOW = 3, BC_INTERFACE = 4 };
 
-// Launch wrappers (sweep_kernels.cu).  All are asynchronous on `stream`.
+// Launch wrappers (sweep_kernels.cu; the equation kernels' own launchers in
+// phase_kernels.cuh).  All are asynchronous on `stream`.
 //
 // Equation kernels: one launch per phase over a tile list (one problem or a
 // batch).  `prec` (PREC_*) selects the arithmetic: FP64; the FP32 assembly

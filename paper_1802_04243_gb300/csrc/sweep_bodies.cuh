@@ -1,10 +1,11 @@
 // sweep_bodies.cuh -- device code of one SIMPLE-TS time step
 // (K. S. Shterev, arXiv:1802.04243, Sections 3.1 and 3.2) shared by the
-// per-phase kernels (sweep_kernels.cu) and the persistent step kernel of
-// batches (persistent.cu): the equation bodies of every phase, templated on
-// the arithmetic, the residual reduction and the tile-list walk.  Both
-// translation units compile these same bodies, so a position's arithmetic is
-// the same whichever kernel runs it.
+// per-phase kernels and the persistent step kernel of batches
+// (phase_kernels.cuh, compiled per arithmetic in phase_*.cu and step_*.cu)
+// and by the support kernels of sweep_kernels.cu: the equation bodies of every
+// phase, templated on the arithmetic, the residual reduction and the
+// tile-list walk.  Every kernel compiles these same bodies, so a position's
+// arithmetic is the same whichever kernel runs it.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -1223,9 +1224,9 @@ __device__ __forceinline__ void reset_residuals(const BatchPlan &bp)
 
 // ------------------------------------------------------------------ phases
 
-// The phases of one loop-2 iteration over a tile list, each what one kernel
-// of sweep_kernels.cu runs; the persistent step kernel of persistent.cu runs
-// them one after another with a grid barrier between them.
+// The phases of one loop-2 iteration over a tile list, each what one
+// per-phase kernel of phase_kernels.cuh runs; the persistent step kernel
+// (k_step) runs them one after another with a grid barrier between them.
 template <int PREC, bool TVD, bool ONE = false>
 __device__ __forceinline__ void faces_phase(const BatchPlan &bp, int level, int limiters)
 {
