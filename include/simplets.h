@@ -158,9 +158,10 @@ sim_status sim_fields(sim_t sim, int field, double *host_dst, size_t n);
 /* Borrow the device array of one field of the current state.  *dev receives
  * the address of element (i, j) = (0, 0); element (i, j) is at
  * dev[j * (*pitch) + i] for -2 <= i, j (two ghost layers).  Valid until the
- * next sim_step, sim_set_fields or sim_destroy.  SIM_DF64: the FP64 array is
- * refreshed from the double-float state by work queued on the handle's
- * stream; synchronise with that stream before reading it elsewhere.
+ * next sim_step, sim_set_fields or sim_destroy.  SIM_DF64 and SIM_MIXED: the
+ * FP64 array is refreshed by work queued on the handle's stream (from the
+ * double-float state; in SIM_MIXED u, v, T and Gamma from the FP32 values the
+ * sweep keeps); synchronise with that stream before reading it elsewhere.
  * Errors: SIM_EINVAL. */
 sim_status sim_field_ptr(sim_t sim, int field, void **dev, size_t *pitch);
 

@@ -312,7 +312,8 @@ class Simulation:
         self._check(self.lib.sim_field_ptr(self.handle, FIELDS[name], ctypes.byref(dev), ctypes.byref(pitch)))
         if self._stream:
             # the handle's stream may still be filling the array (double-float
-            # state): torch's current stream waits for it
+            # state, the mixed path's FP64 u, v, T, Gamma): torch's current
+            # stream waits for it
             torch.cuda.current_stream().wait_stream(torch.cuda.ExternalStream(self._stream))
         ny, nx = self.shape(name)
         base = dev.value - (2 * pitch.value + 2) * 8

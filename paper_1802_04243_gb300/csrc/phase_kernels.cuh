@@ -68,6 +68,15 @@ __global__ void __launch_bounds__(256) k_velocity(const __grid_constant__ BatchP
     velocity_phase<PREC, ONE>(bp, old, nw);
 }
 
+// The mixed path's velocity kernel, latency-bound, held at eight resident
+// CTAs of 256 threads per SM (32 registers; left to itself the compiler took
+// 40 and the kernel ran 8 % slower).
+template <bool ONE>
+__global__ void __launch_bounds__(256, 8) k_velocity_mixed(const __grid_constant__ BatchPlan bp, int old, int nw)
+{
+    velocity_phase<PREC_MIXED, ONE>(bp, old, nw);
+}
+
 // One time step of a batch in one cooperative kernel (persistent.cu launches
 // it): the phases of the list over the tile list, a grid barrier between each
 // two; the descriptor is staged as in the per-phase kernels.
@@ -186,12 +195,19 @@ void launch_velocity_of(const BatchPlan &bp, int old, int nw, void *stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
     const dim3 bl(bp.tx, bp.ty);
-    if constexpr (PREC != PREC_FP64)
-        if (in_place<PREC>(bp)) {
+    if constexpr (PREC == PREC_MIXED) {
+        if (in_place<PREC>(bp))
+            k_velocity_mixed<true><<<bp.grid, bl, 0, s>>>(bp, old, nw);
+        else
+            k_velocity_mixed<false><<<bp.grid, bl, 0, s>>>(bp, old, nw);
+    } else if constexpr (PREC == PREC_DF64) {
+        if (in_place<PREC>(bp))
             k_velocity<PREC, true><<<bp.grid, bl, 0, s>>>(bp, old, nw);
-            return;
-        }
-    k_velocity<PREC, false><<<bp.grid, bl, 0, s>>>(bp, old, nw);
+        else
+            k_velocity<PREC, false><<<bp.grid, bl, 0, s>>>(bp, old, nw);
+    } else {
+        k_velocity<PREC, false><<<bp.grid, bl, 0, s>>>(bp, old, nw);
+    }
 }
 
 template <int PREC>

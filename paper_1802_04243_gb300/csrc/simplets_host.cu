@@ -68,6 +68,7 @@ struct sim_s {
     // mixed precision: FP32 shadow levels, FP32 scratch and grid factors
     bool mixed = false;
     Mixed mx{};
+    bool mx_dirty = false;                     // the FP64 u, v, T, Gamma lag behind the FP32 ones (mixed)
     float *d_pool32 = nullptr;
     float *d_axis32 = nullptr;
     // double-float precision: working levels, scratch and grid factors; the
@@ -456,12 +457,21 @@ LevelT<R> alloc_of(const LevelT<R> &v, long d)
     return LevelT<R>{v.u + d, v.v + d, v.p + d, v.T + d, v.rho + d, v.gam + d};
 }
 
-// The FP64 levels of the current state, brought up to date in DF64 mode.
+// The FP64 level of the current state brought up to date: from the
+// double-float level, or in the mixed path the FP64 u, v, T and Gamma, which
+// its sweep keeps in FP32 only (then the ghost refresh that follows a
+// velocity update, so the FP64 ghosts match too).
 void sync_out(sim_t s)
 {
     if (s->df && s->df_dirty) {
         launch_join(s->dfm.lv[s->cur], s->lv[s->cur], s->nelem, s->stream);
         s->df_dirty = false;
+    }
+    if (s->mixed && s->mx_dirty) {
+        launch_widen_mixed(s->geo, s->lv[s->cur], s->mx.lv[s->cur], s->sides.kind[SIDE_E] == BC_OUTFLOW, 0,
+                           s->pb.nx + 1, s->stream);
+        launch_ghosts(s->geo, s->sides, s->lv[s->cur], true, s->stream);
+        s->mx_dirty = false;
     }
 }
 
@@ -843,6 +853,7 @@ extern "C" sim_status sim_step(sim_t s, int n_steps, int scheme)
     const bool implicit = scheme & SIM_IMPLICIT, tvd = scheme & SIM_TVD;
     const Problem &pb = s->pb;
     if (n_steps > 0 && s->df) s->df_dirty = true;
+    if (n_steps > 0 && s->mixed) s->mx_dirty = true;
 
     // Fixed loop-2 length and no event timing: replay one captured graph per
     // step (the three state levels rotate, so a step graph exists for each
@@ -1060,6 +1071,7 @@ extern "C" sim_status sim_set_state(sim_t s, const double *u, const double *v, c
     if (s->mixed) launch_shadow(s->geo, L, s->mx.lv[s->cur], s->nelem, s->stream);
     if (s->df) launch_split(L, s->dfm.lv[s->cur], s->nelem, s->stream);
     s->df_dirty = false;
+    s->mx_dirty = false;
     CUDA_TRY(s, cudaGetLastError());
     s->diverged = false;
     s->set_mask = 0;
@@ -1386,6 +1398,7 @@ void set_levels(sim_batch_t b, int cur)
         s->cur = cur;
         s->last_iters = b->iters;
         if (s->df) s->df_dirty = true;
+        if (s->mixed) s->mx_dirty = true;
     }
 }
 
@@ -1923,10 +1936,13 @@ extern "C" sim_status sim_strips_fields(sim_strips_t h, int field, double *host_
     const int ns = (int)h->strip.size();
     for (int k = 0; k < ns; k++) {
         sim_t s = h->strip[k];
+        const int i1 = k == ns - 1 ? h->pb.nx + 1 : h->own1[k];
         if (s->df)
             launch_join(alloc_of(s->dfm.lv[h->cur], s->shift), alloc_of(s->lv[h->cur], s->shift), s->nelem, h->stream);
-        launch_gather_cols(s->geo, field, s->lv[h->cur], h->d_stage, h->own0[k], k == ns - 1 ? h->pb.nx + 1 : h->own1[k],
-                           h->stream);
+        if (s->mixed)
+            launch_widen_mixed(s->geo, s->lv[h->cur], s->mx.lv[h->cur], s->sides.kind[SIDE_E] == BC_OUTFLOW,
+                               h->own0[k], i1, h->stream);
+        launch_gather_cols(s->geo, field, s->lv[h->cur], h->d_stage, h->own0[k], i1, h->stream);
     }
     SCUDA_TRY(h, cudaGetLastError());
     SCUDA_TRY(h, cudaMemcpyAsync(host_dst, h->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

@@ -265,6 +265,12 @@ void launch_derive_cols(const Geo &g, const Coef &c, const Level &lv, int i0, in
 void launch_scatter(const Geo &g, int field, const double *src, const Level &lv, void *stream);
 void launch_gather(const Geo &g, int field, const Level &lv, double *dst, void *stream);
 void launch_gather_cols(const Geo &g, int field, const Level &lv, double *dst, int i0, int i1, void *stream);
+// The FP64 u, v, T and Gamma of a mixed-precision level over columns
+// [i0, i1), from their FP32 values where the sweep computes them, and the
+// outflow ghost copies when the east side is an outflow: the mixed sweep keeps
+// those four fields in FP32 only.
+void launch_widen_mixed(const Geo &g, const Level &lv, const LevelT<float> &s32, bool east_outflow, int i0, int i1,
+                        void *stream);
 
 // Halo exchange of an x-decomposed problem: n copies of a block of `rows`
 // rows x `words` 4-byte words between two arrays (row pitches in words),

@@ -858,15 +858,12 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
 
 template <typename R, bool IMPL, bool TVD, bool WALLS>
 __device__ __forceinline__ void assemble_at(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev,
-                                            const LevelT<R> &old, R *__restrict__ T_out,
-                                            double *__restrict__ T64_out, const WorkT<R> &w, int c, uint16_t f,
-                                            int i, int j)
+                                            const LevelT<R> &old, R *__restrict__ T_out, const WorkT<R> &w, int c,
+                                            uint16_t f, int i, int j)
 {
     if (i < g.nx && j < g.ny && (f & F_FLUID)) {
         const R Tn = temperature<R, IMPL, TVD, WALLS>(g, k, prev, old, w, c, i, j);
         T_out[c] = Tn;
-        if constexpr (std::is_same<R, float>::value)
-            T64_out[c] = widen(Tn);
     }
     if (j < g.ny) {
         R uh = old.u[c], d = R(0);            // faces that are not unknowns: stored u, d = 0
@@ -885,12 +882,12 @@ __device__ __forceinline__ void assemble_at(const GeoT<R> &g, const CoefT<R> &k,
 }
 
 // One thread per position: T of the cell, u^/d^u of the u face, v^/d^v of
-// the v face.  The new T goes to T_out (compute precision) and, for the FP32
-// assembly of the mixed path, also to T64_out (the FP64 state).
+// the v face.  The new T goes to T_out, in the compute precision (the mixed
+// path's FP64 view of it is filled when the state is read: widen_mixed_at).
 template <typename R, bool IMPL, bool TVD>
 __device__ __forceinline__ void assemble_body(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev,
-                                              const LevelT<R> &old, R *__restrict__ T_out,
-                                              double *__restrict__ T64_out, const WorkT<R> &w, int i, int j)
+                                              const LevelT<R> &old, R *__restrict__ T_out, const WorkT<R> &w,
+                                              int i, int j)
 {
     if (i > g.nx || j > g.ny) return;
     const int c = Ix{g.pitch}(i, j);
@@ -914,16 +911,14 @@ __device__ __forceinline__ void assemble_body(const GeoT<R> &g, const CoefT<R> &
         pseudo_u<R, IMPL, TVD, false>(g, k, prev, old, w, c, i, j, uh, du);
         pseudo_v<R, IMPL, TVD, false>(g, k, prev, old, w, c, i, j, vh, dv);
         T_out[c] = Tn;
-        if constexpr (std::is_same<R, float>::value)
-            T64_out[c] = widen(Tn);
         w.uhat[c] = uh;
         w.du[c] = du;
         w.vhat[c] = vh;
         w.dv[c] = dv;
     } else if (f & F_INTERIOR) {
-        assemble_at<R, IMPL, TVD, false>(g, k, prev, old, T_out, T64_out, w, c, f, i, j);
+        assemble_at<R, IMPL, TVD, false>(g, k, prev, old, T_out, w, c, f, i, j);
     } else {
-        assemble_at<R, IMPL, TVD, true>(g, k, prev, old, T_out, T64_out, w, c, f, i, j);
+        assemble_at<R, IMPL, TVD, true>(g, k, prev, old, T_out, w, c, f, i, j);
     }
 }
 
@@ -991,6 +986,19 @@ __device__ __forceinline__ void outflow_copy(int j, int ny, int c, LevelT<R> L)
     const R vn = L.v[c];
     L.v[c + 1] = vn;
     L.v[c + 2] = vn;
+}
+
+// The outflow copies of p and rho alone: the FP64 values the mixed path's
+// sweep reads (its FP64 u, v, T and Gamma are filled when the state is read).
+__device__ __forceinline__ void outflow_copy_p_rho(int j, int ny, int c, const Level &L)
+{
+    if (j < ny) {
+        const double p = L.p[c], rho = L.rho[c];
+        L.p[c + 1] = p;
+        L.p[c + 2] = p;
+        L.rho[c + 1] = rho;
+        L.rho[c + 2] = rho;
+    }
 }
 
 // Eqs. pl18, pl19: velocities of the face unknowns from the new pressure,
@@ -1097,7 +1105,6 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
             if (fluid) {
                 nw.p[c] = pn;
                 nw.rho[c] = rho;
-                nw.gam[c] = widen(gm);
                 nw32.p[c] = narrow(pn);
                 nw32.rho[c] = narrow(rho);
                 nw32.gam[c] = gm;
@@ -1113,7 +1120,8 @@ __device__ __forceinline__ void pressure_mixed_body(const Geo &g, const Coef &k,
 // Mixed precision, Eqs. pl18, pl19: FP32 correction of the FP32 pseudo
 // velocities by the FP64 pressure difference.  u and v carry FP32 values in
 // this path: their residual differences are formed in FP32 and reduced as
-// FP64 bit patterns.
+// FP64 bit patterns, and the FP64 state holds them only once it is read
+// (widen_mixed_at).
 __device__ __forceinline__ void velocity_mixed_body(const Geo &g, const Level &nw, const LevelT<float> &old32,
                                                     const LevelT<float> &nw32, const WorkT<float> &w,
                                                     unsigned long long *res, int east_outflow, int i, int j,
@@ -1131,23 +1139,42 @@ __device__ __forceinline__ void velocity_mixed_body(const Geo &g, const Level &n
         const double pc = nw.p[c], pw = nw.p[c - 1], ps = nw.p[c - P];
         if (j < g.ny && (f & F_UACT)) {
             const float un32 = uh - du * narrow(pc - pw);
-            nw.u[c] = widen(un32);
             nw32.u[c] = un32;
             ru = ordered_bits(widen(un32 - uo));
         }
         if (i < g.nx && (f & F_VACT)) {
             const float vn32 = vh - dv * narrow(pc - ps);
-            nw.v[c] = widen(vn32);
             nw32.v[c] = vn32;
             rv = ordered_bits(widen(vn32 - vo));
         }
         if (east_outflow && i == g.nx - 1) {
-            outflow_copy(j, g.ny, c, nw);
+            outflow_copy_p_rho(j, g.ny, c, nw);
             outflow_copy(j, g.ny, c, nw32);
         }
     }
     if (!own) ru = rv = 0;
     block_max2(ru, rv, &res[0], &res[1]);
+}
+
+// The FP64 view of a mixed-precision level at position (i, j): u, v, T and
+// Gamma, which the sweep keeps in FP32 only, widened (exactly) where the
+// sweep computes them -- T and Gamma of fluid cells, u and v of the face
+// unknowns -- then, on an outflow side, the ghost copies of column nx - 1.
+// The other positions keep their FP64 values, which the sweep never changes,
+// so the view holds what a sweep storing FP64 copies would have stored.
+__device__ __forceinline__ void widen_mixed_at(const Geo &g, const Level &L, const LevelT<float> &S,
+                                               int east_outflow, int i, int j)
+{
+    if (i > g.nx || j > g.ny) return;
+    const int c = Ix{g.pitch}(i, j);
+    const uint16_t f = g.flag[c];
+    if (i < g.nx && j < g.ny && (f & F_FLUID)) {
+        L.T[c] = widen(S.T[c]);
+        L.gam[c] = widen(S.gam[c]);
+    }
+    if (j < g.ny && (f & F_UACT)) L.u[c] = widen(S.u[c]);
+    if (i < g.nx && (f & F_VACT)) L.v[c] = widen(S.v[c]);
+    if (east_outflow && i == g.nx - 1) outflow_copy(j, g.ny, c, L);
 }
 
 // ------------------------------------------------------- tile-list kernels
@@ -1263,13 +1290,11 @@ __device__ __forceinline__ void assemble_phase(const BatchPlan &bp, int prev, in
 {
     for_tiles<ONE>(bp, [&](const Inst &I, int i, int j) {
         if constexpr (PREC == PREC_MIXED)
-            assemble_body<float, IMPL, TVD>(I.g32, I.k32, I.lv32[prev], I.lv32[old], I.lv32[nw].T, I.lv[nw].T,
-                                           I.w32, i, j);
+            assemble_body<float, IMPL, TVD>(I.g32, I.k32, I.lv32[prev], I.lv32[old], I.lv32[nw].T, I.w32, i, j);
         else if constexpr (PREC == PREC_DF64)
-            assemble_body<df64, IMPL, TVD>(I.gdf, I.kdf, I.lvdf[prev], I.lvdf[old], I.lvdf[nw].T, nullptr, I.wdf,
-                                          i, j);
+            assemble_body<df64, IMPL, TVD>(I.gdf, I.kdf, I.lvdf[prev], I.lvdf[old], I.lvdf[nw].T, I.wdf, i, j);
         else
-            assemble_body<double, IMPL, TVD>(I.g, I.k, I.lv[prev], I.lv[old], I.lv[nw].T, nullptr, I.w, i, j);
+            assemble_body<double, IMPL, TVD>(I.g, I.k, I.lv[prev], I.lv[old], I.lv[nw].T, I.w, i, j);
     });
 }
 

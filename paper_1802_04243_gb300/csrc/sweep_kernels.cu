@@ -213,6 +213,14 @@ __global__ void k_gather(Geo g, int field, Level L, double *dst, int i0, int i1)
     dst[(size_t)j * w + i] = field_of(L, field)[Ix{g.pitch}(i, j)];
 }
 
+// FP64 view of a mixed-precision level over columns [i0, i1) (widen_mixed_at).
+__global__ void k_widen_mixed(Geo g, Level L, LevelT<float> S, int east_outflow, int i0, int i1)
+{
+    const int i = i0 + blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+    if (i >= i1) return;
+    widen_mixed_at(g, L, S, east_outflow, i, j);
+}
+
 // One 4-byte word of each halo block per thread; blockIdx.y picks the block.
 __global__ void k_halo_copies(const HaloCopy *copies, int n)
 {
@@ -453,6 +461,14 @@ void launch_gather_cols(const Geo &g, int field, const Level &lv, double *dst, i
     if (i1 <= i0) return;
     const dim3 grid((unsigned)((i1 - i0 + BX - 1) / BX), (unsigned)((g.ny + 1 + BY - 1) / BY));
     k_gather<<<grid, dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, field, lv, dst, i0, i1);
+}
+
+void launch_widen_mixed(const Geo &g, const Level &lv, const LevelT<float> &s32, bool east_outflow, int i0, int i1,
+                        void *stream)
+{
+    if (i1 <= i0) return;
+    const dim3 grid((unsigned)((i1 - i0 + BX - 1) / BX), (unsigned)((g.ny + 1 + BY - 1) / BY));
+    k_widen_mixed<<<grid, dim3(BX, BY), 0, (cudaStream_t)stream>>>(g, lv, s32, east_outflow ? 1 : 0, i0, i1);
 }
 
 void launch_halo_copies(const HaloCopy *copies, int n, int max_words, void *stream)
