@@ -575,10 +575,10 @@ def step_hbm(case, ms_per_step):
 # DRAM bytes per cell, from the case named; the commands are in profiles/.
 MIXED_KERNEL_NCU = {
     "case": _C4HALF + ", ncu --metrics (one kernel per capture)",
-    "faces": {"fma_pct": 19.2, "lsu_pct": 34.5, "fp64_pct": 0.0, "warps_active_pct": 85.4, "dram_bytes": 20.4},
-    "assemble": {"fma_pct": 24.9, "lsu_pct": 41.9, "fp64_pct": 0.0, "warps_active_pct": 46.5, "dram_bytes": 71.4},
-    "pressure": {"fma_pct": 12.7, "lsu_pct": 22.3, "fp64_pct": 75.6, "warps_active_pct": 70.3, "dram_bytes": 61.1},
-    "velocity": {"fma_pct": 9.4, "lsu_pct": 34.0, "fp64_pct": 24.8, "warps_active_pct": 88.4, "dram_bytes": 35.9},
+    "faces": {"fma_pct": 19.2, "lsu_pct": 34.5, "fp64_pct": 0.0, "warps_active_pct": 86.2, "dram_bytes": 20.1},
+    "assemble": {"fma_pct": 25.1, "lsu_pct": 43.0, "fp64_pct": 0.0, "warps_active_pct": 46.4, "dram_bytes": 68.0},
+    "pressure": {"fma_pct": 12.5, "lsu_pct": 24.3, "fp64_pct": 76.7, "warps_active_pct": 92.7, "dram_bytes": 57.8},
+    "velocity": {"fma_pct": 12.2, "lsu_pct": 37.2, "fp64_pct": 27.9, "warps_active_pct": 90.2, "dram_bytes": 34.4},
 }
 
 
