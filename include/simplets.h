@@ -104,7 +104,8 @@ typedef struct {
  *   inflow) times (1 + perturb xi), xi in [-1, 1) from splitmix64 of
  *   (seed ^ (field<<40 + j<<20 + i)); v = perturb U_in xi.
  * precision: SIM_FP64; SIM_MIXED (FP32 assembly and relaxation, FP64
- *   pressure accumulation, equation of state and residuals); SIM_DF64 (every
+ *   pressure accumulation, equation of state and residuals; u, v, T and
+ *   Gamma are FP32 values, widened into the FP64 state when read); SIM_DF64 (every
  *   kernel of the iteration in double-float arithmetic -- pairs of floats,
  *   about 48 significant bits -- on the FP32 pipe; the FP64 state is filled
  *   from it when read, and the residual maxima carry FP32 precision).

@@ -65,7 +65,7 @@ struct sim_s {
     double *d_state = nullptr;                 // u, v, p, T staged back to back (allocated on first use)
     unsigned *d_bad = nullptr;                 // admissibility flag of a staged state
     unsigned *h_bad = nullptr;                 // its pinned host copy
-    // mixed precision: FP32 shadow levels, FP32 scratch and grid factors
+    // mixed precision: FP32 levels, FP32 scratch and grid factors
     bool mixed = false;
     Mixed mx{};
     bool mx_dirty = false;                     // the FP64 u, v, T, Gamma lag behind the FP32 ones (mixed)

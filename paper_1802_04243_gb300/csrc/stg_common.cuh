@@ -132,8 +132,9 @@ struct Work : WorkT<double> {
 };
 
 // FP32 side of the mixed-precision sweep: FP32 grid factors and
-// coefficients, FP32 shadow copies of the three state levels (refreshed
-// whenever a level changes) and FP32 iteration scratch.
+// coefficients, FP32 levels (written from the FP64 ones whenever a level is
+// set; during the sweep they carry u, v, T and Gamma, whose FP64 values are
+// filled when the state is read) and FP32 iteration scratch.
 struct Mixed {
     GeoT<float> g;
     CoefT<float> k;
