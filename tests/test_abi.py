@@ -98,3 +98,16 @@ def test_null_arguments(lib):
     assert lib.sim_batch_set_tiles(None, 32, 8, 0) == sim.SIM_EINVAL
     lib.sim_destroy(None)
     assert lib.sim_last_error(None) == b"null handle"
+
+
+def test_every_translation_unit_is_built_and_the_fp32_units_keep_their_rounding():
+    # every .cu file of csrc/ goes into libsimplets.so; the FP32 and
+    # double-float units (per-phase and persistent kernels) are compiled
+    # without multiply-add contraction, so each compiled form of a body rounds
+    # the same way, and the FP64 units with it
+    import os
+    from paper_1802_04243_gb300 import build as B
+    on_disk = sorted(f for f in os.listdir(B.CSRC) if f.endswith(".cu"))
+    assert sorted(B.SOURCES) == on_disk
+    nofma = {f for f, flags in B.EXTRA_FLAGS.items() if "--fmad=false" in flags}
+    assert nofma == {"phase_mixed.cu", "step_mixed.cu", "phase_df64.cu", "step_df64.cu"}
