@@ -441,7 +441,7 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     one.tiles_x = tiles_x;
     one.tile0 = 0;
     k_na_plan<<<(n_tiles + 255) / 256, 256, 0, s>>>(one, inst, tiles, n_tiles);
-    const BatchPlan plan{inst, tiles, 1, n_tiles, 32, 8, n_tiles, one};
+    const BatchPlan plan{inst, tiles, 1, n_tiles, 32, 8, n_tiles, one, 0};
 
     // ------------------------------------------------- the time steps (S0-S9)
     const bool implicit = scheme & SIM_IMPLICIT, tvd = scheme & SIM_TVD;

@@ -193,7 +193,7 @@ struct HostGrid {
     std::vector<uint8_t> kind, side;           // over [-2, nx+2] x [-2, ny+2]
     int at(int i, int j) const { return (j + G) * P + (i + G); }
     bool in(int i, int j) const { return i >= -G && i <= nx + G && j >= -G && j <= ny + G; }
-    int k(int i, int j) const { return in(i, j) ? kind[at(i, j)] : K_WALL; }
+    int k(int i, int j) const { return in(i, j) ? (int)kind[at(i, j)] : (int)K_WALL; }
     // side of the nearest position of the extended grid (lookups one layer
     // beyond it, from the faces of the outermost ghost layer, stay inside)
     int side_at(int i, int j) const
