@@ -282,7 +282,9 @@ sim_status sim_batch_set_tiles(sim_batch_t batch, int tile_x, int tile_y, int ct
  * resident walks the tile list through every phase of the step (explicit
  * terms, face densities, assembly, pressure, velocity correction), with a
  * grid-wide barrier between the phases.  The phases run the same code as the
- * per-phase kernels.  Each barrier wait is bounded (2 s): a wait that runs out
+ * per-phase kernels.  The launch and the reset of its barrier are captured as
+ * the step's CUDA graph (replayed every step), or launched directly when the
+ * runtime refuses to capture the cooperative launch.  Each barrier wait is bounded (2 s): a wait that runs out
  * ends the step, and the next sim_batch_fields or sim_batch_residuals returns
  * SIM_ETIMEOUT.  Not available when a problem has a symmetry side (its ghost
  * refresh is a separate kernel).  sim_batch_tune also times this mode.
@@ -290,7 +292,9 @@ sim_status sim_batch_set_tiles(sim_batch_t batch, int tile_x, int tile_y, int ct
 sim_status sim_batch_set_persistent(sim_batch_t batch, int on);
 
 /* The batch's work distribution: out[0..3] = tile x, tile y, CTAs of the
- * per-phase kernels, 1 if each step is one persistent kernel. */
+ * per-phase kernels, and 0 for one launch per phase, 1 for one persistent
+ * kernel per step replayed from a CUDA graph, 2 for one persistent kernel per
+ * step launched directly (graph capture refused). */
 sim_status sim_batch_plan_info(sim_batch_t batch, int out[4]);
 
 /* Text of the last error on this batch (never NULL). */

@@ -1239,8 +1239,11 @@ struct sim_batch_s {
     size_t tiles_cap = 0;
     BatchPlan plan{};
     bool ghosts = false;                      // some problem has a symmetry side
-    // persistent step: one cooperative kernel per time step (persistent.cu)
+    // persistent step: one cooperative kernel per time step (persistent.cu),
+    // captured with the reset of its barrier in the step's CUDA graph, or
+    // launched directly if the capture is refused (persistent_direct)
     bool persistent = false;
+    bool persistent_direct = false;
     GridBarrier *d_bar = nullptr;
     unsigned *h_err = nullptr;                // pinned copy of the barrier's error word
     struct Graph { cudaGraphExec_t exec = nullptr; int result = 0; };
@@ -1444,16 +1447,14 @@ extern "C" sim_status sim_batch_step(sim_batch_t b, int n_steps, int scheme)
     if (!b) return SIM_EINVAL;
     if (n_steps < 0 || (scheme & ~3)) return bfail(b, SIM_EINVAL, "bad n_steps %d or scheme %d", n_steps, scheme);
     const bool implicit = scheme & SIM_IMPLICIT, tvd = scheme & SIM_TVD;
-    if (b->persistent) {                      // one cooperative launch per step
-        for (int step = 0; step < n_steps; step++) {
+    for (int step = 0; step < n_steps; step++) {
+        if (b->persistent && b->persistent_direct) {      // one cooperative launch per step
             const int result = enqueue_batch_step(b, b->cur, implicit, tvd, b->stream);
             if (result < 0) return bfail(b, SIM_ECUDA, "persistent step launch failed: %s",
                                          cudaGetErrorString(cudaGetLastError()));
             set_levels(b, result);
+            continue;
         }
-        return SIM_OK;
-    }
-    for (int step = 0; step < n_steps; step++) {
         sim_batch_s::Graph &g = b->graphs[b->cur][scheme];
         if (!g.exec) {
             if (!b->cap_stream)
@@ -1461,7 +1462,19 @@ extern "C" sim_status sim_batch_step(sim_batch_t b, int n_steps, int scheme)
             cudaGraph_t graph = nullptr;
             BCUDA_TRY(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
             g.result = enqueue_batch_step(b, b->cur, implicit, tvd, b->cap_stream);
-            BCUDA_TRY(b, cudaStreamEndCapture(b->cap_stream, &graph));
+            const cudaError_t ec = cudaStreamEndCapture(b->cap_stream, &graph);
+            if (g.result < 0 || ec != cudaSuccess) {
+                // the persistent step's cooperative launch was not captured:
+                // launch it directly from now on
+                if (graph) cudaGraphDestroy(graph);
+                const cudaError_t why = ec != cudaSuccess ? ec : cudaGetLastError();
+                cudaGetLastError();
+                if (!b->persistent)
+                    return bfail(b, SIM_ECUDA, "step capture failed: %s", cudaGetErrorString(why));
+                b->persistent_direct = true;
+                step--;
+                continue;
+            }
             cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
             cudaGraphDestroy(graph);
             if (e != cudaSuccess) {
@@ -1520,6 +1533,7 @@ extern "C" sim_status sim_batch_set_persistent(sim_batch_t b, int on)
         BCUDA_TRY(b, cudaMemset(b->d_bar, 0, sizeof(GridBarrier)));
     }
     b->persistent = on != 0;
+    b->persistent_direct = false;
     drop_graphs(b);
     return SIM_OK;
 }
@@ -1530,7 +1544,7 @@ extern "C" sim_status sim_batch_plan_info(sim_batch_t b, int out[4])
     out[0] = b->plan.tx;
     out[1] = b->plan.ty;
     out[2] = b->plan.grid;
-    out[3] = b->persistent ? 1 : 0;
+    out[3] = b->persistent ? (b->persistent_direct ? 2 : 1) : 0;
     return SIM_OK;
 }
 

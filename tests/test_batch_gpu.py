@@ -154,6 +154,7 @@ def test_persistent_step_equals_the_per_phase_launches(precision, implicit, tvd)
         assert b.plan_info()[3] == 1
         a.step(6)
         b.step(6)
+        assert b.plan_info()[3] == 1                # the step ran as a captured CUDA graph
         for q in range(len(cases)):
             fa, fb = a.fields(q), b.fields(q)
             ra, (rb, st) = a.residuals(q)[0], b.residuals(q)
