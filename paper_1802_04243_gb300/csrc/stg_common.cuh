@@ -101,6 +101,8 @@ struct LevelT {
 template <typename R>
 struct WorkT {
     R *ru_dy, *rv_dx;              // face densities (Eqs. pl10, pl11) times the face area: rho^u dy, rho^v dx
+                                   // (FP64: the assembly replaces them by a^px = rho^u dy d^u and
+                                   // a^py = rho^v dx d^v, the pressure kernel's coefficients, Eq. pl24)
     R *Fx, *Fy;                    // mass fluxes F^x = rho^u u dy, F^y = rho^v v dx (Eqs. pl8, pl9)
     R *DTx, *DTy;                  // T conductances of x and y faces, C^T1_f Gamma_harm dy / dx_c (Eqs. pl32, pl33)
     R *Bgc;                        // B Gamma at the corner (x^f_i, y^f_j), bilinear in the four cells
@@ -116,9 +118,11 @@ struct WorkT {
     // on the y face below node (i,j) for flow up (U) and down (D); v likewise
     R *psTx, *psTy, *psUx, *psUyU, *psUyD, *psVy, *psVxU, *psVxD;
     R *uexp, *vexp, *Texp;         // explicit convective terms (Eqs. pl15_11, pl31_1)
+    R *bpx, *bpy;                  // FP64: rho^u dy u^ and rho^v dx v^ of the faces, the pressure
+                                   // equation's source fluxes (Eq. pl24), stored by the assembly
 };
 
-constexpr int kWorkArrays = 28;
+constexpr int kWorkArrays = 30;
 // Arrays of one pool: three levels of six fields, then the scratch.
 constexpr int kPoolArrays = 3 * 6 + kWorkArrays;
 

@@ -856,6 +856,19 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     dv = Adx * r;
 }
 
+// The pressure equation's face terms of Eq. pl24, formed once per face where
+// the pseudo velocity and d are made (FP64; the pressure kernel would form
+// each twice, once for each cell sharing the face): the coefficient
+// a^p = rho^f area d replaces rho^f area in `ra`, the source flux
+// b^p = rho^f area u^ goes to `bp`.  The same products as the pressure kernel
+// formed, so the same bits.
+__device__ __forceinline__ void pressure_face_terms(double *ra, double *bp, int c, double uh, double d)
+{
+    const double r = ra[c];
+    ra[c] = r * d;
+    bp[c] = r * uh;
+}
+
 template <typename R, bool IMPL, bool TVD, bool WALLS>
 __device__ __forceinline__ void assemble_at(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &prev,
                                             const LevelT<R> &old, R *__restrict__ T_out, const WorkT<R> &w, int c,
@@ -871,6 +884,8 @@ __device__ __forceinline__ void assemble_at(const GeoT<R> &g, const CoefT<R> &k,
             pseudo_u<R, IMPL, TVD, WALLS>(g, k, prev, old, w, c, i, j, uh, d);
         w.uhat[c] = uh;
         w.du[c] = d;
+        if constexpr (std::is_same<R, double>::value)
+            pressure_face_terms(w.ru_dy, w.bpx, c, uh, d);
     }
     if (i < g.nx) {
         R vh = old.v[c], d = R(0);
@@ -878,6 +893,8 @@ __device__ __forceinline__ void assemble_at(const GeoT<R> &g, const CoefT<R> &k,
             pseudo_v<R, IMPL, TVD, WALLS>(g, k, prev, old, w, c, i, j, vh, d);
         w.vhat[c] = vh;
         w.dv[c] = d;
+        if constexpr (std::is_same<R, double>::value)
+            pressure_face_terms(w.rv_dx, w.bpy, c, vh, d);
     }
 }
 
@@ -915,6 +932,10 @@ __device__ __forceinline__ void assemble_body(const GeoT<R> &g, const CoefT<R> &
         w.du[c] = du;
         w.vhat[c] = vh;
         w.dv[c] = dv;
+        if constexpr (std::is_same<R, double>::value) {
+            pressure_face_terms(w.ru_dy, w.bpx, c, uh, du);
+            pressure_face_terms(w.rv_dx, w.bpy, c, vh, dv);
+        }
     } else if (f & F_INTERIOR) {
         assemble_at<R, IMPL, TVD, false>(g, k, prev, old, T_out, w, c, f, i, j);
     } else {
@@ -938,12 +959,30 @@ __device__ __forceinline__ void pressure_body(const GeoT<R> &g, const CoefT<R> &
         const int c = Ix{P}(i, j);
         if (g.flag[c] & F_FLUID) {
             const R dxi = at(g.x.d, i), dyj = at(g.y.d, j);
-            // rho^u dy and rho^v dx of the four faces (stored by the face kernel)
-            const R ru_w = w.ru_dy[c], ru_e = w.ru_dy[c + 1], rv_s = w.rv_dx[c], rv_n = w.rv_dx[c + P];
-            const R apw = ru_w * w.du[c], ape = ru_e * w.du[c + 1];
-            const R aps = rv_s * w.dv[c], apn = rv_n * w.dv[c + P];
-            const R bpw = ru_w * w.uhat[c], bpe = ru_e * w.uhat[c + 1];
-            const R bps = rv_s * w.vhat[c], bpn = rv_n * w.vhat[c + P];
+            // coefficients a^p and source fluxes b^p of the four faces: stored
+            // by the FP64 assembly; formed here from rho^u dy and rho^v dx (face
+            // kernel) and u^, d by the double-float sweep
+            R apw, ape, aps, apn, bpw, bpe, bps, bpn;
+            if constexpr (std::is_same<R, double>::value) {
+                apw = w.ru_dy[c];
+                ape = w.ru_dy[c + 1];
+                aps = w.rv_dx[c];
+                apn = w.rv_dx[c + P];
+                bpw = w.bpx[c];
+                bpe = w.bpx[c + 1];
+                bps = w.bpy[c];
+                bpn = w.bpy[c + P];
+            } else {
+                const R ru_w = w.ru_dy[c], ru_e = w.ru_dy[c + 1], rv_s = w.rv_dx[c], rv_n = w.rv_dx[c + P];
+                apw = ru_w * w.du[c];
+                ape = ru_e * w.du[c + 1];
+                aps = rv_s * w.dv[c];
+                apn = rv_n * w.dv[c + P];
+                bpw = ru_w * w.uhat[c];
+                bpe = ru_e * w.uhat[c + 1];
+                bps = rv_s * w.vhat[c];
+                bpn = rv_n * w.vhat[c + P];
+            }
             const R Tn = nw.T[c], inv_T = recip(Tn);
             // Eqs. pl23, pl24 divided by dt (the transient terms take the
             // cell's volume per unit time): the neighbour sum accumulates

@@ -96,6 +96,20 @@ def test_noalloc_matches_sim_step_on_two_calls_in_a_row(name):
     np.testing.assert_allclose(res, r2, rtol=1e-6, atol=1e-14)
 
 
+@pytest.mark.parametrize("nx,ny", [(1000, 250), (500, 500)])
+def test_noalloc_accepts_the_sizes_its_header_names(nx, ny):
+    # the header's examples of problems that fit the static scratch
+    import torch
+    case = W.channel(nx, ny, max(2, ny // 4), name="fits", mach_in=2.0, reynolds=200.0, seed=3)
+    with sim.Simulation(case) as s:
+        start = s.fields()
+    dev = {k: torch.from_numpy(start[k]).to("cuda") for k in "uvpT"}
+    torch.cuda.synchronize()
+    st, res = noalloc(case, dev, 1, torch.cuda.current_stream().cuda_stream)
+    assert st == sim.SIM_OK
+    assert np.all(np.isfinite(res))
+
+
 def test_noalloc_rejects_problems_larger_than_its_static_scratch():
     import torch
     case = W.c3_large()
