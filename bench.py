@@ -44,22 +44,23 @@ UNIT = "Mcell-steps/s"
 # The commands are in profiles/.
 _C4HALF = "2432x608 channel (the 4864x1216 channel at half resolution, 1,478,656 cells)"
 ASSEMBLE_FP64_COUNTS = {
-    "implicit-upwind": {"dfma": 51.15, "dadd": 43.90, "dmul": 41.38, "dram_bytes": 205.9, "fp64_pipe": 0.865,
+    "implicit-upwind": {"dfma": 51.15, "dadd": 43.90, "dmul": 33.52, "dram_bytes": 223.3, "fp64_pipe": 0.865,
                         "case": _C4HALF},
-    "implicit-tvd": {"dfma": 66.88, "dadd": 43.90, "dmul": 41.38, "dram_bytes": 265.3, "fp64_pipe": 0.875,
+    "implicit-tvd": {"dfma": 66.88, "dadd": 43.90, "dmul": 33.52, "dram_bytes": 281.8, "fp64_pipe": 0.873,
                      "case": _C4HALF},
-    "explicit-upwind": {"dfma": 41.31, "dadd": 25.21, "dmul": 45.32, "dram_bytes": 196.5, "fp64_pipe": 0.863,
+    "explicit-upwind": {"dfma": 41.31, "dadd": 25.21, "dmul": 37.45, "dram_bytes": 214.1, "fp64_pipe": 0.860,
                         "case": _C4HALF},
-    "explicit-tvd": {"dfma": 41.31, "dadd": 25.21, "dmul": 45.32, "dram_bytes": 196.5, "fp64_pipe": 0.863,
+    "explicit-tvd": {"dfma": 41.31, "dadd": 25.21, "dmul": 37.45, "dram_bytes": 214.1, "fp64_pipe": 0.860,
                      "case": _C4HALF},
 }
 # Algorithmic HBM bytes of k_assemble per cell: the previous iterate's u, v,
 # p, T, rho, Gamma, level n-1's u, v, T, rho, and the face arrays F^x, F^y,
-# D^T_x, D^T_y, B Gamma (corner), B Gamma dy/dx, B Gamma dx/dy, the two
-# cell-centre mass fluxes, the two cell pair sums and rho^u dy, rho^v dx (23
-# doubles read); T, u^, d^u, v^, d^v and the pressure equation's face terms
-# a^px, a^py, b^px, b^py written (9 doubles).
-ASSEMBLE_BYTES_PER_CELL = 32 * 8
+# D^T_x, D^T_y, B Gamma (corner) and its two control-volume conductances,
+# B Gamma dy/dx, B Gamma dx/dy, the two cell-centre mass fluxes, the two cell
+# pair sums and rho^u dy, rho^v dx (25 doubles read); T, u^, d^u, v^, d^v and
+# the pressure equation's face terms a^px, a^py, b^px, b^py written (9
+# doubles).
+ASSEMBLE_BYTES_PER_CELL = 34 * 8
 # Algorithmic HBM bytes of the method per cell (the sweep's own minimum with
 # perfect neighbour reuse): each loop-2 iteration reads u, v, p, T of the
 # previous iterate and of level n-1 and writes u, v, p, T (12 doubles); the

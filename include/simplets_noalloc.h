@@ -47,9 +47,9 @@ extern "C" {
  *
  * Scratch: one static 96 MiB device array holds three state levels, the
  * scratch of the sweep, the geometry tables and the residual words, about
- * 388 bytes per element of the padded grid (pitch x (ny + 5), pitch =
- * nx + 5 rounded up to a multiple of 8): up to about 259,000 elements,
- * e.g. 1000 x 250 or 500 x 500 cells.  A larger problem returns SIM_ENOMEM
+ * 404 bytes per element of the padded grid (pitch x (ny + 5), pitch =
+ * nx + 5 rounded up to a multiple of 8): up to about 249,000 elements,
+ * e.g. 1000 x 240 or 490 x 490 cells.  A larger problem returns SIM_ENOMEM
  * before any work is queued.
  *
  * First call on a device: it looks up the device address of the static

@@ -407,6 +407,7 @@ extern "C" sim_status sim_step_noalloc(const sim_grid *grid, const sim_gas *gas,
     double **lim[8] = {&w.psTx, &w.psTy, &w.psUx, &w.psUyU, &w.psUyD, &w.psVy, &w.psVxU, &w.psVxD};
     for (double **x : lim) { *x = q; q += nelem; }
     w.bpx = q; q += nelem; w.bpy = q; q += nelem;
+    w.Bgcu = q; q += nelem; w.Bgcv = q; q += nelem;
     w.res = res;
 
     Geo g{};

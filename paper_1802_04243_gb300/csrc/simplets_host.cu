@@ -430,7 +430,7 @@ R *carve_levels(R *q, size_t nelem, LevelT<R> lv[3], WorkT<R> &w)
     R **a[kWorkArrays] = {&w.ru_dy, &w.rv_dx, &w.Fx, &w.Fy, &w.DTx, &w.DTy, &w.Bgc, &w.Bgx, &w.Bgy,
                           &w.Fbu, &w.Fbv, &w.Su, &w.Sv, &w.uhat, &w.du, &w.vhat, &w.dv, &w.uexp, &w.vexp, &w.Texp,
                           &w.psTx, &w.psTy, &w.psUx, &w.psUyU, &w.psUyD, &w.psVy, &w.psVxU, &w.psVxD,
-                          &w.bpx, &w.bpy};
+                          &w.bpx, &w.bpy, &w.Bgcu, &w.Bgcv};
     for (R **x : a) { *x = q; q += nelem; }
     return q;
 }
@@ -448,7 +448,7 @@ void shift_views(LevelT<R> lv[3], WorkT<R> &w, long d)
     R **a[kWorkArrays] = {&w.ru_dy, &w.rv_dx, &w.Fx, &w.Fy, &w.DTx, &w.DTy, &w.Bgc, &w.Bgx, &w.Bgy,
                           &w.Fbu, &w.Fbv, &w.Su, &w.Sv, &w.uhat, &w.du, &w.vhat, &w.dv, &w.uexp, &w.vexp, &w.Texp,
                           &w.psTx, &w.psTy, &w.psUx, &w.psUyU, &w.psUyD, &w.psVy, &w.psVxU, &w.psVxD,
-                          &w.bpx, &w.bpy};
+                          &w.bpx, &w.bpy, &w.Bgcu, &w.Bgcv};
     for (R **x : a) *x -= d;
 }
 

@@ -120,9 +120,12 @@ struct WorkT {
     R *uexp, *vexp, *Texp;         // explicit convective terms (Eqs. pl15_11, pl31_1)
     R *bpx, *bpy;                  // FP64: rho^u dy u^ and rho^v dx v^ of the faces, the pressure
                                    // equation's source fluxes (Eq. pl24), stored by the assembly
+    R *Bgcu, *Bgcv;                // FP64: B Gamma at the corner (i,j) times dc_x(i)/dc_y(j) and times
+                                   // dc_y(j)/dc_x(i): the diffusive conductances of the u control
+                                   // volumes' y faces and of the v control volumes' x faces
 };
 
-constexpr int kWorkArrays = 30;
+constexpr int kWorkArrays = 32;
 // Arrays of one pool: three levels of six fields, then the scratch.
 constexpr int kPoolArrays = 3 * 6 + kWorkArrays;
 

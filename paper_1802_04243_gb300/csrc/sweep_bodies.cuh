@@ -453,7 +453,15 @@ __device__ __forceinline__ void face_densities_body(const GeoT<R> &g, const Coef
         w.Fy[c] = rdx * vel;
         w.DTy[c] = conductance(gam[c - P], gam[c], at(g.y.d, j - 1), dyj, face_ct2(g.x, i, ct1f2, dxi));
     }
-    w.Bgc[c] = k.B * gamma_corner(g, gam, c, i, j);
+    const R bgc = k.B * gamma_corner(g, gam, c, i, j);
+    w.Bgc[c] = bgc;
+    if constexpr (std::is_same<R, double>::value) {
+        // the corner's conductances of the u and v control volumes, formed
+        // once here instead of by the two faces sharing the corner in the
+        // assembly (the same products in the same order, so the same bits)
+        w.Bgcu[c] = bgc * at(g.x.dc, i) * at(g.y.rc, j);
+        w.Bgcv[c] = bgc * at(g.y.dc, j) * at(g.x.rc, i);
+    }
     if (i < g.nx && j < g.ny) {
         const R bg = k.B * gam[c];
         w.Bgx[c] = bg * dyj * at(g.x.rd, i);
@@ -719,9 +727,15 @@ __device__ void pseudo_u(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     const R Fs1 = w.Fy[a - 1], Fs2 = w.Fy[a], Fn1 = w.Fy[a - 1 + P], Fn2 = w.Fy[a + P];
     const R gcs = w.Bgc[a], gcn = w.Bgc[a + P];      // B Gamma at the corners (i, j), (i, j+1)
     const R Dxw = w.Bgx[a - 1], Dxe = w.Bgx[a];
-    const R cx = at(g.x.dc, i);                      // centre distance of cells i-1, i: half the CV width
-    const R Dys = gcs * cx * at(g.y.rc, j);
-    const R Dyn = gcn * cx * at(g.y.rc, j + 1);
+    R Dys, Dyn;                                      // conductances of the CV's y faces (corners j, j+1)
+    if constexpr (std::is_same<R, double>::value) {
+        Dys = w.Bgcu[a];
+        Dyn = w.Bgcu[a + P];
+    } else {
+        const R cx = at(g.x.dc, i);                  // centre distance of cells i-1, i: half the CV width
+        Dys = gcs * cx * at(g.y.rc, j);
+        Dyn = gcn * cx * at(g.y.rc, j + 1);
+    }
     // dy / (2 dt): tabulated in FP64 (a load instead of an FP64 multiply)
     R vdt;
     if constexpr (std::is_same<R, double>::value)
@@ -798,9 +812,15 @@ __device__ void pseudo_v(const GeoT<R> &g, const CoefT<R> &k, const LevelT<R> &p
     const R uw1 = u[b - P], uw2 = u[b], ue1 = u[b + 1 - P], ue2 = u[b + 1];
     const R Fw1 = w.Fx[b - P], Fw2 = w.Fx[b], Fe1 = w.Fx[b + 1 - P], Fe2 = w.Fx[b + 1];
     const R gcw = w.Bgc[b], gce = w.Bgc[b + 1];      // B Gamma at the corners (i, j), (i+1, j)
-    const R cy = at(g.y.dc, j);                      // centre distance of cells j-1, j: half the CV height
-    const R Dxw = gcw * cy * at(g.x.rc, i);
-    const R Dxe = gce * cy * at(g.x.rc, i + 1);
+    R Dxw, Dxe;                                      // conductances of the CV's x faces (corners i, i+1)
+    if constexpr (std::is_same<R, double>::value) {
+        Dxw = w.Bgcv[b];
+        Dxe = w.Bgcv[b + 1];
+    } else {
+        const R cy = at(g.y.dc, j);                  // centre distance of cells j-1, j: half the CV height
+        Dxw = gcw * cy * at(g.x.rc, i);
+        Dxe = gce * cy * at(g.x.rc, i + 1);
+    }
     const R Dys = w.Bgy[b - P], Dyn = w.Bgy[b];
     R vdt;
     if constexpr (std::is_same<R, double>::value)

@@ -96,7 +96,7 @@ def test_noalloc_matches_sim_step_on_two_calls_in_a_row(name):
     np.testing.assert_allclose(res, r2, rtol=1e-6, atol=1e-14)
 
 
-@pytest.mark.parametrize("nx,ny", [(1000, 250), (500, 500)])
+@pytest.mark.parametrize("nx,ny", [(1000, 240), (490, 490)])
 def test_noalloc_accepts_the_sizes_its_header_names(nx, ny):
     # the header's examples of problems that fit the static scratch
     import torch
